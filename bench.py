@@ -1,0 +1,305 @@
+"""Benchmark: plain phase-screen synthesis (quasi-random frequency sampling, Eq. 3).
+
+Workload (the case the metric is quoted on): an 8 m circular pupil sampled on a
+256 x 256 grid (51,468 interior points, FP32 coordinates), von Karman PSD
+r0 = 0.15 m, L0 = 30 m, log-radial frequency domain [1e-3, 16] cycles/m,
+N_f = 4096 frequencies drawn per realisation (continuing R2 stream), 1000
+realisations per step.  One step = the whole hot path: per-realisation draw
+(Philox + R2 + FP64 map + weights + coefficients) and the Eq. 3 sum at every
+point, fused in libqrs's persistent kernel, FP32 output [1000 x 51,468].
+
+Printed: one JSON line.  `value` = freq-term evals/s (point x term x
+realisation) over all ranks, inputs resident on the device; `e2e` = the same
+through the C ABI with host buffers (pinned H2D of the points, D2H of the
+field) inside the timed region; `roofline` = the fused kernel against the
+MUFU (sin/cos) bound of the GPU; `cpu_baseline` = the FP64 CPU reference on a
+bounded sample on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): each rank synthesises its own 1000 realisations
+(real_offset = rank * 1000), no collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+MEASURED_PEAKS = os.path.join(HERE, "MEASURED_PEAKS.json")
+N_SM = 152
+MUFU_PER_SM_CLK = 16  # sin.approx / cos.approx results per SM per clock (measured, GB300)
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 256 << 20
+METRIC = "freq-term evals/s"
+UNIT = "term/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _workload():
+    from paper_2404_02978_gb300 import workloads as wl
+    cfg = wl.PHASE_SCREEN
+    xy = wl.pupil_grid(cfg["grid"], cfg["pupil"])
+    return cfg, wl.method_params(cfg), xy
+
+
+def _config(cfg, xy, world):
+    return {"workload": "phase screen: 8 m pupil 256x256 grid (%d points), von Karman r0=0.15 m L0=30 m, "
+                        "log-radial [1e-3,16] c/m, N_f=%d per-realisation R2 draws, %d realisations/step"
+                        % (xy.shape[0], cfg["n_f"], cfg["n_real"]),
+            "points": int(xy.shape[0]), "n_f": cfg["n_f"], "realizations_per_step": cfg["n_real"],
+            "form": "fused draw+sincos (per-realisation draws)", "parallelism": "realisations sharded, dp%d" % world,
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def cpu_baseline(cfg, p, xy, n_real=2):
+    """The FP64 CPU reference (as it stands, single thread) on n_real full realisations."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.synthesize(p, cfg["n_f"], n_real, xy)
+    dt = time.perf_counter() - t0
+    terms = n_real * xy.shape[0] * cfg["n_f"]
+    return {"value": terms / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d of %d realisations, all %d points, N_f=%d (%.3g terms in %.1f s), single thread FP64"
+                      % (n_real, cfg["n_real"], xy.shape[0], cfg["n_f"], terms, dt),
+            "host": _host()}
+
+
+def _host():
+    try:
+        model = [l.split(":", 1)[1].strip() for l in open("/proc/cpuinfo") if l.lower().startswith(("model name",))]
+    except OSError:
+        model = []
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+            model = [l.split(":", 1)[1].strip() for l in out.splitlines() if l.startswith("Model name")]
+        except OSError:
+            model = []
+    return "%s x%d" % (model[0] if model else "unknown", os.cpu_count() or 0)
+
+
+def run_reference(a):
+    """--impl reference: the FP64 CPU oracle on a bounded sample per step (rank 0 only)."""
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cfg, p, xy = _workload()
+    sample = xy[:8192]
+    per_step = sample.shape[0] * cfg["n_f"]
+    for w in range(a.warmup):
+        oracle.synthesize(p, cfg["n_f"], 1, sample, real_offset=w)
+    t0 = time.perf_counter()
+    for s in range(a.steps):
+        oracle.synthesize(p, cfg["n_f"], 1, sample, real_offset=a.warmup + s)
+    dt = time.perf_counter() - t0
+    v = per_step * a.steps / dt
+    desc = "1 realisation x first 8192 of %d points x N_f=%d per step, single thread FP64" % (xy.shape[0], cfg["n_f"])
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(cfg, xy, 1),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "host": _host()},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_ours(a):
+    import torch
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2404_02978_gb300 import build as B
+    B.build()
+    import paper_2404_02978_gb300 as qrs
+    cfg, p, xy_np = _workload()
+    h = qrs.Handle(local)
+    dev = torch.device("cuda", local)
+    xy = torch.from_numpy(xy_np).to(dev)
+    R, nf, P = cfg["n_real"], cfg["n_f"], xy_np.shape[0]
+    out = torch.empty(R, P, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    off0 = rank * R
+
+    def step(i):
+        qrs.qrs_synthesize_points(h, p, nf, R, xy, out=out, real_offset=off0, stream=stream)
+
+    for w in range(a.warmup):
+        step(w)
+    qrs.qrs_sync(h, stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    barrier()
+    clocks.start()
+    launches0 = h.launch_count()
+    t_wall = time.perf_counter()
+    for i in range(a.steps):
+        flush.zero_()  # untimed: evicts L2 between timed steps
+        ev[i][0].record(stream)
+        step(i)
+        ev[i][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    launches = h.launch_count() - launches0
+    clk = clocks.stop()
+    qrs.qrs_sync(h, stream)
+    times = [s.elapsed_time(e) for s, e in ev]  # ms, device clock, per step
+    t_step = sum(times) / len(times)
+    t_tot = sum(times) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_tot = float(tt.item())
+    terms_step = P * nf * R
+    value = terms_step * a.steps * world / t_tot
+
+    # end to end through the C ABI with host buffers: pinned H2D of the points,
+    # the synthesis, D2H of the field, every step
+    xy_host = torch.from_numpy(xy_np).pin_memory()
+    out_host = torch.empty(R, P, dtype=torch.float32).pin_memory()
+    xy_dev2 = torch.empty_like(xy)
+    e2e_steps = max(2, min(a.steps, 5))
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        xy_dev2.copy_(xy_host, non_blocking=True)
+        qrs.qrs_synthesize_points(h, p, nf, R, xy_dev2, out=out, real_offset=off0, stream=stream)
+        out_host.copy_(out, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    t_e2e = e0.elapsed_time(e1) / 1e3
+    e2e_value = terms_step * e2e_steps * world / t_e2e
+
+    peaks = {}
+    if os.path.exists(MEASURED_PEAKS):
+        peaks = json.load(open(MEASURED_PEAKS))
+    sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ))
+    peak_terms = N_SM * MUFU_PER_SM_CLK / 2 * sm_max * 1e6  # 2 MUFU (sin, cos) per term
+    achieved = terms_step / (t_step / 1e3)  # per launch, one GPU
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": _config(cfg, xy_np, world),
+        "realizations_per_s": R * a.steps * world / t_tot,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_terms / 1e9, "unit": "Gterm/s",
+                     "frac": achieved / peak_terms, "traffic": None,
+                     "kernel": "k_synth_fused (+ k_point_bound prepass, <0.01%)",
+                     "peak_basis": "152 SM x 16 sin|cos per SM-clock (measured) / 2 per term x %.0f MHz max clock"
+                                   % sm_max},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xy_np.nbytes),
+                "d2h_bytes_per_step": int(R * P * 4), "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "wall_s": t_wall,
+    }
+    if clk:
+        line["clocks"] = clk
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

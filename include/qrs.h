@@ -1,0 +1,248 @@
+/*
+ * qrs.h -- C ABI of libqrs, quasi-random frequency-sampling synthesis of
+ * optical-turbulence fields on one GB300 (sm_103a).
+ *
+ * Method: Berdja, Hadjara, Carbillet, Bernardi, Petrov, "Quasi-Random
+ * Frequency Sampling for Optical Turbulence Simulations" (arXiv 2404.02978).
+ * A realisation of a field with phase PSD W is the direct sum of Eq. 3,
+ *     chi(x) = sum_k F_k (a_k cos 2 pi f_k.x - b_k sin 2 pi f_k.x),
+ * F_k = sqrt(W(f_k) J_k / N_f), over N_f frequencies f_k placed by the R2
+ * low-discrepancy sequence of Eq. 6 (mapped by Eq. 5 to a square, by the
+ * square-to-disc map of Sec. 3.2 to a disc, or log-radially to an annulus),
+ * the sequence continuing across realisations (Sec. 3.2).  Pistons filter the
+ * PSD by the aperture factor of Eq. 7 (Sec. 4.1); their pair differences and
+ * structure functions are the statistics of Sec. 4.4.
+ *
+ * Conventions shared by every entry point
+ *   - Array arguments are DEVICE pointers on the handle's device unless the
+ *     comment says "host".  The caller owns them; the library never frees or
+ *     retains them after the call returns.  Parameter structs are host memory,
+ *     read during the call only.
+ *   - Layouts are C order (last index fastest), FP32 unless stated.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and the call returns without synchronising.  Argument errors are
+ *     detected on the host before anything is enqueued and return a negative
+ *     qrs_status with nothing launched; qrs_last_error() gives the reason.
+ *   - Errors detected on the device (a bounded wait that ran out) set a device
+ *     error word that qrs_sync() reports.  The library never aborts, traps or
+ *     prints.
+ *   - Results are a pure function of the inputs, the seed and real_offset:
+ *     one call over realisations [0, R) equals two calls over [0, R1) and
+ *     [R1, R) with real_offset 0 and R1 (checkpoint / resume by counter).
+ *   - Not thread-safe per handle: one host thread drives one handle.
+ */
+#ifndef QRS_H
+#define QRS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QRS_OK = 0,
+    QRS_ERR_ARG = -1,          /* invalid argument (size, pointer, enum, alignment) */
+    QRS_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+    QRS_ERR_TIMEOUT = -3,      /* a bounded device wait ran out (device error word) */
+    QRS_ERR_UNSUPPORTED = -4,  /* valid request this build does not provide */
+    QRS_ERR_NOMEM = -5,        /* workspace allocation failed */
+    QRS_ERR_DEVICE_CHECK = -6  /* a device-side check failed (device error word) */
+} qrs_status;
+
+/* PSD of the phase (Eq. 7, first factor): W(f) = c r0^(-5/3) (f^2 + L0^-2)^(-11/6),
+ * c = Gamma(11/6)^2/(2 pi^(11/3)) (24/5 Gamma(6/5))^(5/6) = 0.0228955871...
+ * (the paper prints its truncation 0.02289).  KOLMOGOROV drops L0^-2. */
+#define QRS_PSD_VON_KARMAN 0
+#define QRS_PSD_KOLMOGOROV 1
+
+/* Frequency domains (unit square [0,1)^2 -> frequency plane, cycles/m):
+ *   SQUARE   f = fmax (2 s - 1) per axis, the map of Eq. 5 with
+ *            delta_f N = 2 max f; cell factor J = (2 fmax)^2.
+ *   DISC     Shirley-Chiu concentric square-to-disc map of radius fmax
+ *            (Sec. 3.2 remark); J = pi fmax^2.
+ *   LOGPOLAR rho = fmin (fmax/fmin)^s_x, theta = 2 pi s_y; J = 2 pi ln(fmax/fmin) rho^2.
+ * The weight of a term is w = W(f) J / N_f (Eq. 3's delta_fx delta_fy for a
+ * cell of the square), F = sqrt(w). */
+#define QRS_DOMAIN_SQUARE 0
+#define QRS_DOMAIN_DISC 1
+#define QRS_DOMAIN_LOGPOLAR 2
+
+/* Placement of the N_f terms of a realisation:
+ *   R2         the R2 sequence of Eq. 6 in exact 0.64 fixed point, point
+ *              n = (real_offset + r) N_f + k of one stream (Sec. 3.2: never
+ *              re-initialised); seed s0 = Philox(seed) or the fixed s0 given.
+ *   JITTER     Eq. 4: one uniformly jittered point per cell of an
+ *              n_rho x n_theta grid on the unit square (N_f = n_rho n_theta).
+ *   UNIFORM    independent uniform points (Sec. 2.3 "fully random").
+ *   IMPORTANCE cells of an n_rho (log-radial) x n_theta (angular) grid over
+ *              [fmin, fmax] chosen by inverse CDF of the R2 x-coordinate's top
+ *              32 bits against `cell_cdf`, placed area-uniformly inside the
+ *              cell by the rest of the R2 point; J = area_c / p_c, which keeps
+ *              the sum unbiased (learned proposal).  Domain must be LOGPOLAR. */
+#define QRS_SAMPLER_R2 0
+#define QRS_SAMPLER_JITTER 1
+#define QRS_SAMPLER_UNIFORM 2
+#define QRS_SAMPLER_IMPORTANCE 3
+
+/* Coefficients of Eq. 3 (from Philox4x32-10 words, counter (n, stream)):
+ *   GAUSS  a, b ~ N(0,1) i.i.d. by Box-Muller from 24-bit uniforms
+ *          U1 = (w2>>8 + 1) 2^-24, U2 = (w3>>8) 2^-24.
+ *   EQ3    the paper's literal sqrt(2) R_n cos(2 pi (f.x + R_u)):
+ *          a = sqrt2 R_n cos 2 pi R_u, b = sqrt2 R_n sin 2 pi R_u,
+ *          R_n the GAUSS a, R_u = (v0>>8) 2^-24 from stream 2.
+ * Both give every term variance F^2 (Eq. 3's 2/sqrt(2) factor). */
+#define QRS_COEF_GAUSS 0
+#define QRS_COEF_EQ3 1
+
+typedef struct qrs_psd {
+    double r0_m;   /* Fried parameter at the simulated wavelength, m (> 0) */
+    double L0_m;   /* outer scale, m (> 0; ignored for KOLMOGOROV) */
+    int32_t kind;  /* QRS_PSD_* */
+    int32_t reserved;
+} qrs_psd;
+
+typedef struct qrs_domain {
+    double fmin;   /* cycles/m; LOGPOLAR only (> 0) */
+    double fmax;   /* cycles/m (> 0) */
+    int32_t kind;  /* QRS_DOMAIN_* */
+    int32_t reserved;
+} qrs_domain;
+
+typedef struct qrs_sampler {
+    uint64_t seed;             /* Philox key (low word, high word) */
+    uint64_t s0[2];            /* fixed R2 seed in 0.64 fixed point, if use_fixed_s0 */
+    const uint32_t* cell_cdf;  /* device [n_rho*n_theta]: cell start points, cdf[0] = 0,
+                                  strictly increasing (every cell width >= 1), implicit
+                                  end 2^32.  IMPORTANCE only, else NULL. */
+    int32_t kind;              /* QRS_SAMPLER_* */
+    int32_t coef_kind;         /* QRS_COEF_* */
+    int32_t use_fixed_s0;      /* 0: s0 = Philox(key=seed, ctr=(0,0,1,0)); 1: s0 above */
+    int32_t n_rho;             /* cell grid (cell ids, JITTER grid, IMPORTANCE cells) >= 1 */
+    int32_t n_theta;           /* >= 1 */
+    int32_t reserved;
+} qrs_sampler;
+
+typedef struct qrs_handle qrs_handle;
+
+/* Create a handle on CUDA device `device` (makes it current for the calling
+ * thread).  The handle owns small device workspaces (error word, launch
+ * descriptors) and its autotune cache.  *h = NULL on failure. */
+qrs_status qrs_create(qrs_handle** h, int32_t device);
+void qrs_destroy(qrs_handle* h);
+/* Last error message of this handle ("" if none); valid until the next call. */
+const char* qrs_last_error(const qrs_handle* h);
+/* Synchronise `stream`, then read and clear the device error word:
+ * QRS_OK, QRS_ERR_TIMEOUT or QRS_ERR_DEVICE_CHECK. */
+qrs_status qrs_sync(qrs_handle* h, void* stream);
+/* Number of kernel launches this handle has enqueued since creation. */
+int64_t qrs_launch_count(const qrs_handle* h);
+
+/* ---------------------------------------------------------------- draw ---
+ * The frequency draw of n_real realisations x n_f terms (Eq. 3 weights, Eq. 5/6
+ * placement, Sec. 3.2 continuation), realisations real_offset .. +n_real-1.
+ * Every output may be NULL; sizes in elements:
+ *   f_xy  [n_real][n_f][2]  FP32 frequency (cycles/m), the round-to-nearest of
+ *                           the FP64 map (within 1 ulp where FP64 exp/sin differ)
+ *   amp   [n_real][n_f]     F_k = sqrt(W(f_k) J_k / N_f), FP32
+ *   coef  [n_real][n_f][2]  (a_k, b_k), FP32
+ *   cell  [n_real][n_f]     cell id i_rho n_theta + i_theta (exact)
+ *   words [n_real][n_f][4]  Philox4x32-10 words of counter (n, 0) (exact)
+ *   r2    [n_real][n_f][2]  R2 state in 0.64 fixed point (exact; 0 if not R2/IMPORTANCE)
+ * n_f in [1, 2^31), n_real >= 0 (0 is a no-op), real_offset >= 0. */
+typedef struct qrs_draw_out {
+    float* f_xy;
+    float* amp;
+    float* coef;
+    int32_t* cell;
+    uint32_t* words;
+    uint64_t* r2;
+} qrs_draw_out;
+
+qrs_status qrs_draw(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, const qrs_sampler* smp,
+                    int64_t n_f, int64_t n_real, int64_t real_offset, const qrs_draw_out* out,
+                    void* stream);
+
+/* ---------------------------------------------------------- synthesis ---
+ * Eq. 3 at arbitrary points (Sec. 3: "simulate at specific areas of
+ * interest"): out[r][m] = sum_k F_k (a_k cos 2 pi phi_mk - b_k sin 2 pi phi_mk),
+ * phi_mk = f_k . x_m reduced mod 1 in double-float (error-free products), FP32
+ * accumulation.
+ *   xy   [n_points][2]  FP32 point coordinates, m
+ *   out  [n_real][n_points]  FP32
+ * mode:
+ *   QRS_SYNTH_FUSED       per-realisation draw (realisation r uses stream points
+ *                         (real_offset + r) N_f + k), draw and sincos-accumulate
+ *                         fused in one persistent kernel; col_psd must be NULL.
+ *   QRS_SYNTH_GEMM_*      shared draw: all n_real columns use the frequencies of
+ *                         realisation real_offset; column r takes its coefficients
+ *                         from stream points (real_offset + r) N_f + k and, if
+ *                         col_psd != NULL, its own (r0, L0) = col_psd[r][0..1]
+ *                         (device FP64 [n_real][2]) in the weight.  The sum is the
+ *                         product of the [n_points x 2 n_f] cos/sin basis and the
+ *                         [2 n_f x n_real] coefficient matrix on the tensor cores:
+ *                         3XTF32 (split TF32, ~FP32 accuracy) or BF16X3 (split
+ *                         BF16, ~2^-16 relative).
+ * Column 0 of a GEMM-mode call equals realisation real_offset of a FUSED call. */
+#define QRS_SYNTH_FUSED 0
+#define QRS_SYNTH_GEMM_3XTF32 1
+#define QRS_SYNTH_GEMM_BF16X3 2
+
+qrs_status qrs_synthesize_points(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom,
+                                 const qrs_sampler* smp, int64_t n_f, int64_t n_real,
+                                 int64_t real_offset, const float* xy, int64_t n_points,
+                                 int32_t mode, const double* col_psd, float* out, void* stream);
+
+/* ------------------------------------------------------------- pistons ---
+ * Differential pistons (Sec. 4.1, 4.4; PSD and filter of Eq. 7):
+ *   piston[r][a] = sum_k F_k A_a(|f_k|) (a_k cos 2 pi f_k.p_a - b_k sin 2 pi f_k.p_a),
+ *   A_a(f) = 2 (D_a J1(pi D_a f) - d_a J1(pi d_a f)) / (pi (D_a^2 - d_a^2) f), A(0) = 1,
+ *   delta[r][q] = piston[r][i_q] - piston[r][j_q]  for pairs[q] = (i_q, j_q).
+ * One job is one interferometer (its own PSD, domain, sampler, N_f, R).
+ *   ap_xy [n_ap][2] aperture centres (m), ap_D, ap_d [n_ap] outer and
+ *   obstruction diameters (m, 0 <= d < D), pairs [n_pairs][2] int32 in [0, n_ap),
+ *   piston [n_real][n_ap] or NULL, delta [n_real][n_pairs] or NULL.
+ * n_ap in [1, 64].  flags: QRS_PISTON_PERSISTENT runs all jobs in one
+ * persistent launch over a cost-sorted work queue (bounded waits); with
+ * QRS_PISTON_GRAPH the launch sequence is captured once per job set into a
+ * CUDA graph and replayed.  Without flags, one launch per job. */
+#define QRS_PISTON_PERSISTENT 1
+#define QRS_PISTON_GRAPH 2
+
+typedef struct qrs_piston_job {
+    qrs_psd psd;
+    qrs_domain dom;
+    qrs_sampler smp;
+    int64_t n_f;
+    int64_t n_real;
+    int64_t real_offset;
+    const float* ap_xy;
+    const float* ap_D;
+    const float* ap_d;
+    const int32_t* pairs;
+    float* piston;
+    float* delta;
+    int32_t n_ap;
+    int32_t n_pairs;
+} qrs_piston_job;
+
+qrs_status qrs_diff_piston(qrs_handle* h, const qrs_piston_job* jobs, int32_t n_jobs, int32_t flags,
+                           void* stream);
+
+/* --------------------------------------------------- structure function ---
+ * Sec. 4.4: for series s and lag L = lags[l],
+ *   L >= 1: x = v[t+L] - v[t], t in [0, T-L)   (temporal structure function)
+ *   L == 0: x = v[t], t in [0, T)              (the value itself: over a baseline
+ *                                               this is the spatial structure function)
+ * acc[s][l][0..2] += (sum x^2, sum x^4, count) over all realisations and t, FP64
+ * (x formed in FP64 from FP32 inputs).  The caller zeroes acc once; calls
+ * accumulate, so the sums of a chunked run equal those of one run up to FP64
+ * rounding order.
+ *   delta [n_real][n_series][T] FP32, lags [n_lags] int32 in [0, T), acc FP64. */
+qrs_status qrs_structure_fn(qrs_handle* h, const float* delta, int64_t n_real, int64_t n_series,
+                            int64_t T, const int32_t* lags, int32_t n_lags, double* acc, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QRS_H */

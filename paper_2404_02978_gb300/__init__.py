@@ -1,0 +1,266 @@
+"""Python binding of libqrs: quasi-random frequency-sampling turbulence synthesis
+on one GB300 (sm_103a).
+
+Thin marshalling over the C ABI declared in ``include/qrs.h`` (ctypes; torch
+tensors are used only as device buffers and for the current CUDA stream).
+Every step of the computation runs in libqrs's CUDA kernels; there is no CPU
+or PyTorch fallback: if ``libqrs.so`` has not been built, every call raises.
+
+The functions carry the C names (``qrs_draw``, ``qrs_synthesize_points``,
+``qrs_diff_piston``, ``qrs_structure_fn``, ...).  Method parameters are a plain
+dictionary, see ``params()``: PSD (Eq. 7), frequency domain (Eq. 5, the
+square-to-disc map of Sec. 3.2, or log-polar), sampler (R2 of Eq. 6, jittered
+grid of Eq. 4, uniform, importance cells) and coefficient form (Eq. 3).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+__all__ = ["params", "Handle", "qrs_create", "qrs_draw", "qrs_synthesize_points", "qrs_diff_piston",
+           "qrs_structure_fn", "qrs_sync", "QrsError", "lib_path", "load"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libqrs.so")
+
+PSD = {"von_karman": 0, "kolmogorov": 1}
+DOMAIN = {"square": 0, "disc": 1, "logpolar": 2}
+SAMPLER = {"r2": 0, "jitter": 1, "uniform": 2, "importance": 3}
+COEF = {"gauss": 0, "eq3": 1}
+MODE = {"fused": 0, "gemm_3xtf32": 1, "gemm_bf16x3": 2}
+PISTON_PERSISTENT, PISTON_GRAPH = 1, 2
+STATUS = {0: "QRS_OK", -1: "QRS_ERR_ARG", -2: "QRS_ERR_CUDA", -3: "QRS_ERR_TIMEOUT", -4: "QRS_ERR_UNSUPPORTED",
+          -5: "QRS_ERR_NOMEM", -6: "QRS_ERR_DEVICE_CHECK"}
+
+
+class QrsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+# ------------------------------------------------------------------ C structs
+class QrsPsd(C.Structure):
+    _fields_ = [("r0_m", C.c_double), ("L0_m", C.c_double), ("kind", C.c_int32), ("reserved", C.c_int32)]
+
+
+class QrsDomain(C.Structure):
+    _fields_ = [("fmin", C.c_double), ("fmax", C.c_double), ("kind", C.c_int32), ("reserved", C.c_int32)]
+
+
+class QrsSampler(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("s0", C.c_uint64 * 2), ("cell_cdf", C.c_void_p), ("kind", C.c_int32),
+                ("coef_kind", C.c_int32), ("use_fixed_s0", C.c_int32), ("n_rho", C.c_int32),
+                ("n_theta", C.c_int32), ("reserved", C.c_int32)]
+
+
+class QrsDrawOut(C.Structure):
+    _fields_ = [("f_xy", C.c_void_p), ("amp", C.c_void_p), ("coef", C.c_void_p), ("cell", C.c_void_p),
+                ("words", C.c_void_p), ("r2", C.c_void_p)]
+
+
+class QrsPistonJob(C.Structure):
+    _fields_ = [("psd", QrsPsd), ("dom", QrsDomain), ("smp", QrsSampler), ("n_f", C.c_int64),
+                ("n_real", C.c_int64), ("real_offset", C.c_int64), ("ap_xy", C.c_void_p), ("ap_D", C.c_void_p),
+                ("ap_d", C.c_void_p), ("pairs", C.c_void_p), ("piston", C.c_void_p), ("delta", C.c_void_p),
+                ("n_ap", C.c_int32), ("n_pairs", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libqrs.so (raises if it has not been built: no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError("libqrs.so is not built (run `python -m paper_2404_02978_gb300.build` "
+                              "or __graft_entry__.build()); this package has no CPU fallback")
+        L = C.CDLL(_LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.qrs_create.argtypes = [C.POINTER(vp), i32]
+        L.qrs_destroy.argtypes = [vp]
+        L.qrs_destroy.restype = None
+        L.qrs_last_error.argtypes = [vp]
+        L.qrs_last_error.restype = C.c_char_p
+        L.qrs_sync.argtypes = [vp, vp]
+        L.qrs_launch_count.argtypes = [vp]
+        L.qrs_launch_count.restype = i64
+        L.qrs_draw.argtypes = [vp, C.POINTER(QrsPsd), C.POINTER(QrsDomain), C.POINTER(QrsSampler), i64, i64, i64,
+                               C.POINTER(QrsDrawOut), vp]
+        L.qrs_synthesize_points.argtypes = [vp, C.POINTER(QrsPsd), C.POINTER(QrsDomain), C.POINTER(QrsSampler),
+                                            i64, i64, i64, vp, i64, i32, vp, vp, vp]
+        L.qrs_diff_piston.argtypes = [vp, C.POINTER(QrsPistonJob), i32, i32, vp]
+        L.qrs_structure_fn.argtypes = [vp, vp, i64, i64, i64, vp, i32, vp, vp]
+        for n in ("qrs_create", "qrs_sync", "qrs_draw", "qrs_synthesize_points", "qrs_diff_piston",
+                  "qrs_structure_fn"):
+            getattr(L, n).restype = C.c_int
+        _lib = L
+        return L
+
+
+# ----------------------------------------------------------------- parameters
+def params(psd="von_karman", r0=0.15, L0=30.0, domain="logpolar", fmin=1e-3, fmax=16.0, sampler="r2", seed=0,
+           s0=None, coef="gauss", n_rho=64, n_theta=32, cdf=None):
+    """Method parameters as a plain dictionary (cdf: device uint32 tensor or None)."""
+    return dict(psd=psd, r0=r0, L0=L0, domain=domain, fmin=fmin, fmax=fmax, sampler=sampler, seed=seed, s0=s0,
+                coef=coef, n_rho=n_rho, n_theta=n_theta, cdf=cdf)
+
+
+def _structs(p):
+    psd = QrsPsd(float(p["r0"]), float(p.get("L0", 0.0) or 0.0), PSD[p["psd"]], 0)
+    dom = QrsDomain(float(p.get("fmin", 0.0) or 0.0), float(p["fmax"]), DOMAIN[p["domain"]], 0)
+    s0 = p.get("s0")
+    cdf = p.get("cdf")
+    if cdf is not None:
+        _check_dev(cdf, torch.int32, "cdf", allow=(torch.int32, getattr(torch, "uint32", torch.int32)))
+    smp = QrsSampler(int(p.get("seed", 0)) & (2**64 - 1), (C.c_uint64 * 2)(*(s0 if s0 is not None else (0, 0))),
+                     cdf.data_ptr() if cdf is not None else None, SAMPLER[p.get("sampler", "r2")],
+                     COEF[p.get("coef", "gauss")], 0 if s0 is None else 1, int(p.get("n_rho", 64)),
+                     int(p.get("n_theta", 32)), 0)
+    return psd, dom, smp
+
+
+def _check_dev(t, dtype, name, allow=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    ok = (t.dtype in allow) if allow else (t.dtype == dtype)
+    if not ok:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+# --------------------------------------------------------------------- handle
+class Handle:
+    """Owns a qrs_handle on one CUDA device."""
+
+    def __init__(self, device=0):
+        self.L = load()
+        self.device = int(device)
+        h = C.c_void_p()
+        st = self.L.qrs_create(C.byref(h), self.device)
+        if st != 0:
+            raise QrsError(st, "qrs_create(device=%d) failed" % self.device)
+        self.h = h
+
+    def _check(self, st):
+        if st != 0:
+            raise QrsError(st, self.L.qrs_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.qrs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        return int(self.L.qrs_launch_count(self.h))
+
+
+def qrs_create(device=0) -> Handle:
+    return Handle(device)
+
+
+def qrs_sync(h: Handle, stream=None):
+    h._check(h.L.qrs_sync(h.h, _stream(stream)))
+
+
+def qrs_draw(h: Handle, p, n_f, n_real, real_offset=0, outputs=("f_xy", "amp", "coef", "cell"), stream=None):
+    """Eq. 3/5/6 draw.  Returns a dict of new device tensors for the requested
+    outputs among f_xy, amp, coef, cell, words, r2."""
+    dev = torch.device("cuda", h.device)
+    shapes = {"f_xy": ((n_real, n_f, 2), torch.float32), "amp": ((n_real, n_f), torch.float32),
+              "coef": ((n_real, n_f, 2), torch.float32), "cell": ((n_real, n_f), torch.int32),
+              "words": ((n_real, n_f, 4), torch.int32), "r2": ((n_real, n_f, 2), torch.int64)}
+    res = {k: torch.empty(*shapes[k][0], dtype=shapes[k][1], device=dev) for k in outputs}
+    o = QrsDrawOut(*[(res[k].data_ptr() if k in res else None) for k in ("f_xy", "amp", "coef", "cell", "words", "r2")])
+    psd, dom, smp = _structs(p)
+    h._check(h.L.qrs_draw(h.h, C.byref(psd), C.byref(dom), C.byref(smp), int(n_f), int(n_real), int(real_offset),
+                          C.byref(o), _stream(stream)))
+    return res
+
+
+def qrs_synthesize_points(h: Handle, p, n_f, n_real, xy, out=None, mode="fused", real_offset=0, col_psd=None,
+                          stream=None):
+    """Eq. 3 at the points xy [P,2] (float32, device); returns out [n_real, P] float32."""
+    _check_dev(xy, torch.float32, "xy")
+    P = xy.shape[0]
+    if out is None:
+        out = torch.empty(n_real, P, dtype=torch.float32, device=xy.device)
+    _check_dev(out, torch.float32, "out")
+    if out.numel() != n_real * P:
+        raise ValueError("out must hold n_real * n_points values")
+    cp = None
+    if col_psd is not None:
+        _check_dev(col_psd, torch.float64, "col_psd")
+        cp = col_psd.data_ptr()
+    psd, dom, smp = _structs(p)
+    h._check(h.L.qrs_synthesize_points(h.h, C.byref(psd), C.byref(dom), C.byref(smp), int(n_f), int(n_real),
+                                       int(real_offset), xy.data_ptr(), int(P), MODE[mode], cp, out.data_ptr(),
+                                       _stream(stream)))
+    return out
+
+
+def piston_job(p, n_f, n_real, ap_xy, ap_D, ap_d=None, pairs=None, piston=None, delta=None, real_offset=0):
+    """Build one QrsPistonJob (device tensors; keeps them referenced in ._keep)."""
+    _check_dev(ap_xy, torch.float32, "ap_xy")
+    n_ap = ap_xy.shape[0]
+    _check_dev(ap_D, torch.float32, "ap_D")
+    if ap_d is not None:
+        _check_dev(ap_d, torch.float32, "ap_d")
+    n_pairs = 0
+    if pairs is not None:
+        _check_dev(pairs, torch.int32, "pairs")
+        n_pairs = pairs.shape[0]
+    psd, dom, smp = _structs(p)
+    j = QrsPistonJob(psd, dom, smp, int(n_f), int(n_real), int(real_offset), ap_xy.data_ptr(), ap_D.data_ptr(),
+                     ap_d.data_ptr() if ap_d is not None else None, pairs.data_ptr() if pairs is not None else None,
+                     piston.data_ptr() if piston is not None else None, delta.data_ptr() if delta is not None else None,
+                     int(n_ap), int(n_pairs))
+    j._keep = (ap_xy, ap_D, ap_d, pairs, piston, delta, p.get("cdf"))
+    return j
+
+
+def qrs_diff_piston(h: Handle, jobs, flags=0, stream=None):
+    """Run a list of piston jobs (see piston_job)."""
+    arr = (QrsPistonJob * len(jobs))(*jobs)
+    h._check(h.L.qrs_diff_piston(h.h, arr, len(jobs), int(flags), _stream(stream)))
+
+
+def qrs_structure_fn(h: Handle, delta, lags, acc=None, stream=None):
+    """Sec. 4.4 sums: delta [R, S, T] float32, lags [L] int32 -> acc [S, L, 3] float64 (accumulated)."""
+    _check_dev(delta, torch.float32, "delta")
+    _check_dev(lags, torch.int32, "lags")
+    R, S, T = delta.shape
+    if acc is None:
+        acc = torch.zeros(S, lags.shape[0], 3, dtype=torch.float64, device=delta.device)
+    _check_dev(acc, torch.float64, "acc")
+    h._check(h.L.qrs_structure_fn(h.h, delta.data_ptr(), int(R), int(S), int(T), lags.data_ptr(),
+                                  int(lags.shape[0]), acc.data_ptr(), _stream(stream)))
+    return acc

@@ -1,0 +1,169 @@
+// k_piston.cu -- K4/K6: differential pistons (Sec. 4.1, 4.4; Eq. 7 filter).
+//
+// One work item = (job, realisation).  The CTA draws the realisation's N_f
+// terms into shared memory (fused draw, chunks of kPisChunk terms), then its
+// warps take (aperture, 256-term slice) units round-robin: the 32 lanes split
+// the slice's terms, each lane forms F A_a(|f|) (a cos 2 pi f.p - b sin 2 pi f.p)
+// with the double-float phase (aperture centres lie up to hundreds of metres
+// from the origin), and a warp-shuffle reduction gives the slice's partial
+// piston.  Partials are folded in a fixed order (deterministic sums), then
+// the pair differences are written.
+//
+// Scheduling: a single job runs as a grid-stride over its realisations; a
+// batch of jobs (QRS_PISTON_PERSISTENT) runs as one persistent grid whose
+// CTAs pull items from an atomic counter over a cost-sorted item order
+// (largest N_f n_ap first), so uneven jobs balance across SMs.  The queue
+// never waits on anything, so there is no spin to bound.
+#include "qrs_internal.h"
+#include "qrs_piston.h"
+
+namespace qrs {
+
+constexpr int kPisTPB = 256;
+constexpr int kPisWarps = kPisTPB / 32;
+constexpr int kPisChunk = 2048;  // terms per shared-memory chunk
+constexpr int kPisSlice = 256;   // terms per (aperture, slice) unit
+constexpr int kPisSlices = kPisChunk / kPisSlice;
+
+struct PisShared {
+    float4 rec[kPisChunk];             // fx, fy, A = F a, nB = -F b
+    float fabs_[kPisChunk];            // |f|
+    float part[kPisMaxAp][kPisSlices];  // per-slice partial pistons of the chunk
+    float total[kPisMaxAp];
+    float apx[kPisMaxAp], apy[kPisMaxAp], apD[kPisMaxAp], apd[kPisMaxAp];
+};
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared& sh, int* err)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_ap = J.n_ap;
+    for (int a = tid; a < n_ap; a += kPisTPB) {
+        const float2 c = J.ap_xy[a];
+        sh.apx[a] = c.x; sh.apy[a] = c.y;
+        sh.apD[a] = J.ap_D[a];
+        sh.apd[a] = J.ap_d ? J.ap_d[a] : 0.0f;
+        sh.total[a] = 0.0f;
+    }
+    const DrawParams& p = J.p;
+    const uint64_t nr0 = (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f;
+    for (int64_t k_begin = 0; k_begin < p.n_f; k_begin += kPisChunk) {
+        const int len = (int)min((int64_t)kPisChunk, p.n_f - k_begin);
+        __syncthreads();  // previous chunk and aperture setup complete
+        for (int q = tid; q < len; q += kPisTPB) {
+            const Term t = draw_term(p, nr0 + (uint64_t)(k_begin + q), k_begin + q);
+            sh.rec[q] = make_float4(t.fx, t.fy, t.F * t.a, -(t.F * t.b));
+            sh.fabs_[q] = sqrtf(t.fx * t.fx + t.fy * t.fy);
+        }
+        __syncthreads();
+        const int n_sl = (len + kPisSlice - 1) / kPisSlice;
+        const int units = n_ap * n_sl;
+        for (int u = warp; u < units; u += kPisWarps) {
+            const int a = u / n_sl, sl = u - (u / n_sl) * n_sl;
+            const float x = sh.apx[a], y = sh.apy[a], D = sh.apD[a], d = sh.apd[a];
+            const int k_end = min(len, (sl + 1) * kPisSlice);
+            float acc = 0.0f;
+            for (int k = sl * kPisSlice + lane; k < k_end; k += 32) {
+                const float4 T = sh.rec[k];
+                const float A = airy_filter(sh.fabs_[k], D, d);
+                float s, c;
+                sincos_turns(phase_df(T.x, T.y, x, y), s, c);
+                acc = fmaf(A * T.z, c, acc);
+                acc = fmaf(A * T.w, s, acc);
+            }
+            acc = warp_sum_f(acc);
+            if (lane == 0) sh.part[a][sl] = acc;
+        }
+        __syncthreads();
+        for (int a = tid; a < n_ap; a += kPisTPB) {
+            float t = sh.total[a];
+            for (int sl = 0; sl < n_sl; ++sl) t += sh.part[a][sl];
+            sh.total[a] = t;
+        }
+    }
+    __syncthreads();
+    if (J.piston)
+        for (int a = tid; a < n_ap; a += kPisTPB) J.piston[r * n_ap + a] = sh.total[a];
+    if (J.delta)
+        for (int q = tid; q < J.n_pairs; q += kPisTPB) {
+            const int2 pr = J.pairs[q];
+            float v = 0.0f;
+            if (pr.x < 0 || pr.x >= n_ap || pr.y < 0 || pr.y >= n_ap) atomicExch(err, (int)QRS_ERR_DEVICE_CHECK);
+            else v = sh.total[pr.x] - sh.total[pr.y];
+            J.delta[r * J.n_pairs + q] = v;
+        }
+    __syncthreads();  // shared state reused by the next item
+}
+
+// Single job: grid-stride over its realisations.
+__global__ void __launch_bounds__(kPisTPB) k_piston_single(PistonJobDev J, int* err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PisShared& sh = *reinterpret_cast<PisShared*>(smem_raw);
+    for (int64_t r = blockIdx.x; r < J.n_real; r += gridDim.x) piston_item(J, r, sh, err);
+}
+
+// Batch: items (job, realisation) in cost-sorted job order, pulled from an
+// atomic counter.  jobs[] sorted by descending cost, item_begin its prefix sums.
+__global__ void __launch_bounds__(kPisTPB) k_piston_persistent(const PistonJobDev* __restrict__ jobs, int n_jobs,
+                                                               int64_t n_items, unsigned long long* counter, int* err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PisShared& sh = *reinterpret_cast<PisShared*>(smem_raw);
+    __shared__ long long s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t g = s_item;
+        __syncthreads();
+        if (g >= n_items) break;
+        int lo = 0, hi = n_jobs;  // last job with item_begin <= g
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (jobs[mid].item_begin <= g) lo = mid; else hi = mid;
+        }
+        const PistonJobDev J = jobs[lo];
+        piston_item(J, g - J.item_begin, sh, err);
+    }
+}
+
+size_t piston_smem_bytes() { return sizeof(PisShared); }
+
+cudaError_t launch_piston_single(const PistonJobDev& J, int num_sms, int* err, cudaStream_t s)
+{
+    const size_t smem = sizeof(PisShared);
+    cudaError_t e = cudaFuncSetAttribute(k_piston_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_piston_single, kPisTPB, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    if (grid > J.n_real) grid = J.n_real;
+    k_piston_single<<<(unsigned)grid, kPisTPB, smem, s>>>(J, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_piston_persistent(const PistonJobDev* d_jobs, int n_jobs, int64_t n_items,
+                                     unsigned long long* d_counter, int num_sms, int* err, cudaStream_t s)
+{
+    const size_t smem = sizeof(PisShared);
+    cudaError_t e = cudaFuncSetAttribute(k_piston_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_piston_persistent, kPisTPB, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    if (grid > n_items) grid = n_items;
+    k_piston_persistent<<<(unsigned)grid, kPisTPB, smem, s>>>(d_jobs, n_jobs, n_items, d_counter, err);
+    return cudaGetLastError();
+}
+
+}  // namespace qrs

@@ -1,0 +1,335 @@
+// qrs_device.cuh -- device-side method of libqrs: counter RNG, R2 placement,
+// domain maps, PSD weights, coefficients, phase reduction.
+//
+// Method: Berdja et al., "Quasi-Random Frequency Sampling for Optical
+// Turbulence Simulations" (arXiv 2404.02978): Eq. 3 (direct sum and its
+// weights), Eq. 4 (jittered grid), Eq. 5 (square map), Eq. 6 (R2 sequence),
+// Sec. 3.2 (seed, continuation across realisations, square-to-disc map),
+// Eq. 7 (von Karman PSD and aperture filter).
+//
+// Precision contract of a drawn term (the CPU reference computes the same in
+// FP64): the placement s is exact (integer fixed point, FP64 with 53 bits);
+// the map to f runs in FP64 and is rounded once to FP32; the weight
+// F = sqrt(W(f) J / N_f) and the coefficients (a, b) are FP32 from that FP32
+// f, within a few FP32 ulp of the FP64 values.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qrs {
+
+// ------------------------------------------------------------- constants ---
+// Philox4x32-10 round multipliers and Weyl key increments (Salmon et al. SC'11).
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u;
+constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u;
+constexpr uint32_t kPhiloxWeylB = 0xBB67AE85u;
+
+// Eq. 6 increments in 0.64 fixed point: 2^64/psi and 2^64/psi^2 rounded,
+// psi = 1.3247179572447460259609... the real root of x^3 = x + 1.
+constexpr uint64_t kR2StepX = 0xC13FA9A902A6328FULL;
+constexpr uint64_t kR2StepY = 0x91E10DA5C79E7B1DULL;
+
+// Counter stream ids (third counter word).
+constexpr uint32_t kStreamTerm = 0u;  // per-term words
+constexpr uint32_t kStreamSeed = 1u;  // random R2 seed
+constexpr uint32_t kStreamEq3 = 2u;   // R_u of the literal Eq. 3 coefficients
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.28318530717958647692;
+
+enum { kPsdVonKarman = 0, kPsdKolmogorov = 1 };
+enum { kDomSquare = 0, kDomDisc = 1, kDomLogPolar = 2 };
+enum { kSmpR2 = 0, kSmpJitter = 1, kSmpUniform = 2, kSmpImportance = 3 };
+enum { kCoefGauss = 0, kCoefEq3 = 1 };
+
+// ---------------------------------------------------------------- Philox ---
+struct Words {
+    uint32_t w0, w1, w2, w3;
+};
+
+__host__ __device__ __forceinline__ Words philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                        uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+#ifdef __CUDA_ARCH__
+        const uint32_t hiA = __umulhi(kPhiloxMulA, c0), loA = kPhiloxMulA * c0;
+        const uint32_t hiB = __umulhi(kPhiloxMulB, c2), loB = kPhiloxMulB * c2;
+#else
+        const uint64_t pA = (uint64_t)kPhiloxMulA * c0, pB = (uint64_t)kPhiloxMulB * c2;
+        const uint32_t hiA = (uint32_t)(pA >> 32), loA = (uint32_t)pA;
+        const uint32_t hiB = (uint32_t)(pB >> 32), loB = (uint32_t)pB;
+#endif
+        const uint32_t n0 = hiB ^ c1 ^ k0;
+        const uint32_t n2 = hiA ^ c3 ^ k1;
+        c0 = n0; c1 = loB; c2 = n2; c3 = loA;
+        k0 += kPhiloxWeylA;
+        k1 += kPhiloxWeylB;
+    }
+    return Words{c0, c1, c2, c3};
+}
+
+// ------------------------------------------------------------ parameters ---
+// Everything a kernel needs to draw term k of realisation r.  Built on the host
+// from the public structs; plain data, passed by value.
+struct DrawParams {
+    double fmin, fmax;      // cycles/m
+    double log_ratio;       // ln(fmax/fmin), LOGPOLAR and IMPORTANCE
+    uint64_t s0x, s0y;      // R2 seed, 0.64 fixed point
+    const uint32_t* cdf;    // IMPORTANCE cell starts (device)
+    int64_t n_f;            // terms per realisation
+    int64_t real_offset;    // first realisation of the call
+    float psd_c;            // c r0^(-5/3)
+    float psd_a;            // L0^-2 (0 for Kolmogorov)
+    float jac_c;            // SQUARE 4 fmax^2, DISC pi fmax^2, LOGPOLAR 2 pi ln(fmax/fmin) (x rho^2)
+    float inv_nf;           // 1 / N_f
+    uint32_t key0, key1;    // Philox key = seed
+    int32_t dom, smp, coef; // enums above
+    int32_t n_rho, n_theta;
+    int32_t pad;
+};
+
+// One drawn term.  J is the cell factor of the weight (w = W J / N_f).
+struct Term {
+    float fx, fy;  // cycles/m (FP32)
+    float F;       // sqrt(W J / N_f)
+    float J;
+    float a, b;    // coefficients
+    int32_t cell;
+};
+
+// ------------------------------------------------------------------- PSD ---
+// W(f) = c r0^(-5/3) (|f|^2 + L0^-2)^(-11/6)  (Eq. 7, first factor), FP32.
+__device__ __forceinline__ float psd_w(float psd_c, float psd_a, float f2)
+{
+    return psd_c * powf(f2 + psd_a, -11.0f / 6.0f);
+}
+
+// g(x) = 2 J1(x) / x.  For x < 4 its Taylor series
+//   g(x) = sum_m c_m u^m,  u = x^2/4,  c_m = (-1)^m / (m! (m+1)!)
+// (m = 0..12: the first omitted term is below 2e-12 at x = 4), by Horner in u
+// with an absolute error near 2e-7; beyond, 2 j1f(x)/x, whose absolute error
+// bound keeps g within about 1e-6 there (where |g| < 0.2).
+struct AiryCoef {
+    float c[13];
+    constexpr AiryCoef() : c()
+    {
+        double v = 1.0;
+        for (int m = 0; m < 13; ++m) {
+            c[m] = (float)v;
+            v = -v / ((double)(m + 1) * (double)(m + 2));
+        }
+    }
+};
+
+__device__ __forceinline__ float airy_g(float x)
+{
+    if (x < 4.0f) {
+        constexpr AiryCoef K;
+        const float u = 0.25f * x * x;
+        float s = K.c[12];
+#pragma unroll
+        for (int m = 11; m >= 0; --m) s = fmaf(s, u, K.c[m]);
+        return s;
+    }
+    return 2.0f * j1f(x) / x;
+}
+
+// Eq. 7 aperture filter A(f) = 2 (D J1(pi D f) - d J1(pi d f)) / (pi (D^2 - d^2) f)
+//                            = (D^2 g(pi D f) - d^2 g(pi d f)) / (D^2 - d^2),  A(0) = 1.
+__device__ __forceinline__ float airy_filter(float f, float D, float d)
+{
+    const float piF = 3.14159265358979f * f;
+    if (d <= 0.0f) return airy_g(piF * D);
+    const float D2 = D * D, d2 = d * d;
+    return (D2 * airy_g(piF * D) - d2 * airy_g(piF * d)) / (D2 - d2);
+}
+
+// --------------------------------------------------------------- domains ---
+// Unit square -> frequency plane in FP64, op for op as the CPU reference
+// (explicit _rn intrinsics: no contraction, identical rounding).
+__device__ __forceinline__ void map_square(double fmax, double sx, double sy, double& fx, double& fy)
+{
+    // Eq. 5: f = delta_f N (s - 1/2) with delta_f N = 2 max f
+    fx = __dmul_rn(fmax, __dsub_rn(__dmul_rn(2.0, sx), 1.0));
+    fy = __dmul_rn(fmax, __dsub_rn(__dmul_rn(2.0, sy), 1.0));
+}
+
+__device__ __forceinline__ void map_disc(double fmax, double sx, double sy, double& fx, double& fy)
+{
+    // Shirley-Chiu concentric map (area ratios preserved), radius fmax.
+    const double a = __dsub_rn(__dmul_rn(2.0, sx), 1.0);
+    const double b = __dsub_rn(__dmul_rn(2.0, sy), 1.0);
+    if (a == 0.0 && b == 0.0) { fx = 0.0; fy = 0.0; return; }
+    double r, phi;
+    if (fabs(a) > fabs(b)) {
+        r = a;
+        phi = __dmul_rn(kPi / 4.0, __ddiv_rn(b, a));
+    } else {
+        r = b;
+        phi = __dsub_rn(kPi / 2.0, __dmul_rn(kPi / 4.0, __ddiv_rn(a, b)));
+    }
+    double s, c;
+    sincos(phi, &s, &c);
+    const double R = __dmul_rn(fmax, r);
+    fx = __dmul_rn(R, c);
+    fy = __dmul_rn(R, s);
+}
+
+__device__ __forceinline__ void map_logpolar(double fmin, double log_ratio, double sx, double sy, double& fx,
+                                             double& fy)
+{
+    // rho = fmin (fmax/fmin)^s_x, theta = 2 pi s_y
+    const double rho = __dmul_rn(fmin, exp(__dmul_rn(sx, log_ratio)));
+    const double th = __dmul_rn(kTwoPi, sy);
+    double s, c;
+    sincos(th, &s, &c);
+    fx = __dmul_rn(rho, c);
+    fy = __dmul_rn(rho, s);
+}
+
+__device__ __forceinline__ double fix_to_unit(uint64_t S) { return (double)(S >> 11) * 0x1p-53; }
+
+// --------------------------------------------------------------- the draw ---
+// Term k of realisation r: global stream index n = (real_offset + r) N_f + k.
+// Optionally returns the Philox words and the R2 state (exact, for parity).
+__device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64_t k, Words* words_out = nullptr,
+                                          uint64_t* Sx_out = nullptr, uint64_t* Sy_out = nullptr)
+{
+    const Words w = philox4x32_10((uint32_t)n, (uint32_t)(n >> 32), kStreamTerm, 0u, p.key0, p.key1);
+    uint64_t Sx = 0, Sy = 0;
+    double sx = 0.0, sy = 0.0, fx = 0.0, fy = 0.0;
+    Term t;
+    t.cell = -1;
+    float J = 0.0f;
+    if (p.smp == kSmpImportance) {
+        // R2 point; its x top 32 bits choose the cell by inverse CDF, the rest
+        // places the frequency area-uniformly inside the annular sector.
+        Sx = p.s0x + n * kR2StepX;
+        Sy = p.s0y + n * kR2StepY;
+        const uint32_t u = (uint32_t)(Sx >> 32);
+        const int nc = p.n_rho * p.n_theta;
+        int lo = 0, hi = nc;  // largest c with cdf[c] <= u (cdf[0] = 0)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(p.cdf + mid) <= u) lo = mid; else hi = mid;
+        }
+        const int c = lo;
+        const uint64_t start = (uint64_t)__ldg(p.cdf + c);
+        const uint64_t end = (c + 1 < nc) ? (uint64_t)__ldg(p.cdf + c + 1) : (1ull << 32);
+        const uint64_t width = end - start;
+        const double tt = __ddiv_rn((double)(Sx - (start << 32)), __dmul_rn((double)width, 0x1p32));
+        const double syi = fix_to_unit(Sy);
+        const int ir = c / p.n_theta, it = c - (c / p.n_theta) * p.n_theta;
+        const double rlo = __dmul_rn(p.fmin, exp(__ddiv_rn(__dmul_rn(p.log_ratio, (double)ir), (double)p.n_rho)));
+        const double rhi =
+            __dmul_rn(p.fmin, exp(__ddiv_rn(__dmul_rn(p.log_ratio, (double)(ir + 1)), (double)p.n_rho)));
+        const double rlo2 = __dmul_rn(rlo, rlo), rhi2 = __dmul_rn(rhi, rhi);
+        const double rho = sqrt(__dadd_rn(rlo2, __dmul_rn(tt, __dsub_rn(rhi2, rlo2))));
+        const double th = __ddiv_rn(__dmul_rn(kTwoPi, __dadd_rn((double)it, syi)), (double)p.n_theta);
+        double s, co;
+        sincos(th, &s, &co);
+        fx = __dmul_rn(rho, co);
+        fy = __dmul_rn(rho, s);
+        const double area = __dmul_rn(__dmul_rn(__ddiv_rn(kTwoPi, (double)p.n_theta), 0.5), __dsub_rn(rhi2, rlo2));
+        const double pc = __dmul_rn((double)width, 0x1p-32);
+        J = (float)__ddiv_rn(area, pc);
+        t.cell = c;
+    } else {
+        if (p.smp == kSmpR2) {
+            Sx = p.s0x + n * kR2StepX;  // Eq. 6, mod 2^64
+            Sy = p.s0y + n * kR2StepY;
+            sx = fix_to_unit(Sx);
+            sy = fix_to_unit(Sy);
+        } else if (p.smp == kSmpUniform) {
+            Sx = (uint64_t)w.w0 << 32;
+            Sy = (uint64_t)w.w1 << 32;
+            sx = (double)w.w0 * 0x1p-32;
+            sy = (double)w.w1 * 0x1p-32;
+        } else {  // Eq. 4 jittered grid: cell (i, j), k = j n_rho + i
+            const int64_t i = k % p.n_rho, j = k / p.n_rho;
+            sx = __ddiv_rn(__dadd_rn((double)i, (double)w.w0 * 0x1p-32), (double)p.n_rho);
+            sy = __ddiv_rn(__dadd_rn((double)j, (double)w.w1 * 0x1p-32), (double)p.n_theta);
+        }
+        if (p.dom == kDomSquare) map_square(p.fmax, sx, sy, fx, fy);
+        else if (p.dom == kDomDisc) map_disc(p.fmax, sx, sy, fx, fy);
+        else map_logpolar(p.fmin, p.log_ratio, sx, sy, fx, fy);
+        int ir = (int)floor(__dmul_rn(sx, (double)p.n_rho));
+        int it = (int)floor(__dmul_rn(sy, (double)p.n_theta));
+        ir = ir > p.n_rho - 1 ? p.n_rho - 1 : ir;
+        it = it > p.n_theta - 1 ? p.n_theta - 1 : it;
+        t.cell = ir * p.n_theta + it;
+    }
+    t.fx = (float)fx;  // the one FP64 -> FP32 rounding of the method
+    t.fy = (float)fy;
+    const float f2 = t.fx * t.fx + t.fy * t.fy;
+    if (p.smp != kSmpImportance) J = (p.dom == kDomLogPolar) ? p.jac_c * f2 : p.jac_c;
+    t.J = J;
+    t.F = sqrtf(psd_w(p.psd_c, p.psd_a, f2) * J * p.inv_nf);
+    // Box-Muller from 24-bit uniforms (exact in FP32 and FP64 alike).
+    const float U1 = (float)((w.w2 >> 8) + 1u) * 0x1p-24f;
+    const float U2 = (float)(w.w3 >> 8) * 0x1p-24f;
+    const float rad = sqrtf(-2.0f * logf(U1));
+    float sb, cb;
+    sincospif(2.0f * U2, &sb, &cb);
+    t.a = rad * cb;
+    t.b = rad * sb;
+    if (p.coef == kCoefEq3) {
+        // literal Eq. 3: sqrt2 R_n cos(2 pi (f.x + R_u)) = a cos - b sin with
+        // a = sqrt2 R_n cos 2 pi R_u, b = sqrt2 R_n sin 2 pi R_u
+        const Words v = philox4x32_10((uint32_t)n, (uint32_t)(n >> 32), kStreamEq3, 0u, p.key0, p.key1);
+        const float Ru = (float)(v.w0 >> 8) * 0x1p-24f;
+        const float Rn = t.a;
+        float su, cu;
+        sincospif(2.0f * Ru, &su, &cu);
+        t.a = 1.41421356237309515f * Rn * cu;
+        t.b = 1.41421356237309515f * Rn * su;
+    }
+    if (words_out) *words_out = w;
+    if (Sx_out) *Sx_out = Sx;
+    if (Sy_out) *Sy_out = Sy;
+    return t;
+}
+
+// ------------------------------------------------------- phase reduction ---
+// Double-float reduction of phi = fx x + fy y mod 1 (cycles): each product is
+// split error-free (p = fl(f x), e = fma(f, x, -p)), the integer parts of the
+// products are removed exactly (magic-number rint, valid for |p| < 2^22), and
+// the small remainders are summed.  Result in [-1 - eps, 1 + eps].
+__device__ __forceinline__ float phase_df(float fx, float fy, float x, float y)
+{
+    const float p1 = __fmul_rn(fx, x);
+    const float e1 = __fmaf_rn(fx, x, -p1);
+    const float p2 = __fmul_rn(fy, y);
+    const float e2 = __fmaf_rn(fy, y, -p2);
+    const float M = 12582912.0f;  // 1.5 * 2^23
+    const float n1 = __fsub_rn(__fadd_rn(p1, M), M);
+    const float n2 = __fsub_rn(__fadd_rn(p2, M), M);
+    const float r = __fadd_rn(__fsub_rn(p1, n1), __fsub_rn(p2, n2));
+    return __fadd_rn(r, __fadd_rn(e1, e2));
+}
+
+// Fixed-point reduction: f and x quantised to int32 at per-launch binary
+// scales 2^a and 2^b (|F|, |X| < 2^31), phi 2^(a+b) = Fx X + Fy Y computed
+// exactly in 64-bit wraparound arithmetic (the integer part falls off the
+// top), 23 fraction bits extracted into a float mantissa.  `bias` adds half a
+// revolution and half an output ulp so that the result is the rounded phase
+// in [-0.5, 0.5).  Two IMAD.WIDE + SHF + LOP3 + FADD per (point, term).
+__device__ __forceinline__ float phase_fx(int32_t Fx, int32_t Fy, int32_t X, int32_t Y, uint64_t bias, uint32_t shift)
+{
+    uint64_t acc = bias + (uint64_t)((int64_t)Fy * (int64_t)Y);
+    acc += (uint64_t)((int64_t)Fx * (int64_t)X);
+    const uint32_t m = __funnelshift_rc((uint32_t)acc, (uint32_t)(acc >> 32), shift);
+    return __int_as_float((m & 0x007FFFFFu) | 0x3F800000u) - 1.5f;
+}
+
+__device__ __forceinline__ void sincos_turns(float turns, float& s, float& c)
+{
+    const float ang = turns * 6.28318530717958648f;
+    s = __sinf(ang);
+    c = __cosf(ang);
+}
+
+}  // namespace qrs

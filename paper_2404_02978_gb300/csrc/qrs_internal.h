@@ -1,0 +1,55 @@
+// qrs_internal.h -- handle layout and kernel launchers shared by the libqrs
+// translation units (not installed; the public ABI is include/qrs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/qrs.h"
+#include "qrs_device.cuh"
+
+struct qrs_handle {
+    int device = 0;
+    int num_sms = 0;
+    int smem_optin = 0;
+    int64_t launches = 0;
+    std::string last_error;
+    // Device workspace owned by the handle (allocated once in qrs_create).
+    int* d_err = nullptr;          // device error word (0 = fine)
+    float* d_xbound = nullptr;     // per-call point bound max(|x|, |y|) of a synthesis
+    // Growing device workspace for the GEMM form and batched pistons.
+    void* d_work = nullptr;
+    size_t work_bytes = 0;
+    // Pinned host staging for launch descriptors.
+    void* h_stage = nullptr;
+    size_t stage_bytes = 0;
+    // Batched-piston state (persistent launch, CUDA graph cache).
+    void* piston_state = nullptr;
+};
+
+namespace qrs {
+
+// Error plumbing: set message, return status.
+qrs_status fail(qrs_handle* h, qrs_status st, const char* fmt, ...);
+qrs_status cuda_fail(qrs_handle* h, cudaError_t e, const char* where);
+qrs_status ensure_work(qrs_handle* h, size_t bytes);
+
+// Host-side construction of the draw parameters from the public structs.
+qrs_status make_draw_params(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, const qrs_sampler* smp,
+                            int64_t n_f, int64_t real_offset, DrawParams* out);
+
+// Largest |f| component a draw can produce (for fixed-point scaling).
+double freq_bound(const DrawParams& p);
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_draw(const DrawParams& p, int64_t n_real, const qrs_draw_out& o, cudaStream_t s);
+cudaError_t launch_point_bound(const float* xy, int64_t n_points, float* d_bound, cudaStream_t s);
+cudaError_t launch_synth_fused(qrs_handle* h, const DrawParams& p, const float* xy, int64_t n_points,
+                               int64_t n_real, float* out, cudaStream_t s);
+cudaError_t launch_structure_fn(const float* delta, int64_t n_real, int64_t n_series, int64_t T,
+                                const int32_t* lags, int32_t n_lags, double* acc, int num_sms, int* err,
+                                cudaStream_t s);
+
+}  // namespace qrs

@@ -1,0 +1,249 @@
+"""GPU parity: libqrs (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (stated per result):
+* Philox words, R2 fixed-point state, cell ids: bit-exact.
+* Frequencies: within 1 FP32 ulp of the oracle's round-to-nearest of its FP64
+  map (the FP64 exp / sin / cos of the GPU and of the host libm may differ in
+  their last bit; identical FP64 placement otherwise).
+* Weights F and coefficients (a, b): within 4 FP32 ulp (relative to F, and to
+  the radius sqrt(a^2 + b^2), respectively).
+* Fields (Eq. 3 sums) and pistons: |gpu - oracle| <= 1e-5 sigma, sigma^2 the
+  variance the draw gives the value (sum_k F_k^2, times A^2 for pistons).
+* Structure-function sums: FP64, relative 1e-12 (summation order differs).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2404_02978_gb300 as qrs
+from paper_2404_02978_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+TOL_FIELD = 1e-5
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_2404_02978_gb300 import build as B
+    B.build()
+    return qrs.Handle(0)
+
+
+def _gp(p, cdf_dev=None):
+    q = dict(p)
+    q["cdf"] = cdf_dev
+    return q
+
+
+def _ulp_dist(a, b):
+    a = np.ascontiguousarray(a, np.float32).view(np.int32).astype(np.int64)
+    b = np.ascontiguousarray(b, np.float32).view(np.int32).astype(np.int64)
+    a = np.where(a < 0, -(a & 0x7FFFFFFF), a)
+    b = np.where(b < 0, -(b & 0x7FFFFFFF), b)
+    return np.abs(a - b)
+
+
+def _cdf(nr, nt, seed):
+    rng = np.random.default_rng(seed)
+    nc = nr * nt
+    p = 0.6 * rng.dirichlet(np.ones(nc) * 0.3) + 0.4 / nc
+    w = np.floor(p * 2**32).astype(np.int64)
+    w = np.maximum(w, 1)
+    w[np.argmax(w)] += 2**32 - w.sum()
+    return np.concatenate([[0], np.cumsum(w)[:-1]]).astype(np.uint32)
+
+
+DRAW_CASES = [
+    dict(domain="logpolar", sampler="r2", coef="gauss"),
+    dict(domain="square", sampler="r2", coef="gauss", fmax=0.25),
+    dict(domain="disc", sampler="r2", coef="eq3", fmax=3.0),
+    dict(domain="logpolar", sampler="uniform", coef="gauss"),
+    dict(domain="square", sampler="jitter", coef="gauss", fmax=1.0, n_rho=16, n_theta=16),
+    dict(domain="logpolar", sampler="importance", coef="gauss", n_rho=16, n_theta=8),
+    dict(domain="logpolar", sampler="r2", coef="gauss", psd="kolmogorov", s0=(1 << 63, 1 << 63)),
+]
+
+
+@pytest.mark.parametrize("case", DRAW_CASES, ids=lambda c: "%s-%s-%s" % (c["domain"], c["sampler"], c["coef"]))
+def test_draw_parity(h, case):
+    p = oracle.params(seed=17, **case)
+    n_f = 256 if case["sampler"] == "jitter" else 333
+    n_real, off = 3, 5
+    cdf_dev = None
+    if case["sampler"] == "importance":
+        cdf = _cdf(case["n_rho"], case["n_theta"], 3)
+        p["cdf"] = cdf
+        cdf_dev = torch.from_numpy(cdf.view(np.int32)).cuda()
+    ref = oracle.draw(p, n_f=n_f, n_real=n_real, real_offset=off, debug=True)
+    got = qrs.qrs_draw(h, _gp(p, cdf_dev), n_f, n_real, real_offset=off,
+                       outputs=("f_xy", "amp", "coef", "cell", "words", "r2"))
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in got.items()}
+    assert np.array_equal(g["words"].view(np.uint32), ref["words"])
+    assert np.array_equal(g["r2"].view(np.uint64), ref["r2"])
+    assert np.array_equal(g["cell"], ref["cell"])
+    assert _ulp_dist(g["f_xy"], ref["f"]).max() <= 1
+    F = ref["F"]
+    assert np.all(np.abs(g["amp"] - F) <= 4 * 2.0 ** -23 * F)
+    rad = np.hypot(ref["coef"][..., 0], ref["coef"][..., 1])[..., None]
+    assert np.all(np.abs(g["coef"] - ref["coef"]) <= 4 * 2.0 ** -23 * np.maximum(rad, 1e-6))
+
+
+def _field_check(got, ref, sig):
+    err = np.abs(got.astype(np.float64) - ref) / sig[:, None]
+    assert np.isfinite(got).all()
+    assert err.max() <= TOL_FIELD, "max err %.3g sigma" % err.max()
+    return err.max()
+
+
+def _sigma(p, n_f, n_real, off):
+    d = oracle.draw(p, n_f=n_f, n_real=n_real, real_offset=off)
+    return np.sqrt(np.sum(d["F"] ** 2, axis=1))
+
+
+@pytest.mark.parametrize("case", [
+    # pupil points, fmax |x| <= 128: fixed-point phase path
+    dict(name="pupil-fixed", pts="pupil", p=dict(domain="logpolar", fmax=16.0), n_f=300, n_real=3),
+    # long baselines: double-float phase path
+    dict(name="wide-df", pts="wide", p=dict(domain="logpolar", fmax=2.0), n_f=300, n_real=3),
+    # square domain, Eq. 5, literal Eq. 3 coefficients
+    dict(name="square-eq3", pts="pupil", p=dict(domain="square", fmax=4.0, coef="eq3"), n_f=37 * 37, n_real=2),
+    # more terms than one shared-memory chunk (chunk re-draw path), ragged group
+    dict(name="multichunk", pts="small", p=dict(domain="logpolar", fmax=16.0), n_f=4096 + 301, n_real=2),
+    dict(name="disc-uniform", pts="pupil", p=dict(domain="disc", fmax=8.0, sampler="uniform"), n_f=200, n_real=2),
+])
+def test_synthesis_parity(h, case):
+    rng = np.random.default_rng(11)
+    if case["pts"] == "pupil":
+        xy = wl.pupil_grid(80, 8.0)[: 2 * 2048 + 777]
+    elif case["pts"] == "wide":
+        xy = rng.uniform(-150, 150, size=(2 * 2048 + 333, 2)).astype(np.float32)
+    else:
+        xy = rng.uniform(-4, 4, size=(600, 2)).astype(np.float32)
+    p = oracle.params(seed=23, **case["p"])
+    off = 7
+    ref = oracle.synthesize(p, case["n_f"], case["n_real"], xy, real_offset=off)
+    got = qrs.qrs_synthesize_points(h, _gp(p), case["n_f"], case["n_real"], torch.from_numpy(xy).cuda(),
+                                    real_offset=off)
+    torch.cuda.synchronize()
+    _field_check(got.cpu().numpy(), ref, _sigma(p, case["n_f"], case["n_real"], off))
+
+
+def test_synthesis_importance_parity(h):
+    nr, nt = 16, 8
+    cdf = _cdf(nr, nt, 5)
+    p = oracle.params(seed=29, sampler="importance", n_rho=nr, n_theta=nt, cdf=cdf)
+    xy = wl.pupil_grid(64, 8.0)[:1500]
+    ref = oracle.synthesize(p, 256, 2, xy)
+    got = qrs.qrs_synthesize_points(h, _gp(p, torch.from_numpy(cdf.view(np.int32)).cuda()), 256, 2,
+                                    torch.from_numpy(xy).cuda())
+    torch.cuda.synchronize()
+    _field_check(got.cpu().numpy(), ref, _sigma(p, 256, 2, 0))
+
+
+def test_synthesis_chunked_equals_single_call(h):
+    """Counter-based stream: realisations [0,5) in one call == [0,2) + [2,5)."""
+    p = qrs.params(seed=31)
+    xy = torch.from_numpy(wl.pupil_grid(64, 8.0)).cuda()
+    one = qrs.qrs_synthesize_points(h, p, 512, 5, xy)
+    a = qrs.qrs_synthesize_points(h, p, 512, 2, xy)
+    b = qrs.qrs_synthesize_points(h, p, 512, 3, xy, real_offset=2)
+    torch.cuda.synchronize()
+    assert torch.equal(one, torch.cat([a, b]))
+
+
+def test_phase_screen_full_size_sampled(h):
+    """The benchmark launch: 51,468 pupil points, N_f = 4096, 1000 realisations;
+    the oracle checks 3 realisations x 128 sampled points."""
+    cfg = wl.PHASE_SCREEN
+    p = wl.method_params(cfg)
+    xy = wl.pupil_grid(cfg["grid"], cfg["pupil"])
+    out = qrs.qrs_synthesize_points(h, p, cfg["n_f"], cfg["n_real"], torch.from_numpy(xy).cuda())
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    assert np.isfinite(o).all()
+    rng = np.random.default_rng(0)
+    for r in (0, 517, cfg["n_real"] - 1):
+        idx = rng.choice(xy.shape[0], 128, replace=False)
+        ref = oracle.synthesize(p, cfg["n_f"], 1, xy[idx], real_offset=r)
+        _field_check(o[r:r + 1, idx], ref, _sigma(p, cfg["n_f"], 1, r))
+
+
+def test_piston_parity_plain_case(h):
+    B, ap_xy, ap_D, ap_d, pairs = wl.piston_plain_apertures()
+    cfg = wl.PISTON_PLAIN
+    p = wl.method_params(cfg)
+    R, off = 40, 3
+    pis_ref, dlt_ref = oracle.diff_piston(p, cfg["n_f"], R, ap_xy, ap_D, ap_d, pairs, real_offset=off)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    pis = torch.empty(R, ap_xy.shape[0], device="cuda")
+    dlt = torch.empty(R, pairs.shape[0], device="cuda")
+    job = qrs.piston_job(p, cfg["n_f"], R, dev(ap_xy), dev(ap_D), dev(ap_d), dev(pairs), pis, dlt, real_offset=off)
+    qrs.qrs_diff_piston(h, [job])
+    qrs.qrs_sync(h)
+    d = oracle.draw(p, n_f=cfg["n_f"], n_real=R, real_offset=off)
+    f = np.hypot(d["f"][..., 0], d["f"][..., 1]).astype(np.float64)
+    from oracle import analytic as an
+    A = an.airy(f.ravel(), 1.0).reshape(f.shape)
+    sig_p = np.sqrt(np.sum((d["F"] * A) ** 2, axis=1))
+    _field_check(pis.cpu().numpy(), pis_ref, sig_p)
+    _field_check(dlt.cpu().numpy(), dlt_ref, np.sqrt(2) * sig_p)
+
+
+def test_piston_annular_and_mixed_diameters(h):
+    rng = np.random.default_rng(5)
+    n_ap = 7
+    ap_xy = rng.uniform(-100, 100, size=(n_ap, 2)).astype(np.float32)
+    ap_D = rng.uniform(1.8, 8, size=n_ap).astype(np.float32)
+    ap_d = (0.14 * ap_D).astype(np.float32)
+    pairs = wl.all_pairs(n_ap)
+    p = oracle.params(seed=41, r0=0.1, L0=22.0, domain="square", fmax=0.25)
+    R, n_f = 6, 44 * 44
+    pis_ref, dlt_ref = oracle.diff_piston(p, n_f, R, ap_xy, ap_D, ap_d, pairs)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    pis = torch.empty(R, n_ap, device="cuda")
+    dlt = torch.empty(R, pairs.shape[0], device="cuda")
+    qrs.qrs_diff_piston(h, [qrs.piston_job(p, n_f, R, dev(ap_xy), dev(ap_D), dev(ap_d), dev(pairs), pis, dlt)])
+    qrs.qrs_sync(h)
+    scale = np.sqrt(np.mean(pis_ref ** 2))
+    assert np.abs(pis.cpu().numpy() - pis_ref).max() <= TOL_FIELD * scale
+    assert np.abs(dlt.cpu().numpy() - dlt_ref).max() <= 2 * TOL_FIELD * scale
+
+
+def test_structure_fn_parity(h):
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=(37, 5, 300)).astype(np.float32)
+    lags = np.array([0, 1, 2, 5, 17, 299], np.int32)
+    ref = oracle.structure_fn(x, lags)
+    acc = qrs.qrs_structure_fn(h, torch.from_numpy(x).cuda(), torch.from_numpy(lags).cuda())
+    qrs.qrs_sync(h)
+    a = acc.cpu().numpy()
+    assert np.array_equal(a[..., 2], ref[..., 2])
+    assert np.allclose(a[..., :2], ref[..., :2], rtol=1e-12, atol=0)
+
+
+def test_structure_fn_bad_lag_sets_device_error(h):
+    x = torch.zeros(2, 1, 8, device="cuda")
+    qrs.qrs_structure_fn(h, x, torch.tensor([9], dtype=torch.int32, device="cuda"))
+    with pytest.raises(qrs.QrsError) as e:
+        qrs.qrs_sync(h)
+    assert e.value.status == -6
+    qrs.qrs_sync(h)  # cleared
+
+
+def test_empty_and_invalid_arguments(h):
+    p = qrs.params()
+    xy = torch.zeros(0, 2, device="cuda")
+    out = qrs.qrs_synthesize_points(h, p, 64, 3, xy)
+    assert out.shape == (3, 0)
+    out = qrs.qrs_synthesize_points(h, p, 64, 0, torch.zeros(5, 2, device="cuda"))
+    assert out.shape == (0, 5)
+    with pytest.raises(qrs.QrsError):
+        qrs.qrs_synthesize_points(h, dict(p, fmin=20.0), 64, 1, torch.zeros(5, 2, device="cuda"))
+    with pytest.raises(qrs.QrsError):
+        qrs.qrs_synthesize_points(h, dict(p, psd="kolmogorov", domain="square"), 64, 1,
+                                  torch.zeros(5, 2, device="cuda"))
+    with pytest.raises(qrs.QrsError):
+        qrs.qrs_draw(h, dict(p, sampler="jitter", n_rho=4, n_theta=4), 15, 1)
+    qrs.qrs_sync(h)
