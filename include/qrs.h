@@ -242,6 +242,34 @@ qrs_status qrs_diff_piston(qrs_handle* h, const qrs_piston_job* jobs, int32_t n_
 qrs_status qrs_structure_fn(qrs_handle* h, const float* delta, int64_t n_real, int64_t n_series,
                             int64_t T, const int32_t* lags, int32_t n_lags, double* acc, void* stream);
 
+/* ------------------------------------------------- no-allocation variant ---
+ * The paper has no counterpart: this is a deployment variant of
+ * qrs_synthesize_points (mode QRS_SYNTH_FUSED) for callers that cannot
+ * allocate device memory -- e.g. code running inside a framework that owns all
+ * device memory through its own pool, or a latency-bound loop where an
+ * allocation could block or synchronise the device.  It takes no handle and
+ * never calls cudaMalloc / cudaFree or any allocating routine.
+ *   Scratch: a file-scope device array of QRS_NOALLOC_SCRATCH_BYTES per GPU,
+ *   held by every GPU that loads the library until the process exits.  The
+ *   fused path keeps one float in it (the point bound that selects the phase
+ *   path), whatever the problem size, so no size outgrows it; requests outside
+ *   the limits of qrs_synthesize_points return QRS_ERR_ARG.  The bound is
+ *   rewritten by every call, so nothing needs clearing between calls.
+ *   Device: the calling thread's current device (at most 64 devices).  The
+ *   first call on each device resolves the scratch's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.
+ *   Concurrency: every call on a device shares the one scratch array, so calls
+ *   that overlap on the GPU (e.g. on two streams at once) race; serialise them.
+ *   Errors: status codes only (there is no handle to hold a message).
+ * Arguments, layouts and results are those of qrs_synthesize_points with
+ * mode = QRS_SYNTH_FUSED and col_psd = NULL; the output is identical. */
+#define QRS_NOALLOC_SCRATCH_BYTES 256
+
+qrs_status qrs_synthesize_points_noalloc(const qrs_psd* psd, const qrs_domain* dom, const qrs_sampler* smp,
+                                         int64_t n_f, int64_t n_real, int64_t real_offset, const float* xy,
+                                         int64_t n_points, float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

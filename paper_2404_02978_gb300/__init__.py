@@ -264,3 +264,27 @@ def qrs_structure_fn(h: Handle, delta, lags, acc=None, stream=None):
     h._check(h.L.qrs_structure_fn(h.h, delta.data_ptr(), int(R), int(S), int(T), lags.data_ptr(),
                                   int(lags.shape[0]), acc.data_ptr(), _stream(stream)))
     return acc
+
+
+def qrs_synthesize_points_noalloc(p, n_f, n_real, xy, out=None, real_offset=0, stream=None):
+    """No-allocation fused synthesis on the current device (no handle; see include/qrs.h).
+    For callers that cannot allocate device memory: pass a preallocated `out`."""
+    L = load()
+    f = L.qrs_synthesize_points_noalloc
+    if f.argtypes is None:
+        f.argtypes = [C.POINTER(QrsPsd), C.POINTER(QrsDomain), C.POINTER(QrsSampler), C.c_int64, C.c_int64,
+                      C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+        f.restype = C.c_int
+    _check_dev(xy, torch.float32, "xy")
+    P = xy.shape[0]
+    if out is None:
+        out = torch.empty(n_real, P, dtype=torch.float32, device=xy.device)
+    _check_dev(out, torch.float32, "out")
+    if out.numel() != n_real * P:
+        raise ValueError("out must hold n_real * n_points values")
+    psd, dom, smp = _structs(p)
+    st = f(C.byref(psd), C.byref(dom), C.byref(smp), int(n_f), int(n_real), int(real_offset), xy.data_ptr(), int(P),
+           out.data_ptr(), _stream(stream))
+    if st != 0:
+        raise QrsError(st, "qrs_synthesize_points_noalloc failed")
+    return out

@@ -214,3 +214,33 @@ cudaError_t launch_synth_fused(qrs_handle* h, const DrawParams& p, const float* 
 }
 
 }  // namespace qrs
+
+namespace qrs {
+
+// Same two launches as launch_synth_fused (point-bound prepass, then the fused
+// kernel), for callers that bring their own device scratch word instead of a
+// handle: `d_bound` receives the point bound; `num_sms` sizes the grid.
+cudaError_t launch_synth_fused_raw(int num_sms, float* d_bound, const DrawParams& p, const float* xy,
+                                   int64_t n_points, int64_t n_real, float* out, cudaStream_t s)
+{
+    cudaError_t e = launch_point_bound(xy, n_points, d_bound, s);
+    if (e != cudaSuccess) return e;
+    const int chunk = (int)(p.n_f < kSynthChunkMax ? p.n_f : kSynthChunkMax);
+    const size_t smem = (size_t)chunk * sizeof(float4);
+    e = cudaFuncSetAttribute(k_synth_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSynthChunkMax * sizeof(float4)));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_synth_fused, kSynthTPB, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t n_tiles = (n_points + kSynthTile - 1) / kSynthTile;
+    const int64_t n_items = n_tiles * n_real;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    if (grid > n_items) grid = n_items;
+    k_synth_fused<<<(unsigned)grid, kSynthTPB, smem, s>>>(p, reinterpret_cast<const float2*>(xy), n_points, out,
+                                                          d_bound, (float)freq_bound(p), chunk, n_tiles, n_items);
+    return cudaGetLastError();
+}
+
+}  // namespace qrs

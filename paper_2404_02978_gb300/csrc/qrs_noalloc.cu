@@ -1,0 +1,76 @@
+// qrs_noalloc.cu -- qrs_synthesize_points_noalloc: the fused synthesis for
+// callers that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs under a framework which
+// owns every byte of device memory through its own pool allocator, or a
+// latency-bound loop in which an allocation could block or synchronise the
+// device.  Creating a qrs_handle allocates its workspace, so those callers
+// use this entry point instead: it takes no handle, allocates nothing, and
+// keeps its only scratch -- the one-float point bound that picks the phase
+// path of the fused kernel -- in the file-scope device array below, which
+// every GPU that loads the library holds until the process exits.
+#include <mutex>
+
+#include "qrs_internal.h"
+
+namespace qrs {
+cudaError_t launch_synth_fused_raw(int num_sms, float* d_bound, const DrawParams& p, const float* xy,
+                                   int64_t n_points, int64_t n_real, float* out, cudaStream_t s);
+}
+
+namespace {
+
+constexpr int kNoAllocScratchBytes = 256;  // QRS_NOALLOC_SCRATCH_BYTES
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+bool g_noalloc_ready[kNoAllocMaxDevices];
+float* g_noalloc_bound[kNoAllocMaxDevices];  // device address of the scratch, per device
+int g_noalloc_sms[kNoAllocMaxDevices];
+
+// Once per device, with that device current: resolve the device address of
+// the scratch array (its name in host code is only a host-side stand-in).
+qrs_status noalloc_setup(int dev)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ready[dev]) return QRS_OK;
+    void* addr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+    if (e != cudaSuccess || addr == nullptr) return QRS_ERR_CUDA;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || sms < 1) return QRS_ERR_CUDA;
+    g_noalloc_bound[dev] = static_cast<float*>(addr);
+    g_noalloc_sms[dev] = sms;
+    g_noalloc_ready[dev] = true;
+    return QRS_OK;
+}
+
+}  // namespace
+
+extern "C" qrs_status qrs_synthesize_points_noalloc(const qrs_psd* psd, const qrs_domain* dom,
+                                                    const qrs_sampler* smp, int64_t n_f, int64_t n_real,
+                                                    int64_t real_offset, const float* xy, int64_t n_points,
+                                                    float* out, void* stream)
+{
+    using namespace qrs;
+    if (n_real < 0 || n_points < 0) return QRS_ERR_ARG;
+    DrawParams p;
+    qrs_status st = make_draw_params(nullptr, psd, dom, smp, n_f, real_offset, &p);  // no message: no handle
+    if (st != QRS_OK) return st;
+    const unsigned __int128 top = (unsigned __int128)(uint64_t)(real_offset + n_real) * (uint64_t)n_f;
+    if ((top >> 64) != 0) return QRS_ERR_ARG;
+    if (n_real == 0 || n_points == 0) return QRS_OK;
+    if (!xy || !out || ((uintptr_t)xy & 7) || ((uintptr_t)out & 3)) return QRS_ERR_ARG;
+    // the fused path needs one float of scratch, whatever the problem size
+    static_assert(sizeof(float) <= kNoAllocScratchBytes, "scratch holds the point bound");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QRS_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return QRS_ERR_UNSUPPORTED;
+    st = noalloc_setup(dev);
+    if (st != QRS_OK) return st;
+    cudaError_t e = launch_synth_fused_raw(g_noalloc_sms[dev], g_noalloc_bound[dev], p, xy, n_points, n_real, out,
+                                           (cudaStream_t)stream);
+    return e == cudaSuccess ? QRS_OK : QRS_ERR_CUDA;
+}
