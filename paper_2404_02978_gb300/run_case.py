@@ -1,0 +1,39 @@
+"""Run one named workload once through the C ABI (for profilers: no CPU reference,
+no timing).  python -m paper_2404_02978_gb300.run_case --case phase_screen --n-real 16"""
+import argparse
+
+import torch
+
+import paper_2404_02978_gb300 as qrs
+from paper_2404_02978_gb300 import build as B
+from paper_2404_02978_gb300 import workloads as wl
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="phase_screen", choices=["phase_screen", "piston_plain"])
+    ap.add_argument("--n-real", type=int, default=16)
+    ap.add_argument("--repeat", type=int, default=2)
+    a = ap.parse_args()
+    B.build()
+    h = qrs.Handle(0)
+    if a.case == "phase_screen":
+        cfg = wl.PHASE_SCREEN
+        xy = torch.from_numpy(wl.pupil_grid(cfg["grid"], cfg["pupil"])).cuda()
+        for i in range(a.repeat):
+            qrs.qrs_synthesize_points(h, wl.method_params(cfg), cfg["n_f"], a.n_real, xy, real_offset=i * a.n_real)
+    else:
+        cfg = wl.PISTON_PLAIN
+        B_, ap_xy, ap_D, ap_d, pairs = wl.piston_plain_apertures()
+        dev = lambda v: torch.from_numpy(v).cuda()
+        delta = torch.empty(a.n_real, pairs.shape[0], device="cuda")
+        for i in range(a.repeat):
+            job = qrs.piston_job(wl.method_params(cfg), cfg["n_f"], a.n_real, dev(ap_xy), dev(ap_D), dev(ap_d),
+                                 dev(pairs), None, delta, real_offset=i * a.n_real)
+            qrs.qrs_diff_piston(h, [job])
+    qrs.qrs_sync(h)
+    print("ok", a.case, a.n_real, "launches", h.launch_count())
+
+
+if __name__ == "__main__":
+    main()
