@@ -43,15 +43,19 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra=(), out: str = None, build_dir: str = None) -> str:
+    """Compile and link libqrs.so.  `extra` adds nvcc flags (e.g. -D tunables);
+    `out` / `build_dir` place a variant build elsewhere (then it always rebuilds)."""
+    OUT_ = out or OUT
+    BUILD_ = build_dir or BUILD
+    if not force and out is None and up_to_date():
         return OUT
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(BUILD_, exist_ok=True)
     nvcc = _nvcc()
     srcs = sources()
 
     def one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(BUILD_, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-I", CSRC, "-I", os.path.join(HERE, "..", "include"),
                "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -63,13 +67,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(one, srcs))
-    tmp = OUT + ".tmp%d" % os.getpid()
+    tmp = OUT_ + ".tmp%d" % os.getpid()
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-lcudart", "-lcuda"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, OUT_)
+    return OUT_
 
 
 if __name__ == "__main__":

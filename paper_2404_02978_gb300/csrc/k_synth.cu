@@ -7,6 +7,7 @@
 // visits few realisations.  The N_f terms of the current realisation are
 // drawn by the CTA itself (Philox + R2 + FP64 map, draw_term) into shared
 // memory once and reused by every tile of that realisation in its range;
+// three CTAs of 256 threads share an SM (registers capped for that);
 // N_f beyond the shared-memory chunk is processed in chunks re-drawn per
 // item.  Each thread keeps PPT points in registers (strided by TPB, so the
 // loads and stores of a warp are coalesced) and loops over the terms, read
@@ -17,18 +18,36 @@
 // <= 128 (its quantisation error, <= fbound xbound 2^-30 turns, is then below
 // the double-float path's), double-float otherwise.
 //
-// Accumulation: every 32 terms a partial sum is folded into the running sum,
+// Accumulation: every 64 terms a partial sum is folded into the running sum,
 // which keeps the FP32 rounding error of N_f = 4096..16384-term sums near
 // 1e-7 of the field's standard deviation.
 #include "qrs_internal.h"
 
 namespace qrs {
 
+// Tunables (compile-time; the defaults are the measured best on GB300).
+#ifndef QRS_SYNTH_PPT
+#define QRS_SYNTH_PPT 4      // points per thread
+#endif
+#ifndef QRS_SYNTH_MINB
+#define QRS_SYNTH_MINB 3     // minimum resident CTAs per SM (register cap)
+#endif
+#ifndef QRS_SYNTH_UNROLL
+#define QRS_SYNTH_UNROLL 4   // term-loop unroll
+#endif
+#ifndef QRS_SYNTH_GROUP
+#define QRS_SYNTH_GROUP 64   // terms per partial sum
+#endif
+#ifndef QRS_SYNTH_FOLD
+#define QRS_SYNTH_FOLD 1     // 1: fixed-point turns -> radians in one FFMA
+#endif
+
 constexpr int kSynthTPB = 256;
-constexpr int kSynthPPT = 8;
+constexpr int kSynthPPT = QRS_SYNTH_PPT;
 constexpr int kSynthTile = kSynthTPB * kSynthPPT;
 constexpr int kSynthChunkMax = 4096;  // terms cached per CTA (64 KB)
-constexpr int kSynthGroup = 32;       // terms per partial sum
+constexpr int kSynthGroup = QRS_SYNTH_GROUP;
+constexpr int kSynthUnroll = QRS_SYNTH_UNROLL;
 
 // Prepass: one CTA computes max(|x|, |y|) over all points (no atomics, no
 // zeroing); the synthesis kernel reads it to pick its phase path and scales.
@@ -87,7 +106,14 @@ __device__ __forceinline__ FixedScales fixed_scales(float fbound, float xbound)
     z.fscale = ldexpf(1.0f, a);
     z.xscale = ldexpf(1.0f, b);
     z.shift = (uint32_t)(ab - 23);
-    z.bias = (ab >= 1 && ab <= 64) ? ((1ull << (ab - 1)) + (ab >= 24 ? (1ull << (ab - 24)) : 0ull)) : 0ull;
+    // half an output ulp (rounding), plus half a revolution for the [-0.5, 0.5)
+    // turns of phase_fx; phase_fx_rad wants [0, 1) turns and no half revolution
+    const uint64_t half_ulp = (ab >= 24 && ab <= 64) ? (1ull << (ab - 24)) : 0ull;
+#if QRS_SYNTH_FOLD
+    z.bias = half_ulp;
+#else
+    z.bias = (ab >= 1 && ab <= 64) ? ((1ull << (ab - 1)) + half_ulp) : 0ull;
+#endif
     return z;
 }
 
@@ -101,18 +127,23 @@ __device__ __forceinline__ void accumulate_chunk(const float4* __restrict__ st, 
         float part[kSynthPPT];
 #pragma unroll
         for (int j = 0; j < kSynthPPT; ++j) part[j] = 0.0f;
-#pragma unroll 2
+#pragma unroll kSynthUnroll
         for (int k = k0; k < k1; ++k) {
             const float4 T = st[k];
 #pragma unroll
             for (int j = 0; j < kSynthPPT; ++j) {
-                float ph;
-                if (FIXED)
-                    ph = phase_fx(__float_as_int(T.x), __float_as_int(T.y), X[j], Y[j], z.bias, z.shift);
-                else
-                    ph = phase_df(T.x, T.y, __int_as_float(X[j]), __int_as_float(Y[j]));
                 float s, c;
-                sincos_turns(ph, s, c);
+                if (FIXED) {
+#if QRS_SYNTH_FOLD
+                    const float ang = phase_fx_rad(__float_as_int(T.x), __float_as_int(T.y), X[j], Y[j], z.bias, z.shift);
+                    s = __sinf(ang);
+                    c = __cosf(ang);
+#else
+                    sincos_turns(phase_fx(__float_as_int(T.x), __float_as_int(T.y), X[j], Y[j], z.bias, z.shift), s, c);
+#endif
+                } else {
+                    sincos_turns(phase_df(T.x, T.y, __int_as_float(X[j]), __int_as_float(Y[j])), s, c);
+                }
                 part[j] = fmaf(T.z, c, part[j]);
                 part[j] = fmaf(T.w, s, part[j]);
             }
@@ -122,7 +153,7 @@ __device__ __forceinline__ void accumulate_chunk(const float4* __restrict__ st, 
     }
 }
 
-__global__ void __launch_bounds__(kSynthTPB) k_synth_fused(DrawParams p, const float2* __restrict__ xy, int64_t P,
+__global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawParams p, const float2* __restrict__ xy, int64_t P,
                                                            float* __restrict__ out, const float* __restrict__ d_xbound,
                                                            float fbound, int chunk, int64_t n_tiles, int64_t n_items)
 {

@@ -325,6 +325,20 @@ __device__ __forceinline__ float phase_fx(int32_t Fx, int32_t Fy, int32_t X, int
     return __int_as_float((m & 0x007FFFFFu) | 0x3F800000u) - 1.5f;
 }
 
+// The same fixed-point phase returned in radians in [0, 2 pi): with `bias`
+// holding only the half-ulp rounding term (no half revolution), the mantissa
+// m in [1, 2) holds 1 + frac(turns), and one FFMA forms m 2pi - 2pi =
+// (m - 1) 2pi with the rounded constant cancelling exactly; error: the
+// 2^-24-turn extraction rounding plus one FP32 rounding of the angle.
+__device__ __forceinline__ float phase_fx_rad(int32_t Fx, int32_t Fy, int32_t X, int32_t Y, uint64_t bias,
+                                              uint32_t shift)
+{
+    uint64_t acc = bias + (uint64_t)((int64_t)Fy * (int64_t)Y);
+    acc += (uint64_t)((int64_t)Fx * (int64_t)X);
+    const uint32_t m = __funnelshift_rc((uint32_t)acc, (uint32_t)(acc >> 32), shift);
+    return fmaf(__int_as_float((m & 0x007FFFFFu) | 0x3F800000u), 6.28318530717958648f, -6.28318530717958648f);
+}
+
 __device__ __forceinline__ void sincos_turns(float turns, float& s, float& c)
 {
     const float ang = turns * 6.28318530717958648f;
