@@ -1,0 +1,506 @@
+// k_gemm.cu -- K3: the shared-draw form of Eq. 3 as a tensor-core GEMM.
+//
+// When a batch of R realisations shares one frequency draw (the frequencies
+// of realisation real_offset; each column r has its own coefficients and
+// optionally its own r0, L0), Eq. 3 for all points and columns is one matrix
+// product
+//     out^T[m][r] = sum_k' A[m][k'] B[r][k'],   k' over 2 N_f,
+//     A = [cos 2 pi phi_mk | sin 2 pi phi_mk]       (the basis; points x 2 N_f)
+//     B = [F_kr a_kr | -F_kr b_kr]                  (coefficients; R x 2 N_f)
+// computed on the 5th-generation tensor cores in split precision:
+//   3XTF32: x = hi + lo with hi, lo TF32 (11-bit significands); the product is
+//           A_hi B_hi + A_hi B_lo + A_lo B_hi (kind::tf32), ~FP32 accuracy.
+//   BF16X3: the same with BF16 halves (kind::f16, BF16 in, FP32 accumulate).
+//
+// Launches: k_point_bound (phase path), k_gemm_freq (the shared draw, FP64
+// map, into the basis representation), k_gemm_coef (B, hi and lo, into the
+// workspace, K'-contiguous rows so TMA can stream them), k_gemm_main.
+//
+// k_gemm_main: one CTA per (128-point tile, 128-column block), 384 threads:
+//   warp 0      TMA producer: B_hi and B_lo tiles (128 rows x 128 B, 128-byte
+//               swizzle) per K chunk into a 3-stage ring (mbarrier complete_tx);
+//   warp 1      TMEM allocator (512 columns = four 128 x 128 FP32 accumulator
+//               slots) and single-thread MMA issuer: 3 x 4 tcgen05.mma per K
+//               chunk; every kGSeg chunks it moves to the next slot and commits
+//               the finished one;
+//   warps 4-7   promoters, one per TMEM lane quarter: tcgen05.ld each finished
+//               slot (their row's 128 columns) and add it into FP32 registers
+//               (round to nearest), then free the slot; at the end they store
+//               out[r][m] (coalesced over m).  The tensor core's accumulation
+//               loses about 2^-26 per step with a consistent sign, so long
+//               chains drift; segments of kGSeg chunks bound that drift.
+//   warps 8-11  basis producers: thread t owns point row t, evaluates the
+//               chunk's cos/sin (fixed-point or double-float phase, MUFU
+//               sin/cos), splits hi/lo and writes its 128-byte row of the
+//               swizzled A tiles, fence.proxy.async, arrive.
+// Every mbarrier wait is bounded in time; on time-out the CTA raises an abort
+// flag, records QRS_ERR_TIMEOUT in the device error word, waits (bounded) for
+// its TMA copies and MMAs in flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "qrs_internal.h"
+#include "qrs_sm100.cuh"
+
+namespace qrs {
+
+template <int PREC>
+struct GemmCfg;
+template <>
+struct GemmCfg<QRS_SYNTH_GEMM_3XTF32> {
+    static constexpr int kElemBytes = 4;
+    static constexpr int kElemsPerRow = 32;    // one 128-byte row of a K chunk
+    static constexpr int kTermsPerChunk = 16;  // cos and sin of 16 terms
+    static constexpr int kTermsPer16B = 4;
+    static constexpr uint32_t kFormat = 2;     // TF32
+    static constexpr bool kTF32 = true;
+};
+template <>
+struct GemmCfg<QRS_SYNTH_GEMM_BF16X3> {
+    static constexpr int kElemBytes = 2;
+    static constexpr int kElemsPerRow = 64;
+    static constexpr int kTermsPerChunk = 32;
+    static constexpr int kTermsPer16B = 8;
+    static constexpr uint32_t kFormat = 1;     // BF16
+    static constexpr bool kTF32 = false;
+};
+
+constexpr int kGM = 128;                                   // points per tile (UMMA M, TMEM lanes)
+constexpr int kGN = 128;                                   // columns per block (UMMA N)
+constexpr int kGStages = 3;
+constexpr int kGSlots = 4;                                 // TMEM accumulator slots (4 x 128 columns)
+constexpr int kGSeg = 4;                                   // K chunks per accumulation segment
+constexpr int kGTileA = kGM * 128;                         // 16 KB
+constexpr int kGTileB = kGN * 128;                         // 16 KB
+constexpr int kGStageBytes = 2 * kGTileA + 2 * kGTileB;    // A hi/lo + B hi/lo = 64 KB
+constexpr int kGThreads = 384;
+constexpr int kGSmemBytes = kGStages * kGStageBytes + 256 + 1024;  // + barriers + alignment slack
+constexpr long long kGWaitCycles = 4000000000LL;           // ~2 s of SM clock per wait
+
+struct GemmArgs {
+    const float2* xy;
+    int64_t P;
+    float* out;
+    int64_t n_real;     // valid columns
+    int64_t R_pad;      // rows of each B half (multiple of 256)
+    int64_t n_chunks;   // K chunks (2 N_f_pad / elements per row)
+    const int2* fbasis; // [N_f_pad] basis frequency (Fx, Fy) or float bits (fx, fy)
+    const float* d_xbound;
+    float fbound;
+    int* err;
+};
+
+// ------------------------------------------------------------- prep kernels
+// The shared draw: frequencies of realisation real_offset in the basis
+// representation, and (|f|^2, J) for the weights.
+__global__ void k_gemm_freq(DrawParams p, int64_t nf_pad, const float* __restrict__ d_xbound, float fbound,
+                            int2* __restrict__ fbasis, float2* __restrict__ fw)
+{
+    const FixedScales z = fixed_scales(fbound, *d_xbound, true);
+    const uint64_t n0 = (uint64_t)p.real_offset * (uint64_t)p.n_f;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nf_pad; k += (int64_t)gridDim.x * blockDim.x) {
+        if (k < p.n_f) {
+            const Term t = draw_term(p, n0 + (uint64_t)k, k);
+            if (z.use_fixed)
+                fbasis[k] = make_int2(__float2int_rn(t.fx * z.fscale), __float2int_rn(t.fy * z.fscale));
+            else
+                fbasis[k] = make_int2(__float_as_int(t.fx), __float_as_int(t.fy));
+            fw[k] = make_float2(t.fx * t.fx + t.fy * t.fy, t.J);
+        } else {
+            fbasis[k] = make_int2(0, 0);
+            fw[k] = make_float2(0.0f, 0.0f);
+        }
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void split_store(void* hi_base, void* lo_base, int64_t idx, float x)
+{
+    if (GemmCfg<PREC>::kTF32) {
+        uint32_t h, l;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+        const float r = x - __uint_as_float(h);
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+        static_cast<uint32_t*>(hi_base)[idx] = h;
+        static_cast<uint32_t*>(lo_base)[idx] = l;
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+        static_cast<__nv_bfloat16*>(hi_base)[idx] = h;
+        static_cast<__nv_bfloat16*>(lo_base)[idx] = l;
+    }
+}
+
+// B[r][k'] (hi half then lo half, R_pad rows each, 2 nf_pad columns):
+// chunk c holds terms [c T, (c+1) T); column c 2T + j = cos part (F a) of
+// term c T + j, column c 2T + T + j = sin part (-F b).  Column r draws its
+// coefficients from stream point (real_offset + r) N_f + k; its weight uses
+// (r0, L0) = col_psd[r] when given.  Rows r >= n_real and terms k >= N_f are 0.
+template <int PREC>
+__global__ void k_gemm_coef(DrawParams p, int64_t nf_pad, int64_t n_real, int64_t R_pad,
+                            const float2* __restrict__ fw, const double* __restrict__ col_psd, double c_vk,
+                            void* __restrict__ B)
+{
+    constexpr int T = GemmCfg<PREC>::kTermsPerChunk;
+    const int64_t r = blockIdx.y;
+    __shared__ float s_c, s_a;
+    if (threadIdx.x == 0) {
+        if (col_psd && r < n_real) {
+            const double r0 = col_psd[2 * r], L0 = col_psd[2 * r + 1];
+            s_c = (float)(c_vk * pow(r0, -5.0 / 3.0));
+            s_a = p.psd_a == 0.0f ? 0.0f : (float)(1.0 / (L0 * L0));
+        } else {
+            s_c = p.psd_c;
+            s_a = p.psd_a;
+        }
+    }
+    __syncthreads();
+    const float pc = s_c, pa = s_a;
+    const int64_t Kp = 2 * nf_pad;
+    unsigned char* hi = static_cast<unsigned char*>(B);
+    unsigned char* lo = hi + (size_t)R_pad * Kp * GemmCfg<PREC>::kElemBytes;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nf_pad; k += (int64_t)gridDim.x * blockDim.x) {
+        float cc = 0.0f, cs = 0.0f;
+        if (r < n_real && k < p.n_f) {
+            const float2 w = fw[k];
+            const float F = sqrtf(psd_w(pc, pa, w.x) * w.y * p.inv_nf);
+            const float2 ab = draw_coef(p, (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k);
+            cc = F * ab.x;
+            cs = -(F * ab.y);
+        }
+        const int64_t c = k / T, j = k - c * T;
+        const int64_t row = r * Kp;
+        split_store<PREC>(hi, lo, row + c * 2 * T + j, cc);
+        split_store<PREC>(hi, lo, row + c * 2 * T + T + j, cs);
+    }
+}
+
+// ------------------------------------------------------------ main kernel
+template <int PREC>
+__device__ __forceinline__ uint4 pack16(const float (&v)[GemmCfg<PREC>::kTermsPer16B], bool want_hi)
+{
+    uint4 q;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&q);
+    if (GemmCfg<PREC>::kTF32) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            uint32_t h;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v[e]));
+            if (want_hi) {
+                w[e] = h;
+            } else {
+                uint32_t l;
+                const float r = v[e] - __uint_as_float(h);
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+                w[e] = l;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float x0 = v[2 * e], x1 = v[2 * e + 1];
+            __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+            if (!want_hi) {
+                h0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                h1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+            }
+            w[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        }
+    }
+    return q;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constant__ CUtensorMap tmapB, GemmArgs g)
+{
+    using Cfg = GemmCfg<PREC>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(smem + kGStages * kGStageBytes);
+    uint64_t* fullB = fullA + kGStages;
+    uint64_t* empty = fullB + kGStages;
+    uint64_t* slot_full = empty + kGStages;
+    uint64_t* slot_free = slot_full + kGSlots;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(slot_free + kGSlots);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tile = blockIdx.x, rblk = blockIdx.y;
+    const int64_t n_chunks = g.n_chunks;
+    const int64_t n_seg = (n_chunks + kGSeg - 1) / kGSeg;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGStages; ++s) {
+            sm100::mbar_init(&fullA[s], 128);
+            sm100::mbar_init(&fullB[s], 1);
+            sm100::mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < kGSlots; ++s) {
+            sm100::mbar_init(&slot_full[s], 1);
+            sm100::mbar_init(&slot_free[s], 128);
+        }
+        *abort_flag = 0;
+        sm100::fence_barrier_init();
+    }
+    if (warp == 1) sm100::tmem_alloc(tmem_slot, 512);
+    if (warp == 0 && lane == 0) sm100::prefetch_tmap(&tmapB);
+    sm100::tc_fence_before();
+    __syncthreads();
+    sm100::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto stageA_hi = [&](int s) { return smem + s * kGStageBytes; };
+    auto stageA_lo = [&](int s) { return smem + s * kGStageBytes + kGTileA; };
+    auto stageB_hi = [&](int s) { return smem + s * kGStageBytes + 2 * kGTileA; };
+    auto stageB_lo = [&](int s) { return smem + s * kGStageBytes + 2 * kGTileA + kGTileB; };
+    auto timeout = [&]() {
+        *abort_flag = 1;
+        atomicExch(g.err, (int)QRS_ERR_TIMEOUT);
+    };
+    int64_t mma_segments = 0;  // segments the MMA thread committed (teardown)
+
+    if (warp == 0) {
+        // ---------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t i = 0; i < n_chunks; ++i) {
+                const int s = (int)(i % kGStages);
+                const uint32_t ph = (uint32_t)((i / kGStages) & 1);
+                if (i >= kGStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kGWaitCycles)) {
+                    if (!*abort_flag) timeout();
+                    break;
+                }
+                sm100::mbar_arrive_expect_tx(&fullB[s], 2u * kGTileB);
+                const int32_t x = (int32_t)(i * Cfg::kElemsPerRow);
+                sm100::tma_load_2d(stageB_hi(s), &tmapB, &fullB[s], x, (int32_t)(rblk * kGN));
+                sm100::tma_load_2d(stageB_lo(s), &tmapB, &fullB[s], x, (int32_t)(g.R_pad + rblk * kGN));
+                issued = i + 1;
+            }
+            if (*abort_flag) {  // let copies in flight land before the CTA exits
+                for (int64_t i = (issued > kGStages ? issued - kGStages : 0); i < issued; ++i)
+                    sm100::mbar_wait_for(&fullB[i % kGStages], (uint32_t)((i / kGStages) & 1), kGWaitCycles / 8);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = sm100::idesc_f32acc(Cfg::kFormat, kGM, kGN);
+            int64_t i = 0;
+            for (int64_t j = 0; j < n_seg && !*abort_flag; ++j) {
+                const int slot = (int)(j % kGSlots);
+                if (j >= kGSlots &&
+                    !sm100::mbar_wait(&slot_free[slot], (uint32_t)(((j / kGSlots) & 1) ^ 1), abort_flag, kGWaitCycles)) {
+                    if (!*abort_flag) timeout();
+                    break;
+                }
+                const uint32_t tacc = tmem_base + (uint32_t)(slot * kGN);
+                const int64_t i_end = ((j + 1) * kGSeg < n_chunks) ? (j + 1) * kGSeg : n_chunks;
+                bool first = true;
+                for (; i < i_end; ++i) {
+                    const int s = (int)(i % kGStages);
+                    const uint32_t ph = (uint32_t)((i / kGStages) & 1);
+                    if (!sm100::mbar_wait(&fullA[s], ph, abort_flag, kGWaitCycles) ||
+                        !sm100::mbar_wait(&fullB[s], ph, abort_flag, kGWaitCycles)) {
+                        if (!*abort_flag) timeout();
+                        break;
+                    }
+                    sm100::tc_fence_after();
+                    const uint32_t ahi = sm100::smem_u32(stageA_hi(s)), alo = sm100::smem_u32(stageA_lo(s));
+                    const uint32_t bhi = sm100::smem_u32(stageB_hi(s)), blo = sm100::smem_u32(stageB_lo(s));
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {  // four 32-byte K steps per 128-byte row
+                        const uint32_t off = (uint32_t)kk * 32u;
+                        const uint64_t dAh = sm100::desc_k_sw128(ahi + off), dAl = sm100::desc_k_sw128(alo + off);
+                        const uint64_t dBh = sm100::desc_k_sw128(bhi + off), dBl = sm100::desc_k_sw128(blo + off);
+                        sm100::mma<Cfg::kTF32>(tacc, dAh, dBh, idesc, first ? 0u : 1u);
+                        first = false;
+                        sm100::mma<Cfg::kTF32>(tacc, dAh, dBl, idesc, 1u);
+                        sm100::mma<Cfg::kTF32>(tacc, dAl, dBh, idesc, 1u);
+                    }
+                    sm100::mma_commit(&empty[s]);  // frees stage s once these MMAs complete
+                }
+                sm100::mma_commit(&slot_full[slot]);  // segment j done (or cut short by an abort)
+                mma_segments = j + 1;
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------------ promoters
+        const int quarter = warp - 4;  // TMEM lanes [32 quarter, 32 quarter + 32)
+        const int row = quarter * 32 + lane;
+        const int64_t m = tile * kGM + row;
+        float sum[kGN];
+#pragma unroll
+        for (int c = 0; c < kGN; ++c) sum[c] = 0.0f;
+        bool ok = true;
+        for (int64_t j = 0; j < n_seg; ++j) {
+            const int slot = (int)(j % kGSlots);
+            if (!sm100::mbar_wait(&slot_full[slot], (uint32_t)((j / kGSlots) & 1), abort_flag, kGWaitCycles)) {
+                if (!*abort_flag) timeout();
+                ok = false;
+                break;
+            }
+            sm100::tc_fence_after();
+            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(slot * kGN);
+#pragma unroll
+            for (int c0 = 0; c0 < kGN; c0 += 32) {
+                uint32_t v[32];
+                sm100::tmem_ld_32x32b_x32(tbase + (uint32_t)c0, v);
+                sm100::tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 32; ++q) sum[c0 + q] += __uint_as_float(v[q]);
+            }
+            sm100::tc_fence_before();
+            sm100::mbar_arrive(&slot_free[slot]);
+        }
+        if (ok && !*abort_flag && m < g.P) {
+#pragma unroll
+            for (int c = 0; c < kGN; ++c) {
+                const int64_t r = rblk * kGN + c;
+                if (r < g.n_real) g.out[r * g.P + m] = sum[c];
+            }
+        }
+    } else if (warp >= 8) {
+        // ------------------------------------------- basis producers
+        const int row = threadIdx.x - 256;
+        const int64_t m = tile * kGM + row;
+        const float2 pt = (m < g.P) ? g.xy[m] : make_float2(0.0f, 0.0f);
+        const FixedScales z = fixed_scales(g.fbound, *g.d_xbound, true);
+        const int32_t X = __float2int_rn(pt.x * z.xscale), Y = __float2int_rn(pt.y * z.xscale);
+        constexpr int TPG = Cfg::kTermsPer16B;
+        for (int64_t i = 0; i < n_chunks && !*abort_flag; ++i) {
+            const int s = (int)(i % kGStages);
+            const uint32_t ph = (uint32_t)((i / kGStages) & 1);
+            if (i >= kGStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kGWaitCycles)) {
+                if (!*abort_flag) timeout();
+                break;
+            }
+            const int2* fb = g.fbasis + i * Cfg::kTermsPerChunk;
+            unsigned char* Ahi = stageA_hi(s);
+            unsigned char* Alo = stageA_lo(s);
+#pragma unroll
+            for (int grp = 0; grp < 4; ++grp) {
+                float cv[TPG], sv[TPG];
+#pragma unroll
+                for (int t = 0; t < TPG; ++t) {
+                    const int2 f = __ldg(fb + grp * TPG + t);
+                    float ang;
+                    if (z.use_fixed) ang = phase_fx_rad(f.x, f.y, X, Y, z.bias, z.shift);
+                    else ang = phase_df(__int_as_float(f.x), __int_as_float(f.y), pt.x, pt.y) * 6.28318530717958648f;
+                    sv[t] = __sinf(ang);
+                    cv[t] = __cosf(ang);
+                }
+                const uint32_t oc = sm100::sw128_offset((uint32_t)row, (uint32_t)grp);
+                const uint32_t os = sm100::sw128_offset((uint32_t)row, (uint32_t)(4 + grp));
+                *reinterpret_cast<uint4*>(Ahi + oc) = pack16<PREC>(cv, true);
+                *reinterpret_cast<uint4*>(Alo + oc) = pack16<PREC>(cv, false);
+                *reinterpret_cast<uint4*>(Ahi + os) = pack16<PREC>(sv, true);
+                *reinterpret_cast<uint4*>(Alo + os) = pack16<PREC>(sv, false);
+            }
+            sm100::fence_proxy_async_smem();
+            sm100::mbar_arrive(&fullA[s]);
+        }
+    }
+    sm100::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        if (*abort_flag && lane == 0) {  // MMAs in flight must finish before their TMEM is freed
+            for (int64_t j = (mma_segments > kGSlots ? mma_segments - kGSlots : 0); j < mma_segments; ++j)
+                sm100::mbar_wait_for(&slot_full[j % kGSlots], (uint32_t)((j / kGSlots) & 1), kGWaitCycles / 8);
+        }
+        __syncwarp();
+        sm100::tc_fence_after();
+        sm100::tmem_dealloc(tmem_base, 512);
+    }
+}
+
+// ------------------------------------------------------------------ host
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real)
+{
+    const int T = mode == QRS_SYNTH_GEMM_3XTF32 ? GemmCfg<QRS_SYNTH_GEMM_3XTF32>::kTermsPerChunk
+                                                : GemmCfg<QRS_SYNTH_GEMM_BF16X3>::kTermsPerChunk;
+    const int eb = mode == QRS_SYNTH_GEMM_3XTF32 ? 4 : 2;
+    const int64_t nf_pad = (n_f + T - 1) / T * T;
+    const int64_t R_pad = (n_real + kGN - 1) / kGN * kGN;
+    const size_t b = (size_t)2 * R_pad * (2 * nf_pad) * eb;  // hi and lo halves
+    return 256 + b + (size_t)nf_pad * (sizeof(int2) + sizeof(float2)) + 1024;
+}
+
+template <int PREC>
+static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float* xy, int64_t P, int64_t n_real,
+                                 const double* col_psd, double c_vk, float* out, cudaStream_t s)
+{
+    using Cfg = GemmCfg<PREC>;
+    constexpr int T = Cfg::kTermsPerChunk;
+    const int64_t nf_pad = (p.n_f + T - 1) / T * T;
+    const int64_t Kp = 2 * nf_pad;
+    const int64_t R_pad = (n_real + kGN - 1) / kGN * kGN;
+    // workspace: [B hi | B lo][R_pad][Kp], fbasis[nf_pad], fw[nf_pad]
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)h->d_work + 255) & ~(uintptr_t)255);
+    void* B = base;
+    const size_t bbytes = (size_t)2 * R_pad * Kp * Cfg::kElemBytes;
+    int2* fbasis = reinterpret_cast<int2*>(base + bbytes);
+    float2* fw = reinterpret_cast<float2*>(fbasis + nf_pad);
+
+    cudaError_t e = launch_point_bound(xy, P, h->d_xbound, s);
+    if (e != cudaSuccess) return e;
+    const float fbound = (float)freq_bound(p);
+    k_gemm_freq<<<(unsigned)((nf_pad + 255) / 256), 256, 0, s>>>(p, nf_pad, h->d_xbound, fbound, fbasis, fw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 cg((unsigned)std::min<int64_t>((nf_pad + 255) / 256, 64), (unsigned)R_pad);
+    k_gemm_coef<PREC><<<cg, 256, 0, s>>>(p, nf_pad, n_real, R_pad, fw, col_psd, c_vk, B);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+    PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode();
+    if (!encode) return cudaErrorNotSupported;
+    CUtensorMap tmap;
+    const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)(2 * R_pad)};
+    const cuuint64_t gstride[1] = {(cuuint64_t)(Kp * Cfg::kElemBytes)};
+    const cuuint32_t box[2] = {(cuuint32_t)Cfg::kElemsPerRow, (cuuint32_t)kGN};
+    const cuuint32_t estride[2] = {1, 1};
+    CUresult cr = encode(&tmap, Cfg::kTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B,
+                         gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+
+    GemmArgs a;
+    a.xy = reinterpret_cast<const float2*>(xy);
+    a.P = P;
+    a.out = out;
+    a.n_real = n_real;
+    a.R_pad = R_pad;
+    a.n_chunks = Kp / Cfg::kElemsPerRow;
+    a.fbasis = fbasis;
+    a.d_xbound = h->d_xbound;
+    a.fbound = fbound;
+    a.err = h->d_err;
+    e = cudaFuncSetAttribute(k_gemm_main<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemBytes);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((P + kGM - 1) / kGM), (unsigned)(R_pad / kGN));
+    k_gemm_main<PREC><<<grid, kGThreads, kGSmemBytes, s>>>(tmap, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_synth_gemm(qrs_handle* h, int mode, const DrawParams& p, const float* xy, int64_t P, int64_t n_real,
+                              const double* col_psd, double c_vk, float* out, cudaStream_t s)
+{
+    if (mode == QRS_SYNTH_GEMM_3XTF32)
+        return launch_gemm_t<QRS_SYNTH_GEMM_3XTF32>(h, p, xy, P, n_real, col_psd, c_vk, out, s);
+    return launch_gemm_t<QRS_SYNTH_GEMM_BF16X3>(h, p, xy, P, n_real, col_psd, c_vk, out, s);
+}
+
+}  // namespace qrs

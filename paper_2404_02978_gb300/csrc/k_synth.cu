@@ -77,46 +77,6 @@ cudaError_t launch_point_bound(const float* xy, int64_t n_points, float* d_bound
     return cudaGetLastError();
 }
 
-// ceil(log2(v)) for v > 0 (exact for powers of two).
-__device__ __host__ __forceinline__ int ceil_log2(double v)
-{
-    int e;
-    const double m = frexp(v, &e);  // v = m 2^e, m in [0.5, 1)
-    return (m == 0.5) ? e - 1 : e;
-}
-
-struct FixedScales {
-    bool use_fixed;
-    float fscale, xscale;  // 2^a, 2^b
-    uint64_t bias;
-    uint32_t shift;
-};
-
-__device__ __forceinline__ FixedScales fixed_scales(float fbound, float xbound)
-{
-    FixedScales z;
-    const double fb = (double)fbound * (1.0 + 0x1p-20);
-    const double xb = (double)xbound * (1.0 + 0x1p-20);
-    z.use_fixed = (fb * xb <= 128.0);
-    const int a = 31 - ceil_log2(fb);
-    int b = (xb > 0.0) ? 31 - ceil_log2(xb) : 54 - a;
-    if (a + b > 54) b = 54 - a;
-    if (a + b < 23) z.use_fixed = false;
-    const int ab = a + b;
-    z.fscale = ldexpf(1.0f, a);
-    z.xscale = ldexpf(1.0f, b);
-    z.shift = (uint32_t)(ab - 23);
-    // half an output ulp (rounding), plus half a revolution for the [-0.5, 0.5)
-    // turns of phase_fx; phase_fx_rad wants [0, 1) turns and no half revolution
-    const uint64_t half_ulp = (ab >= 24 && ab <= 64) ? (1ull << (ab - 24)) : 0ull;
-#if QRS_SYNTH_FOLD
-    z.bias = half_ulp;
-#else
-    z.bias = (ab >= 1 && ab <= 64) ? ((1ull << (ab - 1)) + half_ulp) : 0ull;
-#endif
-    return z;
-}
-
 template <bool FIXED>
 __device__ __forceinline__ void accumulate_chunk(const float4* __restrict__ st, int len, const int32_t (&X)[kSynthPPT],
                                                  const int32_t (&Y)[kSynthPPT], float (&acc)[kSynthPPT],
@@ -158,7 +118,7 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
                                                            float fbound, int chunk, int64_t n_tiles, int64_t n_items)
 {
     extern __shared__ float4 sterm[];
-    const FixedScales z = fixed_scales(fbound, *d_xbound);
+    const FixedScales z = fixed_scales(fbound, *d_xbound, QRS_SYNTH_FOLD != 0);
     const int64_t G = gridDim.x;
     const int64_t it0 = (n_items * (int64_t)blockIdx.x) / G;
     const int64_t it1 = (n_items * ((int64_t)blockIdx.x + 1)) / G;

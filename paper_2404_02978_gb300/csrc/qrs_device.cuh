@@ -192,6 +192,40 @@ __device__ __forceinline__ void map_logpolar(double fmin, double log_ratio, doub
 
 __device__ __forceinline__ double fix_to_unit(uint64_t S) { return (double)(S >> 11) * 0x1p-53; }
 
+// Coefficients of Eq. 3 from the term's Philox words: Box-Muller from 24-bit
+// uniforms (exact in FP32 and FP64 alike), and for the literal Eq. 3 form the
+// extra uniform R_u of stream 2.
+__device__ __forceinline__ void coef_from_words(const DrawParams& p, uint64_t n, const Words& w, float& a, float& b)
+{
+    const float U1 = (float)((w.w2 >> 8) + 1u) * 0x1p-24f;
+    const float U2 = (float)(w.w3 >> 8) * 0x1p-24f;
+    const float rad = sqrtf(-2.0f * logf(U1));
+    float sb, cb;
+    sincospif(2.0f * U2, &sb, &cb);
+    a = rad * cb;
+    b = rad * sb;
+    if (p.coef == kCoefEq3) {
+        // literal Eq. 3: sqrt2 R_n cos(2 pi (f.x + R_u)) = a cos - b sin with
+        // a = sqrt2 R_n cos 2 pi R_u, b = sqrt2 R_n sin 2 pi R_u
+        const Words v = philox4x32_10((uint32_t)n, (uint32_t)(n >> 32), kStreamEq3, 0u, p.key0, p.key1);
+        const float Ru = (float)(v.w0 >> 8) * 0x1p-24f;
+        const float Rn = a;
+        float su, cu;
+        sincospif(2.0f * Ru, &su, &cu);
+        a = 1.41421356237309515f * Rn * cu;
+        b = 1.41421356237309515f * Rn * su;
+    }
+}
+
+// Coefficients of stream point n alone (no placement, no FP64).
+__device__ __forceinline__ float2 draw_coef(const DrawParams& p, uint64_t n)
+{
+    const Words w = philox4x32_10((uint32_t)n, (uint32_t)(n >> 32), kStreamTerm, 0u, p.key0, p.key1);
+    float a, b;
+    coef_from_words(p, n, w, a, b);
+    return make_float2(a, b);
+}
+
 // --------------------------------------------------------------- the draw ---
 // Term k of realisation r: global stream index n = (real_offset + r) N_f + k.
 // Optionally returns the Philox words and the R2 state (exact, for parity).
@@ -268,25 +302,7 @@ __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64
     if (p.smp != kSmpImportance) J = (p.dom == kDomLogPolar) ? p.jac_c * f2 : p.jac_c;
     t.J = J;
     t.F = sqrtf(psd_w(p.psd_c, p.psd_a, f2) * J * p.inv_nf);
-    // Box-Muller from 24-bit uniforms (exact in FP32 and FP64 alike).
-    const float U1 = (float)((w.w2 >> 8) + 1u) * 0x1p-24f;
-    const float U2 = (float)(w.w3 >> 8) * 0x1p-24f;
-    const float rad = sqrtf(-2.0f * logf(U1));
-    float sb, cb;
-    sincospif(2.0f * U2, &sb, &cb);
-    t.a = rad * cb;
-    t.b = rad * sb;
-    if (p.coef == kCoefEq3) {
-        // literal Eq. 3: sqrt2 R_n cos(2 pi (f.x + R_u)) = a cos - b sin with
-        // a = sqrt2 R_n cos 2 pi R_u, b = sqrt2 R_n sin 2 pi R_u
-        const Words v = philox4x32_10((uint32_t)n, (uint32_t)(n >> 32), kStreamEq3, 0u, p.key0, p.key1);
-        const float Ru = (float)(v.w0 >> 8) * 0x1p-24f;
-        const float Rn = t.a;
-        float su, cu;
-        sincospif(2.0f * Ru, &su, &cu);
-        t.a = 1.41421356237309515f * Rn * cu;
-        t.b = 1.41421356237309515f * Rn * su;
-    }
+    coef_from_words(p, n, w, t.a, t.b);
     if (words_out) *words_out = w;
     if (Sx_out) *Sx_out = Sx;
     if (Sy_out) *Sy_out = Sy;
@@ -344,6 +360,47 @@ __device__ __forceinline__ void sincos_turns(float turns, float& s, float& c)
     const float ang = turns * 6.28318530717958648f;
     s = __sinf(ang);
     c = __cosf(ang);
+}
+
+// ceil(log2(v)) for v > 0 (exact for powers of two).
+__device__ __host__ __forceinline__ int ceil_log2(double v)
+{
+    int e;
+    const double m = frexp(v, &e);  // v = m 2^e, m in [0.5, 1)
+    return (m == 0.5) ? e - 1 : e;
+}
+
+// Per-launch scales of the fixed-point phase (phase_fx / phase_fx_rad) from
+// the frequency bound and the point bound: a = 31 - ceil(log2 fbound),
+// b = 31 - ceil(log2 xbound) (capped so that a + b <= 54), use_fixed when
+// fbound xbound <= 128 (then the quantisation error, <= fbound xbound 2^-30
+// turns, is below the double-float path's).  `radians`: bias for
+// phase_fx_rad ([0, 1) turns) instead of phase_fx ([-0.5, 0.5) turns).
+struct FixedScales {
+    bool use_fixed;
+    float fscale, xscale;  // 2^a, 2^b
+    uint64_t bias;
+    uint32_t shift;
+};
+
+__device__ __forceinline__ FixedScales fixed_scales(float fbound, float xbound, bool radians)
+{
+    FixedScales z;
+    const double fb = (double)fbound * (1.0 + 0x1p-20);
+    const double xb = (double)xbound * (1.0 + 0x1p-20);
+    z.use_fixed = (fb * xb <= 128.0);
+    const int a = 31 - ceil_log2(fb);
+    int b = (xb > 0.0) ? 31 - ceil_log2(xb) : 54 - a;
+    if (a + b > 54) b = 54 - a;
+    if (a + b < 24) z.use_fixed = false;
+    const int ab = a + b;
+    z.fscale = ldexpf(1.0f, a);
+    z.xscale = ldexpf(1.0f, b);
+    z.shift = (uint32_t)(ab - 23);
+    // half an output ulp (rounding), plus half a revolution for [-0.5, 0.5) turns
+    const uint64_t half_ulp = (ab >= 24 && ab <= 64) ? (1ull << (ab - 24)) : 0ull;
+    z.bias = radians ? half_ulp : ((ab >= 1 && ab <= 64) ? ((1ull << (ab - 1)) + half_ulp) : 0ull);
+    return z;
 }
 
 }  // namespace qrs

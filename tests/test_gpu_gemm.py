@@ -1,0 +1,99 @@
+"""GPU parity of the shared-draw GEMM form (tcgen05 tensor cores) against the oracle.
+
+One frequency draw (that of realisation real_offset) shared by all columns;
+column r takes its coefficients from stream points (real_offset + r) N_f + k
+and its own (r0, L0).  Tolerances per value, relative to the column's field
+standard deviation sigma_r (sigma_r^2 = sum_k F_kr^2):
+  3XTF32: 1e-5 (split TF32, ~2^-22 per product);
+  BF16X3: 2e-4 (split BF16, ~2^-17 per operand; the measured error is printed).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2404_02978_gb300 as qrs
+from oracle import analytic as an
+from paper_2404_02978_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+TOL = {"gemm_3xtf32": 1e-5, "gemm_bf16x3": 2e-4}
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_2404_02978_gb300 import build as B
+    B.build()
+    return qrs.Handle(0)
+
+
+def _col_sigma(p, n_f, n_real, off, col_psd):
+    d = oracle.draw(p, n_f=n_f, n_real=1, real_offset=off)
+    f = np.hypot(d["f"][0, :, 0].astype(np.float64), d["f"][0, :, 1].astype(np.float64))
+    J = d["J"][0]
+    out = []
+    for r in range(n_real):
+        r0, L0 = (col_psd[r] if col_psd is not None else (p["r0"], p["L0"]))
+        out.append(np.sqrt(np.sum(an.psd(f, r0, L0, p["psd"]) * J / n_f)))
+    return np.array(out)
+
+
+def _run(h, p, n_f, n_real, xy, mode, off, col_psd):
+    cp = None if col_psd is None else torch.from_numpy(np.ascontiguousarray(col_psd, np.float64)).cuda()
+    out = qrs.qrs_synthesize_points(h, p, n_f, n_real, torch.from_numpy(xy).cuda(), mode=mode, real_offset=off,
+                                    col_psd=cp)
+    qrs.qrs_sync(h)
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("mode", ["gemm_3xtf32", "gemm_bf16x3"])
+@pytest.mark.parametrize("case", ["pupil", "wide", "blocks"])
+def test_gemm_parity(h, mode, case):
+    rng = np.random.default_rng(7)
+    if case == "pupil":      # fixed-point phase, ragged tile, padded terms and columns
+        xy = wl.pupil_grid(48, 8.0)[: 3 * 128 + 57]
+        p, n_f, n_real = oracle.params(seed=61), 100, 20
+    elif case == "wide":     # double-float phase path
+        xy = rng.uniform(-40, 40, size=(300, 2)).astype(np.float32)
+        p, n_f, n_real = oracle.params(seed=62, fmax=4.0), 333, 17
+    else:                    # two column blocks, several K chunks per stage ring
+        xy = wl.pupil_grid(32, 8.0)[:200]
+        p, n_f, n_real = oracle.params(seed=63), 1000, 300
+    off = 3
+    col_psd = np.stack([rng.uniform(0.08, 0.2, n_real), rng.uniform(20, 50, n_real)], -1)
+    got = _run(h, p, n_f, n_real, xy, mode, off, col_psd)
+    ref = oracle.synthesize_shared(p, n_f, n_real, xy, real_offset=off, col_psd=col_psd)
+    sig = _col_sigma(p, n_f, n_real, off, col_psd)
+    err = np.abs(got - ref) / sig[:, None]
+    print("%s %s: max err %.3g sigma, rms %.3g sigma" % (mode, case, err.max(), np.sqrt(np.mean(err ** 2))))
+    assert np.isfinite(got).all()
+    assert err.max() <= TOL[mode]
+
+
+def test_gemm_column0_equals_fused_realisation(h):
+    xy = wl.pupil_grid(40, 8.0)
+    p = qrs.params(seed=64)
+    g = _run(h, p, 512, 8, xy, "gemm_3xtf32", 9, None)
+    fu = qrs.qrs_synthesize_points(h, p, 512, 1, torch.from_numpy(xy).cuda(), real_offset=9)
+    torch.cuda.synchronize()
+    sig = _col_sigma(oracle.params(seed=64), 512, 1, 9, None)
+    assert np.max(np.abs(g[0] - fu.cpu().numpy()[0])) <= 2e-5 * sig[0]
+
+
+def test_gemm_full_size_sampled(h):
+    """The 16 m / 512^2 pupil (205,892 points), N_f = 16384 shared by 256
+    columns with r0 in [0.08, 0.2] m, L0 in [20, 50] m: 16 sampled points, all
+    256 columns, against the oracle."""
+    cfg = wl.GEMM_SCREEN
+    p = wl.method_params(cfg)
+    xy = wl.pupil_grid(cfg["grid"], cfg["pupil"])
+    rng = np.random.default_rng(cfg["seed"])
+    R = cfg["n_real"]
+    col_psd = np.stack([rng.uniform(*cfg["r0_range"], R), rng.uniform(*cfg["L0_range"], R)], -1)
+    got = _run(h, p, cfg["n_f"], R, xy, "gemm_3xtf32", 0, col_psd)
+    idx = rng.choice(xy.shape[0], 16, replace=False)
+    ref = oracle.synthesize_shared(p, cfg["n_f"], R, xy[idx], col_psd=col_psd)
+    sig = _col_sigma(p, cfg["n_f"], R, 0, col_psd)
+    err = np.abs(got[:, idx] - ref) / sig[:, None]
+    print("full-size 3xTF32: max err %.3g sigma" % err.max())
+    assert err.max() <= TOL["gemm_3xtf32"]
