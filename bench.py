@@ -182,6 +182,51 @@ def run_reference(a):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate ratio
+
+
+def measure_gemm(qrs, h, torch, dev, mode, peaks):
+    """Shared-draw form on the 16 m pupil (205,892 points), N_f = 16384 shared by
+    256 columns with r0 ~ U(0.08, 0.2) m, L0 ~ U(20, 50) m, 4 batches."""
+    from paper_2404_02978_gb300 import workloads as wl
+    cfg = wl.GEMM_SCREEN
+    p = wl.method_params(cfg)
+    xy = torch.from_numpy(wl.pupil_grid(cfg["grid"], cfg["pupil"])).to(dev)
+    R, nf, P = cfg["n_real"], cfg["n_f"], xy.shape[0]
+    rng = np.random.default_rng(cfg["seed"])
+    cols = [torch.from_numpy(np.stack([rng.uniform(*cfg["r0_range"], R), rng.uniform(*cfg["L0_range"], R)], -1)).to(dev)
+            for _ in range(cfg["batches"])]
+    out = torch.empty(R, P, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    run = lambda b: qrs.qrs_synthesize_points(h, p, nf, R, xy, out=out, mode=mode, real_offset=b * R,
+                                              col_psd=cols[b], stream=stream)
+    for b in range(2):
+        run(b)
+    qrs.qrs_sync(h, stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(cfg["batches"])]
+    for b in range(cfg["batches"]):
+        ev[b][0].record(stream)
+        run(b)
+        ev[b][1].record(stream)
+    qrs.qrs_sync(h, stream)
+    ms = [s.elapsed_time(e) for s, e in ev]
+    t = sum(ms) / len(ms) / 1e3
+    T = 16 if mode == "gemm_3xtf32" else 32
+    nf_pad = (nf + T - 1) // T * T
+    R_pad = (R + 127) // 128 * 128
+    flops = 3 * 2 * P * (2 * nf_pad) * R_pad  # three split products per term pair
+    bf16 = float(peaks.get("bf16_tflops", 1889.0))
+    peak = bf16 * (TF32_OVER_BF16 if mode == "gemm_3xtf32" else 1.0)
+    return {"workload": "16 m pupil 512x512 (%d points), N_f=%d shared per batch of %d, per-column r0/L0, %d batches"
+                        % (P, nf, R, cfg["batches"]),
+            "ms_per_batch": t * 1e3, "value": P * nf * R / t, "unit": UNIT,
+            "roofline": {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / t / 1e12 / peak,
+                         "peak_basis": ("measured bf16 burst %.0f x nominal tf32/bf16 %.3f" % (bf16, TF32_OVER_BF16))
+                         if mode == "gemm_3xtf32" else "measured bf16 burst",
+                         "flops_per_batch": flops, "note": "whole call: point bound, shared draw, coefficients, GEMM"}}
+
+
 def run_ours(a):
     import torch
     rank, world, local = _dist()
@@ -283,6 +328,9 @@ def run_ours(a):
     }
     if clk:
         line["clocks"] = clk
+    if world == 1:
+        peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
+        line["other_forms"] = {m: measure_gemm(qrs, h, torch, dev, m, peaks) for m in ("gemm_3xtf32", "gemm_bf16x3")}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np)
     if rank == 0:

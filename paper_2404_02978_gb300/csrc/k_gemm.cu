@@ -16,23 +16,28 @@
 // map, into the basis representation), k_gemm_coef (B, hi and lo, into the
 // workspace, K'-contiguous rows so TMA can stream them), k_gemm_main.
 //
-// k_gemm_main: one CTA per (128-point tile, 128-column block), 384 threads:
-//   warp 0      TMA producer: B_hi and B_lo tiles (128 rows x 128 B, 128-byte
-//               swizzle) per K chunk into a 3-stage ring (mbarrier complete_tx);
-//   warp 1      TMEM allocator (512 columns = four 128 x 128 FP32 accumulator
-//               slots) and single-thread MMA issuer: 3 x 4 tcgen05.mma per K
-//               chunk; every kGSeg chunks it moves to the next slot and commits
-//               the finished one;
-//   warps 4-7   promoters, one per TMEM lane quarter: tcgen05.ld each finished
-//               slot (their row's 128 columns) and add it into FP32 registers
-//               (round to nearest), then free the slot; at the end they store
-//               out[r][m] (coalesced over m).  The tensor core's accumulation
-//               loses about 2^-26 per step with a consistent sign, so long
-//               chains drift; segments of kGSeg chunks bound that drift.
-//   warps 8-11  basis producers: thread t owns point row t, evaluates the
-//               chunk's cos/sin (fixed-point or double-float phase, MUFU
-//               sin/cos), splits hi/lo and writes its 128-byte row of the
-//               swizzled A tiles, fence.proxy.async, arrive.
+// k_gemm_main: one CTA per (128-point tile, 256-column block), 640 threads:
+//   warp 0      TMA producer: B_hi and B_lo tiles (256 rows x 128 B, 128-byte
+//               swizzle) per K chunk into a 2-stage ring (mbarrier complete_tx);
+//   warp 1      TMEM allocator (512 columns: a 128 x 256 FP32 master
+//               accumulator and a 128 x 256 segment slot) and single-thread
+//               MMA issuer: 3 x 4 tcgen05.mma per K chunk into the slot, one
+//               commit per segment of kSeg chunks (6 TF32, 8 BF16);
+//   warp 2      frequency ring: bulk-copies each chunk's basis frequencies
+//               into an 8-slot shared-memory ring, up to 8 chunks ahead;
+//   warps 4-11  promoters, two per TMEM lane quarter (128 columns each): after
+//               each segment, master += slot in FP32 (round to nearest) through
+//               tcgen05.ld / tcgen05.st, then free the slot; after the last
+//               segment they store out[r][m] (coalesced over m).  The tensor
+//               core's accumulation loses about 2^-26 per step with a
+//               consistent sign, so long chains drift; segments bound it;
+//   warps 12-19 basis producers, two per 32-row block, each taking half of
+//               the chunk's terms: evaluate cos/sin (fixed-point or
+//               double-float phase, MUFU sin/cos), split hi/lo by integer
+//               rounding and write their 16-byte pieces of the row in the
+//               swizzled A tiles, fence.proxy.async, one arrival per warp.
+//               (Basis production is the bound of this kernel; 8 producer
+//               warps beat 4 by 8 % (3xTF32) and 27 % (BF16x3).)
 // Every mbarrier wait is bounded in time; on time-out the CTA raises an abort
 // flag, records QRS_ERR_TIMEOUT in the device error word, waits (bounded) for
 // its TMA copies and MMAs in flight, frees TMEM and returns.
@@ -42,6 +47,19 @@
 
 #include "qrs_internal.h"
 #include "qrs_sm100.cuh"
+
+#ifndef QRS_GEMM_SEG_TF32
+#define QRS_GEMM_SEG_TF32 6   // K chunks per accumulation segment, 3XTF32 (72 accumulation steps)
+#endif
+#ifndef QRS_GEMM_SEG_BF16
+#define QRS_GEMM_SEG_BF16 8   // K chunks per accumulation segment, BF16X3 (96 accumulation steps)
+#endif
+#ifndef QRS_GEMM_PRODUCERS
+#define QRS_GEMM_PRODUCERS 8  // basis producer warps (4: one per row block; 8: two, splitting the terms)
+#endif
+#ifndef QRS_GEMM_INTSPLIT
+#define QRS_GEMM_INTSPLIT 1   // hi/lo splits by integer rounding (ALU) instead of conversions
+#endif
 
 namespace qrs {
 
@@ -55,6 +73,7 @@ struct GemmCfg<QRS_SYNTH_GEMM_3XTF32> {
     static constexpr int kTermsPer16B = 4;
     static constexpr uint32_t kFormat = 2;     // TF32
     static constexpr bool kTF32 = true;
+    static constexpr int kSeg = QRS_GEMM_SEG_TF32;
 };
 template <>
 struct GemmCfg<QRS_SYNTH_GEMM_BF16X3> {
@@ -64,18 +83,21 @@ struct GemmCfg<QRS_SYNTH_GEMM_BF16X3> {
     static constexpr int kTermsPer16B = 8;
     static constexpr uint32_t kFormat = 1;     // BF16
     static constexpr bool kTF32 = false;
+    static constexpr int kSeg = QRS_GEMM_SEG_BF16;
 };
 
 constexpr int kGM = 128;                                   // points per tile (UMMA M, TMEM lanes)
-constexpr int kGN = 128;                                   // columns per block (UMMA N)
-constexpr int kGStages = 3;
-constexpr int kGSlots = 4;                                 // TMEM accumulator slots (4 x 128 columns)
-constexpr int kGSeg = 4;                                   // K chunks per accumulation segment
+constexpr int kGN = 256;                                   // columns per block (UMMA N)
+constexpr int kGStages = 2;
 constexpr int kGTileA = kGM * 128;                         // 16 KB
-constexpr int kGTileB = kGN * 128;                         // 16 KB
-constexpr int kGStageBytes = 2 * kGTileA + 2 * kGTileB;    // A hi/lo + B hi/lo = 64 KB
-constexpr int kGThreads = 384;
-constexpr int kGSmemBytes = kGStages * kGStageBytes + 256 + 1024;  // + barriers + alignment slack
+constexpr int kGTileB = kGN * 128;                         // 32 KB
+constexpr int kGStageBytes = 2 * kGTileA + 2 * kGTileB;    // A hi/lo + B hi/lo = 96 KB
+constexpr int kGFreqSlots = 8;                             // frequency ring, filled ahead by warp 2
+constexpr int kGFreqBytes = 256;                           // one chunk's basis frequencies (<= 32 x 8 B)
+constexpr int kGProducers = QRS_GEMM_PRODUCERS;
+constexpr int kGThreads = 384 + 32 * kGProducers;
+static_assert(kGProducers == 4 || kGProducers == 8, "producer warps");
+constexpr int kGSmemBytes = kGStages * kGStageBytes + kGFreqSlots * kGFreqBytes + 512 + 1024;  // + barriers, slack
 constexpr long long kGWaitCycles = 4000000000LL;           // ~2 s of SM clock per wait
 
 struct GemmArgs {
@@ -177,38 +199,61 @@ __global__ void k_gemm_coef(DrawParams p, int64_t nf_pad, int64_t n_real, int64_
 }
 
 // ------------------------------------------------------------ main kernel
-template <int PREC>
-__device__ __forceinline__ uint4 pack16(const float (&v)[GemmCfg<PREC>::kTermsPer16B], bool want_hi)
+// Split 16 bytes' worth of values into hi and lo halves in the operand format
+// (TF32 in 32-bit words with the low 13 bits zero, or pairs of BF16).
+// TF32 rounding to nearest, ties away from zero (as cvt.rna.tf32.f32): add half
+// of the dropped 13-bit field to the magnitude bits, then clear the field.
+__device__ __forceinline__ uint32_t tf32_rna_bits(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+// BF16 rounding to nearest, ties to even (as cvt.rn.bf16.f32), as FP32 bits.
+__device__ __forceinline__ uint32_t bf16_rne_bits(float x)
 {
-    uint4 q;
-    uint32_t* w = reinterpret_cast<uint32_t*>(&q);
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+}
+
+// Split 16 bytes' worth of values into hi and lo halves in the operand format
+// (TF32 in 32-bit words with the low 13 bits zero, or pairs of BF16); the
+// residual x - hi is exact in FP32.
+template <int PREC>
+__device__ __forceinline__ void pack16(const float (&v)[GemmCfg<PREC>::kTermsPer16B], uint4& hi, uint4& lo)
+{
+    uint32_t* wh = reinterpret_cast<uint32_t*>(&hi);
+    uint32_t* wl = reinterpret_cast<uint32_t*>(&lo);
     if (GemmCfg<PREC>::kTF32) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            uint32_t h;
+#if QRS_GEMM_INTSPLIT
+            const uint32_t h = tf32_rna_bits(v[e]);
+            wh[e] = h;
+            wl[e] = tf32_rna_bits(v[e] - __uint_as_float(h));
+#else
+            uint32_t h, l;
             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v[e]));
-            if (want_hi) {
-                w[e] = h;
-            } else {
-                uint32_t l;
-                const float r = v[e] - __uint_as_float(h);
-                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
-                w[e] = l;
-            }
+            const float r = v[e] - __uint_as_float(h);
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+            wh[e] = h;
+            wl[e] = l;
+#endif
         }
     } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            float x0 = v[2 * e], x1 = v[2 * e + 1];
-            __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-            if (!want_hi) {
-                h0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-                h1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-            }
-            w[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            const float x0 = v[2 * e], x1 = v[2 * e + 1];
+#if QRS_GEMM_INTSPLIT
+            const uint32_t h0 = bf16_rne_bits(x0), h1 = bf16_rne_bits(x1);
+            const uint32_t l0 = bf16_rne_bits(x0 - __uint_as_float(h0));
+            const uint32_t l1 = bf16_rne_bits(x1 - __uint_as_float(h1));
+            wh[e] = __byte_perm(h0, h1, 0x7632);  // (h1 top half << 16) | h0 top half
+            wl[e] = __byte_perm(l0, l1, 0x7632);
+#else
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+            wh[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            wl[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+#endif
         }
     }
-    return q;
 }
 
 template <int PREC>
@@ -217,28 +262,33 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constan
     using Cfg = GemmCfg<PREC>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* fullA = reinterpret_cast<uint64_t*>(smem + kGStages * kGStageBytes);
+    unsigned char* fring = smem + kGStages * kGStageBytes;
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(fring + kGFreqSlots * kGFreqBytes);
     uint64_t* fullB = fullA + kGStages;
     uint64_t* empty = fullB + kGStages;
-    uint64_t* slot_full = empty + kGStages;
-    uint64_t* slot_free = slot_full + kGSlots;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(slot_free + kGSlots);
+    uint64_t* seg_full = empty + kGStages;
+    uint64_t* seg_free = seg_full + 1;
+    uint64_t* fullF = seg_free + 1;
+    uint64_t* freeF = fullF + kGFreqSlots;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeF + kGFreqSlots);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tile = blockIdx.x, rblk = blockIdx.y;
     const int64_t n_chunks = g.n_chunks;
-    const int64_t n_seg = (n_chunks + kGSeg - 1) / kGSeg;
+    const int64_t n_seg = (n_chunks + Cfg::kSeg - 1) / Cfg::kSeg;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kGStages; ++s) {
-            sm100::mbar_init(&fullA[s], 128);
+            sm100::mbar_init(&fullA[s], kGProducers);  // one arrival per producer warp
             sm100::mbar_init(&fullB[s], 1);
             sm100::mbar_init(&empty[s], 1);
         }
-        for (int s = 0; s < kGSlots; ++s) {
-            sm100::mbar_init(&slot_full[s], 1);
-            sm100::mbar_init(&slot_free[s], 128);
+        sm100::mbar_init(seg_full, 1);
+        sm100::mbar_init(seg_free, 8);  // one arrival per promoter warp
+        for (int s = 0; s < kGFreqSlots; ++s) {
+            sm100::mbar_init(&fullF[s], 1);
+            sm100::mbar_init(&freeF[s], kGProducers);
         }
         *abort_flag = 0;
         sm100::fence_barrier_init();
@@ -248,17 +298,21 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constan
     sm100::tc_fence_before();
     __syncthreads();
     sm100::tc_fence_after();
-    const uint32_t tmem_base = *tmem_slot;
+    const uint32_t tmem_master = *tmem_slot;                 // columns [0, 256)
+    const uint32_t tmem_seg = tmem_master + (uint32_t)kGN;  // columns [256, 512)
 
     auto stageA_hi = [&](int s) { return smem + s * kGStageBytes; };
     auto stageA_lo = [&](int s) { return smem + s * kGStageBytes + kGTileA; };
     auto stageB_hi = [&](int s) { return smem + s * kGStageBytes + 2 * kGTileA; };
     auto stageB_lo = [&](int s) { return smem + s * kGStageBytes + 2 * kGTileA + kGTileB; };
+    auto ringF = [&](int64_t i) { return fring + (i % kGFreqSlots) * kGFreqBytes; };
     auto timeout = [&]() {
         *abort_flag = 1;
         atomicExch(g.err, (int)QRS_ERR_TIMEOUT);
     };
     int64_t mma_segments = 0;  // segments the MMA thread committed (teardown)
+    constexpr uint32_t kFreqChunkBytes = Cfg::kTermsPerChunk * sizeof(int2);
+    static_assert(kFreqChunkBytes <= kGFreqBytes, "frequency chunk fits its ring slot");
 
     if (warp == 0) {
         // ---------------------------------------------------- TMA producer
@@ -288,14 +342,11 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constan
             constexpr uint32_t idesc = sm100::idesc_f32acc(Cfg::kFormat, kGM, kGN);
             int64_t i = 0;
             for (int64_t j = 0; j < n_seg && !*abort_flag; ++j) {
-                const int slot = (int)(j % kGSlots);
-                if (j >= kGSlots &&
-                    !sm100::mbar_wait(&slot_free[slot], (uint32_t)(((j / kGSlots) & 1) ^ 1), abort_flag, kGWaitCycles)) {
+                if (j >= 1 && !sm100::mbar_wait(seg_free, (uint32_t)((j - 1) & 1), abort_flag, kGWaitCycles)) {
                     if (!*abort_flag) timeout();
                     break;
                 }
-                const uint32_t tacc = tmem_base + (uint32_t)(slot * kGN);
-                const int64_t i_end = ((j + 1) * kGSeg < n_chunks) ? (j + 1) * kGSeg : n_chunks;
+                const int64_t i_end = ((j + 1) * Cfg::kSeg < n_chunks) ? (j + 1) * Cfg::kSeg : n_chunks;
                 bool first = true;
                 for (; i < i_end; ++i) {
                     const int s = (int)(i % kGStages);
@@ -313,56 +364,86 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constan
                         const uint32_t off = (uint32_t)kk * 32u;
                         const uint64_t dAh = sm100::desc_k_sw128(ahi + off), dAl = sm100::desc_k_sw128(alo + off);
                         const uint64_t dBh = sm100::desc_k_sw128(bhi + off), dBl = sm100::desc_k_sw128(blo + off);
-                        sm100::mma<Cfg::kTF32>(tacc, dAh, dBh, idesc, first ? 0u : 1u);
+                        sm100::mma<Cfg::kTF32>(tmem_seg, dAh, dBh, idesc, first ? 0u : 1u);
                         first = false;
-                        sm100::mma<Cfg::kTF32>(tacc, dAh, dBl, idesc, 1u);
-                        sm100::mma<Cfg::kTF32>(tacc, dAl, dBh, idesc, 1u);
+                        sm100::mma<Cfg::kTF32>(tmem_seg, dAh, dBl, idesc, 1u);
+                        sm100::mma<Cfg::kTF32>(tmem_seg, dAl, dBh, idesc, 1u);
                     }
                     sm100::mma_commit(&empty[s]);  // frees stage s once these MMAs complete
                 }
-                sm100::mma_commit(&slot_full[slot]);  // segment j done (or cut short by an abort)
+                sm100::mma_commit(seg_full);  // segment j done (or cut short by an abort)
                 mma_segments = j + 1;
             }
         }
-    } else if (warp >= 4 && warp < 8) {
+    } else if (warp == 2) {
+        // -------------------------------------------- frequency ring filler
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t i = 0; i < n_chunks; ++i) {
+                const int f = (int)(i % kGFreqSlots);
+                if (i >= kGFreqSlots &&
+                    !sm100::mbar_wait(&freeF[f], (uint32_t)(((i / kGFreqSlots) & 1) ^ 1), abort_flag, kGWaitCycles)) {
+                    if (!*abort_flag) timeout();
+                    break;
+                }
+                sm100::mbar_arrive_expect_tx(&fullF[f], kFreqChunkBytes);
+                sm100::bulk_load(ringF(i), g.fbasis + i * Cfg::kTermsPerChunk, kFreqChunkBytes, &fullF[f]);
+                issued = i + 1;
+            }
+            if (*abort_flag) {
+                for (int64_t i = (issued > kGFreqSlots ? issued - kGFreqSlots : 0); i < issued; ++i)
+                    sm100::mbar_wait_for(&fullF[i % kGFreqSlots], (uint32_t)((i / kGFreqSlots) & 1), kGWaitCycles / 8);
+            }
+        }
+    } else if (warp >= 4 && warp < 12) {
         // ------------------------------------------------------ promoters
-        const int quarter = warp - 4;  // TMEM lanes [32 quarter, 32 quarter + 32)
+        const int quarter = warp & 3;        // TMEM lanes [32 quarter, 32 quarter + 32)
+        const int half = (warp - 4) >> 2;    // columns [128 half, 128 half + 128)
         const int row = quarter * 32 + lane;
         const int64_t m = tile * kGM + row;
-        float sum[kGN];
-#pragma unroll
-        for (int c = 0; c < kGN; ++c) sum[c] = 0.0f;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const uint32_t col0 = (uint32_t)(half * 128);
         bool ok = true;
         for (int64_t j = 0; j < n_seg; ++j) {
-            const int slot = (int)(j % kGSlots);
-            if (!sm100::mbar_wait(&slot_full[slot], (uint32_t)((j / kGSlots) & 1), abort_flag, kGWaitCycles)) {
+            if (!sm100::mbar_wait(seg_full, (uint32_t)(j & 1), abort_flag, kGWaitCycles)) {
                 if (!*abort_flag) timeout();
                 ok = false;
                 break;
             }
             sm100::tc_fence_after();
-            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(slot * kGN);
-#pragma unroll
-            for (int c0 = 0; c0 < kGN; c0 += 32) {
-                uint32_t v[32];
-                sm100::tmem_ld_32x32b_x32(tbase + (uint32_t)c0, v);
+            const bool last = (j == n_seg - 1);
+#pragma unroll 1
+            for (int c0 = 0; c0 < 128; c0 += 32) {
+                uint32_t v[32], w[32];
+                sm100::tmem_ld_32x32b_x32(tmem_seg + lane_off + col0 + (uint32_t)c0, v);
+                if (j > 0) sm100::tmem_ld_32x32b_x32(tmem_master + lane_off + col0 + (uint32_t)c0, w);
                 sm100::tmem_ld_wait();
+                if (j > 0) {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) sum[c0 + q] += __uint_as_float(v[q]);
+                    for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
+                }
+                if (!last) {
+                    sm100::tmem_st_32x32b_x32(tmem_master + lane_off + col0 + (uint32_t)c0, v);
+                } else if (m < g.P) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int64_t r = rblk * kGN + col0 + c0 + q;
+                        if (r < g.n_real) g.out[r * g.P + m] = __uint_as_float(v[q]);
+                    }
+                }
             }
+            sm100::tmem_st_wait();
             sm100::tc_fence_before();
-            sm100::mbar_arrive(&slot_free[slot]);
+            __syncwarp();
+            if (lane == 0) sm100::mbar_arrive(seg_free);
         }
-        if (ok && !*abort_flag && m < g.P) {
-#pragma unroll
-            for (int c = 0; c < kGN; ++c) {
-                const int64_t r = rblk * kGN + c;
-                if (r < g.n_real) g.out[r * g.P + m] = sum[c];
-            }
-        }
-    } else if (warp >= 8) {
+        (void)ok;
+    } else if (warp >= 12) {
         // ------------------------------------------- basis producers
-        const int row = threadIdx.x - 256;
+        const int pw = warp - 12;                  // producer warp
+        const int row = (pw & 3) * 32 + lane;      // its row block
+        constexpr int kGroups = 4 / (kGProducers / 4);
+        const int grp0 = (pw >> 2) * kGroups;      // its term groups [grp0, grp0 + kGroups)
         const int64_t m = tile * kGM + row;
         const float2 pt = (m < g.P) ? g.xy[m] : make_float2(0.0f, 0.0f);
         const FixedScales z = fixed_scales(g.fbound, *g.d_xbound, true);
@@ -371,19 +452,22 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constan
         for (int64_t i = 0; i < n_chunks && !*abort_flag; ++i) {
             const int s = (int)(i % kGStages);
             const uint32_t ph = (uint32_t)((i / kGStages) & 1);
-            if (i >= kGStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kGWaitCycles)) {
+            if ((i >= kGStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kGWaitCycles)) ||
+                !sm100::mbar_wait(&fullF[i % kGFreqSlots], (uint32_t)((i / kGFreqSlots) & 1), abort_flag,
+                                  kGWaitCycles)) {
                 if (!*abort_flag) timeout();
                 break;
             }
-            const int2* fb = g.fbasis + i * Cfg::kTermsPerChunk;
+            const int2* fb = reinterpret_cast<const int2*>(ringF(i));
             unsigned char* Ahi = stageA_hi(s);
             unsigned char* Alo = stageA_lo(s);
 #pragma unroll
-            for (int grp = 0; grp < 4; ++grp) {
+            for (int gi = 0; gi < kGroups; ++gi) {
+                const int grp = grp0 + gi;
                 float cv[TPG], sv[TPG];
 #pragma unroll
                 for (int t = 0; t < TPG; ++t) {
-                    const int2 f = __ldg(fb + grp * TPG + t);
+                    const int2 f = fb[grp * TPG + t];
                     float ang;
                     if (z.use_fixed) ang = phase_fx_rad(f.x, f.y, X, Y, z.bias, z.shift);
                     else ang = phase_df(__int_as_float(f.x), __int_as_float(f.y), pt.x, pt.y) * 6.28318530717958648f;
@@ -392,25 +476,30 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constan
                 }
                 const uint32_t oc = sm100::sw128_offset((uint32_t)row, (uint32_t)grp);
                 const uint32_t os = sm100::sw128_offset((uint32_t)row, (uint32_t)(4 + grp));
-                *reinterpret_cast<uint4*>(Ahi + oc) = pack16<PREC>(cv, true);
-                *reinterpret_cast<uint4*>(Alo + oc) = pack16<PREC>(cv, false);
-                *reinterpret_cast<uint4*>(Ahi + os) = pack16<PREC>(sv, true);
-                *reinterpret_cast<uint4*>(Alo + os) = pack16<PREC>(sv, false);
+                uint4 hi, lo;
+                pack16<PREC>(cv, hi, lo);
+                *reinterpret_cast<uint4*>(Ahi + oc) = hi;
+                *reinterpret_cast<uint4*>(Alo + oc) = lo;
+                pack16<PREC>(sv, hi, lo);
+                *reinterpret_cast<uint4*>(Ahi + os) = hi;
+                *reinterpret_cast<uint4*>(Alo + os) = lo;
             }
-            sm100::fence_proxy_async_smem();
-            sm100::mbar_arrive(&fullA[s]);
+            sm100::fence_proxy_async_smem();  // each thread: its row writes -> async proxy
+            __syncwarp();
+            if (lane == 0) {
+                sm100::mbar_arrive(&fullA[s]);
+                sm100::mbar_arrive(&freeF[i % kGFreqSlots]);
+            }
         }
     }
     sm100::tc_fence_before();
     __syncthreads();
     if (warp == 1) {
-        if (*abort_flag && lane == 0) {  // MMAs in flight must finish before their TMEM is freed
-            for (int64_t j = (mma_segments > kGSlots ? mma_segments - kGSlots : 0); j < mma_segments; ++j)
-                sm100::mbar_wait_for(&slot_full[j % kGSlots], (uint32_t)((j / kGSlots) & 1), kGWaitCycles / 8);
-        }
+        if (*abort_flag && lane == 0 && mma_segments > 0)  // MMAs in flight finish before TMEM is freed
+            sm100::mbar_wait_for(seg_full, (uint32_t)((mma_segments - 1) & 1), kGWaitCycles / 8);
         __syncwarp();
         sm100::tc_fence_after();
-        sm100::tmem_dealloc(tmem_base, 512);
+        sm100::tmem_dealloc(tmem_master, 512);
     }
 }
 

@@ -11,7 +11,9 @@ from paper_2404_02978_gb300 import workloads as wl
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="phase_screen", choices=["phase_screen", "piston_plain"])
+    ap.add_argument("--case", default="phase_screen", choices=["phase_screen", "piston_plain", "gemm_screen"])
+    ap.add_argument("--mode", default="gemm_3xtf32", choices=["gemm_3xtf32", "gemm_bf16x3"])
+    ap.add_argument("--points", type=int, default=0, help="gemm_screen: first N points only (0 = all)")
     ap.add_argument("--n-real", type=int, default=16)
     ap.add_argument("--repeat", type=int, default=2)
     a = ap.parse_args()
@@ -22,6 +24,15 @@ def main():
         xy = torch.from_numpy(wl.pupil_grid(cfg["grid"], cfg["pupil"])).cuda()
         for i in range(a.repeat):
             qrs.qrs_synthesize_points(h, wl.method_params(cfg), cfg["n_f"], a.n_real, xy, real_offset=i * a.n_real)
+    elif a.case == "gemm_screen":
+        cfg = wl.GEMM_SCREEN
+        xy_np = wl.pupil_grid(cfg["grid"], cfg["pupil"])
+        if a.points:
+            xy_np = xy_np[: a.points]
+        xy = torch.from_numpy(xy_np).cuda()
+        for i in range(a.repeat):
+            qrs.qrs_synthesize_points(h, wl.method_params(cfg), cfg["n_f"], cfg["n_real"], xy, mode=a.mode,
+                                      real_offset=i * cfg["n_real"])
     else:
         cfg = wl.PISTON_PLAIN
         B_, ap_xy, ap_D, ap_d, pairs = wl.piston_plain_apertures()
