@@ -13,22 +13,31 @@
 // batch of jobs (QRS_PISTON_PERSISTENT) runs as one persistent grid whose
 // CTAs pull items from an atomic counter over a cost-sorted item order
 // (largest N_f n_ap first), so uneven jobs balance across SMs.  The queue
-// never waits on anything, so there is no spin to bound.
+// never waits on anything, so there is no spin to bound.  The persistent
+// kernel comes in three shapes (threads per CTA x terms per slice) among
+// which the host-side autotuner picks per job-set shape.
 #include "qrs_internal.h"
 #include "qrs_piston.h"
 
 namespace qrs {
 
-constexpr int kPisTPB = 256;
-constexpr int kPisWarps = kPisTPB / 32;
 constexpr int kPisChunk = 2048;  // terms per shared-memory chunk
-constexpr int kPisSlice = 256;   // terms per (aperture, slice) unit
-constexpr int kPisSlices = kPisChunk / kPisSlice;
 
+// Kernel shapes the autotuner chooses from: threads per CTA and terms per
+// (aperture, slice) unit.
+template <int TPB, int SLICE>
+struct PisShape {
+    static constexpr int kTPB = TPB;
+    static constexpr int kWarps = TPB / 32;
+    static constexpr int kSlice = SLICE;
+    static constexpr int kSlices = kPisChunk / SLICE;
+};
+
+template <int SLICES>
 struct PisShared {
     float4 rec[kPisChunk];             // fx, fy, A = F a, nB = -F b
     float fabs_[kPisChunk];            // |f|
-    float part[kPisMaxAp][kPisSlices];  // per-slice partial pistons of the chunk
+    float part[kPisMaxAp][SLICES];     // per-slice partial pistons of the chunk
     float total[kPisMaxAp];
     float apx[kPisMaxAp], apy[kPisMaxAp], apD[kPisMaxAp], apd[kPisMaxAp];
 };
@@ -40,8 +49,10 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-__device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared& sh, int* err)
+template <class S>
+__device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlices>& sh, int* err)
 {
+    constexpr int kPisTPB = S::kTPB, kPisWarps = S::kWarps, kPisSlice = S::kSlice;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_ap = J.n_ap;
     for (int a = tid; a < n_ap; a += kPisTPB) {
@@ -102,20 +113,23 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared& sh, int
 }
 
 // Single job: grid-stride over its realisations.
-__global__ void __launch_bounds__(kPisTPB) k_piston_single(PistonJobDev J, int* err)
+using PisDefault = PisShape<256, 256>;
+
+__global__ void __launch_bounds__(256) k_piston_single(PistonJobDev J, int* err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PisShared& sh = *reinterpret_cast<PisShared*>(smem_raw);
-    for (int64_t r = blockIdx.x; r < J.n_real; r += gridDim.x) piston_item(J, r, sh, err);
+    auto& sh = *reinterpret_cast<PisShared<PisDefault::kSlices>*>(smem_raw);
+    for (int64_t r = blockIdx.x; r < J.n_real; r += gridDim.x) piston_item<PisDefault>(J, r, sh, err);
 }
 
 // Batch: items (job, realisation) in cost-sorted job order, pulled from an
 // atomic counter.  jobs[] sorted by descending cost, item_begin its prefix sums.
-__global__ void __launch_bounds__(kPisTPB) k_piston_persistent(const PistonJobDev* __restrict__ jobs, int n_jobs,
+template <class S>
+__global__ void __launch_bounds__(S::kTPB) k_piston_persistent(const PistonJobDev* __restrict__ jobs, int n_jobs,
                                                                int64_t n_items, unsigned long long* counter, int* err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PisShared& sh = *reinterpret_cast<PisShared*>(smem_raw);
+    auto& sh = *reinterpret_cast<PisShared<S::kSlices>*>(smem_raw);
     __shared__ long long s_item;
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
@@ -129,41 +143,60 @@ __global__ void __launch_bounds__(kPisTPB) k_piston_persistent(const PistonJobDe
             if (jobs[mid].item_begin <= g) lo = mid; else hi = mid;
         }
         const PistonJobDev J = jobs[lo];
-        piston_item(J, g - J.item_begin, sh, err);
+        piston_item<S>(J, g - J.item_begin, sh, err);
     }
 }
 
-size_t piston_smem_bytes() { return sizeof(PisShared); }
+size_t piston_smem_bytes() { return sizeof(PisShared<PisDefault::kSlices>); }
 
 cudaError_t launch_piston_single(const PistonJobDev& J, int num_sms, int* err, cudaStream_t s)
 {
-    const size_t smem = sizeof(PisShared);
+    const size_t smem = sizeof(PisShared<PisDefault::kSlices>);
     cudaError_t e = cudaFuncSetAttribute(k_piston_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_piston_single, kPisTPB, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_piston_single, 256, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > J.n_real) grid = J.n_real;
-    k_piston_single<<<(unsigned)grid, kPisTPB, smem, s>>>(J, err);
+    k_piston_single<<<(unsigned)grid, 256, smem, s>>>(J, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_piston_persistent(const PistonJobDev* d_jobs, int n_jobs, int64_t n_items,
-                                     unsigned long long* d_counter, int num_sms, int* err, cudaStream_t s)
+template <class S>
+static cudaError_t launch_persistent_t(const PistonJobDev* d_jobs, int n_jobs, int64_t n_items,
+                                       unsigned long long* d_counter, int num_sms, int* err, cudaStream_t s)
 {
-    const size_t smem = sizeof(PisShared);
-    cudaError_t e = cudaFuncSetAttribute(k_piston_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sizeof(PisShared<S::kSlices>);
+    cudaError_t e = cudaFuncSetAttribute(k_piston_persistent<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_piston_persistent, kPisTPB, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_piston_persistent<S>, S::kTPB, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > n_items) grid = n_items;
-    k_piston_persistent<<<(unsigned)grid, kPisTPB, smem, s>>>(d_jobs, n_jobs, n_items, d_counter, err);
+    k_piston_persistent<S><<<(unsigned)grid, S::kTPB, smem, s>>>(d_jobs, n_jobs, n_items, d_counter, err);
     return cudaGetLastError();
+}
+
+int piston_shape_count() { return 3; }
+
+const char* piston_shape_name(int shape)
+{
+    static const char* names[] = {"tpb256_slice256", "tpb256_slice128", "tpb128_slice128"};
+    return (shape >= 0 && shape < 3) ? names[shape] : "?";
+}
+
+cudaError_t launch_piston_persistent(int shape, const PistonJobDev* d_jobs, int n_jobs, int64_t n_items,
+                                     unsigned long long* d_counter, int num_sms, int* err, cudaStream_t s)
+{
+    switch (shape) {
+    case 1: return launch_persistent_t<PisShape<256, 128>>(d_jobs, n_jobs, n_items, d_counter, num_sms, err, s);
+    case 2: return launch_persistent_t<PisShape<128, 128>>(d_jobs, n_jobs, n_items, d_counter, num_sms, err, s);
+    default: return launch_persistent_t<PisShape<256, 256>>(d_jobs, n_jobs, n_items, d_counter, num_sms, err, s);
+    }
 }
 
 }  // namespace qrs

@@ -49,23 +49,6 @@ qrs_status ensure_work(qrs_handle* h, size_t bytes)
     return QRS_OK;
 }
 
-static qrs_status ensure_stage(qrs_handle* h, size_t bytes)
-{
-    if (h->stage_bytes >= bytes) return QRS_OK;
-    if (h->h_stage) {
-        cudaError_t e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) return cuda_fail(h, e, "staging sync");
-        cudaFreeHost(h->h_stage);
-        h->h_stage = nullptr;
-        h->stage_bytes = 0;
-    }
-    size_t want = std::max(bytes, (size_t)1 << 16);
-    cudaError_t e = cudaMallocHost(&h->h_stage, want);
-    if (e != cudaSuccess) return cuda_fail(h, e, "pinned staging allocation");
-    h->stage_bytes = want;
-    return QRS_OK;
-}
-
 // Von Karman constant c = Gamma(11/6)^2 / (2 pi^(11/3)) (24/5 Gamma(6/5))^(5/6), from tgamma.
 static double vk_constant()
 {
@@ -186,6 +169,7 @@ void qrs_destroy(qrs_handle* h)
     if (!h) return;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
+    destroy_piston_state(h);
     if (h->d_err) cudaFree(h->d_err);
     if (h->d_work) cudaFree(h->d_work);
     if (h->h_stage) cudaFreeHost(h->h_stage);
@@ -318,7 +302,7 @@ qrs_status qrs_diff_piston(qrs_handle* h, const qrs_piston_job* jobs, int32_t n_
         }
         return QRS_OK;
     }
-    return fail(h, QRS_ERR_UNSUPPORTED, "persistent / graph piston batches are not built in this library version");
+    return run_piston_batch(h, dev, (flags & QRS_PISTON_GRAPH) != 0, s);
 }
 
 qrs_status qrs_structure_fn(qrs_handle* h, const float* delta, int64_t n_real, int64_t n_series, int64_t T,

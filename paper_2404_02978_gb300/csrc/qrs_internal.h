@@ -52,6 +52,9 @@ cudaError_t launch_structure_fn(const float* delta, int64_t n_real, int64_t n_se
                                 const int32_t* lags, int32_t n_lags, double* acc, int num_sms, int* err,
                                 cudaStream_t s);
 
+struct PistonJobDev;
+void destroy_piston_state(qrs_handle* h);
+
 size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real);
 cudaError_t launch_synth_gemm(qrs_handle* h, int mode, const DrawParams& p, const float* xy, int64_t P,
                               int64_t n_real, const double* col_psd, double c_vk, float* out, cudaStream_t s);

@@ -1,7 +1,9 @@
 // qrs_piston.h -- device-side job descriptor of the piston kernels.
 #pragma once
 
-#include "qrs_device.cuh"
+#include <vector>
+
+#include "qrs_internal.h"
 
 namespace qrs {
 
@@ -23,7 +25,10 @@ struct PistonJobDev {
 
 size_t piston_smem_bytes();
 cudaError_t launch_piston_single(const PistonJobDev& J, int num_sms, int* err, cudaStream_t s);
-cudaError_t launch_piston_persistent(const PistonJobDev* d_jobs, int n_jobs, int64_t n_items,
+qrs_status run_piston_batch(qrs_handle* h, std::vector<PistonJobDev>& jobs, bool graph, cudaStream_t s);
+int piston_shape_count();
+const char* piston_shape_name(int shape);
+cudaError_t launch_piston_persistent(int shape, const PistonJobDev* d_jobs, int n_jobs, int64_t n_items,
                                      unsigned long long* d_counter, int num_sms, int* err, cudaStream_t s);
 
 }  // namespace qrs
