@@ -1,0 +1,83 @@
+/*
+ * qrs_proposal.h -- learned frequency-sampling proposal of libqrs.
+ *
+ * The paper samples frequencies by a fixed heuristic and notes (Sec. 5) that
+ * a mapping that takes the properties of the PSD into account may be
+ * possible.  This is such a mapping: a small MLP maps a differential-piston
+ * geometry g = (r0, L0, D, Bx, By) -- Fried parameter, outer scale, aperture
+ * diameter, baseline vector -- to a density over the n_rho x n_theta
+ * log-polar cells of [fmin, fmax]; mixed with the uniform cell density and
+ * quantised to an integer CDF it drives the IMPORTANCE sampler of qrs.h,
+ * whose weights w = W area_c / (N_f p_c) keep Eq. 3 unbiased.  It is trained
+ * on what the plain method itself produces: per-cell contributions of plain
+ * log-polar R2 draws to the differential-piston structure function of the
+ * geometry (Sec. 4.4 with the Eq. 7 filter),
+ *     V_c = sum_{draws} sum_{k in c} w_k A(|f_k|)^2 2 (1 - cos 2 pi f_k . B),
+ * normalised to a target distribution t_c = V_c / sum V.
+ *
+ * Network (FP32): features x = ((ln r0 - ln 0.12)/0.6, (ln L0 - ln 30)/0.8,
+ * (ln D - ln 3)/0.6, (ln|B| - ln 15)/1.5, Bx/|B|, By/|B|); h1 = relu(x W1 + b1),
+ * h2 = relu(h1 W2 + b2), z = h2 W3 + b3 (logits); widths 6 -> 128 -> 128 -> C,
+ * C = n_rho n_theta (2048 for 64 x 32).  Loss: mean over samples of the cross
+ * entropy -sum_c t_c log softmax(z)_c.  Optimiser: Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8, bias-corrected).
+ * Parameter vector (FP32, this order, row-major, "in x out"):
+ *     W1[6][128] b1[128] W2[128][128] b2[128] W3[128][C] b3[C]
+ * qrs_mlp_param_count(C) gives its length (281,600 for C = 2048).
+ *
+ * Conventions as in qrs.h: device pointers, caller-owned, enqueued on `stream`.
+ */
+#ifndef QRS_PROPOSAL_H
+#define QRS_PROPOSAL_H
+
+#include <stdint.h>
+
+#include "qrs.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Number of FP32 parameters of the network with C output cells. */
+int64_t qrs_mlp_param_count(int32_t n_cells);
+
+/* He-normal initialisation (weights N(0, 2/fan_in) from Philox4x32-10 of `seed`
+ * by Box-Muller, biases 0) of params [qrs_mlp_param_count(n_cells)]. */
+qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float* params, void* stream);
+
+/* Training targets from plain draws: for each geometry geom[i] = (r0, L0, D,
+ * Bx, By) (device FP64 [n][5]), the per-cell structure-function contributions
+ * of n_draws plain realisations (LOGPOLAR [dom.fmin, dom.fmax], R2, n_f terms,
+ * stream seed `seed`, cells n_rho x n_theta; the PSD kind of `psd`, its
+ * r0/L0 replaced by the geometry's), normalised to sum 1:
+ *   targets [n][n_rho n_theta] FP32.   workspace: n_draws n_f draw records. */
+qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, int32_t n_rho,
+                                int32_t n_theta, uint64_t seed, int64_t n_f, int32_t n_draws, const double* geom,
+                                int64_t n, float* targets, void* stream);
+
+/* Forward pass: logits [n][C] from geometries geom [n][5] (device FP64). */
+qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, const double* geom, int64_t n,
+                           float* logits, void* stream);
+
+/* Loss and gradient at params: grad [param_count] (overwritten), loss [1]
+ * (device FP32, the mean cross entropy).  targets [n][C] rows sum to 1. */
+qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params, const double* geom,
+                             const float* targets, int64_t n, float* grad, float* loss, void* stream);
+
+/* One Adam step (step >= 1: bias correction t = step) with learning rate lr:
+ * params, m, v [param_count] updated in place from grad. */
+qrs_status qrs_mlp_adam(qrs_handle* h, int32_t n_cells, float* params, float* m, float* v, const float* grad,
+                        float lr, int64_t step, void* stream);
+
+/* Sampling CDF from one row of logits (device [C]): p = (1 - eps) softmax(z) +
+ * eps / C, quantised to integer widths W_c >= 1 with sum 2^32 (floor of
+ * p_c (2^32 - C) plus one, the remainder to the largest cell); cdf[c] = sum of
+ * widths before c (device uint32 [C], cdf[0] = 0), the format of
+ * qrs_sampler.cell_cdf.  0 < eps <= 1. */
+qrs_status qrs_proposal_cdf(qrs_handle* h, int32_t n_cells, const float* logits, float eps, uint32_t* cdf,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QRS_PROPOSAL_H */

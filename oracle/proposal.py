@@ -1,0 +1,156 @@
+"""FP64 CPU reference of the learned frequency-sampling proposal (test
+infrastructure only; never imported by the product package).
+
+Written from the definitions stated in include/qrs_proposal.h:
+* features of a geometry (r0, L0, D, Bx, By);
+* the 6 -> 128 -> 128 -> C ReLU network, softmax cross entropy, its analytic
+  backward pass (pinned by central finite differences in the tests) and the
+  bias-corrected Adam step;
+* the training targets: per-cell contributions of plain log-polar R2 draws
+  (the oracle's own draw) to the differential-piston structure function of
+  the geometry (Sec. 4.4 with the Eq. 7 filter), normalised;
+* the integer sampling CDF built from a row of logits.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import analytic as an
+from . import draw as _draw
+from . import lib as _lib
+
+H = 128
+STREAM_INIT = 3
+
+
+def param_count(n_cells: int) -> int:
+    return 6 * H + H + H * H + H + H * n_cells + n_cells
+
+
+def unpack(P, n_cells):
+    P = np.asarray(P, np.float64)
+    o = 0
+    out = []
+    for shape in ((6, H), (H,), (H, H), (H,), (H, n_cells), (n_cells,)):
+        size = int(np.prod(shape))
+        out.append(P[o:o + size].reshape(shape))
+        o += size
+    return out
+
+
+def pack(parts):
+    return np.concatenate([np.asarray(p, np.float64).ravel() for p in parts])
+
+
+def features(geom):
+    g = np.asarray(geom, np.float64).reshape(-1, 5)
+    r0, L0, D, Bx, By = g.T
+    B = np.hypot(Bx, By)
+    return np.stack([(np.log(r0) - np.log(0.12)) / 0.6, (np.log(L0) - np.log(30.0)) / 0.8,
+                     (np.log(D) - np.log(3.0)) / 0.6, (np.log(B) - np.log(15.0)) / 1.5, Bx / B, By / B], -1)
+
+
+def init(n_cells, seed):
+    """He-normal weights from Philox normals (counter = parameter index, stream 3), zero biases."""
+    n = param_count(n_cells)
+    z = np.zeros(n, np.float64)
+    _lib().oracle_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_void_p]
+    _lib().oracle_normals(int(seed) & (2**64 - 1), STREAM_INIT, n, z.ctypes.data_as(C.c_void_p))
+    fan = np.zeros(n)
+    o = 0
+    for (size, fan_in) in ((6 * H, 6), (H, 0), (H * H, H), (H, 0), (H * n_cells, H), (n_cells, 0)):
+        fan[o:o + size] = fan_in
+        o += size
+    return np.where(fan > 0, z * np.sqrt(2.0 / np.maximum(fan, 1)), 0.0)
+
+
+def forward(P, geom, n_cells, keep=False):
+    W1, b1, W2, b2, W3, b3 = unpack(P, n_cells)
+    X = features(geom)
+    A1 = X @ W1 + b1
+    H1 = np.maximum(A1, 0.0)
+    A2 = H1 @ W2 + b2
+    H2 = np.maximum(A2, 0.0)
+    Z = H2 @ W3 + b3
+    if keep:
+        return Z, (X, A1, H1, A2, H2)
+    return Z
+
+
+def log_softmax(Z):
+    m = Z.max(axis=1, keepdims=True)
+    return Z - m - np.log(np.exp(Z - m).sum(axis=1, keepdims=True))
+
+
+def loss(P, geom, T, n_cells):
+    Z = forward(P, geom, n_cells)
+    return float(-np.mean(np.sum(np.asarray(T, np.float64) * log_softmax(Z), axis=1)))
+
+
+def loss_grad(P, geom, T, n_cells):
+    """Mean cross entropy and its gradient by the chain rule, layer by layer."""
+    W1, b1, W2, b2, W3, b3 = unpack(P, n_cells)
+    T = np.asarray(T, np.float64)
+    n = T.shape[0]
+    Z, (X, A1, H1, A2, H2) = forward(P, geom, n_cells, keep=True)
+    ls = log_softmax(Z)
+    L = float(-np.mean(np.sum(T * ls, axis=1)))
+    dZ = (np.exp(ls) - T) / n            # d L / d z (rows of T sum to 1)
+    dW3 = H2.T @ dZ
+    db3 = dZ.sum(axis=0)
+    dA2 = (dZ @ W3.T) * (A2 > 0)
+    dW2 = H1.T @ dA2
+    db2 = dA2.sum(axis=0)
+    dA1 = (dA2 @ W2.T) * (A1 > 0)
+    dW1 = X.T @ dA1
+    db1 = dA1.sum(axis=0)
+    return L, pack([dW1, db1, dW2, db2, dW3, db3])
+
+
+def adam(P, m, v, g, lr, step, b1=0.9, b2=0.999, eps=1e-8):
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** step)
+    vh = v / (1 - b2 ** step)
+    return P - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def plain_draws(dom, n_rho, n_theta, seed, n_f, n_draws):
+    """The plain log-polar R2 draws the targets are built from (the oracle's own draw)."""
+    p = dict(psd="von_karman", r0=1.0, L0=1.0, domain="logpolar", fmin=dom[0], fmax=dom[1], sampler="r2",
+             seed=seed, s0=None, coef="gauss", n_rho=n_rho, n_theta=n_theta, cdf=None)
+    return _draw(p, n_f=n_f, n_real=n_draws)
+
+
+def targets(psd_kind, dom, n_rho, n_theta, seed, n_f, n_draws, geom, raw=False):
+    """t[i][c] = V_c / sum V, V_c = sum over draws and terms k in cell c of
+    w_k A(|f_k|)^2 2 (1 - cos 2 pi f_k . B), w_k = W(f_k; r0_i, L0_i) J_k / N_f."""
+    d = plain_draws(dom, n_rho, n_theta, seed, n_f, n_draws)
+    fx = d["f"][..., 0].astype(np.float64).ravel()
+    fy = d["f"][..., 1].astype(np.float64).ravel()
+    J = d["J"].ravel()
+    cell = d["cell"].ravel()
+    nc = n_rho * n_theta
+    g = np.asarray(geom, np.float64).reshape(-1, 5)
+    out = np.zeros((g.shape[0], nc))
+    fr = np.hypot(fx, fy)
+    for i, (r0, L0, D, Bx, By) in enumerate(g):
+        w = an.psd(fr, r0, L0, psd_kind) * J / n_f
+        A = an.airy(fr, D)
+        c = w * A ** 2 * 2.0 * (1.0 - np.cos(2.0 * np.pi * (fx * Bx + fy * By)))
+        out[i] = np.bincount(cell, weights=c, minlength=nc) / n_draws
+    return out if raw else out / out.sum(axis=1, keepdims=True)
+
+
+def cdf(logits, eps):
+    """Integer widths W_c = floor(p_c (2^32 - C)) + 1, remainder to the largest cell."""
+    z = np.asarray(logits, np.float64).ravel()
+    C_ = z.size
+    q = np.exp(z - z.max())
+    q /= q.sum()
+    p = (1 - eps) * q + eps / C_
+    w = np.floor(p * float(2**32 - C_)).astype(np.int64) + 1
+    w[np.argmax(w)] += 2**32 - int(w.sum())
+    return np.concatenate([[0], np.cumsum(w)[:-1]]).astype(np.uint64).astype(np.uint32), w

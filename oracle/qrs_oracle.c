@@ -478,3 +478,19 @@ int oracle_structure_fn(const float* delta, int64_t n_real, int64_t n_series, in
         }
     return 0;
 }
+
+/* ------------------------------------------------ normals for MLP init ---
+ * out[i] = N(0,1) by Box-Muller from the Philox words of counter
+ * (i_lo, i_hi, stream, 0) and key seed: U1 = (hi24(w0) + 1) 2^-24,
+ * U2 = hi24(w1) 2^-24, out = sqrt(-2 ln U1) cos(2 pi U2). */
+int oracle_normals(uint64_t seed, uint32_t stream, int64_t n, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t w[4];
+        or_words(seed, (uint64_t)i, stream, w);
+        double U1 = (double)((w[0] >> 8) + 1u) * 0x1p-24;
+        double U2 = (double)(w[1] >> 8) * 0x1p-24;
+        out[i] = sqrt(-2.0 * log(U1)) * cos(2.0 * OR_PI * U2);
+    }
+    return 0;
+}
