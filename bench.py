@@ -265,6 +265,83 @@ def measure_batched(qrs, h, torch, dev):
             "gpu_launches_first_call": h.launch_count() - launches0 - 3}
 
 
+def hankel_piston_sf(B, r0, L0, D, fmin, fmax):
+    """Expected differential-piston SF of equal unobscured apertures over the
+    annulus: 4 pi int f W(f) A(f)^2 (1 - J0(2 pi f B)) df, von Karman W,
+    8-point Gauss-Legendre on geometric panels no wider than 1/(4B)."""
+    from scipy import special as sp
+    e = np.geomspace(fmin, fmax, 400)
+    e = np.concatenate([np.linspace(a, c, max(1, int(np.ceil((c - a) * 4 * B))) + 1)[:-1] for a, c in zip(e[:-1], e[1:])]
+                       + [[fmax]])
+    x, w = np.polynomial.legendre.leggauss(8)
+    a, c = e[:-1, None], e[1:, None]
+    f = (0.5 * (c - a) * x + 0.5 * (c + a)).ravel()
+    ww = (0.5 * (c - a) * w).ravel()
+    W = 0.0228955871 * r0 ** (-5 / 3) * (f * f + L0 ** -2) ** (-11 / 6)
+    u = np.pi * D * f
+    A = 2 * sp.j1(u) / u
+    return float(np.sum(ww * 4 * np.pi * f * W * A * A * (1 - sp.j0(2 * np.pi * f * B))))
+
+
+def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8):
+    """Learned proposal (6 -> 128 -> 128 -> 64 x 32 logits): targets from the
+    plain method's own draws, training on the GPU, then the matched
+    structure-function error (RMS over held-out geometries and draws of the
+    per-draw SF relative to the Hankel integral) of learned importance draws
+    at N_f = 256..1024 against plain draws at N_f = 256..4096."""
+    def geom(n, seed):
+        rng = np.random.default_rng(seed)
+        B = np.exp(rng.uniform(np.log(1), np.log(200), n))
+        th = rng.uniform(0, 2 * np.pi, n)
+        return np.stack([np.exp(rng.uniform(np.log(0.05), np.log(0.3), n)),
+                         np.exp(rng.uniform(np.log(10), np.log(100), n)), rng.uniform(1, 8, n),
+                         B * np.cos(th), B * np.sin(th)], -1)
+
+    dom = dict(domain="logpolar", fmin=1e-3, fmax=10.0)
+    C = 64 * 32
+    gtr = torch.from_numpy(geom(n_train, 1)).to(dev)
+    gte_np = geom(n_test, 2)
+    t0 = time.perf_counter()
+    T = qrs.qrs_proposal_targets(h, qrs.params(**dom), 64, 32, 77, 4096, 256, gtr, kind="rms")
+    torch.cuda.synchronize()
+    t_targets = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P, hist = qrs.train_proposal(h, C, gtr, T, steps=3000, lr=2e-3, seed=3, log_every=1000)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    logits = qrs.qrs_mlp_forward(h, C, P, torch.from_numpy(gte_np).to(dev))
+    err = {}
+    for i, (r0, L0, D, Bx, By) in enumerate(gte_np):
+        Dref = hankel_piston_sf(np.hypot(Bx, By), r0, L0, D, 1e-3, 10.0)
+        p = qrs.params(r0=r0, L0=L0, seed=1000 + i, **dom)
+        cdf = qrs.qrs_proposal_cdf(h, 64, 32, logits[i].contiguous(), 0.05)
+        pi = dict(p, sampler="importance", n_rho=64, n_theta=32, cdf=cdf)
+        for name, pp, nfs in (("plain", p, (256, 512, 1024, 2048, 4096)), ("learned", pi, (256, 512, 1024))):
+            for nf in nfs:
+                d = qrs.qrs_draw(h, pp, nf, draws, outputs=("f_xy", "amp"))
+                f, F = d["f_xy"].double(), d["amp"].double()
+                fr = torch.sqrt(f[..., 0] ** 2 + f[..., 1] ** 2)
+                x = np.pi * D * fr
+                A = torch.where(x > 1e-6, 2 * torch.special.bessel_j1(x) / x, torch.ones_like(x))
+                ph = 2 * np.pi * (f[..., 0] * Bx + f[..., 1] * By)
+                e = ((F ** 2 * A ** 2 * 2 * (1 - torch.cos(ph))).sum(-1).cpu().numpy() - Dref) / Dref
+                err.setdefault("%s_%d" % (name, nf), []).append(float(np.mean(e ** 2)))
+    rms = {k: float(np.sqrt(np.mean(v))) for k, v in err.items()}
+    plain_n = np.array([256, 512, 1024, 2048, 4096], float)
+    plain_e = np.array([rms["plain_%d" % n] for n in plain_n.astype(int)])
+    # plain terms needed for the learned error (log-log interpolation of the plain curve)
+    equiv = {}
+    for nf in (256, 512, 1024):
+        e = rms["learned_%d" % nf]
+        equiv[nf] = float(np.exp(np.interp(-np.log(e), -np.log(plain_e), np.log(plain_n))))
+    return {"workload": "2000 training geometries (r0 0.05-0.3 m, L0 10-100 m, D 1-8 m, |B| 1-200 m), "
+                        "%d held out, %d draws each, cells 64x32 over [1e-3, 10] c/m" % (n_test, draws),
+            "targets_s": t_targets, "train_s": t_train, "train_steps": 3000, "loss_first_last": [hist[0][1], hist[-1][1]],
+            "matched_sf_error": rms,
+            "plain_terms_for_equal_error": {str(k): v for k, v in equiv.items()},
+            "term_reduction": {str(k): v / k for k, v in equiv.items()}}
+
+
 def run_ours(a):
     import torch
     rank, world, local = _dist()
@@ -370,6 +447,7 @@ def run_ours(a):
         peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
         line["other_forms"] = {m: measure_gemm(qrs, h, torch, dev, m, peaks) for m in ("gemm_3xtf32", "gemm_bf16x3")}
         line["other_forms"]["batched_pistons"] = measure_batched(qrs, h, torch, dev)
+        line["other_forms"]["learned_proposal"] = measure_learned(qrs, h, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np)
     if rank == 0:

@@ -76,10 +76,16 @@ typedef enum {
  *              n_rho x n_theta grid on the unit square (N_f = n_rho n_theta).
  *   UNIFORM    independent uniform points (Sec. 2.3 "fully random").
  *   IMPORTANCE cells of an n_rho (log-radial) x n_theta (angular) grid over
- *              [fmin, fmax] chosen by inverse CDF of the R2 x-coordinate's top
- *              32 bits against `cell_cdf`, placed area-uniformly inside the
- *              cell by the rest of the R2 point; J = area_c / p_c, which keeps
- *              the sum unbiased (learned proposal).  Domain must be LOGPOLAR. */
+ *              [fmin, fmax] by two-level inversion of the R2 point: the radial
+ *              band from the marginal CDF with the x coordinate's top 32 bits,
+ *              the angular cell from that band's conditional CDF with the y
+ *              coordinate's top 32 bits (so the point keeps its 2-D
+ *              stratification); the remainders (t_x, t_y) place it by the
+ *              cell's log-polar map, rho = fmin (fmax/fmin)^((i_rho + t_x)/n_rho),
+ *              theta = 2 pi (i_theta + t_y)/n_theta; J = 2 pi ln(fmax/fmin)
+ *              rho^2 / (n_rho n_theta p_c), p_c = p_band p_cell|band, which
+ *              keeps the sum unbiased (learned proposal; uniform CDFs give the
+ *              plain log-polar weights).  Domain must be LOGPOLAR. */
 #define QRS_SAMPLER_R2 0
 #define QRS_SAMPLER_JITTER 1
 #define QRS_SAMPLER_UNIFORM 2
@@ -112,9 +118,11 @@ typedef struct qrs_domain {
 typedef struct qrs_sampler {
     uint64_t seed;             /* Philox key (low word, high word) */
     uint64_t s0[2];            /* fixed R2 seed in 0.64 fixed point, if use_fixed_s0 */
-    const uint32_t* cell_cdf;  /* device [n_rho*n_theta]: cell start points, cdf[0] = 0,
-                                  strictly increasing (every cell width >= 1), implicit
-                                  end 2^32.  IMPORTANCE only, else NULL. */
+    const uint32_t* cell_cdf;  /* device uint32 [n_rho + n_rho*n_theta]: the marginal CDF
+                                  over radial bands (start points, [0] = 0, strictly
+                                  increasing, implicit end 2^32), then for each band
+                                  the conditional CDF over its angular cells (same
+                                  form).  IMPORTANCE only, else NULL. */
     int32_t kind;              /* QRS_SAMPLER_* */
     int32_t coef_kind;         /* QRS_COEF_* */
     int32_t use_fixed_s0;      /* 0: s0 = Philox(key=seed, ctr=(0,0,1,0)); 1: s0 above */

@@ -7,8 +7,9 @@
  * geometry g = (r0, L0, D, Bx, By) -- Fried parameter, outer scale, aperture
  * diameter, baseline vector -- to a density over the n_rho x n_theta
  * log-polar cells of [fmin, fmax]; mixed with the uniform cell density and
- * quantised to an integer CDF it drives the IMPORTANCE sampler of qrs.h,
- * whose weights w = W area_c / (N_f p_c) keep Eq. 3 unbiased.  It is trained
+ * quantised to a two-level integer CDF it drives the IMPORTANCE sampler of
+ * qrs.h, whose weights w = W J / N_f with J = 2 pi ln(fmax/fmin) rho^2 /
+ * (C p_c) keep Eq. 3 unbiased.  It is trained
  * on what the plain method itself produces: per-cell contributions of plain
  * log-polar R2 draws to the differential-piston structure function of the
  * geometry (Sec. 4.4 with the Eq. 7 filter),
@@ -47,13 +48,21 @@ qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float* pa
 
 /* Training targets from plain draws: for each geometry geom[i] = (r0, L0, D,
  * Bx, By) (device FP64 [n][5]), the per-cell structure-function contributions
- * of n_draws plain realisations (LOGPOLAR [dom.fmin, dom.fmax], R2, n_f terms,
- * stream seed `seed`, cells n_rho x n_theta; the PSD kind of `psd`, its
- * r0/L0 replaced by the geometry's), normalised to sum 1:
+ * v_k = w_k A(|f_k|)^2 2 (1 - cos 2 pi f_k . B) of n_draws plain realisations
+ * (LOGPOLAR [dom.fmin, dom.fmax], R2, n_f terms, stream seed `seed`, cells
+ * n_rho x n_theta; the PSD kind of `psd`, its r0/L0 replaced by the
+ * geometry's), reduced per cell and normalised to sum 1:
+ *   QRS_TARGET_MEAN  t_c ~ sum_{k in c} v_k         (the cell's share of D(B))
+ *   QRS_TARGET_RMS   t_c ~ sqrt(sum_{k in c} v_k^2) (the variance-optimal cell
+ *                    probability of the importance estimator when v varies
+ *                    inside cells: minimises sum_c (1/p_c) int_c g^2 rho^2)
  *   targets [n][n_rho n_theta] FP32.   workspace: n_draws n_f draw records. */
+#define QRS_TARGET_MEAN 0
+#define QRS_TARGET_RMS 1
+
 qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, int32_t n_rho,
-                                int32_t n_theta, uint64_t seed, int64_t n_f, int32_t n_draws, const double* geom,
-                                int64_t n, float* targets, void* stream);
+                                int32_t n_theta, uint64_t seed, int64_t n_f, int32_t n_draws, int32_t kind,
+                                const double* geom, int64_t n, float* targets, void* stream);
 
 /* Forward pass: logits [n][C] from geometries geom [n][5] (device FP64). */
 qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, const double* geom, int64_t n,
@@ -69,13 +78,15 @@ qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params
 qrs_status qrs_mlp_adam(qrs_handle* h, int32_t n_cells, float* params, float* m, float* v, const float* grad,
                         float lr, int64_t step, void* stream);
 
-/* Sampling CDF from one row of logits (device [C]): p = (1 - eps) softmax(z) +
- * eps / C, quantised to integer widths W_c >= 1 with sum 2^32 (floor of
- * p_c (2^32 - C) plus one, the remainder to the largest cell); cdf[c] = sum of
- * widths before c (device uint32 [C], cdf[0] = 0), the format of
- * qrs_sampler.cell_cdf.  0 < eps <= 1. */
-qrs_status qrs_proposal_cdf(qrs_handle* h, int32_t n_cells, const float* logits, float eps, uint32_t* cdf,
-                            void* stream);
+/* Two-level sampling CDF from one row of logits (device [n_rho n_theta]):
+ * p = (1 - eps) softmax(z) + eps / C over the cells; the marginal over radial
+ * bands and, per band, the conditional over its angular cells, each quantised
+ * to integer widths >= 1 summing to 2^32 (floor of p (2^32 - n) plus one, the
+ * remainder to the largest entry); cdf [n_rho + n_rho n_theta] (device uint32)
+ * holds their start points in the format of qrs_sampler.cell_cdf.
+ * 0 < eps <= 1 (the mixture with the uniform density bounds every weight). */
+qrs_status qrs_proposal_cdf(qrs_handle* h, int32_t n_rho, int32_t n_theta, const float* logits, float eps,
+                            uint32_t* cdf, void* stream);
 
 #ifdef __cplusplus
 }

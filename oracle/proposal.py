@@ -124,9 +124,10 @@ def plain_draws(dom, n_rho, n_theta, seed, n_f, n_draws):
     return _draw(p, n_f=n_f, n_real=n_draws)
 
 
-def targets(psd_kind, dom, n_rho, n_theta, seed, n_f, n_draws, geom, raw=False):
-    """t[i][c] = V_c / sum V, V_c = sum over draws and terms k in cell c of
-    w_k A(|f_k|)^2 2 (1 - cos 2 pi f_k . B), w_k = W(f_k; r0_i, L0_i) J_k / N_f."""
+def targets(psd_kind, dom, n_rho, n_theta, seed, n_f, n_draws, geom, raw=False, kind="mean"):
+    """v_k = w_k A(|f_k|)^2 2 (1 - cos 2 pi f_k . B), w_k = W(f_k; r0_i, L0_i) J_k / N_f
+    over the plain draws; kind "mean": t_c ~ sum_{k in c} v_k (raw: / n_draws);
+    kind "rms": t_c ~ sqrt(sum_{k in c} v_k^2); rows normalised to 1."""
     d = plain_draws(dom, n_rho, n_theta, seed, n_f, n_draws)
     fx = d["f"][..., 0].astype(np.float64).ravel()
     fy = d["f"][..., 1].astype(np.float64).ravel()
@@ -140,17 +141,40 @@ def targets(psd_kind, dom, n_rho, n_theta, seed, n_f, n_draws, geom, raw=False):
         w = an.psd(fr, r0, L0, psd_kind) * J / n_f
         A = an.airy(fr, D)
         c = w * A ** 2 * 2.0 * (1.0 - np.cos(2.0 * np.pi * (fx * Bx + fy * By)))
-        out[i] = np.bincount(cell, weights=c, minlength=nc) / n_draws
+        if kind == "rms":
+            out[i] = np.sqrt(np.bincount(cell, weights=c * c, minlength=nc))
+        else:
+            out[i] = np.bincount(cell, weights=c, minlength=nc) / n_draws
     return out if raw else out / out.sum(axis=1, keepdims=True)
 
 
-def cdf(logits, eps):
-    """Integer widths W_c = floor(p_c (2^32 - C)) + 1, remainder to the largest cell."""
+def quantise(p, scale_count):
+    """Integer widths of a probability vector: floor(p (2^32 - n)) + 1, the
+    remainder to the largest (first on ties); returns (starts, widths)."""
+    p = np.asarray(p, np.float64)
+    n = p.size
+    w = np.floor(p * float(2**32 - n)).astype(np.int64) + 1
+    w[np.argmax(w)] += 2**32 - int(w.sum())
+    return np.concatenate([[0], np.cumsum(w)[:-1]]).astype(np.int64), w
+
+
+def cdf(logits, eps, n_rho, n_theta):
+    """Two-level sampling CDF: p = (1 - eps) softmax(z) + eps / C over the
+    n_rho x n_theta cells; the marginal over radial bands, then each band's
+    conditional over its angular cells, each quantised to widths summing to
+    2^32.  Returns (uint32 [n_rho + n_rho n_theta], cell probabilities as
+    quantised (p_band p_cell|band))."""
     z = np.asarray(logits, np.float64).ravel()
-    C_ = z.size
+    C_ = n_rho * n_theta
     q = np.exp(z - z.max())
     q /= q.sum()
-    p = (1 - eps) * q + eps / C_
-    w = np.floor(p * float(2**32 - C_)).astype(np.int64) + 1
-    w[np.argmax(w)] += 2**32 - int(w.sum())
-    return np.concatenate([[0], np.cumsum(w)[:-1]]).astype(np.uint64).astype(np.uint32), w
+    p = ((1 - eps) * q + eps / C_).reshape(n_rho, n_theta)
+    Pr = p.sum(axis=1)
+    rs, rw = quantise(Pr, n_rho)
+    out = [rs]
+    pq = np.zeros((n_rho, n_theta))
+    for i in range(n_rho):
+        ts, tw = quantise(p[i] / Pr[i], n_theta)
+        out.append(ts)
+        pq[i] = (rw[i] / 2.0**32) * (tw / 2.0**32)
+    return np.concatenate(out).astype(np.uint32), pq

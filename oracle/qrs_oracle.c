@@ -221,7 +221,7 @@ static void or_draw_term(const or_params* p, const uint64_t s0[2], int64_t n_f, 
     uint32_t w[4];
     or_words(p->seed, n, OR_STREAM_TERM, w);
     uint64_t S[2] = {0, 0};
-    double sx, sy, J = 0.0;
+    double sx, sy, J = 0.0, p_cell = 1.0;
     int32_t c = -1;
     double fd[2];
     if (p->smp_kind == OR_SMP_R2) {
@@ -238,30 +238,33 @@ static void or_draw_term(const or_params* p, const uint64_t s0[2], int64_t n_f, 
         int64_t i = k % p->n_rho, j = k / p->n_rho;
         sx = ((double)i + (double)w[0] * 0x1p-32) / (double)p->n_rho;
         sy = ((double)j + (double)w[1] * 0x1p-32) / (double)p->n_theta;
-    } else { /* IMPORTANCE: integer inverse CDF over log-polar cells */
+    } else { /* IMPORTANCE: two-level integer inversion over log-polar cells */
         oracle_r2_point(s0, n, S);
-        uint32_t u = (uint32_t)(S[0] >> 32);
-        int nc = p->n_rho * p->n_theta;
-        int lo = 0;
-        for (int q = 1; q < nc; ++q)  /* plain linear scan: largest q with cdf[q] <= u */
-            if (p->cdf[q] <= u) lo = q;
-        c = lo;
-        uint64_t start = (uint64_t)p->cdf[c];
-        uint64_t end = (c + 1 < nc) ? (uint64_t)p->cdf[c + 1] : ((uint64_t)1 << 32);
-        uint64_t width = end - start;
-        double t = (double)(S[0] - (start << 32)) / ((double)width * 0x1p32);
-        double sy_in = or_fix_to_unit(S[1]);
-        int ir = c / p->n_theta, it = c % p->n_theta;
+        /* radial band from the marginal CDF with the x coordinate,
+         * angular cell from that band's conditional CDF with the y coordinate */
+        const uint32_t* cr = p->cdf;
+        const uint32_t* ct;
+        uint32_t ux = (uint32_t)(S[0] >> 32), uy = (uint32_t)(S[1] >> 32);
+        int ir = 0, it = 0;
+        for (int q = 1; q < p->n_rho; ++q)  /* plain linear scans */
+            if (cr[q] <= ux) ir = q;
+        ct = p->cdf + p->n_rho + (size_t)ir * p->n_theta;
+        for (int q = 1; q < p->n_theta; ++q)
+            if (ct[q] <= uy) it = q;
+        uint64_t r_start = (uint64_t)cr[ir];
+        uint64_t r_end = (ir + 1 < p->n_rho) ? (uint64_t)cr[ir + 1] : ((uint64_t)1 << 32);
+        uint64_t t_start = (uint64_t)ct[it];
+        uint64_t t_end = (it + 1 < p->n_theta) ? (uint64_t)ct[it + 1] : ((uint64_t)1 << 32);
+        double tx = (double)(S[0] - (r_start << 32)) / ((double)(r_end - r_start) * 0x1p32);
+        double ty = (double)(S[1] - (t_start << 32)) / ((double)(t_end - t_start) * 0x1p32);
+        c = ir * p->n_theta + it;
+        /* inside the cell, the log-polar map of the cell's own square */
         double L = log(p->fmax / p->fmin);
-        double r_lo = p->fmin * exp(L * (double)ir / (double)p->n_rho);
-        double r_hi = p->fmin * exp(L * (double)(ir + 1) / (double)p->n_rho);
-        double rho = sqrt(r_lo * r_lo + t * (r_hi * r_hi - r_lo * r_lo));
-        double th = 2.0 * OR_PI * ((double)it + sy_in) / (double)p->n_theta;
+        double rho = p->fmin * exp(L * ((double)ir + tx) / (double)p->n_rho);
+        double th = 2.0 * OR_PI * ((double)it + ty) / (double)p->n_theta;
         fd[0] = rho * cos(th);
         fd[1] = rho * sin(th);
-        double area = (2.0 * OR_PI / (double)p->n_theta) * 0.5 * (r_hi * r_hi - r_lo * r_lo);
-        double pc = (double)width * 0x1p-32;
-        J = area / pc;
+        p_cell = ((double)(r_end - r_start) * 0x1p-32) * ((double)(t_end - t_start) * 0x1p-32);
         sx = sy = 0.0;
     }
     if (p->smp_kind != OR_SMP_IMPORTANCE) {
@@ -277,6 +280,8 @@ static void or_draw_term(const or_params* p, const uint64_t s0[2], int64_t n_f, 
     double fx = (double)f32[0], fy = (double)f32[1];
     if (p->smp_kind != OR_SMP_IMPORTANCE)
         J = oracle_domain_jacobian(p->dom_kind, p->fmin, p->fmax, fx, fy);
+    else  /* the log-polar Jacobian 2 pi L rho^2, divided by n_rho n_theta p_c */
+        J = 2.0 * OR_PI * log(p->fmax / p->fmin) * (fx * fx + fy * fy) / ((double)p->n_rho * (double)p->n_theta * p_cell);
     double W = oracle_psd(p->psd_kind, p->r0, p->L0, fx * fx + fy * fy);
     *F = sqrt(W * J / (double)n_f);
     *Jo = J;

@@ -288,3 +288,107 @@ def qrs_synthesize_points_noalloc(p, n_f, n_real, xy, out=None, real_offset=0, s
     if st != 0:
         raise QrsError(st, "qrs_synthesize_points_noalloc failed")
     return out
+
+
+# ------------------------------------------------------- learned proposal
+def _prop_fn(name, argtypes, restype=C.c_int):
+    f = getattr(load(), name)
+    if f.argtypes is None:
+        f.argtypes = argtypes
+        f.restype = restype
+    return f
+
+
+def qrs_mlp_param_count(n_cells) -> int:
+    return int(_prop_fn("qrs_mlp_param_count", [C.c_int32], C.c_int64)(int(n_cells)))
+
+
+def qrs_mlp_init(h: Handle, n_cells, seed, params=None, stream=None):
+    n = qrs_mlp_param_count(n_cells)
+    if params is None:
+        params = torch.empty(n, dtype=torch.float32, device=torch.device("cuda", h.device))
+    _check_dev(params, torch.float32, "params")
+    f = _prop_fn("qrs_mlp_init", [C.c_void_p, C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p])
+    h._check(f(h.h, int(n_cells), int(seed) & (2**64 - 1), params.data_ptr(), _stream(stream)))
+    return params
+
+
+TARGET = {"mean": 0, "rms": 1}
+
+
+def qrs_proposal_targets(h: Handle, p, n_rho, n_theta, seed, n_f, n_draws, geom, kind="rms", out=None, stream=None):
+    """Per-cell training targets [n][n_rho n_theta] from plain draws (geom: device float64 [n][5])."""
+    _check_dev(geom, torch.float64, "geom")
+    n = geom.shape[0]
+    if out is None:
+        out = torch.empty(n, n_rho * n_theta, dtype=torch.float32, device=geom.device)
+    psd, dom, _ = _structs(p)
+    f = _prop_fn("qrs_proposal_targets", [C.c_void_p, C.POINTER(QrsPsd), C.POINTER(QrsDomain), C.c_int32, C.c_int32,
+                                          C.c_uint64, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                          C.c_void_p, C.c_void_p])
+    h._check(f(h.h, C.byref(psd), C.byref(dom), int(n_rho), int(n_theta), int(seed) & (2**64 - 1), int(n_f),
+               int(n_draws), TARGET[kind], geom.data_ptr(), int(n), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def qrs_mlp_forward(h: Handle, n_cells, params, geom, out=None, stream=None):
+    _check_dev(params, torch.float32, "params")
+    _check_dev(geom, torch.float64, "geom")
+    n = geom.shape[0]
+    if out is None:
+        out = torch.empty(n, n_cells, dtype=torch.float32, device=geom.device)
+    f = _prop_fn("qrs_mlp_forward", [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p])
+    h._check(f(h.h, int(n_cells), params.data_ptr(), geom.data_ptr(), int(n), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def qrs_mlp_loss_grad(h: Handle, n_cells, params, geom, targets, grad=None, loss=None, stream=None):
+    _check_dev(params, torch.float32, "params")
+    _check_dev(geom, torch.float64, "geom")
+    _check_dev(targets, torch.float32, "targets")
+    if grad is None:
+        grad = torch.empty_like(params)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    f = _prop_fn("qrs_mlp_loss_grad", [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                       C.c_void_p, C.c_void_p])
+    h._check(f(h.h, int(n_cells), params.data_ptr(), geom.data_ptr(), targets.data_ptr(), int(geom.shape[0]),
+               grad.data_ptr(), loss.data_ptr(), _stream(stream)))
+    return grad, loss
+
+
+def qrs_mlp_adam(h: Handle, n_cells, params, m, v, grad, lr, step, stream=None):
+    f = _prop_fn("qrs_mlp_adam", [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
+                                  C.c_int64, C.c_void_p])
+    h._check(f(h.h, int(n_cells), params.data_ptr(), m.data_ptr(), v.data_ptr(), grad.data_ptr(), float(lr), int(step),
+               _stream(stream)))
+
+
+def qrs_proposal_cdf(h: Handle, n_rho, n_theta, logits_row, eps=0.1, out=None, stream=None):
+    """Two-level sampling CDF (device int32 view of uint32 [n_rho + n_rho n_theta])
+    from one row of logits [n_rho n_theta]."""
+    _check_dev(logits_row, torch.float32, "logits_row")
+    if out is None:
+        out = torch.empty(n_rho * (1 + n_theta), dtype=torch.int32, device=logits_row.device)
+    f = _prop_fn("qrs_proposal_cdf", [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_float, C.c_void_p, C.c_void_p])
+    h._check(f(h.h, int(n_rho), int(n_theta), logits_row.data_ptr(), float(eps), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def train_proposal(h: Handle, n_cells, geom, targets, steps=2000, lr=2e-3, seed=0, params=None, stream=None,
+                   log_every=0):
+    """Adam on the mean cross entropy, full batch; every step is two libqrs calls
+    (loss and gradient, Adam update).  Returns (params, list of (step, loss))."""
+    if params is None:
+        params = qrs_mlp_init(h, n_cells, seed, stream=stream)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    hist = []
+    for step in range(1, steps + 1):
+        qrs_mlp_loss_grad(h, n_cells, params, geom, targets, grad=grad, loss=loss, stream=stream)
+        qrs_mlp_adam(h, n_cells, params, m, v, grad, lr, step, stream=stream)
+        if log_every and (step % log_every == 0 or step == 1):
+            hist.append((step, float(loss.item())))
+    return params, hist

@@ -1,0 +1,546 @@
+// k_proposal.cu -- the learned frequency-sampling proposal (include/qrs_proposal.h):
+// training targets from plain draws, the 6 -> 128 -> 128 -> C network's
+// forward / backward passes, Adam, and the integer sampling CDF.  All FP32
+// except where stated; every sum has a fixed order (deterministic) except the
+// per-cell target histograms (shared-memory atomics).
+#include <cmath>
+#include <cstring>
+
+#include "../../include/qrs_proposal.h"
+#include "qrs_internal.h"
+
+namespace qrs {
+
+constexpr int kHid = 128;
+constexpr uint32_t kStreamInit = 3u;  // Philox stream of the initial weights
+
+__host__ __device__ inline int64_t mlp_params(int C) { return 6 * kHid + kHid + kHid * kHid + kHid + (int64_t)kHid * C + C; }
+
+struct MlpView {
+    float *W1, *b1, *W2, *b2, *W3, *b3;
+};
+
+__host__ __device__ inline MlpView mlp_view(float* P, int C)
+{
+    MlpView v;
+    v.W1 = P;
+    v.b1 = v.W1 + 6 * kHid;
+    v.W2 = v.b1 + kHid;
+    v.b2 = v.W2 + kHid * kHid;
+    v.W3 = v.b2 + kHid;
+    v.b3 = v.W3 + (int64_t)kHid * C;
+    return v;
+}
+
+// ------------------------------------------------------------------ init
+__global__ void k_mlp_init(int C, uint64_t seed, float* __restrict__ P)
+{
+    const int64_t n = mlp_params(C);
+    const int64_t e1 = 6 * kHid, e2 = e1 + kHid, e3 = e2 + kHid * kHid, e4 = e3 + kHid, e5 = e4 + (int64_t)kHid * C;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int fan = 0;
+        if (i < e1) fan = 6;
+        else if (i >= e2 && i < e3) fan = kHid;
+        else if (i >= e4 && i < e5) fan = kHid;
+        float v = 0.0f;
+        if (fan) {
+            const Words w = philox4x32_10((uint32_t)i, (uint32_t)((uint64_t)i >> 32), kStreamInit, 0u, (uint32_t)seed,
+                                          (uint32_t)(seed >> 32));
+            const float U1 = (float)((w.w0 >> 8) + 1u) * 0x1p-24f;
+            const float U2 = (float)(w.w1 >> 8) * 0x1p-24f;
+            v = sqrtf(-2.0f * logf(U1)) * cospif(2.0f * U2) * sqrtf(2.0f / (float)fan);
+        }
+        P[i] = v;
+    }
+}
+
+// -------------------------------------------------------------- features
+__global__ void k_features(const double* __restrict__ geom, int64_t n, float* __restrict__ X)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double* g = geom + 5 * i;
+        const double B = hypot(g[3], g[4]);
+        float* x = X + 6 * i;
+        x[0] = (float)((log(g[0]) - log(0.12)) / 0.6);
+        x[1] = (float)((log(g[1]) - log(30.0)) / 0.8);
+        x[2] = (float)((log(g[2]) - log(3.0)) / 0.6);
+        x[3] = (float)((log(B) - log(15.0)) / 1.5);
+        x[4] = (float)(g[3] / B);
+        x[5] = (float)(g[4] / B);
+    }
+}
+
+// ------------------------------------------------------------------ SGEMM
+// C[M][N] = op(A) op(B) with op(A) [M][K] (A stored [M][K], or [K][M] if TA),
+// op(B) [K][N] (B stored [K][N], or [N][K] if TB); epilogue: + bias[n],
+// relu, multiply by (mask[m][n] > 0).  64 x 64 tiles, 16-deep K steps,
+// 256 threads with 4 x 4 outputs each; ragged edges bounds-checked.
+enum { kEpiNone = 0, kEpiBias = 1, kEpiRelu = 2, kEpiMask = 4 };
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda,
+                                               const float* __restrict__ B, int ldb, float* __restrict__ Cm, int ldc,
+                                               const float* __restrict__ bias, const float* __restrict__ mask, int ldm)
+{
+    __shared__ float As[16][64 + 4];
+    __shared__ float Bs[16][64 + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = threadIdx.x; e < 1024; e += 256) {
+            int mm, kk;
+            if (TA) { kk = e >> 6; mm = e & 63; } else { mm = e >> 4; kk = e & 15; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < K) ? (TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk]) : 0.0f;
+            int nn, kb;
+            if (TB) { nn = e >> 4; kb = e & 15; } else { kb = e >> 6; nn = e & 63; }
+            const int gn = n0 + nn, gkb = k0 + kb;
+            Bs[kb][nn] = (gn < N && gkb < K) ? (TB ? B[(int64_t)gn * ldb + gkb] : B[(int64_t)gkb * ldb + gn]) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty * 4 + i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx * 4 + j;
+            if (n >= N) continue;
+            float v = acc[i][j];
+            if (EPI & kEpiBias) v += bias[n];
+            if (EPI & kEpiRelu) v = fmaxf(v, 0.0f);
+            if (EPI & kEpiMask) v = mask[(int64_t)m * ldm + n] > 0.0f ? v : 0.0f;
+            Cm[(int64_t)m * ldc + n] = v;
+        }
+    }
+}
+
+template <bool TA, bool TB, int EPI>
+static cudaError_t sgemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                         const float* bias, const float* mask, int ldm, cudaStream_t s)
+{
+    dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+    k_sgemm<TA, TB, EPI><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, ldm);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------- softmax cross entropy
+__device__ __forceinline__ float block_reduce(float v, float* red, bool is_max)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max ? fmaxf(v, w) : v + w;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    v = lane < nw ? red[lane] : (is_max ? -INFINITY : 0.0f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max ? fmaxf(v, w) : v + w;
+    }
+    return v;
+}
+
+// One CTA per sample: dZ = (softmax(z) - t) / n, loss_row = sum_c t_c (lse - z_c).
+__global__ void __launch_bounds__(256) k_softmax_ce(const float* __restrict__ Z, const float* __restrict__ T, int C,
+                                                    int64_t n, float* __restrict__ dZ, float* __restrict__ loss_row)
+{
+    __shared__ float red[32];
+    const int64_t i = blockIdx.x;
+    const float* z = Z + i * C;
+    const float* t = T + i * C;
+    float mx = -INFINITY;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) mx = fmaxf(mx, z[c]);
+    mx = block_reduce(mx, red, true);
+    float se = 0.0f;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) se += expf(z[c] - mx);
+    se = block_reduce(se, red, false);
+    const float lse = mx + logf(se);
+    const float inv_n = 1.0f / (float)n;
+    float l = 0.0f;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        const float q = expf(z[c] - lse);
+        dZ[i * C + c] = (q - t[c]) * inv_n;
+        l += t[c] * (lse - z[c]);
+    }
+    l = block_reduce(l, red, false);
+    if (threadIdx.x == 0) loss_row[i] = l;
+}
+
+// Mean of loss_row in a fixed order (one CTA).
+__global__ void k_loss_mean(const float* __restrict__ loss_row, int64_t n, float* __restrict__ loss)
+{
+    __shared__ float red[32];
+    float s = 0.0f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += loss_row[i];
+    s = block_reduce(s, red, false);
+    if (threadIdx.x == 0) *loss = s / (float)n;
+}
+
+__global__ void k_fill(float* __restrict__ x, int64_t n, float v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
+// ------------------------------------------------------------------- Adam
+__global__ void k_adam(int64_t n, float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, float lr, float c1, float c2)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = 0.9f * m[i] + 0.1f * gi;
+        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        P[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+    }
+}
+
+// --------------------------------------------------------- training targets
+// Plain log-polar draws: records (fx, fy, J, cell bits) of n_draws x n_f terms.
+__global__ void k_prop_draws(DrawParams p, int n_draws, float4* __restrict__ rec)
+{
+    const int64_t total = (int64_t)n_draws * p.n_f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i % p.n_f;
+        const Term t = draw_term(p, (uint64_t)i, k);
+        rec[i] = make_float4(t.fx, t.fy, t.J, __int_as_float(t.cell));
+    }
+}
+
+// One CTA per geometry: shared histogram of w A^2 2 (1 - cos 2 pi f.B) over the cells.
+__global__ void __launch_bounds__(512) k_prop_targets(const float4* __restrict__ rec, int64_t n_rec, float inv_nf,
+                                                      const double* __restrict__ geom, int psd_kind, double c_vk, int C,
+                                                      int kind, float* __restrict__ out)
+{
+    extern __shared__ float hist[];
+    __shared__ float red[32];
+    __shared__ float s_pc, s_pa, s_D, s_Bx, s_By;
+    const int64_t i = blockIdx.x;
+    if (threadIdx.x == 0) {
+        const double* g = geom + 5 * i;
+        s_pc = (float)(c_vk * pow(g[0], -5.0 / 3.0));
+        s_pa = psd_kind == QRS_PSD_KOLMOGOROV ? 0.0f : (float)(1.0 / (g[1] * g[1]));
+        s_D = (float)g[2];
+        s_Bx = (float)g[3];
+        s_By = (float)g[4];
+    }
+    for (int c = threadIdx.x; c < C; c += blockDim.x) hist[c] = 0.0f;
+    __syncthreads();
+    const float pc = s_pc, pa = s_pa, D = s_D, Bx = s_Bx, By = s_By;
+    for (int64_t k = threadIdx.x; k < n_rec; k += blockDim.x) {
+        const float4 r = rec[k];
+        const float f2 = r.x * r.x + r.y * r.y;
+        const float w = psd_w(pc, pa, f2) * r.z * inv_nf;
+        const float A = airy_filter(sqrtf(f2), D, 0.0f);
+        float s, c;
+        sincos_turns(phase_df(r.x, r.y, Bx, By), s, c);
+        const float v = w * A * A * 2.0f * (1.0f - c);
+        atomicAdd(&hist[__float_as_int(r.w)], kind == QRS_TARGET_RMS ? v * v : v);
+    }
+    __syncthreads();
+    if (kind == QRS_TARGET_RMS)
+        for (int c = threadIdx.x; c < C; c += blockDim.x) hist[c] = sqrtf(hist[c]);
+    __syncthreads();
+    float tot = 0.0f;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) tot += hist[c];
+    tot = block_reduce(tot, red, false);
+    const float inv = tot > 0.0f ? 1.0f / tot : 0.0f;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) out[i * C + c] = hist[c] * inv;
+}
+
+// ------------------------------------------------------------ sampling CDF
+// Integer widths floor(p (2^32 - n)) + 1 of a probability vector x[0..n) (FP64,
+// stride `stride`), remainder to the largest (first on ties), exclusive scan
+// into out[0..n).  Serial: n is a band count or a band's cell count.
+__device__ void quantise_scan(const double* x, int n, int stride, double total, uint32_t* out)
+{
+    const double scale = 4294967296.0 - (double)n;
+    unsigned long long sum = 0, best = 0;
+    int arg = 0;
+    for (int j = 0; j < n; ++j) {
+        const unsigned long long w = (unsigned long long)floor(x[j * stride] / total * scale) + 1ull;
+        sum += w;
+        if (w > best) { best = w; arg = j; }
+    }
+    const unsigned long long rem = (1ull << 32) - sum;
+    unsigned long long run = 0;
+    for (int j = 0; j < n; ++j) {
+        out[j] = (uint32_t)run;
+        run += (unsigned long long)floor(x[j * stride] / total * scale) + 1ull + (j == arg ? rem : 0ull);
+    }
+}
+
+// One CTA: p = (1 - eps) softmax(z) + eps / C in FP64 (FP32 exponentials),
+// band sums, the marginal CDF (thread 0), the conditional CDFs (one thread
+// per band).  pbuf: C + n_rho doubles of workspace.
+__global__ void __launch_bounds__(1024) k_prop_cdf(const float* __restrict__ z, int n_rho, int n_theta, float eps,
+                                                   uint32_t* __restrict__ cdf, double* __restrict__ pbuf)
+{
+    __shared__ float redf[32];
+    __shared__ double redd[32];
+    const int C = n_rho * n_theta;
+    float mx = -INFINITY;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) mx = fmaxf(mx, z[c]);
+    mx = block_reduce(mx, redf, true);
+    double se = 0.0;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) se += (double)expf(z[c] - mx);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+    if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = se;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += redd[q];
+        redd[0] = t;
+    }
+    __syncthreads();
+    const double sum = redd[0];
+    for (int c = threadIdx.x; c < C; c += blockDim.x)
+        pbuf[c] = (1.0 - (double)eps) * ((double)expf(z[c] - mx) / sum) + (double)eps / (double)C;
+    __syncthreads();
+    double* band = pbuf + C;
+    for (int i = threadIdx.x; i < n_rho; i += blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < n_theta; ++j) s += pbuf[i * n_theta + j];
+        band[i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n_rho; ++i) t += band[i];
+        quantise_scan(band, n_rho, 1, t, cdf);
+    }
+    for (int i = threadIdx.x; i < n_rho; i += blockDim.x)
+        quantise_scan(pbuf + i * n_theta, n_theta, 1, band[i], cdf + n_rho + (int64_t)i * n_theta);
+}
+
+static double vk_c()
+{
+    const double pi = 3.14159265358979323846;
+    return std::tgamma(11.0 / 6.0) * std::tgamma(11.0 / 6.0) / (2.0 * std::pow(pi, 11.0 / 3.0)) *
+           std::pow(24.0 / 5.0 * std::tgamma(6.0 / 5.0), 5.0 / 6.0);
+}
+
+}  // namespace qrs
+
+using namespace qrs;
+
+extern "C" {
+
+int64_t qrs_mlp_param_count(int32_t n_cells) { return n_cells >= 1 ? mlp_params(n_cells) : 0; }
+
+static bool cells_ok(int32_t C) { return C >= 1 && C <= 16384; }
+
+qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float* params, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    if (!cells_ok(n_cells) || !params) return fail(h, QRS_ERR_ARG, "n_cells must be in [1, 16384] and params non-NULL");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) {
+        k_mlp_init<<<256, 256, 0, (cudaStream_t)stream>>>(n_cells, seed, params);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_init");
+    ++h->launches;
+    return QRS_OK;
+}
+
+qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, int32_t n_rho,
+                                int32_t n_theta, uint64_t seed, int64_t n_f, int32_t n_draws, int32_t kind,
+                                const double* geom, int64_t n, float* targets, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    if (kind != QRS_TARGET_MEAN && kind != QRS_TARGET_RMS) return fail(h, QRS_ERR_ARG, "unknown target kind %d", kind);
+    if (!dom || dom->kind != QRS_DOMAIN_LOGPOLAR) return fail(h, QRS_ERR_ARG, "targets need a LOGPOLAR domain");
+    if (n_draws < 1 || n < 0) return fail(h, QRS_ERR_ARG, "n_draws >= 1, n >= 0");
+    const int64_t C = (int64_t)n_rho * n_theta;
+    if (!cells_ok((int32_t)C) || n_rho < 1 || n_theta < 1) return fail(h, QRS_ERR_ARG, "n_rho x n_theta in [1, 16384]");
+    qrs_sampler smp;
+    memset(&smp, 0, sizeof(smp));
+    smp.seed = seed;
+    smp.kind = QRS_SAMPLER_R2;
+    smp.coef_kind = QRS_COEF_GAUSS;
+    smp.n_rho = n_rho;
+    smp.n_theta = n_theta;
+    DrawParams p;
+    qrs_status st = make_draw_params(h, psd, dom, &smp, n_f, 0, &p);
+    if (st != QRS_OK) return st;
+    if (n == 0) return QRS_OK;
+    if (!geom || !targets) return fail(h, QRS_ERR_ARG, "geom and targets must be non-NULL");
+    const int64_t n_rec = (int64_t)n_draws * n_f;
+    st = ensure_work(h, (size_t)n_rec * sizeof(float4) + 256);
+    if (st != QRS_OK) return st;
+    float4* rec = reinterpret_cast<float4*>(((uintptr_t)h->d_work + 255) & ~(uintptr_t)255);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) {
+        k_prop_draws<<<(unsigned)std::min<int64_t>((n_rec + 255) / 256, 8192), 256, 0, s>>>(p, n_draws, rec);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && C * sizeof(float) > 48 * 1024)
+        e = cudaFuncSetAttribute(k_prop_targets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(C * sizeof(float)));
+    if (e == cudaSuccess) {
+        k_prop_targets<<<(unsigned)n, 512, (size_t)C * sizeof(float), s>>>(rec, n_rec, p.inv_nf, geom, psd->kind, vk_c(),
+                                                                          (int)C, kind, targets);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_proposal_targets");
+    h->launches += 2;
+    return QRS_OK;
+}
+
+// Forward pass into workspace (X, H1, H2) and Z.
+static cudaError_t mlp_forward(int C, const float* P, const double* geom, int64_t n, float* X, float* H1, float* H2,
+                               float* Z, cudaStream_t s)
+{
+    MlpView w = mlp_view(const_cast<float*>(P), C);
+    const int N = (int)n;
+    k_features<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(geom, n, X);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = sgemm<false, false, kEpiBias | kEpiRelu>(N, kHid, 6, X, 6, w.W1, kHid, H1, kHid, w.b1, nullptr, 0, s);
+    if (e == cudaSuccess) e = sgemm<false, false, kEpiBias | kEpiRelu>(N, kHid, kHid, H1, kHid, w.W2, kHid, H2, kHid, w.b2, nullptr, 0, s);
+    if (e == cudaSuccess) e = sgemm<false, false, kEpiBias>(N, C, kHid, H2, kHid, w.W3, C, Z, C, w.b3, nullptr, 0, s);
+    return e;
+}
+
+static size_t mlp_ws_floats(int C, int64_t n) { return (size_t)n * (8 + 4 * kHid + 2 * (size_t)C + 2) + 64; }
+
+qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, const double* geom, int64_t n,
+                           float* logits, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    if (!cells_ok(n_cells) || n < 0 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 16384], n in [0, 2^24]");
+    if (n == 0) return QRS_OK;
+    if (!params || !geom || !logits) return fail(h, QRS_ERR_ARG, "params, geom and logits must be non-NULL");
+    qrs_status st = ensure_work(h, mlp_ws_floats(n_cells, n) * sizeof(float));
+    if (st != QRS_OK) return st;
+    float* X = static_cast<float*>(h->d_work);
+    float* H1 = X + 8 * n;
+    float* H2 = H1 + kHid * n;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = mlp_forward(n_cells, params, geom, n, X, H1, H2, logits, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_forward");
+    h->launches += 4;
+    return QRS_OK;
+}
+
+qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params, const double* geom,
+                             const float* targets, int64_t n, float* grad, float* loss, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    if (!cells_ok(n_cells) || n < 1 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 16384], n in [1, 2^24]");
+    if (!params || !geom || !targets || !grad || !loss) return fail(h, QRS_ERR_ARG, "null pointer argument");
+    const int C = n_cells;
+    qrs_status st = ensure_work(h, mlp_ws_floats(C, n) * sizeof(float));
+    if (st != QRS_OK) return st;
+    float* X = static_cast<float*>(h->d_work);
+    float* H1 = X + 8 * n;
+    float* H2 = H1 + kHid * n;
+    float* dA2 = H2 + kHid * n;
+    float* dA1 = dA2 + kHid * n;
+    float* Z = dA1 + kHid * n;
+    float* dZ = Z + (int64_t)C * n;
+    float* ones = dZ + (int64_t)C * n;
+    float* lrow = ones + n;
+    cudaStream_t s = (cudaStream_t)stream;
+    MlpView w = mlp_view(const_cast<float*>(params), C);
+    MlpView g = mlp_view(grad, C);
+    const int N = (int)n;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = mlp_forward(C, params, geom, n, X, H1, H2, Z, s);
+    if (e == cudaSuccess) {
+        k_softmax_ce<<<(unsigned)n, 256, 0, s>>>(Z, targets, C, n, dZ, lrow);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_loss_mean<<<1, 1024, 0, s>>>(lrow, n, loss);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_fill<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(ones, n, 1.0f);
+        e = cudaGetLastError();
+    }
+    // layer 3: dW3 = H2^T dZ, db3 = 1^T dZ, dA2 = (dZ W3^T) * (H2 > 0)
+    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(kHid, C, N, H2, kHid, dZ, C, g.W3, C, nullptr, nullptr, 0, s);
+    if (e == cudaSuccess) e = sgemm<false, false, kEpiNone>(1, C, N, ones, N, dZ, C, g.b3, C, nullptr, nullptr, 0, s);
+    if (e == cudaSuccess) e = sgemm<false, true, kEpiMask>(N, kHid, C, dZ, C, w.W3, C, dA2, kHid, nullptr, H2, kHid, s);
+    // layer 2
+    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(kHid, kHid, N, H1, kHid, dA2, kHid, g.W2, kHid, nullptr, nullptr, 0, s);
+    if (e == cudaSuccess) e = sgemm<false, false, kEpiNone>(1, kHid, N, ones, N, dA2, kHid, g.b2, kHid, nullptr, nullptr, 0, s);
+    if (e == cudaSuccess) e = sgemm<false, true, kEpiMask>(N, kHid, kHid, dA2, kHid, w.W2, kHid, dA1, kHid, nullptr, H1, kHid, s);
+    // layer 1
+    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(6, kHid, N, X, 6, dA1, kHid, g.W1, kHid, nullptr, nullptr, 0, s);
+    if (e == cudaSuccess) e = sgemm<false, false, kEpiNone>(1, kHid, N, ones, N, dA1, kHid, g.b1, kHid, nullptr, nullptr, 0, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_loss_grad");
+    h->launches += 4 + 3 + 9;
+    return QRS_OK;
+}
+
+qrs_status qrs_mlp_adam(qrs_handle* h, int32_t n_cells, float* params, float* m, float* v, const float* grad, float lr,
+                        int64_t step, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    if (!cells_ok(n_cells) || step < 1 || !(lr > 0.0f)) return fail(h, QRS_ERR_ARG, "n_cells, step >= 1, lr > 0");
+    if (!params || !m || !v || !grad) return fail(h, QRS_ERR_ARG, "null pointer argument");
+    const int64_t n = mlp_params(n_cells);
+    const float c1 = (float)(1.0 / (1.0 - std::pow(0.9, (double)step)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow(0.999, (double)step)));
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) {
+        k_adam<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(n, params, m, v, grad, lr,
+                                                                                                     c1, c2);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_adam");
+    ++h->launches;
+    return QRS_OK;
+}
+
+qrs_status qrs_proposal_cdf(qrs_handle* h, int32_t n_rho, int32_t n_theta, const float* logits, float eps,
+                            uint32_t* cdf, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    const int64_t C = (int64_t)n_rho * n_theta;
+    if (n_rho < 1 || n_theta < 1 || !cells_ok((int32_t)C) || !(eps > 0.0f && eps <= 1.0f))
+        return fail(h, QRS_ERR_ARG, "n_rho x n_theta in [1, 16384], 0 < eps <= 1");
+    if (!logits || !cdf) return fail(h, QRS_ERR_ARG, "logits and cdf must be non-NULL");
+    qrs_status st = ensure_work(h, (size_t)(C + n_rho) * sizeof(double) + 256);
+    if (st != QRS_OK) return st;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) {
+        k_prop_cdf<<<1, 1024, 0, (cudaStream_t)stream>>>(logits, n_rho, n_theta, eps, cdf,
+                                                         static_cast<double*>(h->d_work));
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_proposal_cdf");
+    ++h->launches;
+    return QRS_OK;
+}
+
+}  // extern "C"

@@ -237,39 +237,46 @@ __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64
     double sx = 0.0, sy = 0.0, fx = 0.0, fy = 0.0;
     Term t;
     t.cell = -1;
-    float J = 0.0f;
+    float J = 0.0f, p_cell = 1.0f;
     if (p.smp == kSmpImportance) {
-        // R2 point; its x top 32 bits choose the cell by inverse CDF, the rest
-        // places the frequency area-uniformly inside the annular sector.
+        // R2 point; the radial band from the marginal CDF with the top 32 bits
+        // of x, the angular cell from that band's conditional CDF with the top
+        // 32 bits of y; the remainders place the frequency inside the cell by
+        // the cell's own log-polar map.
         Sx = p.s0x + n * kR2StepX;
         Sy = p.s0y + n * kR2StepY;
-        const uint32_t u = (uint32_t)(Sx >> 32);
-        const int nc = p.n_rho * p.n_theta;
-        int lo = 0, hi = nc;  // largest c with cdf[c] <= u (cdf[0] = 0)
+        const uint32_t ux = (uint32_t)(Sx >> 32), uy = (uint32_t)(Sy >> 32);
+        const uint32_t* cr = p.cdf;
+        int lo = 0, hi = p.n_rho;  // largest band with cr[band] <= ux (cr[0] = 0)
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (__ldg(p.cdf + mid) <= u) lo = mid; else hi = mid;
+            if (__ldg(cr + mid) <= ux) lo = mid; else hi = mid;
         }
-        const int c = lo;
-        const uint64_t start = (uint64_t)__ldg(p.cdf + c);
-        const uint64_t end = (c + 1 < nc) ? (uint64_t)__ldg(p.cdf + c + 1) : (1ull << 32);
-        const uint64_t width = end - start;
-        const double tt = __ddiv_rn((double)(Sx - (start << 32)), __dmul_rn((double)width, 0x1p32));
-        const double syi = fix_to_unit(Sy);
-        const int ir = c / p.n_theta, it = c - (c / p.n_theta) * p.n_theta;
-        const double rlo = __dmul_rn(p.fmin, exp(__ddiv_rn(__dmul_rn(p.log_ratio, (double)ir), (double)p.n_rho)));
-        const double rhi =
-            __dmul_rn(p.fmin, exp(__ddiv_rn(__dmul_rn(p.log_ratio, (double)(ir + 1)), (double)p.n_rho)));
-        const double rlo2 = __dmul_rn(rlo, rlo), rhi2 = __dmul_rn(rhi, rhi);
-        const double rho = sqrt(__dadd_rn(rlo2, __dmul_rn(tt, __dsub_rn(rhi2, rlo2))));
-        const double th = __ddiv_rn(__dmul_rn(kTwoPi, __dadd_rn((double)it, syi)), (double)p.n_theta);
+        const int ir = lo;
+        const uint32_t* ct = p.cdf + p.n_rho + (int64_t)ir * p.n_theta;
+        lo = 0;
+        hi = p.n_theta;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(ct + mid) <= uy) lo = mid; else hi = mid;
+        }
+        const int it = lo;
+        const uint64_t r_start = (uint64_t)__ldg(cr + ir);
+        const uint64_t r_end = (ir + 1 < p.n_rho) ? (uint64_t)__ldg(cr + ir + 1) : (1ull << 32);
+        const uint64_t t_start = (uint64_t)__ldg(ct + it);
+        const uint64_t t_end = (it + 1 < p.n_theta) ? (uint64_t)__ldg(ct + it + 1) : (1ull << 32);
+        const double tx = __ddiv_rn((double)(Sx - (r_start << 32)), __dmul_rn((double)(r_end - r_start), 0x1p32));
+        const double ty = __ddiv_rn((double)(Sy - (t_start << 32)), __dmul_rn((double)(t_end - t_start), 0x1p32));
+        const int c = ir * p.n_theta + it;
+        const double rho =
+            __dmul_rn(p.fmin, exp(__ddiv_rn(__dmul_rn(p.log_ratio, __dadd_rn((double)ir, tx)), (double)p.n_rho)));
+        const double th = __ddiv_rn(__dmul_rn(kTwoPi, __dadd_rn((double)it, ty)), (double)p.n_theta);
         double s, co;
         sincos(th, &s, &co);
         fx = __dmul_rn(rho, co);
         fy = __dmul_rn(rho, s);
-        const double area = __dmul_rn(__dmul_rn(__ddiv_rn(kTwoPi, (double)p.n_theta), 0.5), __dsub_rn(rhi2, rlo2));
-        const double pc = __dmul_rn((double)width, 0x1p-32);
-        J = (float)__ddiv_rn(area, pc);
+        p_cell = (float)__dmul_rn(__dmul_rn((double)(r_end - r_start), 0x1p-32),
+                                  __dmul_rn((double)(t_end - t_start), 0x1p-32));
         t.cell = c;
     } else {
         if (p.smp == kSmpR2) {
@@ -300,6 +307,7 @@ __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64
     t.fy = (float)fy;
     const float f2 = t.fx * t.fx + t.fy * t.fy;
     if (p.smp != kSmpImportance) J = (p.dom == kDomLogPolar) ? p.jac_c * f2 : p.jac_c;
+    else J = p.jac_c * f2 / ((float)(p.n_rho * p.n_theta) * p_cell);  // log-polar Jacobian / (cells x p_c)
     t.J = J;
     t.F = sqrtf(psd_w(p.psd_c, p.psd_a, f2) * J * p.inv_nf);
     coef_from_words(p, n, w, t.a, t.b);

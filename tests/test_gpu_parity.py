@@ -17,6 +17,7 @@ import torch
 
 import oracle
 import paper_2404_02978_gb300 as qrs
+from cdf_inputs import two_level_cdf
 from paper_2404_02978_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -48,10 +49,7 @@ def _cdf(nr, nt, seed):
     rng = np.random.default_rng(seed)
     nc = nr * nt
     p = 0.6 * rng.dirichlet(np.ones(nc) * 0.3) + 0.4 / nc
-    w = np.floor(p * 2**32).astype(np.int64)
-    w = np.maximum(w, 1)
-    w[np.argmax(w)] += 2**32 - w.sum()
-    return np.concatenate([[0], np.cumsum(w)[:-1]]).astype(np.uint32)
+    return two_level_cdf(p, nr, nt)[0]
 
 
 DRAW_CASES = [

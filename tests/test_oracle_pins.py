@@ -28,6 +28,7 @@ import pytest
 from scipy import stats
 
 import oracle
+from cdf_inputs import two_level_cdf
 from oracle import analytic as an
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -253,9 +254,7 @@ def test_importance_uniform_cdf_is_unbiased():
     nc = nr * nt
     rng = np.random.default_rng(5)
     p_c = 0.5 * rng.dirichlet(np.ones(nc)) + 0.5 / nc
-    widths = np.floor(p_c * 2**32).astype(np.int64)
-    widths[np.argmax(widths)] += 2**32 - widths.sum()
-    cdf = np.concatenate([[0], np.cumsum(widths)[:-1]]).astype(np.uint32)
+    cdf, p_q = two_level_cdf(p_c, nr, nt)
     p = oracle.params(sampler="importance", n_rho=nr, n_theta=nt, cdf=cdf, r0=0.15, L0=30.0,
                       fmin=1e-3, fmax=16.0, seed=9)
     d = oracle.draw(p, n_f=1024, n_real=30)
@@ -271,7 +270,7 @@ def test_importance_uniform_cdf_is_unbiased():
     assert np.all((rho >= lo) & (rho <= hi))
     # cell frequencies follow p_c
     cnt = np.bincount(d["cell"].ravel(), minlength=nc)
-    assert stats.chisquare(cnt, p_c * cnt.sum()).pvalue > 1e-4
+    assert stats.chisquare(cnt, p_q * cnt.sum()).pvalue > 1e-4
 
 
 def test_jitter_one_point_per_cell():

@@ -72,14 +72,19 @@ def test_targets_sum_to_hankel_integral():
 
 def test_cdf_valid_uniform_and_floor():
     rng = np.random.default_rng(2)
-    for C in (16, 2048):
+    for nr, nt in ((4, 4), (64, 32)):
+        C = nr * nt
         z = rng.normal(scale=4.0, size=C)
-        cdf, w = pr.cdf(z, 0.1)
-        assert cdf[0] == 0 and np.all(w >= 1) and w.sum() == 2**32
-        assert np.all(np.diff(cdf.astype(np.int64)) > 0)
-        assert np.all(w >= np.floor(0.1 / C * (2**32 - C)))
-        _, wu = pr.cdf(np.zeros(C), 0.1)
-        assert wu.max() - wu.min() <= C
+        cdf, pq = pr.cdf(z, 0.1, nr, nt)
+        starts = [cdf[:nr]] + [cdf[nr + i * nt: nr + (i + 1) * nt] for i in range(nr)]
+        for s in starts:
+            s = s.astype(np.int64)
+            w = np.diff(np.concatenate([s, [2**32]]))
+            assert s[0] == 0 and np.all(w >= 1) and w.sum() == 2**32
+        assert pq.sum() == pytest.approx(1.0, abs=1e-9)
+        assert np.all(pq >= 0.1 / C * (1 - 1e-6))  # the mixture floor survives quantisation
+        _, pu = pr.cdf(np.zeros(C), 0.1, nr, nt)
+        assert np.allclose(pu, 1.0 / C, rtol=1e-6)
 
 
 def test_he_init_statistics():
