@@ -51,6 +51,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other forms (GEMM, batched, learned)")
     return ap.parse_args()
 
 
@@ -283,8 +284,9 @@ def hankel_piston_sf(B, r0, L0, D, fmin, fmax):
     return float(np.sum(ww * 4 * np.pi * f * W * A * A * (1 - sp.j0(2 * np.pi * f * B))))
 
 
-def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8):
-    """Learned proposal (6 -> 128 -> 128 -> 64 x 32 logits): targets from the
+def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho=64, n_theta=32, steps=3000,
+                    target_draws=256):
+    """Learned proposal (6 -> 128 -> 128 -> n_rho x n_theta logits): targets from the
     plain method's own draws, training on the GPU, then the matched
     structure-function error (RMS over held-out geometries and draws of the
     per-draw SF relative to the Hankel integral) of learned importance draws
@@ -298,25 +300,31 @@ def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8):
                          B * np.cos(th), B * np.sin(th)], -1)
 
     dom = dict(domain="logpolar", fmin=1e-3, fmax=10.0)
-    C = 64 * 32
+    C = n_rho * n_theta
     gtr = torch.from_numpy(geom(n_train, 1)).to(dev)
     gte_np = geom(n_test, 2)
     t0 = time.perf_counter()
-    T = qrs.qrs_proposal_targets(h, qrs.params(**dom), 64, 32, 77, 4096, 256, gtr, kind="rms")
+    T = qrs.qrs_proposal_targets(h, qrs.params(**dom), n_rho, n_theta, 77, 4096, target_draws, gtr, kind="rms")
     torch.cuda.synchronize()
     t_targets = time.perf_counter() - t0
     t0 = time.perf_counter()
-    P, hist = qrs.train_proposal(h, C, gtr, T, steps=3000, lr=2e-3, seed=3, log_every=1000)
+    P, hist = qrs.train_proposal(h, C, gtr, T, steps=steps, lr=2e-3, seed=3, log_every=1000)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     logits = qrs.qrs_mlp_forward(h, C, P, torch.from_numpy(gte_np).to(dev))
+    T_test = qrs.qrs_proposal_targets(h, qrs.params(**dom), n_rho, n_theta, 78, 4096, 512,
+                                      torch.from_numpy(gte_np).to(dev), kind="rms")
     err = {}
     for i, (r0, L0, D, Bx, By) in enumerate(gte_np):
         Dref = hankel_piston_sf(np.hypot(Bx, By), r0, L0, D, 1e-3, 10.0)
         p = qrs.params(r0=r0, L0=L0, seed=1000 + i, **dom)
-        cdf = qrs.qrs_proposal_cdf(h, 64, 32, logits[i].contiguous(), 0.05)
-        pi = dict(p, sampler="importance", n_rho=64, n_theta=32, cdf=cdf)
-        for name, pp, nfs in (("plain", p, (256, 512, 1024, 2048, 4096)), ("learned", pi, (256, 512, 1024))):
+        cdf = qrs.qrs_proposal_cdf(h, n_rho, n_theta, logits[i].contiguous(), 0.05)
+        pi = dict(p, sampler="importance", n_rho=n_rho, n_theta=n_theta, cdf=cdf)
+        # the ceiling of any cell density on this grid: the geometry's own targets as the proposal
+        cdf_x = qrs.qrs_proposal_cdf(h, n_rho, n_theta, torch.log(T_test[i].clamp_min(1e-30)).contiguous(), 0.05)
+        px = dict(pi, cdf=cdf_x)
+        for name, pp, nfs in (("plain", p, (256, 512, 1024, 2048, 4096)), ("learned", pi, (256, 512, 1024)),
+                              ("own_targets", px, (256, 512, 1024))):
             for nf in nfs:
                 d = qrs.qrs_draw(h, pp, nf, draws, outputs=("f_xy", "amp"))
                 f, F = d["f_xy"].double(), d["amp"].double()
@@ -330,16 +338,19 @@ def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8):
     plain_n = np.array([256, 512, 1024, 2048, 4096], float)
     plain_e = np.array([rms["plain_%d" % n] for n in plain_n.astype(int)])
     # plain terms needed for the learned error (log-log interpolation of the plain curve)
-    equiv = {}
+    equiv, cap = {}, {}
     for nf in (256, 512, 1024):
-        e = rms["learned_%d" % nf]
-        equiv[nf] = float(np.exp(np.interp(-np.log(e), -np.log(plain_e), np.log(plain_n))))
-    return {"workload": "2000 training geometries (r0 0.05-0.3 m, L0 10-100 m, D 1-8 m, |B| 1-200 m), "
-                        "%d held out, %d draws each, cells 64x32 over [1e-3, 10] c/m" % (n_test, draws),
-            "targets_s": t_targets, "train_s": t_train, "train_steps": 3000, "loss_first_last": [hist[0][1], hist[-1][1]],
+        for name, d in (("learned", equiv), ("own_targets", cap)):
+            e = rms["%s_%d" % (name, nf)]
+            d[nf] = float(np.exp(np.interp(-np.log(e), -np.log(plain_e), np.log(plain_n))))
+    return {"workload": "%d training geometries (r0 0.05-0.3 m, L0 10-100 m, D 1-8 m, |B| 1-200 m), "
+                        "%d held out, %d draws each, cells %dx%d over [1e-3, 10] c/m"
+                        % (n_train, n_test, draws, n_rho, n_theta),
+            "targets_s": t_targets, "train_s": t_train, "train_steps": steps, "loss_first_last": [hist[0][1], hist[-1][1]],
             "matched_sf_error": rms,
             "plain_terms_for_equal_error": {str(k): v for k, v in equiv.items()},
-            "term_reduction": {str(k): v / k for k, v in equiv.items()}}
+            "term_reduction": {str(k): v / k for k, v in equiv.items()},
+            "term_reduction_own_targets": {str(k): v / k for k, v in cap.items()}}
 
 
 def run_ours(a):
@@ -443,7 +454,7 @@ def run_ours(a):
     }
     if clk:
         line["clocks"] = clk
-    if world == 1:
+    if world == 1 and not a.headline_only:
         peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
         line["other_forms"] = {m: measure_gemm(qrs, h, torch, dev, m, peaks) for m in ("gemm_3xtf32", "gemm_bf16x3")}
         line["other_forms"]["batched_pistons"] = measure_batched(qrs, h, torch, dev)

@@ -11,10 +11,11 @@ from paper_2404_02978_gb300 import workloads as wl
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="phase_screen", choices=["phase_screen", "piston_plain", "gemm_screen"])
+    ap.add_argument("--case", default="phase_screen", choices=["phase_screen", "piston_plain", "gemm_screen", "batched"])
     ap.add_argument("--mode", default="gemm_3xtf32", choices=["gemm_3xtf32", "gemm_bf16x3"])
     ap.add_argument("--points", type=int, default=0, help="gemm_screen: first N points only (0 = all)")
     ap.add_argument("--n-real", type=int, default=16)
+    ap.add_argument("--n-inst", type=int, default=1000, help="batched: number of interferometers")
     ap.add_argument("--repeat", type=int, default=2)
     a = ap.parse_args()
     B.build()
@@ -33,6 +34,16 @@ def main():
         for i in range(a.repeat):
             qrs.qrs_synthesize_points(h, wl.method_params(cfg), cfg["n_f"], cfg["n_real"], xy, mode=a.mode,
                                       real_offset=i * cfg["n_real"])
+    elif a.case == "batched":
+        cfg = wl.BATCHED
+        dev = lambda v: torch.from_numpy(v).cuda()
+        jobs = []
+        for i in wl.batched_instances(a.n_inst, seed=cfg["seed"]):
+            dlt = torch.empty(i["n_real"], i["pairs"].shape[0], device="cuda")
+            jobs.append(qrs.piston_job(wl.method_params(dict(cfg, seed=i["seed"])), i["n_f"], i["n_real"],
+                                       dev(i["ap_xy"]), dev(i["ap_D"]), dev(i["ap_d"]), dev(i["pairs"]), None, dlt))
+        for i in range(a.repeat):
+            qrs.qrs_diff_piston(h, jobs, flags=qrs.PISTON_PERSISTENT | qrs.PISTON_GRAPH)
     else:
         cfg = wl.PISTON_PLAIN
         B_, ap_xy, ap_D, ap_d, pairs = wl.piston_plain_apertures()
