@@ -228,6 +228,59 @@ def measure_gemm(qrs, h, torch, dev, mode, peaks):
                          "flops_per_batch": flops, "note": "whole call: point bound, shared draw, coefficients, GEMM"}}
 
 
+def measure_grid(qrs, h, torch, dev, peaks, mode="gemm_3xtf32", reps=5):
+    """Separable-grid form on the benchmark's own workload: the 8 m / 256^2
+    pupil (51,468 interior points, written in pupil order through the node
+    index), N_f = 4096 drawn per realisation, 1000 realisations per call --
+    the same field as the fused form (realisation r from stream points r N_f + k)."""
+    from paper_2404_02978_gb300 import workloads as wl
+    cfg = wl.PHASE_SCREEN
+    n, L = cfg["grid"], cfg["pupil"]
+    c = (np.arange(n, dtype=np.float64) + 0.5 - n / 2) * (L / n)
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    inside = (X ** 2 + Y ** 2 <= (L / 2) ** 2).ravel()
+    index = np.full(n * n, -1, np.int32)
+    index[inside] = np.arange(int(inside.sum()), dtype=np.int32)
+    P = int(inside.sum())
+    cd = torch.from_numpy(c.astype(np.float32)).to(dev)
+    idx = torch.from_numpy(index).to(dev)
+    p = wl.method_params(cfg)
+    R, nf = cfg["n_real"], cfg["n_f"]
+    out = torch.empty(R, P, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    run = lambda i: qrs.qrs_synthesize_grid(h, p, nf, R, cd, cd, index=idx, n_points=P, out=out, mode=mode,
+                                            real_offset=i * R, stream=stream)
+    for i in range(3):
+        run(i)
+    qrs.qrs_sync(h, stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for i in range(reps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        run(3 + i)
+        ev[i][1].record(stream)
+    qrs.qrs_sync(h, stream)
+    t = sum(s.elapsed_time(e) for s, e in ev) / reps / 1e3
+    T = 16 if mode == "gemm_3xtf32" else 32
+    nf_pad = (nf + T - 1) // T * T
+    n_pad = (n + 127) // 128 * 128
+    m_pad = (n + 255) // 256 * 256
+    flops = 3 * 2 * n_pad * m_pad * (2 * nf_pad) * R  # three split products, executed tiles
+    bf16 = float(peaks.get("bf16_tflops", 1889.0))
+    peak = bf16 * (TF32_OVER_BF16 if mode == "gemm_3xtf32" else 1.0)
+    return {"workload": "8 m pupil 256x256 grid (%d interior points), N_f=%d per realisation, %d realisations, %s"
+                        % (P, nf, R, mode),
+            "ms_per_call": t * 1e3, "value": P * nf * R / t, "unit": UNIT,
+            "grid_nodes_per_s": n * n * nf * R / t,
+            "roofline": {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / t / 1e12 / peak,
+                         "peak_basis": ("measured bf16 burst %.0f x nominal tf32/bf16 %.3f" % (bf16, TF32_OVER_BF16))
+                         if mode == "gemm_3xtf32" else "measured bf16 burst",
+                         "flops_per_call": flops,
+                         "note": "whole call: bound prepass, draw records, grid kernel; L2 flushed between calls"}}
+
+
 def measure_batched(qrs, h, torch, dev):
     """1000 interferometers (n_ap ~ U{4..64}, D ~ U(1.8, 8) m, 200 m disc,
     N_f ~ U{256..8192}, 256 realisations, all pairs): one persistent,
@@ -363,6 +416,7 @@ def run_ours(a):
     from paper_2404_02978_gb300 import build as B
     B.build()
     import paper_2404_02978_gb300 as qrs
+    from paper_2404_02978_gb300.shard import max_over_ranks, realisation_slice
     cfg, p, xy_np = _workload()
     h = qrs.Handle(local)
     dev = torch.device("cuda", local)
@@ -371,7 +425,7 @@ def run_ours(a):
     out = torch.empty(R, P, dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    off0 = rank * R
+    off0, _ = realisation_slice(rank, world, R)
 
     def step(i):
         qrs.qrs_synthesize_points(h, p, nf, R, xy, out=out, real_offset=off0, stream=stream)
@@ -405,11 +459,7 @@ def run_ours(a):
     times = [s.elapsed_time(e) for s, e in ev]  # ms, device clock, per step
     t_step = sum(times) / len(times)
     t_tot = sum(times) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_tot = float(tt.item())
+    t_tot = max_over_ranks(t_tot, world, dev)
     terms_step = P * nf * R
     value = terms_step * a.steps * world / t_tot
 
@@ -457,6 +507,7 @@ def run_ours(a):
     if world == 1 and not a.headline_only:
         peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
         line["other_forms"] = {m: measure_gemm(qrs, h, torch, dev, m, peaks) for m in ("gemm_3xtf32", "gemm_bf16x3")}
+        line["other_forms"]["grid_3xtf32"] = measure_grid(qrs, h, torch, dev, peaks)
         line["other_forms"]["batched_pistons"] = measure_batched(qrs, h, torch, dev)
         line["other_forms"]["learned_proposal"] = measure_learned(qrs, h, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -201,6 +201,31 @@ qrs_status qrs_synthesize_points(qrs_handle* h, const qrs_psd* psd, const qrs_do
                                  int64_t real_offset, const float* xy, int64_t n_points,
                                  int32_t mode, const double* col_psd, float* out, void* stream);
 
+/* ------------------------------------------------ synthesis on a grid ---
+ * Eq. 3 on a tensor-product point set {x_i} x {y_j} (a pupil sampled on a
+ * grid, Sec. 3 and 4): the same field as qrs_synthesize_points in FUSED mode
+ * at the points (x_i, y_j) -- realisation r uses stream points
+ * (real_offset + r) N_f + k -- computed through the factorisation
+ * e^{i 2 pi f.x} = e^{i 2 pi fx x} e^{i 2 pi fy y} as one matrix product per
+ * realisation on the tensor cores (cos/sin of fx x_i against the
+ * coefficient-weighted cos/sin of fy y_j; (n_x + n_y) N_f sin/cos pairs per
+ * realisation instead of n_x n_y N_f).  The paper has no such form: it is the
+ * Eq. 3 sum regrouped, exact up to rounding.
+ *   x [nx], y [ny]   FP32 coordinates, m (any values; a uniform grid is not needed)
+ *   index            NULL: out [n_real][ny][nx] (x fastest);
+ *                    else int32 [ny][nx]: node (i, j) goes to out[r][index[j][i]]
+ *                    when index[j][i] >= 0 (each point at most once), out
+ *                    [n_real][n_points] -- e.g. the interior of a pupil.
+ *   mode             QRS_SYNTH_GEMM_3XTF32 (split TF32, ~FP32 accuracy) or
+ *                    QRS_SYNTH_GEMM_BF16X3 (split BF16, ~2^-16 relative).
+ * Workspace: draw records of up to 256 MB of realisations at a time, owned by
+ * the handle; calls on one handle must not overlap in time.
+ * nx, ny in [0, 2^24], n_real >= 0 (an empty grid or n_real = 0 is a no-op). */
+qrs_status qrs_synthesize_grid(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom,
+                               const qrs_sampler* smp, int64_t n_f, int64_t n_real, int64_t real_offset,
+                               const float* x, int64_t nx, const float* y, int64_t ny, const int32_t* index,
+                               int64_t n_points, int32_t mode, float* out, void* stream);
+
 /* ------------------------------------------------------------- pistons ---
  * Differential pistons (Sec. 4.1, 4.4; PSD and filter of Eq. 7):
  *   piston[r][a] = sum_k F_k A_a(|f_k|) (a_k cos 2 pi f_k.p_a - b_k sin 2 pi f_k.p_a),

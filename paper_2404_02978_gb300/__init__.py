@@ -20,7 +20,7 @@ import threading
 
 import torch
 
-__all__ = ["params", "Handle", "qrs_create", "qrs_draw", "qrs_synthesize_points", "qrs_diff_piston",
+__all__ = ["params", "Handle", "qrs_create", "qrs_draw", "qrs_synthesize_points", "qrs_synthesize_grid", "qrs_diff_piston",
            "qrs_structure_fn", "qrs_sync", "QrsError", "lib_path", "load"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -224,6 +224,44 @@ def qrs_synthesize_points(h: Handle, p, n_f, n_real, xy, out=None, mode="fused",
     h._check(h.L.qrs_synthesize_points(h.h, C.byref(psd), C.byref(dom), C.byref(smp), int(n_f), int(n_real),
                                        int(real_offset), xy.data_ptr(), int(P), MODE[mode], cp, out.data_ptr(),
                                        _stream(stream)))
+    return out
+
+
+def qrs_synthesize_grid(h: Handle, p, n_f, n_real, x, y, index=None, n_points=None, out=None, mode="gemm_3xtf32",
+                        real_offset=0, stream=None):
+    """Eq. 3 on the tensor-product grid {x} x {y} (float32 device vectors) by the
+    separable tensor-core form.  index None: returns out [n_real, ny, nx];
+    else index int32 [ny, nx] (output point per node, -1 = none) and out
+    [n_real, n_points] (n_points defaults to index.max() + 1)."""
+    _check_dev(x, torch.float32, "x")
+    _check_dev(y, torch.float32, "y")
+    nx, ny = x.numel(), y.numel()
+    ip = None
+    if index is not None:
+        _check_dev(index, torch.int32, "index")
+        if index.numel() != nx * ny:
+            raise ValueError("index must hold ny * nx entries")
+        if n_points is None:
+            n_points = int(index.max().item()) + 1 if index.numel() else 0
+        ip = index.data_ptr()
+        shape = (n_real, n_points)
+    else:
+        n_points = nx * ny
+        shape = (n_real, ny, nx)
+    if out is None:
+        out = torch.empty(*shape, dtype=torch.float32, device=x.device)
+    _check_dev(out, torch.float32, "out")
+    if out.numel() != n_real * n_points:
+        raise ValueError("out must hold n_real * n_points values")
+    f = h.L.qrs_synthesize_grid
+    if f.argtypes is None:
+        f.argtypes = [C.c_void_p, C.POINTER(QrsPsd), C.POINTER(QrsDomain), C.POINTER(QrsSampler), C.c_int64,
+                      C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                      C.c_int32, C.c_void_p, C.c_void_p]
+        f.restype = C.c_int
+    psd, dom, smp = _structs(p)
+    h._check(f(h.h, C.byref(psd), C.byref(dom), C.byref(smp), int(n_f), int(n_real), int(real_offset), x.data_ptr(),
+               int(nx), y.data_ptr(), int(ny), ip, int(n_points), MODE[mode], out.data_ptr(), _stream(stream)))
     return out
 
 

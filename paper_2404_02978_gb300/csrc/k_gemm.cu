@@ -47,44 +47,13 @@
 
 #include "qrs_internal.h"
 #include "qrs_sm100.cuh"
+#include "qrs_tc_split.cuh"
 
-#ifndef QRS_GEMM_SEG_TF32
-#define QRS_GEMM_SEG_TF32 6   // K chunks per accumulation segment, 3XTF32 (72 accumulation steps)
-#endif
-#ifndef QRS_GEMM_SEG_BF16
-#define QRS_GEMM_SEG_BF16 8   // K chunks per accumulation segment, BF16X3 (96 accumulation steps)
-#endif
 #ifndef QRS_GEMM_PRODUCERS
 #define QRS_GEMM_PRODUCERS 8  // basis producer warps (4: one per row block; 8: two, splitting the terms)
 #endif
-#ifndef QRS_GEMM_INTSPLIT
-#define QRS_GEMM_INTSPLIT 1   // hi/lo splits by integer rounding (ALU) instead of conversions
-#endif
 
 namespace qrs {
-
-template <int PREC>
-struct GemmCfg;
-template <>
-struct GemmCfg<QRS_SYNTH_GEMM_3XTF32> {
-    static constexpr int kElemBytes = 4;
-    static constexpr int kElemsPerRow = 32;    // one 128-byte row of a K chunk
-    static constexpr int kTermsPerChunk = 16;  // cos and sin of 16 terms
-    static constexpr int kTermsPer16B = 4;
-    static constexpr uint32_t kFormat = 2;     // TF32
-    static constexpr bool kTF32 = true;
-    static constexpr int kSeg = QRS_GEMM_SEG_TF32;
-};
-template <>
-struct GemmCfg<QRS_SYNTH_GEMM_BF16X3> {
-    static constexpr int kElemBytes = 2;
-    static constexpr int kElemsPerRow = 64;
-    static constexpr int kTermsPerChunk = 32;
-    static constexpr int kTermsPer16B = 8;
-    static constexpr uint32_t kFormat = 1;     // BF16
-    static constexpr bool kTF32 = false;
-    static constexpr int kSeg = QRS_GEMM_SEG_BF16;
-};
 
 constexpr int kGM = 128;                                   // points per tile (UMMA M, TMEM lanes)
 constexpr int kGN = 256;                                   // columns per block (UMMA N)
@@ -199,63 +168,6 @@ __global__ void k_gemm_coef(DrawParams p, int64_t nf_pad, int64_t n_real, int64_
 }
 
 // ------------------------------------------------------------ main kernel
-// Split 16 bytes' worth of values into hi and lo halves in the operand format
-// (TF32 in 32-bit words with the low 13 bits zero, or pairs of BF16).
-// TF32 rounding to nearest, ties away from zero (as cvt.rna.tf32.f32): add half
-// of the dropped 13-bit field to the magnitude bits, then clear the field.
-__device__ __forceinline__ uint32_t tf32_rna_bits(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
-// BF16 rounding to nearest, ties to even (as cvt.rn.bf16.f32), as FP32 bits.
-__device__ __forceinline__ uint32_t bf16_rne_bits(float x)
-{
-    const uint32_t u = __float_as_uint(x);
-    return (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
-}
-
-// Split 16 bytes' worth of values into hi and lo halves in the operand format
-// (TF32 in 32-bit words with the low 13 bits zero, or pairs of BF16); the
-// residual x - hi is exact in FP32.
-template <int PREC>
-__device__ __forceinline__ void pack16(const float (&v)[GemmCfg<PREC>::kTermsPer16B], uint4& hi, uint4& lo)
-{
-    uint32_t* wh = reinterpret_cast<uint32_t*>(&hi);
-    uint32_t* wl = reinterpret_cast<uint32_t*>(&lo);
-    if (GemmCfg<PREC>::kTF32) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-#if QRS_GEMM_INTSPLIT
-            const uint32_t h = tf32_rna_bits(v[e]);
-            wh[e] = h;
-            wl[e] = tf32_rna_bits(v[e] - __uint_as_float(h));
-#else
-            uint32_t h, l;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v[e]));
-            const float r = v[e] - __uint_as_float(h);
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
-            wh[e] = h;
-            wl[e] = l;
-#endif
-        }
-    } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float x0 = v[2 * e], x1 = v[2 * e + 1];
-#if QRS_GEMM_INTSPLIT
-            const uint32_t h0 = bf16_rne_bits(x0), h1 = bf16_rne_bits(x1);
-            const uint32_t l0 = bf16_rne_bits(x0 - __uint_as_float(h0));
-            const uint32_t l1 = bf16_rne_bits(x1 - __uint_as_float(h1));
-            wh[e] = __byte_perm(h0, h1, 0x7632);  // (h1 top half << 16) | h0 top half
-            wl[e] = __byte_perm(l0, l1, 0x7632);
-#else
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-            const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-            const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-            wh[e] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            wl[e] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-#endif
-        }
-    }
-}
-
 template <int PREC>
 __global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constant__ CUtensorMap tmapB, GemmArgs g)
 {

@@ -254,6 +254,37 @@ qrs_status qrs_synthesize_points(qrs_handle* h, const qrs_psd* psd, const qrs_do
     return fail(h, QRS_ERR_ARG, "unknown synthesis mode %d", mode);
 }
 
+qrs_status qrs_synthesize_grid(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, const qrs_sampler* smp,
+                               int64_t n_f, int64_t n_real, int64_t real_offset, const float* x, int64_t nx,
+                               const float* y, int64_t ny, const int32_t* index, int64_t n_points, int32_t mode,
+                               float* out, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    if (mode != QRS_SYNTH_GEMM_3XTF32 && mode != QRS_SYNTH_GEMM_BF16X3)
+        return fail(h, QRS_ERR_ARG, "grid synthesis modes: QRS_SYNTH_GEMM_3XTF32 or QRS_SYNTH_GEMM_BF16X3");
+    if (n_real < 0 || nx < 0 || ny < 0 || nx > (1 << 24) || ny > (1 << 24))
+        return fail(h, QRS_ERR_ARG, "n_real >= 0 and nx, ny in [0, 2^24]");
+    if (index && n_points < 0) return fail(h, QRS_ERR_ARG, "n_points must be >= 0");
+    DrawParams p;
+    qrs_status st = make_draw_params(h, psd, dom, smp, n_f, real_offset, &p);
+    if (st != QRS_OK) return st;
+    if (!counters_fit(n_f, real_offset, n_real)) return fail(h, QRS_ERR_ARG, "stream index overflows 2^64");
+    if (n_real == 0 || nx == 0 || ny == 0 || (index && n_points == 0)) return QRS_OK;
+    if (!x || !y || !out) return fail(h, QRS_ERR_ARG, "x, y and out must be non-NULL");
+    if (((uintptr_t)x & 3) || ((uintptr_t)y & 3) || ((uintptr_t)out & 3) || ((uintptr_t)index & 3))
+        return fail(h, QRS_ERR_ARG, "x, y, index and out must be 4-byte aligned");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    st = ensure_work(h, grid_workspace_bytes(mode, n_f, n_real));
+    if (st != QRS_OK) return st;
+    e = launch_synth_grid(h, mode, p, x, nx, y, ny, index, index ? n_points : nx * ny, n_real, out,
+                          (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_synthesize_grid launch");
+    h->launches += grid_launch_count(mode, n_f, n_real);
+    return QRS_OK;
+}
+
 static qrs_status build_piston_job(qrs_handle* h, const qrs_piston_job& j, PistonJobDev* d)
 {
     qrs_status st = make_draw_params(h, &j.psd, &j.dom, &j.smp, j.n_f, j.real_offset, &d->p);

@@ -11,7 +11,7 @@ from paper_2404_02978_gb300 import workloads as wl
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="phase_screen", choices=["phase_screen", "piston_plain", "gemm_screen", "batched"])
+    ap.add_argument("--case", default="phase_screen", choices=["phase_screen", "piston_plain", "gemm_screen", "batched", "grid_screen"])
     ap.add_argument("--mode", default="gemm_3xtf32", choices=["gemm_3xtf32", "gemm_bf16x3"])
     ap.add_argument("--points", type=int, default=0, help="gemm_screen: first N points only (0 = all)")
     ap.add_argument("--n-real", type=int, default=16)
@@ -34,6 +34,20 @@ def main():
         for i in range(a.repeat):
             qrs.qrs_synthesize_points(h, wl.method_params(cfg), cfg["n_f"], cfg["n_real"], xy, mode=a.mode,
                                       real_offset=i * cfg["n_real"])
+    elif a.case == "grid_screen":
+        import numpy as np
+        cfg = wl.PHASE_SCREEN
+        n, L = cfg["grid"], cfg["pupil"]
+        c = (np.arange(n, dtype=np.float64) + 0.5 - n / 2) * (L / n)
+        X, Y = np.meshgrid(c, c, indexing="xy")
+        inside = (X ** 2 + Y ** 2 <= (L / 2) ** 2).ravel()
+        index = np.full(n * n, -1, np.int32)
+        index[inside] = np.arange(int(inside.sum()), dtype=np.int32)
+        cd = torch.from_numpy(c.astype(np.float32)).cuda()
+        idx = torch.from_numpy(index).cuda()
+        for i in range(a.repeat):
+            qrs.qrs_synthesize_grid(h, wl.method_params(cfg), cfg["n_f"], a.n_real, cd, cd, index=idx,
+                                    mode=a.mode, real_offset=i * a.n_real)
     elif a.case == "batched":
         cfg = wl.BATCHED
         dev = lambda v: torch.from_numpy(v).cuda()
