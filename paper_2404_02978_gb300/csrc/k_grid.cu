@@ -26,16 +26,19 @@
 // k_grid_main: a persistent grid, one CTA per SM, walking work items
 // (realisation, 128-column x tile, 256-row y block), realisation-major, so
 // neighbouring CTAs share a realisation's draw records in L2.  Warps:
-//   warp 1      TMEM allocator (512 columns: a 128 x 256 FP32 master and a
-//               128 x 256 segment slot) and single-thread MMA issuer: 3 x 4
-//               tcgen05.mma per K chunk into the slot, a commit per segment;
+//   warp 1      TMEM allocator (512 columns: two 128 x 256 FP32 segment
+//               slots) and single-thread MMA issuer: 3 x 4 tcgen05.mma per K
+//               chunk into the segment's slot, a commit per segment, the two
+//               slots alternating so the MMAs never wait for a promotion;
 //   warp 2      record ring: bulk-copies each chunk's draw records into an
 //               8-slot shared-memory ring, up to 8 chunks ahead;
 //   promoters  (4 or 8 warps from warp 4): after each segment, master +=
-//               slot in FP32 through tcgen05.ld / st (the tensor core's
+//               slot in FP32 (tcgen05.ld of the slot; the master is the CTA's
+//               128 KB scratch in L2, each element owned by one thread, lanes
+//               along x so every access is coalesced).  The tensor core's
 //               accumulation drifts by about 2^-26 per step with a consistent
-//               sign; segments bound the chain); after the last one they
-//               store the tile, lanes along x (coalesced);
+//               sign, so segments bound the chain.  After the last segment
+//               they store the tile (lanes along x: coalesced);
 //   producers  (8, 12 or 16 warps after them): build the chunk's x rows and
 //               y rows -- phase (fixed point or double-float), MUFU sin/cos,
 //               the coefficient products on one side (the x side by
@@ -92,6 +95,7 @@ struct GridArgs {
     int64_t nf_pad;
     int64_t n_mt, n_nb, n_items;
     const int4* rec;       // [slab realisations][nf_pad] {Fx|fx, Fy|fy, F a, F b}
+    float* master;         // [gridDim.x][kXN][kXM] FP32 accumulators of the CTAs' current items
     const float* d_bound;
     float fbound;
     int* err;
@@ -237,9 +241,9 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
     unsigned char* rring = smem + kXStages * kXStageBytes;
     uint64_t* full = reinterpret_cast<uint64_t*>(rring + kXRecSlots * kXRecBytes);
     uint64_t* empty = full + kXStages;
-    uint64_t* seg_full = empty + kXStages;
-    uint64_t* seg_free = seg_full + 1;
-    uint64_t* fullR = seg_free + 1;
+    uint64_t* seg_full = empty + kXStages;  // [2], one per TMEM segment slot
+    uint64_t* seg_free = seg_full + 2;      // [2]
+    uint64_t* fullR = seg_free + 2;
     uint64_t* freeR = fullR + kXRecSlots;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeR + kXRecSlots);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -254,8 +258,10 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
             sm100::mbar_init(&full[s], kXProducers);
             sm100::mbar_init(&empty[s], 1);
         }
-        sm100::mbar_init(seg_full, 1);
-        sm100::mbar_init(seg_free, kXPromoters);
+        for (int b = 0; b < 2; ++b) {
+            sm100::mbar_init(&seg_full[b], 1);
+            sm100::mbar_init(&seg_free[b], kXPromoters);
+        }
         for (int s = 0; s < kXRecSlots; ++s) {
             sm100::mbar_init(&fullR[s], 1);
             sm100::mbar_init(&freeR[s], kXProducers);
@@ -267,8 +273,7 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
     sm100::tc_fence_before();
     __syncthreads();
     sm100::tc_fence_after();
-    const uint32_t tmem_master = *tmem_slot;
-    const uint32_t tmem_seg = tmem_master + (uint32_t)kXN;
+    const uint32_t tmem_base = *tmem_slot;  // slot b: columns [256 b, 256 b + 256)
 
     auto stageA_hi = [&](int s) { return smem + s * kXStageBytes; };
     auto stageA_lo = [&](int s) { return smem + s * kXStageBytes + kXTileA; };
@@ -290,13 +295,15 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
             for (int64_t it = blockIdx.x; it < g.n_items && !stop; it += gridDim.x) {
                 int64_t i = 0;
                 for (int64_t j = 0; j < n_seg; ++j, ++J) {
-                    if (*abort_flag || (J >= 1 && !sm100::mbar_wait(seg_free, (uint32_t)((J - 1) & 1), abort_flag,
-                                                                     kXWaitCycles))) {
+                    const int b = (int)(J & 1);
+                    if (*abort_flag || (J >= 2 && !sm100::mbar_wait(&seg_free[b], (uint32_t)(((J - 2) >> 1) & 1),
+                                                                     abort_flag, kXWaitCycles))) {
                         if (!*abort_flag) timeout();
                         stop = true;
                         break;
                     }
                     const int64_t i_end = ((j + 1) * Cfg::kSeg < n_chunks) ? (j + 1) * Cfg::kSeg : n_chunks;
+                    const uint32_t tmem_seg = tmem_base + (uint32_t)(b * kXN);
                     bool first = true;
                     for (; i < i_end; ++i, ++gc) {
                         const int s = (int)(gc % kXStages);
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                         }
                         sm100::mma_commit(&empty[s]);
                     }
-                    sm100::mma_commit(seg_full);
+                    sm100::mma_commit(&seg_full[b]);
                     mma_segments = J + 1;
                     if (stop) break;
                 }
@@ -360,6 +367,7 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         const uint32_t col0 = (uint32_t)(((warp - 4) >> 2) * kSpan);
+        float* mrow = g.master + (int64_t)blockIdx.x * kXN * kXM + row;  // this thread's master column
         int64_t J = 0;
         bool stop = false;
         for (int64_t it = blockIdx.x; it < g.n_items && !stop; it += gridDim.x) {
@@ -368,26 +376,33 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
             const int64_t xi = mt * kXM + row;
             const int64_t orow = g.r0 + r;
             for (int64_t j = 0; j < n_seg; ++j, ++J) {
-                if (!sm100::mbar_wait(seg_full, (uint32_t)(J & 1), abort_flag, kXWaitCycles)) {
+                const int b = (int)(J & 1);
+                if (!sm100::mbar_wait(&seg_full[b], (uint32_t)((J >> 1) & 1), abort_flag, kXWaitCycles)) {
                     if (!*abort_flag) timeout();
                     stop = true;
                     break;
                 }
                 sm100::tc_fence_after();
+                const uint32_t slot = tmem_base + (uint32_t)(b * kXN) + lane_off + col0;
                 const bool last = (j == n_seg - 1);
 #pragma unroll 1
                 for (int c0 = 0; c0 < kSpan; c0 += 32) {
-                    uint32_t v[32], w[32];
-                    sm100::tmem_ld_32x32b_x32(tmem_seg + lane_off + col0 + (uint32_t)c0, v);
-                    if (j > 0) sm100::tmem_ld_32x32b_x32(tmem_master + lane_off + col0 + (uint32_t)c0, w);
+                    float* mp = mrow + (int64_t)(col0 + c0) * kXM;
+                    float m[32];
+                    uint32_t v[32];
+                    if (j > 0) {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) m[q] = mp[q * kXM];
+                    }
+                    sm100::tmem_ld_32x32b_x32(slot + (uint32_t)c0, v);
                     sm100::tmem_ld_wait();
                     if (j > 0) {
 #pragma unroll
-                        for (int q = 0; q < 32; ++q)
-                            v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
+                        for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + m[q]);
                     }
                     if (!last) {
-                        sm100::tmem_st_32x32b_x32(tmem_master + lane_off + col0 + (uint32_t)c0, v);
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) mp[q * kXM] = __uint_as_float(v[q]);
                     } else if (xi < g.nx) {
 #pragma unroll
                         for (int q = 0; q < 32; ++q) {
@@ -404,10 +419,9 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                         }
                     }
                 }
-                sm100::tmem_st_wait();
                 sm100::tc_fence_before();
                 __syncwarp();
-                if (lane == 0) sm100::mbar_arrive(seg_free);
+                if (lane == 0) sm100::mbar_arrive(&seg_free[b]);
             }
         }
     } else if (warp >= 4 + kXPromoters) {
@@ -457,11 +471,13 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
     sm100::tc_fence_before();
     __syncthreads();
     if (warp == 1) {
-        if (*abort_flag && lane == 0 && mma_segments > 0)
-            sm100::mbar_wait_for(seg_full, (uint32_t)((mma_segments - 1) & 1), kXWaitCycles / 8);
+        if (*abort_flag && lane == 0 && mma_segments > 0) {  // MMAs in flight finish before TMEM is freed
+            const int64_t Jl = mma_segments - 1;
+            sm100::mbar_wait_for(&seg_full[Jl & 1], (uint32_t)((Jl >> 1) & 1), kXWaitCycles / 8);
+        }
         __syncwarp();
         sm100::tc_fence_after();
-        sm100::tmem_dealloc(tmem_master, 512);
+        sm100::tmem_dealloc(tmem_base, 512);
     }
 }
 
@@ -479,11 +495,16 @@ static int64_t grid_slab(int64_t nf_pad, int64_t n_real)
     return s < n_real ? s : n_real;
 }
 
-size_t grid_workspace_bytes(int mode, int64_t n_f, int64_t n_real)
+static size_t grid_record_bytes(int64_t nf_pad, int64_t n_real)
+{
+    return ((size_t)grid_slab(nf_pad, n_real) * (size_t)nf_pad * sizeof(int4) + 255) / 256 * 256;
+}
+
+size_t grid_workspace_bytes(int mode, int64_t n_f, int64_t n_real, int num_sms)
 {
     const int64_t T = grid_terms_per_chunk(mode);
     const int64_t nf_pad = (n_f + T - 1) / T * T;
-    return 256 + (size_t)grid_slab(nf_pad, n_real) * (size_t)nf_pad * sizeof(int4);
+    return 256 + grid_record_bytes(nf_pad, n_real) + (size_t)num_sms * kXN * kXM * sizeof(float);
 }
 
 int64_t grid_launch_count(int mode, int64_t n_f, int64_t n_real)
@@ -504,6 +525,7 @@ static cudaError_t launch_grid_t(qrs_handle* h, const DrawParams& p, const float
     const int64_t nf_pad = (p.n_f + T - 1) / T * T;
     const int64_t slab = grid_slab(nf_pad, n_real);
     int4* rec = reinterpret_cast<int4*>(((uintptr_t)h->d_work + 255) & ~(uintptr_t)255);
+    float* master = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(rec) + grid_record_bytes(nf_pad, n_real));
 
     k_grid_bound<<<1, 1024, 0, s>>>(x, nx, y, ny, h->d_xbound);
     cudaError_t e = cudaGetLastError();
@@ -523,6 +545,7 @@ static cudaError_t launch_grid_t(qrs_handle* h, const DrawParams& p, const float
     a.n_mt = (nx + kXM - 1) / kXM;
     a.n_nb = (ny + kXN - 1) / kXN;
     a.rec = rec;
+    a.master = master;
     a.d_bound = h->d_xbound;
     a.fbound = (float)freq_bound(p);
     a.err = h->d_err;

@@ -276,7 +276,7 @@ qrs_status qrs_synthesize_grid(qrs_handle* h, const qrs_psd* psd, const qrs_doma
         return fail(h, QRS_ERR_ARG, "x, y, index and out must be 4-byte aligned");
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
-    st = ensure_work(h, grid_workspace_bytes(mode, n_f, n_real));
+    st = ensure_work(h, grid_workspace_bytes(mode, n_f, n_real, h->num_sms));
     if (st != QRS_OK) return st;
     e = launch_synth_grid(h, mode, p, x, nx, y, ny, index, index ? n_points : nx * ny, n_real, out,
                           (cudaStream_t)stream);

@@ -59,7 +59,7 @@ size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real);
 cudaError_t launch_synth_gemm(qrs_handle* h, int mode, const DrawParams& p, const float* xy, int64_t P,
                               int64_t n_real, const double* col_psd, double c_vk, float* out, cudaStream_t s);
 
-size_t grid_workspace_bytes(int mode, int64_t n_f, int64_t n_real);
+size_t grid_workspace_bytes(int mode, int64_t n_f, int64_t n_real, int num_sms);
 int64_t grid_launch_count(int mode, int64_t n_f, int64_t n_real);
 cudaError_t launch_synth_grid(qrs_handle* h, int mode, const DrawParams& p, const float* x, int64_t nx,
                               const float* y, int64_t ny, const int32_t* index, int64_t P, int64_t n_real, float* out,
