@@ -42,6 +42,9 @@ SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq-term evals/s"
 UNIT = "term/s"
+# DRAM bytes (read + write) per k_synth_fused launch on the workload above, from the ncu launch
+# list summarised in profiles/k_synth_fused_phase_screen.md (6.26 MB read + 147.29 MB write).
+SYNTH_TRAFFIC_BYTES = 153.55e6
 
 
 def _args():
@@ -493,7 +496,10 @@ def run_ours(a):
         "data": "synthetic", "config": _config(cfg, xy_np, world),
         "realizations_per_s": R * a.steps * world / t_tot,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_terms / 1e9, "unit": "Gterm/s",
-                     "frac": achieved / peak_terms, "traffic": None,
+                     "frac": achieved / peak_terms, "traffic": SYNTH_TRAFFIC_BYTES,
+                     "traffic_source": "profiles/k_synth_fused_phase_screen.md (ncu dram__bytes_read.sum + "
+                                       "dram__bytes_write.sum per launch of this kernel on this workload)",
+                     "algorithmic_bytes": int(xy_np.nbytes + R * P * 4),
                      "kernel": "k_synth_fused (+ k_point_bound prepass, <0.01%)",
                      "peak_basis": "152 SM x 16 sin|cos per SM-clock (measured) / 2 per term x %.0f MHz max clock"
                                    % sm_max},
