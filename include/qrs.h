@@ -101,11 +101,22 @@ typedef enum {
 #define QRS_COEF_GAUSS 0
 #define QRS_COEF_EQ3 1
 
+/* Aperture filter (Eq. 7): with ap_D_m > 0 the PSD is W(f) A(|f|)^2, the
+ * piston PSD of a circular aperture of diameter ap_D_m with a central
+ * obstruction of diameter ap_d_m, A(f) = 2 (D J1(pi D f) - d J1(pi d f)) /
+ * (pi (D^2 - d^2) f), A(0) = 1; every term's amplitude carries the signed A,
+ * so the Eq. 3 sum at a point is the piston of such an aperture centred there
+ * (Sec. 4.1: pistons simulated at arbitrary positions, e.g. a telescope's
+ * track through a frozen-flow layer).  ap_D_m = 0: no filter (ap_d_m = 0).
+ * 0 <= ap_d_m < ap_D_m.  qrs_diff_piston jobs and qrs_proposal_targets filter
+ * per aperture themselves and take ap_D_m = 0. */
 typedef struct qrs_psd {
     double r0_m;   /* Fried parameter at the simulated wavelength, m (> 0) */
     double L0_m;   /* outer scale, m (> 0; ignored for KOLMOGOROV) */
     int32_t kind;  /* QRS_PSD_* */
     int32_t reserved;
+    double ap_D_m; /* aperture filter diameter, m (0: none) */
+    double ap_d_m; /* its central obstruction diameter, m */
 } qrs_psd;
 
 typedef struct qrs_domain {
@@ -261,6 +272,32 @@ typedef struct qrs_piston_job {
 
 qrs_status qrs_diff_piston(qrs_handle* h, const qrs_piston_job* jobs, int32_t n_jobs, int32_t flags,
                            void* stream);
+
+/* ------------------------------------------------------ pair differences ---
+ * Differential pistons of synthesised values (Sec. 4.4):
+ *   out[r][q] = values[r][pairs[q][0]] - values[r][pairs[q][1]]
+ *   values [n_real][n_points] FP32 (e.g. the output of qrs_synthesize_points
+ *   with an aperture-filtered PSD), pairs [n_pairs][2] int32, out
+ *   [n_real][n_pairs] FP32.  A pair index outside [0, n_points) gives NaN and
+ *   records QRS_ERR_DEVICE_CHECK in the device error word (no out-of-bounds
+ *   read). */
+qrs_status qrs_pair_diff(qrs_handle* h, const float* values, int64_t n_real, int64_t n_points,
+                         const int32_t* pairs, int64_t n_pairs, float* out, void* stream);
+
+/* ------------------------------------------------------ hyper-parameters ---
+ * Sec. 4.2 choice of N for a square domain with cell delta_f: with the
+ * isotropic PSD W (von Karman; times A^2 when psd->ap_D_m > 0),
+ *   g(x) = int_0^x f W(f) df
+ * saturates at g_inf = sigma^2 / (2 pi); the criterion stops at the first
+ * m past the largest panel increment (where g saturates) with
+ * g(m delta_f) - g((m-1) delta_f) < eps_rel g_inf, and N = 2 m
+ * (2 max f = N delta_f, Eq. 5).  Host computation (composite Simpson
+ * per delta_f panel), no handle and no GPU.  g_out (may be NULL) receives
+ * {g(m delta_f), g_inf, the stopping increment}.  Errors: QRS_ERR_ARG for a
+ * non-positive delta_f or eps_rel, a KOLMOGOROV PSD (g diverges at f = 0), or
+ * no m <= n_max / 2 meeting the criterion. */
+qrs_status qrs_choose_n(const qrs_psd* psd, double delta_f, double eps_rel, int32_t n_max, int32_t* n_out,
+                        double* g_out);
 
 /* --------------------------------------------------- structure function ---
  * Sec. 4.4: for series s and lag L = lags[l],

@@ -61,7 +61,7 @@ def lib():
                                             C.POINTER(C.c_double)]
             L.oracle_domain_jacobian.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
             L.oracle_domain_jacobian.restype = C.c_double
-            P = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double,
+            P = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double,
                  C.c_int, C.c_uint64, C.c_int, C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.c_int,
                  C.c_void_p]
             L.oracle_draw.argtypes = P + [C.c_int64, C.c_int64, C.c_int64] + [C.c_void_p] * 7
@@ -84,10 +84,11 @@ def lib():
 
 
 def params(psd="von_karman", r0=0.15, L0=30.0, domain="logpolar", fmin=1e-3, fmax=16.0,
-           sampler="r2", seed=0, s0=None, coef="gauss", n_rho=64, n_theta=32, cdf=None):
-    """Plain dictionary of method parameters (shared vocabulary, no arithmetic)."""
+           sampler="r2", seed=0, s0=None, coef="gauss", n_rho=64, n_theta=32, cdf=None, ap_D=0.0, ap_d=0.0):
+    """Plain dictionary of method parameters (shared vocabulary, no arithmetic).
+    ap_D > 0 filters the PSD by the Eq. 7 aperture factor (the piston PSD)."""
     return dict(psd=psd, r0=r0, L0=L0, domain=domain, fmin=fmin, fmax=fmax, sampler=sampler,
-                seed=seed, s0=s0, coef=coef, n_rho=n_rho, n_theta=n_theta, cdf=cdf)
+                seed=seed, s0=s0, coef=coef, n_rho=n_rho, n_theta=n_theta, cdf=cdf, ap_D=ap_D, ap_d=ap_d)
 
 
 def _ptr(a):
@@ -101,7 +102,8 @@ def _pargs(p):
     s0 = p.get("s0")
     use_fixed = 0 if s0 is None else 1
     s0x, s0y = (0, 0) if s0 is None else (int(s0[0]), int(s0[1]))
-    args = [PSD[p["psd"]], float(p["r0"]), float(p["L0"]), DOMAIN[p["domain"]], float(p["fmin"]),
+    args = [PSD[p["psd"]], float(p["r0"]), float(p["L0"]), float(p.get("ap_D", 0.0) or 0.0),
+            float(p.get("ap_d", 0.0) or 0.0), DOMAIN[p["domain"]], float(p["fmin"]),
             float(p["fmax"]), SAMPLER[p["sampler"]], int(p["seed"]) & (2**64 - 1), use_fixed, s0x, s0y,
             COEF[p["coef"]], int(p["n_rho"]), int(p["n_theta"]), _ptr(cdf)]
     return args, cdf  # keep cdf alive

@@ -136,3 +136,64 @@ def temporal_piston_sf(tau, B, v, r0, L0, D, d, fmin, fmax, wind_angle=0.0, kind
         lambda f: 8 * PI * f * psd(f, r0, L0, kind) * airy(f, D, d) ** 2
         * (1 - sp.j0(2 * PI * f * B) - sp.j0(2 * PI * f * vt)
            + 0.5 * sp.j0(2 * PI * f * bp) + 0.5 * sp.j0(2 * PI * f * bm)), fmin, fmax, osc_len=osc)
+
+
+def choose_n(r0, L0, D, d, delta_f, eps_rel, n_max=10000):
+    """Sec. 4.2 choice of N: g(x) = int_0^x f W(f) A(f)^2 df (A = 1 when D = 0)
+    saturates at g_inf; N = 2 m for the first m past the largest panel
+    increment with g(m df) - g((m-1) df) < eps_rel g_inf.  Panels by adaptive
+    quadrature (scipy.integrate.quad); g_inf from the full radial integral.
+    Returns (N, g(m df), g_inf)."""
+    from scipy import integrate
+
+    def g(f):
+        a = airy(f, D, d) if D > 0 else 1.0
+        return f * psd(f, r0, L0) * a * a
+
+    g_inf = radial_integral(g, 1e-12, 1e6) if D > 0 else radial_integral(g, 1e-12, 1e9)
+    gm, peak = 0.0, 0.0
+    for m in range(1, n_max // 2 + 1):
+        inc = integrate.quad(g, (m - 1) * delta_f, m * delta_f, epsabs=0.0, epsrel=1e-12, limit=200)[0]
+        gm += inc
+        if inc < eps_rel * g_inf and inc < peak:
+            return 2 * m, gm, g_inf
+        peak = max(peak, inc)
+    raise ValueError("criterion not met below n_max")
+
+
+def square_temporal_piston_sf(taus, B, v, r0, L0, D, d, fmax, wind_angle=0.0, panel_nodes=8):
+    """Frozen-flow temporal structure function of the differential piston of two
+    equal apertures B = (|B|, 0) apart, wind speed v at wind_angle to B, for
+    the SQUARE domain [-fmax, fmax)^2 (Eq. 5): with s = v tau (cos, sin)(angle),
+      D(tau) = int W A^2 [4 - 4 cos 2 pi f.B - 4 cos 2 pi f.s
+                          + 2 cos 2 pi f.(B + s) + 2 cos 2 pi f.(B - s)] d^2 f,
+    the variance of Delta(t + tau) - Delta(t) for the covariance
+    C(r) = int W A^2 cos 2 pi f.r of the piston field.  Tensor Gauss-Legendre
+    on panels narrower than 1/8 of the shortest period of the cosines (one
+    node grid for all lags).  Returns an array over taus."""
+    taus = np.atleast_1d(np.asarray(taus, dtype=np.float64))
+    Bv = np.array([B, 0.0])
+    wdir = np.array([np.cos(wind_angle), np.sin(wind_angle)])
+    Lmax = max([1.0 / fmax, abs(B)] + [np.linalg.norm(Bv + sg * wdir * v * t) for t in taus for sg in (-1, 1)])
+    n_pan = int(np.ceil(2 * fmax * 8 * Lmax))
+    x, w = np.polynomial.legendre.leggauss(panel_nodes)
+    edges = np.linspace(-fmax, fmax, n_pan + 1)
+    h = edges[1] - edges[0]
+    nodes = (edges[:-1, None] + 0.5 * h * (x[None, :] + 1.0)).ravel()
+    wts = np.tile(0.5 * h * w, n_pan)
+    out = np.zeros(taus.size)
+    for i0 in range(0, nodes.size, 256):  # blocks of rows
+        fx = nodes[i0:i0 + 256, None]
+        fy = nodes[None, :]
+        fr = np.hypot(fx, fy)
+        a = airy(fr.ravel(), D, d).reshape(fr.shape) if D > 0 else 1.0
+        K = wts[i0:i0 + 256, None] * wts[None, :] * psd(fr, r0, L0) * a * a
+        c0 = np.sum(K)
+        cB = np.sum(K * np.cos(2 * PI * fx * B))
+        for j, t in enumerate(taus):
+            sx, sy = wdir * v * t
+            cs = np.sum(K * np.cos(2 * PI * (fx * sx + fy * sy)))
+            cp = np.sum(K * np.cos(2 * PI * (fx * (B + sx) + fy * sy)))
+            cm = np.sum(K * np.cos(2 * PI * (fx * (B - sx) - fy * sy)))
+            out[j] += 4 * c0 - 4 * cB - 4 * cs + 2 * cp + 2 * cm
+    return out

@@ -193,6 +193,7 @@ enum { OR_COEF_GAUSS = 0, OR_COEF_EQ3 = 1 };
 
 typedef struct {
     int psd_kind; double r0, L0;
+    double ap_D, ap_d;  /* Eq. 7 aperture filter of the PSD (piston PSD); ap_D = 0: none */
     int dom_kind; double fmin, fmax;
     int smp_kind; uint64_t seed; int use_fixed_s0; uint64_t s0x, s0y;
     int coef_kind; int n_rho, n_theta;
@@ -284,6 +285,10 @@ static void or_draw_term(const or_params* p, const uint64_t s0[2], int64_t n_f, 
         J = 2.0 * OR_PI * log(p->fmax / p->fmin) * (fx * fx + fy * fy) / ((double)p->n_rho * (double)p->n_theta * p_cell);
     double W = oracle_psd(p->psd_kind, p->r0, p->L0, fx * fx + fy * fy);
     *F = sqrt(W * J / (double)n_f);
+    /* Eq. 7: the piston PSD is W times the squared aperture filter; the
+     * amplitude carries the signed filter, so that the sum at a point is the
+     * piston of an aperture centred there (Sec. 4.1) */
+    if (p->ap_D > 0.0) *F *= oracle_airy(sqrt(fx * fx + fy * fy), p->ap_D, p->ap_d);
     *Jo = J;
     double a, b;
     or_box_muller(w[2], w[3], &a, &b);
@@ -300,22 +305,25 @@ static void or_draw_term(const or_params* p, const uint64_t s0[2], int64_t n_f, 
     if (S_out) { S_out[0] = S[0]; S_out[1] = S[1]; }
 }
 
-static or_params or_pack(int psd_kind, double r0, double L0, int dom_kind, double fmin, double fmax,
+static or_params or_pack(int psd_kind, double r0, double L0, double ap_D, double ap_d, int dom_kind,
+                         double fmin, double fmax,
                          int smp_kind, uint64_t seed, int use_fixed_s0, uint64_t s0x, uint64_t s0y,
                          int coef_kind, int n_rho, int n_theta, const uint32_t* cdf)
 {
     or_params p;
-    p.psd_kind = psd_kind; p.r0 = r0; p.L0 = L0;
+    p.psd_kind = psd_kind; p.r0 = r0; p.L0 = L0; p.ap_D = ap_D; p.ap_d = ap_d;
     p.dom_kind = dom_kind; p.fmin = fmin; p.fmax = fmax;
     p.smp_kind = smp_kind; p.seed = seed; p.use_fixed_s0 = use_fixed_s0; p.s0x = s0x; p.s0y = s0y;
     p.coef_kind = coef_kind; p.n_rho = n_rho; p.n_theta = n_theta; p.cdf = cdf;
     return p;
 }
 
-#define OR_PARAMS_DECL int psd_kind, double r0, double L0, int dom_kind, double fmin, double fmax, \
+#define OR_PARAMS_DECL int psd_kind, double r0, double L0, double psd_apD, double psd_apd, int dom_kind, \
+    double fmin, double fmax, \
     int smp_kind, uint64_t seed, int use_fixed_s0, uint64_t s0x, uint64_t s0y, int coef_kind, \
     int n_rho, int n_theta, const uint32_t* cdf
-#define OR_PARAMS_PASS psd_kind, r0, L0, dom_kind, fmin, fmax, smp_kind, seed, use_fixed_s0, s0x, s0y, \
+#define OR_PARAMS_PASS psd_kind, r0, L0, psd_apD, psd_apd, dom_kind, fmin, fmax, smp_kind, seed, use_fixed_s0, s0x, \
+    s0y, \
     coef_kind, n_rho, n_theta, cdf
 
 /* The draw of n_real realisations of n_f terms.  Any output may be NULL.
@@ -407,6 +415,7 @@ int oracle_synthesize_shared(OR_PARAMS_DECL, int64_t n_f, int64_t n_real, int64_
             double fx = (double)f[2 * k], fy = (double)f[2 * k + 1];
             double W = oracle_psd(psd_kind, cr0, cL0, fx * fx + fy * fy);
             Fr[k] = sqrt(W * J[k] / (double)n_f);
+            if (psd_apD > 0.0) Fr[k] *= oracle_airy(sqrt(fx * fx + fy * fy), psd_apD, psd_apd);
         }
         oracle_synth_terms(f, Fr, cr, n_f, xy, n_points, out + r * n_points);
     }
@@ -424,6 +433,7 @@ int oracle_diff_piston(OR_PARAMS_DECL, int64_t n_f, int64_t n_real, int64_t real
                        const float* ap_xy, const float* ap_D, const float* ap_d, int n_ap,
                        const int32_t* pairs, int n_pairs, double* piston, double* out)
 {
+    if (psd_apD > 0.0) return -2;  /* the apertures filter here: a filtered PSD would filter twice */
     float* f = (float*)malloc(sizeof(float) * 2 * n_f);
     double* F = (double*)malloc(sizeof(double) * n_f);
     double* c = (double*)malloc(sizeof(double) * 2 * n_f);

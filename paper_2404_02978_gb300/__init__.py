@@ -21,7 +21,7 @@ import threading
 import torch
 
 __all__ = ["params", "Handle", "qrs_create", "qrs_draw", "qrs_synthesize_points", "qrs_synthesize_grid", "qrs_diff_piston",
-           "qrs_structure_fn", "qrs_sync", "QrsError", "lib_path", "load"]
+           "qrs_pair_diff", "qrs_choose_n", "qrs_structure_fn", "qrs_sync", "QrsError", "lib_path", "load"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libqrs.so")
@@ -44,7 +44,8 @@ class QrsError(RuntimeError):
 
 # ------------------------------------------------------------------ C structs
 class QrsPsd(C.Structure):
-    _fields_ = [("r0_m", C.c_double), ("L0_m", C.c_double), ("kind", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("r0_m", C.c_double), ("L0_m", C.c_double), ("kind", C.c_int32), ("reserved", C.c_int32),
+                ("ap_D_m", C.c_double), ("ap_d_m", C.c_double)]
 
 
 class QrsDomain(C.Structure):
@@ -111,14 +112,16 @@ def load():
 
 # ----------------------------------------------------------------- parameters
 def params(psd="von_karman", r0=0.15, L0=30.0, domain="logpolar", fmin=1e-3, fmax=16.0, sampler="r2", seed=0,
-           s0=None, coef="gauss", n_rho=64, n_theta=32, cdf=None):
-    """Method parameters as a plain dictionary (cdf: device uint32 tensor or None)."""
+           s0=None, coef="gauss", n_rho=64, n_theta=32, cdf=None, ap_D=0.0, ap_d=0.0):
+    """Method parameters as a plain dictionary (cdf: device uint32 tensor or None;
+    ap_D > 0: the PSD filtered by the Eq. 7 aperture factor, see include/qrs.h)."""
     return dict(psd=psd, r0=r0, L0=L0, domain=domain, fmin=fmin, fmax=fmax, sampler=sampler, seed=seed, s0=s0,
-                coef=coef, n_rho=n_rho, n_theta=n_theta, cdf=cdf)
+                coef=coef, n_rho=n_rho, n_theta=n_theta, cdf=cdf, ap_D=ap_D, ap_d=ap_d)
 
 
 def _structs(p):
-    psd = QrsPsd(float(p["r0"]), float(p.get("L0", 0.0) or 0.0), PSD[p["psd"]], 0)
+    psd = QrsPsd(float(p["r0"]), float(p.get("L0", 0.0) or 0.0), PSD[p["psd"]], 0, float(p.get("ap_D", 0.0) or 0.0),
+                 float(p.get("ap_d", 0.0) or 0.0))
     dom = QrsDomain(float(p.get("fmin", 0.0) or 0.0), float(p["fmax"]), DOMAIN[p["domain"]], 0)
     s0 = p.get("s0")
     cdf = p.get("cdf")
@@ -263,6 +266,44 @@ def qrs_synthesize_grid(h: Handle, p, n_f, n_real, x, y, index=None, n_points=No
     h._check(f(h.h, C.byref(psd), C.byref(dom), C.byref(smp), int(n_f), int(n_real), int(real_offset), x.data_ptr(),
                int(nx), y.data_ptr(), int(ny), ip, int(n_points), MODE[mode], out.data_ptr(), _stream(stream)))
     return out
+
+
+def qrs_pair_diff(h: Handle, values, pairs, out=None, stream=None):
+    """Pair differences out[r][q] = values[r][pairs[q][0]] - values[r][pairs[q][1]]
+    (values [n_real, n_points] float32, pairs [n_pairs, 2] int32, device)."""
+    _check_dev(values, torch.float32, "values")
+    _check_dev(pairs, torch.int32, "pairs")
+    n_real, n_points = values.shape
+    n_pairs = pairs.shape[0]
+    if out is None:
+        out = torch.empty(n_real, n_pairs, dtype=torch.float32, device=values.device)
+    _check_dev(out, torch.float32, "out")
+    if out.numel() != n_real * n_pairs:
+        raise ValueError("out must hold n_real * n_pairs values")
+    f = h.L.qrs_pair_diff
+    if f.argtypes is None:
+        f.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+        f.restype = C.c_int
+    h._check(f(h.h, values.data_ptr(), int(n_real), int(n_points), pairs.data_ptr(), int(n_pairs), out.data_ptr(),
+               _stream(stream)))
+    return out
+
+
+def qrs_choose_n(p, delta_f, eps_rel, n_max=10000):
+    """Sec. 4.2 choice of N (host computation in libqrs): returns
+    (N, g(N delta_f / 2), g_inf, stopping increment) for the PSD of p (von
+    Karman, optionally aperture-filtered by p["ap_D"], p["ap_d"])."""
+    f = load().qrs_choose_n
+    if f.argtypes is None:
+        f.argtypes = [C.POINTER(QrsPsd), C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_int32),
+                      C.POINTER(C.c_double)]
+        f.restype = C.c_int
+    psd, _, _ = _structs(p)
+    n, g = C.c_int32(), (C.c_double * 3)()
+    st = f(C.byref(psd), float(delta_f), float(eps_rel), int(n_max), C.byref(n), g)
+    if st != 0:
+        raise QrsError(st, "qrs_choose_n: invalid PSD or arguments, or the criterion is not met below n_max")
+    return n.value, g[0], g[1], g[2]
 
 
 def piston_job(p, n_f, n_real, ap_xy, ap_D, ap_d=None, pairs=None, piston=None, delta=None, real_offset=0):

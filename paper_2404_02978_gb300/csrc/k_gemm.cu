@@ -84,9 +84,9 @@ struct GemmArgs {
 
 // ------------------------------------------------------------- prep kernels
 // The shared draw: frequencies of realisation real_offset in the basis
-// representation, and (|f|^2, J) for the weights.
+// representation, and (|f|^2, J, A) for the weights (A: the aperture filter, 1 if none).
 __global__ void k_gemm_freq(DrawParams p, int64_t nf_pad, const float* __restrict__ d_xbound, float fbound,
-                            int2* __restrict__ fbasis, float2* __restrict__ fw)
+                            int2* __restrict__ fbasis, float4* __restrict__ fw)
 {
     const FixedScales z = fixed_scales(fbound, *d_xbound, true);
     const uint64_t n0 = (uint64_t)p.real_offset * (uint64_t)p.n_f;
@@ -97,10 +97,10 @@ __global__ void k_gemm_freq(DrawParams p, int64_t nf_pad, const float* __restric
                 fbasis[k] = make_int2(__float2int_rn(t.fx * z.fscale), __float2int_rn(t.fy * z.fscale));
             else
                 fbasis[k] = make_int2(__float_as_int(t.fx), __float_as_int(t.fy));
-            fw[k] = make_float2(t.fx * t.fx + t.fy * t.fy, t.J);
+            fw[k] = make_float4(t.fx * t.fx + t.fy * t.fy, t.J, t.A, 0.0f);
         } else {
             fbasis[k] = make_int2(0, 0);
-            fw[k] = make_float2(0.0f, 0.0f);
+            fw[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
     }
 }
@@ -130,7 +130,7 @@ __device__ __forceinline__ void split_store(void* hi_base, void* lo_base, int64_
 // (r0, L0) = col_psd[r] when given.  Rows r >= n_real and terms k >= N_f are 0.
 template <int PREC>
 __global__ void k_gemm_coef(DrawParams p, int64_t nf_pad, int64_t n_real, int64_t R_pad,
-                            const float2* __restrict__ fw, const double* __restrict__ col_psd, double c_vk,
+                            const float4* __restrict__ fw, const double* __restrict__ col_psd, double c_vk,
                             void* __restrict__ B)
 {
     constexpr int T = GemmCfg<PREC>::kTermsPerChunk;
@@ -154,8 +154,8 @@ __global__ void k_gemm_coef(DrawParams p, int64_t nf_pad, int64_t n_real, int64_
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nf_pad; k += (int64_t)gridDim.x * blockDim.x) {
         float cc = 0.0f, cs = 0.0f;
         if (r < n_real && k < p.n_f) {
-            const float2 w = fw[k];
-            const float F = sqrtf(psd_w(pc, pa, w.x) * w.y * p.inv_nf);
+            const float4 w = fw[k];
+            const float F = sqrtf(psd_w(pc, pa, w.x) * w.y * p.inv_nf) * w.z;  // w.z: aperture filter
             const float2 ab = draw_coef(p, (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k);
             cc = F * ab.x;
             cs = -(F * ab.y);
@@ -438,7 +438,7 @@ size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real)
     const int64_t nf_pad = (n_f + T - 1) / T * T;
     const int64_t R_pad = (n_real + kGN - 1) / kGN * kGN;
     const size_t b = (size_t)2 * R_pad * (2 * nf_pad) * eb;  // hi and lo halves
-    return 256 + b + (size_t)nf_pad * (sizeof(int2) + sizeof(float2)) + 1024;
+    return 256 + b + (size_t)nf_pad * (sizeof(int2) + sizeof(float4)) + 1024;
 }
 
 template <int PREC>
@@ -455,7 +455,7 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     void* B = base;
     const size_t bbytes = (size_t)2 * R_pad * Kp * Cfg::kElemBytes;
     int2* fbasis = reinterpret_cast<int2*>(base + bbytes);
-    float2* fw = reinterpret_cast<float2*>(fbasis + nf_pad);
+    float4* fw = reinterpret_cast<float4*>(fbasis + nf_pad);
 
     cudaError_t e = launch_point_bound(xy, P, h->d_xbound, s);
     if (e != cudaSuccess) return e;

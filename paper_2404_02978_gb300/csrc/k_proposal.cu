@@ -385,6 +385,8 @@ qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_dom
     smp.n_rho = n_rho;
     smp.n_theta = n_theta;
     DrawParams p;
+    if (psd && psd->ap_D_m > 0.0)
+        return fail(h, QRS_ERR_ARG, "targets apply each geometry's aperture filter: the PSD's filter must be off");
     qrs_status st = make_draw_params(h, psd, dom, &smp, n_f, 0, &p);
     if (st != QRS_OK) return st;
     if (n == 0) return QRS_OK;

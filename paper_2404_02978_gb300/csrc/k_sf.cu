@@ -1,4 +1,5 @@
-// k_sf.cu -- K5: FP64 structure-function sums (Sec. 4.4).
+// k_sf.cu -- K5: FP64 structure-function sums (Sec. 4.4), and the pair
+// differences of synthesised values they are usually taken of.
 // For every (series s, lag L): x = v[t+L] - v[t] (L >= 1) or x = v[t] (L = 0),
 // summed over realisations and t as (sum x^2, sum x^4, count) in FP64.
 // Grid: y = series-lag pair, x = slices of the flat (realisation, t) range.
@@ -66,6 +67,41 @@ __global__ void __launch_bounds__(256) k_structure_fn(const float* __restrict__ 
             }
         }
     }
+}
+
+// out[r][q] = v[r][i_q] - v[r][j_q] (differential pistons, Sec. 4.4).  An
+// index outside [0, n_points) gives NaN and records QRS_ERR_DEVICE_CHECK
+// instead of reading out of bounds.
+__global__ void k_pair_diff(const float* __restrict__ v, int64_t n_real, int64_t n_points,
+                            const int2* __restrict__ pairs, int64_t n_pairs, float* __restrict__ out,
+                            int* __restrict__ err)
+{
+    const int64_t total = n_real * n_pairs;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / n_pairs, q = i - r * n_pairs;
+        const int2 pq = pairs[q];
+        float d;
+        if (pq.x < 0 || pq.x >= n_points || pq.y < 0 || pq.y >= n_points) {
+            d = __int_as_float(0x7FC00000);
+            atomicExch(err, (int)QRS_ERR_DEVICE_CHECK);
+        } else {
+            const float* row = v + r * n_points;
+            d = row[pq.x] - row[pq.y];
+        }
+        out[i] = d;
+    }
+}
+
+cudaError_t launch_pair_diff(const float* v, int64_t n_real, int64_t n_points, const int32_t* pairs, int64_t n_pairs,
+                             float* out, int num_sms, int* err, cudaStream_t s)
+{
+    const int64_t total = n_real * n_pairs;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
+    if (blocks < 1) blocks = 1;
+    k_pair_diff<<<(unsigned)blocks, 256, 0, s>>>(v, n_real, n_points, reinterpret_cast<const int2*>(pairs), n_pairs,
+                                                 out, err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_structure_fn(const float* delta, int64_t n_real, int64_t n_series, int64_t T, const int32_t* lags,

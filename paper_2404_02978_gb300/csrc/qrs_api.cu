@@ -68,6 +68,9 @@ qrs_status make_draw_params(qrs_handle* h, const qrs_psd* psd, const qrs_domain*
     if (!finite_pos(psd->r0_m)) return fail(h, QRS_ERR_ARG, "r0 must be finite and > 0");
     if (psd->kind == QRS_PSD_VON_KARMAN && !finite_pos(psd->L0_m))
         return fail(h, QRS_ERR_ARG, "L0 must be finite and > 0 for the von Karman PSD");
+    if (!(std::isfinite(psd->ap_D_m) && std::isfinite(psd->ap_d_m) && psd->ap_D_m >= 0.0 && psd->ap_d_m >= 0.0 &&
+          (psd->ap_D_m > 0.0 ? psd->ap_d_m < psd->ap_D_m : psd->ap_d_m == 0.0)))
+        return fail(h, QRS_ERR_ARG, "aperture filter: 0 <= ap_d < ap_D, or ap_D = ap_d = 0 for none");
     if (dom->kind < QRS_DOMAIN_SQUARE || dom->kind > QRS_DOMAIN_LOGPOLAR)
         return fail(h, QRS_ERR_ARG, "unknown domain kind %d", dom->kind);
     if (!finite_pos(dom->fmax)) return fail(h, QRS_ERR_ARG, "fmax must be finite and > 0");
@@ -99,6 +102,8 @@ qrs_status make_draw_params(qrs_handle* h, const qrs_psd* psd, const qrs_domain*
     p.real_offset = real_offset;
     p.psd_c = (float)(vk_constant() * std::pow(psd->r0_m, -5.0 / 3.0));
     p.psd_a = psd->kind == QRS_PSD_KOLMOGOROV ? 0.0f : (float)(1.0 / (psd->L0_m * psd->L0_m));
+    p.ap_D = (float)psd->ap_D_m;
+    p.ap_d = (float)psd->ap_d_m;
     const double pi = 3.14159265358979323846;
     if (dom->kind == QRS_DOMAIN_SQUARE) p.jac_c = (float)(4.0 * dom->fmax * dom->fmax);
     else if (dom->kind == QRS_DOMAIN_DISC) p.jac_c = (float)(pi * dom->fmax * dom->fmax);
@@ -289,6 +294,8 @@ static qrs_status build_piston_job(qrs_handle* h, const qrs_piston_job& j, Pisto
 {
     qrs_status st = make_draw_params(h, &j.psd, &j.dom, &j.smp, j.n_f, j.real_offset, &d->p);
     if (st != QRS_OK) return st;
+    if (j.psd.ap_D_m > 0.0)
+        return fail(h, QRS_ERR_ARG, "piston jobs filter per aperture: the PSD's aperture filter must be off");
     if (j.n_real < 0) return fail(h, QRS_ERR_ARG, "n_real must be >= 0");
     if (!counters_fit(j.n_f, j.real_offset, j.n_real)) return fail(h, QRS_ERR_ARG, "stream index overflows 2^64");
     if (j.n_ap < 1 || j.n_ap > kPisMaxAp) return fail(h, QRS_ERR_ARG, "n_ap must be in [1, %d]", kPisMaxAp);
@@ -334,6 +341,24 @@ qrs_status qrs_diff_piston(qrs_handle* h, const qrs_piston_job* jobs, int32_t n_
         return QRS_OK;
     }
     return run_piston_batch(h, dev, (flags & QRS_PISTON_GRAPH) != 0, s);
+}
+
+qrs_status qrs_pair_diff(qrs_handle* h, const float* values, int64_t n_real, int64_t n_points, const int32_t* pairs,
+                         int64_t n_pairs, float* out, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    if (n_real < 0 || n_points < 0 || n_pairs < 0) return fail(h, QRS_ERR_ARG, "sizes must be >= 0");
+    if (n_real == 0 || n_pairs == 0) return QRS_OK;
+    if (!values || !pairs || !out) return fail(h, QRS_ERR_ARG, "values, pairs and out must be non-NULL");
+    if (((uintptr_t)values & 3) || ((uintptr_t)pairs & 7) || ((uintptr_t)out & 3))
+        return fail(h, QRS_ERR_ARG, "misaligned values/out (4 B) or pairs (8 B)");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess)
+        e = launch_pair_diff(values, n_real, n_points, pairs, n_pairs, out, h->num_sms, h->d_err, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_pair_diff launch");
+    ++h->launches;
+    return QRS_OK;
 }
 
 qrs_status qrs_structure_fn(qrs_handle* h, const float* delta, int64_t n_real, int64_t n_series, int64_t T,

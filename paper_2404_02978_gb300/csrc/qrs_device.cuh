@@ -88,14 +88,16 @@ struct DrawParams {
     uint32_t key0, key1;    // Philox key = seed
     int32_t dom, smp, coef; // enums above
     int32_t n_rho, n_theta;
+    float ap_D, ap_d;       // Eq. 7 aperture filter of the PSD (ap_D = 0: none)
     int32_t pad;
 };
 
 // One drawn term.  J is the cell factor of the weight (w = W J / N_f).
 struct Term {
     float fx, fy;  // cycles/m (FP32)
-    float F;       // sqrt(W J / N_f)
+    float F;       // sqrt(W J / N_f), times A(|f|) when the PSD is filtered
     float J;
+    float A;       // the aperture filter A(|f|) (1 without filter)
     float a, b;    // coefficients
     int32_t cell;
 };
@@ -309,7 +311,8 @@ __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64
     if (p.smp != kSmpImportance) J = (p.dom == kDomLogPolar) ? p.jac_c * f2 : p.jac_c;
     else J = p.jac_c * f2 / ((float)(p.n_rho * p.n_theta) * p_cell);  // log-polar Jacobian / (cells x p_c)
     t.J = J;
-    t.F = sqrtf(psd_w(p.psd_c, p.psd_a, f2) * J * p.inv_nf);
+    t.A = (p.ap_D > 0.0f) ? airy_filter(sqrtf(f2), p.ap_D, p.ap_d) : 1.0f;
+    t.F = sqrtf(psd_w(p.psd_c, p.psd_a, f2) * J * p.inv_nf) * t.A;
     coef_from_words(p, n, w, t.a, t.b);
     if (words_out) *words_out = w;
     if (Sx_out) *Sx_out = Sx;
