@@ -284,6 +284,94 @@ def measure_grid(qrs, h, torch, dev, peaks, mode="gemm_3xtf32", reps=5):
                          "note": "whole call: bound prepass, draw records, grid kernel; L2 flushed between calls"}}
 
 
+def square_temporal_sf_expected(taus, B, v, r0, L0, D, d, fmax):
+    """Expected temporal SF of the differential piston (frozen flow along B) over
+    the square domain [-fmax, fmax)^2: int W A^2 [4 - 4 cos 2 pi f.B
+    - 4 cos 2 pi f.s + 2 cos 2 pi f.(B + s) + 2 cos 2 pi f.(B - s)] d^2 f with
+    s = v tau along B; tensor Gauss-Legendre, panels below 1/8 period."""
+    from scipy import special as sp
+    taus = np.asarray(taus, np.float64)
+    Lmax = max(1.0 / fmax, B + v * taus.max())
+    n_pan = int(np.ceil(2 * fmax * 8 * Lmax))
+    x, w = np.polynomial.legendre.leggauss(8)
+    e = np.linspace(-fmax, fmax, n_pan + 1)
+    hh = e[1] - e[0]
+    nodes = (e[:-1, None] + 0.5 * hh * (x[None, :] + 1)).ravel()
+    wts = np.tile(0.5 * hh * w, n_pan)
+    c = 0.0228955871 * r0 ** (-5 / 3)
+    out = np.zeros(taus.size)
+    for i0 in range(0, nodes.size, 256):
+        fx, fy = nodes[i0:i0 + 256, None], nodes[None, :]
+        fr = np.hypot(fx, fy)
+        u, ud = np.pi * D * fr, np.pi * d * fr
+        A = 2 * (D * sp.j1(u) - d * sp.j1(ud)) / (np.pi * (D * D - d * d) * np.where(fr > 0, fr, 1.0))
+        A = np.where(fr > 0, A, 1.0)
+        K = wts[i0:i0 + 256, None] * wts[None, :] * c * (fr * fr + L0 ** -2) ** (-11 / 6) * A * A
+        base = 4 * K.sum() - 4 * (K * np.cos(2 * np.pi * fx * B)).sum()
+        for j, t in enumerate(taus):
+            s = v * t
+            out[j] += base - 4 * (K * np.cos(2 * np.pi * fx * s)).sum() + 2 * (K * np.cos(2 * np.pi * fx * (B + s))).sum() \
+                + 2 * (K * np.cos(2 * np.pi * fx * (B - s))).sum()
+    return out
+
+
+def measure_vlti(qrs, h, torch, dev, R=2000, M=4096, dt=1e-3):
+    """The experiment of Sec. 4.3-4.4 at its own size: the VLTI unit-telescope
+    pair (D = 8 m, d = 1.1 m, B = 56.5 m), wind 10.2 m/s along the baseline,
+    SQUARE domain delta_f = 0.25/22, f_max = 0.25 (N = 44, N_f = 1936),
+    r0 = 0.10 m, L0 = 22 m, 2000 realisations of 4096 samples at 1 ms: piston
+    field synthesis (Eq. 7 PSD) at both tracks -> pair differences -> FP64
+    lagged sums per realisation; the mean structure function against its
+    expected value over the square."""
+    r0, L0, D, d, B, v = 0.10, 22.0, 8.0, 1.1, 56.5, 10.2
+    p = qrs.params(seed=5, r0=r0, L0=L0, domain="square", fmax=0.25, ap_D=D, ap_d=d)
+    n_f = 44 * 44
+    N_choice = qrs.qrs_choose_n(p, 0.25 / 22, 2e-5)
+    t = np.arange(M) * dt
+    xy = torch.from_numpy(np.concatenate([np.stack([-v * t, 0 * t], -1),
+                                          np.stack([B - v * t, 0 * t], -1)]).astype(np.float32)).to(dev)
+    pairs = torch.from_numpy(np.stack([np.arange(M), M + np.arange(M)], -1).astype(np.int32)).to(dev)
+    lags_np = np.unique(np.round(np.logspace(0, np.log10(M - 1), 24)).astype(np.int32))
+    lags = torch.from_numpy(lags_np).to(dev)
+    chi = torch.empty(R, 2 * M, device=dev)
+    delta = torch.empty(R, M, device=dev)
+    acc = torch.zeros(R, lags_np.size, 3, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def run(off):
+        acc.zero_()
+        qrs.qrs_synthesize_points(h, p, n_f, R, xy, out=chi, real_offset=off, stream=stream)
+        ev[1].record(stream)
+        qrs.qrs_pair_diff(h, chi, pairs, out=delta, stream=stream)
+        ev[2].record(stream)
+        qrs.qrs_structure_fn(h, delta.view(1, R, M), lags, acc=acc, stream=stream)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    run(R)  # warm-up (other realisations)
+    qrs.qrs_sync(h, stream)
+    ev[0].record(stream)
+    run(0)
+    ev[3].record(stream)
+    qrs.qrs_sync(h, stream)
+    ms = [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+    a = acc.cpu().numpy()
+    per = a[:, :, 0] / a[:, :, 2]
+    mean, sem = per.mean(0), per.std(0, ddof=1) / np.sqrt(R)
+    ref = square_temporal_sf_expected(lags_np * dt, B, v, r0, L0, D, d, 0.25)
+    z = (mean - ref) / sem
+    opd = (0.5 / (2 * np.pi)) ** 2  # rad^2 -> um^2 of OPD at 500 nm
+    total = sum(ms) / 1e3
+    return {"workload": "VLTI UT pair (Sec. 4.3): SQUARE N=44 (N_f=1936), D=8 m d=1.1 m, B=56.5 m, wind 10.2 m/s "
+                        "along B, r0=0.10 m L0=22 m, %d realisations x %d samples at 1 ms, %d lags" % (R, M, lags_np.size),
+            "ms": {"synthesis": ms[0], "pair_diff": ms[1], "structure_fn": ms[2], "total": sum(ms)},
+            "realizations_per_s": R / total, "term_evals_per_s": R * 2 * M * n_f / (ms[0] / 1e3),
+            "sec42_choice_of_N": {"eps_rel": 2e-5, "N": N_choice[0]},
+            "lags_ms": (lags_np * dt * 1e3).tolist(), "D_opd_um2": (mean * opd).tolist(),
+            "D_opd_expected_um2": (ref * opd).tolist(), "z_max_abs": float(np.abs(z).max()),
+            "note": "z = (mean - expected) / (std across realisations / sqrt(R))"}
+
+
 def measure_batched(qrs, h, torch, dev):
     """1000 interferometers (n_ap ~ U{4..64}, D ~ U(1.8, 8) m, 200 m disc,
     N_f ~ U{256..8192}, 256 realisations, all pairs): one persistent,
@@ -515,6 +603,7 @@ def run_ours(a):
         line["other_forms"] = {m: measure_gemm(qrs, h, torch, dev, m, peaks) for m in ("gemm_3xtf32", "gemm_bf16x3")}
         line["other_forms"]["grid_3xtf32"] = measure_grid(qrs, h, torch, dev, peaks)
         line["other_forms"]["batched_pistons"] = measure_batched(qrs, h, torch, dev)
+        line["other_forms"]["vlti_temporal_sf"] = measure_vlti(qrs, h, torch, dev)
         line["other_forms"]["learned_proposal"] = measure_learned(qrs, h, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np)

@@ -231,6 +231,10 @@ __device__ __forceinline__ float2 draw_coef(const DrawParams& p, uint64_t n)
 // --------------------------------------------------------------- the draw ---
 // Term k of realisation r: global stream index n = (real_offset + r) N_f + k.
 // Optionally returns the Philox words and the R2 state (exact, for parity).
+// The filter as an out-of-line call for the draw: kernels whose draw never
+// filters keep their register allocation (an inlined j1f enlarges it).
+static __device__ __noinline__ float airy_filter_call(float f, float D, float d) { return airy_filter(f, D, d); }
+
 __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64_t k, Words* words_out = nullptr,
                                           uint64_t* Sx_out = nullptr, uint64_t* Sy_out = nullptr)
 {
@@ -311,7 +315,7 @@ __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64
     if (p.smp != kSmpImportance) J = (p.dom == kDomLogPolar) ? p.jac_c * f2 : p.jac_c;
     else J = p.jac_c * f2 / ((float)(p.n_rho * p.n_theta) * p_cell);  // log-polar Jacobian / (cells x p_c)
     t.J = J;
-    t.A = (p.ap_D > 0.0f) ? airy_filter(sqrtf(f2), p.ap_D, p.ap_d) : 1.0f;
+    t.A = (p.ap_D > 0.0f) ? airy_filter_call(sqrtf(f2), p.ap_D, p.ap_d) : 1.0f;
     t.F = sqrtf(psd_w(p.psd_c, p.psd_a, f2) * J * p.inv_nf) * t.A;
     coef_from_words(p, n, w, t.a, t.b);
     if (words_out) *words_out = w;
