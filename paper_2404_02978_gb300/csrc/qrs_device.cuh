@@ -112,8 +112,9 @@ __device__ __forceinline__ float psd_w(float psd_c, float psd_a, float f2)
 // g(x) = 2 J1(x) / x.  For x < 4 its Taylor series
 //   g(x) = sum_m c_m u^m,  u = x^2/4,  c_m = (-1)^m / (m! (m+1)!)
 // (m = 0..12: the first omitted term is below 2e-12 at x = 4), by Horner in u
-// with an absolute error near 2e-7; beyond, 2 j1f(x)/x, whose absolute error
-// bound keeps g within about 1e-6 there (where |g| < 0.2).
+// with an absolute error near 2e-7; beyond, the large-argument form below
+// (absolute error of g below 1e-8 from the approximation, a few 1e-8 from
+// FP32 evaluation, where |g| < 0.2).
 struct AiryCoef {
     float c[13];
     constexpr AiryCoef() : c()
@@ -126,6 +127,13 @@ struct AiryCoef {
     }
 };
 
+// g(x) = 2 J1(x) / x.  Below x = 4: the Taylor series of J1 (13 terms, Horner
+// in x^2/4).  From x = 4: the large-argument form of Abramowitz & Stegun
+// (1964) eq. 9.4.6, x^(1/2) J1(x) = f1(3/x) cos(theta1), theta1 = x - 3 pi/4
+// + t1(3/x), degree-6 polynomials with |error| < 4e-8 (f1) and 9e-8 (theta1);
+// the cosine is taken in turns, x / (2 pi) - 3/8 + t1 / (2 pi) reduced mod 1,
+// so arguments in the hundreds keep their accuracy.  Both branches are short,
+// so warps whose lanes straddle x = 4 stay cheap.
 __device__ __forceinline__ float airy_g(float x)
 {
     if (x < 4.0f) {
@@ -136,7 +144,15 @@ __device__ __forceinline__ float airy_g(float x)
         for (int m = 11; m >= 0; --m) s = fmaf(s, u, K.c[m]);
         return s;
     }
-    return 2.0f * j1f(x) / x;
+    const float z = __fdividef(3.0f, x);
+    const float f1 = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(-0.00020033f, z, 0.00113653f), z, -0.00249511f), z, 0.00017105f), z,
+                                    0.01659667f), z, 0.00000156f), z, 0.79788456f);
+    const float t1 = z * fmaf(fmaf(fmaf(fmaf(fmaf(-0.00029166f, z, 0.00079824f), z, 0.00074348f), z, -0.00637879f), z,
+                                   0.00005650f), z, 0.12499612f);
+    float turns = fmaf(x, 0.159154943091895f, fmaf(t1, 0.159154943091895f, -0.375f));
+    turns -= rintf(turns);
+    const float j1 = f1 * __cosf(turns * 6.28318530717958648f) * rsqrtf(x);
+    return __fdividef(2.0f * j1, x);
 }
 
 // Eq. 7 aperture filter A(f) = 2 (D J1(pi D f) - d J1(pi d f)) / (pi (D^2 - d^2) f)
@@ -232,7 +248,7 @@ __device__ __forceinline__ float2 draw_coef(const DrawParams& p, uint64_t n)
 // Term k of realisation r: global stream index n = (real_offset + r) N_f + k.
 // Optionally returns the Philox words and the R2 state (exact, for parity).
 // The filter as an out-of-line call for the draw: kernels whose draw never
-// filters keep their register allocation (an inlined j1f enlarges it).
+// filters keep their register allocation (an inlined filter enlarges it).
 static __device__ __noinline__ float airy_filter_call(float f, float D, float d) { return airy_filter(f, D, d); }
 
 __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64_t k, Words* words_out = nullptr,

@@ -57,8 +57,9 @@ def test_filtered_draw_parity(h, dom):
     ref = oracle.draw(p, n_f=n_f, n_real=3, real_offset=4)
     F0 = oracle.draw(dict(p, ap_D=0.0, ap_d=0.0), n_f=n_f, n_real=3, real_offset=4)["F"]
     assert np.array_equal(got["f_xy"].cpu().numpy(), ref["f"])
-    # the filter in FP32 (Taylor series / j1f) against FP64: relative to the unfiltered amplitude
-    assert np.all(np.abs(got["amp"].cpu().numpy() - ref["F"]) <= 2e-6 * F0)
+    # the filter in FP32 (Taylor series / large-argument form) against FP64, relative to the
+    # unfiltered amplitude: |A_gpu - A| <= 5e-7
+    assert np.all(np.abs(got["amp"].cpu().numpy() - ref["F"]) <= 5e-7 * F0)
 
 
 @pytest.mark.parametrize("mode", ["fused", "gemm_3xtf32", "grid"])
