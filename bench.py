@@ -372,6 +372,37 @@ def measure_vlti(qrs, h, torch, dev, R=2000, M=4096, dt=1e-3):
             "note": "z = (mean - expected) / (std across realisations / sqrt(R))"}
 
 
+def measure_sampling(qrs, h, torch, dev, side=32, R=64, K=4):
+    """Clusters and gaps (Sec. 2.3, 3.2, Figs. 2-3): jittered grid (Eq. 4),
+    uniform random and R2 (Eq. 6) draws of N = side^2 terms on the SQUARE
+    domain, in unit-square coordinates.  Per realisation: nearest-neighbour
+    distances (minimum, mean, share closer than a quarter cell) and the exact
+    star discrepancy; across realisations: the discrepancy of the union of K
+    consecutive realisations (the R2 stream continues, the jitter redraws)."""
+    n = side * side
+    res = {}
+    stream = torch.cuda.current_stream()
+    for smp in ("r2", "jitter", "uniform"):
+        p = qrs.params(domain="square", fmax=0.5, sampler=smp, seed=11, n_rho=side, n_theta=side)
+        pts = qrs.qrs_draw(h, p, n, R, outputs=("f_xy",))["f_xy"] + 0.5
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        nn = qrs.qrs_nearest_neighbour(h, pts)
+        e[1].record(stream)
+        ds = qrs.qrs_star_discrepancy(h, pts)
+        e[2].record(stream)
+        union = qrs.qrs_star_discrepancy(h, pts[:K].reshape(1, K * n, 2))
+        qrs.qrs_sync(h, stream)
+        nn_np = nn.cpu().numpy() * side  # in units of the cell size 1/side
+        res[smp] = {"nn_min_cells": float(nn_np.min()), "nn_mean_cells": float(nn_np.mean()),
+                    "share_nn_below_quarter_cell": float(np.mean(nn_np < 0.25)),
+                    "star_discrepancy_mean": float(ds.mean().item()), "star_discrepancy_max": float(ds.max().item()),
+                    "union_%d_star_discrepancy" % K: float(union.item()),
+                    "ms_nearest_neighbour": e[0].elapsed_time(e[1]), "ms_star_discrepancy": e[1].elapsed_time(e[2])}
+    return {"workload": "SQUARE draws of %d terms (%dx%d), %d realisations per sampler, unit-square coordinates"
+                        % (n, side, side, R), "samplers": res}
+
+
 def measure_batched(qrs, h, torch, dev):
     """1000 interferometers (n_ap ~ U{4..64}, D ~ U(1.8, 8) m, 200 m disc,
     N_f ~ U{256..8192}, 256 realisations, all pairs): one persistent,
@@ -604,6 +635,7 @@ def run_ours(a):
         line["other_forms"]["grid_3xtf32"] = measure_grid(qrs, h, torch, dev, peaks)
         line["other_forms"]["batched_pistons"] = measure_batched(qrs, h, torch, dev)
         line["other_forms"]["vlti_temporal_sf"] = measure_vlti(qrs, h, torch, dev)
+        line["other_forms"]["sampling_quality"] = measure_sampling(qrs, h, torch, dev)
         line["other_forms"]["learned_proposal"] = measure_learned(qrs, h, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np)

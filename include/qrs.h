@@ -284,6 +284,23 @@ qrs_status qrs_diff_piston(qrs_handle* h, const qrs_piston_job* jobs, int32_t n_
 qrs_status qrs_pair_diff(qrs_handle* h, const float* values, int64_t n_real, int64_t n_points,
                          const int32_t* pairs, int64_t n_pairs, float* out, void* stream);
 
+/* -------------------------------------------------- sampling statistics ---
+ * Clusters and gaps of frequency draws (Sec. 2.3, 3.2, Figs. 2-3: jittered
+ * and random sampling leave clusters and gaps, quasi-random sampling does
+ * not).  pts [n_sets][n][2] FP32 (e.g. one realisation's frequencies per set,
+ * from qrs_draw; for the discrepancy, points in [0,1]^2 such as a SQUARE draw
+ * with fmax = 0.5 shifted by 0.5).
+ *   qrs_nearest_neighbour: out [n_sets][n] FP32, each point's distance to its
+ *     nearest other point (0 when n = 1).
+ *   qrs_star_discrepancy:  out [n_sets] FP64, D* = sup over boxes [0,u)x[0,v)
+ *     of |#points in the box / n - u v|, exact (integer counts at the
+ *     (n+1)^2 corner candidates, exact FP64 products); O(n^3) work per set.
+ * 1 <= n <= 65536, 0 <= n_sets <= 65535. */
+qrs_status qrs_nearest_neighbour(qrs_handle* h, const float* pts, int64_t n_sets, int64_t n, float* out,
+                                 void* stream);
+qrs_status qrs_star_discrepancy(qrs_handle* h, const float* pts, int64_t n_sets, int64_t n, double* out,
+                                void* stream);
+
 /* ------------------------------------------------------ hyper-parameters ---
  * Sec. 4.2 choice of N for a square domain with cell delta_f: with the
  * isotropic PSD W (von Karman; times A^2 when psd->ap_D_m > 0),

@@ -76,7 +76,10 @@ def lib():
                                                  C.c_int, C.c_void_p, C.c_void_p]
             L.oracle_structure_fn.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
                                               C.c_void_p, C.c_int, C.c_void_p]
-            for name in ("oracle_draw", "oracle_synth_terms", "oracle_synthesize",
+            L.oracle_nearest_neighbour.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
+            L.oracle_star_discrepancy.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
+            for name in ("oracle_nearest_neighbour", "oracle_star_discrepancy", "oracle_draw", "oracle_synth_terms",
+                         "oracle_synthesize",
                          "oracle_synthesize_shared", "oracle_diff_piston", "oracle_structure_fn"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -234,3 +237,23 @@ def structure_fn(delta, lags):
     lib().oracle_structure_fn(_ptr(delta), delta.shape[0], delta.shape[1], delta.shape[2], _ptr(lags),
                               lags.shape[0], _ptr(acc))
     return acc
+
+
+def nearest_neighbour(pts):
+    """pts [n_sets][n][2] float32 -> nearest-other-point distance [n_sets][n] FP64."""
+    pts = np.ascontiguousarray(pts, np.float32)
+    if pts.ndim == 2:
+        pts = pts[None]
+    out = np.zeros(pts.shape[:2], np.float64)
+    lib().oracle_nearest_neighbour(_ptr(pts), pts.shape[0], pts.shape[1], _ptr(out))
+    return out
+
+
+def star_discrepancy(pts):
+    """pts [n_sets][n][2] float32 in [0,1]^2 -> D* [n_sets] FP64 (exact, O(n^3))."""
+    pts = np.ascontiguousarray(pts, np.float32)
+    if pts.ndim == 2:
+        pts = pts[None]
+    out = np.zeros(pts.shape[0], np.float64)
+    lib().oracle_star_discrepancy(_ptr(pts), pts.shape[0], pts.shape[1], _ptr(out))
+    return out

@@ -509,3 +509,60 @@ int oracle_normals(uint64_t seed, uint32_t stream, int64_t n, double* out)
     }
     return 0;
 }
+
+/* ------------------------------------------------- sampling statistics ---
+ * Clusters and gaps of a frequency draw (Sec. 2.3, 3.2, Figs. 2-3): per set of
+ * n points, the distance from each point to its nearest other point
+ * (Euclidean, FP64 from the FP32 coordinates, brute force; 0 for n = 1), and
+ * the star discrepancy of points in [0,1]^2,
+ *   D* = sup over boxes B = [0,u) x [0,v) of | #(points in B) / n - u v |,
+ * written out from its definition: the supremum is approached at corners
+ * u in {x_i} U {1}, v in {y_j} U {1}, from above (closed box, count with <=,
+ * |C/n - uv| with C the closed count) and from below (open box, count with
+ * <, |uv - O/n|).  Both counts are integers and u v is one FP64 product of
+ * FP32 values. */
+int oracle_nearest_neighbour(const float* pts, int64_t n_sets, int64_t n, double* out)
+{
+    for (int64_t s = 0; s < n_sets; ++s) {
+        const float* p = pts + s * n * 2;
+        for (int64_t i = 0; i < n; ++i) {
+            double best = -1.0;
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                double dx = (double)p[2 * j] - (double)p[2 * i];
+                double dy = (double)p[2 * j + 1] - (double)p[2 * i + 1];
+                double d = sqrt(dx * dx + dy * dy);
+                if (best < 0.0 || d < best) best = d;
+            }
+            out[s * n + i] = best < 0.0 ? 0.0 : best;
+        }
+    }
+    return 0;
+}
+
+int oracle_star_discrepancy(const float* pts, int64_t n_sets, int64_t n, double* out)
+{
+    for (int64_t s = 0; s < n_sets; ++s) {
+        const float* p = pts + s * n * 2;
+        double D = 0.0;
+        for (int64_t i = 0; i <= n; ++i) {
+            double u = (i < n) ? (double)p[2 * i] : 1.0;
+            for (int64_t j = 0; j <= n; ++j) {
+                double v = (j < n) ? (double)p[2 * j + 1] : 1.0;
+                int64_t closed = 0, open = 0;
+                for (int64_t k = 0; k < n; ++k) {
+                    double x = (double)p[2 * k], y = (double)p[2 * k + 1];
+                    if (x <= u && y <= v) ++closed;
+                    if (x < u && y < v) ++open;
+                }
+                double uv = u * v;
+                double a = (double)closed / (double)n - uv;
+                double b = uv - (double)open / (double)n;
+                if (a > D) D = a;
+                if (b > D) D = b;
+            }
+        }
+        out[s] = D;
+    }
+    return 0;
+}

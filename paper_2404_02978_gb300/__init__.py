@@ -21,7 +21,7 @@ import threading
 import torch
 
 __all__ = ["params", "Handle", "qrs_create", "qrs_draw", "qrs_synthesize_points", "qrs_synthesize_grid", "qrs_diff_piston",
-           "qrs_pair_diff", "qrs_choose_n", "qrs_structure_fn", "qrs_sync", "QrsError", "lib_path", "load"]
+           "qrs_pair_diff", "qrs_choose_n", "qrs_nearest_neighbour", "qrs_star_discrepancy", "qrs_structure_fn", "qrs_sync", "QrsError", "lib_path", "load"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libqrs.so")
@@ -287,6 +287,32 @@ def qrs_pair_diff(h: Handle, values, pairs, out=None, stream=None):
     h._check(f(h.h, values.data_ptr(), int(n_real), int(n_points), pairs.data_ptr(), int(n_pairs), out.data_ptr(),
                _stream(stream)))
     return out
+
+
+def _stats(h, name, pts, out, dtype, shape):
+    _check_dev(pts, torch.float32, "pts")
+    if pts.dim() == 2:
+        pts = pts.unsqueeze(0)
+    n_sets, n = pts.shape[0], pts.shape[1]
+    if out is None:
+        out = torch.empty(*shape(n_sets, n), dtype=dtype, device=pts.device)
+    _check_dev(out, dtype, "out")
+    f = getattr(h.L, name)
+    if f.argtypes is None:
+        f.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
+        f.restype = C.c_int
+    h._check(f(h.h, pts.data_ptr(), int(n_sets), int(n), out.data_ptr(), _stream(None)))
+    return out
+
+
+def qrs_nearest_neighbour(h: Handle, pts, out=None):
+    """pts [n_sets, n, 2] (or [n, 2]) float32 -> nearest-other-point distance [n_sets, n] float32."""
+    return _stats(h, "qrs_nearest_neighbour", pts, out, torch.float32, lambda s, n: (s, n))
+
+
+def qrs_star_discrepancy(h: Handle, pts, out=None):
+    """pts [n_sets, n, 2] (or [n, 2]) float32 in [0,1]^2 -> exact star discrepancy [n_sets] float64."""
+    return _stats(h, "qrs_star_discrepancy", pts, out, torch.float64, lambda s, n: (s,))
 
 
 def qrs_choose_n(p, delta_f, eps_rel, n_max=10000):

@@ -361,6 +361,42 @@ qrs_status qrs_pair_diff(qrs_handle* h, const float* values, int64_t n_real, int
     return QRS_OK;
 }
 
+static qrs_status stats_args(qrs_handle* h, const void* pts, int64_t n_sets, int64_t n, const void* out, int out_align)
+{
+    if (n_sets < 0 || n_sets > 65535 || n < 1 || n > 65536)
+        return fail(h, QRS_ERR_ARG, "need 1 <= n <= 65536 and 0 <= n_sets <= 65535");
+    if (n_sets > 0 && (!pts || !out)) return fail(h, QRS_ERR_ARG, "pts and out must be non-NULL");
+    if (((uintptr_t)pts & 7) || ((uintptr_t)out & (uintptr_t)(out_align - 1)))
+        return fail(h, QRS_ERR_ARG, "pts must be 8-byte aligned, out %d-byte", out_align);
+    return QRS_OK;
+}
+
+qrs_status qrs_nearest_neighbour(qrs_handle* h, const float* pts, int64_t n_sets, int64_t n, float* out, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    qrs_status st = stats_args(h, pts, n_sets, n, out, 4);
+    if (st != QRS_OK || n_sets == 0) return st;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = launch_nearest_neighbour(pts, n_sets, n, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_nearest_neighbour launch");
+    ++h->launches;
+    return QRS_OK;
+}
+
+qrs_status qrs_star_discrepancy(qrs_handle* h, const float* pts, int64_t n_sets, int64_t n, double* out, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    qrs_status st = stats_args(h, pts, n_sets, n, out, 8);
+    if (st != QRS_OK || n_sets == 0) return st;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = launch_star_discrepancy(pts, n_sets, n, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_star_discrepancy launch");
+    ++h->launches;
+    return QRS_OK;
+}
+
 qrs_status qrs_structure_fn(qrs_handle* h, const float* delta, int64_t n_real, int64_t n_series, int64_t T,
                             const int32_t* lags, int32_t n_lags, double* acc, void* stream)
 {

@@ -50,6 +50,8 @@ cudaError_t launch_synth_fused(qrs_handle* h, const DrawParams& p, const float* 
                                int64_t n_real, float* out, cudaStream_t s);
 cudaError_t launch_pair_diff(const float* v, int64_t n_real, int64_t n_points, const int32_t* pairs, int64_t n_pairs,
                              float* out, int num_sms, int* err, cudaStream_t s);
+cudaError_t launch_nearest_neighbour(const float* pts, int64_t n_sets, int64_t n, float* out, cudaStream_t s);
+cudaError_t launch_star_discrepancy(const float* pts, int64_t n_sets, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_structure_fn(const float* delta, int64_t n_real, int64_t n_series, int64_t T,
                                 const int32_t* lags, int32_t n_lags, double* acc, int num_sms, int* err,
                                 cudaStream_t s);
