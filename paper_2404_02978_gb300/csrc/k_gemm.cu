@@ -92,7 +92,7 @@ __global__ void k_gemm_freq(DrawParams p, int64_t nf_pad, const float* __restric
     const uint64_t n0 = (uint64_t)p.real_offset * (uint64_t)p.n_f;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nf_pad; k += (int64_t)gridDim.x * blockDim.x) {
         if (k < p.n_f) {
-            const Term t = draw_term(p, n0 + (uint64_t)k, k);
+            const Term t = draw_term<false>(p, n0 + (uint64_t)k, k);
             if (z.use_fixed)
                 fbasis[k] = make_int2(__float2int_rn(t.fx * z.fscale), __float2int_rn(t.fy * z.fscale));
             else

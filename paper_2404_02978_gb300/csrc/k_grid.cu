@@ -133,7 +133,7 @@ __global__ void k_grid_draw(DrawParams p, int64_t n_real, int64_t nf_pad, const 
         const int64_t r = q / nf_pad, k = q - r * nf_pad;
         int4 v = make_int4(0, 0, 0, 0);
         if (k < p.n_f) {
-            const Term t = draw_term(p, (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k, k);
+            const Term t = draw_term<false>(p, (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k, k);
             if (z.use_fixed) {
                 v.x = __float2int_rn(t.fx * z.fscale);
                 v.y = __float2int_rn(t.fy * z.fscale);

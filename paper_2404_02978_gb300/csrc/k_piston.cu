@@ -68,7 +68,7 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
         const int len = (int)min((int64_t)kPisChunk, p.n_f - k_begin);
         __syncthreads();  // previous chunk and aperture setup complete
         for (int q = tid; q < len; q += kPisTPB) {
-            const Term t = draw_term(p, nr0 + (uint64_t)(k_begin + q), k_begin + q);
+            const Term t = draw_term<false>(p, nr0 + (uint64_t)(k_begin + q), k_begin + q);
             sh.rec[q] = make_float4(t.fx, t.fy, t.F * t.a, -(t.F * t.b));
             sh.fabs_[q] = sqrtf(t.fx * t.fx + t.fy * t.fy);
         }

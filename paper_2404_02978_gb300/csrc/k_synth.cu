@@ -5,7 +5,7 @@
 // items are numbered realisation-major and each CTA of a persistent grid (a
 // whole number of CTAs per SM) takes one contiguous range of them, so it
 // visits few realisations.  The N_f terms of the current realisation are
-// drawn by the CTA itself (Philox + R2 + FP64 map, draw_term) into shared
+// drawn by the CTA itself (Philox + R2 + domain map, draw_term) into shared
 // memory once and reused by every tile of that realisation in its range;
 // three CTAs of 256 threads share an SM (registers capped for that);
 // N_f beyond the shared-memory chunk is processed in chunks re-drawn per
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
                 __syncthreads();  // previous chunk fully consumed
                 const uint64_t n0 = (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k_begin;
                 for (int q = threadIdx.x; q < len; q += kSynthTPB) {
-                    const Term t = draw_term(p, n0 + (uint64_t)q, k_begin + q);
+                    const Term t = draw_term<false>(p, n0 + (uint64_t)q, k_begin + q);
                     float4 rec;
                     if (z.use_fixed) {
                         rec.x = __int_as_float(__float2int_rn(t.fx * z.fscale));

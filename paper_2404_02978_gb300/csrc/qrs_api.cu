@@ -104,6 +104,13 @@ qrs_status make_draw_params(qrs_handle* h, const qrs_psd* psd, const qrs_domain*
     p.psd_a = psd->kind == QRS_PSD_KOLMOGOROV ? 0.0f : (float)(1.0 / (psd->L0_m * psd->L0_m));
     p.ap_D = (float)psd->ap_D_m;
     p.ap_d = (float)psd->ap_d_m;
+    if (dom->kind == QRS_DOMAIN_LOGPOLAR) {
+        const double l2 = std::log2(dom->fmax / dom->fmin);
+        p.l2_hi = (float)l2;
+        p.l2_lo = (float)(l2 - (double)p.l2_hi);
+        p.fmin_hi = (float)dom->fmin;
+        p.fmin_lo = (float)(dom->fmin - (double)p.fmin_hi);
+    }
     const double pi = 3.14159265358979323846;
     if (dom->kind == QRS_DOMAIN_SQUARE) p.jac_c = (float)(4.0 * dom->fmax * dom->fmax);
     else if (dom->kind == QRS_DOMAIN_DISC) p.jac_c = (float)(pi * dom->fmax * dom->fmax);

@@ -89,6 +89,8 @@ struct DrawParams {
     int32_t dom, smp, coef; // enums above
     int32_t n_rho, n_theta;
     float ap_D, ap_d;       // Eq. 7 aperture filter of the PSD (ap_D = 0: none)
+    float l2_hi, l2_lo;     // log2(fmax/fmin) as a double-float (LOGPOLAR)
+    float fmin_hi, fmin_lo; // fmin as a double-float (LOGPOLAR)
     int32_t pad;
 };
 
@@ -210,6 +212,180 @@ __device__ __forceinline__ void map_logpolar(double fmin, double log_ratio, doub
 
 __device__ __forceinline__ double fix_to_unit(uint64_t S) { return (double)(S >> 11) * 0x1p-53; }
 
+// ------------------------------------------- double-float log-polar map ---
+// The LOGPOLAR map of an R2 or uniform point without FP64 arithmetic (the
+// FP64 pipe runs at 1/64 of the FP32 rate): values carried as unevaluated
+// sums hi + lo of two floats (about 48 significant bits) with the classical
+// error-free transformations -- Knuth's two-sum, the FMA-based exact product
+// -- in explicit round-to-nearest intrinsics, so that no contraction or
+// reassociation alters them.  The point is the exact 53-bit fraction
+// s = (S >> 11) 2^-53 of the FP64 path, and
+//   rho = fmin 2^(s log2(fmax/fmin)),  (cos, sin)(2 pi s_y),
+// are evaluated to a relative error near 2^-46 before the one rounding to
+// FP32, which therefore agrees with the FP64 map's except when the exact
+// value lies within about 2^-46 of a rounding boundary.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b)  // |a| >= |b| (or a = 0)
+{
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    DF t = df_two_sum(a.hi, b.hi);
+    t.lo = __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo));
+    return df_fast_two_sum(t.hi, t.lo);
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_scale(DF a, int k) { return DF{ldexpf(a.hi, k), ldexpf(a.lo, k)}; }
+
+// Compile-time tables in double, split into (hi, lo) floats:
+//   e2[j] = 2^(j/64), j < 64;  sc[j] = (sin, cos)(2 pi j / 256), j < 256,
+// from Taylor series summed to convergence (first octant) and the circle's
+// symmetries.
+struct DfTables {
+    float e2[64][2];
+    float sc[256][4];
+    static constexpr double exp_series(double x)
+    {
+        double term = 1.0, sum = 1.0;
+        for (int n = 1; n < 40; ++n) {
+            term = term * x / n;
+            sum += term;
+        }
+        return sum;
+    }
+    static constexpr double sin_series(double x)
+    {
+        double term = x, sum = x;
+        for (int n = 1; n < 30; ++n) {
+            term = -term * x * x / ((2.0 * n) * (2.0 * n + 1.0));
+            sum += term;
+        }
+        return sum;
+    }
+    static constexpr double cos_series(double x)
+    {
+        double term = 1.0, sum = 1.0;
+        for (int n = 1; n < 30; ++n) {
+            term = -term * x * x / ((2.0 * n - 1.0) * (2.0 * n));
+            sum += term;
+        }
+        return sum;
+    }
+    constexpr DfTables() : e2(), sc()
+    {
+        const double ln2 = 0.69314718055994530942;
+        for (int j = 0; j < 64; ++j) {
+            const double v = exp_series(ln2 * j / 64.0);
+            e2[j][0] = (float)v;
+            e2[j][1] = (float)(v - (double)(float)v);
+        }
+        for (int j = 0; j < 256; ++j) {
+            // angle 2 pi j / 256 = (j mod 64) steps into quadrant q = j / 64
+            const int q = j / 64, m = j % 64;
+            const double a = kPi * m / 128.0;
+            double sn = sin_series(a), cs = cos_series(a);
+            for (int r = 0; r < q; ++r) {  // rotate by a quarter turn
+                const double t = sn;
+                sn = cs;
+                cs = -t;
+            }
+            sc[j][0] = (float)sn;
+            sc[j][1] = (float)(sn - (double)(float)sn);
+            sc[j][2] = (float)cs;
+            sc[j][3] = (float)(cs - (double)(float)cs);
+        }
+    }
+};
+static __device__ const DfTables kDfTab{};
+
+// rho = fmin 2^(L2 s): u = L2 s = k + v, v = j/64 + w (w < 1/64),
+// 2^w = exp(w ln 2) by its Taylor series (t = w ln 2 < 0.011: the t^2 term in
+// double-float, t^3 onwards in float, the first omitted term below 1e-17).
+__device__ __forceinline__ DF df_logpolar_rho(uint64_t S, float l2_hi, float l2_lo, float fmin_hi, float fmin_lo)
+{
+    const uint64_t i = S >> 11;  // 53 bits
+    const float s0 = (float)(uint32_t)(i >> 29) * 0x1p-24f;
+    const float s1 = __fadd_rn((float)(uint32_t)((i >> 5) & 0xFFFFFFu) * 0x1p-48f, (float)(uint32_t)(i & 31u) * 0x1p-53f);
+    const DF s = df_fast_two_sum(s0, s1);
+    const DF u = df_mul(DF{l2_hi, l2_lo}, s);
+    float k = floorf(u.hi);
+    float vh = __fsub_rn(u.hi, k);  // exact
+    if (vh == 0.0f && u.lo < 0.0f) {
+        k = __fsub_rn(k, 1.0f);
+        vh = 1.0f;
+    }
+    int j = (int)(vh * 64.0f);
+    j = j > 63 ? 63 : j;
+    const DF w = df_fast_two_sum(__fsub_rn(vh, (float)j * 0.015625f), u.lo);  // first part exact
+    const DF t = df_mul(w, DF{0.693147182464599609375f, -1.9046542121259336e-09f});  // ln 2
+    const DF t2 = df_mul(t, t);
+    const float th = t.hi;
+    const float tail = __fmul_rn(__fmul_rn(th, t2.hi),
+                                 __fmaf_rn(th, __fmaf_rn(th, __fmaf_rn(th, 1.0f / 720.0f, 1.0f / 120.0f), 1.0f / 24.0f),
+                                           1.0f / 6.0f));
+    DF e = df_add(t, DF{__fmul_rn(t2.hi, 0.5f), __fmul_rn(t2.lo, 0.5f)});
+    e = df_add(e, DF{tail, 0.0f});
+    e = df_add(DF{1.0f, 0.0f}, e);  // 2^w
+    const DF tj{__ldg(&kDfTab.e2[j][0]), __ldg(&kDfTab.e2[j][1])};
+    const DF r = df_mul(df_mul(DF{fmin_hi, fmin_lo}, tj), e);
+    return df_scale(r, (int)k);
+}
+
+// (sin, cos)(2 pi s): s = j/256 + r (r < 1/256 turns, exact from the 53-bit
+// integer), a = 2 pi r < 0.0246; sin a = a - a^3/6 + ..., cos a = 1 - a^2/2 +
+// ... (the leading corrections in double-float, the rest in float, the first
+// omitted terms below 1e-17), then the angle-sum rotation by the table.
+__device__ __forceinline__ void df_sincos_2pi(uint64_t S, DF& sn, DF& cs)
+{
+    const uint64_t i = S >> 11;  // 53 bits
+    const int j = (int)(i >> 45);
+    const uint64_t r = i & ((1ull << 45) - 1);
+    const DF rr = df_fast_two_sum((float)(uint32_t)(r >> 21) * 0x1p-32f, (float)(uint32_t)(r & 0x1FFFFFu) * 0x1p-53f);
+    const DF a = df_mul(rr, DF{6.283185482025146484375f, -1.7484555314695172e-7f});  // 2 pi
+    const DF a2 = df_mul(a, a);
+    const DF a3 = df_mul(a2, a);
+    const float x2 = a2.hi;
+    const DF s3 = df_mul(a3, DF{0.16666667163372039795f, -4.967053879312289e-9f});  // 1/6
+    const float s_tail = __fmul_rn(__fmul_rn(a3.hi, x2), __fmaf_rn(x2, -1.0f / 5040.0f, 1.0f / 120.0f));
+    DF sa = df_add(a, DF{-s3.hi, -s3.lo});
+    sa = df_add(sa, DF{s_tail, 0.0f});
+    const float c_tail = __fmul_rn(__fmul_rn(x2, x2), __fmaf_rn(x2, __fmaf_rn(x2, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f));
+    DF ca = df_add(DF{1.0f, 0.0f}, DF{__fmul_rn(a2.hi, -0.5f), __fmul_rn(a2.lo, -0.5f)});
+    ca = df_add(ca, DF{c_tail, 0.0f});
+    const DF sj{__ldg(&kDfTab.sc[j][0]), __ldg(&kDfTab.sc[j][1])};
+    const DF cj{__ldg(&kDfTab.sc[j][2]), __ldg(&kDfTab.sc[j][3])};
+    sn = df_add(df_mul(sj, ca), df_mul(cj, sa));
+    const DF m = df_mul(sj, sa);
+    cs = df_add(df_mul(cj, ca), DF{-m.hi, -m.lo});
+}
+
+__device__ __forceinline__ void map_logpolar_df(uint64_t Sx, uint64_t Sy, float l2_hi, float l2_lo, float fmin_hi,
+                                                float fmin_lo, float& fx, float& fy)
+{
+    const DF rho = df_logpolar_rho(Sx, l2_hi, l2_lo, fmin_hi, fmin_lo);
+    DF sn, cs;
+    df_sincos_2pi(Sy, sn, cs);
+    const DF x = df_mul(rho, cs), y = df_mul(rho, sn);
+    fx = __fadd_rn(x.hi, x.lo);
+    fy = __fadd_rn(y.hi, y.lo);
+}
+
 // Coefficients of Eq. 3 from the term's Philox words: Box-Muller from 24-bit
 // uniforms (exact in FP32 and FP64 alike), and for the literal Eq. 3 form the
 // extra uniform R_u of stream 2.
@@ -251,6 +427,9 @@ __device__ __forceinline__ float2 draw_coef(const DrawParams& p, uint64_t n)
 // filters keep their register allocation (an inlined filter enlarges it).
 static __device__ __noinline__ float airy_filter_call(float f, float D, float d) { return airy_filter(f, D, d); }
 
+// CELL = false skips the cell index (FP64 work the synthesis and piston
+// kernels do not use).
+template <bool CELL = true>
 __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64_t k, Words* words_out = nullptr,
                                           uint64_t* Sx_out = nullptr, uint64_t* Sy_out = nullptr)
 {
@@ -301,32 +480,46 @@ __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64
                                   __dmul_rn((double)(t_end - t_start), 0x1p-32));
         t.cell = c;
     } else {
-        if (p.smp == kSmpR2) {
-            Sx = p.s0x + n * kR2StepX;  // Eq. 6, mod 2^64
-            Sy = p.s0y + n * kR2StepY;
-            sx = fix_to_unit(Sx);
-            sy = fix_to_unit(Sy);
-        } else if (p.smp == kSmpUniform) {
-            Sx = (uint64_t)w.w0 << 32;
-            Sy = (uint64_t)w.w1 << 32;
-            sx = (double)w.w0 * 0x1p-32;
-            sy = (double)w.w1 * 0x1p-32;
+        const bool df_map = p.dom == kDomLogPolar && p.smp != kSmpJitter;
+        if (p.smp == kSmpR2 || p.smp == kSmpUniform) {
+            if (p.smp == kSmpR2) {
+                Sx = p.s0x + n * kR2StepX;  // Eq. 6, mod 2^64
+                Sy = p.s0y + n * kR2StepY;
+            } else {
+                Sx = (uint64_t)w.w0 << 32;  // s = w 2^-32
+                Sy = (uint64_t)w.w1 << 32;
+            }
+            if (CELL || !df_map) {
+                sx = fix_to_unit(Sx);
+                sy = fix_to_unit(Sy);
+            }
         } else {  // Eq. 4 jittered grid: cell (i, j), k = j n_rho + i
             const int64_t i = k % p.n_rho, j = k / p.n_rho;
             sx = __ddiv_rn(__dadd_rn((double)i, (double)w.w0 * 0x1p-32), (double)p.n_rho);
             sy = __ddiv_rn(__dadd_rn((double)j, (double)w.w1 * 0x1p-32), (double)p.n_theta);
         }
-        if (p.dom == kDomSquare) map_square(p.fmax, sx, sy, fx, fy);
-        else if (p.dom == kDomDisc) map_disc(p.fmax, sx, sy, fx, fy);
-        else map_logpolar(p.fmin, p.log_ratio, sx, sy, fx, fy);
-        int ir = (int)floor(__dmul_rn(sx, (double)p.n_rho));
-        int it = (int)floor(__dmul_rn(sy, (double)p.n_theta));
-        ir = ir > p.n_rho - 1 ? p.n_rho - 1 : ir;
-        it = it > p.n_theta - 1 ? p.n_theta - 1 : it;
-        t.cell = ir * p.n_theta + it;
+        if (df_map) {
+            // the same point, map in double-float: one rounding to FP32
+            map_logpolar_df(Sx, Sy, p.l2_hi, p.l2_lo, p.fmin_hi, p.fmin_lo, t.fx, t.fy);
+        } else {
+            if (p.dom == kDomSquare) map_square(p.fmax, sx, sy, fx, fy);
+            else if (p.dom == kDomDisc) map_disc(p.fmax, sx, sy, fx, fy);
+            else map_logpolar(p.fmin, p.log_ratio, sx, sy, fx, fy);
+            t.fx = (float)fx;  // the one FP64 -> FP32 rounding of the method
+            t.fy = (float)fy;
+        }
+        if (CELL) {
+            int ir = (int)floor(__dmul_rn(sx, (double)p.n_rho));
+            int it = (int)floor(__dmul_rn(sy, (double)p.n_theta));
+            ir = ir > p.n_rho - 1 ? p.n_rho - 1 : ir;
+            it = it > p.n_theta - 1 ? p.n_theta - 1 : it;
+            t.cell = ir * p.n_theta + it;
+        }
     }
-    t.fx = (float)fx;  // the one FP64 -> FP32 rounding of the method
-    t.fy = (float)fy;
+    if (p.smp == kSmpImportance) {
+        t.fx = (float)fx;  // the one FP64 -> FP32 rounding of the method
+        t.fy = (float)fy;
+    }
     const float f2 = t.fx * t.fx + t.fy * t.fy;
     if (p.smp != kSmpImportance) J = (p.dom == kDomLogPolar) ? p.jac_c * f2 : p.jac_c;
     else J = p.jac_c * f2 / ((float)(p.n_rho * p.n_theta) * p_cell);  // log-polar Jacobian / (cells x p_c)
