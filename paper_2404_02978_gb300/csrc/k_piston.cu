@@ -40,6 +40,7 @@ struct PisShared {
     float part[kPisMaxAp][SLICES];     // per-slice partial pistons of the chunk
     float total[kPisMaxAp];
     float apx[kPisMaxAp], apy[kPisMaxAp], apD[kPisMaxAp], apd[kPisMaxAp];
+    float apwD[kPisMaxAp], apwd[kPisMaxAp];  // D^2 / (D^2 - d^2), d^2 / (D^2 - d^2)
 };
 
 __device__ __forceinline__ float warp_sum_f(float v)
@@ -58,8 +59,11 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
     for (int a = tid; a < n_ap; a += kPisTPB) {
         const float2 c = J.ap_xy[a];
         sh.apx[a] = c.x; sh.apy[a] = c.y;
-        sh.apD[a] = J.ap_D[a];
-        sh.apd[a] = J.ap_d ? J.ap_d[a] : 0.0f;
+        const float D = J.ap_D[a], d = J.ap_d ? J.ap_d[a] : 0.0f;
+        sh.apD[a] = D;
+        sh.apd[a] = d;
+        sh.apwD[a] = d > 0.0f ? (D * D) / (D * D - d * d) : 1.0f;
+        sh.apwd[a] = d > 0.0f ? (d * d) / (D * D - d * d) : 0.0f;
         sh.total[a] = 0.0f;
     }
     const DrawParams& p = J.p;
@@ -78,11 +82,12 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
         for (int u = warp; u < units; u += kPisWarps) {
             const int a = u / n_sl, sl = u - (u / n_sl) * n_sl;
             const float x = sh.apx[a], y = sh.apy[a], D = sh.apD[a], d = sh.apd[a];
+            const float wD = sh.apwD[a], wd = sh.apwd[a];
             const int k_end = min(len, (sl + 1) * kPisSlice);
             float acc = 0.0f;
             for (int k = sl * kPisSlice + lane; k < k_end; k += 32) {
                 const float4 T = sh.rec[k];
-                const float A = airy_filter(sh.fabs_[k], D, d);
+                const float A = airy_filter_w(sh.fabs_[k], D, d, wD, wd);
                 float s, c;
                 sincos_turns(phase_df(T.x, T.y, x, y), s, c);
                 acc = fmaf(A * T.z, c, acc);
@@ -115,7 +120,7 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
 // Single job: grid-stride over its realisations.
 using PisDefault = PisShape<256, 256>;
 
-__global__ void __launch_bounds__(256) k_piston_single(PistonJobDev J, int* err)
+__global__ void __launch_bounds__(256, 4) k_piston_single(PistonJobDev J, int* err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sh = *reinterpret_cast<PisShared<PisDefault::kSlices>*>(smem_raw);
@@ -125,7 +130,7 @@ __global__ void __launch_bounds__(256) k_piston_single(PistonJobDev J, int* err)
 // Batch: items (job, realisation) in cost-sorted job order, pulled from an
 // atomic counter.  jobs[] sorted by descending cost, item_begin its prefix sums.
 template <class S>
-__global__ void __launch_bounds__(S::kTPB) k_piston_persistent(const PistonJobDev* __restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(S::kTPB, 1024 / S::kTPB) k_piston_persistent(const PistonJobDev* __restrict__ jobs, int n_jobs,
                                                                int64_t n_items, unsigned long long* counter, int* err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

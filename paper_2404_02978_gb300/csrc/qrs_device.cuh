@@ -113,23 +113,23 @@ __device__ __forceinline__ float psd_w(float psd_c, float psd_a, float f2)
 
 // g(x) = 2 J1(x) / x.  For x < 4 its Taylor series
 //   g(x) = sum_m c_m u^m,  u = x^2/4,  c_m = (-1)^m / (m! (m+1)!)
-// (m = 0..12: the first omitted term is below 2e-12 at x = 4), by Horner in u
+// (m = 0..10: the first omitted term is below 3e-10 at x = 4), by Horner in u
 // with an absolute error near 2e-7; beyond, the large-argument form below
 // (absolute error of g below 1e-8 from the approximation, a few 1e-8 from
 // FP32 evaluation, where |g| < 0.2).
 struct AiryCoef {
-    float c[13];
+    float c[11];
     constexpr AiryCoef() : c()
     {
         double v = 1.0;
-        for (int m = 0; m < 13; ++m) {
+        for (int m = 0; m < 11; ++m) {
             c[m] = (float)v;
             v = -v / ((double)(m + 1) * (double)(m + 2));
         }
     }
 };
 
-// g(x) = 2 J1(x) / x.  Below x = 4: the Taylor series of J1 (13 terms, Horner
+// g(x) = 2 J1(x) / x.  Below x = 4: the Taylor series of J1 (11 terms, Horner
 // in x^2/4).  From x = 4: the large-argument form of Abramowitz & Stegun
 // (1964) eq. 9.4.6, x^(1/2) J1(x) = f1(3/x) cos(theta1), theta1 = x - 3 pi/4
 // + t1(3/x), degree-6 polynomials with |error| < 4e-8 (f1) and 9e-8 (theta1);
@@ -141,9 +141,9 @@ __device__ __forceinline__ float airy_g(float x)
     if (x < 4.0f) {
         constexpr AiryCoef K;
         const float u = 0.25f * x * x;
-        float s = K.c[12];
+        float s = K.c[10];
 #pragma unroll
-        for (int m = 11; m >= 0; --m) s = fmaf(s, u, K.c[m]);
+        for (int m = 9; m >= 0; --m) s = fmaf(s, u, K.c[m]);
         return s;
     }
     const float z = __fdividef(3.0f, x);
@@ -165,6 +165,15 @@ __device__ __forceinline__ float airy_filter(float f, float D, float d)
     if (d <= 0.0f) return airy_g(piF * D);
     const float D2 = D * D, d2 = d * d;
     return (D2 * airy_g(piF * D) - d2 * airy_g(piF * d)) / (D2 - d2);
+}
+
+// The same with the aperture's weights wD = D^2 / (D^2 - d^2), wd = d^2 /
+// (D^2 - d^2) computed once per aperture (no division per term).
+__device__ __forceinline__ float airy_filter_w(float f, float D, float d, float wD, float wd)
+{
+    const float piF = 3.14159265358979f * f;
+    if (d <= 0.0f) return airy_g(piF * D);
+    return fmaf(wD, airy_g(piF * D), -wd * airy_g(piF * d));
 }
 
 // --------------------------------------------------------------- domains ---
