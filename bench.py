@@ -531,11 +531,14 @@ def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho
 def run_ours(a):
     import torch
     rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_2404_02978_gb300 import build as B
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    from paper_2404_02978_gb300 import build as B
+        if local == 0:  # one compile per node; the others wait for it
+            B.build()
+        dist.barrier()
     B.build()
     import paper_2404_02978_gb300 as qrs
     from paper_2404_02978_gb300.shard import max_over_ranks, realisation_slice
