@@ -18,6 +18,9 @@
 #ifndef QRS_GEMM_INTSPLIT
 #define QRS_GEMM_INTSPLIT 1   // hi/lo splits by integer rounding (ALU) instead of conversions
 #endif
+#ifndef QRS_BF16_PACKED_CVT
+#define QRS_BF16_PACKED_CVT 1 // BF16 halves by the paired conversion cvt.rn.bf16x2.f32
+#endif
 
 namespace qrs {
 
@@ -82,7 +85,17 @@ __device__ __forceinline__ void pack16(const float (&v)[GemmCfg<PREC>::kTermsPer
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float x0 = v[2 * e], x1 = v[2 * e + 1];
-#if QRS_GEMM_INTSPLIT
+#if QRS_BF16_PACKED_CVT
+            // one conversion rounds both values (x1 to the high half); the
+            // residuals x - hi are exact in FP32 and converted the same way
+            uint32_t h, l;
+            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(x1), "f"(x0));
+            const float r0 = __fsub_rn(x0, __uint_as_float(h << 16));
+            const float r1 = __fsub_rn(x1, __uint_as_float(h & 0xFFFF0000u));
+            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(r1), "f"(r0));
+            wh[e] = h;
+            wl[e] = l;
+#elif QRS_GEMM_INTSPLIT
             const uint32_t h0 = bf16_rne_bits(x0), h1 = bf16_rne_bits(x1);
             const uint32_t l0 = bf16_rne_bits(x0 - __uint_as_float(h0));
             const uint32_t l1 = bf16_rne_bits(x1 - __uint_as_float(h1));
