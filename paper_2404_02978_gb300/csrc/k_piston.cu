@@ -22,6 +22,9 @@
 namespace qrs {
 
 constexpr int kPisChunk = 2048;  // terms per shared-memory chunk
+constexpr int kPisBuckets = 64;  // |f| buckets of the per-chunk counting sort (8 per octave)
+constexpr int kPisSortMinAp = 8; // items with at least this many apertures sort their chunks
+constexpr int kPisMaxWarps = 8;
 
 // Kernel shapes the autotuner chooses from: threads per CTA and terms per
 // (aperture, slice) unit.
@@ -37,11 +40,22 @@ template <int SLICES>
 struct PisShared {
     float4 rec[kPisChunk];             // fx, fy, A = F a, nB = -F b
     float fabs_[kPisChunk];            // |f|
+    uint16_t sidx[kPisChunk];          // terms in bucket order (sorted chunks)
+    int bcount[kPisMaxWarps][kPisBuckets];
     float part[kPisMaxAp][SLICES];     // per-slice partial pistons of the chunk
     float total[kPisMaxAp];
     float apx[kPisMaxAp], apy[kPisMaxAp], apD[kPisMaxAp], apd[kPisMaxAp];
     float apwD[kPisMaxAp], apwd[kPisMaxAp];  // D^2 / (D^2 - d^2), d^2 / (D^2 - d^2)
 };
+
+// Bucket of |f| for the chunk sort: the float's exponent and top three
+// mantissa bits (8 buckets per octave), the top bucket holding fmax, the
+// lowest collecting everything 8 octaves or more below it.
+__device__ __forceinline__ int pis_bucket(float fa, int base)
+{
+    const int e = (int)(__float_as_uint(fa) >> 20) - base;
+    return e < 0 ? 0 : (e >= kPisBuckets ? kPisBuckets - 1 : e);
+}
 
 __device__ __forceinline__ float warp_sum_f(float v)
 {
@@ -77,6 +91,63 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             sh.fabs_[q] = sqrtf(t.fx * t.fx + t.fy * t.fy);
         }
         __syncthreads();
+        // Terms in order of |f| bucket: a warp's lanes then share the Eq. 7
+        // filter's branch (x = pi D |f| below or above 4) instead of paying
+        // both, consecutive R2 terms having unrelated |f|.  Stable counting
+        // sort: per-warp bucket counts (match_any, no atomics), offsets
+        // bucket-major then warp, then ranks -- a deterministic order.
+        const bool sorted = n_ap >= kPisSortMinAp;
+        if (sorted) {
+            static_assert(kPisWarps <= kPisMaxWarps, "bucket counters per warp");
+            const int base = (int)(__float_as_uint((float)p.fmax) >> 20) - (kPisBuckets - 1);
+            const int per_warp = (len + kPisTPB - 1) / kPisTPB * 32;  // items per warp, a multiple of 32
+            const int q_begin = warp * per_warp, q_end = q_begin + per_warp;
+            for (int b = lane; b < kPisBuckets; b += 32) sh.bcount[warp][b] = 0;
+            __syncwarp();
+            for (int q0 = q_begin; q0 < q_end; q0 += 32) {
+                const int q = q0 + lane;
+                const int b = q < len ? pis_bucket(sh.fabs_[q], base) : kPisBuckets;
+                const unsigned peers = __match_any_sync(0xffffffffu, b);
+                if (b < kPisBuckets && lane == __ffs(peers) - 1) sh.bcount[warp][b] += __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            if (warp == 0) {
+                int t0 = 0, t1 = 0;  // bucket totals: lane holds buckets lane and lane + 32
+                for (int w = 0; w < kPisWarps; ++w) {
+                    t0 += sh.bcount[w][lane];
+                    t1 += sh.bcount[w][lane + 32];
+                }
+                int i0 = t0, i1 = t1;  // inclusive scans over the lanes
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v0 = __shfl_up_sync(0xffffffffu, i0, o), v1 = __shfl_up_sync(0xffffffffu, i1, o);
+                    if (lane >= o) {
+                        i0 += v0;
+                        i1 += v1;
+                    }
+                }
+                int e0 = i0 - t0, e1 = __shfl_sync(0xffffffffu, i0, 31) + i1 - t1;
+                for (int w = 0; w < kPisWarps; ++w) {
+                    const int c0 = sh.bcount[w][lane], c1 = sh.bcount[w][lane + 32];
+                    sh.bcount[w][lane] = e0;
+                    sh.bcount[w][lane + 32] = e1;
+                    e0 += c0;
+                    e1 += c1;
+                }
+            }
+            __syncthreads();
+            for (int q0 = q_begin; q0 < q_end; q0 += 32) {
+                const int q = q0 + lane;
+                const int b = q < len ? pis_bucket(sh.fabs_[q], base) : kPisBuckets;
+                const unsigned peers = __match_any_sync(0xffffffffu, b);
+                if (b < kPisBuckets) sh.sidx[sh.bcount[warp][b] + __popc(peers & ((1u << lane) - 1u))] = (uint16_t)q;
+                __syncwarp();
+                if (b < kPisBuckets && lane == __ffs(peers) - 1) sh.bcount[warp][b] += __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+        }
         const int n_sl = (len + kPisSlice - 1) / kPisSlice;
         const int units = n_ap * n_sl;
         for (int u = warp; u < units; u += kPisWarps) {
@@ -86,8 +157,9 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             const int k_end = min(len, (sl + 1) * kPisSlice);
             float acc = 0.0f;
             for (int k = sl * kPisSlice + lane; k < k_end; k += 32) {
-                const float4 T = sh.rec[k];
-                const float A = airy_filter_w(sh.fabs_[k], D, d, wD, wd);
+                const int j = sorted ? (int)sh.sidx[k] : k;
+                const float4 T = sh.rec[j];
+                const float A = airy_filter_w(sh.fabs_[j], D, d, wD, wd);
                 float s, c;
                 sincos_turns(phase_df(T.x, T.y, x, y), s, c);
                 acc = fmaf(A * T.z, c, acc);
