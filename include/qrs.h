@@ -226,7 +226,9 @@ qrs_status qrs_synthesize_points(qrs_handle* h, const qrs_psd* psd, const qrs_do
  *   index            NULL: out [n_real][ny][nx] (x fastest);
  *                    else int32 [ny][nx]: node (i, j) goes to out[r][index[j][i]]
  *                    when index[j][i] >= 0 (each point at most once), out
- *                    [n_real][n_points] -- e.g. the interior of a pupil.
+ *                    [n_real][n_points] -- e.g. the interior of a pupil; an
+ *                    index >= n_points is not written and records
+ *                    QRS_ERR_DEVICE_CHECK in the device error word.
  *   mode             QRS_SYNTH_GEMM_3XTF32 (split TF32, ~FP32 accuracy) or
  *                    QRS_SYNTH_GEMM_BF16X3 (split BF16, ~2^-16 relative).
  * Workspace: draw records of up to 256 MB of realisations at a time, owned by

@@ -1,7 +1,7 @@
 """Build libqrs.so in-tree: every CUDA translation unit compiled for sm_103a
 in parallel with nvcc, then linked into one shared library next to this file.
 
-Usage: python -m paper_2404_02978_gb300.build [--force] [--checked]
+Usage: python -m paper_2404_02978_gb300.build [--force]
 """
 from __future__ import annotations
 

@@ -411,7 +411,8 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                                 const int64_t node = yj * g.nx + xi;
                                 if (g.index) {
                                     const int32_t pidx = g.index[node];
-                                    if (pidx >= 0) g.out[orow * g.P + pidx] = __uint_as_float(v[q]);
+                                    if (pidx >= 0 && pidx < g.P) g.out[orow * g.P + pidx] = __uint_as_float(v[q]);
+                                    else if (pidx >= g.P) atomicExch(g.err, (int)QRS_ERR_DEVICE_CHECK);
                                 } else {
                                     g.out[orow * g.ny * g.nx + node] = __uint_as_float(v[q]);
                                 }

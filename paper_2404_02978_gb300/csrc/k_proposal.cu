@@ -354,6 +354,8 @@ static bool cells_ok(int32_t C) { return C >= 1 && C <= 16384; }
 qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float* params, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_mlp_init");
+    if (qrs::injected_launch_fault(h, "qrs_mlp_init") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (!cells_ok(n_cells) || !params) return fail(h, QRS_ERR_ARG, "n_cells must be in [1, 16384] and params non-NULL");
     cudaError_t e = cudaSetDevice(h->device);
@@ -371,6 +373,8 @@ qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_dom
                                 const double* geom, int64_t n, float* targets, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_proposal_targets");
+    if (qrs::injected_launch_fault(h, "qrs_proposal_targets") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (kind != QRS_TARGET_MEAN && kind != QRS_TARGET_RMS) return fail(h, QRS_ERR_ARG, "unknown target kind %d", kind);
     if (!dom || dom->kind != QRS_DOMAIN_LOGPOLAR) return fail(h, QRS_ERR_ARG, "targets need a LOGPOLAR domain");
@@ -433,6 +437,8 @@ qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, 
                            float* logits, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_mlp_forward");
+    if (qrs::injected_launch_fault(h, "qrs_mlp_forward") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (!cells_ok(n_cells) || n < 0 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 16384], n in [0, 2^24]");
     if (n == 0) return QRS_OK;
@@ -453,6 +459,8 @@ qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params
                              const float* targets, int64_t n, float* grad, float* loss, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_mlp_loss_grad");
+    if (qrs::injected_launch_fault(h, "qrs_mlp_loss_grad") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (!cells_ok(n_cells) || n < 1 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 16384], n in [1, 2^24]");
     if (!params || !geom || !targets || !grad || !loss) return fail(h, QRS_ERR_ARG, "null pointer argument");
@@ -506,6 +514,8 @@ qrs_status qrs_mlp_adam(qrs_handle* h, int32_t n_cells, float* params, float* m,
                         int64_t step, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_mlp_adam");
+    if (qrs::injected_launch_fault(h, "qrs_mlp_adam") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (!cells_ok(n_cells) || step < 1 || !(lr > 0.0f)) return fail(h, QRS_ERR_ARG, "n_cells, step >= 1, lr > 0");
     if (!params || !m || !v || !grad) return fail(h, QRS_ERR_ARG, "null pointer argument");
@@ -527,6 +537,8 @@ qrs_status qrs_proposal_cdf(qrs_handle* h, int32_t n_rho, int32_t n_theta, const
                             uint32_t* cdf, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_proposal_cdf");
+    if (qrs::injected_launch_fault(h, "qrs_proposal_cdf") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     const int64_t C = (int64_t)n_rho * n_theta;
     if (n_rho < 1 || n_theta < 1 || !cells_ok((int32_t)C) || !(eps > 0.0f && eps <= 1.0f))

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -32,9 +33,16 @@ qrs_status cuda_fail(qrs_handle* h, cudaError_t e, const char* where)
     return fail(h, QRS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+qrs_status injected_launch_fault(qrs_handle* h, const char* where)
+{
+    if (h->fault & kFaultLaunch) return fail(h, QRS_ERR_CUDA, "%s: injected launch failure (QRS_FAULT=launch)", where);
+    return QRS_OK;
+}
+
 qrs_status ensure_work(qrs_handle* h, size_t bytes)
 {
     if (h->work_bytes >= bytes) return QRS_OK;
+    if (h->fault & kFaultAlloc) return fail(h, QRS_ERR_NOMEM, "injected workspace allocation failure (QRS_FAULT=alloc)");
     if (h->d_work) {
         cudaError_t e = cudaDeviceSynchronize();  // workspace may be in use by earlier launches
         if (e != cudaSuccess) return cuda_fail(h, e, "workspace sync");
@@ -167,6 +175,10 @@ qrs_status qrs_create(qrs_handle** out, int32_t device)
     if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 64);
     if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, 64);
     if (e == cudaSuccess) h->d_xbound = reinterpret_cast<float*>(reinterpret_cast<char*>(h->d_err) + 16);
+    if (const char* f = std::getenv("QRS_FAULT")) {
+        if (std::strstr(f, "alloc")) h->fault |= kFaultAlloc;
+        if (std::strstr(f, "launch")) h->fault |= kFaultLaunch;
+    }
     if (e != cudaSuccess) {
         if (h->d_err) cudaFree(h->d_err);
         delete h;
@@ -212,6 +224,8 @@ qrs_status qrs_draw(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, co
                     int64_t n_real, int64_t real_offset, const qrs_draw_out* out, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_draw");
+    if (qrs::injected_launch_fault(h, "qrs_draw") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (!out) return fail(h, QRS_ERR_ARG, "out must be non-NULL");
     if (n_real < 0) return fail(h, QRS_ERR_ARG, "n_real must be >= 0");
@@ -235,6 +249,8 @@ qrs_status qrs_synthesize_points(qrs_handle* h, const qrs_psd* psd, const qrs_do
                                  int32_t mode, const double* col_psd, float* out, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_synthesize_points");
+    if (qrs::injected_launch_fault(h, "qrs_synthesize_points") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (n_real < 0 || n_points < 0) return fail(h, QRS_ERR_ARG, "n_real and n_points must be >= 0");
     DrawParams p;
@@ -272,6 +288,8 @@ qrs_status qrs_synthesize_grid(qrs_handle* h, const qrs_psd* psd, const qrs_doma
                                float* out, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_synthesize_grid");
+    if (qrs::injected_launch_fault(h, "qrs_synthesize_grid") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (mode != QRS_SYNTH_GEMM_3XTF32 && mode != QRS_SYNTH_GEMM_BF16X3)
         return fail(h, QRS_ERR_ARG, "grid synthesis modes: QRS_SYNTH_GEMM_3XTF32 or QRS_SYNTH_GEMM_BF16X3");
@@ -327,6 +345,8 @@ static qrs_status build_piston_job(qrs_handle* h, const qrs_piston_job& j, Pisto
 qrs_status qrs_diff_piston(qrs_handle* h, const qrs_piston_job* jobs, int32_t n_jobs, int32_t flags, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_diff_piston");
+    if (qrs::injected_launch_fault(h, "qrs_diff_piston") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(h, QRS_ERR_ARG, "jobs must hold n_jobs >= 0 entries");
     if (flags & ~(QRS_PISTON_PERSISTENT | QRS_PISTON_GRAPH)) return fail(h, QRS_ERR_ARG, "unknown flags 0x%x", flags);
@@ -354,6 +374,8 @@ qrs_status qrs_pair_diff(qrs_handle* h, const float* values, int64_t n_real, int
                          int64_t n_pairs, float* out, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_pair_diff");
+    if (qrs::injected_launch_fault(h, "qrs_pair_diff") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (n_real < 0 || n_points < 0 || n_pairs < 0) return fail(h, QRS_ERR_ARG, "sizes must be >= 0");
     if (n_real == 0 || n_pairs == 0) return QRS_OK;
@@ -381,6 +403,8 @@ static qrs_status stats_args(qrs_handle* h, const void* pts, int64_t n_sets, int
 qrs_status qrs_nearest_neighbour(qrs_handle* h, const float* pts, int64_t n_sets, int64_t n, float* out, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_nearest_neighbour");
+    if (qrs::injected_launch_fault(h, "qrs_nearest_neighbour") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     qrs_status st = stats_args(h, pts, n_sets, n, out, 4);
     if (st != QRS_OK || n_sets == 0) return st;
@@ -394,6 +418,8 @@ qrs_status qrs_nearest_neighbour(qrs_handle* h, const float* pts, int64_t n_sets
 qrs_status qrs_star_discrepancy(qrs_handle* h, const float* pts, int64_t n_sets, int64_t n, double* out, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_star_discrepancy");
+    if (qrs::injected_launch_fault(h, "qrs_star_discrepancy") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     qrs_status st = stats_args(h, pts, n_sets, n, out, 8);
     if (st != QRS_OK || n_sets == 0) return st;
@@ -408,6 +434,8 @@ qrs_status qrs_structure_fn(qrs_handle* h, const float* delta, int64_t n_real, i
                             const int32_t* lags, int32_t n_lags, double* acc, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_structure_fn");
+    if (qrs::injected_launch_fault(h, "qrs_structure_fn") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (n_real < 0 || n_series < 0 || T < 0 || n_lags < 0) return fail(h, QRS_ERR_ARG, "sizes must be >= 0");
     if (n_real == 0 || n_series == 0 || T == 0 || n_lags == 0) return QRS_OK;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -27,14 +28,31 @@ struct qrs_handle {
     size_t stage_bytes = 0;
     // Batched-piston state (persistent launch, CUDA graph cache).
     void* piston_state = nullptr;
+    // Host-side fault injection, from QRS_FAULT at qrs_create ("alloc",
+    // "launch", or both separated by a comma): workspace allocations and
+    // launches then fail with their error status without touching the GPU.
+    int fault = 0;
 };
 
 namespace qrs {
+
+constexpr int kFaultAlloc = 1;
+constexpr int kFaultLaunch = 2;
+
+// An NVTX range over a C-ABI call (seen by profilers, free otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Error plumbing: set message, return status.
 qrs_status fail(qrs_handle* h, qrs_status st, const char* fmt, ...);
 qrs_status cuda_fail(qrs_handle* h, cudaError_t e, const char* where);
 qrs_status ensure_work(qrs_handle* h, size_t bytes);
+// QRS_ERR_CUDA with a message when launch-fault injection is on, else QRS_OK.
+qrs_status injected_launch_fault(qrs_handle* h, const char* where);
 
 // Host-side construction of the draw parameters from the public structs.
 qrs_status make_draw_params(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, const qrs_sampler* smp,
