@@ -18,6 +18,7 @@ import ctypes as C
 import os
 import threading
 
+import numpy as np
 import torch
 
 __all__ = ["params", "Handle", "qrs_create", "qrs_draw", "qrs_synthesize_points", "qrs_synthesize_grid", "qrs_diff_piston",
@@ -480,20 +481,48 @@ def qrs_proposal_cdf(h: Handle, n_rho, n_theta, logits_row, eps=0.1, out=None, s
     return out
 
 
+class ProposalState:
+    """Resumable training state of the learned proposal: parameters, Adam
+    moments and the step count; save() writes one binary .npz file."""
+
+    def __init__(self, n_cells, params, m, v, step):
+        self.n_cells, self.params, self.m, self.v, self.step = int(n_cells), params, m, v, int(step)
+
+    def save(self, path):
+        np.savez(path, n_cells=self.n_cells, step=self.step, params=self.params.detach().cpu().numpy(),
+                 m=self.m.detach().cpu().numpy(), v=self.v.detach().cpu().numpy())
+
+    @staticmethod
+    def load(path, device="cuda"):
+        z = np.load(path)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+        return ProposalState(int(z["n_cells"]), t(z["params"]), t(z["m"]), t(z["v"]), int(z["step"]))
+
+
 def train_proposal(h: Handle, n_cells, geom, targets, steps=2000, lr=2e-3, seed=0, params=None, stream=None,
-                   log_every=0):
+                   log_every=0, state=None, return_state=False):
     """Adam on the mean cross entropy, full batch; every step is two libqrs calls
-    (loss and gradient, Adam update).  Returns (params, list of (step, loss))."""
-    if params is None:
-        params = qrs_mlp_init(h, n_cells, seed, stream=stream)
-    m = torch.zeros_like(params)
-    v = torch.zeros_like(params)
+    (loss and gradient, Adam update).  Returns (params, list of (step, loss)),
+    and the ProposalState after the last step when return_state is set; a
+    `state` continues a checkpointed run (same result as an uninterrupted one)."""
+    if state is not None:
+        if state.n_cells != n_cells:
+            raise ValueError("checkpoint has %d cells, not %d" % (state.n_cells, n_cells))
+        params, m, v, step0 = state.params, state.m, state.v, state.step
+    else:
+        if params is None:
+            params = qrs_mlp_init(h, n_cells, seed, stream=stream)
+        m = torch.zeros_like(params)
+        v = torch.zeros_like(params)
+        step0 = 0
     grad = torch.empty_like(params)
     loss = torch.empty(1, dtype=torch.float32, device=params.device)
     hist = []
-    for step in range(1, steps + 1):
+    for step in range(step0 + 1, step0 + steps + 1):
         qrs_mlp_loss_grad(h, n_cells, params, geom, targets, grad=grad, loss=loss, stream=stream)
         qrs_mlp_adam(h, n_cells, params, m, v, grad, lr, step, stream=stream)
         if log_every and (step % log_every == 0 or step == 1):
             hist.append((step, float(loss.item())))
+    if return_state:
+        return params, hist, ProposalState(n_cells, params, m, v, step0 + steps)
     return params, hist

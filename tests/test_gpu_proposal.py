@@ -126,3 +126,18 @@ def test_trained_proposal_lowers_structure_function_error(h):
     for nf in (256, 512, 1024):
         assert rms[("learned", nf)] * 1.8 <= rms[("plain", nf)]
     assert rms[("learned", 1024)] < rms[("plain", 2048)]
+
+
+def test_training_checkpoint_resumes_exactly(h, tmp_path):
+    """20 Adam steps in one run equal 10 steps, a checkpoint written and read
+    back, and 10 more (deterministic kernels: bit-identical parameters)."""
+    g = _dev(_geom(64, 9), torch.float64)
+    T = torch.softmax(torch.randn(64, C, device="cuda"), 1)
+    P1, _ = qrs.train_proposal(h, C, g, T, steps=20, lr=1e-3, seed=5)
+    _, _, st = qrs.train_proposal(h, C, g, T, steps=10, lr=1e-3, seed=5, return_state=True)
+    st.save(tmp_path / "ck.npz")
+    st2 = qrs.ProposalState.load(tmp_path / "ck.npz")
+    assert st2.step == 10 and torch.equal(st2.params, st.params) and torch.equal(st2.v, st.v)
+    P2, _ = qrs.train_proposal(h, C, g, T, steps=10, lr=1e-3, state=st2)
+    torch.cuda.synchronize()
+    assert torch.equal(P1, P2)
