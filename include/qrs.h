@@ -23,13 +23,22 @@
  *     stream) and the call returns without synchronising.  Argument errors are
  *     detected on the host before anything is enqueued and return a negative
  *     qrs_status with nothing launched; qrs_last_error() gives the reason.
- *   - Errors detected on the device (a bounded wait that ran out) set a device
- *     error word that qrs_sync() reports.  The library never aborts, traps or
- *     prints.
+ *   - Errors detected on the device (a bounded wait that ran out, a caller
+ *     index out of range) set a device error word that qrs_sync() reports and
+ *     clears.  The library never aborts, traps or prints.
  *   - Results are a pure function of the inputs, the seed and real_offset:
  *     one call over realisations [0, R) equals two calls over [0, R1) and
  *     [R1, R) with real_offset 0 and R1 (checkpoint / resume by counter).
- *   - Not thread-safe per handle: one host thread drives one handle.
+ *   - Not thread-safe per handle: one host thread drives one handle.  The
+ *     handle's device workspaces (shared-draw coefficients, grid draw records
+ *     and accumulators, piston job tables) serve one call at a time: calls on
+ *     one handle must not run concurrently on the GPU (issue them on one
+ *     stream, or use one handle per stream).
+ *   - Environment: QRS_AUTOTUNE_CACHE (a file of the piston kernel-shape
+ *     choices, read and written by the autotuner), QRS_FAULT (read at
+ *     qrs_create; "alloc", "launch": host-side fault injection -- workspace
+ *     allocations fail with QRS_ERR_NOMEM, compute calls fail with
+ *     QRS_ERR_CUDA before launching anything).
  */
 #ifndef QRS_H
 #define QRS_H
