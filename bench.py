@@ -133,17 +133,26 @@ def _config(cfg, xy, world):
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
-def cpu_baseline(cfg, p, xy, n_real=2):
-    """The FP64 CPU reference (as it stands, single thread) on n_real full realisations."""
+def cpu_baseline(cfg, p, xy, n_real=2, gpu_rows=None):
+    """The FP64 CPU reference (as it stands, single thread) on n_real full
+    realisations; with the GPU's values of the same realisations (gpu_rows
+    [n_real][P]), also their error against it per value, in units of each
+    realisation's field standard deviation (sigma^2 = sum_k F_k^2)."""
     import oracle
     t0 = time.perf_counter()
-    oracle.synthesize(p, cfg["n_f"], n_real, xy)
+    ref = oracle.synthesize(p, cfg["n_f"], n_real, xy)
     dt = time.perf_counter() - t0
     terms = n_real * xy.shape[0] * cfg["n_f"]
-    return {"value": terms / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d of %d realisations, all %d points, N_f=%d (%.3g terms in %.1f s), single thread FP64"
-                      % (n_real, cfg["n_real"], xy.shape[0], cfg["n_f"], terms, dt),
-            "host": _host()}
+    res = {"value": terms / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d of %d realisations, all %d points, N_f=%d (%.3g terms in %.1f s), single thread FP64"
+                     % (n_real, cfg["n_real"], xy.shape[0], cfg["n_f"], terms, dt),
+           "host": _host()}
+    if gpu_rows is not None:
+        sig = np.sqrt(np.sum(oracle.draw(p, n_f=cfg["n_f"], n_real=n_real)["F"] ** 2, axis=1))
+        err = np.abs(np.asarray(gpu_rows, np.float64) - ref) / sig[:, None]
+        res["gpu_error_vs_fp64"] = {"max_sigma": float(err.max()), "rms_sigma": float(np.sqrt(np.mean(err ** 2))),
+                                    "values": int(err.size), "tolerance_sigma": 1e-5}
+    return res
 
 
 def _host():
@@ -641,7 +650,7 @@ def run_ours(a):
         line["other_forms"]["sampling_quality"] = measure_sampling(qrs, h, torch, dev)
         line["other_forms"]["learned_proposal"] = measure_learned(qrs, h, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np)
+        line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np, gpu_rows=out[:2].cpu().numpy())
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
