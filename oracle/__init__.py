@@ -63,7 +63,7 @@ def lib():
             L.oracle_domain_jacobian.restype = C.c_double
             P = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, C.c_double,
                  C.c_int, C.c_uint64, C.c_int, C.c_uint64, C.c_uint64, C.c_int, C.c_int, C.c_int,
-                 C.c_void_p]
+                 C.c_void_p, C.c_int, C.c_double]
             L.oracle_draw.argtypes = P + [C.c_int64, C.c_int64, C.c_int64] + [C.c_void_p] * 7
             L.oracle_synth_terms.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                              C.c_void_p, C.c_int64, C.c_void_p]
@@ -87,11 +87,15 @@ def lib():
 
 
 def params(psd="von_karman", r0=0.15, L0=30.0, domain="logpolar", fmin=1e-3, fmax=16.0,
-           sampler="r2", seed=0, s0=None, coef="gauss", n_rho=64, n_theta=32, cdf=None, ap_D=0.0, ap_d=0.0):
+           sampler="r2", seed=0, s0=None, coef="gauss", n_rho=64, n_theta=32, cdf=None, ap_D=0.0, ap_d=0.0,
+           fold=0, frame=0.0):
     """Plain dictionary of method parameters (shared vocabulary, no arithmetic).
-    ap_D > 0 filters the PSD by the Eq. 7 aperture factor (the piston PSD)."""
+    ap_D > 0 filters the PSD by the Eq. 7 aperture factor (the piston PSD);
+    fold (2 or 4) and frame (turns) lay the IMPORTANCE cells over one mirrored
+    sector of a rotated frame."""
     return dict(psd=psd, r0=r0, L0=L0, domain=domain, fmin=fmin, fmax=fmax, sampler=sampler,
-                seed=seed, s0=s0, coef=coef, n_rho=n_rho, n_theta=n_theta, cdf=cdf, ap_D=ap_D, ap_d=ap_d)
+                seed=seed, s0=s0, coef=coef, n_rho=n_rho, n_theta=n_theta, cdf=cdf, ap_D=ap_D, ap_d=ap_d,
+                fold=fold, frame=frame)
 
 
 def _ptr(a):
@@ -108,7 +112,8 @@ def _pargs(p):
     args = [PSD[p["psd"]], float(p["r0"]), float(p["L0"]), float(p.get("ap_D", 0.0) or 0.0),
             float(p.get("ap_d", 0.0) or 0.0), DOMAIN[p["domain"]], float(p["fmin"]),
             float(p["fmax"]), SAMPLER[p["sampler"]], int(p["seed"]) & (2**64 - 1), use_fixed, s0x, s0y,
-            COEF[p["coef"]], int(p["n_rho"]), int(p["n_theta"]), _ptr(cdf)]
+            COEF[p["coef"]], int(p["n_rho"]), int(p["n_theta"]), _ptr(cdf), int(p.get("fold", 0) or 0),
+            float(p.get("frame", 0.0) or 0.0)]
     return args, cdf  # keep cdf alive
 
 

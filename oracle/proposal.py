@@ -121,18 +121,51 @@ def plain_draws(dom, n_rho, n_theta, seed, n_f, n_draws):
     """The plain log-polar R2 draws the targets are built from (the oracle's own draw)."""
     p = dict(psd="von_karman", r0=1.0, L0=1.0, domain="logpolar", fmin=dom[0], fmax=dom[1], sampler="r2",
              seed=seed, s0=None, coef="gauss", n_rho=n_rho, n_theta=n_theta, cdf=None)
-    return _draw(p, n_f=n_f, n_real=n_draws)
+    return _draw(p, n_f=n_f, n_real=n_draws, debug=True)
 
 
-def targets(psd_kind, dom, n_rho, n_theta, seed, n_f, n_draws, geom, raw=False, kind="mean"):
+FOLD_SHIFT = {1: 0, 2: 1, 4: 2}
+
+
+def frame_fixed(Bx, By):
+    """The baseline direction atan2(By, Bx) / 2 pi as a 0.64 fixed-point turn:
+    the FP64 value x in (-1/2, 1/2] times 2^63, truncated to an integer, doubled
+    modulo 2^64."""
+    x = np.arctan2(By, Bx) / (2.0 * np.pi)
+    return np.uint64(np.int64(x * 2.0 ** 63).astype(np.uint64)) * np.uint64(2)
+
+
+def folded_cells(Sy, ir, n_theta, fold, Bx, By):
+    """Cell of each plain draw in the baseline frame, folded F = fold times.
+    The term's angle is 2 pi Sy 2^-64; its turn relative to the baseline
+    direction is W = Sy - frame (mod 2^64); sector q = the top log2 F bits of W;
+    the rest, W << log2 F (complemented in odd sectors, the mirror images), puts
+    the term in angular cell ((W' >> 32) n_theta) >> 32 of the sector."""
+    sh = FOLD_SHIFT[fold]
+    with np.errstate(over="ignore"):
+        W = Sy - frame_fixed(Bx, By)
+        if sh:
+            q = W >> np.uint64(64 - sh)
+            W = W << np.uint64(sh)
+            W = np.where((q & np.uint64(1)) == 1, ~W, W)
+        it = ((W >> np.uint64(32)) * np.uint64(n_theta)) >> np.uint64(32)
+    return ir * n_theta + it.astype(np.int64)
+
+
+def targets(psd_kind, dom, n_rho, n_theta, seed, n_f, n_draws, geom, raw=False, kind="mean", fold=0):
     """v_k = w_k A(|f_k|)^2 2 (1 - cos 2 pi f_k . B), w_k = W(f_k; r0_i, L0_i) J_k / N_f
     over the plain draws; kind "mean": t_c ~ sum_{k in c} v_k (raw: / n_draws);
-    kind "rms": t_c ~ sqrt(sum_{k in c} v_k^2); rows normalised to 1."""
+    kind "rms": t_c ~ sqrt(sum_{k in c} v_k^2); rows normalised to 1.
+    fold 0: the draw's own cells (angle from the x axis); fold 1, 2, 4: cells of
+    the geometry's baseline frame over one of `fold` mirrored sectors
+    (folded_cells)."""
     d = plain_draws(dom, n_rho, n_theta, seed, n_f, n_draws)
     fx = d["f"][..., 0].astype(np.float64).ravel()
     fy = d["f"][..., 1].astype(np.float64).ravel()
     J = d["J"].ravel()
     cell = d["cell"].ravel()
+    Sy = d["r2"][..., 1].ravel()
+    ir = cell.astype(np.int64) // n_theta
     nc = n_rho * n_theta
     g = np.asarray(geom, np.float64).reshape(-1, 5)
     out = np.zeros((g.shape[0], nc))
@@ -141,10 +174,11 @@ def targets(psd_kind, dom, n_rho, n_theta, seed, n_f, n_draws, geom, raw=False, 
         w = an.psd(fr, r0, L0, psd_kind) * J / n_f
         A = an.airy(fr, D)
         c = w * A ** 2 * 2.0 * (1.0 - np.cos(2.0 * np.pi * (fx * Bx + fy * By)))
+        ci = cell if not fold else folded_cells(Sy, ir, n_theta, fold, Bx, By)
         if kind == "rms":
-            out[i] = np.sqrt(np.bincount(cell, weights=c * c, minlength=nc))
+            out[i] = np.sqrt(np.bincount(ci, weights=c * c, minlength=nc))
         else:
-            out[i] = np.bincount(cell, weights=c, minlength=nc) / n_draws
+            out[i] = np.bincount(ci, weights=c, minlength=nc) / n_draws
     return out if raw else out / out.sum(axis=1, keepdims=True)
 
 

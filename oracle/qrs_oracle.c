@@ -198,6 +198,8 @@ typedef struct {
     int smp_kind; uint64_t seed; int use_fixed_s0; uint64_t s0x, s0y;
     int coef_kind; int n_rho, n_theta;
     const uint32_t* cdf;  /* IMPORTANCE: n_rho*n_theta cell starts, cdf[0]=0, implicit end 2^32 */
+    int fold;             /* IMPORTANCE: 0/1 cells over the whole turn; 2, 4: over one mirrored sector */
+    double frame;         /* IMPORTANCE: angle of the cell frame, turns */
 } or_params;
 
 /* Box-Muller (1958) from two 24-bit uniforms:
@@ -242,10 +244,17 @@ static void or_draw_term(const or_params* p, const uint64_t s0[2], int64_t n_f, 
     } else { /* IMPORTANCE: two-level integer inversion over log-polar cells */
         oracle_r2_point(s0, n, S);
         /* radial band from the marginal CDF with the x coordinate,
-         * angular cell from that band's conditional CDF with the y coordinate */
+         * angular cell from that band's conditional CDF with the y coordinate.
+         * Folded (F = 2^sh sectors of 1/F turn): the top sh bits of y name the
+         * sector q, the remaining bits (complemented in odd sectors, which are
+         * mirror images) are inverted by the same conditional CDF. */
+        const int sh = (p->fold == 4) ? 2 : (p->fold == 2) ? 1 : 0;
+        const uint64_t q = sh ? (S[1] >> (64 - sh)) : 0;
+        uint64_t Y = S[1] << sh;
+        if (q & 1) Y = ~Y;
         const uint32_t* cr = p->cdf;
         const uint32_t* ct;
-        uint32_t ux = (uint32_t)(S[0] >> 32), uy = (uint32_t)(S[1] >> 32);
+        uint32_t ux = (uint32_t)(S[0] >> 32), uy = (uint32_t)(Y >> 32);
         int ir = 0, it = 0;
         for (int q = 1; q < p->n_rho; ++q)  /* plain linear scans */
             if (cr[q] <= ux) ir = q;
@@ -257,12 +266,14 @@ static void or_draw_term(const or_params* p, const uint64_t s0[2], int64_t n_f, 
         uint64_t t_start = (uint64_t)ct[it];
         uint64_t t_end = (it + 1 < p->n_theta) ? (uint64_t)ct[it + 1] : ((uint64_t)1 << 32);
         double tx = (double)(S[0] - (r_start << 32)) / ((double)(r_end - r_start) * 0x1p32);
-        double ty = (double)(S[1] - (t_start << 32)) / ((double)(t_end - t_start) * 0x1p32);
+        double ty = (double)(Y - (t_start << 32)) / ((double)(t_end - t_start) * 0x1p32);
         c = ir * p->n_theta + it;
         /* inside the cell, the log-polar map of the cell's own square */
         double L = log(p->fmax / p->fmin);
         double rho = p->fmin * exp(L * ((double)ir + tx) / (double)p->n_rho);
-        double th = 2.0 * OR_PI * ((double)it + ty) / (double)p->n_theta;
+        double v = ((double)it + ty) / (double)p->n_theta;           /* place in the sector */
+        double turn = (q & 1) ? ((double)q + 1.0 - v) : ((double)q + v);  /* sectors of the turn */
+        double th = 2.0 * OR_PI * (p->frame + turn / (double)(1 << sh));
         fd[0] = rho * cos(th);
         fd[1] = rho * sin(th);
         p_cell = ((double)(r_end - r_start) * 0x1p-32) * ((double)(t_end - t_start) * 0x1p-32);
@@ -308,23 +319,24 @@ static void or_draw_term(const or_params* p, const uint64_t s0[2], int64_t n_f, 
 static or_params or_pack(int psd_kind, double r0, double L0, double ap_D, double ap_d, int dom_kind,
                          double fmin, double fmax,
                          int smp_kind, uint64_t seed, int use_fixed_s0, uint64_t s0x, uint64_t s0y,
-                         int coef_kind, int n_rho, int n_theta, const uint32_t* cdf)
+                         int coef_kind, int n_rho, int n_theta, const uint32_t* cdf, int fold, double frame)
 {
     or_params p;
     p.psd_kind = psd_kind; p.r0 = r0; p.L0 = L0; p.ap_D = ap_D; p.ap_d = ap_d;
     p.dom_kind = dom_kind; p.fmin = fmin; p.fmax = fmax;
     p.smp_kind = smp_kind; p.seed = seed; p.use_fixed_s0 = use_fixed_s0; p.s0x = s0x; p.s0y = s0y;
     p.coef_kind = coef_kind; p.n_rho = n_rho; p.n_theta = n_theta; p.cdf = cdf;
+    p.fold = fold; p.frame = frame;
     return p;
 }
 
 #define OR_PARAMS_DECL int psd_kind, double r0, double L0, double psd_apD, double psd_apd, int dom_kind, \
     double fmin, double fmax, \
     int smp_kind, uint64_t seed, int use_fixed_s0, uint64_t s0x, uint64_t s0y, int coef_kind, \
-    int n_rho, int n_theta, const uint32_t* cdf
+    int n_rho, int n_theta, const uint32_t* cdf, int fold, double frame
 #define OR_PARAMS_PASS psd_kind, r0, L0, psd_apD, psd_apd, dom_kind, fmin, fmax, smp_kind, seed, use_fixed_s0, s0x, \
     s0y, \
-    coef_kind, n_rho, n_theta, cdf
+    coef_kind, n_rho, n_theta, cdf, fold, frame
 
 /* The draw of n_real realisations of n_f terms.  Any output may be NULL.
  *   f_xy [n_real][n_f][2] float, F [n_real][n_f], J [n_real][n_f] (the
