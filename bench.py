@@ -469,12 +469,13 @@ def hankel_piston_sf(B, r0, L0, D, fmin, fmax):
 
 
 def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho=64, n_theta=32, steps=3000,
-                    target_draws=256):
+                    target_draws=256, fold=4):
     """Learned proposal (6 -> 128 -> 128 -> n_rho x n_theta logits): targets from the
     plain method's own draws, training on the GPU, then the matched
     structure-function error (RMS over held-out geometries and draws of the
     per-draw SF relative to the Hankel integral) of learned importance draws
-    at N_f = 256..1024 against plain draws at N_f = 256..4096."""
+    at N_f = 256..1024 against plain draws at N_f = 256..4096.  The cells lie in
+    each geometry's baseline frame, folded over `fold` mirrored sectors."""
     def geom(n, seed):
         rng = np.random.default_rng(seed)
         B = np.exp(rng.uniform(np.log(1), np.log(200), n))
@@ -488,7 +489,8 @@ def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho
     gtr = torch.from_numpy(geom(n_train, 1)).to(dev)
     gte_np = geom(n_test, 2)
     t0 = time.perf_counter()
-    T = qrs.qrs_proposal_targets(h, qrs.params(**dom), n_rho, n_theta, 77, 4096, target_draws, gtr, kind="rms")
+    T = qrs.qrs_proposal_targets(h, qrs.params(**dom), n_rho, n_theta, 77, 4096, target_draws, gtr, kind="rms",
+                                 fold=fold)
     torch.cuda.synchronize()
     t_targets = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -497,13 +499,14 @@ def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho
     t_train = time.perf_counter() - t0
     logits = qrs.qrs_mlp_forward(h, C, P, torch.from_numpy(gte_np).to(dev))
     T_test = qrs.qrs_proposal_targets(h, qrs.params(**dom), n_rho, n_theta, 78, 4096, 512,
-                                      torch.from_numpy(gte_np).to(dev), kind="rms")
+                                      torch.from_numpy(gte_np).to(dev), kind="rms", fold=fold)
     err = {}
     for i, (r0, L0, D, Bx, By) in enumerate(gte_np):
         Dref = hankel_piston_sf(np.hypot(Bx, By), r0, L0, D, 1e-3, 10.0)
         p = qrs.params(r0=r0, L0=L0, seed=1000 + i, **dom)
         cdf = qrs.qrs_proposal_cdf(h, n_rho, n_theta, logits[i].contiguous(), 0.05)
-        pi = dict(p, sampler="importance", n_rho=n_rho, n_theta=n_theta, cdf=cdf)
+        pi = dict(p, sampler="importance", n_rho=n_rho, n_theta=n_theta, cdf=cdf, fold=fold,
+                  frame=float(np.arctan2(By, Bx) / (2 * np.pi)) if fold else 0.0)
         # the ceiling of any cell density on this grid: the geometry's own targets as the proposal
         cdf_x = qrs.qrs_proposal_cdf(h, n_rho, n_theta, torch.log(T_test[i].clamp_min(1e-30)).contiguous(), 0.05)
         px = dict(pi, cdf=cdf_x)
@@ -528,8 +531,8 @@ def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho
             e = rms["%s_%d" % (name, nf)]
             d[nf] = float(np.exp(np.interp(-np.log(e), -np.log(plain_e), np.log(plain_n))))
     return {"workload": "%d training geometries (r0 0.05-0.3 m, L0 10-100 m, D 1-8 m, |B| 1-200 m), "
-                        "%d held out, %d draws each, cells %dx%d over [1e-3, 10] c/m"
-                        % (n_train, n_test, draws, n_rho, n_theta),
+                        "%d held out, %d draws each, cells %dx%d over [1e-3, 10] c/m, baseline frame, "
+                        "%d mirrored sectors" % (n_train, n_test, draws, n_rho, n_theta, fold),
             "targets_s": t_targets, "train_s": t_train, "train_steps": steps, "loss_first_last": [hist[0][1], hist[-1][1]],
             "matched_sf_error": rms,
             "plain_terms_for_equal_error": {str(k): v for k, v in equiv.items()},

@@ -148,7 +148,20 @@ typedef struct qrs_sampler {
     int32_t use_fixed_s0;      /* 0: s0 = Philox(key=seed, ctr=(0,0,1,0)); 1: s0 above */
     int32_t n_rho;             /* cell grid (cell ids, JITTER grid, IMPORTANCE cells) >= 1 */
     int32_t n_theta;           /* >= 1 */
-    int32_t reserved;
+    int32_t fold;              /* IMPORTANCE only (else 0 or 1): 0 or 1, the angular
+                                  cells cover the whole turn; 2 or 4, they cover one
+                                  sector of 1/fold turn, repeated over the fold
+                                  sectors with every other sector mirrored (the top
+                                  log2(fold) bits of the R2 y coordinate pick the
+                                  sector, the rest, complemented in odd sectors, is
+                                  inverted by the band's conditional CDF).  The density
+                                  still covers the whole annulus and the weights stay
+                                  unbiased; it suits integrands that depend on the
+                                  angle only through |cos(angle - frame)|, such as
+                                  the structure function at a baseline along frame. */
+    double frame;              /* IMPORTANCE only (else 0): angle of the cells' frame
+                                  in turns (cell angles are frame + turn, the turn
+                                  made of sectors as above); finite */
 } qrs_sampler;
 
 typedef struct qrs_handle qrs_handle;

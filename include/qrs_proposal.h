@@ -57,12 +57,23 @@ qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float* pa
  *                    probability of the importance estimator when v varies
  *                    inside cells: minimises sum_c (1/p_c) int_c g^2 rho^2)
  *   targets [n][n_rho n_theta] FP32.   workspace: n_draws n_f draw records. */
+/* fold selects the cells the contributions are binned into:
+ *   0        the draw's own cells (angles from the x axis, the whole turn);
+ *   1, 2, 4  cells in the frame of the geometry's baseline, over one of `fold`
+ *            mirrored sectors of 1/fold turn -- the cells of an IMPORTANCE
+ *            sampler with this fold and frame = atan2(By, Bx) / 2 pi (qrs.h).
+ *            Term k (stream point k) has R2 coordinate Y (0.64 turns); with
+ *            the frame as a 0.64 turn (x = atan2(By, Bx) / 2 pi in FP64,
+ *            trunc(x 2^63) as a signed integer, doubled mod 2^64),
+ *            W = Y - frame mod 2^64, the sector q is the top log2(fold) bits
+ *            of W, the rest W' (complemented when q is odd) gives the angular
+ *            cell ((W' >> 32) n_theta) >> 32; the radial band is the draw's. */
 #define QRS_TARGET_MEAN 0
 #define QRS_TARGET_RMS 1
 
 qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, int32_t n_rho,
                                 int32_t n_theta, uint64_t seed, int64_t n_f, int32_t n_draws, int32_t kind,
-                                const double* geom, int64_t n, float* targets, void* stream);
+                                int32_t fold, const double* geom, int64_t n, float* targets, void* stream);
 
 /* Forward pass: logits [n][C] from geometries geom [n][5] (device FP64). */
 qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, const double* geom, int64_t n,

@@ -56,7 +56,7 @@ class QrsDomain(C.Structure):
 class QrsSampler(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("s0", C.c_uint64 * 2), ("cell_cdf", C.c_void_p), ("kind", C.c_int32),
                 ("coef_kind", C.c_int32), ("use_fixed_s0", C.c_int32), ("n_rho", C.c_int32),
-                ("n_theta", C.c_int32), ("reserved", C.c_int32)]
+                ("n_theta", C.c_int32), ("fold", C.c_int32), ("frame", C.c_double)]
 
 
 class QrsDrawOut(C.Structure):
@@ -113,11 +113,13 @@ def load():
 
 # ----------------------------------------------------------------- parameters
 def params(psd="von_karman", r0=0.15, L0=30.0, domain="logpolar", fmin=1e-3, fmax=16.0, sampler="r2", seed=0,
-           s0=None, coef="gauss", n_rho=64, n_theta=32, cdf=None, ap_D=0.0, ap_d=0.0):
+           s0=None, coef="gauss", n_rho=64, n_theta=32, cdf=None, ap_D=0.0, ap_d=0.0, fold=0, frame=0.0):
     """Method parameters as a plain dictionary (cdf: device uint32 tensor or None;
-    ap_D > 0: the PSD filtered by the Eq. 7 aperture factor, see include/qrs.h)."""
+    ap_D > 0: the PSD filtered by the Eq. 7 aperture factor; fold 2 or 4 and
+    frame (turns): IMPORTANCE cells over mirrored sectors of a rotated frame;
+    see include/qrs.h)."""
     return dict(psd=psd, r0=r0, L0=L0, domain=domain, fmin=fmin, fmax=fmax, sampler=sampler, seed=seed, s0=s0,
-                coef=coef, n_rho=n_rho, n_theta=n_theta, cdf=cdf, ap_D=ap_D, ap_d=ap_d)
+                coef=coef, n_rho=n_rho, n_theta=n_theta, cdf=cdf, ap_D=ap_D, ap_d=ap_d, fold=fold, frame=frame)
 
 
 def _structs(p):
@@ -131,7 +133,7 @@ def _structs(p):
     smp = QrsSampler(int(p.get("seed", 0)) & (2**64 - 1), (C.c_uint64 * 2)(*(s0 if s0 is not None else (0, 0))),
                      cdf.data_ptr() if cdf is not None else None, SAMPLER[p.get("sampler", "r2")],
                      COEF[p.get("coef", "gauss")], 0 if s0 is None else 1, int(p.get("n_rho", 64)),
-                     int(p.get("n_theta", 32)), 0)
+                     int(p.get("n_theta", 32)), int(p.get("fold", 0) or 0), float(p.get("frame", 0.0) or 0.0))
     return psd, dom, smp
 
 
@@ -422,18 +424,20 @@ def qrs_mlp_init(h: Handle, n_cells, seed, params=None, stream=None):
 TARGET = {"mean": 0, "rms": 1}
 
 
-def qrs_proposal_targets(h: Handle, p, n_rho, n_theta, seed, n_f, n_draws, geom, kind="rms", out=None, stream=None):
-    """Per-cell training targets [n][n_rho n_theta] from plain draws (geom: device float64 [n][5])."""
+def qrs_proposal_targets(h: Handle, p, n_rho, n_theta, seed, n_f, n_draws, geom, kind="rms", fold=0, out=None,
+                         stream=None):
+    """Per-cell training targets [n][n_rho n_theta] from plain draws (geom: device float64 [n][5]);
+    fold 1, 2, 4: cells of each geometry's baseline frame over `fold` mirrored sectors."""
     _check_dev(geom, torch.float64, "geom")
     n = geom.shape[0]
     if out is None:
         out = torch.empty(n, n_rho * n_theta, dtype=torch.float32, device=geom.device)
     psd, dom, _ = _structs(p)
     f = _prop_fn("qrs_proposal_targets", [C.c_void_p, C.POINTER(QrsPsd), C.POINTER(QrsDomain), C.c_int32, C.c_int32,
-                                          C.c_uint64, C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
-                                          C.c_void_p, C.c_void_p])
+                                          C.c_uint64, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                          C.c_int64, C.c_void_p, C.c_void_p])
     h._check(f(h.h, C.byref(psd), C.byref(dom), int(n_rho), int(n_theta), int(seed) & (2**64 - 1), int(n_f),
-               int(n_draws), TARGET[kind], geom.data_ptr(), int(n), out.data_ptr(), _stream(stream)))
+               int(n_draws), TARGET[kind], int(fold), geom.data_ptr(), int(n), out.data_ptr(), _stream(stream)))
     return out
 
 

@@ -228,13 +228,23 @@ __global__ void k_prop_draws(DrawParams p, int n_draws, float4* __restrict__ rec
 }
 
 // One CTA per geometry: shared histogram of w A^2 2 (1 - cos 2 pi f.B) over the cells.
+// fold_sh < 0: the draw's own cells (record .w).  fold_sh = 0, 1, 2: cells of the
+// geometry's baseline frame over 2^fold_sh mirrored sectors: record k is stream
+// point n = k, its R2 y coordinate Y = s0y + k step (0.64 turns); W = Y - frame
+// with the baseline direction atan2(By, Bx) / 2 pi as a 0.64 fixed-point turn
+// (FP64 x in (-1/2, 1/2], times 2^63, truncated, doubled mod 2^64); the top
+// fold_sh bits of W are the sector, the rest (complemented in odd sectors)
+// W' gives the angular cell ((W' >> 32) n_theta) >> 32; the radial band is
+// the draw's own.
 __global__ void __launch_bounds__(512) k_prop_targets(const float4* __restrict__ rec, int64_t n_rec, float inv_nf,
                                                       const double* __restrict__ geom, int psd_kind, double c_vk, int C,
-                                                      int kind, float* __restrict__ out)
+                                                      int kind, int n_theta, int fold_sh, uint64_t s0y,
+                                                      float* __restrict__ out)
 {
     extern __shared__ float hist[];
     __shared__ float red[32];
     __shared__ float s_pc, s_pa, s_D, s_Bx, s_By;
+    __shared__ unsigned long long s_frame;
     const int64_t i = blockIdx.x;
     if (threadIdx.x == 0) {
         const double* g = geom + 5 * i;
@@ -243,6 +253,8 @@ __global__ void __launch_bounds__(512) k_prop_targets(const float4* __restrict__
         s_D = (float)g[2];
         s_Bx = (float)g[3];
         s_By = (float)g[4];
+        const double x = __ddiv_rn(atan2(g[4], g[3]), kTwoPi);
+        s_frame = (unsigned long long)(long long)__dmul_rn(x, 0x1p63) * 2ull;
     }
     for (int c = threadIdx.x; c < C; c += blockDim.x) hist[c] = 0.0f;
     __syncthreads();
@@ -255,7 +267,15 @@ __global__ void __launch_bounds__(512) k_prop_targets(const float4* __restrict__
         float s, c;
         sincos_turns(phase_df(r.x, r.y, Bx, By), s, c);
         const float v = w * A * A * 2.0f * (1.0f - c);
-        atomicAdd(&hist[__float_as_int(r.w)], kind == QRS_TARGET_RMS ? v * v : v);
+        int cell = __float_as_int(r.w);
+        if (fold_sh >= 0) {
+            uint64_t W = s0y + (uint64_t)k * kR2StepY - (uint64_t)s_frame;
+            const uint64_t sec = fold_sh ? (W >> (64 - fold_sh)) : 0ull;
+            W <<= fold_sh;
+            if (sec & 1ull) W = ~W;
+            cell = (cell / n_theta) * n_theta + (int)(((W >> 32) * (uint64_t)n_theta) >> 32);
+        }
+        atomicAdd(&hist[cell], kind == QRS_TARGET_RMS ? v * v : v);
     }
     __syncthreads();
     if (kind == QRS_TARGET_RMS)
@@ -370,13 +390,14 @@ qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float* pa
 
 qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, int32_t n_rho,
                                 int32_t n_theta, uint64_t seed, int64_t n_f, int32_t n_draws, int32_t kind,
-                                const double* geom, int64_t n, float* targets, void* stream)
+                                int32_t fold, const double* geom, int64_t n, float* targets, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
     qrs::NvtxRange nvtx_range("qrs_proposal_targets");
     if (qrs::injected_launch_fault(h, "qrs_proposal_targets") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (kind != QRS_TARGET_MEAN && kind != QRS_TARGET_RMS) return fail(h, QRS_ERR_ARG, "unknown target kind %d", kind);
+    if (fold != 0 && fold != 1 && fold != 2 && fold != 4) return fail(h, QRS_ERR_ARG, "fold must be 0, 1, 2 or 4");
     if (!dom || dom->kind != QRS_DOMAIN_LOGPOLAR) return fail(h, QRS_ERR_ARG, "targets need a LOGPOLAR domain");
     if (n_draws < 1 || n < 0) return fail(h, QRS_ERR_ARG, "n_draws >= 1, n >= 0");
     const int64_t C = (int64_t)n_rho * n_theta;
@@ -409,7 +430,9 @@ qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_dom
         e = cudaFuncSetAttribute(k_prop_targets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(C * sizeof(float)));
     if (e == cudaSuccess) {
         k_prop_targets<<<(unsigned)n, 512, (size_t)C * sizeof(float), s>>>(rec, n_rec, p.inv_nf, geom, psd->kind, vk_c(),
-                                                                          (int)C, kind, targets);
+                                                                          (int)C, kind, n_theta,
+                                                                          fold == 0 ? -1 : fold == 4 ? 2 : fold - 1,
+                                                                          p.s0y, targets);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "qrs_proposal_targets");

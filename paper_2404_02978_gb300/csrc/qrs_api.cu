@@ -100,6 +100,11 @@ qrs_status make_draw_params(qrs_handle* h, const qrs_psd* psd, const qrs_domain*
         if (dom->kind != QRS_DOMAIN_LOGPOLAR) return fail(h, QRS_ERR_ARG, "IMPORTANCE cells need a LOGPOLAR domain");
         if (!smp->cell_cdf) return fail(h, QRS_ERR_ARG, "IMPORTANCE needs cell_cdf");
         if (((uintptr_t)smp->cell_cdf & 3) != 0) return fail(h, QRS_ERR_ARG, "cell_cdf must be 4-byte aligned");
+        if (smp->fold != 0 && smp->fold != 1 && smp->fold != 2 && smp->fold != 4)
+            return fail(h, QRS_ERR_ARG, "fold must be 0, 1, 2 or 4");
+        if (!std::isfinite(smp->frame)) return fail(h, QRS_ERR_ARG, "frame must be finite");
+    } else if ((smp->fold != 0 && smp->fold != 1) || smp->frame != 0.0) {
+        return fail(h, QRS_ERR_ARG, "fold and frame apply to the IMPORTANCE sampler only");
     }
     DrawParams p;
     std::memset(&p, 0, sizeof(p));
@@ -140,6 +145,10 @@ qrs_status make_draw_params(qrs_handle* h, const qrs_psd* psd, const qrs_domain*
     p.coef = smp->coef_kind;
     p.n_rho = smp->n_rho;
     p.n_theta = smp->n_theta;
+    if (smp->kind == QRS_SAMPLER_IMPORTANCE) {
+        p.fold_sh = smp->fold == 4 ? 2 : smp->fold == 2 ? 1 : 0;
+        p.frame = smp->frame;
+    }
     *out = p;
     return QRS_OK;
 }

@@ -91,7 +91,8 @@ struct DrawParams {
     float ap_D, ap_d;       // Eq. 7 aperture filter of the PSD (ap_D = 0: none)
     float l2_hi, l2_lo;     // log2(fmax/fmin) as a double-float (LOGPOLAR)
     float fmin_hi, fmin_lo; // fmin as a double-float (LOGPOLAR)
-    int32_t pad;
+    int32_t fold_sh;        // IMPORTANCE: log2 of the sector count (0, 1, 2)
+    double frame;           // IMPORTANCE: angle of the cell frame, turns
 };
 
 // One drawn term.  J is the cell factor of the weight (w = W J / N_f).
@@ -452,10 +453,15 @@ __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64
         // R2 point; the radial band from the marginal CDF with the top 32 bits
         // of x, the angular cell from that band's conditional CDF with the top
         // 32 bits of y; the remainders place the frequency inside the cell by
-        // the cell's own log-polar map.
+        // the cell's own log-polar map.  With 2^fold_sh sectors the top
+        // fold_sh bits of y pick the sector and the rest, complemented in the
+        // mirrored (odd) sectors, takes y's place.
         Sx = p.s0x + n * kR2StepX;
         Sy = p.s0y + n * kR2StepY;
-        const uint32_t ux = (uint32_t)(Sx >> 32), uy = (uint32_t)(Sy >> 32);
+        const uint64_t sec = p.fold_sh ? (Sy >> (64 - p.fold_sh)) : 0ull;
+        uint64_t Y = Sy << p.fold_sh;
+        if (sec & 1ull) Y = ~Y;
+        const uint32_t ux = (uint32_t)(Sx >> 32), uy = (uint32_t)(Y >> 32);
         const uint32_t* cr = p.cdf;
         int lo = 0, hi = p.n_rho;  // largest band with cr[band] <= ux (cr[0] = 0)
         while (hi - lo > 1) {
@@ -476,11 +482,13 @@ __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64
         const uint64_t t_start = (uint64_t)__ldg(ct + it);
         const uint64_t t_end = (it + 1 < p.n_theta) ? (uint64_t)__ldg(ct + it + 1) : (1ull << 32);
         const double tx = __ddiv_rn((double)(Sx - (r_start << 32)), __dmul_rn((double)(r_end - r_start), 0x1p32));
-        const double ty = __ddiv_rn((double)(Sy - (t_start << 32)), __dmul_rn((double)(t_end - t_start), 0x1p32));
+        const double ty = __ddiv_rn((double)(Y - (t_start << 32)), __dmul_rn((double)(t_end - t_start), 0x1p32));
         const int c = ir * p.n_theta + it;
         const double rho =
             __dmul_rn(p.fmin, exp(__ddiv_rn(__dmul_rn(p.log_ratio, __dadd_rn((double)ir, tx)), (double)p.n_rho)));
-        const double th = __ddiv_rn(__dmul_rn(kTwoPi, __dadd_rn((double)it, ty)), (double)p.n_theta);
+        const double v = __ddiv_rn(__dadd_rn((double)it, ty), (double)p.n_theta);  // place in the sector
+        const double turn = (sec & 1ull) ? __dsub_rn(__dadd_rn((double)sec, 1.0), v) : __dadd_rn((double)sec, v);
+        const double th = __dmul_rn(kTwoPi, __dadd_rn(p.frame, __ddiv_rn(turn, (double)(1 << p.fold_sh))));
         double s, co;
         sincos(th, &s, &co);
         fx = __dmul_rn(rho, co);

@@ -47,7 +47,8 @@ def test_empty_inputs_launch_nothing(h):
 
 
 @pytest.mark.parametrize("call", ["n_f_zero", "n_f_huge", "negative_real", "negative_offset", "grid_too_wide",
-                                  "stats_too_many", "lag_out_of_range"])
+                                  "stats_too_many", "lag_out_of_range", "fold_not_importance", "fold_three",
+                                  "frame_not_finite"])
 def test_size_limits_are_argument_errors(h, call):
     p = qrs.params(seed=2)
     xy = _dev(np.zeros((4, 2), np.float32))
@@ -60,6 +61,13 @@ def test_size_limits_are_argument_errors(h, call):
                                                         torch.zeros(1, device="cuda"),
                                                         out=torch.empty(1, device="cuda")),
         "stats_too_many": lambda: qrs.qrs_star_discrepancy(h, torch.zeros(1, 65537, 2, device="cuda")),
+        "fold_not_importance": lambda: qrs.qrs_draw(h, qrs.params(seed=2, fold=4), 16, 1),
+        "fold_three": lambda: qrs.qrs_draw(h, qrs.params(sampler="importance", n_rho=2, n_theta=2, fold=3,
+                                                         cdf=torch.zeros(6, dtype=torch.int32, device="cuda")), 16, 1),
+        "frame_not_finite": lambda: qrs.qrs_draw(h, qrs.params(sampler="importance", n_rho=2, n_theta=2,
+                                                               frame=float("nan"),
+                                                               cdf=torch.zeros(6, dtype=torch.int32, device="cuda")),
+                                                 16, 1),
         "lag_out_of_range": None,
     }
     if call == "lag_out_of_range":  # a device-side check, reported by qrs_sync

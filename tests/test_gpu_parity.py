@@ -59,11 +59,15 @@ DRAW_CASES = [
     dict(domain="logpolar", sampler="uniform", coef="gauss"),
     dict(domain="square", sampler="jitter", coef="gauss", fmax=1.0, n_rho=16, n_theta=16),
     dict(domain="logpolar", sampler="importance", coef="gauss", n_rho=16, n_theta=8),
+    dict(domain="logpolar", sampler="importance", coef="gauss", n_rho=16, n_theta=8, fold=4, frame=0.37),
+    dict(domain="logpolar", sampler="importance", coef="eq3", n_rho=8, n_theta=12, fold=2, frame=-0.1),
+    dict(domain="logpolar", sampler="importance", coef="gauss", n_rho=16, n_theta=8, fold=1, frame=0.6),
     dict(domain="logpolar", sampler="r2", coef="gauss", psd="kolmogorov", s0=(1 << 63, 1 << 63)),
 ]
 
 
-@pytest.mark.parametrize("case", DRAW_CASES, ids=lambda c: "%s-%s-%s" % (c["domain"], c["sampler"], c["coef"]))
+@pytest.mark.parametrize("case", DRAW_CASES, ids=lambda c: "%s-%s-%s%s" % (c["domain"], c["sampler"], c["coef"],
+                                                                           "-fold%d" % c["fold"] if "fold" in c else ""))
 def test_draw_parity(h, case):
     p = oracle.params(seed=17, **case)
     n_f = 256 if case["sampler"] == "jitter" else 333
@@ -128,10 +132,11 @@ def test_synthesis_parity(h, case):
     _field_check(got.cpu().numpy(), ref, _sigma(p, case["n_f"], case["n_real"], off))
 
 
-def test_synthesis_importance_parity(h):
+@pytest.mark.parametrize("fold,frame", [(0, 0.0), (4, 0.21)])
+def test_synthesis_importance_parity(h, fold, frame):
     nr, nt = 16, 8
     cdf = _cdf(nr, nt, 5)
-    p = oracle.params(seed=29, sampler="importance", n_rho=nr, n_theta=nt, cdf=cdf)
+    p = oracle.params(seed=29, sampler="importance", n_rho=nr, n_theta=nt, cdf=cdf, fold=fold, frame=frame)
     xy = wl.pupil_grid(64, 8.0)[:1500]
     ref = oracle.synthesize(p, 256, 2, xy)
     got = qrs.qrs_synthesize_points(h, _gp(p, torch.from_numpy(cdf.view(np.int32)).cuda()), 256, 2,

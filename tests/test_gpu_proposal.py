@@ -63,12 +63,15 @@ def test_forward_loss_grad_adam_match_reference(h):
     assert np.max(np.abs(Pd.cpu().numpy() - P2)) <= 1e-6 + 1e-5 * np.max(np.abs(P2 - P))
 
 
-@pytest.mark.parametrize("kind", ["mean", "rms"])
-def test_targets_match_reference(h, kind):
+@pytest.mark.parametrize("kind,fold", [("mean", 0), ("rms", 0), ("rms", 4), ("mean", 2), ("rms", 1)])
+def test_targets_match_reference(h, kind, fold):
     g = _geom(6, 8)
+    g[0, 3:] = (30.0, 0.0)   # baseline along +x
+    g[1, 3:] = (-12.0, 0.0)  # frame at half a turn exactly
     p = qrs.params(psd="von_karman", r0=0.1, L0=25.0, **DOM)
-    t = qrs.qrs_proposal_targets(h, p, 64, 32, 13, 1024, 4, _dev(g, torch.float64), kind=kind).cpu().numpy()
-    ref = pr.targets("von_karman", (1e-3, 10.0), 64, 32, 13, 1024, 4, g, kind=kind)
+    t = qrs.qrs_proposal_targets(h, p, 64, 32, 13, 1024, 4, _dev(g, torch.float64), kind=kind,
+                                 fold=fold).cpu().numpy()
+    ref = pr.targets("von_karman", (1e-3, 10.0), 64, 32, 13, 1024, 4, g, kind=kind, fold=fold)
     assert np.allclose(t.sum(axis=1), 1.0, atol=1e-5)
     assert np.max(np.abs(t - ref)) <= 1e-5 + 1e-4 * np.max(ref)
 
@@ -98,15 +101,18 @@ def _cond_sf(f, F, D, B):
     return (F.double() ** 2 * A ** 2 * 2 * (1 - torch.cos(ph))).sum(-1)
 
 
-def test_trained_proposal_lowers_structure_function_error(h):
+@pytest.mark.parametrize("fold", [0, 4])
+def test_trained_proposal_lowers_structure_function_error(h, fold):
     """Trained on 2000 geometries (targets from the plain method's own draws),
     evaluated on 48 held-out ones: RMS relative error of the per-draw SF at
     the geometry's baseline vs the analytic Hankel integral.  The learned
     importance draw at N_f beats the plain draw at N_f by >= 1.8x for
-    N_f = 256, 512, 1024, and at 1024 beats the plain draw at 2048."""
+    N_f = 256, 512, 1024, and at 1024 beats the plain draw at 2048.  fold 4:
+    cells in the baseline frame over four mirrored sectors."""
     from oracle import analytic as an
     gtr, gte = _geom(2000, 1), _geom(48, 2)
-    T = qrs.qrs_proposal_targets(h, qrs.params(**DOM), 64, 32, 77, 4096, 256, _dev(gtr, torch.float64), kind="rms")
+    T = qrs.qrs_proposal_targets(h, qrs.params(**DOM), 64, 32, 77, 4096, 256, _dev(gtr, torch.float64), kind="rms",
+                                 fold=fold)
     P, hist = qrs.train_proposal(h, C, _dev(gtr, torch.float64), T, steps=3000, lr=2e-3, seed=3, log_every=1000)
     assert hist[-1][1] < hist[0][1] - 1.5
     logits = qrs.qrs_mlp_forward(h, C, P, _dev(gte, torch.float64))
@@ -115,7 +121,8 @@ def test_trained_proposal_lowers_structure_function_error(h):
         Dref = an.piston_sf(np.hypot(Bx, By), r0, L0, D, 0.0, 1e-3, 10.0)
         p = qrs.params(r0=r0, L0=L0, seed=1000 + i, **DOM)
         cdf = qrs.qrs_proposal_cdf(h, 64, 32, logits[i].contiguous(), 0.05)
-        pi = dict(p, sampler="importance", n_rho=64, n_theta=32, cdf=cdf)
+        pi = dict(p, sampler="importance", n_rho=64, n_theta=32, cdf=cdf, fold=fold,
+                  frame=float(np.arctan2(By, Bx) / (2 * np.pi)) if fold else 0.0)
         for name, pp, nfs in (("plain", p, (256, 512, 1024, 2048)), ("learned", pi, (256, 512, 1024))):
             for nf in nfs:
                 d = qrs.qrs_draw(h, pp, nf, 8, outputs=("f_xy", "amp"))

@@ -61,7 +61,8 @@ def test_ctypes_layouts_match_c(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(qrs_psd), sizeof(qrs_domain), sizeof(qrs_sampler),
          sizeof(qrs_draw_out), sizeof(qrs_piston_job));
-  printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(qrs_sampler, cell_cdf), offsetof(qrs_sampler, kind),
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(qrs_sampler, cell_cdf), offsetof(qrs_sampler, kind),
+         offsetof(qrs_sampler, frame),
          offsetof(qrs_piston_job, n_f), offsetof(qrs_piston_job, ap_xy), offsetof(qrs_piston_job, n_ap),
          offsetof(qrs_piston_job, n_pairs));
   return 0;
@@ -72,7 +73,8 @@ int main(void) {
     sizes, offs = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().splitlines()]
     assert sizes == [C.sizeof(qrs.QrsPsd), C.sizeof(qrs.QrsDomain), C.sizeof(qrs.QrsSampler),
                      C.sizeof(qrs.QrsDrawOut), C.sizeof(qrs.QrsPistonJob)]
-    assert offs == [qrs.QrsSampler.cell_cdf.offset, qrs.QrsSampler.kind.offset, qrs.QrsPistonJob.n_f.offset,
+    assert offs == [qrs.QrsSampler.cell_cdf.offset, qrs.QrsSampler.kind.offset, qrs.QrsSampler.frame.offset,
+                    qrs.QrsPistonJob.n_f.offset,
                     qrs.QrsPistonJob.ap_xy.offset, qrs.QrsPistonJob.n_ap.offset, qrs.QrsPistonJob.n_pairs.offset]
 
 
