@@ -90,14 +90,17 @@ qrs_status qrs_mlp_adam(qrs_handle* h, int32_t n_cells, float* params, float* m,
                         float lr, int64_t step, void* stream);
 
 /* Two-level sampling CDF from one row of logits (device [n_rho n_theta]):
- * p = (1 - eps) softmax(z) + eps / C over the cells; the marginal over radial
- * bands and, per band, the conditional over its angular cells, each quantised
- * to integer widths >= 1 summing to 2^32 (floor of p (2^32 - n) plus one, the
- * remainder to the largest entry); cdf [n_rho + n_rho n_theta] (device uint32)
- * holds their start points in the format of qrs_sampler.cell_cdf.
- * 0 < eps <= 1 (the mixture with the uniform density bounds every weight). */
+ * p = (1 - eps) softmax(beta z) + eps / C over the cells; the marginal over
+ * radial bands and, per band, the conditional over its angular cells, each
+ * quantised to integer widths >= 1 summing to 2^32 (floor of p (2^32 - n) plus
+ * one, the remainder to the largest entry); cdf [n_rho + n_rho n_theta]
+ * (device uint32) holds their start points in the format of
+ * qrs_sampler.cell_cdf.  0 < eps <= 1 (the mixture with the uniform density
+ * bounds every weight); 0 < beta <= 16 (beta < 1 flattens the network's
+ * density: the targets are variance-optimal for independent draws, and the
+ * stratified R2 draws gain from a flatter one). */
 qrs_status qrs_proposal_cdf(qrs_handle* h, int32_t n_rho, int32_t n_theta, const float* logits, float eps,
-                            uint32_t* cdf, void* stream);
+                            float beta, uint32_t* cdf, void* stream);
 
 #ifdef __cplusplus
 }

@@ -192,15 +192,16 @@ def quantise(p, scale_count):
     return np.concatenate([[0], np.cumsum(w)[:-1]]).astype(np.int64), w
 
 
-def cdf(logits, eps, n_rho, n_theta):
-    """Two-level sampling CDF: p = (1 - eps) softmax(z) + eps / C over the
-    n_rho x n_theta cells; the marginal over radial bands, then each band's
-    conditional over its angular cells, each quantised to widths summing to
-    2^32.  Returns (uint32 [n_rho + n_rho n_theta], cell probabilities as
-    quantised (p_band p_cell|band))."""
+def cdf(logits, eps, n_rho, n_theta, beta=1.0):
+    """Two-level sampling CDF: p = (1 - eps) softmax(beta z) + eps / C over the
+    n_rho x n_theta cells (beta: the softmax temperature's inverse); the
+    marginal over radial bands, then each band's conditional over its angular
+    cells, each quantised to widths summing to 2^32.  Returns (uint32
+    [n_rho + n_rho n_theta], cell probabilities as quantised
+    (p_band p_cell|band))."""
     z = np.asarray(logits, np.float64).ravel()
     C_ = n_rho * n_theta
-    q = np.exp(z - z.max())
+    q = np.exp(beta * (z - z.max()))
     q /= q.sum()
     p = ((1 - eps) * q + eps / C_).reshape(n_rho, n_theta)
     Pr = p.sum(axis=1)

@@ -15,6 +15,7 @@ grid of Eq. 4, uniform, importance cells) and coefficient form (Eq. 3).
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import threading
 
@@ -474,14 +475,16 @@ def qrs_mlp_adam(h: Handle, n_cells, params, m, v, grad, lr, step, stream=None):
                _stream(stream)))
 
 
-def qrs_proposal_cdf(h: Handle, n_rho, n_theta, logits_row, eps=0.1, out=None, stream=None):
+def qrs_proposal_cdf(h: Handle, n_rho, n_theta, logits_row, eps=0.1, beta=1.0, out=None, stream=None):
     """Two-level sampling CDF (device int32 view of uint32 [n_rho + n_rho n_theta])
-    from one row of logits [n_rho n_theta]."""
+    from one row of logits [n_rho n_theta]: p = (1 - eps) softmax(beta z) + eps / C."""
     _check_dev(logits_row, torch.float32, "logits_row")
     if out is None:
         out = torch.empty(n_rho * (1 + n_theta), dtype=torch.int32, device=logits_row.device)
-    f = _prop_fn("qrs_proposal_cdf", [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_float, C.c_void_p, C.c_void_p])
-    h._check(f(h.h, int(n_rho), int(n_theta), logits_row.data_ptr(), float(eps), out.data_ptr(), _stream(stream)))
+    f = _prop_fn("qrs_proposal_cdf", [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_float, C.c_float, C.c_void_p,
+                                      C.c_void_p])
+    h._check(f(h.h, int(n_rho), int(n_theta), logits_row.data_ptr(), float(eps), float(beta), out.data_ptr(),
+               _stream(stream)))
     return out
 
 
@@ -504,11 +507,16 @@ class ProposalState:
 
 
 def train_proposal(h: Handle, n_cells, geom, targets, steps=2000, lr=2e-3, seed=0, params=None, stream=None,
-                   log_every=0, state=None, return_state=False):
+                   log_every=0, state=None, return_state=False, schedule="constant", total_steps=None):
     """Adam on the mean cross entropy, full batch; every step is two libqrs calls
-    (loss and gradient, Adam update).  Returns (params, list of (step, loss)),
-    and the ProposalState after the last step when return_state is set; a
-    `state` continues a checkpointed run (same result as an uninterrupted one)."""
+    (loss and gradient, Adam update).  schedule "cosine": step t of a run of
+    total_steps (default: this call's last step) uses lr (1 + cos(pi (t - 1) /
+    total_steps)) / 2.  Returns (params, list of (step, loss)), and the
+    ProposalState after the last step when return_state is set; a `state`
+    continues a checkpointed run (same result as an uninterrupted one when
+    total_steps names the whole run)."""
+    if schedule not in ("constant", "cosine"):
+        raise ValueError("schedule must be 'constant' or 'cosine'")
     if state is not None:
         if state.n_cells != n_cells:
             raise ValueError("checkpoint has %d cells, not %d" % (state.n_cells, n_cells))
@@ -522,9 +530,11 @@ def train_proposal(h: Handle, n_cells, geom, targets, steps=2000, lr=2e-3, seed=
     grad = torch.empty_like(params)
     loss = torch.empty(1, dtype=torch.float32, device=params.device)
     hist = []
+    total = total_steps if total_steps is not None else step0 + steps
     for step in range(step0 + 1, step0 + steps + 1):
+        lr_t = lr if schedule == "constant" else lr * 0.5 * (1.0 + math.cos(math.pi * (step - 1) / total))
         qrs_mlp_loss_grad(h, n_cells, params, geom, targets, grad=grad, loss=loss, stream=stream)
-        qrs_mlp_adam(h, n_cells, params, m, v, grad, lr, step, stream=stream)
+        qrs_mlp_adam(h, n_cells, params, m, v, grad, lr_t, step, stream=stream)
         if log_every and (step % log_every == 0 or step == 1):
             hist.append((step, float(loss.item())))
     if return_state:

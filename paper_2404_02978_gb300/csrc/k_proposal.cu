@@ -314,7 +314,7 @@ __device__ void quantise_scan(const double* x, int n, int stride, double total, 
 // band sums, the marginal CDF (thread 0), the conditional CDFs (one thread
 // per band).  pbuf: C + n_rho doubles of workspace.
 __global__ void __launch_bounds__(1024) k_prop_cdf(const float* __restrict__ z, int n_rho, int n_theta, float eps,
-                                                   uint32_t* __restrict__ cdf, double* __restrict__ pbuf)
+                                                   float beta, uint32_t* __restrict__ cdf, double* __restrict__ pbuf)
 {
     __shared__ float redf[32];
     __shared__ double redd[32];
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(1024) k_prop_cdf(const float* __restrict__ z, 
     for (int c = threadIdx.x; c < C; c += blockDim.x) mx = fmaxf(mx, z[c]);
     mx = block_reduce(mx, redf, true);
     double se = 0.0;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) se += (double)expf(z[c] - mx);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) se += (double)expf(beta * (z[c] - mx));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
     if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = se;
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(1024) k_prop_cdf(const float* __restrict__ z, 
     __syncthreads();
     const double sum = redd[0];
     for (int c = threadIdx.x; c < C; c += blockDim.x)
-        pbuf[c] = (1.0 - (double)eps) * ((double)expf(z[c] - mx) / sum) + (double)eps / (double)C;
+        pbuf[c] = (1.0 - (double)eps) * ((double)expf(beta * (z[c] - mx)) / sum) + (double)eps / (double)C;
     __syncthreads();
     double* band = pbuf + C;
     for (int i = threadIdx.x; i < n_rho; i += blockDim.x) {
@@ -557,7 +557,7 @@ qrs_status qrs_mlp_adam(qrs_handle* h, int32_t n_cells, float* params, float* m,
 }
 
 qrs_status qrs_proposal_cdf(qrs_handle* h, int32_t n_rho, int32_t n_theta, const float* logits, float eps,
-                            uint32_t* cdf, void* stream)
+                            float beta, uint32_t* cdf, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
     qrs::NvtxRange nvtx_range("qrs_proposal_cdf");
@@ -566,12 +566,13 @@ qrs_status qrs_proposal_cdf(qrs_handle* h, int32_t n_rho, int32_t n_theta, const
     const int64_t C = (int64_t)n_rho * n_theta;
     if (n_rho < 1 || n_theta < 1 || !cells_ok((int32_t)C) || !(eps > 0.0f && eps <= 1.0f))
         return fail(h, QRS_ERR_ARG, "n_rho x n_theta in [1, 16384], 0 < eps <= 1");
+    if (!(beta > 0.0f && beta <= 16.0f)) return fail(h, QRS_ERR_ARG, "0 < beta <= 16");
     if (!logits || !cdf) return fail(h, QRS_ERR_ARG, "logits and cdf must be non-NULL");
     qrs_status st = ensure_work(h, (size_t)(C + n_rho) * sizeof(double) + 256);
     if (st != QRS_OK) return st;
     cudaError_t e = cudaSetDevice(h->device);
     if (e == cudaSuccess) {
-        k_prop_cdf<<<1, 1024, 0, (cudaStream_t)stream>>>(logits, n_rho, n_theta, eps, cdf,
+        k_prop_cdf<<<1, 1024, 0, (cudaStream_t)stream>>>(logits, n_rho, n_theta, eps, beta, cdf,
                                                          static_cast<double*>(h->d_work));
         e = cudaGetLastError();
     }

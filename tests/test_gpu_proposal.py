@@ -76,12 +76,13 @@ def test_targets_match_reference(h, kind, fold):
     assert np.max(np.abs(t - ref)) <= 1e-5 + 1e-4 * np.max(ref)
 
 
-def test_cdf_valid_and_close(h):
+@pytest.mark.parametrize("beta", [1.0, 0.8, 2.5])
+def test_cdf_valid_and_close(h, beta):
     rng = np.random.default_rng(9)
     nr, nt = 64, 32
     z = (3.0 * rng.normal(size=C)).astype(np.float32)
-    cdf = qrs.qrs_proposal_cdf(h, nr, nt, _dev(z), 0.1).cpu().numpy().view(np.uint32).astype(np.int64)
-    ref, _ = pr.cdf(z.astype(np.float64), 0.1, nr, nt)
+    cdf = qrs.qrs_proposal_cdf(h, nr, nt, _dev(z), 0.1, beta=beta).cpu().numpy().view(np.uint32).astype(np.int64)
+    ref, _ = pr.cdf(z.astype(np.float64), 0.1, nr, nt, beta=beta)
     ref = ref.astype(np.int64)
     for lo, n in [(0, nr)] + [(nr + i * nt, nt) for i in range(nr)]:
         s, r = cdf[lo:lo + n], ref[lo:lo + n]
@@ -107,20 +108,27 @@ def test_trained_proposal_lowers_structure_function_error(h, fold):
     evaluated on 48 held-out ones: RMS relative error of the per-draw SF at
     the geometry's baseline vs the analytic Hankel integral.  The learned
     importance draw at N_f beats the plain draw at N_f by >= 1.8x for
-    N_f = 256, 512, 1024, and at 1024 beats the plain draw at 2048.  fold 4:
-    cells in the baseline frame over four mirrored sectors."""
+    N_f = 256, 512, 1024, and at 1024 beats the plain draw at 2048.  fold 4
+    (cells in the baseline frame over four mirrored sectors, the density
+    tempered by beta = 0.8, 8000 cosine-scheduled steps): the learned draw at
+    256 terms also comes within 1.3x of the plain draw's error at 1024."""
     from oracle import analytic as an
     gtr, gte = _geom(2000, 1), _geom(48, 2)
-    T = qrs.qrs_proposal_targets(h, qrs.params(**DOM), 64, 32, 77, 4096, 256, _dev(gtr, torch.float64), kind="rms",
-                                 fold=fold)
-    P, hist = qrs.train_proposal(h, C, _dev(gtr, torch.float64), T, steps=3000, lr=2e-3, seed=3, log_every=1000)
+    T = qrs.qrs_proposal_targets(h, qrs.params(**DOM), 64, 32, 77, 4096, 1024 if fold else 256,
+                                 _dev(gtr, torch.float64), kind="rms", fold=fold)
+    if fold:
+        P, hist = qrs.train_proposal(h, C, _dev(gtr, torch.float64), T, steps=8000, lr=4e-3, seed=3, log_every=1000,
+                                     schedule="cosine")
+    else:
+        P, hist = qrs.train_proposal(h, C, _dev(gtr, torch.float64), T, steps=3000, lr=2e-3, seed=3, log_every=1000)
+    beta = 0.8 if fold else 1.0
     assert hist[-1][1] < hist[0][1] - 1.5
     logits = qrs.qrs_mlp_forward(h, C, P, _dev(gte, torch.float64))
     err = {}
     for i, (r0, L0, D, Bx, By) in enumerate(gte):
         Dref = an.piston_sf(np.hypot(Bx, By), r0, L0, D, 0.0, 1e-3, 10.0)
         p = qrs.params(r0=r0, L0=L0, seed=1000 + i, **DOM)
-        cdf = qrs.qrs_proposal_cdf(h, 64, 32, logits[i].contiguous(), 0.05)
+        cdf = qrs.qrs_proposal_cdf(h, 64, 32, logits[i].contiguous(), 0.05, beta=beta)
         pi = dict(p, sampler="importance", n_rho=64, n_theta=32, cdf=cdf, fold=fold,
                   frame=float(np.arctan2(By, Bx) / (2 * np.pi)) if fold else 0.0)
         for name, pp, nfs in (("plain", p, (256, 512, 1024, 2048)), ("learned", pi, (256, 512, 1024))):
@@ -133,6 +141,8 @@ def test_trained_proposal_lowers_structure_function_error(h, fold):
     for nf in (256, 512, 1024):
         assert rms[("learned", nf)] * 1.8 <= rms[("plain", nf)]
     assert rms[("learned", 1024)] < rms[("plain", 2048)]
+    if fold:
+        assert rms[("learned", 256)] <= 1.3 * rms[("plain", 1024)]
 
 
 def test_training_checkpoint_resumes_exactly(h, tmp_path):

@@ -87,6 +87,21 @@ def test_cdf_valid_uniform_and_floor():
         assert np.allclose(pu, 1.0 / C, rtol=1e-6)
 
 
+def test_cdf_temperature_vs_scipy_softmax():
+    """p = (1 - eps) softmax(beta z) + eps / C against scipy's softmax of the
+    scaled logits, to the quantisation (2^-32 per level); beta -> 0 is uniform."""
+    from scipy.special import softmax
+    rng = np.random.default_rng(4)
+    nr, nt = 8, 16
+    z = rng.normal(scale=3.0, size=nr * nt)
+    for beta in (0.5, 0.8, 2.0):
+        _, pq = pr.cdf(z, 0.05, nr, nt, beta=beta)
+        p = 0.95 * softmax(beta * z) + 0.05 / z.size
+        assert np.allclose(pq.ravel(), p, rtol=1e-7, atol=1e-9)
+    _, pu = pr.cdf(z, 0.05, nr, nt, beta=1e-9)
+    assert np.allclose(pu, 1.0 / z.size, rtol=1e-6)
+
+
 def test_he_init_statistics():
     C = 2048
     P = pr.init(C, 11)
