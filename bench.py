@@ -38,6 +38,11 @@ sys.path.insert(0, HERE)
 MEASURED_PEAKS = os.path.join(HERE, "MEASURED_PEAKS.json")
 N_SM = 152
 MUFU_PER_SM_CLK = 16  # sin.approx / cos.approx results per SM per clock (measured, GB300)
+FMA_PER_SM_CLK = 128  # FP32 FMA lanes per SM per clock
+# FP32-pipe operations per aperture-term unit of the piston path that the method needs: the
+# phase f.x (2) and its double-float reduction (7), the accumulation (2), the Eq. 7 filter
+# (11-term series by Horner below x = 4: 12) and its product with the two coefficients (2).
+PISTON_FMA_OPS = 25
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq-term evals/s"
@@ -147,12 +152,39 @@ def cpu_baseline(cfg, p, xy, n_real=2, gpu_rows=None):
            "sample": "%d of %d realisations, all %d points, N_f=%d (%.3g terms in %.1f s), single thread FP64"
                      % (n_real, cfg["n_real"], xy.shape[0], cfg["n_f"], terms, dt),
            "host": _host()}
+    try:
+        res["all_cores"] = cpu_all_cores(cfg, p, xy, first=n_real)
+    except Exception as e:  # the single-thread figure above stands on its own
+        res["all_cores"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if gpu_rows is not None:
         sig = np.sqrt(np.sum(oracle.draw(p, n_f=cfg["n_f"], n_real=n_real)["F"] ** 2, axis=1))
         err = np.abs(np.asarray(gpu_rows, np.float64) - ref) / sig[:, None]
         res["gpu_error_vs_fp64"] = {"max_sigma": float(err.max()), "rms_sigma": float(np.sqrt(np.mean(err ** 2))),
                                     "values": int(err.size), "tolerance_sigma": 1e-5}
     return res
+
+
+def cpu_all_cores(cfg, p, xy, first):
+    """The same oracle, one realisation per process on every host core (a
+    spawn pool: the parent already holds a CUDA context), on realisations
+    first .. first + cores - 1."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    import oracle
+    cores = os.cpu_count() or 1
+    # an executor, not a Pool: a worker that dies raises here instead of being respawned forever
+    with ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
+        for f in [ex.submit(oracle.synthesize, p, 8, 1, xy[:64], 0) for _ in range(cores)]:
+            f.result(timeout=120)  # workers up, library loaded
+        t0 = time.perf_counter()
+        fs = [ex.submit(oracle.synthesize, p, cfg["n_f"], 1, xy, first + i) for i in range(cores)]
+        for f in fs:
+            f.result(timeout=600)
+        dt = time.perf_counter() - t0
+    terms = cores * xy.shape[0] * cfg["n_f"]
+    return {"value": terms / dt, "unit": UNIT, "cores": cores,
+            "sample": "%d realisations (one per process), all %d points, N_f=%d (%.3g terms in %.1f s), FP64"
+                      % (cores, xy.shape[0], cfg["n_f"], terms, dt)}
 
 
 def _host():
@@ -443,11 +475,19 @@ def measure_batched(qrs, h, torch, dev):
         qrs.qrs_sync(h, stream)
         ms.append(e0.elapsed_time(e1))
     t = min(ms) / 1e3
+    mufu = N_SM * MUFU_PER_SM_CLK / 2 * SM_MAX_MHZ * 1e6
+    fma = N_SM * FMA_PER_SM_CLK / PISTON_FMA_OPS * SM_MAX_MHZ * 1e6
+    peak = min(mufu, fma)
     return {"workload": "1000 interferometers, n_ap 4-64, N_f 256-8192, 256 realisations, all pairs "
                         "(%d aperture-term-realisation units, %d pair values)" % (units, pairs),
             "ms_per_launch": t * 1e3, "value": units / t, "unit": "aperture-term evals/s",
             "pairs_per_s": pairs / t, "launch": "one persistent graph-captured kernel, autotuned shape",
-            "gpu_launches_first_call": h.launch_count() - launches0 - 3}
+            "gpu_launches_first_call": h.launch_count() - launches0 - 3,
+            "roofline": {"bound": "alu", "achieved": units / t / 1e9, "peak": peak / 1e9, "unit": "Gunit/s",
+                         "frac": units / t / peak, "kernel": "k_piston_persistent",
+                         "peak_basis": "min(2 MUFU per unit: %.0f, %d FP32-pipe ops per unit at 128 per SM-clock: "
+                                       "%.0f) Gunit/s at %.0f MHz" % (mufu / 1e9, PISTON_FMA_OPS, fma / 1e9,
+                                                                       SM_MAX_MHZ)}}
 
 
 def hankel_piston_sf(B, r0, L0, D, fmin, fmax):
@@ -648,6 +688,8 @@ def run_ours(a):
     }
     if clk:
         line["clocks"] = clk
+        # the same fraction against the bound at the SM clock sampled during the timed steps
+        line["roofline"]["frac_at_sampled_clock"] = achieved / (peak_terms * clk["sm_mhz"] / sm_max)
     if world == 1 and not a.headline_only:
         peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
         line["other_forms"] = {m: measure_gemm(qrs, h, torch, dev, m, peaks) for m in ("gemm_3xtf32", "gemm_bf16x3")}
