@@ -64,6 +64,28 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
+// One (aperture, slice) unit: the lanes split the slice's terms [k0, k_end)
+// (in bucket order through sidx when SORTED); the filter's obstruction term
+// only when OBST.  Both are uniform per unit, so they select a loop instead
+// of being tested per term.
+template <bool SORTED, bool OBST, int SLICES>
+__device__ __forceinline__ float unit_sum(const PisShared<SLICES>& sh, int k0, int k_end, float x, float y, float D,
+                                          float d, float wD, float wd)
+{
+    float acc = 0.0f;
+    for (int k = k0; k < k_end; k += 32) {
+        const int j = SORTED ? (int)sh.sidx[k] : k;
+        const float4 T = sh.rec[j];
+        const float fa = sh.fabs_[j];
+        const float A = OBST ? airy_filter_w(fa, D, d, wD, wd) : airy_g(3.14159265358979f * fa * D);
+        float s, c;
+        sincos_turns(phase_df(T.x, T.y, x, y), s, c);
+        acc = fmaf(A * T.z, c, acc);
+        acc = fmaf(A * T.w, s, acc);
+    }
+    return acc;
+}
+
 template <class S>
 __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlices>& sh, int* err)
 {
@@ -154,16 +176,14 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             const int a = u / n_sl, sl = u - (u / n_sl) * n_sl;
             const float x = sh.apx[a], y = sh.apy[a], D = sh.apD[a], d = sh.apd[a];
             const float wD = sh.apwD[a], wd = sh.apwd[a];
-            const int k_end = min(len, (sl + 1) * kPisSlice);
-            float acc = 0.0f;
-            for (int k = sl * kPisSlice + lane; k < k_end; k += 32) {
-                const int j = sorted ? (int)sh.sidx[k] : k;
-                const float4 T = sh.rec[j];
-                const float A = airy_filter_w(sh.fabs_[j], D, d, wD, wd);
-                float s, c;
-                sincos_turns(phase_df(T.x, T.y, x, y), s, c);
-                acc = fmaf(A * T.z, c, acc);
-                acc = fmaf(A * T.w, s, acc);
+            const int k0 = sl * kPisSlice + lane, k_end = min(len, (sl + 1) * kPisSlice);
+            float acc;
+            if (sorted) {
+                acc = d > 0.0f ? unit_sum<true, true>(sh, k0, k_end, x, y, D, d, wD, wd)
+                               : unit_sum<true, false>(sh, k0, k_end, x, y, D, d, wD, wd);
+            } else {
+                acc = d > 0.0f ? unit_sum<false, true>(sh, k0, k_end, x, y, D, d, wD, wd)
+                               : unit_sum<false, false>(sh, k0, k_end, x, y, D, d, wD, wd);
             }
             acc = warp_sum_f(acc);
             if (lane == 0) sh.part[a][sl] = acc;
