@@ -86,6 +86,29 @@ __device__ __forceinline__ float unit_sum(const PisShared<SLICES>& sh, int k0, i
     return acc;
 }
 
+// Two unobstructed apertures per unit: one pass over the terms, the record,
+// |f| and index loads and the loop control shared, two independent chains.
+template <bool SORTED, int SLICES>
+__device__ __forceinline__ void unit_sum2(const PisShared<SLICES>& sh, int k0, int k_end, float x0, float y0, float D0,
+                                          float x1, float y1, float D1, float& acc0, float& acc1)
+{
+    acc0 = 0.0f;
+    acc1 = 0.0f;
+    for (int k = k0; k < k_end; k += 32) {
+        const int j = SORTED ? (int)sh.sidx[k] : k;
+        const float4 T = sh.rec[j];
+        const float piF = 3.14159265358979f * sh.fabs_[j];
+        const float A0 = airy_g(piF * D0), A1 = airy_g(piF * D1);
+        float s0, c0, s1, c1;
+        sincos_turns(phase_df(T.x, T.y, x0, y0), s0, c0);
+        sincos_turns(phase_df(T.x, T.y, x1, y1), s1, c1);
+        acc0 = fmaf(A0 * T.z, c0, acc0);
+        acc0 = fmaf(A0 * T.w, s0, acc0);
+        acc1 = fmaf(A1 * T.z, c1, acc1);
+        acc1 = fmaf(A1 * T.w, s1, acc1);
+    }
+}
+
 template <class S>
 __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlices>& sh, int* err)
 {
@@ -170,23 +193,44 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             }
             __syncthreads();
         }
+        // units: (pair of apertures 2q, 2q + 1, slice); a lone last aperture
+        // or an obstructed one runs on its own
         const int n_sl = (len + kPisSlice - 1) / kPisSlice;
-        const int units = n_ap * n_sl;
+        const int units = ((n_ap + 1) >> 1) * n_sl;
         for (int u = warp; u < units; u += kPisWarps) {
-            const int a = u / n_sl, sl = u - (u / n_sl) * n_sl;
-            const float x = sh.apx[a], y = sh.apy[a], D = sh.apD[a], d = sh.apd[a];
-            const float wD = sh.apwD[a], wd = sh.apwd[a];
+            const int q = u / n_sl, sl = u - q * n_sl;
+            const int a0 = 2 * q, a1 = 2 * q + 1;
             const int k0 = sl * kPisSlice + lane, k_end = min(len, (sl + 1) * kPisSlice);
-            float acc;
-            if (sorted) {
-                acc = d > 0.0f ? unit_sum<true, true>(sh, k0, k_end, x, y, D, d, wD, wd)
-                               : unit_sum<true, false>(sh, k0, k_end, x, y, D, d, wD, wd);
-            } else {
-                acc = d > 0.0f ? unit_sum<false, true>(sh, k0, k_end, x, y, D, d, wD, wd)
-                               : unit_sum<false, false>(sh, k0, k_end, x, y, D, d, wD, wd);
+            if (a1 < n_ap && sh.apd[a0] <= 0.0f && sh.apd[a1] <= 0.0f) {
+                float acc0, acc1;
+                if (sorted)
+                    unit_sum2<true>(sh, k0, k_end, sh.apx[a0], sh.apy[a0], sh.apD[a0], sh.apx[a1], sh.apy[a1],
+                                    sh.apD[a1], acc0, acc1);
+                else
+                    unit_sum2<false>(sh, k0, k_end, sh.apx[a0], sh.apy[a0], sh.apD[a0], sh.apx[a1], sh.apy[a1],
+                                     sh.apD[a1], acc0, acc1);
+                acc0 = warp_sum_f(acc0);
+                acc1 = warp_sum_f(acc1);
+                if (lane == 0) {
+                    sh.part[a0][sl] = acc0;
+                    sh.part[a1][sl] = acc1;
+                }
+                continue;
             }
-            acc = warp_sum_f(acc);
-            if (lane == 0) sh.part[a][sl] = acc;
+            for (int a = a0; a <= a1 && a < n_ap; ++a) {
+                const float x = sh.apx[a], y = sh.apy[a], D = sh.apD[a], d = sh.apd[a];
+                const float wD = sh.apwD[a], wd = sh.apwd[a];
+                float acc;
+                if (sorted) {
+                    acc = d > 0.0f ? unit_sum<true, true>(sh, k0, k_end, x, y, D, d, wD, wd)
+                                   : unit_sum<true, false>(sh, k0, k_end, x, y, D, d, wD, wd);
+                } else {
+                    acc = d > 0.0f ? unit_sum<false, true>(sh, k0, k_end, x, y, D, d, wD, wd)
+                                   : unit_sum<false, false>(sh, k0, k_end, x, y, D, d, wD, wd);
+                }
+                acc = warp_sum_f(acc);
+                if (lane == 0) sh.part[a][sl] = acc;
+            }
         }
         __syncthreads();
         for (int a = tid; a < n_ap; a += kPisTPB) {
