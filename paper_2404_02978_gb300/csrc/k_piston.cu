@@ -25,6 +25,10 @@ constexpr int kPisChunk = 2048;  // terms per shared-memory chunk
 constexpr int kPisBuckets = 64;  // |f| buckets of the per-chunk counting sort (8 per octave)
 constexpr int kPisSortMinAp = 8; // items with at least this many apertures sort their chunks
 constexpr int kPisMaxWarps = 8;
+#ifndef QRS_PISTON_GROUP
+#define QRS_PISTON_GROUP 4
+#endif
+constexpr int kPisGroup = QRS_PISTON_GROUP;  // apertures sharing one pass over a slice's terms
 
 // Kernel shapes the autotuner chooses from: threads per CTA and terms per
 // (aperture, slice) unit.
@@ -86,26 +90,31 @@ __device__ __forceinline__ float unit_sum(const PisShared<SLICES>& sh, int k0, i
     return acc;
 }
 
-// Two unobstructed apertures per unit: one pass over the terms, the record,
-// |f| and index loads and the loop control shared, two independent chains.
-template <bool SORTED, int SLICES>
-__device__ __forceinline__ void unit_sum2(const PisShared<SLICES>& sh, int k0, int k_end, float x0, float y0, float D0,
-                                          float x1, float y1, float D1, float& acc0, float& acc1)
+// NA unobstructed apertures per unit: one pass over the terms, the record,
+// |f| and index loads and the loop control shared, NA independent chains.
+template <bool SORTED, int NA, int SLICES>
+__device__ __forceinline__ void unit_sum_n(const PisShared<SLICES>& sh, int k0, int k_end, int a0, float (&acc)[NA])
 {
-    acc0 = 0.0f;
-    acc1 = 0.0f;
+    float x[NA], y[NA], D[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+        x[i] = sh.apx[a0 + i];
+        y[i] = sh.apy[a0 + i];
+        D[i] = sh.apD[a0 + i];
+        acc[i] = 0.0f;
+    }
     for (int k = k0; k < k_end; k += 32) {
         const int j = SORTED ? (int)sh.sidx[k] : k;
         const float4 T = sh.rec[j];
         const float piF = 3.14159265358979f * sh.fabs_[j];
-        const float A0 = airy_g(piF * D0), A1 = airy_g(piF * D1);
-        float s0, c0, s1, c1;
-        sincos_turns(phase_df(T.x, T.y, x0, y0), s0, c0);
-        sincos_turns(phase_df(T.x, T.y, x1, y1), s1, c1);
-        acc0 = fmaf(A0 * T.z, c0, acc0);
-        acc0 = fmaf(A0 * T.w, s0, acc0);
-        acc1 = fmaf(A1 * T.z, c1, acc1);
-        acc1 = fmaf(A1 * T.w, s1, acc1);
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            const float A = airy_g(piF * D[i]);
+            float s, c;
+            sincos_turns(phase_df(T.x, T.y, x[i], y[i]), s, c);
+            acc[i] = fmaf(A * T.z, c, acc[i]);
+            acc[i] = fmaf(A * T.w, s, acc[i]);
+        }
     }
 }
 
@@ -193,27 +202,24 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             }
             __syncthreads();
         }
-        // units: (pair of apertures 2q, 2q + 1, slice); a lone last aperture
-        // or an obstructed one runs on its own
+        // units: (group of kPisGroup apertures, slice); a group with an
+        // obstructed aperture, or the short last group, runs aperture by aperture
         const int n_sl = (len + kPisSlice - 1) / kPisSlice;
-        const int units = ((n_ap + 1) >> 1) * n_sl;
+        const int units = ((n_ap + kPisGroup - 1) / kPisGroup) * n_sl;
         for (int u = warp; u < units; u += kPisWarps) {
             const int q = u / n_sl, sl = u - q * n_sl;
-            const int a0 = 2 * q, a1 = 2 * q + 1;
+            const int a0 = kPisGroup * q, a1 = a0 + kPisGroup - 1;
             const int k0 = sl * kPisSlice + lane, k_end = min(len, (sl + 1) * kPisSlice);
-            if (a1 < n_ap && sh.apd[a0] <= 0.0f && sh.apd[a1] <= 0.0f) {
-                float acc0, acc1;
-                if (sorted)
-                    unit_sum2<true>(sh, k0, k_end, sh.apx[a0], sh.apy[a0], sh.apD[a0], sh.apx[a1], sh.apy[a1],
-                                    sh.apD[a1], acc0, acc1);
-                else
-                    unit_sum2<false>(sh, k0, k_end, sh.apx[a0], sh.apy[a0], sh.apD[a0], sh.apx[a1], sh.apy[a1],
-                                     sh.apD[a1], acc0, acc1);
-                acc0 = warp_sum_f(acc0);
-                acc1 = warp_sum_f(acc1);
-                if (lane == 0) {
-                    sh.part[a0][sl] = acc0;
-                    sh.part[a1][sl] = acc1;
+            bool plain = a1 < n_ap;
+            for (int a = a0; plain && a <= a1; ++a) plain = sh.apd[a] <= 0.0f;
+            if (plain) {
+                float acc[kPisGroup];
+                if (sorted) unit_sum_n<true>(sh, k0, k_end, a0, acc);
+                else unit_sum_n<false>(sh, k0, k_end, a0, acc);
+#pragma unroll
+                for (int i = 0; i < kPisGroup; ++i) {
+                    const float v = warp_sum_f(acc[i]);
+                    if (lane == 0) sh.part[a0 + i][sl] = v;
                 }
                 continue;
             }
