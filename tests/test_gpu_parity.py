@@ -214,6 +214,43 @@ def test_piston_annular_and_mixed_diameters(h):
     assert np.abs(dlt.cpu().numpy() - dlt_ref).max() <= 2 * TOL_FIELD * scale
 
 
+@pytest.mark.parametrize("flags", [0, qrs.PISTON_PERSISTENT | qrs.PISTON_GRAPH])
+def test_piston_with_learned_cells(h, flags):
+    """Pistons from importance draws in a baseline's frame folded over four
+    mirrored sectors (the learned proposal's use): 9 apertures, so groups of
+    four and a lone one, one of them obstructed (its group runs aperture by
+    aperture); per value within 1e-5 of the value's piston sigma."""
+    rng = np.random.default_rng(12)
+    n_ap, nr, nt = 9, 16, 8
+    ap_xy = rng.uniform(-90, 90, size=(n_ap, 2)).astype(np.float32)
+    ap_D = rng.uniform(1.8, 8, size=n_ap).astype(np.float32)
+    ap_d = np.zeros(n_ap, np.float32)
+    ap_d[6] = 1.1
+    pairs = wl.all_pairs(n_ap)
+    cdf = _cdf(nr, nt, 13)
+    B = ap_xy[1] - ap_xy[0]
+    p = oracle.params(seed=47, r0=0.1, L0=25.0, fmin=1e-3, fmax=10.0, sampler="importance", n_rho=nr, n_theta=nt,
+                      cdf=cdf, fold=4, frame=float(np.arctan2(B[1], B[0]) / (2 * np.pi)))
+    R, n_f, off = 5, 700, 3
+    pis_ref, dlt_ref = oracle.diff_piston(p, n_f, R, ap_xy, ap_D, ap_d, pairs, real_offset=off)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    pis = torch.empty(R, n_ap, device="cuda")
+    dlt = torch.empty(R, pairs.shape[0], device="cuda")
+    cdf_dev = dev(cdf.view(np.int32))  # referenced until the launch has finished
+    job = qrs.piston_job(_gp(p, cdf_dev), n_f, R, dev(ap_xy), dev(ap_D), dev(ap_d), dev(pairs), pis, dlt,
+                         real_offset=off)
+    qrs.qrs_diff_piston(h, [job], flags=flags)
+    qrs.qrs_sync(h)
+    from oracle import analytic as an
+    d = oracle.draw(p, n_f=n_f, n_real=R, real_offset=off)
+    f = np.hypot(d["f"][..., 0].astype(np.float64), d["f"][..., 1].astype(np.float64))
+    A = np.stack([an.airy(f.ravel(), D, dd).reshape(f.shape) for D, dd in zip(ap_D, ap_d)], -1)
+    sig = np.sqrt(np.einsum("rk,rka->ra", d["F"] ** 2, A ** 2))
+    assert np.all(np.abs(pis.cpu().numpy() - pis_ref) <= TOL_FIELD * sig)
+    sig_pair = np.sqrt(sig[:, pairs[:, 0]] ** 2 + sig[:, pairs[:, 1]] ** 2)
+    assert np.all(np.abs(dlt.cpu().numpy() - dlt_ref) <= TOL_FIELD * sig_pair)
+
+
 def test_structure_fn_parity(h):
     rng = np.random.default_rng(6)
     x = rng.normal(size=(37, 5, 300)).astype(np.float32)
