@@ -41,6 +41,9 @@ namespace qrs {
 #ifndef QRS_SYNTH_FOLD
 #define QRS_SYNTH_FOLD 1     // 1: fixed-point turns -> radians in one FFMA
 #endif
+#ifndef QRS_SYNTH_PAIRED
+#define QRS_SYNTH_PAIRED 1   // 1: paired FP32 instructions (two points per FFMA2) where they apply
+#endif
 
 constexpr int kSynthTPB = 256;
 constexpr int kSynthPPT = QRS_SYNTH_PPT;
@@ -75,6 +78,51 @@ cudaError_t launch_point_bound(const float* xy, int64_t n_points, float* d_bound
 {
     k_point_bound<<<1, 1024, 0, s>>>(reinterpret_cast<const float2*>(xy), n_points, d_bound);
     return cudaGetLastError();
+}
+
+// The fixed-point path with paired FP32 instructions (FFMA2, two points per
+// instruction): the turn-to-radian conversion and the two accumulating FMAs
+// of points 2i and 2i + 1 share one instruction each.  Each element is
+// rounded exactly as the scalar fmaf would round it, so the sums are the
+// scalar path's bit for bit.
+__device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restrict__ st, int len,
+                                                           const int32_t (&X)[kSynthPPT], const int32_t (&Y)[kSynthPPT],
+                                                           float (&acc)[kSynthPPT], const FixedScales& z)
+{
+    static_assert(kSynthPPT % 2 == 0, "points in pairs");
+    constexpr int NP = kSynthPPT / 2;
+    const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
+    const float2 neg_two_pi = make_float2(-6.28318530717958648f, -6.28318530717958648f);
+    for (int k0 = 0; k0 < len; k0 += kSynthGroup) {
+        const int k1 = min(k0 + kSynthGroup, len);
+        float2 part[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) part[q] = make_float2(0.0f, 0.0f);
+#pragma unroll kSynthUnroll
+        for (int k = k0; k < k1; ++k) {
+            const float4 T = st[k];
+            const float2 A = make_float2(T.z, T.z), nB = make_float2(T.w, T.w);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const uint32_t m0 = phase_fx_word(__float_as_int(T.x), __float_as_int(T.y), X[2 * q], Y[2 * q],
+                                                  z.bias, z.shift);
+                const uint32_t m1 = phase_fx_word(__float_as_int(T.x), __float_as_int(T.y), X[2 * q + 1],
+                                                  Y[2 * q + 1], z.bias, z.shift);
+                const float2 mant = make_float2(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u),
+                                                __uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u));
+                const float2 ang = __ffma2_rn(mant, two_pi, neg_two_pi);  // (1 + t) 2 pi - 2 pi
+                const float2 c = make_float2(__cosf(ang.x), __cosf(ang.y));
+                const float2 sn = make_float2(__sinf(ang.x), __sinf(ang.y));
+                part[q] = __ffma2_rn(A, c, part[q]);
+                part[q] = __ffma2_rn(nB, sn, part[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            acc[2 * q] += part[q].x;
+            acc[2 * q + 1] += part[q].y;
+        }
+    }
 }
 
 template <bool FIXED>
@@ -168,8 +216,15 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
                 cached_r = r;
                 cached_c = c;
             }
-            if (z.use_fixed) accumulate_chunk<true>(sterm, len, X, Y, acc, z);
-            else accumulate_chunk<false>(sterm, len, X, Y, acc, z);
+            if (z.use_fixed) {
+#if QRS_SYNTH_PAIRED && QRS_SYNTH_FOLD
+                accumulate_chunk_fx_paired(sterm, len, X, Y, acc, z);
+#else
+                accumulate_chunk<true>(sterm, len, X, Y, acc, z);
+#endif
+            } else {
+                accumulate_chunk<false>(sterm, len, X, Y, acc, z);
+            }
         }
         float* o = out + r * P;
 #pragma unroll

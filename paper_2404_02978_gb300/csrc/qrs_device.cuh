@@ -587,12 +587,20 @@ __device__ __forceinline__ float phase_fx(int32_t Fx, int32_t Fy, int32_t X, int
 // m in [1, 2) holds 1 + frac(turns), and one FFMA forms m 2pi - 2pi =
 // (m - 1) 2pi with the rounded constant cancelling exactly; error: the
 // 2^-24-turn extraction rounding plus one FP32 rounding of the angle.
-__device__ __forceinline__ float phase_fx_rad(int32_t Fx, int32_t Fy, int32_t X, int32_t Y, uint64_t bias,
-                                              uint32_t shift)
+// The 32-bit word whose low 23 bits are frac(f.x) in units of 2^-23 turn
+// (rounded by `bias`): the extraction step of phase_fx_rad.
+__device__ __forceinline__ uint32_t phase_fx_word(int32_t Fx, int32_t Fy, int32_t X, int32_t Y, uint64_t bias,
+                                                  uint32_t shift)
 {
     uint64_t acc = bias + (uint64_t)((int64_t)Fy * (int64_t)Y);
     acc += (uint64_t)((int64_t)Fx * (int64_t)X);
-    const uint32_t m = __funnelshift_rc((uint32_t)acc, (uint32_t)(acc >> 32), shift);
+    return __funnelshift_rc((uint32_t)acc, (uint32_t)(acc >> 32), shift);
+}
+
+__device__ __forceinline__ float phase_fx_rad(int32_t Fx, int32_t Fy, int32_t X, int32_t Y, uint64_t bias,
+                                              uint32_t shift)
+{
+    const uint32_t m = phase_fx_word(Fx, Fy, X, Y, bias, shift);
     return fmaf(__int_as_float((m & 0x007FFFFFu) | 0x3F800000u), 6.28318530717958648f, -6.28318530717958648f);
 }
 
