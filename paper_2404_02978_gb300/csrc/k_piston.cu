@@ -29,6 +29,9 @@ constexpr int kPisMaxWarps = 8;
 #define QRS_PISTON_GROUP 4
 #endif
 constexpr int kPisGroup = QRS_PISTON_GROUP;  // apertures sharing one pass over a slice's terms
+#ifndef QRS_PISTON_PAIRED
+#define QRS_PISTON_PAIRED 1  // 1: the group's apertures in pairs through paired FP32 instructions
+#endif
 
 // Kernel shapes the autotuner chooses from: threads per CTA and terms per
 // (aperture, slice) unit.
@@ -103,6 +106,52 @@ __device__ __forceinline__ void unit_sum_n(const PisShared<SLICES>& sh, int k0, 
         D[i] = sh.apD[a0 + i];
         acc[i] = 0.0f;
     }
+#if QRS_PISTON_PAIRED
+    // apertures in pairs: one paired FP32 instruction (FFMA2 / FMUL2 / FADD2)
+    // does both apertures' step, rounded as the scalar one
+    static_assert(NA % 2 == 0, "apertures in pairs");
+    constexpr int NP = NA / 2;
+    float2 x2[NP], y2[NP], D2[NP], acc2[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        x2[q] = make_float2(x[2 * q], x[2 * q + 1]);
+        y2[q] = make_float2(y[2 * q], y[2 * q + 1]);
+        D2[q] = make_float2(D[2 * q], D[2 * q + 1]);
+        acc2[q] = make_float2(0.0f, 0.0f);
+    }
+    const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
+    const float2 quarter = make_float2(0.25f, 0.25f);
+    for (int k = k0; k < k_end; k += 32) {
+        const int j = SORTED ? (int)sh.sidx[k] : k;
+        const float4 T = sh.rec[j];
+        const float piF = 3.14159265358979f * sh.fabs_[j];
+        const float2 PF = make_float2(piF, piF), Tz = make_float2(T.z, T.z), Tw = make_float2(T.w, T.w);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            const float2 xx = __fmul2_rn(PF, D2[q]);
+            float2 A;
+            if (xx.x < 4.0f && xx.y < 4.0f) {  // both on the series branch of airy_g
+                constexpr AiryCoef K;
+                const float2 u = __fmul2_rn(__fmul2_rn(quarter, xx), xx);
+                A = make_float2(K.c[10], K.c[10]);
+#pragma unroll
+                for (int m = 9; m >= 0; --m) A = __ffma2_rn(A, u, make_float2(K.c[m], K.c[m]));
+            } else {
+                A = make_float2(airy_g(xx.x), airy_g(xx.y));
+            }
+            const float2 ang = __fmul2_rn(phase_df2(T.x, T.y, x2[q], y2[q]), two_pi);
+            const float2 c = make_float2(__cosf(ang.x), __cosf(ang.y));
+            const float2 sn = make_float2(__sinf(ang.x), __sinf(ang.y));
+            acc2[q] = __ffma2_rn(__fmul2_rn(A, Tz), c, acc2[q]);
+            acc2[q] = __ffma2_rn(__fmul2_rn(A, Tw), sn, acc2[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        acc[2 * q] = acc2[q].x;
+        acc[2 * q + 1] = acc2[q].y;
+    }
+#else
     for (int k = k0; k < k_end; k += 32) {
         const int j = SORTED ? (int)sh.sidx[k] : k;
         const float4 T = sh.rec[j];
@@ -116,6 +165,7 @@ __device__ __forceinline__ void unit_sum_n(const PisShared<SLICES>& sh, int k0, 
             acc[i] = fmaf(A * T.w, s, acc[i]);
         }
     }
+#endif
 }
 
 template <class S>

@@ -568,6 +568,22 @@ __device__ __forceinline__ float phase_df(float fx, float fy, float x, float y)
     return __fadd_rn(r, __fadd_rn(e1, e2));
 }
 
+// phase_df for two positions at once (x.x, y.x) and (x.y, y.y), in paired FP32
+// instructions; each element is rounded exactly as in phase_df.
+__device__ __forceinline__ float2 phase_df2(float fx, float fy, float2 x, float2 y)
+{
+    const float2 FX = make_float2(fx, fx), FY = make_float2(fy, fy);
+    const float2 M = make_float2(12582912.0f, 12582912.0f), NM = make_float2(-12582912.0f, -12582912.0f);
+    const float2 p1 = __fmul2_rn(FX, x);
+    const float2 e1 = __ffma2_rn(FX, x, make_float2(-p1.x, -p1.y));
+    const float2 p2 = __fmul2_rn(FY, y);
+    const float2 e2 = __ffma2_rn(FY, y, make_float2(-p2.x, -p2.y));
+    const float2 n1 = __fadd2_rn(__fadd2_rn(p1, M), NM);
+    const float2 n2 = __fadd2_rn(__fadd2_rn(p2, M), NM);
+    const float2 r = __fadd2_rn(__fadd2_rn(p1, make_float2(-n1.x, -n1.y)), __fadd2_rn(p2, make_float2(-n2.x, -n2.y)));
+    return __fadd2_rn(r, __fadd2_rn(e1, e2));
+}
+
 // Fixed-point reduction: f and x quantised to int32 at per-launch binary
 // scales 2^a and 2^b (|F|, |X| < 2^31), phi 2^(a+b) = Fx X + Fy Y computed
 // exactly in 64-bit wraparound arithmetic (the integer part falls off the
