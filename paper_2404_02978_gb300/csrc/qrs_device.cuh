@@ -137,6 +137,8 @@ struct AiryCoef {
 // the cosine is taken in turns, x / (2 pi) - 3/8 + t1 / (2 pi) reduced mod 1,
 // so arguments in the hundreds keep their accuracy.  Both branches are short,
 // so warps whose lanes straddle x = 4 stay cheap.
+__device__ __forceinline__ float airy_g_large(float x);
+
 __device__ __forceinline__ float airy_g(float x)
 {
     if (x < 4.0f) {
@@ -147,6 +149,12 @@ __device__ __forceinline__ float airy_g(float x)
         for (int m = 9; m >= 0; --m) s = fmaf(s, u, K.c[m]);
         return s;
     }
+    return airy_g_large(x);
+}
+
+// The large-argument branch of airy_g (x >= 4).
+__device__ __forceinline__ float airy_g_large(float x)
+{
     const float z = __fdividef(3.0f, x);
     const float f1 = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(-0.00020033f, z, 0.00113653f), z, -0.00249511f), z, 0.00017105f), z,
                                     0.01659667f), z, 0.00000156f), z, 0.79788456f);
@@ -569,19 +577,24 @@ __device__ __forceinline__ float phase_df(float fx, float fy, float x, float y)
 }
 
 // phase_df for two positions at once (x.x, y.x) and (x.y, y.y), in paired FP32
-// instructions; each element is rounded exactly as in phase_df.
+// instructions, without a negation of a pair: the product errors are formed
+// negated (fma(-f, x, p) = -fma(f, x, -p) exactly, rounding being symmetric),
+// the differences a - b as fma(b, -1, a); each element is rounded exactly as
+// in phase_df.
 __device__ __forceinline__ float2 phase_df2(float fx, float fy, float2 x, float2 y)
 {
     const float2 FX = make_float2(fx, fx), FY = make_float2(fy, fy);
+    const float2 NFX = make_float2(-fx, -fx), NFY = make_float2(-fy, -fy);
     const float2 M = make_float2(12582912.0f, 12582912.0f), NM = make_float2(-12582912.0f, -12582912.0f);
+    const float2 MINUS1 = make_float2(-1.0f, -1.0f);
     const float2 p1 = __fmul2_rn(FX, x);
-    const float2 e1 = __ffma2_rn(FX, x, make_float2(-p1.x, -p1.y));
+    const float2 ne1 = __ffma2_rn(NFX, x, p1);  // -e1
     const float2 p2 = __fmul2_rn(FY, y);
-    const float2 e2 = __ffma2_rn(FY, y, make_float2(-p2.x, -p2.y));
+    const float2 ne2 = __ffma2_rn(NFY, y, p2);  // -e2
     const float2 n1 = __fadd2_rn(__fadd2_rn(p1, M), NM);
     const float2 n2 = __fadd2_rn(__fadd2_rn(p2, M), NM);
-    const float2 r = __fadd2_rn(__fadd2_rn(p1, make_float2(-n1.x, -n1.y)), __fadd2_rn(p2, make_float2(-n2.x, -n2.y)));
-    return __fadd2_rn(r, __fadd2_rn(e1, e2));
+    const float2 r = __fadd2_rn(__ffma2_rn(n1, MINUS1, p1), __ffma2_rn(n2, MINUS1, p2));
+    return __ffma2_rn(__fadd2_rn(ne1, ne2), MINUS1, r);  // r + (e1 + e2)
 }
 
 // Fixed-point reduction: f and x quantised to int32 at per-launch binary
