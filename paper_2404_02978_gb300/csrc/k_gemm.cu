@@ -361,6 +361,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constan
         const FixedScales z = fixed_scales(g.fbound, *g.d_xbound, true);
         const int32_t X = __float2int_rn(pt.x * z.xscale), Y = __float2int_rn(pt.y * z.xscale);
         constexpr int TPG = Cfg::kTermsPer16B;
+        const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
+        const float2 neg_two_pi = make_float2(-6.28318530717958648f, -6.28318530717958648f);
         for (int64_t i = 0; i < n_chunks && !*abort_flag; ++i) {
             const int s = (int)(i % kGStages);
             const uint32_t ph = (uint32_t)((i / kGStages) & 1);
@@ -378,13 +380,24 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constan
                 const int grp = grp0 + gi;
                 float cv[TPG], sv[TPG];
 #pragma unroll
-                for (int t = 0; t < TPG; ++t) {
-                    const int2 f = fb[grp * TPG + t];
-                    float ang;
-                    if (z.use_fixed) ang = phase_fx_rad(f.x, f.y, X, Y, z.bias, z.shift);
-                    else ang = phase_df(__int_as_float(f.x), __int_as_float(f.y), pt.x, pt.y) * 6.28318530717958648f;
-                    sv[t] = __sinf(ang);
-                    cv[t] = __cosf(ang);
+                for (int t = 0; t < TPG; t += 2) {  // two terms per paired FP32 instruction
+                    const int2 f0 = fb[grp * TPG + t], f1 = fb[grp * TPG + t + 1];
+                    float2 ang;
+                    if (z.use_fixed) {
+                        const uint32_t m0 = phase_fx_word(f0.x, f0.y, X, Y, z.bias, z.shift);
+                        const uint32_t m1 = phase_fx_word(f1.x, f1.y, X, Y, z.bias, z.shift);
+                        ang = __ffma2_rn(make_float2(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u),
+                                                     __uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u)),
+                                         two_pi, neg_two_pi);
+                    } else {
+                        ang = __fmul2_rn(phase_df2f(make_float2(__int_as_float(f0.x), __int_as_float(f1.x)),
+                                                    make_float2(__int_as_float(f0.y), __int_as_float(f1.y)), pt.x, pt.y),
+                                         two_pi);
+                    }
+                    sv[t] = __sinf(ang.x);
+                    cv[t] = __cosf(ang.x);
+                    sv[t + 1] = __sinf(ang.y);
+                    cv[t + 1] = __cosf(ang.y);
                 }
                 const uint32_t oc = sm100::sw128_offset((uint32_t)row, (uint32_t)grp);
                 const uint32_t os = sm100::sw128_offset((uint32_t)row, (uint32_t)(4 + grp));

@@ -597,6 +597,23 @@ __device__ __forceinline__ float2 phase_df2(float fx, float fy, float2 x, float2
     return __ffma2_rn(__fadd2_rn(ne1, ne2), MINUS1, r);  // r + (e1 + e2)
 }
 
+// phase_df of two frequencies (fx.x, fy.x), (fx.y, fy.y) at one position, in
+// paired FP32 instructions; each element is rounded exactly as in phase_df.
+__device__ __forceinline__ float2 phase_df2f(float2 fx, float2 fy, float x, float y)
+{
+    const float2 X = make_float2(x, x), Y = make_float2(y, y), NX = make_float2(-x, -x), NY = make_float2(-y, -y);
+    const float2 M = make_float2(12582912.0f, 12582912.0f), NM = make_float2(-12582912.0f, -12582912.0f);
+    const float2 MINUS1 = make_float2(-1.0f, -1.0f);
+    const float2 p1 = __fmul2_rn(fx, X);
+    const float2 ne1 = __ffma2_rn(fx, NX, p1);  // -e1
+    const float2 p2 = __fmul2_rn(fy, Y);
+    const float2 ne2 = __ffma2_rn(fy, NY, p2);  // -e2
+    const float2 n1 = __fadd2_rn(__fadd2_rn(p1, M), NM);
+    const float2 n2 = __fadd2_rn(__fadd2_rn(p2, M), NM);
+    const float2 r = __fadd2_rn(__ffma2_rn(n1, MINUS1, p1), __ffma2_rn(n2, MINUS1, p2));
+    return __ffma2_rn(__fadd2_rn(ne1, ne2), MINUS1, r);  // r + (e1 + e2)
+}
+
 // Fixed-point reduction: f and x quantised to int32 at per-launch binary
 // scales 2^a and 2^b (|F|, |X| < 2^31), phi 2^(a+b) = Fx X + Fy Y computed
 // exactly in 64-bit wraparound arithmetic (the integer part falls off the

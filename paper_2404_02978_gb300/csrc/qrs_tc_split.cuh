@@ -66,21 +66,29 @@ __device__ __forceinline__ void pack16(const float (&v)[GemmCfg<PREC>::kTermsPer
     uint32_t* wh = reinterpret_cast<uint32_t*>(&hi);
     uint32_t* wl = reinterpret_cast<uint32_t*>(&lo);
     if (GemmCfg<PREC>::kTF32) {
+#if QRS_GEMM_INTSPLIT
+        // residuals x - hi two at a time, as fma(hi, -1, x) (exact, the same bits)
+#pragma unroll
+        for (int e = 0; e < 4; e += 2) {
+            const uint32_t h0 = tf32_rna_bits(v[e]), h1 = tf32_rna_bits(v[e + 1]);
+            const float2 r = __ffma2_rn(make_float2(__uint_as_float(h0), __uint_as_float(h1)), make_float2(-1.0f, -1.0f),
+                                        make_float2(v[e], v[e + 1]));
+            wh[e] = h0;
+            wh[e + 1] = h1;
+            wl[e] = tf32_rna_bits(r.x);
+            wl[e + 1] = tf32_rna_bits(r.y);
+        }
+#else
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-#if QRS_GEMM_INTSPLIT
-            const uint32_t h = tf32_rna_bits(v[e]);
-            wh[e] = h;
-            wl[e] = tf32_rna_bits(v[e] - __uint_as_float(h));
-#else
             uint32_t h, l;
             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v[e]));
             const float r = v[e] - __uint_as_float(h);
             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
             wh[e] = h;
             wl[e] = l;
-#endif
         }
+#endif
     } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -90,9 +98,9 @@ __device__ __forceinline__ void pack16(const float (&v)[GemmCfg<PREC>::kTermsPer
             // residuals x - hi are exact in FP32 and converted the same way
             uint32_t h, l;
             asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(x1), "f"(x0));
-            const float r0 = __fsub_rn(x0, __uint_as_float(h << 16));
-            const float r1 = __fsub_rn(x1, __uint_as_float(h & 0xFFFF0000u));
-            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(r1), "f"(r0));
+            const float2 r = __ffma2_rn(make_float2(__uint_as_float(h << 16), __uint_as_float(h & 0xFFFF0000u)),
+                                        make_float2(-1.0f, -1.0f), make_float2(x0, x1));  // x - hi, exact
+            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(r.y), "f"(r.x));
             wh[e] = h;
             wl[e] = l;
 #elif QRS_GEMM_INTSPLIT
