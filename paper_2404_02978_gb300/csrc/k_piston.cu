@@ -136,6 +136,8 @@ __device__ __forceinline__ void unit_sum_n(const PisShared<SLICES>& sh, int k0, 
                 A = make_float2(K.c[10], K.c[10]);
 #pragma unroll
                 for (int m = 9; m >= 0; --m) A = __ffma2_rn(A, u, make_float2(K.c[m], K.c[m]));
+            } else if (xx.x >= 4.0f && xx.y >= 4.0f) {  // both on the large-argument branch
+                A = airy_g_large2(xx);
             } else {
                 A = make_float2(airy_g(xx.x), airy_g(xx.y));
             }

@@ -166,6 +166,32 @@ __device__ __forceinline__ float airy_g_large(float x)
     return __fdividef(2.0f * j1, x);
 }
 
+// airy_g_large of two arguments, the polynomial and product steps in paired
+// FP32 instructions; each element is rounded exactly as in airy_g_large.
+__device__ __forceinline__ float2 airy_g_large2(float2 x)
+{
+    auto C = [](float c) { return make_float2(c, c); };
+    const float2 z = make_float2(__fdividef(3.0f, x.x), __fdividef(3.0f, x.y));
+    const float2 f1 = __ffma2_rn(
+        __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(C(-0.00020033f), z, C(0.00113653f)), z, C(-0.00249511f)), z,
+                                         C(0.00017105f)),
+                              z, C(0.01659667f)),
+                   z, C(0.00000156f)),
+        z, C(0.79788456f));
+    const float2 t1 = __fmul2_rn(
+        z, __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(C(-0.00029166f), z, C(0.00079824f)), z, C(0.00074348f)), z,
+                                            C(-0.00637879f)),
+                                 z, C(0.00005650f)),
+                      z, C(0.12499612f)));
+    float2 turns = __ffma2_rn(x, C(0.159154943091895f), __ffma2_rn(t1, C(0.159154943091895f), C(-0.375f)));
+    turns = __ffma2_rn(make_float2(rintf(turns.x), rintf(turns.y)), C(-1.0f), turns);  // turns - rint(turns)
+    const float2 a = __fmul2_rn(turns, C(6.28318530717958648f));
+    const float2 j1 = __fmul2_rn(__fmul2_rn(f1, make_float2(__cosf(a.x), __cosf(a.y))),
+                                 make_float2(rsqrtf(x.x), rsqrtf(x.y)));
+    const float2 tj = __fmul2_rn(C(2.0f), j1);
+    return make_float2(__fdividef(tj.x, x.x), __fdividef(tj.y, x.y));
+}
+
 // Eq. 7 aperture filter A(f) = 2 (D J1(pi D f) - d J1(pi d f)) / (pi (D^2 - d^2) f)
 //                            = (D^2 g(pi D f) - d^2 g(pi d f)) / (D^2 - d^2),  A(0) = 1.
 __device__ __forceinline__ float airy_filter(float f, float D, float d)
