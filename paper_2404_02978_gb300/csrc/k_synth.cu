@@ -125,6 +125,48 @@ __device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restr
     }
 }
 
+// The double-float path with paired FP32 instructions: phase_df2 of points
+// 2i and 2i + 1 (their coordinates as float bits in X, Y), the turn-to-radian
+// product and the accumulating FMAs two points at a time, each lane rounded
+// as in the scalar path.
+__device__ __forceinline__ void accumulate_chunk_df_paired(const float4* __restrict__ st, int len,
+                                                           const int32_t (&X)[kSynthPPT], const int32_t (&Y)[kSynthPPT],
+                                                           float (&acc)[kSynthPPT])
+{
+    constexpr int NP = kSynthPPT / 2;
+    const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
+    float2 px[NP], py[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        px[q] = make_float2(__int_as_float(X[2 * q]), __int_as_float(X[2 * q + 1]));
+        py[q] = make_float2(__int_as_float(Y[2 * q]), __int_as_float(Y[2 * q + 1]));
+    }
+    for (int k0 = 0; k0 < len; k0 += kSynthGroup) {
+        const int k1 = min(k0 + kSynthGroup, len);
+        float2 part[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) part[q] = make_float2(0.0f, 0.0f);
+#pragma unroll kSynthUnroll
+        for (int k = k0; k < k1; ++k) {
+            const float4 T = st[k];
+            const float2 A = make_float2(T.z, T.z), nB = make_float2(T.w, T.w);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const float2 ang = __fmul2_rn(phase_df2(T.x, T.y, px[q], py[q]), two_pi);
+                const float2 c = make_float2(__cosf(ang.x), __cosf(ang.y));
+                const float2 sn = make_float2(__sinf(ang.x), __sinf(ang.y));
+                part[q] = __ffma2_rn(A, c, part[q]);
+                part[q] = __ffma2_rn(nB, sn, part[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            acc[2 * q] += part[q].x;
+            acc[2 * q + 1] += part[q].y;
+        }
+    }
+}
+
 template <bool FIXED>
 __device__ __forceinline__ void accumulate_chunk(const float4* __restrict__ st, int len, const int32_t (&X)[kSynthPPT],
                                                  const int32_t (&Y)[kSynthPPT], float (&acc)[kSynthPPT],
@@ -223,7 +265,11 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
                 accumulate_chunk<true>(sterm, len, X, Y, acc, z);
 #endif
             } else {
+#if QRS_SYNTH_PAIRED
+                accumulate_chunk_df_paired(sterm, len, X, Y, acc);
+#else
                 accumulate_chunk<false>(sterm, len, X, Y, acc, z);
+#endif
             }
         }
         float* o = out + r * P;
