@@ -86,33 +86,41 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
     __shared__ float Bs[16][64 + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    float2 acc[4][2];  // acc[i][jp] = outputs (i, 2 jp), (i, 2 jp + 1): one FFMA2 updates both
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = make_float2(0.0f, 0.0f);
+    const int kz0 = (int)(((int64_t)K * blockIdx.z) / gridDim.z), kz1 = (int)(((int64_t)K * (blockIdx.z + 1)) / gridDim.z);
+    for (int k0 = kz0; k0 < kz1; k0 += 16) {
         for (int e = threadIdx.x; e < 1024; e += 256) {
             int mm, kk;
             if (TA) { kk = e >> 6; mm = e & 63; } else { mm = e >> 4; kk = e & 15; }
             const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < K) ? (TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk]) : 0.0f;
+            As[kk][mm] = (gm < M && gk < kz1) ? (TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk]) : 0.0f;
             int nn, kb;
             if (TB) { nn = e >> 4; kb = e & 15; } else { kb = e >> 6; nn = e & 63; }
             const int gn = n0 + nn, gkb = k0 + kb;
-            Bs[kb][nn] = (gn < N && gkb < K) ? (TB ? B[(int64_t)gn * ldb + gkb] : B[(int64_t)gkb * ldb + gn]) : 0.0f;
+            Bs[kb][nn] = (gn < N && gkb < kz1) ? (TB ? B[(int64_t)gn * ldb + gkb] : B[(int64_t)gkb * ldb + gn]) : 0.0f;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
+            float a[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+            const float2 b01 = make_float2(Bs[kk][tx * 4 + 0], Bs[kk][tx * 4 + 1]);
+            const float2 b23 = make_float2(Bs[kk][tx * 4 + 2], Bs[kk][tx * 4 + 3]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            for (int i = 0; i < 4; ++i) {
+                const float2 ai = make_float2(a[i], a[i]);
+                acc[i][0] = __ffma2_rn(ai, b01, acc[i][0]);
+                acc[i][1] = __ffma2_rn(ai, b23, acc[i][1]);
+            }
         }
         __syncthreads();
     }
+    // split K (gridDim.z > 1): raw partial sums into slice z of Cm, [z][M][ldc]; the
+    // epilogue then runs in k_sgemm_reduce
+    if (gridDim.z > 1) Cm += (int64_t)blockIdx.z * M * ldc;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int m = m0 + ty * 4 + i;
@@ -121,7 +129,11 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
         for (int j = 0; j < 4; ++j) {
             const int n = n0 + tx * 4 + j;
             if (n >= N) continue;
-            float v = acc[i][j];
+            float v = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
+            if (gridDim.z > 1) {
+                Cm[(int64_t)m * ldc + n] = v;
+                continue;
+            }
             if (EPI & kEpiBias) v += bias[n];
             if (EPI & kEpiRelu) v = fmaxf(v, 0.0f);
             if (EPI & kEpiMask) v = mask[(int64_t)m * ldm + n] > 0.0f ? v : 0.0f;
@@ -130,13 +142,63 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
     }
 }
 
+// Sum of the S split-K slices [S][M][ldc] in slice order (deterministic), then
+// the epilogue (mask only: the split products have no bias or relu).
+template <int EPI>
+__global__ void k_sgemm_reduce(int M, int N, int S, const float* __restrict__ part, float* __restrict__ Cm, int ldc,
+                               const float* __restrict__ mask, int ldm)
+{
+    const int64_t total = (int64_t)M * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e / N), n = (int)(e - (int64_t)m * N);
+        float v = part[(int64_t)m * ldc + n];
+        for (int z = 1; z < S; ++z) v += part[((int64_t)z * M + m) * ldc + n];
+        if (EPI & kEpiMask) v = mask[(int64_t)m * ldm + n] > 0.0f ? v : 0.0f;
+        Cm[(int64_t)m * ldc + n] = v;
+    }
+}
+
+// split > 1: K in `split` slices, partials in `work` (split M ldc floats), then
+// reduced in fixed order; for long K (the weight and input gradients: K = the
+// sample count or the cell count) on small outputs, whose 64 x 64 tiles alone
+// would not fill the GPU.
 template <bool TA, bool TB, int EPI>
 static cudaError_t sgemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                         const float* bias, const float* mask, int ldm, cudaStream_t s)
+                         const float* bias, const float* mask, int ldm, cudaStream_t s, int split = 1,
+                         float* work = nullptr)
 {
+    if (split > 1 && work && !(EPI & (kEpiBias | kEpiRelu))) {  // split products carry no bias or relu
+        dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64), (unsigned)split);
+        k_sgemm<TA, TB, kEpiNone><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, work, ldc, nullptr, nullptr, 0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int64_t total = (int64_t)M * N;
+        k_sgemm_reduce<EPI><<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, s>>>(M, N, split, work, C,
+                                                                                                   ldc, mask, ldm);
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
     k_sgemm<TA, TB, EPI><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, ldm);
     return cudaGetLastError();
+}
+
+// Column sums out[c] = sum_r A[r][c] (the bias gradients), deterministic: thread
+// (g, c) of a 8 x 32 block sums rows g, g + 8, ... of column c in order, then
+// the 8 partials are added in order.
+__global__ void __launch_bounds__(256) k_colsum(const float* __restrict__ A, int rows, int cols, float* __restrict__ out)
+{
+    __shared__ float red[8][33];
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31), g = threadIdx.x >> 5;
+    float v = 0.0f;
+    if (c < cols)
+        for (int r = g; r < rows; r += 8) v += A[(int64_t)r * cols + c];
+    red[g][threadIdx.x & 31] = v;
+    __syncthreads();
+    if (g == 0 && c < cols) {
+        float t = red[0][threadIdx.x];
+        for (int q = 1; q < 8; ++q) t += red[q][threadIdx.x];
+        out[c] = t;
+    }
 }
 
 // ----------------------------------------------------- softmax cross entropy
@@ -454,7 +516,24 @@ static cudaError_t mlp_forward(int C, const float* P, const double* geom, int64_
     return e;
 }
 
-static size_t mlp_ws_floats(int C, int64_t n) { return (size_t)n * (8 + 4 * kHid + 2 * (size_t)C + 2) + 64; }
+constexpr int kMaxSplit = 8;  // K slices of the long-K gradient products
+
+// Slices for a long-K product: enough 64 x 64 tiles for about two per SM on a
+// 152-SM part, at most kMaxSplit, each slice at least 128 deep.
+static int split_for(int M, int N, int K)
+{
+    const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
+    int sp = (304 + tiles - 1) / tiles;
+    sp = std::min(sp, kMaxSplit);
+    sp = std::min(sp, std::max(1, K / 128));
+    return std::max(sp, 1);
+}
+
+static size_t mlp_ws_floats(int C, int64_t n)
+{
+    return (size_t)n * (8 + 4 * kHid + 2 * (size_t)C + 2) + 64 +
+           (size_t)kMaxSplit * std::max((size_t)kHid * (size_t)C, (size_t)n * kHid) + 64;
+}
 
 qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, const double* geom, int64_t n,
                            float* logits, void* stream)
@@ -497,8 +576,8 @@ qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params
     float* dA1 = dA2 + kHid * n;
     float* Z = dA1 + kHid * n;
     float* dZ = Z + (int64_t)C * n;
-    float* ones = dZ + (int64_t)C * n;
-    float* lrow = ones + n;
+    float* lrow = dZ + (int64_t)C * n + n;
+    float* part = reinterpret_cast<float*>(((uintptr_t)(lrow + n) + 255) & ~(uintptr_t)255);  // split-K slices
     cudaStream_t s = (cudaStream_t)stream;
     MlpView w = mlp_view(const_cast<float*>(params), C);
     MlpView g = mlp_view(grad, C);
@@ -513,23 +592,35 @@ qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params
         k_loss_mean<<<1, 1024, 0, s>>>(lrow, n, loss);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) {
-        k_fill<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(ones, n, 1.0f);
-        e = cudaGetLastError();
-    }
-    // layer 3: dW3 = H2^T dZ, db3 = 1^T dZ, dA2 = (dZ W3^T) * (H2 > 0)
-    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(kHid, C, N, H2, kHid, dZ, C, g.W3, C, nullptr, nullptr, 0, s);
-    if (e == cudaSuccess) e = sgemm<false, false, kEpiNone>(1, C, N, ones, N, dZ, C, g.b3, C, nullptr, nullptr, 0, s);
-    if (e == cudaSuccess) e = sgemm<false, true, kEpiMask>(N, kHid, C, dZ, C, w.W3, C, dA2, kHid, nullptr, H2, kHid, s);
+    int launches = 4 + 2;
+    auto colsum = [&](const float* A, int cols, float* out) {
+        k_colsum<<<(unsigned)((cols + 31) / 32), 256, 0, s>>>(A, N, cols, out);
+        ++launches;
+        return cudaGetLastError();
+    };
+    auto gemm_launches = [&](int sp) { launches += sp > 1 ? 2 : 1; };
+    // layer 3: dW3 = H2^T dZ, db3 = column sums of dZ, dA2 = (dZ W3^T) * (H2 > 0)
+    int sp = split_for(kHid, C, N);
+    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(kHid, C, N, H2, kHid, dZ, C, g.W3, C, nullptr, nullptr, 0, s, sp, part);
+    gemm_launches(sp);
+    if (e == cudaSuccess) e = colsum(dZ, C, g.b3);
+    sp = split_for(N, kHid, C);
+    if (e == cudaSuccess) e = sgemm<false, true, kEpiMask>(N, kHid, C, dZ, C, w.W3, C, dA2, kHid, nullptr, H2, kHid, s, sp, part);
+    gemm_launches(sp);
     // layer 2
-    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(kHid, kHid, N, H1, kHid, dA2, kHid, g.W2, kHid, nullptr, nullptr, 0, s);
-    if (e == cudaSuccess) e = sgemm<false, false, kEpiNone>(1, kHid, N, ones, N, dA2, kHid, g.b2, kHid, nullptr, nullptr, 0, s);
+    sp = split_for(kHid, kHid, N);
+    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(kHid, kHid, N, H1, kHid, dA2, kHid, g.W2, kHid, nullptr, nullptr, 0, s, sp, part);
+    gemm_launches(sp);
+    if (e == cudaSuccess) e = colsum(dA2, kHid, g.b2);
     if (e == cudaSuccess) e = sgemm<false, true, kEpiMask>(N, kHid, kHid, dA2, kHid, w.W2, kHid, dA1, kHid, nullptr, H1, kHid, s);
+    gemm_launches(1);
     // layer 1
-    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(6, kHid, N, X, 6, dA1, kHid, g.W1, kHid, nullptr, nullptr, 0, s);
-    if (e == cudaSuccess) e = sgemm<false, false, kEpiNone>(1, kHid, N, ones, N, dA1, kHid, g.b1, kHid, nullptr, nullptr, 0, s);
+    sp = split_for(6, kHid, N);
+    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(6, kHid, N, X, 6, dA1, kHid, g.W1, kHid, nullptr, nullptr, 0, s, sp, part);
+    gemm_launches(sp);
+    if (e == cudaSuccess) e = colsum(dA1, kHid, g.b1);
     if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_loss_grad");
-    h->launches += 4 + 3 + 9;
+    h->launches += launches;
     return QRS_OK;
 }
 
