@@ -509,7 +509,7 @@ def hankel_piston_sf(B, r0, L0, D, fmin, fmax):
 
 
 def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho=64, n_theta=32, steps=8000,
-                    target_draws=1024, fold=4, lr=4e-3, beta=0.8):
+                    target_draws=1024, fold=4, lr=4e-3, beta=0.8, seeds=(3, 4, 5, 6)):
     """Learned proposal (6 -> 128 -> 128 -> n_rho x n_theta logits): targets from the
     plain method's own draws, training on the GPU, then the matched
     structure-function error (RMS over held-out geometries and draws of the
@@ -518,7 +518,9 @@ def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho
     each geometry's baseline frame, folded over `fold` mirrored sectors; Adam
     with a cosine learning-rate schedule; the sampled density is
     softmax(beta z) (beta = 0.8 was chosen on 100 validation geometries
-    disjoint from the held-out ones)."""
+    disjoint from the held-out ones).  The network of the first seed is
+    reported in full; the others (other initialisations, same data) give the
+    spread of the term reduction over training seeds."""
     def geom(n, seed):
         rng = np.random.default_rng(seed)
         B = np.exp(rng.uniform(np.log(1), np.log(200), n))
@@ -537,42 +539,64 @@ def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho
     torch.cuda.synchronize()
     t_targets = time.perf_counter() - t0
     t0 = time.perf_counter()
-    P, hist = qrs.train_proposal(h, C, gtr, T, steps=steps, lr=lr, seed=3, log_every=1000, schedule="cosine")
+    P, hist = qrs.train_proposal(h, C, gtr, T, steps=steps, lr=lr, seed=seeds[0], log_every=1000, schedule="cosine")
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     logits = qrs.qrs_mlp_forward(h, C, P, torch.from_numpy(gte_np).to(dev))
     T_test = qrs.qrs_proposal_targets(h, qrs.params(**dom), n_rho, n_theta, 78, 4096, 512,
                                       torch.from_numpy(gte_np).to(dev), kind="rms", fold=fold)
+    Drefs = [hankel_piston_sf(np.hypot(g[3], g[4]), g[0], g[1], g[2], 1e-3, 10.0) for g in gte_np]
+
+    def sq_err(pp, nf, i):
+        """Mean over the draws of the squared relative SF error of geometry i."""
+        r0, L0, D, Bx, By = gte_np[i]
+        d = qrs.qrs_draw(h, pp, nf, draws, outputs=("f_xy", "amp"))
+        f, F = d["f_xy"].double(), d["amp"].double()
+        fr = torch.sqrt(f[..., 0] ** 2 + f[..., 1] ** 2)
+        x = np.pi * D * fr
+        A = torch.where(x > 1e-6, 2 * torch.special.bessel_j1(x) / x, torch.ones_like(x))
+        ph = 2 * np.pi * (f[..., 0] * Bx + f[..., 1] * By)
+        e = ((F ** 2 * A ** 2 * 2 * (1 - torch.cos(ph))).sum(-1).cpu().numpy() - Drefs[i]) / Drefs[i]
+        return float(np.mean(e ** 2))
+
+    def importance(i, z_row, b):
+        r0, L0, D, Bx, By = gte_np[i]
+        cdf = qrs.qrs_proposal_cdf(h, n_rho, n_theta, z_row.contiguous(), 0.05, beta=b)
+        return dict(qrs.params(r0=r0, L0=L0, seed=1000 + i, **dom), sampler="importance", n_rho=n_rho,
+                    n_theta=n_theta, cdf=cdf, fold=fold, frame=float(np.arctan2(By, Bx) / (2 * np.pi)) if fold else 0.0)
+
     err = {}
     for i, (r0, L0, D, Bx, By) in enumerate(gte_np):
-        Dref = hankel_piston_sf(np.hypot(Bx, By), r0, L0, D, 1e-3, 10.0)
         p = qrs.params(r0=r0, L0=L0, seed=1000 + i, **dom)
-        cdf = qrs.qrs_proposal_cdf(h, n_rho, n_theta, logits[i].contiguous(), 0.05, beta=beta)
-        pi = dict(p, sampler="importance", n_rho=n_rho, n_theta=n_theta, cdf=cdf, fold=fold,
-                  frame=float(np.arctan2(By, Bx) / (2 * np.pi)) if fold else 0.0)
+        pi = importance(i, logits[i], beta)
         # the ceiling of any cell density on this grid: the geometry's own targets as the proposal
-        cdf_x = qrs.qrs_proposal_cdf(h, n_rho, n_theta, torch.log(T_test[i].clamp_min(1e-30)).contiguous(), 0.05)
-        px = dict(pi, cdf=cdf_x)
+        px = importance(i, torch.log(T_test[i].clamp_min(1e-30)), 1.0)
         for name, pp, nfs in (("plain", p, (256, 512, 1024, 2048, 4096)), ("learned", pi, (256, 512, 1024)),
                               ("own_targets", px, (256, 512, 1024))):
             for nf in nfs:
-                d = qrs.qrs_draw(h, pp, nf, draws, outputs=("f_xy", "amp"))
-                f, F = d["f_xy"].double(), d["amp"].double()
-                fr = torch.sqrt(f[..., 0] ** 2 + f[..., 1] ** 2)
-                x = np.pi * D * fr
-                A = torch.where(x > 1e-6, 2 * torch.special.bessel_j1(x) / x, torch.ones_like(x))
-                ph = 2 * np.pi * (f[..., 0] * Bx + f[..., 1] * By)
-                e = ((F ** 2 * A ** 2 * 2 * (1 - torch.cos(ph))).sum(-1).cpu().numpy() - Dref) / Dref
-                err.setdefault("%s_%d" % (name, nf), []).append(float(np.mean(e ** 2)))
+                err.setdefault("%s_%d" % (name, nf), []).append(sq_err(pp, nf, i))
     rms = {k: float(np.sqrt(np.mean(v))) for k, v in err.items()}
     plain_n = np.array([256, 512, 1024, 2048, 4096], float)
     plain_e = np.array([rms["plain_%d" % n] for n in plain_n.astype(int)])
-    # plain terms needed for the learned error (log-log interpolation of the plain curve)
+
+    def reduction(e, nf):
+        """Plain terms needed for error e (log-log interpolation of the plain curve) / nf."""
+        return float(np.exp(np.interp(-np.log(e), -np.log(plain_e), np.log(plain_n)))) / nf
+
     equiv, cap = {}, {}
     for nf in (256, 512, 1024):
-        for name, d in (("learned", equiv), ("own_targets", cap)):
-            e = rms["%s_%d" % (name, nf)]
-            d[nf] = float(np.exp(np.interp(-np.log(e), -np.log(plain_e), np.log(plain_n))))
+        equiv[nf] = reduction(rms["learned_%d" % nf], nf) * nf
+        cap[nf] = reduction(rms["own_targets_%d" % nf], nf) * nf
+    # the other training seeds: the spread of the reduction over initialisations
+    per_seed = {str(seeds[0]): {str(nf): equiv[nf] / nf for nf in (256, 512, 1024)}}
+    gte_dev = torch.from_numpy(gte_np).to(dev)
+    for sd in seeds[1:]:
+        Ps, _ = qrs.train_proposal(h, C, gtr, T, steps=steps, lr=lr, seed=sd, schedule="cosine")
+        zs = qrs.qrs_mlp_forward(h, C, Ps, gte_dev)
+        per_seed[str(sd)] = {}
+        for nf in (256, 512, 1024):
+            e = float(np.sqrt(np.mean([sq_err(importance(i, zs[i], beta), nf, i) for i in range(len(gte_np))])))
+            per_seed[str(sd)][str(nf)] = reduction(e, nf)
     return {"workload": "%d training geometries (r0 0.05-0.3 m, L0 10-100 m, D 1-8 m, |B| 1-200 m), "
                         "%d held out, %d draws each, cells %dx%d over [1e-3, 10] c/m, baseline frame, "
                         "%d mirrored sectors" % (n_train, n_test, draws, n_rho, n_theta, fold),
@@ -581,6 +605,9 @@ def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho
             "matched_sf_error": rms,
             "plain_terms_for_equal_error": {str(k): v for k, v in equiv.items()},
             "term_reduction": {str(k): v / k for k, v in equiv.items()},
+            "term_reduction_by_seed": per_seed,
+            "term_reduction_seed_mean": {str(nf): float(np.mean([v[str(nf)] for v in per_seed.values()]))
+                                         for nf in (256, 512, 1024)},
             "term_reduction_own_targets": {str(k): v / k for k, v in cap.items()}}
 
 
