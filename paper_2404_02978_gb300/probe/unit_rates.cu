@@ -1,4 +1,4 @@
-// Unit-rate probe (sin.approx, cos.approx, ex2.approx, FFMA, DFMA per SM per clock): the
+// Unit-rate probe (sin.approx, cos.approx, ex2.approx, FFMA, DFMA, paired FFMA2 per SM per clock): the
 // denominators of the ALU rooflines.  Build and run on the GPU:
 //   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o /tmp/unit_rates paper_2404_02978_gb300/probe/unit_rates.cu && /tmp/unit_rates
 #include <cstdio>
@@ -24,6 +24,19 @@ __global__ void kd(double* out, int iters, double a) {
   }
   out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3+x4+x5+x6+x7;
 }
+// Paired FP32 FMA (FFMA2: two lanes' FMAs in one instruction), 8 independent float2 chains.
+__global__ void k2(float* out, int iters, float a) {
+  const float2 av = make_float2(a, a);
+  float2 x[8];
+  for (int j = 0; j < 8; ++j) x[j] = make_float2(threadIdx.x * 1e-3f + 0.1f * j, threadIdx.x * 1e-3f - 0.1f * j);
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = __ffma2_rn(x[j], av, av);
+  }
+  float t = 0.0f;
+  for (int j = 0; j < 8; ++j) t += x[j].x + x[j].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
 int main(){
   cudaDeviceProp p; CK(cudaGetDeviceProperties(&p,0));
   int clk=0; cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0);
@@ -32,7 +45,7 @@ int main(){
   float* o; CK(cudaMalloc(&o, blocks*thr*sizeof(double)));
   cudaEvent_t a,b; cudaEventCreate(&a); cudaEventCreate(&b);
   const char* names[4]={"sin.approx","cos.approx","ex2.approx","ffma"};
-  for(int op=0;op<5;op++){
+  for(int op=0;op<6;op++){
     int iters = op==4? 256 : 4096;
     for(int rep=0;rep<3;rep++){
       cudaEventRecord(a);
@@ -41,10 +54,11 @@ int main(){
       if(op==2)k<2><<<blocks,thr>>>(o,iters,0.999f);
       if(op==3)k<3><<<blocks,thr>>>(o,iters,0.999f);
       if(op==4)kd<<<blocks,thr>>>((double*)o,iters,0.999);
+      if(op==5)k2<<<blocks,thr>>>(o,iters,0.999f);
       cudaEventRecord(b); CK(cudaEventSynchronize(b));
       float ms; cudaEventElapsedTime(&ms,a,b);
-      double ops=(double)blocks*thr*iters*8;
-      if(rep==2) printf("%-11s %.3f ms  %.3e ops/s  per-SM-per-clk@2070MHz=%.2f  @1900=%.2f\n", op==4?"dfma":names[op], ms, ops/(ms*1e-3), ops/(ms*1e-3)/nsm/2.07e9, ops/(ms*1e-3)/nsm/1.9e9);
+      double ops=(double)blocks*thr*iters*8*(op==5?2:1);  // FFMA2: two FMAs per instruction
+      if(rep==2) printf("%-11s %.3f ms  %.3e ops/s  per-SM-per-clk@2070MHz=%.2f  @1900=%.2f\n", op==4?"dfma":op==5?"ffma2 (FMAs)":names[op], ms, ops/(ms*1e-3), ops/(ms*1e-3)/nsm/2.07e9, ops/(ms*1e-3)/nsm/1.9e9);
     }
   }
   CK(cudaGetLastError());
