@@ -53,10 +53,13 @@
 #include "qrs_tc_split.cuh"
 
 #ifndef QRS_GRID_PRODUCERS
-#define QRS_GRID_PRODUCERS 12  // producer warps: 8 (threads share an x row and own a y row), 12, 16
+#define QRS_GRID_PRODUCERS 16  // producer warps: 8 (threads share an x row and own a y row), 12, 16
 #endif
 #ifndef QRS_GRID_PROMOTERS
 #define QRS_GRID_PROMOTERS 4   // promoter warps: 4 (256 columns each) or 8 (128)
+#endif
+#ifndef QRS_GRID_PROMOTE_COLS
+#define QRS_GRID_PROMOTE_COLS 16  // TMEM columns a promoter thread holds at a time (32 or 16)
 #endif
 #ifndef QRS_GRID_COEF_X
 #define QRS_GRID_COEF_X 1      // coefficients on the x side (128 rows per tile) instead of the y side (256)
@@ -100,6 +103,10 @@ struct GridArgs {
     float fbound;
     int* err;
 };
+
+// A promoter's TMEM read: 32 lanes x 32 or 16 consecutive columns.
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&v)[32]) { sm100::tmem_ld_32x32b_x32(taddr, v); }
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&v)[16]) { sm100::tmem_ld_32x32b_x16(taddr, v); }
 
 // max(|x|, |y|) over both coordinate vectors (one CTA, no atomics).
 __global__ void k_grid_bound(const float* __restrict__ x, int64_t nx, const float* __restrict__ y, int64_t ny,
@@ -385,27 +392,29 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                 sm100::tc_fence_after();
                 const uint32_t slot = tmem_base + (uint32_t)(b * kXN) + lane_off + col0;
                 const bool last = (j == n_seg - 1);
+                constexpr int PC = QRS_GRID_PROMOTE_COLS;
+                static_assert(PC == 32 || PC == 16, "promotion width");
 #pragma unroll 1
-                for (int c0 = 0; c0 < kSpan; c0 += 32) {
+                for (int c0 = 0; c0 < kSpan; c0 += PC) {
                     float* mp = mrow + (int64_t)(col0 + c0) * kXM;
-                    float m[32];
-                    uint32_t v[32];
+                    float m[PC];
+                    uint32_t v[PC];
                     if (j > 0) {
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) m[q] = mp[q * kXM];
+                        for (int q = 0; q < PC; ++q) m[q] = mp[q * kXM];
                     }
-                    sm100::tmem_ld_32x32b_x32(slot + (uint32_t)c0, v);
+                    tmem_ld_cols(slot + (uint32_t)c0, v);
                     sm100::tmem_ld_wait();
                     if (j > 0) {
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + m[q]);
+                        for (int q = 0; q < PC; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + m[q]);
                     }
                     if (!last) {
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) mp[q * kXM] = __uint_as_float(v[q]);
+                        for (int q = 0; q < PC; ++q) mp[q * kXM] = __uint_as_float(v[q]);
                     } else if (xi < g.nx) {
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) {
+                        for (int q = 0; q < PC; ++q) {
                             const int64_t yj = nb * kXN + col0 + c0 + q;
                             if (yj < g.ny) {
                                 const int64_t node = yj * g.nx + xi;
