@@ -509,7 +509,7 @@ def hankel_piston_sf(B, r0, L0, D, fmin, fmax):
 
 
 def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho=64, n_theta=32, steps=8000,
-                    target_draws=1024, fold=4, lr=4e-3, beta=0.8, seeds=(3, 4, 5, 6)):
+                    target_draws=1024, fold=4, lr=4e-3, beta=0.7, seeds=(3, 4, 5, 6)):
     """Learned proposal (6 -> 128 -> 128 -> n_rho x n_theta logits): targets from the
     plain method's own draws, training on the GPU, then the matched
     structure-function error (RMS over held-out geometries and draws of the
@@ -517,7 +517,7 @@ def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho
     at N_f = 256..1024 against plain draws at N_f = 256..4096.  The cells lie in
     each geometry's baseline frame, folded over `fold` mirrored sectors; Adam
     with a cosine learning-rate schedule; the sampled density is
-    softmax(beta z) (beta = 0.8 was chosen on 100 validation geometries
+    softmax(beta z) (beta = 0.7 was chosen on 100 validation geometries
     disjoint from the held-out ones).  The network of the first seed is
     reported in full; the others (other initialisations, same data) give the
     spread of the term reduction over training seeds."""
