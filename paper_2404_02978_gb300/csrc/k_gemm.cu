@@ -49,8 +49,22 @@
 #include "qrs_sm100.cuh"
 #include "qrs_tc_split.cuh"
 
-#ifndef QRS_GEMM_PRODUCERS
-#define QRS_GEMM_PRODUCERS 8  // basis producer warps (4: one per row block; 8: two, splitting the terms)
+// Basis producer warps (4: one per row block; 8 / 16: two / four, splitting
+// the terms) and the TMEM columns a promoter thread holds at a time (32 or
+// 16), per precision: BF16X3 has twice the basis elements per K chunk and
+// gains from 16 producers (promoters then read 16 columns to fit the
+// registers); 3XTF32 is fastest with 8.
+#ifndef QRS_GEMM_PRODUCERS_TF32
+#define QRS_GEMM_PRODUCERS_TF32 8
+#endif
+#ifndef QRS_GEMM_PRODUCERS_BF16
+#define QRS_GEMM_PRODUCERS_BF16 16
+#endif
+#ifndef QRS_GEMM_PROMOTE_COLS_TF32
+#define QRS_GEMM_PROMOTE_COLS_TF32 32
+#endif
+#ifndef QRS_GEMM_PROMOTE_COLS_BF16
+#define QRS_GEMM_PROMOTE_COLS_BF16 16
 #endif
 
 namespace qrs {
@@ -63,9 +77,15 @@ constexpr int kGTileB = kGN * 128;                         // 32 KB
 constexpr int kGStageBytes = 2 * kGTileA + 2 * kGTileB;    // A hi/lo + B hi/lo = 96 KB
 constexpr int kGFreqSlots = 8;                             // frequency ring, filled ahead by warp 2
 constexpr int kGFreqBytes = 256;                           // one chunk's basis frequencies (<= 32 x 8 B)
-constexpr int kGProducers = QRS_GEMM_PRODUCERS;
-constexpr int kGThreads = 384 + 32 * kGProducers;
-static_assert(kGProducers == 4 || kGProducers == 8, "producer warps");
+template <int PREC>
+struct GemmShape {
+    static constexpr bool kBF16 = !GemmCfg<PREC>::kTF32;
+    static constexpr int kProducers = kBF16 ? QRS_GEMM_PRODUCERS_BF16 : QRS_GEMM_PRODUCERS_TF32;
+    static constexpr int kPromoteCols = kBF16 ? QRS_GEMM_PROMOTE_COLS_BF16 : QRS_GEMM_PROMOTE_COLS_TF32;
+    static constexpr int kThreads = 384 + 32 * kProducers;
+    static_assert(kProducers == 4 || kProducers == 8 || kProducers == 16, "producer warps");
+    static_assert(kPromoteCols == 32 || kPromoteCols == 16, "promotion width");
+};
 constexpr int kGSmemBytes = kGStages * kGStageBytes + kGFreqSlots * kGFreqBytes + 512 + 1024;  // + barriers, slack
 constexpr long long kGWaitCycles = 4000000000LL;           // ~2 s of SM clock per wait
 
@@ -169,9 +189,11 @@ __global__ void k_gemm_coef(DrawParams p, int64_t nf_pad, int64_t n_real, int64_
 
 // ------------------------------------------------------------ main kernel
 template <int PREC>
-__global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constant__ CUtensorMap tmapB, GemmArgs g)
+__global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(const __grid_constant__ CUtensorMap tmapB,
+                                                                           GemmArgs g)
 {
     using Cfg = GemmCfg<PREC>;
+    constexpr int kGProducers = GemmShape<PREC>::kProducers;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* fring = smem + kGStages * kGStageBytes;
@@ -324,21 +346,22 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gemm_main(const __grid_constan
             }
             sm100::tc_fence_after();
             const bool last = (j == n_seg - 1);
+            constexpr int PC = GemmShape<PREC>::kPromoteCols;
 #pragma unroll 1
-            for (int c0 = 0; c0 < 128; c0 += 32) {
-                uint32_t v[32], w[32];
-                sm100::tmem_ld_32x32b_x32(tmem_seg + lane_off + col0 + (uint32_t)c0, v);
-                if (j > 0) sm100::tmem_ld_32x32b_x32(tmem_master + lane_off + col0 + (uint32_t)c0, w);
+            for (int c0 = 0; c0 < 128; c0 += PC) {
+                uint32_t v[PC], w[PC];
+                sm100::tmem_ld_cols(tmem_seg + lane_off + col0 + (uint32_t)c0, v);
+                if (j > 0) sm100::tmem_ld_cols(tmem_master + lane_off + col0 + (uint32_t)c0, w);
                 sm100::tmem_ld_wait();
                 if (j > 0) {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
+                    for (int q = 0; q < PC; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
                 }
                 if (!last) {
-                    sm100::tmem_st_32x32b_x32(tmem_master + lane_off + col0 + (uint32_t)c0, v);
+                    sm100::tmem_st_cols(tmem_master + lane_off + col0 + (uint32_t)c0, v);
                 } else if (m < g.P) {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
+                    for (int q = 0; q < PC; ++q) {
                         const int64_t r = rblk * kGN + col0 + c0 + q;
                         if (r < g.n_real) g.out[r * g.P + m] = __uint_as_float(v[q]);
                     }
@@ -505,7 +528,7 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     e = cudaFuncSetAttribute(k_gemm_main<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemBytes);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((P + kGM - 1) / kGM), (unsigned)(R_pad / kGN));
-    k_gemm_main<PREC><<<grid, kGThreads, kGSmemBytes, s>>>(tmap, a);
+    k_gemm_main<PREC><<<grid, GemmShape<PREC>::kThreads, kGSmemBytes, s>>>(tmap, a);
     return cudaGetLastError();
 }
 

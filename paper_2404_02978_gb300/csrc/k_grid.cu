@@ -104,10 +104,6 @@ struct GridArgs {
     int* err;
 };
 
-// A promoter's TMEM read: 32 lanes x 32 or 16 consecutive columns.
-__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&v)[32]) { sm100::tmem_ld_32x32b_x32(taddr, v); }
-__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&v)[16]) { sm100::tmem_ld_32x32b_x16(taddr, v); }
-
 // max(|x|, |y|) over both coordinate vectors (one CTA, no atomics).
 __global__ void k_grid_bound(const float* __restrict__ x, int64_t nx, const float* __restrict__ y, int64_t ny,
                              float* __restrict__ out)
@@ -403,7 +399,7 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
 #pragma unroll
                         for (int q = 0; q < PC; ++q) m[q] = mp[q * kXM];
                     }
-                    tmem_ld_cols(slot + (uint32_t)c0, v);
+                    sm100::tmem_ld_cols(slot + (uint32_t)c0, v);
                     sm100::tmem_ld_wait();
                     if (j > 0) {
 #pragma unroll
