@@ -258,11 +258,6 @@ __global__ void k_loss_mean(const float* __restrict__ loss_row, int64_t n, float
     if (threadIdx.x == 0) *loss = s / (float)n;
 }
 
-__global__ void k_fill(float* __restrict__ x, int64_t n, float v)
-{
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
-}
-
 // ------------------------------------------------------------------- Adam
 __global__ void k_adam(int64_t n, float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ g, float lr, float c1, float c2)
@@ -576,7 +571,7 @@ qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params
     float* dA1 = dA2 + kHid * n;
     float* Z = dA1 + kHid * n;
     float* dZ = Z + (int64_t)C * n;
-    float* lrow = dZ + (int64_t)C * n + n;
+    float* lrow = dZ + (int64_t)C * n + n;  // (n floats after dZ unused)
     float* part = reinterpret_cast<float*>(((uintptr_t)(lrow + n) + 255) & ~(uintptr_t)255);  // split-K slices
     cudaStream_t s = (cudaStream_t)stream;
     MlpView w = mlp_view(const_cast<float*>(params), C);
