@@ -345,10 +345,11 @@ qrs_status qrs_choose_n(const qrs_psd* psd, double delta_f, double eps_rel, int3
  *   L >= 1: x = v[t+L] - v[t], t in [0, T-L)   (temporal structure function)
  *   L == 0: x = v[t], t in [0, T)              (the value itself: over a baseline
  *                                               this is the spatial structure function)
- * acc[s][l][0..2] += (sum x^2, sum x^4, count) over all realisations and t, FP64
- * (x formed in FP64 from FP32 inputs).  The caller zeroes acc once; calls
- * accumulate, so the sums of a chunked run equal those of one run up to FP64
- * rounding order.
+ * acc[s][l][0..2] += (sum x^2, sum x^4, count) over all realisations and t:
+ * x formed exactly from the FP32 inputs, per-thread partial sums in
+ * double-float (FP32 pairs, about 48 significant bits), combined in FP64.
+ * The caller zeroes acc once; calls accumulate, so the sums of a chunked run
+ * equal those of one run up to rounding order.
  *   delta [n_real][n_series][T] FP32, lags [n_lags] int32 in [0, T), acc FP64. */
 qrs_status qrs_structure_fn(qrs_handle* h, const float* delta, int64_t n_real, int64_t n_series,
                             int64_t T, const int32_t* lags, int32_t n_lags, double* acc, void* stream);

@@ -1,7 +1,8 @@
 // k_sf.cu -- K5: FP64 structure-function sums (Sec. 4.4), and the pair
 // differences of synthesised values they are usually taken of.
 // For every (series s, lag L): x = v[t+L] - v[t] (L >= 1) or x = v[t] (L = 0),
-// summed over realisations and t as (sum x^2, sum x^4, count) in FP64.
+// summed over realisations and t as (sum x^2, sum x^4, count): per thread in
+// double-float on the FP32 pipe (below), across threads and blocks in FP64.
 // Grid: y = series-lag pair, x = slices of the flat (realisation, t) range.
 // Each thread keeps FP64 partial sums, the block reduces them with warp
 // shuffles, and one thread per block adds them to acc with FP64 atomics.
@@ -16,6 +17,11 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Per-thread sums in double-float (hi + lo FP32 pairs, qrs_device.cuh) on the
+// FP32 pipe, whose rate is 64 times the FP64 pipe's on this part: x = v1 - v0
+// exactly by two-sum, x^2 and x^4 by the FMA-based exact product, sums by
+// df_add (about 48 significant bits each step); a thread's partials go to FP64
+// at the end.
 __global__ void __launch_bounds__(256) k_structure_fn(const float* __restrict__ delta, int64_t n_real, int64_t n_series,
                                                       int64_t T, const int32_t* __restrict__ lags, int32_t n_lags,
                                                       double* __restrict__ acc, int* __restrict__ err)
@@ -32,18 +38,31 @@ __global__ void __launch_bounds__(256) k_structure_fn(const float* __restrict__ 
         }
         const int64_t per = (L == 0) ? T : T - L;  // values per (realisation, series)
         const int64_t total = n_real * per;
-        double s2 = 0.0, s4 = 0.0, cnt = 0.0;
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t r = i / per;
-            const int64_t t = i - r * per;
+        // the flat index i = r per + t advances by the grid stride: (r, t) are
+        // carried along (one division per thread, not per value)
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        const int64_t dq = stride / per, dr = stride - dq * per;
+        int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        int64_t r = i / per, t = i - r * per;
+        DF a2 = {0.0f, 0.0f}, a4 = {0.0f, 0.0f};
+        int64_t n = 0;
+        for (; i < total; i += stride) {
             const float* v = delta + (r * n_series + s) * T;
-            const double x = (L == 0) ? (double)v[t] : (double)v[t + L] - (double)v[t];
-            const double x2 = x * x;
-            s2 += x2;
-            s4 += x2 * x2;
-            cnt += 1.0;
+            const DF x = (L == 0) ? DF{v[t], 0.0f} : df_two_sum(v[t + L], -v[t]);  // exact difference
+            const DF x2 = df_mul(x, x);
+            const DF x4 = df_mul(x2, x2);
+            a2 = df_add(a2, x2);
+            a4 = df_add(a4, x4);
+            ++n;
+            r += dq;
+            t += dr;
+            if (t >= per) {
+                t -= per;
+                ++r;
+            }
         }
+        double s2 = (double)a2.hi + (double)a2.lo, s4 = (double)a4.hi + (double)a4.lo;
+        double cnt = (double)n;
         s2 = warp_sum(s2);
         s4 = warp_sum(s4);
         cnt = warp_sum(cnt);
