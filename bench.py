@@ -721,6 +721,7 @@ def run_ours(a):
         peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
         line["other_forms"] = {m: measure_gemm(qrs, h, torch, dev, m, peaks) for m in ("gemm_3xtf32", "gemm_bf16x3")}
         line["other_forms"]["grid_3xtf32"] = measure_grid(qrs, h, torch, dev, peaks)
+        line["other_forms"]["grid_bf16x3"] = measure_grid(qrs, h, torch, dev, peaks, mode="gemm_bf16x3")
         line["other_forms"]["batched_pistons"] = measure_batched(qrs, h, torch, dev)
         line["other_forms"]["vlti_temporal_sf"] = measure_vlti(qrs, h, torch, dev)
         line["other_forms"]["sampling_quality"] = measure_sampling(qrs, h, torch, dev)
