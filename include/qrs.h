@@ -347,7 +347,8 @@ qrs_status qrs_choose_n(const qrs_psd* psd, double delta_f, double eps_rel, int3
  *                                               this is the spatial structure function)
  * acc[s][l][0..2] += (sum x^2, sum x^4, count) over all realisations and t:
  * x formed exactly from the FP32 inputs, per-thread partial sums in
- * double-float (FP32 pairs, about 48 significant bits), combined in FP64.
+ * double-float (FP32 pairs, about 48 significant bits; |x| >= 1e9 and NaN in
+ * FP64), combined in FP64.
  * The caller zeroes acc once; calls accumulate, so the sums of a chunked run
  * equal those of one run up to rounding order.
  *   delta [n_real][n_series][T] FP32, lags [n_lags] int32 in [0, T), acc FP64. */

@@ -21,7 +21,8 @@ __device__ __forceinline__ double warp_sum(double v)
 // FP32 pipe, whose rate is 64 times the FP64 pipe's on this part: x = v1 - v0
 // exactly by two-sum, x^2 and x^4 by the FMA-based exact product, sums by
 // df_add (about 48 significant bits each step); a thread's partials go to FP64
-// at the end.
+// at the end.  Values of magnitude 1e9 or more (whose fourth power would leave
+// the FP32 range), and NaN, are summed in FP64 instead.
 __global__ void __launch_bounds__(256) k_structure_fn(const float* __restrict__ delta, int64_t n_real, int64_t n_series,
                                                       int64_t T, const int32_t* __restrict__ lags, int32_t n_lags,
                                                       double* __restrict__ acc, int* __restrict__ err)
@@ -45,14 +46,21 @@ __global__ void __launch_bounds__(256) k_structure_fn(const float* __restrict__ 
         int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         int64_t r = i / per, t = i - r * per;
         DF a2 = {0.0f, 0.0f}, a4 = {0.0f, 0.0f};
+        double b2 = 0.0, b4 = 0.0;  // values too large for the FP32 fourth power
         int64_t n = 0;
         for (; i < total; i += stride) {
             const float* v = delta + (r * n_series + s) * T;
             const DF x = (L == 0) ? DF{v[t], 0.0f} : df_two_sum(v[t + L], -v[t]);  // exact difference
-            const DF x2 = df_mul(x, x);
-            const DF x4 = df_mul(x2, x2);
-            a2 = df_add(a2, x2);
-            a4 = df_add(a4, x4);
+            if (fabsf(x.hi) < 1.0e9f) {
+                const DF x2 = df_mul(x, x);
+                const DF x4 = df_mul(x2, x2);
+                a2 = df_add(a2, x2);
+                a4 = df_add(a4, x4);
+            } else {  // x^4 would leave the FP32 range: this value in FP64 (also NaN, inf)
+                const double xd = (double)x.hi + (double)x.lo, xd2 = xd * xd;
+                b2 += xd2;
+                b4 += xd2 * xd2;
+            }
             ++n;
             r += dq;
             t += dr;
@@ -61,7 +69,7 @@ __global__ void __launch_bounds__(256) k_structure_fn(const float* __restrict__ 
                 ++r;
             }
         }
-        double s2 = (double)a2.hi + (double)a2.lo, s4 = (double)a4.hi + (double)a4.lo;
+        double s2 = ((double)a2.hi + (double)a2.lo) + b2, s4 = ((double)a4.hi + (double)a4.lo) + b4;
         double cnt = (double)n;
         s2 = warp_sum(s2);
         s4 = warp_sum(s4);

@@ -263,6 +263,22 @@ def test_structure_fn_parity(h):
     assert np.allclose(a[..., :2], ref[..., :2], rtol=1e-12, atol=0)
 
 
+def test_structure_fn_large_values_keep_fp64_range(h):
+    """Differences whose fourth power leaves the FP32 range (|x| >= 1e9) are
+    summed in FP64: the sums match the oracle instead of overflowing."""
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=(4, 2, 64)).astype(np.float32)
+    x[1, 0, 10] = 3.0e12
+    x[2, 1, 5] = -2.0e10
+    lags = np.array([0, 1, 3], np.int32)
+    ref = oracle.structure_fn(x, lags)
+    acc = qrs.qrs_structure_fn(h, torch.from_numpy(x).cuda(), torch.from_numpy(lags).cuda())
+    qrs.qrs_sync(h)
+    a = acc.cpu().numpy()
+    assert np.all(np.isfinite(a))
+    assert np.allclose(a[..., :2], ref[..., :2], rtol=1e-12, atol=0)
+
+
 def test_structure_fn_bad_lag_sets_device_error(h):
     x = torch.zeros(2, 1, 8, device="cuda")
     qrs.qrs_structure_fn(h, x, torch.tensor([9], dtype=torch.int32, device="cuda"))
