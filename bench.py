@@ -48,8 +48,8 @@ L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq-term evals/s"
 UNIT = "term/s"
 # DRAM bytes (read + write) per k_synth_fused launch on the workload above, from the ncu launch
-# list summarised in profiles/k_synth_fused_phase_screen.md (5.91 MB read + 147.13 MB write).
-SYNTH_TRAFFIC_BYTES = 153.04e6
+# list summarised in profiles/k_synth_fused_phase_screen.md (6.06 MB read + 147.19 MB write).
+SYNTH_TRAFFIC_BYTES = 153.25e6
 
 
 def _args():
