@@ -12,7 +12,8 @@ Printed: one JSON line.  `value` = freq-term evals/s (point x term x
 realisation) over all ranks, inputs resident on the device; `e2e` = the same
 through the C ABI with host buffers (pinned H2D of the points, D2H of the
 field) inside the timed region; `roofline` = the fused kernel against the
-MUFU (sin/cos) bound of the GPU; `cpu_baseline` = the FP64 CPU reference on a
+smaller of its two ALU bounds (one cosine per term on the MUFU, two 64-bit
+integer multiply-adds per term for the exact phase); `cpu_baseline` = the FP64 CPU reference on a
 bounded sample on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -38,6 +39,9 @@ sys.path.insert(0, HERE)
 MEASURED_PEAKS = os.path.join(HERE, "MEASURED_PEAKS.json")
 N_SM = 152
 MUFU_PER_SM_CLK = 16  # sin.approx / cos.approx results per SM per clock (measured, GB300)
+# 32 x 32 -> 64-bit integer multiply-adds (mad.wide.s32) per SM per clock, measured in dependent
+# chains (profiles/gb300_unit_rates.md); the exact fixed-point phase takes two per term.
+IMAD_WIDE_PER_SM_CLK = 25.07
 FMA_PER_SM_CLK = 128  # FP32 FMA lanes per SM per clock
 # FP32-pipe operations per aperture-term unit of the piston path that the method needs: the
 # phase f.x (2) and its double-float reduction (7), the accumulation (2), the Eq. 7 filter
@@ -48,8 +52,8 @@ L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq-term evals/s"
 UNIT = "term/s"
 # DRAM bytes (read + write) per k_synth_fused launch on the workload above, from the ncu launch
-# list summarised in profiles/k_synth_fused_phase_screen.md (6.06 MB read + 147.19 MB write).
-SYNTH_TRAFFIC_BYTES = 153.25e6
+# list summarised in profiles/k_synth_fused_phase_screen.md (5.53 MB read + 146.55 MB write).
+SYNTH_TRAFFIC_BYTES = 152.08e6
 
 
 def _args():
@@ -693,7 +697,10 @@ def run_ours(a):
     if os.path.exists(MEASURED_PEAKS):
         peaks = json.load(open(MEASURED_PEAKS))
     sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ))
-    peak_terms = N_SM * MUFU_PER_SM_CLK / 2 * sm_max * 1e6  # 2 MUFU (sin, cos) per term
+    # per term: 1 MUFU cosine (amplitude-phase form of Eq. 3) and 2 wide multiply-adds (exact phase)
+    mufu_terms = N_SM * MUFU_PER_SM_CLK * sm_max * 1e6
+    imad_terms = N_SM * IMAD_WIDE_PER_SM_CLK / 2 * sm_max * 1e6
+    peak_terms = min(mufu_terms, imad_terms)
     achieved = terms_step / (t_step / 1e3)  # per launch, one GPU
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -706,8 +713,10 @@ def run_ours(a):
                                        "dram__bytes_write.sum per launch of this kernel on this workload)",
                      "algorithmic_bytes": int(xy_np.nbytes + R * P * 4),
                      "kernel": "k_synth_fused (+ k_point_bound prepass, <0.01%)",
-                     "peak_basis": "152 SM x 16 sin|cos per SM-clock (measured) / 2 per term x %.0f MHz max clock"
-                                   % sm_max},
+                     "peak_basis": "min(1 cos per term at 16 per SM-clock: %.0f, 2 mad.wide.s32 per term at %.2f "
+                                   "per SM-clock: %.0f) Gterm/s, 152 SM at %.0f MHz (unit rates measured)"
+                                   % (mufu_terms / 1e9, IMAD_WIDE_PER_SM_CLK, imad_terms / 1e9, sm_max),
+                     "frac_of_mufu_bound": achieved / mufu_terms},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xy_np.nbytes),
                 "d2h_bytes_per_step": int(R * P * 4), "steps": e2e_steps},
         "gpu_launches": int(launches),

@@ -1,4 +1,4 @@
-// k_synth.cu -- K2: fused per-realisation draw + sincos-accumulate (Eq. 3 at
+// k_synth.cu -- K2: fused per-realisation draw + cosine-accumulate (Eq. 3 at
 // arbitrary points), and the point-bound prepass that picks its phase path.
 //
 // Work decomposition.  A work item is (realisation r, tile of TPB*PPT points);
@@ -7,16 +7,27 @@
 // visits few realisations.  The N_f terms of the current realisation are
 // drawn by the CTA itself (Philox + R2 + domain map, draw_term) into shared
 // memory once and reused by every tile of that realisation in its range;
-// three CTAs of 256 threads share an SM (registers capped for that);
+// two CTAs of 128 threads with 12 points each share an SM (registers capped
+// for that: the points give each thread 12 independent chains per term);
 // N_f beyond the shared-memory chunk is processed in chunks re-drawn per
 // item.  Each thread keeps PPT points in registers (strided by TPB, so the
 // loads and stores of a warp are coalesced) and loops over the terms, read
-// as one broadcast 16-byte shared-memory record per term:
-//   fixed-point path: {Fx, Fy (int32 scaled 2^a), A = F a, nB = -F b}
-//   double-float path: {fx, fy (float), A, nB}
+// as one broadcast 16-byte shared-memory record per term.
+//
+// Amplitude-phase form: the term F (a cos 2 pi phi - b sin 2 pi phi) of Eq. 3
+// is F amp cos 2 pi (phi + u 2^-24), with (amp, u) the Box-Muller radius and
+// 24-bit angle (or, for the literal Eq. 3 coefficients, sqrt2 R_n and R_u),
+// the angle's top bit moved into the sign of amp (u < 2^23): one cosine per
+// (point, term) instead of a sine and a cosine.  Records:
+//   fixed-point path: {Fx, Fy (int32 scaled 2^a), F amp, u (uint32)}; the
+//     offset u 2^(a+b-24) joins the 64-bit phase word as the addend of its
+//     first multiply-add, exactly
+//   double-float path: {fx, fy (float), F amp, psi = u 2^-24 in [0, 0.5)}
 // The phase path is uniform per launch: fixed point when fbound * xbound
 // <= 128 (its quantisation error, <= fbound xbound 2^-30 turns, is then below
-// the double-float path's), double-float otherwise.
+// the double-float path's), double-float otherwise.  Where the scales allow
+// a + b = 55 (fbound * xbound <= 64 with room in the ceilings), the fraction
+// is the low 23 bits of the phase word's high half and needs no shift.
 //
 // Accumulation: every 64 terms a partial sum is folded into the running sum,
 // which keeps the FP32 rounding error of N_f = 4096..16384-term sums near
@@ -27,10 +38,10 @@ namespace qrs {
 
 // Tunables (compile-time; the defaults are the measured best on GB300).
 #ifndef QRS_SYNTH_PPT
-#define QRS_SYNTH_PPT 4      // points per thread
+#define QRS_SYNTH_PPT 12     // points per thread
 #endif
 #ifndef QRS_SYNTH_MINB
-#define QRS_SYNTH_MINB 3     // minimum resident CTAs per SM (register cap)
+#define QRS_SYNTH_MINB 2     // minimum resident CTAs per SM (register cap)
 #endif
 #ifndef QRS_SYNTH_UNROLL
 #define QRS_SYNTH_UNROLL 4   // term-loop unroll
@@ -45,12 +56,18 @@ namespace qrs {
 #define QRS_SYNTH_PAIRED 1   // 1: paired FP32 instructions (two points per FFMA2) where they apply
 #endif
 
-constexpr int kSynthTPB = 256;
+#ifndef QRS_SYNTH_TPB
+#define QRS_SYNTH_TPB 128    // threads per CTA
+#endif
+constexpr int kSynthTPB = QRS_SYNTH_TPB;
 constexpr int kSynthPPT = QRS_SYNTH_PPT;
 constexpr int kSynthTile = kSynthTPB * kSynthPPT;
 constexpr int kSynthChunkMax = 4096;  // terms cached per CTA (64 KB)
 constexpr int kSynthGroup = QRS_SYNTH_GROUP;
 constexpr int kSynthUnroll = QRS_SYNTH_UNROLL;
+// Largest a + b of the fixed-point phase: 55 where the paired path can take
+// the fraction from the high word, 54 (funnel-shift extraction) otherwise.
+constexpr int kSynthMaxAB = (QRS_SYNTH_PAIRED && QRS_SYNTH_FOLD) ? 55 : 54;
 
 // Prepass: one CTA computes max(|x|, |y|) over all points (no atomics, no
 // zeroing); the synthesis kernel reads it to pick its phase path and scales.
@@ -81,10 +98,13 @@ cudaError_t launch_point_bound(const float* xy, int64_t n_points, float* d_bound
 }
 
 // The fixed-point path with paired FP32 instructions (FFMA2, two points per
-// instruction): the turn-to-radian conversion and the two accumulating FMAs
-// of points 2i and 2i + 1 share one instruction each.  Each element is
-// rounded exactly as the scalar fmaf would round it, so the sums are the
-// scalar path's bit for bit.
+// instruction): the turn-to-radian conversion and the accumulating FMA of
+// points 2i and 2i + 1 share one instruction each.  Each element is rounded
+// exactly as the scalar fmaf would round it, so the sums are the scalar
+// path's bit for bit.  The term's phase offset and the rounding bias form
+// the 64-bit addend C of the phase word once per term.  HI: a + b = 55, the
+// fraction bits are the low bits of the phase word's high half (no shift).
+template <bool HI>
 __device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restrict__ st, int len,
                                                            const int32_t (&X)[kSynthPPT], const int32_t (&Y)[kSynthPPT],
                                                            float (&acc)[kSynthPPT], const FixedScales& z)
@@ -101,20 +121,20 @@ __device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restr
 #pragma unroll kSynthUnroll
         for (int k = k0; k < k1; ++k) {
             const float4 T = st[k];
-            const float2 A = make_float2(T.z, T.z), nB = make_float2(T.w, T.w);
+            const float2 A = make_float2(T.z, T.z);
+            const uint64_t C = (uint64_t)__float_as_uint(T.w) * z.psi_mul + z.bias;
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                const uint32_t m0 = phase_fx_word(__float_as_int(T.x), __float_as_int(T.y), X[2 * q], Y[2 * q],
-                                                  z.bias, z.shift);
-                const uint32_t m1 = phase_fx_word(__float_as_int(T.x), __float_as_int(T.y), X[2 * q + 1],
-                                                  Y[2 * q + 1], z.bias, z.shift);
+                const int32_t Fx = __float_as_int(T.x), Fy = __float_as_int(T.y);
+                const uint32_t m0 = HI ? phase_fx_word_hi(Fx, Fy, X[2 * q], Y[2 * q], C)
+                                       : phase_fx_word(Fx, Fy, X[2 * q], Y[2 * q], C, z.shift);
+                const uint32_t m1 = HI ? phase_fx_word_hi(Fx, Fy, X[2 * q + 1], Y[2 * q + 1], C)
+                                       : phase_fx_word(Fx, Fy, X[2 * q + 1], Y[2 * q + 1], C, z.shift);
                 const float2 mant = make_float2(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u),
                                                 __uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u));
                 const float2 ang = __ffma2_rn(mant, two_pi, neg_two_pi);  // (1 + t) 2 pi - 2 pi
                 const float2 c = make_float2(__cosf(ang.x), __cosf(ang.y));
-                const float2 sn = make_float2(__sinf(ang.x), __sinf(ang.y));
                 part[q] = __ffma2_rn(A, c, part[q]);
-                part[q] = __ffma2_rn(nB, sn, part[q]);
             }
         }
 #pragma unroll
@@ -125,10 +145,10 @@ __device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restr
     }
 }
 
-// The double-float path with paired FP32 instructions: phase_df2 of points
-// 2i and 2i + 1 (their coordinates as float bits in X, Y), the turn-to-radian
-// product and the accumulating FMAs two points at a time, each lane rounded
-// as in the scalar path.
+// The double-float path with paired FP32 instructions: phase_df2_psi of
+// points 2i and 2i + 1 (their coordinates as float bits in X, Y), the
+// turn-to-radian product and the accumulating FMA two points at a time, each
+// lane rounded as in the scalar path.
 __device__ __forceinline__ void accumulate_chunk_df_paired(const float4* __restrict__ st, int len,
                                                            const int32_t (&X)[kSynthPPT], const int32_t (&Y)[kSynthPPT],
                                                            float (&acc)[kSynthPPT])
@@ -149,14 +169,12 @@ __device__ __forceinline__ void accumulate_chunk_df_paired(const float4* __restr
 #pragma unroll kSynthUnroll
         for (int k = k0; k < k1; ++k) {
             const float4 T = st[k];
-            const float2 A = make_float2(T.z, T.z), nB = make_float2(T.w, T.w);
+            const float2 A = make_float2(T.z, T.z);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                const float2 ang = __fmul2_rn(phase_df2(T.x, T.y, px[q], py[q]), two_pi);
+                const float2 ang = __fmul2_rn(phase_df2_psi(T.x, T.y, px[q], py[q], T.w), two_pi);
                 const float2 c = make_float2(__cosf(ang.x), __cosf(ang.y));
-                const float2 sn = make_float2(__sinf(ang.x), __sinf(ang.y));
                 part[q] = __ffma2_rn(A, c, part[q]);
-                part[q] = __ffma2_rn(nB, sn, part[q]);
             }
         }
 #pragma unroll
@@ -180,22 +198,22 @@ __device__ __forceinline__ void accumulate_chunk(const float4* __restrict__ st, 
 #pragma unroll kSynthUnroll
         for (int k = k0; k < k1; ++k) {
             const float4 T = st[k];
+            const uint64_t C = FIXED ? (uint64_t)__float_as_uint(T.w) * z.psi_mul + z.bias : 0ull;
 #pragma unroll
             for (int j = 0; j < kSynthPPT; ++j) {
-                float s, c;
+                float ang;
                 if (FIXED) {
 #if QRS_SYNTH_FOLD
-                    const float ang = phase_fx_rad(__float_as_int(T.x), __float_as_int(T.y), X[j], Y[j], z.bias, z.shift);
-                    s = __sinf(ang);
-                    c = __cosf(ang);
+                    ang = phase_fx_rad(__float_as_int(T.x), __float_as_int(T.y), X[j], Y[j], C, z.shift);
 #else
-                    sincos_turns(phase_fx(__float_as_int(T.x), __float_as_int(T.y), X[j], Y[j], z.bias, z.shift), s, c);
+                    ang = phase_fx(__float_as_int(T.x), __float_as_int(T.y), X[j], Y[j], C, z.shift) *
+                          6.28318530717958648f;
 #endif
                 } else {
-                    sincos_turns(phase_df(T.x, T.y, __int_as_float(X[j]), __int_as_float(Y[j])), s, c);
+                    ang = phase_df_psi(T.x, T.y, __int_as_float(X[j]), __int_as_float(Y[j]), T.w) *
+                          6.28318530717958648f;
                 }
-                part[j] = fmaf(T.z, c, part[j]);
-                part[j] = fmaf(T.w, s, part[j]);
+                part[j] = fmaf(T.z, __cosf(ang), part[j]);
             }
         }
 #pragma unroll
@@ -208,7 +226,7 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
                                                            float fbound, int chunk, int64_t n_tiles, int64_t n_items)
 {
     extern __shared__ float4 sterm[];
-    const FixedScales z = fixed_scales(fbound, *d_xbound, QRS_SYNTH_FOLD != 0);
+    const FixedScales z = fixed_scales(fbound, *d_xbound, QRS_SYNTH_FOLD != 0, kSynthMaxAB);
     const int64_t G = gridDim.x;
     const int64_t it0 = (n_items * (int64_t)blockIdx.x) / G;
     const int64_t it1 = (n_items * ((int64_t)blockIdx.x + 1)) / G;
@@ -241,17 +259,22 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
                 __syncthreads();  // previous chunk fully consumed
                 const uint64_t n0 = (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k_begin;
                 for (int q = threadIdx.x; q < len; q += kSynthTPB) {
-                    const Term t = draw_term<false>(p, n0 + (uint64_t)q, k_begin + q);
+                    Words w;
+                    const Term t = draw_term<false, false>(p, n0 + (uint64_t)q, k_begin + q, &w);
+                    float amp;
+                    uint32_t u;
+                    coef_polar_from_words(p, n0 + (uint64_t)q, w, amp, u);
                     float4 rec;
                     if (z.use_fixed) {
                         rec.x = __int_as_float(__float2int_rn(t.fx * z.fscale));
                         rec.y = __int_as_float(__float2int_rn(t.fy * z.fscale));
+                        rec.w = __uint_as_float(u);
                     } else {
                         rec.x = t.fx;
                         rec.y = t.fy;
+                        rec.w = (float)u * 0x1p-24f;
                     }
-                    rec.z = t.F * t.a;
-                    rec.w = -(t.F * t.b);
+                    rec.z = t.F * amp;
                     sterm[q] = rec;
                 }
                 __syncthreads();
@@ -260,7 +283,8 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
             }
             if (z.use_fixed) {
 #if QRS_SYNTH_PAIRED && QRS_SYNTH_FOLD
-                accumulate_chunk_fx_paired(sterm, len, X, Y, acc, z);
+                if (z.shift == 32) accumulate_chunk_fx_paired<true>(sterm, len, X, Y, acc, z);
+                else accumulate_chunk_fx_paired<false>(sterm, len, X, Y, acc, z);
 #else
                 accumulate_chunk<true>(sterm, len, X, Y, acc, z);
 #endif

@@ -455,6 +455,37 @@ __device__ __forceinline__ void coef_from_words(const DrawParams& p, uint64_t n,
     }
 }
 
+// The same coefficients in amplitude-phase form: a cos t - b sin t =
+// amp cos(t + 2 pi u 2^-24), so that a sum over terms takes one cosine each.
+// GAUSS: (a, b) = rad (cos, sin)(2 pi U2), hence amp = rad, u = the 24-bit
+// integer of U2; literal Eq. 3: amp = sqrt2 R_n (signed), u = the 24-bit
+// integer of R_u.  The top bit of u (half a turn) then moves into the sign of
+// amp (cos(t + pi) = -cos t), leaving u < 2^23 (an offset in [0, 0.5) turns,
+// exact): the sign of amp is thereby independent of the angle, so that angle
+// errors odd in the angle (the FP32 rounding of 2 pi in the turn-to-radian
+// step, the cosine's own reduction) average out over the terms instead of
+// adding up with the always-positive Box-Muller radius.
+__device__ __forceinline__ void coef_polar_from_words(const DrawParams& p, uint64_t n, const Words& w, float& amp,
+                                                      uint32_t& u)
+{
+    const float U1 = (float)((w.w2 >> 8) + 1u) * 0x1p-24f;
+    const float rad = sqrtf(-2.0f * logf(U1));
+    if (p.coef == kCoefEq3) {
+        const float U2 = (float)(w.w3 >> 8) * 0x1p-24f;
+        const float Rn = rad * cospif(2.0f * U2);
+        const Words v = philox4x32_10((uint32_t)n, (uint32_t)(n >> 32), kStreamEq3, 0u, p.key0, p.key1);
+        amp = 1.41421356237309515f * Rn;
+        u = v.w0 >> 8;
+    } else {
+        amp = rad;
+        u = w.w3 >> 8;
+    }
+    if (u & 0x800000u) {
+        amp = -amp;
+        u &= 0x7FFFFFu;
+    }
+}
+
 // Coefficients of stream point n alone (no placement, no FP64).
 __device__ __forceinline__ float2 draw_coef(const DrawParams& p, uint64_t n)
 {
@@ -472,8 +503,9 @@ __device__ __forceinline__ float2 draw_coef(const DrawParams& p, uint64_t n)
 static __device__ __noinline__ float airy_filter_call(float f, float D, float d) { return airy_filter(f, D, d); }
 
 // CELL = false skips the cell index (FP64 work the synthesis and piston
-// kernels do not use).
-template <bool CELL = true>
+// kernels do not use); COEF = false skips the coefficients (a, b) for callers
+// that take them in amplitude-phase form from the returned words.
+template <bool CELL = true, bool COEF = true>
 __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64_t k, Words* words_out = nullptr,
                                           uint64_t* Sx_out = nullptr, uint64_t* Sy_out = nullptr)
 {
@@ -577,7 +609,12 @@ __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64
     t.J = J;
     t.A = (p.ap_D > 0.0f) ? airy_filter_call(sqrtf(f2), p.ap_D, p.ap_d) : 1.0f;
     t.F = sqrtf(psd_w(p.psd_c, p.psd_a, f2) * J * p.inv_nf) * t.A;
-    coef_from_words(p, n, w, t.a, t.b);
+    if (COEF) {
+        coef_from_words(p, n, w, t.a, t.b);
+    } else {
+        t.a = 0.0f;
+        t.b = 0.0f;
+    }
     if (words_out) *words_out = w;
     if (Sx_out) *Sx_out = Sx;
     if (Sy_out) *Sy_out = Sy;
@@ -602,6 +639,21 @@ __device__ __forceinline__ float phase_df(float fx, float fy, float x, float y)
     return __fadd_rn(r, __fadd_rn(e1, e2));
 }
 
+// phase_df with a per-term phase offset psi (turns, |psi| <= 0.5) taken into
+// the small parts: r + (psi + (e1 + e2)) (the scalar form of phase_df2_psi).
+__device__ __forceinline__ float phase_df_psi(float fx, float fy, float x, float y, float psi)
+{
+    const float p1 = __fmul_rn(fx, x);
+    const float e1 = __fmaf_rn(fx, x, -p1);
+    const float p2 = __fmul_rn(fy, y);
+    const float e2 = __fmaf_rn(fy, y, -p2);
+    const float M = 12582912.0f;  // 1.5 * 2^23
+    const float n1 = __fsub_rn(__fadd_rn(p1, M), M);
+    const float n2 = __fsub_rn(__fadd_rn(p2, M), M);
+    const float r = __fadd_rn(__fsub_rn(p1, n1), __fsub_rn(p2, n2));
+    return __fadd_rn(r, __fadd_rn(psi, __fadd_rn(e1, e2)));
+}
+
 // phase_df for two positions at once (x.x, y.x) and (x.y, y.y), in paired FP32
 // instructions, without a negation of a pair: the product errors are formed
 // negated (fma(-f, x, p) = -fma(f, x, -p) exactly, rounding being symmetric),
@@ -621,6 +673,25 @@ __device__ __forceinline__ float2 phase_df2(float fx, float fy, float2 x, float2
     const float2 n2 = __fadd2_rn(__fadd2_rn(p2, M), NM);
     const float2 r = __fadd2_rn(__ffma2_rn(n1, MINUS1, p1), __ffma2_rn(n2, MINUS1, p2));
     return __ffma2_rn(__fadd2_rn(ne1, ne2), MINUS1, r);  // r + (e1 + e2)
+}
+
+// phase_df2 with a per-term phase offset psi (turns, |psi| <= 0.5) taken into
+// the small parts: r + (psi + (e1 + e2)), |result| <= 1.5 + eps turns.
+__device__ __forceinline__ float2 phase_df2_psi(float fx, float fy, float2 x, float2 y, float psi)
+{
+    const float2 FX = make_float2(fx, fx), FY = make_float2(fy, fy);
+    const float2 NFX = make_float2(-fx, -fx), NFY = make_float2(-fy, -fy);
+    const float2 M = make_float2(12582912.0f, 12582912.0f), NM = make_float2(-12582912.0f, -12582912.0f);
+    const float2 MINUS1 = make_float2(-1.0f, -1.0f);
+    const float2 p1 = __fmul2_rn(FX, x);
+    const float2 ne1 = __ffma2_rn(NFX, x, p1);  // -e1
+    const float2 p2 = __fmul2_rn(FY, y);
+    const float2 ne2 = __ffma2_rn(NFY, y, p2);  // -e2
+    const float2 n1 = __fadd2_rn(__fadd2_rn(p1, M), NM);
+    const float2 n2 = __fadd2_rn(__fadd2_rn(p2, M), NM);
+    const float2 r = __fadd2_rn(__ffma2_rn(n1, MINUS1, p1), __ffma2_rn(n2, MINUS1, p2));
+    const float2 sm = __ffma2_rn(__fadd2_rn(ne1, ne2), MINUS1, make_float2(psi, psi));  // psi + (e1 + e2)
+    return __fadd2_rn(r, sm);
 }
 
 // phase_df of two frequencies (fx.x, fy.x), (fx.y, fy.y) at one position, in
@@ -669,6 +740,15 @@ __device__ __forceinline__ uint32_t phase_fx_word(int32_t Fx, int32_t Fy, int32_
     return __funnelshift_rc((uint32_t)acc, (uint32_t)(acc >> 32), shift);
 }
 
+// phase_fx_word at a + b = 55: the 23 fraction bits are the low bits of the
+// high word of the phase word, taken without a shift.
+__device__ __forceinline__ uint32_t phase_fx_word_hi(int32_t Fx, int32_t Fy, int32_t X, int32_t Y, uint64_t bias)
+{
+    uint64_t acc = bias + (uint64_t)((int64_t)Fy * (int64_t)Y);
+    acc += (uint64_t)((int64_t)Fx * (int64_t)X);
+    return (uint32_t)(acc >> 32);
+}
+
 __device__ __forceinline__ float phase_fx_rad(int32_t Fx, int32_t Fy, int32_t X, int32_t Y, uint64_t bias,
                                               uint32_t shift)
 {
@@ -693,7 +773,9 @@ __device__ __host__ __forceinline__ int ceil_log2(double v)
 
 // Per-launch scales of the fixed-point phase (phase_fx / phase_fx_rad) from
 // the frequency bound and the point bound: a = 31 - ceil(log2 fbound),
-// b = 31 - ceil(log2 xbound) (capped so that a + b <= 54), use_fixed when
+// b = 31 - ceil(log2 xbound), b lowered so that a + b <= max_ab (54 for the
+// funnel-shift extraction, whose shift a + b - 23 is at most 31; 55 for a
+// caller that takes the high word when shift = 32), use_fixed when
 // fbound xbound <= 128 (then the quantisation error, <= fbound xbound 2^-30
 // turns, is below the double-float path's).  `radians`: bias for
 // phase_fx_rad ([0, 1) turns) instead of phase_fx ([-0.5, 0.5) turns).
@@ -702,22 +784,24 @@ struct FixedScales {
     float fscale, xscale;  // 2^a, 2^b
     uint64_t bias;
     uint32_t shift;
+    uint32_t psi_mul;      // 2^(a+b-24): a 24-bit phase offset u 2^-24 turns is u psi_mul in the phase word
 };
 
-__device__ __forceinline__ FixedScales fixed_scales(float fbound, float xbound, bool radians)
+__device__ __forceinline__ FixedScales fixed_scales(float fbound, float xbound, bool radians, int max_ab = 54)
 {
     FixedScales z;
     const double fb = (double)fbound * (1.0 + 0x1p-20);
     const double xb = (double)xbound * (1.0 + 0x1p-20);
     z.use_fixed = (fb * xb <= 128.0);
     const int a = 31 - ceil_log2(fb);
-    int b = (xb > 0.0) ? 31 - ceil_log2(xb) : 54 - a;
-    if (a + b > 54) b = 54 - a;
+    int b = (xb > 0.0) ? 31 - ceil_log2(xb) : max_ab - a;
+    if (a + b > max_ab) b = max_ab - a;
     if (a + b < 24) z.use_fixed = false;
     const int ab = a + b;
     z.fscale = ldexpf(1.0f, a);
     z.xscale = ldexpf(1.0f, b);
     z.shift = (uint32_t)(ab - 23);
+    z.psi_mul = (ab >= 24 && ab <= 55) ? (1u << (ab - 24)) : 0u;
     // half an output ulp (rounding), plus half a revolution for [-0.5, 0.5) turns
     const uint64_t half_ulp = (ab >= 24 && ab <= 64) ? (1ull << (ab - 24)) : 0ull;
     z.bias = radians ? half_ulp : ((ab >= 1 && ab <= 64) ? ((1ull << (ab - 1)) + half_ulp) : 0ull);

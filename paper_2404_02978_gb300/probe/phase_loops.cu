@@ -1,5 +1,9 @@
 // Inner-loop probe: (point, term) throughput of the fused synthesis inner loop with the
-// double-float phase, the 64-bit fixed-point phase, and no reduction (the MUFU bound).
+// double-float phase, the 64-bit fixed-point phase, and no reduction (the MUFU bound); then the
+// same in amplitude-phase form (one cosine per (point, term)): no reduction, the fixed-point
+// phase with the fraction in the high word (scalar and with paired FP32 instructions), a
+// bare cosine per (point, term), and variants of the integer phase (alone; one 64-bit product;
+// two independent products; 32-bit halves with an explicit carry; explicit mad.wide.s32; unsigned products).
 //   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o /tmp/phase_loops paper_2404_02978_gb300/probe/phase_loops.cu && /tmp/phase_loops
 #include <cstdio>
 #include <cstdint>
@@ -47,12 +51,77 @@ __global__ void __launch_bounds__(TPB) k(const float4* terms, const float2* xy, 
           float s=sinr(a), co=cosr(a);
           acc[j]=fmaf(T.z,co,acc[j]); acc[j]=fmaf(T.w,s,acc[j]);
         }
-      } else {
+      } else if(V==2){
         #pragma unroll
         for(int j=0;j<PPT;j++){
           float a=fmaf(T.x,x[j],T.y*y[j]);
           float s=sinr(a), co=cosr(a);
           acc[j]=fmaf(T.z,co,acc[j]); acc[j]=fmaf(T.w,s,acc[j]);
+        }
+      } else if(V==3){
+        #pragma unroll
+        for(int j=0;j<PPT;j++){
+          float a=fmaf(T.x,x[j],T.y*y[j]);
+          acc[j]=fmaf(T.z,cosr(a),acc[j]);
+        }
+      } else if(V==4 || V==5){
+        int fx=__float_as_int(T.x), fy=__float_as_int(T.y);
+        const uint64_t C=(uint64_t)__float_as_uint(T.w)*(1u<<30)+(1ull<<31);
+        if(V==4){
+          #pragma unroll
+          for(int j=0;j<PPT;j++){
+            uint64_t pr=C+(uint64_t)((long long)fy*yi[j]); pr+=(uint64_t)((long long)fx*xi[j]);
+            uint32_t hi=(uint32_t)(pr>>32);
+            float a=fmaf(__uint_as_float((hi&0x007FFFFFu)|0x3F800000u),6.2831853f,-6.2831853f);
+            acc[j]=fmaf(T.z,cosr(a),acc[j]);
+          }
+        } else {
+          const float2 A=make_float2(T.z,T.z), tp=make_float2(6.2831853f,6.2831853f), ntp=make_float2(-6.2831853f,-6.2831853f);
+          #pragma unroll
+          for(int q=0;q<PPT/2;q++){
+            uint64_t p0=C+(uint64_t)((long long)fy*yi[2*q]); p0+=(uint64_t)((long long)fx*xi[2*q]);
+            uint64_t p1=C+(uint64_t)((long long)fy*yi[2*q+1]); p1+=(uint64_t)((long long)fx*xi[2*q+1]);
+            const float2 m=make_float2(__uint_as_float(((uint32_t)(p0>>32)&0x007FFFFFu)|0x3F800000u),
+                                       __uint_as_float(((uint32_t)(p1>>32)&0x007FFFFFu)|0x3F800000u));
+            const float2 a=__ffma2_rn(m,tp,ntp);
+            float2 pa=make_float2(acc[2*q],acc[2*q+1]);
+            pa=__ffma2_rn(A,make_float2(cosr(a.x),cosr(a.y)),pa);
+            acc[2*q]=pa.x; acc[2*q+1]=pa.y;
+          }
+        }
+      } else if(V==6){
+        #pragma unroll
+        for(int j=0;j<PPT;j++) acc[j]+=cosr(T.x*x[j]);
+      } else {
+        int fx=__float_as_int(T.x), fy=__float_as_int(T.y);
+        const uint64_t C=(uint64_t)__float_as_uint(T.w)*(1u<<30)+(1ull<<31);
+        #pragma unroll
+        for(int j=0;j<PPT;j++){
+          uint32_t hi;
+          if(V==7){         // the integer phase alone, no cosine
+            uint64_t pr=C+(uint64_t)((long long)fy*yi[j]); pr+=(uint64_t)((long long)fx*xi[j]); hi=(uint32_t)(pr>>32);
+          } else if(V==8){  // one 64-bit product per (point, term)
+            uint64_t pr=C+(uint64_t)((long long)fx*xi[j]); hi=(uint32_t)(pr>>32);
+          } else if(V==9){  // two independent 64-bit products, then a 64-bit add
+            uint64_t p1=C+(uint64_t)((long long)fy*yi[j]); uint64_t p2=(uint64_t)((long long)fx*xi[j]); hi=(uint32_t)((p1+p2)>>32);
+          } else if(V==11 || V==12){  // the two products as explicit mad.wide.s32 (64-bit addend)
+            uint64_t pr;
+            asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(pr) : "r"(fy), "r"(yi[j]), "l"(C));
+            asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(pr) : "r"(fx), "r"(xi[j]));
+            hi=(uint32_t)(pr>>32);
+          } else if(V==13 || V==14){  // unsigned 32 x 32 -> 64 products (C++), with and without the cosine
+            uint64_t pr=C+(uint64_t)(uint32_t)fy*(uint32_t)yi[j]; pr+=(uint64_t)(uint32_t)fx*(uint32_t)xi[j];
+            hi=(uint32_t)(pr>>32);
+          } else {          // 32-bit halves: lo and hi products, carry by add.cc
+            uint32_t l1=(uint32_t)fy*(uint32_t)yi[j], h1=__mulhi(fy,yi[j]);
+            uint32_t l2=(uint32_t)fx*(uint32_t)xi[j], h2=__mulhi(fx,xi[j]);
+            uint32_t lo, hh;
+            asm("{.reg .u32 c1; add.cc.u32 c1, %2, %3; addc.u32 %1, %4, %5; add.cc.u32 %0, c1, %6; addc.u32 %1, %1, %7;}"
+                : "=r"(lo), "=r"(hh) : "r"(l1), "r"(l2), "r"(h1), "r"(h2), "r"((uint32_t)C), "r"((uint32_t)(C>>32)));
+            hi=hh; (void)lo;
+          }
+          float a=fmaf(__uint_as_float((hi&0x007FFFFFu)|0x3F800000u),6.2831853f,-6.2831853f);
+          if(V==7 || V==12 || V==14) acc[j]=fmaf(T.z,a,acc[j]); else acc[j]=fmaf(T.z,cosr(a),acc[j]);
         }
       }
     }
@@ -67,13 +136,20 @@ int main(){
   float4 h[NT]; for(int i=0;i<NT;i++) h[i]=make_float4(0.01f*(i%97)-0.4f,0.013f*(i%89)-0.5f,0.1f,-0.1f);
   CK(cudaMemcpy(terms,h,sizeof(h),cudaMemcpyHostToDevice)); CK(cudaMemset(xy,0,np*sizeof(float2)));
   cudaEvent_t a,b; cudaEventCreate(&a); cudaEventCreate(&b);
-  const char* nm[3]={"doublefloat13","fixedpoint64","noreduce"};
-  for(int v=0;v<3;v++){ for(int rep=0;rep<3;rep++){
+  const char* nm[15]={"doublefloat13","fixedpoint64","noreduce","noreduce-1cos","fixedhi-1cos","fixedhi-1cos-x2","cos-only",
+                      "fixedhi-nocos","onewide-1cos","twoindep-1cos","halves-1cos","madwide-1cos","madwide-nocos","unsigned-1cos","unsigned-nocos"};
+  for(int v=0;v<15;v++){ for(int rep=0;rep<3;rep++){
     cudaEventRecord(a);
     if(v==0)k<0><<<blocks,TPB>>>(terms,xy,out,2); if(v==1)k<1><<<blocks,TPB>>>(terms,xy,out,2); if(v==2)k<2><<<blocks,TPB>>>(terms,xy,out,2);
+    if(v==3)k<3><<<blocks,TPB>>>(terms,xy,out,2); if(v==4)k<4><<<blocks,TPB>>>(terms,xy,out,2);
+    if(v==5)k<5><<<blocks,TPB>>>(terms,xy,out,2); if(v==6)k<6><<<blocks,TPB>>>(terms,xy,out,2);
+    if(v==7)k<7><<<blocks,TPB>>>(terms,xy,out,2); if(v==8)k<8><<<blocks,TPB>>>(terms,xy,out,2);
+    if(v==9)k<9><<<blocks,TPB>>>(terms,xy,out,2); if(v==10)k<10><<<blocks,TPB>>>(terms,xy,out,2);
+    if(v==11)k<11><<<blocks,TPB>>>(terms,xy,out,2); if(v==12)k<12><<<blocks,TPB>>>(terms,xy,out,2);
+    if(v==13)k<13><<<blocks,TPB>>>(terms,xy,out,2); if(v==14)k<14><<<blocks,TPB>>>(terms,xy,out,2);
     cudaEventRecord(b); CK(cudaEventSynchronize(b)); float ms; cudaEventElapsedTime(&ms,a,b);
     double tp=(double)np*NT*2;
-    if(rep==2) printf("%-14s %.3f ms %.3e term-pts/s  per-SM-clk@1995=%.2f\n",nm[v],ms,tp/(ms*1e-3),tp/(ms*1e-3)/nsm/1.995e9);
+    if(rep==2) printf("%-14s %.3f ms %.3e term-pts/s  per-SM-clk@2070=%.2f\n",nm[v],ms,tp/(ms*1e-3),tp/(ms*1e-3)/nsm/2.07e9);
   }}
   CK(cudaGetLastError()); return 0;
 }

@@ -1,5 +1,5 @@
-// Unit-rate probe (sin.approx, cos.approx, ex2.approx, FFMA, DFMA, paired FFMA2 per SM per clock): the
-// denominators of the ALU rooflines.  Build and run on the GPU:
+// Unit-rate probe (sin.approx, cos.approx, ex2.approx, FFMA, DFMA, paired FFMA2, and the 32 x 32 -> 64-bit
+// and 32-bit integer multiply-adds, per SM per clock): the denominators of the ALU rooflines.  Build and run on the GPU:
 //   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o /tmp/unit_rates paper_2404_02978_gb300/probe/unit_rates.cu && /tmp/unit_rates
 #include <cstdio>
 #include <cuda_runtime.h>
@@ -37,6 +37,26 @@ __global__ void k2(float* out, int iters, float a) {
   for (int j = 0; j < 8; ++j) t += x[j].x + x[j].y;
   out[blockIdx.x * blockDim.x + threadIdx.x] = t;
 }
+// Integer multiply-adds, 8 independent chains per thread, each step depending on the last through
+// its multiplicand (nothing to hoist): OP 0 = mad.wide.s32 w = lo(w) a + w (64-bit addend and
+// result), OP 1 = mad.lo.s32, OP 2 = mul.hi.s32 feeding an add.
+template <int OP>
+__global__ void ki(long long* out, int iters, int a) {
+  long long w[8];
+  int v[8];
+  for (int j = 0; j < 8; ++j) { w[j] = threadIdx.x * 7 + j; v[j] = threadIdx.x * 13 + j; }
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (OP == 0) asm volatile("{.reg .s32 l; cvt.u32.u64 l, %0; mad.wide.s32 %0, l, %1, %0;}" : "+l"(w[j]) : "r"(a));
+      else if (OP == 1) asm volatile("mad.lo.s32 %0, %0, %1, %1;" : "+r"(v[j]) : "r"(a));
+      else asm volatile("{.reg .s32 t; mul.hi.s32 t, %0, %1; add.s32 %0, %0, t;}" : "+r"(v[j]) : "r"(a));
+    }
+  }
+  long long t = 0;
+  for (int j = 0; j < 8; ++j) t += w[j] + v[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
 int main(){
   cudaDeviceProp p; CK(cudaGetDeviceProperties(&p,0));
   int clk=0; cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0);
@@ -59,6 +79,20 @@ int main(){
       float ms; cudaEventElapsedTime(&ms,a,b);
       double ops=(double)blocks*thr*iters*8*(op==5?2:1);  // FFMA2: two FMAs per instruction
       if(rep==2) printf("%-11s %.3f ms  %.3e ops/s  per-SM-per-clk@2070MHz=%.2f  @1900=%.2f\n", op==4?"dfma":op==5?"ffma2 (FMAs)":names[op], ms, ops/(ms*1e-3), ops/(ms*1e-3)/nsm/2.07e9, ops/(ms*1e-3)/nsm/1.9e9);
+    }
+  }
+  const char* inames[3] = {"mad.wide.s32", "mad.lo.s32", "mul.hi+add"};
+  for (int op = 0; op < 3; op++) {
+    for (int rep = 0; rep < 3; rep++) {
+      cudaEventRecord(a);
+      if (op == 0) ki<0><<<blocks, thr>>>((long long*)o, 4096, 0x12345);
+      if (op == 1) ki<1><<<blocks, thr>>>((long long*)o, 4096, 0x12345);
+      if (op == 2) ki<2><<<blocks, thr>>>((long long*)o, 4096, 0x12345);
+      cudaEventRecord(b); CK(cudaEventSynchronize(b));
+      float ms; cudaEventElapsedTime(&ms, a, b);
+      double ops = (double)blocks * thr * 4096 * 8;
+      if (rep == 2) printf("%-11s %.3f ms  %.3e ops/s  per-SM-per-clk@2070MHz=%.2f\n", inames[op], ms, ops / (ms * 1e-3),
+                           ops / (ms * 1e-3) / nsm / 2.07e9);
     }
   }
   CK(cudaGetLastError());
