@@ -43,10 +43,11 @@ MUFU_PER_SM_CLK = 16  # sin.approx / cos.approx results per SM per clock (measur
 # chains (profiles/gb300_unit_rates.md); the exact fixed-point phase takes two per term.
 IMAD_WIDE_PER_SM_CLK = 25.07
 FMA_PER_SM_CLK = 128  # FP32 FMA lanes per SM per clock
-# FP32-pipe operations per aperture-term unit of the piston path that the method needs: the
-# phase f.x (2) and its double-float reduction (7), the accumulation (2), the Eq. 7 filter
-# (11-term series by Horner below x = 4: 12) and its product with the two coefficients (2).
-PISTON_FMA_OPS = 25
+# FP32-pipe operations per aperture-term unit of the piston path that the method needs, in the
+# amplitude-phase form of Eq. 3 (one cosine): the phase f.x (2), its double-float reduction (7)
+# and the term's phase offset (1), the accumulation (1), the Eq. 7 filter (11-term series by
+# Horner below x = 4: 12) and its product with the amplitude (1).
+PISTON_FMA_OPS = 24
 SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq-term evals/s"
@@ -479,7 +480,7 @@ def measure_batched(qrs, h, torch, dev):
         qrs.qrs_sync(h, stream)
         ms.append(e0.elapsed_time(e1))
     t = min(ms) / 1e3
-    mufu = N_SM * MUFU_PER_SM_CLK / 2 * SM_MAX_MHZ * 1e6
+    mufu = N_SM * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6  # one cosine per unit
     fma = N_SM * FMA_PER_SM_CLK / PISTON_FMA_OPS * SM_MAX_MHZ * 1e6
     peak = min(mufu, fma)
     return {"workload": "1000 interferometers, n_ap 4-64, N_f 256-8192, 256 realisations, all pairs "
@@ -489,7 +490,7 @@ def measure_batched(qrs, h, torch, dev):
             "gpu_launches_first_call": h.launch_count() - launches0 - 3,
             "roofline": {"bound": "alu", "achieved": units / t / 1e9, "peak": peak / 1e9, "unit": "Gunit/s",
                          "frac": units / t / peak, "kernel": "k_piston_persistent",
-                         "peak_basis": "min(2 MUFU per unit: %.0f, %d FP32-pipe ops per unit at 128 per SM-clock: "
+                         "peak_basis": "min(1 MUFU per unit: %.0f, %d FP32-pipe ops per unit at 128 per SM-clock: "
                                        "%.0f) Gunit/s at %.0f MHz" % (mufu / 1e9, PISTON_FMA_OPS, fma / 1e9,
                                                                        SM_MAX_MHZ)}}
 

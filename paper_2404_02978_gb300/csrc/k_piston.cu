@@ -4,9 +4,10 @@
 // terms into shared memory (fused draw, chunks of kPisChunk terms), then its
 // warps take (aperture, 256-term slice) units round-robin: the 32 lanes split
 // the slice's terms, each lane forms F A_a(|f|) (a cos 2 pi f.p - b sin 2 pi f.p)
-// with the double-float phase (aperture centres lie up to hundreds of metres
-// from the origin), and a warp-shuffle reduction gives the slice's partial
-// piston.  Partials are folded in a fixed order (deterministic sums), then
+// in amplitude-phase form, A_a(|f|) F amp cos 2 pi (f.p + psi) (one cosine;
+// amp and psi as in the fused synthesis kernel), with the double-float phase
+// (aperture centres lie up to hundreds of metres from the origin), and a
+// warp-shuffle reduction gives the slice's partial piston.  Partials are folded in a fixed order (deterministic sums), then
 // the pair differences are written.
 //
 // Scheduling: a single job runs as a grid-stride over its realisations; a
@@ -45,7 +46,7 @@ struct PisShape {
 
 template <int SLICES>
 struct PisShared {
-    float4 rec[kPisChunk];             // fx, fy, A = F a, nB = -F b
+    float4 rec[kPisChunk];             // fx, fy, F amp, psi (turns, [0, 0.5))
     float fabs_[kPisChunk];            // |f|
     uint16_t sidx[kPisChunk];          // terms in bucket order (sorted chunks)
     int bcount[kPisMaxWarps][kPisBuckets];
@@ -85,10 +86,7 @@ __device__ __forceinline__ float unit_sum(const PisShared<SLICES>& sh, int k0, i
         const float4 T = sh.rec[j];
         const float fa = sh.fabs_[j];
         const float A = OBST ? airy_filter_w(fa, D, d, wD, wd) : airy_g(3.14159265358979f * fa * D);
-        float s, c;
-        sincos_turns(phase_df(T.x, T.y, x, y), s, c);
-        acc = fmaf(A * T.z, c, acc);
-        acc = fmaf(A * T.w, s, acc);
+        acc = fmaf(A * T.z, __cosf(phase_df_psi(T.x, T.y, x, y, T.w) * 6.28318530717958648f), acc);
     }
     return acc;
 }
@@ -125,7 +123,7 @@ __device__ __forceinline__ void unit_sum_n(const PisShared<SLICES>& sh, int k0, 
         const int j = SORTED ? (int)sh.sidx[k] : k;
         const float4 T = sh.rec[j];
         const float piF = 3.14159265358979f * sh.fabs_[j];
-        const float2 PF = make_float2(piF, piF), Tz = make_float2(T.z, T.z), Tw = make_float2(T.w, T.w);
+        const float2 PF = make_float2(piF, piF), Tz = make_float2(T.z, T.z);
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             const float2 xx = __fmul2_rn(PF, D2[q]);
@@ -141,11 +139,9 @@ __device__ __forceinline__ void unit_sum_n(const PisShared<SLICES>& sh, int k0, 
             } else {
                 A = make_float2(airy_g(xx.x), airy_g(xx.y));
             }
-            const float2 ang = __fmul2_rn(phase_df2(T.x, T.y, x2[q], y2[q]), two_pi);
+            const float2 ang = __fmul2_rn(phase_df2_psi(T.x, T.y, x2[q], y2[q], T.w), two_pi);
             const float2 c = make_float2(__cosf(ang.x), __cosf(ang.y));
-            const float2 sn = make_float2(__sinf(ang.x), __sinf(ang.y));
             acc2[q] = __ffma2_rn(__fmul2_rn(A, Tz), c, acc2[q]);
-            acc2[q] = __ffma2_rn(__fmul2_rn(A, Tw), sn, acc2[q]);
         }
     }
 #pragma unroll
@@ -161,10 +157,7 @@ __device__ __forceinline__ void unit_sum_n(const PisShared<SLICES>& sh, int k0, 
 #pragma unroll
         for (int i = 0; i < NA; ++i) {
             const float A = airy_g(piF * D[i]);
-            float s, c;
-            sincos_turns(phase_df(T.x, T.y, x[i], y[i]), s, c);
-            acc[i] = fmaf(A * T.z, c, acc[i]);
-            acc[i] = fmaf(A * T.w, s, acc[i]);
+            acc[i] = fmaf(A * T.z, __cosf(phase_df_psi(T.x, T.y, x[i], y[i], T.w) * 6.28318530717958648f), acc[i]);
         }
     }
 #endif
@@ -192,8 +185,13 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
         const int len = (int)min((int64_t)kPisChunk, p.n_f - k_begin);
         __syncthreads();  // previous chunk and aperture setup complete
         for (int q = tid; q < len; q += kPisTPB) {
-            const Term t = draw_term<false>(p, nr0 + (uint64_t)(k_begin + q), k_begin + q);
-            sh.rec[q] = make_float4(t.fx, t.fy, t.F * t.a, -(t.F * t.b));
+            const uint64_t n = nr0 + (uint64_t)(k_begin + q);
+            Words w;
+            const Term t = draw_term<false, false>(p, n, k_begin + q, &w);
+            float amp;
+            uint32_t u;
+            coef_polar_from_words(p, n, w, amp, u);
+            sh.rec[q] = make_float4(t.fx, t.fy, t.F * amp, (float)u * 0x1p-24f);
             sh.fabs_[q] = sqrtf(t.fx * t.fx + t.fy * t.fy);
         }
         __syncthreads();
