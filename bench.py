@@ -139,7 +139,7 @@ def _config(cfg, xy, world):
                         "log-radial [1e-3,16] c/m, N_f=%d per-realisation R2 draws, %d realisations/step"
                         % (xy.shape[0], cfg["n_f"], cfg["n_real"]),
             "points": int(xy.shape[0]), "n_f": cfg["n_f"], "realizations_per_step": cfg["n_real"],
-            "form": "fused draw+sincos (per-realisation draws)", "parallelism": "realisations sharded, dp%d" % world,
+            "form": "fused draw + one cosine per term (per-realisation draws)", "parallelism": "realisations sharded, dp%d" % world,
             "l2": "flushed between timed steps (256 MiB write)"}
 
 

@@ -207,14 +207,18 @@ qrs_status qrs_draw(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, co
 /* ---------------------------------------------------------- synthesis ---
  * Eq. 3 at arbitrary points (Sec. 3: "simulate at specific areas of
  * interest"): out[r][m] = sum_k F_k (a_k cos 2 pi phi_mk - b_k sin 2 pi phi_mk),
- * phi_mk = f_k . x_m reduced mod 1 in double-float (error-free products), FP32
+ * phi_mk = f_k . x_m reduced mod 1 exactly (64-bit fixed point when
+ * f_max max|x| <= 128, else double-float error-free products), FP32
  * accumulation.
  *   xy   [n_points][2]  FP32 point coordinates, m
  *   out  [n_real][n_points]  FP32
  * mode:
  *   QRS_SYNTH_FUSED       per-realisation draw (realisation r uses stream points
- *                         (real_offset + r) N_f + k), draw and sincos-accumulate
- *                         fused in one persistent kernel; col_psd must be NULL.
+ *                         (real_offset + r) N_f + k), draw and accumulate fused
+ *                         in one persistent kernel, each term as one cosine in
+ *                         Eq. 3's amplitude-phase form F amp cos 2 pi (phi + psi)
+ *                         (amp, psi: the polar form of (a, b)); col_psd must be
+ *                         NULL.
  *   QRS_SYNTH_GEMM_*      shared draw: all n_real columns use the frequencies of
  *                         realisation real_offset; column r takes its coefficients
  *                         from stream points (real_offset + r) N_f + k and, if
