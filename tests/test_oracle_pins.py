@@ -220,6 +220,38 @@ def test_box_muller_from_words():
     assert np.allclose(rad2, -2 * np.log(U1), rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("coef", ["gauss", "eq3"])
+def test_terms_in_amplitude_phase_form(coef):
+    """The one-cosine form of Eq. 3 that the fused and piston kernels evaluate:
+    with (a, b) of a term, a cos t - b sin t = amp cos(t + 2 pi u 2^-24), where
+    for GAUSS amp = sqrt(-2 ln U1) and u is the 24-bit integer of U2, and for the
+    literal Eq. 3 amp = sqrt2 R_n and u is that of R_u; the half turn in u's top
+    bit then moves into the sign of amp (cos(x + pi) = -cos x).  Checked against
+    the oracle's own coefficients at random angles t: a slip in which uniform is
+    the angle, in its sign, or in the moved half turn fails."""
+    seed = 14
+    n_f, R = 512, 2
+    d = oracle.draw(oracle.params(seed=seed, coef=coef), n_f=n_f, n_real=R, debug=True)
+    w = d["words"].reshape(-1, 4).astype(np.uint64)
+    ab = d["coef"].reshape(-1, 2)
+    rad = np.sqrt(-2 * np.log(((w[:, 2] >> np.uint64(8)) + np.uint64(1)).astype(np.float64) * 2.0 ** -24))
+    if coef == "gauss":
+        amp = rad
+        u = (w[:, 3] >> np.uint64(8)).astype(np.int64)
+    else:
+        U2 = (w[:, 3] >> np.uint64(8)).astype(np.float64) * 2.0 ** -24
+        amp = math.sqrt(2) * rad * np.cos(2 * np.pi * U2)
+        u = np.array([oracle.philox([n, n >> 32, 2, 0], [seed, seed >> 32])[0] >> 8 for n in range(R * n_f)],
+                     np.int64)
+    amp = np.where(u >> 23, -amp, amp)
+    u = u & 0x7FFFFF
+    t = np.random.default_rng(5).uniform(0, 2 * np.pi, size=amp.shape)
+    lhs = ab[:, 0] * np.cos(t) - ab[:, 1] * np.sin(t)
+    rhs = amp * np.cos(t + 2 * np.pi * u * 2.0 ** -24)
+    assert np.allclose(lhs, rhs, rtol=0, atol=1e-12 * np.abs(amp).max())
+    assert np.all(u < 2 ** 23) and np.mean(amp < 0) == pytest.approx(0.5, abs=0.05)
+
+
 # --------------------------------------------------------------- weights, Parseval
 def test_parseval_logpolar_config2():
     """E sum_k w_k = integral of W over the annulus (589.919 rad^2 for r0=0.15, L0=30, [1e-3,16])."""
