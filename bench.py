@@ -53,8 +53,8 @@ L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq-term evals/s"
 UNIT = "term/s"
 # DRAM bytes (read + write) per k_synth_fused launch on the workload above, from the ncu launch
-# list summarised in profiles/k_synth_fused_phase_screen.md (5.53 MB read + 146.55 MB write).
-SYNTH_TRAFFIC_BYTES = 152.08e6
+# list summarised in profiles/k_synth_fused_phase_screen.md (5.28 MB read + 146.66 MB write).
+SYNTH_TRAFFIC_BYTES = 151.94e6
 
 
 def _args():

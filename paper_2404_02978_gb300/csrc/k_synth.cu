@@ -44,7 +44,7 @@ namespace qrs {
 #define QRS_SYNTH_MINB 2     // minimum resident CTAs per SM (register cap)
 #endif
 #ifndef QRS_SYNTH_UNROLL
-#define QRS_SYNTH_UNROLL 4   // term-loop unroll
+#define QRS_SYNTH_UNROLL 8   // term-loop unroll
 #endif
 #ifndef QRS_SYNTH_GROUP
 #define QRS_SYNTH_GROUP 64   // terms per partial sum
