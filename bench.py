@@ -513,7 +513,7 @@ def hankel_piston_sf(B, r0, L0, D, fmin, fmax):
     return float(np.sum(ww * 4 * np.pi * f * W * A * A * (1 - sp.j0(2 * np.pi * f * B))))
 
 
-def measure_learned(qrs, h, torch, dev, n_train=2000, n_test=200, draws=8, n_rho=64, n_theta=32, steps=8000,
+def measure_learned(qrs, h, torch, dev, n_train=8000, n_test=200, draws=8, n_rho=128, n_theta=32, steps=8000,
                     target_draws=1024, fold=4, lr=4e-3, beta=0.7, seeds=(3, 4, 5, 6)):
     """Learned proposal (6 -> 128 -> 128 -> n_rho x n_theta logits): targets from the
     plain method's own draws, training on the GPU, then the matched
