@@ -24,8 +24,9 @@
 //     first multiply-add, exactly
 //   double-float path: {fx, fy (float), F amp, psi = u 2^-24 in [0, 0.5)}
 // The phase path is uniform per launch: fixed point when fbound * xbound
-// <= 128 (its quantisation error, <= fbound xbound 2^-30 turns, is then below
-// the double-float path's), double-float otherwise.  Where the scales allow
+// <= 128 (its quantisation error, about max(fbound xbound 2^-30, 2^-25) turns
+// with the cap on a + b, is then below the double-float path's),
+// double-float otherwise.  Where the scales allow
 // a + b = 55 (fbound * xbound <= 64 with room in the ceilings), the fraction
 // is the low 23 bits of the phase word's high half and needs no shift.
 //
