@@ -143,7 +143,7 @@ def _config(cfg, xy, world):
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
-def cpu_baseline(cfg, p, xy, n_real=2, gpu_rows=None):
+def cpu_baseline(cfg, p, xy, n_real=4, gpu_rows=None):
     """The FP64 CPU reference (as it stands, single thread) on n_real full
     realisations; with the GPU's values of the same realisations (gpu_rows
     [n_real][P]), also their error against it per value, in units of each
@@ -169,10 +169,10 @@ def cpu_baseline(cfg, p, xy, n_real=2, gpu_rows=None):
     return res
 
 
-def cpu_all_cores(cfg, p, xy, first):
-    """The same oracle, one realisation per process on every host core (a
-    spawn pool: the parent already holds a CUDA context), on realisations
-    first .. first + cores - 1."""
+def cpu_all_cores(cfg, p, xy, first, per_core=3):
+    """The same oracle, one realisation per task on every host core (a spawn
+    pool: the parent already holds a CUDA context), per_core tasks per core,
+    on realisations first .. first + per_core cores - 1."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
     import oracle
@@ -182,14 +182,14 @@ def cpu_all_cores(cfg, p, xy, first):
         for f in [ex.submit(oracle.synthesize, p, 8, 1, xy[:64], 0) for _ in range(cores)]:
             f.result(timeout=120)  # workers up, library loaded
         t0 = time.perf_counter()
-        fs = [ex.submit(oracle.synthesize, p, cfg["n_f"], 1, xy, first + i) for i in range(cores)]
+        fs = [ex.submit(oracle.synthesize, p, cfg["n_f"], 1, xy, first + i) for i in range(per_core * cores)]
         for f in fs:
             f.result(timeout=600)
         dt = time.perf_counter() - t0
-    terms = cores * xy.shape[0] * cfg["n_f"]
+    terms = per_core * cores * xy.shape[0] * cfg["n_f"]
     return {"value": terms / dt, "unit": UNIT, "cores": cores,
-            "sample": "%d realisations (one per process), all %d points, N_f=%d (%.3g terms in %.1f s), FP64"
-                      % (cores, xy.shape[0], cfg["n_f"], terms, dt)}
+            "sample": "%d realisations (one per task), all %d points, N_f=%d (%.3g terms in %.1f s), FP64"
+                      % (per_core * cores, xy.shape[0], cfg["n_f"], terms, dt)}
 
 
 def _host():
@@ -737,7 +737,7 @@ def run_ours(a):
         line["other_forms"]["sampling_quality"] = measure_sampling(qrs, h, torch, dev)
         line["other_forms"]["learned_proposal"] = measure_learned(qrs, h, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np, gpu_rows=out[:2].cpu().numpy())
+        line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np, gpu_rows=out[:4].cpu().numpy())
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
