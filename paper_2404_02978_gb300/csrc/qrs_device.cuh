@@ -654,29 +654,12 @@ __device__ __forceinline__ float phase_df_psi(float fx, float fy, float x, float
     return __fadd_rn(r, __fadd_rn(psi, __fadd_rn(e1, e2)));
 }
 
-// phase_df for two positions at once (x.x, y.x) and (x.y, y.y), in paired FP32
-// instructions, without a negation of a pair: the product errors are formed
-// negated (fma(-f, x, p) = -fma(f, x, -p) exactly, rounding being symmetric),
-// the differences a - b as fma(b, -1, a); each element is rounded exactly as
-// in phase_df.
-__device__ __forceinline__ float2 phase_df2(float fx, float fy, float2 x, float2 y)
-{
-    const float2 FX = make_float2(fx, fx), FY = make_float2(fy, fy);
-    const float2 NFX = make_float2(-fx, -fx), NFY = make_float2(-fy, -fy);
-    const float2 M = make_float2(12582912.0f, 12582912.0f), NM = make_float2(-12582912.0f, -12582912.0f);
-    const float2 MINUS1 = make_float2(-1.0f, -1.0f);
-    const float2 p1 = __fmul2_rn(FX, x);
-    const float2 ne1 = __ffma2_rn(NFX, x, p1);  // -e1
-    const float2 p2 = __fmul2_rn(FY, y);
-    const float2 ne2 = __ffma2_rn(NFY, y, p2);  // -e2
-    const float2 n1 = __fadd2_rn(__fadd2_rn(p1, M), NM);
-    const float2 n2 = __fadd2_rn(__fadd2_rn(p2, M), NM);
-    const float2 r = __fadd2_rn(__ffma2_rn(n1, MINUS1, p1), __ffma2_rn(n2, MINUS1, p2));
-    return __ffma2_rn(__fadd2_rn(ne1, ne2), MINUS1, r);  // r + (e1 + e2)
-}
-
-// phase_df2 with a per-term phase offset psi (turns, |psi| <= 0.5) taken into
-// the small parts: r + (psi + (e1 + e2)), |result| <= 1.5 + eps turns.
+// phase_df_psi for two positions at once (x.x, y.x) and (x.y, y.y), in paired
+// FP32 instructions: r + (psi + (e1 + e2)), |result| <= 1.5 + eps turns for
+// |psi| <= 0.5.  No pair is negated: the product errors are formed negated
+// (fma(-f, x, p) = -fma(f, x, -p) exactly, rounding being symmetric) and the
+// differences a - b as fma(b, -1, a); each element is rounded exactly as in
+// phase_df_psi.
 __device__ __forceinline__ float2 phase_df2_psi(float fx, float fy, float2 x, float2 y, float psi)
 {
     const float2 FX = make_float2(fx, fx), FY = make_float2(fy, fy);
