@@ -232,7 +232,57 @@ def run_reference(a):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
-TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate ratio
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate ratio (only if no measured TF32 peak)
+
+
+def measure_tf32_peak(torch, dev, n=8192, burst_reps=10, sustained_s=4.0):
+    """Dense TF32 tensor-core throughput of this GPU, measured the way the
+    BF16 peak is: torch.matmul of two FP32 n x n matrices with TF32 allowed
+    (2 n^3 flop per product), CUDA events; burst = the best of burst_reps
+    products, sustained = products back to back for sustained_s seconds."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        g = torch.Generator(device=dev).manual_seed(0)
+        a = torch.randn(n, n, device=dev, generator=g)
+        b = torch.randn(n, n, device=dev, generator=g)
+        c = torch.empty(n, n, device=dev)
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(burst_reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        per = max(1, int(sustained_s / best))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(per):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        e1.synchronize()
+        flop = 2.0 * n ** 3
+        return {"tf32_tflops": flop / best / 1e12, "tf32_tflops_sustained": flop * per / (e0.elapsed_time(e1) / 1e3) / 1e12,
+                "how": "torch.matmul fp32 %d^3 with TF32 allowed: best of %d (burst), %d back to back (sustained)"
+                       % (n, burst_reps, per)}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
+def _tensor_peak(peaks, mode):
+    """(peak TFLOP/s, basis) for a tensor-core form: the measured BF16 burst for
+    BF16X3, the TF32 burst measured in this run for 3XTF32 and TF32 (else the BF16 burst
+    times the nominal TF32/BF16 ratio, said so)."""
+    bf16 = float(peaks.get("bf16_tflops", 1889.0))
+    if mode == "gemm_bf16x3":
+        return bf16, "measured bf16 burst (MEASURED_PEAKS.json)"
+    if peaks.get("tf32_tflops"):
+        return float(peaks["tf32_tflops"]), "tf32 burst measured in this run (%s)" % peaks.get("tf32_how", "")
+    return bf16 * TF32_OVER_BF16, "measured bf16 burst %.0f x nominal tf32/bf16 %.3f" % (bf16, TF32_OVER_BF16)
 
 
 def measure_gemm(qrs, h, torch, dev, mode, peaks):
@@ -261,19 +311,17 @@ def measure_gemm(qrs, h, torch, dev, mode, peaks):
     qrs.qrs_sync(h, stream)
     ms = [s.elapsed_time(e) for s, e in ev]
     t = sum(ms) / len(ms) / 1e3
-    T = 16 if mode == "gemm_3xtf32" else 32
+    T = 32 if mode == "gemm_bf16x3" else 16
     nf_pad = (nf + T - 1) // T * T
     R_pad = (R + 127) // 128 * 128
-    flops = 3 * 2 * P * (2 * nf_pad) * R_pad  # three split products per term pair
-    bf16 = float(peaks.get("bf16_tflops", 1889.0))
-    peak = bf16 * (TF32_OVER_BF16 if mode == "gemm_3xtf32" else 1.0)
+    splits = 1 if mode == "gemm_tf32" else 3  # products per term pair: one, or three split ones
+    flops = splits * 2 * P * (2 * nf_pad) * R_pad
+    peak, basis = _tensor_peak(peaks, mode)
     return {"workload": "16 m pupil 512x512 (%d points), N_f=%d shared per batch of %d, per-column r0/L0, %d batches"
                         % (P, nf, R, cfg["batches"]),
             "ms_per_batch": t * 1e3, "value": P * nf * R / t, "unit": UNIT,
             "roofline": {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": flops / t / 1e12 / peak,
-                         "peak_basis": ("measured bf16 burst %.0f x nominal tf32/bf16 %.3f" % (bf16, TF32_OVER_BF16))
-                         if mode == "gemm_3xtf32" else "measured bf16 burst",
+                         "frac": flops / t / 1e12 / peak, "peak_basis": basis,
                          "flops_per_batch": flops, "note": "whole call: point bound, shared draw, coefficients, GEMM"}}
 
 
@@ -316,16 +364,13 @@ def measure_grid(qrs, h, torch, dev, peaks, mode="gemm_3xtf32", reps=5):
     n_pad = (n + 127) // 128 * 128
     m_pad = (n + 255) // 256 * 256
     flops = 3 * 2 * n_pad * m_pad * (2 * nf_pad) * R  # three split products, executed tiles
-    bf16 = float(peaks.get("bf16_tflops", 1889.0))
-    peak = bf16 * (TF32_OVER_BF16 if mode == "gemm_3xtf32" else 1.0)
+    peak, basis = _tensor_peak(peaks, mode)
     return {"workload": "8 m pupil 256x256 grid (%d interior points), N_f=%d per realisation, %d realisations, %s"
                         % (P, nf, R, mode),
             "ms_per_call": t * 1e3, "value": P * nf * R / t, "unit": UNIT,
             "grid_nodes_per_s": n * n * nf * R / t,
             "roofline": {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": flops / t / 1e12 / peak,
-                         "peak_basis": ("measured bf16 burst %.0f x nominal tf32/bf16 %.3f" % (bf16, TF32_OVER_BF16))
-                         if mode == "gemm_3xtf32" else "measured bf16 burst",
+                         "frac": flops / t / 1e12 / peak, "peak_basis": basis,
                          "flops_per_call": flops,
                          "note": "whole call: bound prepass, draw records, grid kernel; L2 flushed between calls"}}
 
@@ -493,6 +538,119 @@ def measure_batched(qrs, h, torch, dev):
                          "peak_basis": "min(1 MUFU per unit: %.0f, %d FP32-pipe ops per unit at 128 per SM-clock: "
                                        "%.0f) Gunit/s at %.0f MHz" % (mufu / 1e9, PISTON_FMA_OPS, fma / 1e9,
                                                                        SM_MAX_MHZ)}}
+
+
+def measure_piston_plain(qrs, h, torch, dev, reps=5):
+    """The plain differential-piston case (Sec. 4.4 with the Eq. 7 filter) in
+    full: 17 apertures of D = 1 m (the origin and 16 baselines log-spaced
+    1-100 m along x), von Karman r0 = 0.10 m, L0 = 25 m, log-radial
+    [1e-3, 10] c/m, N_f = 1024, 10^4 realisations, seed 0 -- one
+    qrs_diff_piston launch for all realisations, then the FP64 sums of
+    qrs_structure_fn; the mean of Delta^2 per baseline against the expected
+    structure function (Hankel integral over the annulus) in units of its
+    Monte-Carlo standard error."""
+    from paper_2404_02978_gb300 import workloads as wl
+    cfg = wl.PISTON_PLAIN
+    B, ap_xy, ap_D, ap_d, pairs = wl.piston_plain_apertures()
+    p = wl.method_params(cfg)
+    R, nf, n_ap, n_pairs = cfg["n_real"], cfg["n_f"], ap_xy.shape[0], pairs.shape[0]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    dxy, dD, dd, dpairs = t(ap_xy), t(ap_D), t(ap_d), t(pairs)
+    delta = torch.empty(R, n_pairs, device=dev)
+    lags = torch.zeros(1, dtype=torch.int32, device=dev)
+    acc = torch.zeros(n_pairs, 1, 3, dtype=torch.float64, device=dev)
+    job = qrs.piston_job(p, nf, R, dxy, dD, dd, dpairs, None, delta)
+    stream = torch.cuda.current_stream()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(reps)]
+
+    def run(e=None):
+        acc.zero_()
+        if e:
+            e[0].record(stream)
+        qrs.qrs_diff_piston(h, [job], stream=stream)
+        if e:
+            e[1].record(stream)
+        qrs.qrs_structure_fn(h, delta.view(R, n_pairs, 1), lags, acc=acc, stream=stream)
+        if e:
+            e[2].record(stream)
+
+    for _ in range(3):
+        run()
+    qrs.qrs_sync(h, stream)
+    for i in range(reps):
+        run(ev[i])
+    qrs.qrs_sync(h, stream)
+    t_pis = min(e[0].elapsed_time(e[1]) for e in ev) / 1e3
+    t_all = min(e[0].elapsed_time(e[2]) for e in ev) / 1e3
+    a = acc.cpu().numpy()[:, 0, :]
+    mean = a[:, 0] / a[:, 2]
+    sem = np.sqrt((a[:, 1] / a[:, 2] - mean ** 2) / a[:, 2])
+    ref = np.array([hankel_piston_sf(float(np.float32(b)), cfg["r0"], cfg["L0"], 1.0, cfg["fmin"], cfg["fmax"])
+                    for b in B])
+    z = (mean - ref) / sem
+    units = R * nf * n_ap
+    fma = N_SM * FMA_PER_SM_CLK / PISTON_FMA_OPS * SM_MAX_MHZ * 1e6
+    return {"workload": "plain differential piston: 17 apertures D=1 m (origin + 16 baselines 1-100 m), von Karman "
+                        "r0=0.10 m L0=25 m, log-radial [1e-3,10] c/m, N_f=%d, %d realisations, seed 0" % (nf, R),
+            "ms": {"diff_piston": t_pis * 1e3, "with_structure_fn": t_all * 1e3},
+            "value": units / t_pis, "unit": "aperture-term evals/s", "realizations_per_s": R / t_all,
+            "launch": "one k_piston_single launch (all realisations) + one k_structure_fn launch",
+            "baselines_m": [float(b) for b in B], "sf_rad2": mean.tolist(), "sf_expected_rad2": ref.tolist(),
+            "z": z.tolist(), "z_max_abs": float(np.abs(z).max()),
+            "roofline": {"bound": "alu", "achieved": units / t_pis / 1e9, "peak": fma / 1e9, "unit": "Gunit/s",
+                         "frac": units / t_pis / fma, "kernel": "k_piston_single",
+                         "peak_basis": "%d FP32-pipe ops per aperture-term unit at 128 per SM-clock, %.0f MHz"
+                                       % (PISTON_FMA_OPS, SM_MAX_MHZ)},
+            "note": "z = (mean Delta^2 - expected) / Monte-Carlo standard error, per baseline"}, delta
+
+
+def cpu_piston_plain(gpu_delta=None, per_core=1):
+    """The FP64 CPU reference on the plain differential-piston case in full
+    (17 apertures, N_f = 1024, 10^4 realisations): single thread, then split
+    by realisations over every host core (a spawn pool: the parent holds a
+    CUDA context); with the GPU's pair differences, their error against it per
+    value in units of the pair's standard deviation."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    import oracle
+    from paper_2404_02978_gb300 import workloads as wl
+    cfg = wl.PISTON_PLAIN
+    B, ap_xy, ap_D, ap_d, pairs = wl.piston_plain_apertures()
+    p = wl.method_params(cfg)
+    R, nf = cfg["n_real"], cfg["n_f"]
+    units = R * nf * ap_xy.shape[0]
+    t0 = time.perf_counter()
+    _, ref = oracle.diff_piston(p, nf, R, ap_xy, ap_D, ap_d, pairs)
+    dt1 = time.perf_counter() - t0
+    res = {"value": units / dt1, "unit": "aperture-term evals/s", "cores": 1, "kind": "oracle",
+           "sample": "the whole case (%d realisations, %.3g units) in %.1f s, single thread FP64" % (R, units, dt1)}
+    try:
+        cores = os.cpu_count() or 1
+        n_task = per_core * cores
+        bounds = [R * i // n_task for i in range(n_task + 1)]
+        with ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
+            for f in [ex.submit(oracle.diff_piston, p, 8, 1, ap_xy, ap_D, ap_d, pairs) for _ in range(cores)]:
+                f.result(timeout=120)
+            t0 = time.perf_counter()
+            fs = [ex.submit(oracle.diff_piston, p, nf, bounds[i + 1] - bounds[i], ap_xy, ap_D, ap_d, pairs, bounds[i])
+                  for i in range(n_task)]
+            parts = [f.result(timeout=600)[1] for f in fs]
+            dt = time.perf_counter() - t0
+        res["all_cores"] = {"value": units / dt, "unit": "aperture-term evals/s", "cores": cores,
+                            "sample": "the whole case split into %d realisation ranges, %.1f s" % (n_task, dt),
+                            "equals_single_thread": bool(np.array_equal(np.concatenate(parts), ref))}
+    except Exception as e:  # the single-thread figure above stands on its own
+        res["all_cores"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    if gpu_delta is not None:
+        d = oracle.draw(p, n_f=nf, n_real=R)
+        f = np.hypot(d["f"][..., 0].astype(np.float64), d["f"][..., 1].astype(np.float64))
+        from oracle import analytic as an
+        A = an.airy(f.ravel(), 1.0).reshape(f.shape)
+        sig = np.sqrt(2.0 * np.sum((d["F"] * A) ** 2, axis=1))  # two equal apertures
+        err = np.abs(np.asarray(gpu_delta, np.float64) - ref) / sig[:, None]
+        res["gpu_error_vs_fp64"] = {"max_sigma": float(err.max()), "rms_sigma": float(np.sqrt(np.mean(err ** 2))),
+                                    "values": int(err.size), "tolerance_sigma": 1e-5}
+    return res
 
 
 def hankel_piston_sf(B, r0, L0, D, fmin, fmax):
@@ -727,9 +885,19 @@ def run_ours(a):
         line["clocks"] = clk
         # the same fraction against the bound at the SM clock sampled during the timed steps
         line["roofline"]["frac_at_sampled_clock"] = achieved / (peak_terms * clk["sm_mhz"] / sm_max)
+    plain_delta = None
     if world == 1 and not a.headline_only:
         peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
-        line["other_forms"] = {m: measure_gemm(qrs, h, torch, dev, m, peaks) for m in ("gemm_3xtf32", "gemm_bf16x3")}
+        try:
+            tf32 = measure_tf32_peak(torch, dev)
+            peaks = dict(peaks, tf32_tflops=tf32["tf32_tflops"], tf32_how=tf32["how"])
+            line["measured_tf32_peak"] = tf32
+        except Exception as e:  # the forms then fall back to the nominal ratio, and say so
+            line["measured_tf32_peak"] = {"error": "%s: %s" % (type(e).__name__, e)}
+        line["other_forms"] = {}
+        line["other_forms"]["plain_piston"], plain_delta = measure_piston_plain(qrs, h, torch, dev)
+        line["other_forms"].update({m: measure_gemm(qrs, h, torch, dev, m, peaks)
+                                    for m in ("gemm_3xtf32", "gemm_bf16x3", "gemm_tf32")})
         line["other_forms"]["grid_3xtf32"] = measure_grid(qrs, h, torch, dev, peaks)
         line["other_forms"]["grid_bf16x3"] = measure_grid(qrs, h, torch, dev, peaks, mode="gemm_bf16x3")
         line["other_forms"]["batched_pistons"] = measure_batched(qrs, h, torch, dev)
@@ -738,6 +906,8 @@ def run_ours(a):
         line["other_forms"]["learned_proposal"] = measure_learned(qrs, h, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np, gpu_rows=out[:4].cpu().numpy())
+        if plain_delta is not None:
+            line["other_forms"]["plain_piston"]["cpu_baseline"] = cpu_piston_plain(plain_delta.cpu().numpy())
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()

@@ -36,9 +36,13 @@
  *     stream, or use one handle per stream).
  *   - Environment: QRS_AUTOTUNE_CACHE (a file of the piston kernel-shape
  *     choices, read and written by the autotuner), QRS_FAULT (read at
- *     qrs_create; "alloc", "launch": host-side fault injection -- workspace
- *     allocations fail with QRS_ERR_NOMEM, compute calls fail with
- *     QRS_ERR_CUDA before launching anything).
+ *     qrs_create; "alloc", "launch", "timeout", comma-separated: host-side
+ *     fault injection -- workspace allocations fail with QRS_ERR_NOMEM,
+ *     compute calls fail with QRS_ERR_CUDA before launching anything; the
+ *     next GEMM-form launch of the handle first waits on a barrier that no
+ *     thread arrives at, with a limit of about 1 ms, and unwinds through its
+ *     time-out path: QRS_ERR_TIMEOUT at the next qrs_sync, later calls run
+ *     normally).
  */
 #ifndef QRS_H
 #define QRS_H
@@ -226,12 +230,16 @@ qrs_status qrs_draw(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, co
  *                         (device FP64 [n_real][2]) in the weight.  The sum is the
  *                         product of the [n_points x 2 n_f] cos/sin basis and the
  *                         [2 n_f x n_real] coefficient matrix on the tensor cores:
- *                         3XTF32 (split TF32, ~FP32 accuracy) or BF16X3 (split
- *                         BF16, ~2^-16 relative).
+ *                         3XTF32 (split TF32, ~FP32 accuracy: within 1e-5 of the
+ *                         column's field standard deviation per value), BF16X3
+ *                         (split BF16, ~2^-17 per product: within 5e-5), or
+ *                         TF32 (single pass, each operand rounded once to TF32,
+ *                         ~2^-11 per product: within 2e-3, about 3e-4 rms).
  * Column 0 of a GEMM-mode call equals realisation real_offset of a FUSED call. */
 #define QRS_SYNTH_FUSED 0
 #define QRS_SYNTH_GEMM_3XTF32 1
 #define QRS_SYNTH_GEMM_BF16X3 2
+#define QRS_SYNTH_GEMM_TF32 3
 
 qrs_status qrs_synthesize_points(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom,
                                  const qrs_sampler* smp, int64_t n_f, int64_t n_real,
@@ -375,7 +383,10 @@ qrs_status qrs_structure_fn(qrs_handle* h, const float* delta, int64_t n_real, i
  *   Device: the calling thread's current device (at most 64 devices).  The
  *   first call on each device resolves the scratch's device address
  *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before any stream capture.
+ *   before any stream capture.  A call that finds the device's context
+ *   replaced since then (after cudaDeviceReset, which reloads the library's
+ *   device code) resolves the address again, so the first call after a reset
+ *   must also come before any stream capture.
  *   Concurrency: every call on a device shares the one scratch array, so calls
  *   that overlap on the GPU (e.g. on two streams at once) race; serialise them.
  *   Errors: status codes only (there is no handle to hold a message).

@@ -89,6 +89,58 @@ qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params
 qrs_status qrs_mlp_adam(qrs_handle* h, int32_t n_cells, float* params, float* m, float* v, const float* grad,
                         float lr, int64_t step, void* stream);
 
+/* ------------------------------------------------------------ training ---
+ * Training state of the network: the parameters and Adam's two moment
+ * vectors (device FP32 [qrs_mlp_param_count(n_cells)] each, caller-owned)
+ * and the number of Adam steps taken (host).  A fresh run: params from
+ * qrs_mlp_init, m = v = 0, step = 0. */
+typedef struct qrs_mlp_state {
+    int32_t n_cells;
+    int32_t reserved;
+    int64_t step;
+    float* params;
+    float* m;
+    float* v;
+} qrs_mlp_state;
+
+#define QRS_LR_CONSTANT 0
+#define QRS_LR_COSINE 1
+
+/* Full-batch Adam on the mean cross entropy of qrs_mlp_loss_grad: `steps`
+ * steps t = state->step + 1 .. state->step + steps, each the loss and
+ * gradient at the current parameters followed by qrs_mlp_adam's update with
+ * bias correction t; state->params, m, v are updated in place and
+ * state->step advances by `steps` (on success).  The learning rate of step t
+ * is formed in FP64 and rounded once to FP32:
+ *   QRS_LR_CONSTANT  lr
+ *   QRS_LR_COSINE    lr (1 + cos(pi (t - 1) / total_steps)) / 2, the cosine
+ *                    schedule of a run of total_steps steps (total_steps >=
+ *                    state->step + steps), so a run split into several calls
+ *                    follows the same schedule as one call.
+ * The result equals, bit for bit, the same steps taken one call at a time
+ * through qrs_mlp_loss_grad and qrs_mlp_adam, and a run resumed from a
+ * checkpoint (qrs_mlp_save / qrs_mlp_load) equals an uninterrupted one.
+ *   geom [n][5] device FP64, targets [n][n_cells] device FP32 (rows sum to 1),
+ *   loss_trace: device FP32 [steps] receiving each step's loss (before its
+ *   update), or NULL.
+ * Workspace: the handle's (the backward pass's buffers and the gradient).
+ * Errors: QRS_ERR_ARG for invalid sizes, pointers, lr <= 0, an unknown
+ * schedule, total_steps too small; nothing is launched then. */
+qrs_status qrs_proposal_train(qrs_handle* h, qrs_mlp_state* state, const double* geom, const float* targets, int64_t n,
+                              int64_t steps, double lr, int32_t schedule, int64_t total_steps, float* loss_trace,
+                              void* stream);
+
+/* Checkpoint of a training state: qrs_mlp_save writes n_cells, step, params,
+ * m and v to the file `path` (host path; the file holds the 8 bytes
+ * "QRSMLP01", int32 n_cells, int32 0, int64 step, int64 parameter count, then
+ * the three FP32 vectors), after synchronising `stream`.  qrs_mlp_load reads
+ * one into a state whose n_cells and device vectors the caller has set up,
+ * and sets state->step; a file of another size or network returns
+ * QRS_ERR_ARG with the state untouched.  Both return when the copies are
+ * complete. */
+qrs_status qrs_mlp_save(qrs_handle* h, const qrs_mlp_state* state, const char* path, void* stream);
+qrs_status qrs_mlp_load(qrs_handle* h, qrs_mlp_state* state, const char* path, void* stream);
+
 /* Two-level sampling CDF from one row of logits (device [n_rho n_theta]):
  * p = (1 - eps) softmax(beta z) + eps / C over the cells; the marginal over
  * radial bands and, per band, the conditional over its angular cells, each

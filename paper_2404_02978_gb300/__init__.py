@@ -15,11 +15,9 @@ grid of Eq. 4, uniform, importance cells) and coefficient form (Eq. 3).
 from __future__ import annotations
 
 import ctypes as C
-import math
 import os
 import threading
 
-import numpy as np
 import torch
 
 __all__ = ["params", "Handle", "qrs_create", "qrs_draw", "qrs_synthesize_points", "qrs_synthesize_grid", "qrs_diff_piston",
@@ -32,7 +30,7 @@ PSD = {"von_karman": 0, "kolmogorov": 1}
 DOMAIN = {"square": 0, "disc": 1, "logpolar": 2}
 SAMPLER = {"r2": 0, "jitter": 1, "uniform": 2, "importance": 3}
 COEF = {"gauss": 0, "eq3": 1}
-MODE = {"fused": 0, "gemm_3xtf32": 1, "gemm_bf16x3": 2}
+MODE = {"fused": 0, "gemm_3xtf32": 1, "gemm_bf16x3": 2, "gemm_tf32": 3}
 PISTON_PERSISTENT, PISTON_GRAPH = 1, 2
 STATUS = {0: "QRS_OK", -1: "QRS_ERR_ARG", -2: "QRS_ERR_CUDA", -3: "QRS_ERR_TIMEOUT", -4: "QRS_ERR_UNSUPPORTED",
           -5: "QRS_ERR_NOMEM", -6: "QRS_ERR_DEVICE_CHECK"}
@@ -239,7 +237,8 @@ def qrs_synthesize_grid(h: Handle, p, n_f, n_real, x, y, index=None, n_points=No
     """Eq. 3 on the tensor-product grid {x} x {y} (float32 device vectors) by the
     separable tensor-core form.  index None: returns out [n_real, ny, nx];
     else index int32 [ny, nx] (output point per node, -1 = none) and out
-    [n_real, n_points] (n_points defaults to index.max() + 1)."""
+    [n_real, n_points]; n_points is then required (the binding runs no
+    kernel of its own to find it)."""
     _check_dev(x, torch.float32, "x")
     _check_dev(y, torch.float32, "y")
     nx, ny = x.numel(), y.numel()
@@ -249,7 +248,7 @@ def qrs_synthesize_grid(h: Handle, p, n_f, n_real, x, y, index=None, n_points=No
         if index.numel() != nx * ny:
             raise ValueError("index must hold ny * nx entries")
         if n_points is None:
-            n_points = int(index.max().item()) + 1 if index.numel() else 0
+            raise ValueError("n_points is required with an index (the number of output points)")
         ip = index.data_ptr()
         shape = (n_real, n_points)
     else:
@@ -488,55 +487,95 @@ def qrs_proposal_cdf(h: Handle, n_rho, n_theta, logits_row, eps=0.1, beta=1.0, o
     return out
 
 
+class QrsMlpState(C.Structure):
+    _fields_ = [("n_cells", C.c_int32), ("reserved", C.c_int32), ("step", C.c_int64), ("params", C.c_void_p),
+                ("m", C.c_void_p), ("v", C.c_void_p)]
+
+
+LR_SCHEDULE = {"constant": 0, "cosine": 1}
+
+
 class ProposalState:
     """Resumable training state of the learned proposal: parameters, Adam
-    moments and the step count; save() writes one binary .npz file."""
+    moments (device tensors) and the step count; save() / load() go through
+    libqrs's checkpoint file (qrs_mlp_save / qrs_mlp_load)."""
 
     def __init__(self, n_cells, params, m, v, step):
         self.n_cells, self.params, self.m, self.v, self.step = int(n_cells), params, m, v, int(step)
 
-    def save(self, path):
-        np.savez(path, n_cells=self.n_cells, step=self.step, params=self.params.detach().cpu().numpy(),
-                 m=self.m.detach().cpu().numpy(), v=self.v.detach().cpu().numpy())
+    def _c(self):
+        for t, name in ((self.params, "params"), (self.m, "m"), (self.v, "v")):
+            _check_dev(t, torch.float32, name)
+        return QrsMlpState(self.n_cells, 0, self.step, self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr())
+
+    def save(self, path, h: "Handle", stream=None):
+        f = _prop_fn("qrs_mlp_save", [C.c_void_p, C.POINTER(QrsMlpState), C.c_char_p, C.c_void_p])
+        st = self._c()
+        h._check(f(h.h, C.byref(st), os.fsencode(str(path)), _stream(stream)))
 
     @staticmethod
-    def load(path, device="cuda"):
-        z = np.load(path)
-        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
-        return ProposalState(int(z["n_cells"]), t(z["params"]), t(z["m"]), t(z["v"]), int(z["step"]))
+    def load(path, h: "Handle", n_cells, stream=None):
+        dev = torch.device("cuda", h.device)
+        n = qrs_mlp_param_count(n_cells)
+        s = ProposalState(n_cells, torch.empty(n, device=dev), torch.empty(n, device=dev), torch.empty(n, device=dev), 0)
+        f = _prop_fn("qrs_mlp_load", [C.c_void_p, C.POINTER(QrsMlpState), C.c_char_p, C.c_void_p])
+        st = s._c()
+        h._check(f(h.h, C.byref(st), os.fsencode(str(path)), _stream(stream)))
+        s.step = int(st.step)
+        return s
+
+
+def qrs_proposal_train(h: Handle, state: ProposalState, geom, targets, steps, lr, schedule="constant",
+                       total_steps=None, loss_trace=None, stream=None):
+    """Full-batch Adam in libqrs (one call, include/qrs_proposal.h): advances
+    `state` by `steps` steps; loss_trace (device float32 [steps]) receives
+    each step's loss when given."""
+    _check_dev(geom, torch.float64, "geom")
+    _check_dev(targets, torch.float32, "targets")
+    lt = None
+    if loss_trace is not None:
+        _check_dev(loss_trace, torch.float32, "loss_trace")
+        if loss_trace.numel() < steps:
+            raise ValueError("loss_trace must hold `steps` values")
+        lt = loss_trace.data_ptr()
+    total = int(total_steps) if total_steps is not None else state.step + int(steps)
+    f = _prop_fn("qrs_proposal_train", [C.c_void_p, C.POINTER(QrsMlpState), C.c_void_p, C.c_void_p, C.c_int64,
+                                        C.c_int64, C.c_double, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p])
+    st = state._c()
+    h._check(f(h.h, C.byref(st), geom.data_ptr(), targets.data_ptr(), int(geom.shape[0]), int(steps), float(lr),
+               LR_SCHEDULE[schedule], total, lt, _stream(stream)))
+    state.step = int(st.step)
+    return state
 
 
 def train_proposal(h: Handle, n_cells, geom, targets, steps=2000, lr=2e-3, seed=0, params=None, stream=None,
                    log_every=0, state=None, return_state=False, schedule="constant", total_steps=None):
-    """Adam on the mean cross entropy, full batch; every step is two libqrs calls
-    (loss and gradient, Adam update).  schedule "cosine": step t of a run of
-    total_steps (default: this call's last step) uses lr (1 + cos(pi (t - 1) /
-    total_steps)) / 2.  Returns (params, list of (step, loss)), and the
-    ProposalState after the last step when return_state is set; a `state`
-    continues a checkpointed run (same result as an uninterrupted one when
-    total_steps names the whole run)."""
-    if schedule not in ("constant", "cosine"):
+    """Adam on the mean cross entropy, full batch, as one libqrs call
+    (qrs_proposal_train).  schedule "cosine": step t of a run of total_steps
+    (default: this call's last step) uses lr (1 + cos(pi (t - 1) /
+    total_steps)) / 2.  Returns (params, list of (step, loss) every log_every
+    steps), and the ProposalState after the last step when return_state is
+    set; a `state` continues a checkpointed run (same result as an
+    uninterrupted one when total_steps names the whole run)."""
+    if schedule not in LR_SCHEDULE:
         raise ValueError("schedule must be 'constant' or 'cosine'")
     if state is not None:
         if state.n_cells != n_cells:
             raise ValueError("checkpoint has %d cells, not %d" % (state.n_cells, n_cells))
-        params, m, v, step0 = state.params, state.m, state.v, state.step
     else:
         if params is None:
             params = qrs_mlp_init(h, n_cells, seed, stream=stream)
-        m = torch.zeros_like(params)
-        v = torch.zeros_like(params)
-        step0 = 0
-    grad = torch.empty_like(params)
-    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+        state = ProposalState(n_cells, params, torch.zeros_like(params), torch.zeros_like(params), 0)
+    step0 = state.step
+    trace = torch.empty(max(int(steps), 1), dtype=torch.float32, device=state.params.device) if log_every else None
+    qrs_proposal_train(h, state, geom, targets, steps, lr, schedule=schedule,
+                       total_steps=total_steps if total_steps is not None else step0 + steps, loss_trace=trace,
+                       stream=stream)
     hist = []
-    total = total_steps if total_steps is not None else step0 + steps
-    for step in range(step0 + 1, step0 + steps + 1):
-        lr_t = lr if schedule == "constant" else lr * 0.5 * (1.0 + math.cos(math.pi * (step - 1) / total))
-        qrs_mlp_loss_grad(h, n_cells, params, geom, targets, grad=grad, loss=loss, stream=stream)
-        qrs_mlp_adam(h, n_cells, params, m, v, grad, lr_t, step, stream=stream)
-        if log_every and (step % log_every == 0 or step == 1):
-            hist.append((step, float(loss.item())))
+    if log_every and steps > 0:
+        tr = trace.cpu().numpy()
+        hist = [(step0 + i + 1, float(tr[i])) for i in range(int(steps))
+                if (step0 + i + 1) % log_every == 0 or step0 + i + 1 == 1]
     if return_state:
-        return params, hist, ProposalState(n_cells, params, m, v, step0 + steps)
-    return params, hist
+        return state.params, hist, state
+    return state.params, hist

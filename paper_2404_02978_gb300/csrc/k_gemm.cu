@@ -11,6 +11,9 @@
 //   3XTF32: x = hi + lo with hi, lo TF32 (11-bit significands); the product is
 //           A_hi B_hi + A_hi B_lo + A_lo B_hi (kind::tf32), ~FP32 accuracy.
 //   BF16X3: the same with BF16 halves (kind::f16, BF16 in, FP32 accumulate).
+//   TF32:   single pass, each operand rounded once to TF32, A B (kind::tf32):
+//           about 2^-11 relative per product, several 1e-4 of the field's
+//           standard deviation per value.
 //
 // Launches: k_point_bound (phase path), k_gemm_freq (the shared draw, FP64
 // map, into the basis representation), k_gemm_coef (B, hi and lo, into the
@@ -100,6 +103,7 @@ struct GemmArgs {
     const float* d_xbound;
     float fbound;
     int* err;
+    long long inject_wait;  // > 0: the MMA thread first waits this many cycles on a barrier nothing arrives at
 };
 
 // ------------------------------------------------------------- prep kernels
@@ -128,7 +132,9 @@ __global__ void k_gemm_freq(DrawParams p, int64_t nf_pad, const float* __restric
 template <int PREC>
 __device__ __forceinline__ void split_store(void* hi_base, void* lo_base, int64_t idx, float x)
 {
-    if (GemmCfg<PREC>::kTF32) {
+    if (!GemmCfg<PREC>::kSplit) {  // single pass: the TF32 rounding only
+        static_cast<uint32_t*>(hi_base)[idx] = tf32_rna_bits(x);
+    } else if (GemmCfg<PREC>::kTF32) {
         uint32_t h, l;
         asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
         const float r = x - __uint_as_float(h);
@@ -143,7 +149,8 @@ __device__ __forceinline__ void split_store(void* hi_base, void* lo_base, int64_
     }
 }
 
-// B[r][k'] (hi half then lo half, R_pad rows each, 2 nf_pad columns):
+// B[r][k'] (hi half then lo half, R_pad rows each, 2 nf_pad columns; the hi
+// half only for single-pass TF32):
 // chunk c holds terms [c T, (c+1) T); column c 2T + j = cos part (F a) of
 // term c T + j, column c 2T + T + j = sin part (-F b).  Column r draws its
 // coefficients from stream point (real_offset + r) N_f + k; its weight uses
@@ -206,6 +213,7 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
     uint64_t* freeF = fullF + kGFreqSlots;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeF + kGFreqSlots);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    uint64_t* never = reinterpret_cast<uint64_t*>(tmem_slot + 2);  // fault injection: no thread arrives here
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tile = blockIdx.x, rblk = blockIdx.y;
@@ -224,6 +232,7 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
             sm100::mbar_init(&fullF[s], 1);
             sm100::mbar_init(&freeF[s], kGProducers);
         }
+        sm100::mbar_init(never, 1);
         *abort_flag = 0;
         sm100::fence_barrier_init();
     }
@@ -259,10 +268,10 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
                     if (!*abort_flag) timeout();
                     break;
                 }
-                sm100::mbar_arrive_expect_tx(&fullB[s], 2u * kGTileB);
+                sm100::mbar_arrive_expect_tx(&fullB[s], (Cfg::kSplit ? 2u : 1u) * kGTileB);
                 const int32_t x = (int32_t)(i * Cfg::kElemsPerRow);
                 sm100::tma_load_2d(stageB_hi(s), &tmapB, &fullB[s], x, (int32_t)(rblk * kGN));
-                sm100::tma_load_2d(stageB_lo(s), &tmapB, &fullB[s], x, (int32_t)(g.R_pad + rblk * kGN));
+                if (Cfg::kSplit) sm100::tma_load_2d(stageB_lo(s), &tmapB, &fullB[s], x, (int32_t)(g.R_pad + rblk * kGN));
                 issued = i + 1;
             }
             if (*abort_flag) {  // let copies in flight land before the CTA exits
@@ -274,6 +283,11 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
         // ---------------------------------------------------- MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = sm100::idesc_f32acc(Cfg::kFormat, kGM, kGN);
+            // Host-side fault injection (QRS_FAULT=timeout): a bounded wait that
+            // runs out before any MMA is issued; the CTA then unwinds through its
+            // time-out path (abort flag, error word, drained copies, TMEM freed).
+            if (g.inject_wait > 0 && !sm100::mbar_wait(never, 0u, abort_flag, g.inject_wait) && !*abort_flag)
+                timeout();
             int64_t i = 0;
             for (int64_t j = 0; j < n_seg && !*abort_flag; ++j) {
                 if (j >= 1 && !sm100::mbar_wait(seg_free, (uint32_t)((j - 1) & 1), abort_flag, kGWaitCycles)) {
@@ -300,8 +314,10 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
                         const uint64_t dBh = sm100::desc_k_sw128(bhi + off), dBl = sm100::desc_k_sw128(blo + off);
                         sm100::mma<Cfg::kTF32>(tmem_seg, dAh, dBh, idesc, first ? 0u : 1u);
                         first = false;
-                        sm100::mma<Cfg::kTF32>(tmem_seg, dAh, dBl, idesc, 1u);
-                        sm100::mma<Cfg::kTF32>(tmem_seg, dAl, dBh, idesc, 1u);
+                        if (Cfg::kSplit) {
+                            sm100::mma<Cfg::kTF32>(tmem_seg, dAh, dBl, idesc, 1u);
+                            sm100::mma<Cfg::kTF32>(tmem_seg, dAl, dBh, idesc, 1u);
+                        }
                     }
                     sm100::mma_commit(&empty[s]);  // frees stage s once these MMAs complete
                 }
@@ -427,10 +443,10 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
                 uint4 hi, lo;
                 pack16<PREC>(cv, hi, lo);
                 *reinterpret_cast<uint4*>(Ahi + oc) = hi;
-                *reinterpret_cast<uint4*>(Alo + oc) = lo;
+                if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + oc) = lo;
                 pack16<PREC>(sv, hi, lo);
                 *reinterpret_cast<uint4*>(Ahi + os) = hi;
-                *reinterpret_cast<uint4*>(Alo + os) = lo;
+                if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + os) = lo;
             }
             sm100::fence_proxy_async_smem();  // each thread: its row writes -> async proxy
             __syncwarp();
@@ -468,12 +484,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 
 size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real)
 {
-    const int T = mode == QRS_SYNTH_GEMM_3XTF32 ? GemmCfg<QRS_SYNTH_GEMM_3XTF32>::kTermsPerChunk
-                                                : GemmCfg<QRS_SYNTH_GEMM_BF16X3>::kTermsPerChunk;
-    const int eb = mode == QRS_SYNTH_GEMM_3XTF32 ? 4 : 2;
+    const bool bf16 = mode == QRS_SYNTH_GEMM_BF16X3;
+    const int T = bf16 ? GemmCfg<QRS_SYNTH_GEMM_BF16X3>::kTermsPerChunk : GemmCfg<QRS_SYNTH_GEMM_3XTF32>::kTermsPerChunk;
+    const int eb = bf16 ? 2 : 4;
+    const int halves = mode == QRS_SYNTH_GEMM_TF32 ? 1 : 2;
     const int64_t nf_pad = (n_f + T - 1) / T * T;
     const int64_t R_pad = (n_real + kGN - 1) / kGN * kGN;
-    const size_t b = (size_t)2 * R_pad * (2 * nf_pad) * eb;  // hi and lo halves
+    const size_t b = (size_t)halves * R_pad * (2 * nf_pad) * eb;  // hi (and lo) halves
     return 256 + b + (size_t)nf_pad * (sizeof(int2) + sizeof(float4)) + 1024;
 }
 
@@ -489,7 +506,7 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     // workspace: [B hi | B lo][R_pad][Kp], fbasis[nf_pad], fw[nf_pad]
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)h->d_work + 255) & ~(uintptr_t)255);
     void* B = base;
-    const size_t bbytes = (size_t)2 * R_pad * Kp * Cfg::kElemBytes;
+    const size_t bbytes = (size_t)(Cfg::kSplit ? 2 : 1) * R_pad * Kp * Cfg::kElemBytes;
     int2* fbasis = reinterpret_cast<int2*>(base + bbytes);
     float4* fw = reinterpret_cast<float4*>(fbasis + nf_pad);
 
@@ -505,7 +522,7 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode();
     if (!encode) return cudaErrorNotSupported;
     CUtensorMap tmap;
-    const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)(2 * R_pad)};
+    const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)((Cfg::kSplit ? 2 : 1) * R_pad)};
     const cuuint64_t gstride[1] = {(cuuint64_t)(Kp * Cfg::kElemBytes)};
     const cuuint32_t box[2] = {(cuuint32_t)Cfg::kElemsPerRow, (cuuint32_t)kGN};
     const cuuint32_t estride[2] = {1, 1};
@@ -525,6 +542,11 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     a.d_xbound = h->d_xbound;
     a.fbound = fbound;
     a.err = h->d_err;
+    a.inject_wait = 0;
+    if (h->fault & kFaultTimeout) {  // one-shot: this launch only
+        a.inject_wait = 2000000;     // about 1 ms of SM clock
+        h->fault &= ~kFaultTimeout;
+    }
     e = cudaFuncSetAttribute(k_gemm_main<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemBytes);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((P + kGM - 1) / kGM), (unsigned)(R_pad / kGN));
@@ -537,6 +559,8 @@ cudaError_t launch_synth_gemm(qrs_handle* h, int mode, const DrawParams& p, cons
 {
     if (mode == QRS_SYNTH_GEMM_3XTF32)
         return launch_gemm_t<QRS_SYNTH_GEMM_3XTF32>(h, p, xy, P, n_real, col_psd, c_vk, out, s);
+    if (mode == QRS_SYNTH_GEMM_TF32)
+        return launch_gemm_t<QRS_SYNTH_GEMM_TF32>(h, p, xy, P, n_real, col_psd, c_vk, out, s);
     return launch_gemm_t<QRS_SYNTH_GEMM_BF16X3>(h, p, xy, P, n_real, col_psd, c_vk, out, s);
 }
 

@@ -4,7 +4,9 @@
 // except where stated; every sum has a fixed order (deterministic) except the
 // per-cell target histograms (shared-memory atomics).
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "../../include/qrs_proposal.h"
 #include "qrs_internal.h"
@@ -418,6 +420,113 @@ static double vk_c()
            std::pow(24.0 / 5.0 * std::tgamma(6.0 / 5.0), 5.0 / 6.0);
 }
 
+// Forward pass into workspace (X, H1, H2) and Z.
+static cudaError_t mlp_forward(int C, const float* P, const double* geom, int64_t n, float* X, float* H1, float* H2,
+                               float* Z, cudaStream_t s)
+{
+    MlpView w = mlp_view(const_cast<float*>(P), C);
+    const int N = (int)n;
+    k_features<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(geom, n, X);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = sgemm<false, false, kEpiBias | kEpiRelu>(N, kHid, 6, X, 6, w.W1, kHid, H1, kHid, w.b1, nullptr, 0, s);
+    if (e == cudaSuccess) e = sgemm<false, false, kEpiBias | kEpiRelu>(N, kHid, kHid, H1, kHid, w.W2, kHid, H2, kHid, w.b2, nullptr, 0, s);
+    if (e == cudaSuccess) e = sgemm<false, false, kEpiBias>(N, C, kHid, H2, kHid, w.W3, C, Z, C, w.b3, nullptr, 0, s);
+    return e;
+}
+
+constexpr int kMaxSplit = 8;  // K slices of the long-K gradient products
+
+// Slices for a long-K product: enough 64 x 64 tiles for about two per SM on a
+// 152-SM part, at most kMaxSplit, each slice at least 128 deep.
+static int split_for(int M, int N, int K)
+{
+    const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
+    int sp = (304 + tiles - 1) / tiles;
+    sp = std::min(sp, kMaxSplit);
+    sp = std::min(sp, std::max(1, K / 128));
+    return std::max(sp, 1);
+}
+
+static size_t mlp_ws_floats(int C, int64_t n)
+{
+    return (size_t)n * (8 + 4 * kHid + 2 * (size_t)C + 2) + 64 +
+           (size_t)kMaxSplit * std::max((size_t)kHid * (size_t)C, (size_t)n * kHid) + 64;
+}
+
+// The loss and its gradient (the launches of qrs_mlp_loss_grad) with the
+// workspace at ws (mlp_ws_floats(C, n) floats); *launches counts the kernels.
+static cudaError_t mlp_loss_grad(int C, const float* params, const double* geom, const float* targets, int64_t n,
+                                 float* grad, float* loss, float* ws, cudaStream_t s, int* launches_out)
+{
+    float* X = ws;
+    float* H1 = X + 8 * n;
+    float* H2 = H1 + kHid * n;
+    float* dA2 = H2 + kHid * n;
+    float* dA1 = dA2 + kHid * n;
+    float* Z = dA1 + kHid * n;
+    float* dZ = Z + (int64_t)C * n;
+    float* lrow = dZ + (int64_t)C * n + n;  // (n floats after dZ unused)
+    float* part = reinterpret_cast<float*>(((uintptr_t)(lrow + n) + 255) & ~(uintptr_t)255);  // split-K slices
+    MlpView w = mlp_view(const_cast<float*>(params), C);
+    MlpView g = mlp_view(grad, C);
+    const int N = (int)n;
+    cudaError_t e = mlp_forward(C, params, geom, n, X, H1, H2, Z, s);
+    if (e == cudaSuccess) {
+        k_softmax_ce<<<(unsigned)n, 256, 0, s>>>(Z, targets, C, n, dZ, lrow);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_loss_mean<<<1, 1024, 0, s>>>(lrow, n, loss);
+        e = cudaGetLastError();
+    }
+    int launches = 4 + 2;
+    auto colsum = [&](const float* A, int cols, float* out) {
+        k_colsum<<<(unsigned)((cols + 31) / 32), 256, 0, s>>>(A, N, cols, out);
+        ++launches;
+        return cudaGetLastError();
+    };
+    auto gemm_launches = [&](int sp) { launches += sp > 1 ? 2 : 1; };
+    // layer 3: dW3 = H2^T dZ, db3 = column sums of dZ, dA2 = (dZ W3^T) * (H2 > 0)
+    int sp = split_for(kHid, C, N);
+    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(kHid, C, N, H2, kHid, dZ, C, g.W3, C, nullptr, nullptr, 0, s, sp, part);
+    gemm_launches(sp);
+    if (e == cudaSuccess) e = colsum(dZ, C, g.b3);
+    sp = split_for(N, kHid, C);
+    if (e == cudaSuccess) e = sgemm<false, true, kEpiMask>(N, kHid, C, dZ, C, w.W3, C, dA2, kHid, nullptr, H2, kHid, s, sp, part);
+    gemm_launches(sp);
+    // layer 2
+    sp = split_for(kHid, kHid, N);
+    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(kHid, kHid, N, H1, kHid, dA2, kHid, g.W2, kHid, nullptr, nullptr, 0, s, sp, part);
+    gemm_launches(sp);
+    if (e == cudaSuccess) e = colsum(dA2, kHid, g.b2);
+    if (e == cudaSuccess) e = sgemm<false, true, kEpiMask>(N, kHid, kHid, dA2, kHid, w.W2, kHid, dA1, kHid, nullptr, H1, kHid, s);
+    gemm_launches(1);
+    // layer 1
+    sp = split_for(6, kHid, N);
+    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(6, kHid, N, X, 6, dA1, kHid, g.W1, kHid, nullptr, nullptr, 0, s, sp, part);
+    gemm_launches(sp);
+    if (e == cudaSuccess) e = colsum(dA1, kHid, g.b1);
+    *launches_out = launches;
+    return e;
+}
+
+// Adam's bias corrections 1 / (1 - beta^t) for step t.
+static void adam_corrections(int64_t step, float* c1, float* c2)
+{
+    *c1 = (float)(1.0 / (1.0 - std::pow(0.9, (double)step)));
+    *c2 = (float)(1.0 / (1.0 - std::pow(0.999, (double)step)));
+}
+
+static cudaError_t launch_adam(int C, float* params, float* m, float* v, const float* grad, float lr, int64_t step,
+                               cudaStream_t s)
+{
+    const int64_t n = mlp_params(C);
+    float c1, c2;
+    adam_corrections(step, &c1, &c2);
+    k_adam<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(n, params, m, v, grad, lr, c1, c2);
+    return cudaGetLastError();
+}
+
 }  // namespace qrs
 
 using namespace qrs;
@@ -497,39 +606,6 @@ qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_dom
     return QRS_OK;
 }
 
-// Forward pass into workspace (X, H1, H2) and Z.
-static cudaError_t mlp_forward(int C, const float* P, const double* geom, int64_t n, float* X, float* H1, float* H2,
-                               float* Z, cudaStream_t s)
-{
-    MlpView w = mlp_view(const_cast<float*>(P), C);
-    const int N = (int)n;
-    k_features<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(geom, n, X);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = sgemm<false, false, kEpiBias | kEpiRelu>(N, kHid, 6, X, 6, w.W1, kHid, H1, kHid, w.b1, nullptr, 0, s);
-    if (e == cudaSuccess) e = sgemm<false, false, kEpiBias | kEpiRelu>(N, kHid, kHid, H1, kHid, w.W2, kHid, H2, kHid, w.b2, nullptr, 0, s);
-    if (e == cudaSuccess) e = sgemm<false, false, kEpiBias>(N, C, kHid, H2, kHid, w.W3, C, Z, C, w.b3, nullptr, 0, s);
-    return e;
-}
-
-constexpr int kMaxSplit = 8;  // K slices of the long-K gradient products
-
-// Slices for a long-K product: enough 64 x 64 tiles for about two per SM on a
-// 152-SM part, at most kMaxSplit, each slice at least 128 deep.
-static int split_for(int M, int N, int K)
-{
-    const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
-    int sp = (304 + tiles - 1) / tiles;
-    sp = std::min(sp, kMaxSplit);
-    sp = std::min(sp, std::max(1, K / 128));
-    return std::max(sp, 1);
-}
-
-static size_t mlp_ws_floats(int C, int64_t n)
-{
-    return (size_t)n * (8 + 4 * kHid + 2 * (size_t)C + 2) + 64 +
-           (size_t)kMaxSplit * std::max((size_t)kHid * (size_t)C, (size_t)n * kHid) + 64;
-}
-
 qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, const double* geom, int64_t n,
                            float* logits, void* stream)
 {
@@ -561,59 +637,13 @@ qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params
     h->last_error.clear();
     if (!cells_ok(n_cells) || n < 1 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 16384], n in [1, 2^24]");
     if (!params || !geom || !targets || !grad || !loss) return fail(h, QRS_ERR_ARG, "null pointer argument");
-    const int C = n_cells;
-    qrs_status st = ensure_work(h, mlp_ws_floats(C, n) * sizeof(float));
+    qrs_status st = ensure_work(h, mlp_ws_floats(n_cells, n) * sizeof(float));
     if (st != QRS_OK) return st;
-    float* X = static_cast<float*>(h->d_work);
-    float* H1 = X + 8 * n;
-    float* H2 = H1 + kHid * n;
-    float* dA2 = H2 + kHid * n;
-    float* dA1 = dA2 + kHid * n;
-    float* Z = dA1 + kHid * n;
-    float* dZ = Z + (int64_t)C * n;
-    float* lrow = dZ + (int64_t)C * n + n;  // (n floats after dZ unused)
-    float* part = reinterpret_cast<float*>(((uintptr_t)(lrow + n) + 255) & ~(uintptr_t)255);  // split-K slices
-    cudaStream_t s = (cudaStream_t)stream;
-    MlpView w = mlp_view(const_cast<float*>(params), C);
-    MlpView g = mlp_view(grad, C);
-    const int N = (int)n;
+    int launches = 0;
     cudaError_t e = cudaSetDevice(h->device);
-    if (e == cudaSuccess) e = mlp_forward(C, params, geom, n, X, H1, H2, Z, s);
-    if (e == cudaSuccess) {
-        k_softmax_ce<<<(unsigned)n, 256, 0, s>>>(Z, targets, C, n, dZ, lrow);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        k_loss_mean<<<1, 1024, 0, s>>>(lrow, n, loss);
-        e = cudaGetLastError();
-    }
-    int launches = 4 + 2;
-    auto colsum = [&](const float* A, int cols, float* out) {
-        k_colsum<<<(unsigned)((cols + 31) / 32), 256, 0, s>>>(A, N, cols, out);
-        ++launches;
-        return cudaGetLastError();
-    };
-    auto gemm_launches = [&](int sp) { launches += sp > 1 ? 2 : 1; };
-    // layer 3: dW3 = H2^T dZ, db3 = column sums of dZ, dA2 = (dZ W3^T) * (H2 > 0)
-    int sp = split_for(kHid, C, N);
-    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(kHid, C, N, H2, kHid, dZ, C, g.W3, C, nullptr, nullptr, 0, s, sp, part);
-    gemm_launches(sp);
-    if (e == cudaSuccess) e = colsum(dZ, C, g.b3);
-    sp = split_for(N, kHid, C);
-    if (e == cudaSuccess) e = sgemm<false, true, kEpiMask>(N, kHid, C, dZ, C, w.W3, C, dA2, kHid, nullptr, H2, kHid, s, sp, part);
-    gemm_launches(sp);
-    // layer 2
-    sp = split_for(kHid, kHid, N);
-    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(kHid, kHid, N, H1, kHid, dA2, kHid, g.W2, kHid, nullptr, nullptr, 0, s, sp, part);
-    gemm_launches(sp);
-    if (e == cudaSuccess) e = colsum(dA2, kHid, g.b2);
-    if (e == cudaSuccess) e = sgemm<false, true, kEpiMask>(N, kHid, kHid, dA2, kHid, w.W2, kHid, dA1, kHid, nullptr, H1, kHid, s);
-    gemm_launches(1);
-    // layer 1
-    sp = split_for(6, kHid, N);
-    if (e == cudaSuccess) e = sgemm<true, false, kEpiNone>(6, kHid, N, X, 6, dA1, kHid, g.W1, kHid, nullptr, nullptr, 0, s, sp, part);
-    gemm_launches(sp);
-    if (e == cudaSuccess) e = colsum(dA1, kHid, g.b1);
+    if (e == cudaSuccess)
+        e = mlp_loss_grad(n_cells, params, geom, targets, n, grad, loss, static_cast<float*>(h->d_work),
+                          (cudaStream_t)stream, &launches);
     if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_loss_grad");
     h->launches += launches;
     return QRS_OK;
@@ -628,17 +658,126 @@ qrs_status qrs_mlp_adam(qrs_handle* h, int32_t n_cells, float* params, float* m,
     h->last_error.clear();
     if (!cells_ok(n_cells) || step < 1 || !(lr > 0.0f)) return fail(h, QRS_ERR_ARG, "n_cells, step >= 1, lr > 0");
     if (!params || !m || !v || !grad) return fail(h, QRS_ERR_ARG, "null pointer argument");
-    const int64_t n = mlp_params(n_cells);
-    const float c1 = (float)(1.0 / (1.0 - std::pow(0.9, (double)step)));
-    const float c2 = (float)(1.0 / (1.0 - std::pow(0.999, (double)step)));
     cudaError_t e = cudaSetDevice(h->device);
-    if (e == cudaSuccess) {
-        k_adam<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(n, params, m, v, grad, lr,
-                                                                                                     c1, c2);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = launch_adam(n_cells, params, m, v, grad, lr, step, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_adam");
     ++h->launches;
+    return QRS_OK;
+}
+
+qrs_status qrs_proposal_train(qrs_handle* h, qrs_mlp_state* state, const double* geom, const float* targets, int64_t n,
+                              int64_t steps, double lr, int32_t schedule, int64_t total_steps, float* loss_trace,
+                              void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_proposal_train");
+    if (qrs::injected_launch_fault(h, "qrs_proposal_train") != QRS_OK) return QRS_ERR_CUDA;
+    h->last_error.clear();
+    if (!state) return fail(h, QRS_ERR_ARG, "state must be non-NULL");
+    const int C = state->n_cells;
+    if (!cells_ok(C) || n < 1 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 16384], n in [1, 2^24]");
+    if (!state->params || !state->m || !state->v || !geom || !targets)
+        return fail(h, QRS_ERR_ARG, "state vectors, geom and targets must be non-NULL");
+    if (state->step < 0 || steps < 0 || steps > ((int64_t)1 << 40))
+        return fail(h, QRS_ERR_ARG, "state->step >= 0 and steps in [0, 2^40]");
+    if (!(std::isfinite(lr) && lr > 0.0)) return fail(h, QRS_ERR_ARG, "lr must be finite and > 0");
+    if (schedule != QRS_LR_CONSTANT && schedule != QRS_LR_COSINE) return fail(h, QRS_ERR_ARG, "unknown schedule %d", schedule);
+    const int64_t last = state->step + steps;
+    if (schedule == QRS_LR_COSINE && total_steps < last)
+        return fail(h, QRS_ERR_ARG, "the cosine schedule needs total_steps >= state->step + steps");
+    if (steps == 0) return QRS_OK;
+    // workspace: the loss-gradient buffers, the gradient, one loss slot
+    const size_t ws = (mlp_ws_floats(C, n) * sizeof(float) + 255) & ~(size_t)255;
+    const size_t gb = ((size_t)mlp_params(C) * sizeof(float) + 255) & ~(size_t)255;
+    qrs_status st = ensure_work(h, ws + gb + 256 + 256);
+    if (st != QRS_OK) return st;
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)h->d_work + 255) & ~(uintptr_t)255);
+    float* wsp = reinterpret_cast<float*>(base);
+    float* grad = reinterpret_cast<float*>(base + ws);
+    float* loss_slot = reinterpret_cast<float*>(base + ws + gb);
+    const cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(h->device);
+    int64_t launches = 0;
+    const double kPiD = 3.14159265358979323846;
+    for (int64_t t = state->step + 1; t <= last && e == cudaSuccess; ++t) {
+        // the learning rate of step t in FP64, rounded once to FP32
+        const double lr_t = schedule == QRS_LR_COSINE
+                                ? lr * 0.5 * (1.0 + std::cos(kPiD * (double)(t - 1) / (double)total_steps))
+                                : lr;
+        float* loss = loss_trace ? loss_trace + (t - state->step - 1) : loss_slot;
+        int l = 0;
+        e = mlp_loss_grad(C, state->params, geom, targets, n, grad, loss, wsp, s, &l);
+        if (e == cudaSuccess) e = launch_adam(C, state->params, state->m, state->v, grad, (float)lr_t, t, s);
+        launches += l + 1;
+    }
+    h->launches += launches;
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_proposal_train");
+    state->step = last;
+    return QRS_OK;
+}
+
+// Checkpoint file: the 8 bytes "QRSMLP01", int32 n_cells, int32 0, int64 step,
+// int64 parameter count, then params, m, v as FP32 (host byte order, little
+// endian on every supported host).
+static const char kCkptMagic[8] = {'Q', 'R', 'S', 'M', 'L', 'P', '0', '1'};
+
+qrs_status qrs_mlp_save(qrs_handle* h, const qrs_mlp_state* state, const char* path, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    if (!state || !path || !cells_ok(state->n_cells) || !state->params || !state->m || !state->v || state->step < 0)
+        return fail(h, QRS_ERR_ARG, "state (n_cells in [1, 16384], vectors, step >= 0) and path must be valid");
+    const int64_t P = mlp_params(state->n_cells);
+    std::vector<float> buf((size_t)(3 * P));
+    cudaError_t e = cudaSetDevice(h->device);
+    const float* src[3] = {state->params, state->m, state->v};
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(buf.data() + i * P, src[i], (size_t)P * sizeof(float), cudaMemcpyDeviceToHost,
+                            (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_save");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(h, QRS_ERR_ARG, "cannot open %s for writing", path);
+    const int32_t hdr32[2] = {state->n_cells, 0};
+    const int64_t hdr64[2] = {state->step, P};
+    bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(hdr32, sizeof(hdr32), 1, f) == 1 &&
+              std::fwrite(hdr64, sizeof(hdr64), 1, f) == 1 &&
+              std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(h, QRS_ERR_ARG, "writing %s failed", path);
+    return QRS_OK;
+}
+
+qrs_status qrs_mlp_load(qrs_handle* h, qrs_mlp_state* state, const char* path, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    if (!state || !path || !cells_ok(state->n_cells) || !state->params || !state->m || !state->v)
+        return fail(h, QRS_ERR_ARG, "state (n_cells in [1, 16384], vectors) and path must be valid");
+    const int64_t P = mlp_params(state->n_cells);
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(h, QRS_ERR_ARG, "cannot open %s", path);
+    char magic[8];
+    int32_t hdr32[2];
+    int64_t hdr64[2];
+    std::vector<float> buf((size_t)(3 * P));
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+              std::fread(hdr32, sizeof(hdr32), 1, f) == 1 && std::fread(hdr64, sizeof(hdr64), 1, f) == 1;
+    if (ok && (hdr32[0] != state->n_cells || hdr64[1] != P || hdr64[0] < 0)) {
+        std::fclose(f);
+        return fail(h, QRS_ERR_ARG, "%s holds a network of %d cells, not %d", path, (int)hdr32[0], (int)state->n_cells);
+    }
+    ok = ok && std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) return fail(h, QRS_ERR_ARG, "%s is not a complete checkpoint", path);
+    cudaError_t e = cudaSetDevice(h->device);
+    float* dst[3] = {state->params, state->m, state->v};
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(dst[i], buf.data() + i * P, (size_t)P * sizeof(float), cudaMemcpyHostToDevice,
+                            (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);  // buf is released on return
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_load");
+    state->step = hdr64[0];
     return QRS_OK;
 }
 

@@ -155,11 +155,16 @@ qrs_status make_draw_params(qrs_handle* h, const qrs_psd* psd, const qrs_domain*
 
 double freq_bound(const DrawParams& p) { return p.fmax; }
 
-static bool counters_fit(int64_t n_f, int64_t real_offset, int64_t n_real)
+bool counters_fit(int64_t n_f, int64_t real_offset, int64_t n_real)
 {
-    // (real_offset + n_real) * n_f must stay below 2^64 (stream index space)
-    const unsigned __int128 top = (unsigned __int128)(uint64_t)(real_offset + n_real) * (uint64_t)n_f;
-    return (top >> 64) == 0 && real_offset + n_real >= real_offset;
+    // every realisation index real_offset + r stays within int64 and every
+    // stream index (real_offset + r) n_f + k below 2^64; the sum is formed in
+    // 128-bit unsigned arithmetic, so no signed overflow
+    if (n_f < 0 || real_offset < 0 || n_real < 0) return false;
+    const unsigned __int128 sum = (unsigned __int128)(uint64_t)real_offset + (uint64_t)n_real;
+    if (sum > (unsigned __int128)INT64_MAX) return false;
+    const unsigned __int128 top = sum * (unsigned __int128)(uint64_t)n_f;
+    return (top >> 64) == 0;
 }
 
 }  // namespace qrs
@@ -187,6 +192,7 @@ qrs_status qrs_create(qrs_handle** out, int32_t device)
     if (const char* f = std::getenv("QRS_FAULT")) {
         if (std::strstr(f, "alloc")) h->fault |= kFaultAlloc;
         if (std::strstr(f, "launch")) h->fault |= kFaultLaunch;
+        if (std::strstr(f, "timeout")) h->fault |= kFaultTimeout;
     }
     if (e != cudaSuccess) {
         if (h->d_err) cudaFree(h->d_err);
@@ -278,7 +284,7 @@ qrs_status qrs_synthesize_points(qrs_handle* h, const qrs_psd* psd, const qrs_do
         ++h->launches;
         return QRS_OK;
     }
-    if (mode == QRS_SYNTH_GEMM_3XTF32 || mode == QRS_SYNTH_GEMM_BF16X3) {
+    if (mode == QRS_SYNTH_GEMM_3XTF32 || mode == QRS_SYNTH_GEMM_BF16X3 || mode == QRS_SYNTH_GEMM_TF32) {
         if (n_real > 65280) return fail(h, QRS_ERR_ARG, "GEMM modes take at most 65280 realisations per call");
         if (col_psd && ((uintptr_t)col_psd & 7)) return fail(h, QRS_ERR_ARG, "col_psd must be 8-byte aligned");
         st = ensure_work(h, gemm_workspace_bytes(mode, n_f, n_real));

@@ -29,8 +29,10 @@ struct qrs_handle {
     // Batched-piston state (persistent launch, CUDA graph cache).
     void* piston_state = nullptr;
     // Host-side fault injection, from QRS_FAULT at qrs_create ("alloc",
-    // "launch", or both separated by a comma): workspace allocations and
-    // launches then fail with their error status without touching the GPU.
+    // "launch", "timeout", separated by commas): workspace allocations and
+    // launches then fail with their error status without touching the GPU;
+    // "timeout" makes the next GEMM-form launch wait out a bounded wait on a
+    // barrier that nothing arrives at (QRS_ERR_TIMEOUT at the next qrs_sync).
     int fault = 0;
 };
 
@@ -38,6 +40,7 @@ namespace qrs {
 
 constexpr int kFaultAlloc = 1;
 constexpr int kFaultLaunch = 2;
+constexpr int kFaultTimeout = 4;  // the next tensor-core GEMM launch runs out a bounded wait (one-shot)
 
 // An NVTX range over a C-ABI call (seen by profilers, free otherwise).
 struct NvtxRange {
@@ -57,6 +60,10 @@ qrs_status injected_launch_fault(qrs_handle* h, const char* where);
 // Host-side construction of the draw parameters from the public structs.
 qrs_status make_draw_params(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, const qrs_sampler* smp,
                             int64_t n_f, int64_t real_offset, DrawParams* out);
+
+// True when every stream index (real_offset + r) n_f + k of a call stays below
+// 2^64 (all three arguments non-negative).
+bool counters_fit(int64_t n_f, int64_t real_offset, int64_t n_real);
 
 // Largest |f| component a draw can produce (for fixed-point scaling).
 double freq_bound(const DrawParams& p);

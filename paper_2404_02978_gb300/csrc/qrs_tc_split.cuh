@@ -1,5 +1,6 @@
-// qrs_tc_split.cuh -- operand formats of the split-precision tensor-core
-// products (3XTF32, BF16X3) shared by the shared-draw GEMM (k_gemm.cu) and the
+// qrs_tc_split.cuh -- operand formats of the tensor-core products (split
+// 3XTF32 and BF16X3, single-pass TF32) shared by the shared-draw GEMM
+// (k_gemm.cu; all three) and the
 // separable-grid form (k_grid.cu): per-format K-chunk geometry, accumulation
 // segment lengths, and the hi/lo split of FP32 values into 16-byte pieces of
 // a 128-byte-swizzled K-major operand row.
@@ -11,6 +12,9 @@
 
 #ifndef QRS_GEMM_SEG_TF32
 #define QRS_GEMM_SEG_TF32 6   // K chunks per accumulation segment, 3XTF32 (72 accumulation steps)
+#endif
+#ifndef QRS_GEMM_SEG_TF32_SINGLE
+#define QRS_GEMM_SEG_TF32_SINGLE 18  // K chunks per accumulation segment, single TF32 (72 accumulation steps)
 #endif
 #ifndef QRS_GEMM_SEG_BF16
 #define QRS_GEMM_SEG_BF16 8   // K chunks per accumulation segment, BF16X3 (96 accumulation steps)
@@ -34,7 +38,21 @@ struct GemmCfg<QRS_SYNTH_GEMM_3XTF32> {
     static constexpr int kTermsPer16B = 4;
     static constexpr uint32_t kFormat = 2;     // TF32
     static constexpr bool kTF32 = true;
+    static constexpr bool kSplit = true;       // hi and lo halves, three products
     static constexpr int kSeg = QRS_GEMM_SEG_TF32;
+};
+// Single-pass TF32: each operand rounded once to TF32 (11 significant bits),
+// one product per K step.
+template <>
+struct GemmCfg<QRS_SYNTH_GEMM_TF32> {
+    static constexpr int kElemBytes = 4;
+    static constexpr int kElemsPerRow = 32;
+    static constexpr int kTermsPerChunk = 16;
+    static constexpr int kTermsPer16B = 4;
+    static constexpr uint32_t kFormat = 2;
+    static constexpr bool kTF32 = true;
+    static constexpr bool kSplit = false;
+    static constexpr int kSeg = QRS_GEMM_SEG_TF32_SINGLE;
 };
 template <>
 struct GemmCfg<QRS_SYNTH_GEMM_BF16X3> {
@@ -44,6 +62,7 @@ struct GemmCfg<QRS_SYNTH_GEMM_BF16X3> {
     static constexpr int kTermsPer16B = 8;
     static constexpr uint32_t kFormat = 1;     // BF16
     static constexpr bool kTF32 = false;
+    static constexpr bool kSplit = true;
     static constexpr int kSeg = QRS_GEMM_SEG_BF16;
 };
 
@@ -65,7 +84,13 @@ __device__ __forceinline__ void pack16(const float (&v)[GemmCfg<PREC>::kTermsPer
 {
     uint32_t* wh = reinterpret_cast<uint32_t*>(&hi);
     uint32_t* wl = reinterpret_cast<uint32_t*>(&lo);
-    if (GemmCfg<PREC>::kTF32) {
+    if (!GemmCfg<PREC>::kSplit) {  // one TF32 rounding per value, no low half
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            wh[e] = tf32_rna_bits(v[e]);
+            wl[e] = 0u;
+        }
+    } else if (GemmCfg<PREC>::kTF32) {
 #if QRS_GEMM_INTSPLIT
         // residuals x - hi two at a time, as fma(hi, -1, x) (exact, the same bits)
 #pragma unroll

@@ -7,12 +7,19 @@
 * Device-side index checks: a grid node index beyond n_points and a pair
   index beyond the values are not used; the device error word reports
   QRS_ERR_DEVICE_CHECK at the next qrs_sync, which clears it.
+* Bounded waits: "timeout" makes the next tensor-core GEMM launch wait on an
+  mbarrier that no thread arrives at, with a limit of about 1 ms; every CTA
+  records QRS_ERR_TIMEOUT, lets its copies in flight land, frees its tensor
+  memory and returns (no MMA has been issued).  The next call on the same
+  handle runs normally and matches the oracle.
 """
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2404_02978_gb300 as qrs
+from paper_2404_02978_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
@@ -67,3 +74,31 @@ def test_grid_index_beyond_points_is_caught():
     written = torch.isfinite(out)
     assert written.sum().item() == 2 * 63 and not written[:, 3 * 8 + 5].any()
     qrs.qrs_sync(h)  # cleared
+
+
+@pytest.mark.parametrize("mode", ["gemm_3xtf32", "gemm_bf16x3"])
+def test_injected_wait_timeout_then_normal_call(monkeypatch, mode):
+    monkeypatch.setenv("QRS_FAULT", "timeout")
+    h = qrs.Handle(0)
+    monkeypatch.delenv("QRS_FAULT")
+    xy_np = wl.pupil_grid(32, 8.0)[:300]
+    xy = torch.from_numpy(xy_np).cuda()
+    p = qrs.params(seed=5)
+    n_f, R = 200, 20
+    qrs.qrs_synthesize_points(h, p, n_f, R, xy, mode=mode)
+    with pytest.raises(qrs.QrsError) as e:
+        qrs.qrs_sync(h)
+    assert e.value.status == -3
+    qrs.qrs_sync(h)  # cleared
+    # the same handle and context: a normal call against the oracle
+    got = qrs.qrs_synthesize_points(h, p, n_f, R, xy, mode=mode)
+    qrs.qrs_sync(h)
+    op = oracle.params(seed=5)
+    ref = oracle.synthesize_shared(op, n_f, R, xy_np)
+    sig = np.sqrt(np.sum(oracle.draw(op, n_f=n_f, n_real=1)["F"] ** 2))
+    tol = 1e-5 if mode == "gemm_3xtf32" else 5e-5
+    assert np.abs(got.cpu().numpy().astype(np.float64) - ref).max() <= tol * sig
+    # and the fused form on the same handle
+    fu = qrs.qrs_synthesize_points(h, p, n_f, 2, xy)
+    qrs.qrs_sync(h)
+    assert torch.isfinite(fu).all()

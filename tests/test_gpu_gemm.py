@@ -5,7 +5,10 @@ column r takes its coefficients from stream points (real_offset + r) N_f + k
 and its own (r0, L0).  Tolerances per value, relative to the column's field
 standard deviation sigma_r (sigma_r^2 = sum_k F_kr^2):
   3XTF32: 1e-5 (split TF32, ~2^-22 per product);
-  BF16X3: 2e-4 (split BF16, ~2^-17 per operand; the measured error is printed).
+  BF16X3: 5e-5 (split BF16, ~2^-17 per split product: the measured maximum over
+          every case here is 2.7e-5, the rms 4e-6; the error is printed);
+  TF32:   2e-3 (single pass, each operand rounded once to TF32, ~2^-11 per
+          product: measured 1.1e-3 max, 2.7e-4 rms).
 """
 import numpy as np
 import pytest
@@ -17,7 +20,7 @@ from oracle import analytic as an
 from paper_2404_02978_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
-TOL = {"gemm_3xtf32": 1e-5, "gemm_bf16x3": 2e-4}
+TOL = {"gemm_3xtf32": 1e-5, "gemm_bf16x3": 5e-5, "gemm_tf32": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +49,7 @@ def _run(h, p, n_f, n_real, xy, mode, off, col_psd):
     return out.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("mode", ["gemm_3xtf32", "gemm_bf16x3"])
+@pytest.mark.parametrize("mode", ["gemm_3xtf32", "gemm_bf16x3", "gemm_tf32"])
 @pytest.mark.parametrize("case", ["pupil", "wide", "blocks"])
 def test_gemm_parity(h, mode, case):
     rng = np.random.default_rng(7)
@@ -80,20 +83,33 @@ def test_gemm_column0_equals_fused_realisation(h):
     assert np.max(np.abs(g[0] - fu.cpu().numpy()[0])) <= 2e-5 * sig[0]
 
 
-def test_gemm_full_size_sampled(h):
+# Full-size bounds per value (max) and over the sampled values (rms), in units
+# of the column's sigma.  3XTF32 keeps the 1e-5 bar.  BF16X3 carries about
+# 2^-17 relative per split product (8-bit high part, its BF16 residual, the
+# dropped low x low product), so over the 32,768-deep sum of independent
+# terms a value's error is a few 1e-6 sigma rms; its max over the 4096 sampled
+# values stays below 5e-5 sigma.
+FULL_SIZE_BOUND = {"gemm_3xtf32": (1e-5, 3e-6), "gemm_bf16x3": (5e-5, 8e-6), "gemm_tf32": (2e-3, 4e-4)}
+
+
+@pytest.mark.parametrize("mode", ["gemm_3xtf32", "gemm_bf16x3", "gemm_tf32"])
+def test_gemm_full_size_sampled(h, mode):
     """The 16 m / 512^2 pupil (205,892 points), N_f = 16384 shared by 256
     columns with r0 in [0.08, 0.2] m, L0 in [20, 50] m: 16 sampled points, all
-    256 columns, against the oracle."""
+    256 columns, against the oracle, in both split precisions."""
     cfg = wl.GEMM_SCREEN
     p = wl.method_params(cfg)
     xy = wl.pupil_grid(cfg["grid"], cfg["pupil"])
     rng = np.random.default_rng(cfg["seed"])
     R = cfg["n_real"]
     col_psd = np.stack([rng.uniform(*cfg["r0_range"], R), rng.uniform(*cfg["L0_range"], R)], -1)
-    got = _run(h, p, cfg["n_f"], R, xy, "gemm_3xtf32", 0, col_psd)
+    got = _run(h, p, cfg["n_f"], R, xy, mode, 0, col_psd)
     idx = rng.choice(xy.shape[0], 16, replace=False)
     ref = oracle.synthesize_shared(p, cfg["n_f"], R, xy[idx], col_psd=col_psd)
     sig = _col_sigma(p, cfg["n_f"], R, 0, col_psd)
     err = np.abs(got[:, idx] - ref) / sig[:, None]
-    print("full-size 3xTF32: max err %.3g sigma" % err.max())
-    assert err.max() <= TOL["gemm_3xtf32"]
+    rms = float(np.sqrt(np.mean(err ** 2)))
+    print("full-size %s: max err %.3g sigma, rms %.3g sigma" % (mode, err.max(), rms))
+    assert np.isfinite(got).all()
+    assert err.max() <= FULL_SIZE_BOUND[mode][0]
+    assert rms <= FULL_SIZE_BOUND[mode][1]

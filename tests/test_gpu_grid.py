@@ -6,7 +6,7 @@ tensor-core product.  The field is the same as the fused form's at those
 points (realisation r from stream points (real_offset + r) N_f + k), so the
 oracle is its plain Eq. 3 sum at the grid points.  Tolerance per value,
 relative to the realisation's field standard deviation sigma_r
-(sigma_r^2 = sum_k F_k^2): 3XTF32 1e-5, BF16X3 2e-4 (the measured error is
+(sigma_r^2 = sum_k F_k^2): 3XTF32 1e-5, BF16X3 5e-5 (the measured error is
 printed).
 """
 import numpy as np
@@ -18,7 +18,7 @@ import paper_2404_02978_gb300 as qrs
 from paper_2404_02978_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
-TOL = {"gemm_3xtf32": 1e-5, "gemm_bf16x3": 2e-4}
+TOL = {"gemm_3xtf32": 1e-5, "gemm_bf16x3": 5e-5}
 
 
 @pytest.fixture(scope="module")
@@ -96,7 +96,8 @@ def test_grid_pupil_index_equals_fused(h):
     assert index.max() + 1 == xy.shape[0]
     p = qrs.params(seed=72)
     out = torch.full((3, xy.shape[0]), float("nan"), device="cuda")
-    qrs.qrs_synthesize_grid(h, p, 700, 3, _dev(c), _dev(c), index=_dev(index), out=out, real_offset=4)
+    qrs.qrs_synthesize_grid(h, p, 700, 3, _dev(c), _dev(c), index=_dev(index), n_points=xy.shape[0], out=out,
+                            real_offset=4)
     fu = qrs.qrs_synthesize_points(h, p, 700, 3, _dev(xy), real_offset=4)
     qrs.qrs_sync(h)
     g, f = out.cpu().numpy().astype(np.float64), fu.cpu().numpy().astype(np.float64)
@@ -137,7 +138,7 @@ def test_grid_phase_screen_full_size(h):
     xy = wl.pupil_grid(cfg["grid"], cfg["pupil"])
     p = wl.method_params(cfg)
     R = cfg["n_real"]
-    g = qrs.qrs_synthesize_grid(h, p, cfg["n_f"], R, _dev(c), _dev(c), index=_dev(index))
+    g = qrs.qrs_synthesize_grid(h, p, cfg["n_f"], R, _dev(c), _dev(c), index=_dev(index), n_points=xy.shape[0])
     f = qrs.qrs_synthesize_points(h, p, cfg["n_f"], R, _dev(xy))
     qrs.qrs_sync(h)
     sig = _sigma(p, cfg["n_f"], R, 0)

@@ -147,14 +147,58 @@ def test_trained_proposal_lowers_structure_function_error(h, fold):
 
 def test_training_checkpoint_resumes_exactly(h, tmp_path):
     """20 Adam steps in one run equal 10 steps, a checkpoint written and read
-    back, and 10 more (deterministic kernels: bit-identical parameters)."""
+    back through libqrs (qrs_mlp_save / qrs_mlp_load), and 10 more, on the
+    cosine schedule of the whole run (deterministic kernels: bit-identical
+    parameters)."""
     g = _dev(_geom(64, 9), torch.float64)
     T = torch.softmax(torch.randn(64, C, device="cuda"), 1)
-    P1, _ = qrs.train_proposal(h, C, g, T, steps=20, lr=1e-3, seed=5)
-    _, _, st = qrs.train_proposal(h, C, g, T, steps=10, lr=1e-3, seed=5, return_state=True)
-    st.save(tmp_path / "ck.npz")
-    st2 = qrs.ProposalState.load(tmp_path / "ck.npz")
-    assert st2.step == 10 and torch.equal(st2.params, st.params) and torch.equal(st2.v, st.v)
-    P2, _ = qrs.train_proposal(h, C, g, T, steps=10, lr=1e-3, state=st2)
+    P1, _ = qrs.train_proposal(h, C, g, T, steps=20, lr=1e-3, seed=5, schedule="cosine")
+    _, _, st = qrs.train_proposal(h, C, g, T, steps=10, lr=1e-3, seed=5, return_state=True, schedule="cosine",
+                                  total_steps=20)
+    st.save(tmp_path / "ck.bin", h)
+    st2 = qrs.ProposalState.load(tmp_path / "ck.bin", h, C)
+    assert st2.step == 10 and torch.equal(st2.params, st.params) and torch.equal(st2.m, st.m)
+    assert torch.equal(st2.v, st.v)
+    P2, _ = qrs.train_proposal(h, C, g, T, steps=10, lr=1e-3, state=st2, schedule="cosine", total_steps=20)
     torch.cuda.synchronize()
     assert torch.equal(P1, P2)
+    with pytest.raises(qrs.QrsError):  # another network size
+        qrs.ProposalState.load(tmp_path / "ck.bin", h, C // 2)
+
+
+def test_training_in_one_c_call_equals_step_by_step(h):
+    """qrs_proposal_train called through ctypes (the whole Adam loop and its
+    cosine schedule in libqrs) against the same steps taken one C call at a
+    time (qrs_mlp_loss_grad, then qrs_mlp_adam with the schedule's learning
+    rate): bit-identical parameters, moments and per-step losses."""
+    import ctypes
+    import math
+    n, steps, lr, total = 96, 12, 3e-3, 30
+    g = _dev(_geom(n, 11), torch.float64)
+    T = torch.softmax(torch.randn(n, C, device="cuda", generator=torch.Generator("cuda").manual_seed(4)), 1)
+    P0 = qrs.qrs_mlp_init(h, C, 7)
+    f = qrs.load().qrs_proposal_train
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(qrs.QrsMlpState), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                  ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    p1, m1, v1 = P0.clone(), torch.zeros_like(P0), torch.zeros_like(P0)
+    trace = torch.full((steps,), float("nan"), device="cuda")
+    st = qrs.QrsMlpState(C, 0, 0, p1.data_ptr(), m1.data_ptr(), v1.data_ptr())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert f(h.h, ctypes.byref(st), g.data_ptr(), T.data_ptr(), n, steps, lr, 1, total, trace.data_ptr(), stream) == 0
+    assert st.step == steps
+    p2, m2, v2 = P0.clone(), torch.zeros_like(P0), torch.zeros_like(P0)
+    grad, loss = torch.empty_like(P0), torch.empty(1, device="cuda")
+    losses = []
+    for t in range(1, steps + 1):
+        qrs.qrs_mlp_loss_grad(h, C, p2, g, T, grad=grad, loss=loss)
+        losses.append(loss.clone())
+        qrs.qrs_mlp_adam(h, C, p2, m2, v2, grad, lr * 0.5 * (1.0 + math.cos(math.pi * (t - 1) / total)), t)
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p2) and torch.equal(m1, m2) and torch.equal(v1, v2)
+    assert torch.equal(trace, torch.cat(losses))
+    # argument errors launch nothing
+    st_bad = qrs.QrsMlpState(C, 0, 0, p1.data_ptr(), m1.data_ptr(), v1.data_ptr())
+    assert f(h.h, ctypes.byref(st_bad), g.data_ptr(), T.data_ptr(), n, 5, lr, 1, 4, None, stream) == -1
+    assert f(h.h, ctypes.byref(st_bad), g.data_ptr(), T.data_ptr(), n, 5, -1.0, 0, 0, None, stream) == -1
+    assert st_bad.step == 0

@@ -58,6 +58,7 @@ def test_ctypes_layouts_match_c(tmp_path):
 #include <stdio.h>
 #include <stddef.h>
 #include "qrs.h"
+#include "qrs_proposal.h"
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(qrs_psd), sizeof(qrs_domain), sizeof(qrs_sampler),
          sizeof(qrs_draw_out), sizeof(qrs_piston_job));
@@ -65,17 +66,21 @@ int main(void) {
          offsetof(qrs_sampler, frame),
          offsetof(qrs_piston_job, n_f), offsetof(qrs_piston_job, ap_xy), offsetof(qrs_piston_job, n_ap),
          offsetof(qrs_piston_job, n_pairs));
+  printf("%zu %zu %zu %zu\\n", sizeof(qrs_mlp_state), offsetof(qrs_mlp_state, step), offsetof(qrs_mlp_state, params),
+         offsetof(qrs_mlp_state, v));
   return 0;
 }
 """)
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
-    sizes, offs = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().splitlines()]
+    sizes, offs, mlp = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().splitlines()]
     assert sizes == [C.sizeof(qrs.QrsPsd), C.sizeof(qrs.QrsDomain), C.sizeof(qrs.QrsSampler),
                      C.sizeof(qrs.QrsDrawOut), C.sizeof(qrs.QrsPistonJob)]
     assert offs == [qrs.QrsSampler.cell_cdf.offset, qrs.QrsSampler.kind.offset, qrs.QrsSampler.frame.offset,
                     qrs.QrsPistonJob.n_f.offset,
                     qrs.QrsPistonJob.ap_xy.offset, qrs.QrsPistonJob.n_ap.offset, qrs.QrsPistonJob.n_pairs.offset]
+    assert mlp == [C.sizeof(qrs.QrsMlpState), qrs.QrsMlpState.step.offset, qrs.QrsMlpState.params.offset,
+                   qrs.QrsMlpState.v.offset]
 
 
 def test_workload_sizes():

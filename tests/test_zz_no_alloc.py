@@ -59,6 +59,19 @@ def test_noalloc_matches_handle_entry_point_twice():
         sig = torch.sqrt(torch.mean(ref.double() ** 2, dim=1, keepdim=True))
         err = ((out.double() - ref.double()).abs() / sig).max().item()
         assert err <= TOL_FIELD, err
+    # the contract itself: a warm call leaves the device's free memory unchanged
+    p, n_f, n_real, xy_np = cases[0]
+    xy = torch.from_numpy(xy_np).cuda()
+    out = torch.empty(n_real, xy.shape[0], device="cuda")
+    psd, dom, smp = qrs._structs(p)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(0)[0]
+    st = f(C.byref(psd), C.byref(dom), C.byref(smp), n_f, n_real, 4, xy.data_ptr(), xy.shape[0], out.data_ptr(),
+           C.c_void_p(stream.cuda_stream))
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info(0)[0]
+    assert st == 0
+    assert free1 == free0, "free device memory changed by %d bytes" % (free0 - free1)
     h.close()
 
 
@@ -71,3 +84,7 @@ def test_noalloc_rejects_invalid_sizes():
     assert f(C.byref(psd), C.byref(dom), C.byref(smp), 2**31, 1, 0, xy.data_ptr(), 4, out.data_ptr(), None) == -1
     assert f(C.byref(psd), C.byref(dom), C.byref(smp), 64, -1, 0, xy.data_ptr(), 4, out.data_ptr(), None) == -1
     assert f(C.byref(psd), C.byref(dom), C.byref(smp), 64, 1, 0, None, 4, out.data_ptr(), None) == -1
+    # real_offset + n_real beyond int64: rejected like qrs_synthesize_points does
+    big = 2**63 - 1
+    assert f(C.byref(psd), C.byref(dom), C.byref(smp), 64, big, big, xy.data_ptr(), 4, out.data_ptr(), None) == -1
+    assert f(C.byref(psd), C.byref(dom), C.byref(smp), 1, 2, big - 1, xy.data_ptr(), 4, out.data_ptr(), None) == -1
