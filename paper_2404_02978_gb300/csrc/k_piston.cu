@@ -2,13 +2,26 @@
 //
 // One work item = (job, realisation).  The CTA draws the realisation's N_f
 // terms into shared memory (fused draw, chunks of kPisChunk terms), then its
-// warps take (aperture, 256-term slice) units round-robin: the 32 lanes split
-// the slice's terms, each lane forms F A_a(|f|) (a cos 2 pi f.p - b sin 2 pi f.p)
-// in amplitude-phase form, A_a(|f|) F amp cos 2 pi (f.p + psi) (one cosine;
-// amp and psi as in the fused synthesis kernel), with the double-float phase
-// (aperture centres lie up to hundreds of metres from the origin), and a
-// warp-shuffle reduction gives the slice's partial piston.  Partials are folded in a fixed order (deterministic sums), then
-// the pair differences are written.
+// warps take (group of apertures, slice of terms) units round-robin: the 32
+// lanes split the slice's terms, each lane forms F A_a(|f|) (a cos 2 pi f.p -
+// b sin 2 pi f.p) in amplitude-phase form, A_a(|f|) F amp cos 2 pi (f.p + psi)
+// (one cosine; amp and psi as in the fused synthesis kernel), with the
+// double-float phase (aperture centres lie up to hundreds of metres from the
+// origin), and a warp-shuffle reduction gives the slice's partial piston.
+// Partials are folded in a fixed order (deterministic sums), then the pair
+// differences are written.
+//
+// The Eq. 7 filter g(pi D |f|) of each (aperture, term):
+//   - if every aperture of the job has the same (D, d), once per term, into
+//     the term's amplitude (the units then evaluate no filter);
+//   - else per unit, in the cheapest form valid over the unit's range of
+//     x = pi D |f|: a chunk's terms are ordered by |f| bucket and the
+//     apertures by D, so a unit covers a limited range of x, and its bounds
+//     pick a Taylor series of 5 or 11 terms (x below 0.5, 4) or a
+//     large-argument form of degree 1 or 4 (x from 16, 4 on); only a unit
+//     whose range straddles x = 4 tests each term.  (More forms, e.g. 7-term
+//     series below x = 1.5 and degree 2 from x = 8, were timed slower: the
+//     kernel's code outgrows the instruction cache.)
 //
 // Scheduling: a single job runs as a grid-stride over its realisations; a
 // batch of jobs (QRS_PISTON_PERSISTENT) runs as one persistent grid whose
@@ -26,13 +39,7 @@ constexpr int kPisChunk = 2048;  // terms per shared-memory chunk
 constexpr int kPisBuckets = 64;  // |f| buckets of the per-chunk counting sort (8 per octave)
 constexpr int kPisSortMinAp = 8; // items with at least this many apertures sort their chunks
 constexpr int kPisMaxWarps = 8;
-#ifndef QRS_PISTON_GROUP
-#define QRS_PISTON_GROUP 4
-#endif
-constexpr int kPisGroup = QRS_PISTON_GROUP;  // apertures sharing one pass over a slice's terms
-#ifndef QRS_PISTON_PAIRED
-#define QRS_PISTON_PAIRED 1  // 1: the group's apertures in pairs through paired FP32 instructions
-#endif
+constexpr int kPisGroup = 4;     // apertures sharing one pass over a slice's terms (two pairs)
 
 // Kernel shapes the autotuner chooses from: threads per CTA and terms per
 // (aperture, slice) unit.
@@ -47,21 +54,51 @@ struct PisShape {
 template <int SLICES>
 struct PisShared {
     float4 rec[kPisChunk];             // fx, fy, F amp, psi (turns, [0, 0.5))
-    float fabs_[kPisChunk];            // |f|
+    float pif[kPisChunk];              // pi |f|
     uint16_t sidx[kPisChunk];          // terms in bucket order (sorted chunks)
     int bcount[kPisMaxWarps][kPisBuckets];
     float part[kPisMaxAp][SLICES];     // per-slice partial pistons of the chunk
     float total[kPisMaxAp];
     float apx[kPisMaxAp], apy[kPisMaxAp], apD[kPisMaxAp], apd[kPisMaxAp];
     float apwD[kPisMaxAp], apwd[kPisMaxAp];  // D^2 / (D^2 - d^2), d^2 / (D^2 - d^2)
+    uint8_t rank[kPisMaxAp];           // the job's aperture a sits in slot rank[a] (slots in order of D)
 };
 
-// Bucket of |f| for the chunk sort: the float's exponent and top three
-// mantissa bits (8 buckets per octave), the top bucket holding fmax, the
-// lowest collecting everything 8 octaves or more below it.
-__device__ __forceinline__ int pis_bucket(float fa, int base)
+// The filter form a unit of unobstructed apertures takes (valid where every
+// x = pi D |f| of the unit lies): Taylor series in x^2 through x^8 or x^20
+// (x < 0.5, 4), the large-argument form of degree 1 or 4 in 1/x^2 (x >= 16,
+// 4), or a per-term choice between the 11-term series and degree 4.
+enum { kFltSer4, kFltSer10, kFltLrg1, kFltLrg4, kFltMixed };
+
+__device__ __forceinline__ int filter_form(float x_lo, float x_hi)
 {
-    const int e = (int)(__float_as_uint(fa) >> 20) - base;
+    if (x_hi < 4.0f) return x_hi < 0.5f ? kFltSer4 : kFltSer10;
+    if (x_lo >= 4.0f) return x_lo >= 16.0f ? kFltLrg1 : kFltLrg4;
+    return kFltMixed;
+}
+
+// The filter of two apertures (D, D^2 pairs) at one term (pi |f| and its square).
+template <int FORM>
+__device__ __forceinline__ float2 filter2(float pf, float pf2, float2 D, float2 DD)
+{
+    if constexpr (FORM == kFltSer4) return airy_series_v2<4>(__fmul2_rn(make_float2(pf2, pf2), DD));
+    else if constexpr (FORM == kFltSer10) return airy_series_v2<10>(__fmul2_rn(make_float2(pf2, pf2), DD));
+    else if constexpr (FORM == kFltLrg1) return airy_large2<1>(__fmul2_rn(make_float2(pf, pf), D));
+    else if constexpr (FORM == kFltLrg4) return airy_large2<4>(__fmul2_rn(make_float2(pf, pf), D));
+    else {
+        const float2 x = __fmul2_rn(make_float2(pf, pf), D);
+        if (x.x < 4.0f && x.y < 4.0f) return airy_series_v2<10>(__fmul2_rn(x, x));
+        if (x.x >= 4.0f && x.y >= 4.0f) return airy_large2<4>(x);
+        return make_float2(airy_g(x.x), airy_g(x.y));
+    }
+}
+
+// Bucket of pi |f| for the chunk sort: the float's exponent and top three
+// mantissa bits (8 buckets per octave), the top bucket holding pi fmax, the
+// lowest collecting everything 8 octaves or more below it.
+__device__ __forceinline__ int pis_bucket(float v, int base)
+{
+    const int e = (int)(__float_as_uint(v) >> 20) - base;
     return e < 0 ? 0 : (e >= kPisBuckets ? kPisBuckets - 1 : e);
 }
 
@@ -72,10 +109,10 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-// One (aperture, slice) unit: the lanes split the slice's terms [k0, k_end)
-// (in bucket order through sidx when SORTED); the filter's obstruction term
-// only when OBST.  Both are uniform per unit, so they select a loop instead
-// of being tested per term.
+// One (aperture, slice) unit, aperture by aperture: the lanes split the
+// slice's terms [k0, k_end) (in bucket order through sidx when SORTED); the
+// filter's obstruction term only when OBST.  Both are uniform per unit, so
+// they select a loop instead of being tested per term.
 template <bool SORTED, bool OBST, int SLICES>
 __device__ __forceinline__ float unit_sum(const PisShared<SLICES>& sh, int k0, int k_end, float x, float y, float D,
                                           float d, float wD, float wd)
@@ -84,61 +121,42 @@ __device__ __forceinline__ float unit_sum(const PisShared<SLICES>& sh, int k0, i
     for (int k = k0; k < k_end; k += 32) {
         const int j = SORTED ? (int)sh.sidx[k] : k;
         const float4 T = sh.rec[j];
-        const float fa = sh.fabs_[j];
-        const float A = OBST ? airy_filter_w(fa, D, d, wD, wd) : airy_g(3.14159265358979f * fa * D);
+        const float pf = sh.pif[j];
+        const float A = OBST ? fmaf(wD, airy_g(pf * D), -wd * airy_g(pf * d)) : airy_g(pf * D);
         acc = fmaf(A * T.z, __cosf(phase_df_psi(T.x, T.y, x, y, T.w) * 6.28318530717958648f), acc);
     }
     return acc;
 }
 
-// NA unobstructed apertures per unit: one pass over the terms, the record,
-// |f| and index loads and the loop control shared, NA independent chains.
-template <bool SORTED, int NA, int SLICES>
-__device__ __forceinline__ void unit_sum_n(const PisShared<SLICES>& sh, int k0, int k_end, int a0, float (&acc)[NA])
+// kPisGroup unobstructed apertures (slots a0 ..) per unit: one pass over the
+// terms, the record, pi |f| and index loads and the loop control shared, two
+// pairs of apertures through paired FP32 instructions (FFMA2 / FMUL2 /
+// FADD2, each element rounded as the scalar instruction); the filter in
+// the form FORM.
+template <int FORM, bool SORTED, int SLICES>
+__device__ __forceinline__ void unit_sum_group(const PisShared<SLICES>& sh, int k0, int k_end, int a0,
+                                               float (&acc)[kPisGroup])
 {
-    float x[NA], y[NA], D[NA];
-#pragma unroll
-    for (int i = 0; i < NA; ++i) {
-        x[i] = sh.apx[a0 + i];
-        y[i] = sh.apy[a0 + i];
-        D[i] = sh.apD[a0 + i];
-        acc[i] = 0.0f;
-    }
-#if QRS_PISTON_PAIRED
-    // apertures in pairs: one paired FP32 instruction (FFMA2 / FMUL2 / FADD2)
-    // does both apertures' step, rounded as the scalar one
-    static_assert(NA % 2 == 0, "apertures in pairs");
-    constexpr int NP = NA / 2;
-    float2 x2[NP], y2[NP], D2[NP], acc2[NP];
+    constexpr int NP = kPisGroup / 2;
+    float2 x2[NP], y2[NP], D2[NP], DD2[NP], acc2[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-        x2[q] = make_float2(x[2 * q], x[2 * q + 1]);
-        y2[q] = make_float2(y[2 * q], y[2 * q + 1]);
-        D2[q] = make_float2(D[2 * q], D[2 * q + 1]);
+        x2[q] = make_float2(sh.apx[a0 + 2 * q], sh.apx[a0 + 2 * q + 1]);
+        y2[q] = make_float2(sh.apy[a0 + 2 * q], sh.apy[a0 + 2 * q + 1]);
+        D2[q] = make_float2(sh.apD[a0 + 2 * q], sh.apD[a0 + 2 * q + 1]);
+        DD2[q] = __fmul2_rn(D2[q], D2[q]);
         acc2[q] = make_float2(0.0f, 0.0f);
     }
     const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
-    const float2 quarter = make_float2(0.25f, 0.25f);
     for (int k = k0; k < k_end; k += 32) {
         const int j = SORTED ? (int)sh.sidx[k] : k;
         const float4 T = sh.rec[j];
-        const float piF = 3.14159265358979f * sh.fabs_[j];
-        const float2 PF = make_float2(piF, piF), Tz = make_float2(T.z, T.z);
+        const float pf = sh.pif[j];
+        const float pf2 = (FORM <= kFltSer10) ? pf * pf : 0.0f;
+        const float2 Tz = make_float2(T.z, T.z);
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            const float2 xx = __fmul2_rn(PF, D2[q]);
-            float2 A;
-            if (xx.x < 4.0f && xx.y < 4.0f) {  // both on the series branch of airy_g
-                constexpr AiryCoef K;
-                const float2 u = __fmul2_rn(__fmul2_rn(quarter, xx), xx);
-                A = make_float2(K.c[10], K.c[10]);
-#pragma unroll
-                for (int m = 9; m >= 0; --m) A = __ffma2_rn(A, u, make_float2(K.c[m], K.c[m]));
-            } else if (xx.x >= 4.0f && xx.y >= 4.0f) {  // both on the large-argument branch
-                A = airy_g_large2(xx);
-            } else {
-                A = make_float2(airy_g(xx.x), airy_g(xx.y));
-            }
+            const float2 A = filter2<FORM>(pf, pf2, D2[q], DD2[q]);
             const float2 ang = __fmul2_rn(phase_df2_psi(T.x, T.y, x2[q], y2[q], T.w), two_pi);
             const float2 c = make_float2(__cosf(ang.x), __cosf(ang.y));
             acc2[q] = __ffma2_rn(__fmul2_rn(A, Tz), c, acc2[q]);
@@ -149,18 +167,65 @@ __device__ __forceinline__ void unit_sum_n(const PisShared<SLICES>& sh, int k0, 
         acc[2 * q] = acc2[q].x;
         acc[2 * q + 1] = acc2[q].y;
     }
-#else
-    for (int k = k0; k < k_end; k += 32) {
-        const int j = SORTED ? (int)sh.sidx[k] : k;
-        const float4 T = sh.rec[j];
-        const float piF = 3.14159265358979f * sh.fabs_[j];
+}
+
+// Sorted chunks: the unit's form.  (Unsorted chunks, of items with few
+// apertures, run the per-term choice: their units span the whole |f| range.)
+template <int SLICES>
+__device__ __forceinline__ void unit_sum_group_form(int form, const PisShared<SLICES>& sh, int k0, int k_end, int a0,
+                                                    float (&acc)[kPisGroup])
+{
+    switch (form) {
+    case kFltSer4: unit_sum_group<kFltSer4, true>(sh, k0, k_end, a0, acc); break;
+    case kFltSer10: unit_sum_group<kFltSer10, true>(sh, k0, k_end, a0, acc); break;
+    case kFltLrg1: unit_sum_group<kFltLrg1, true>(sh, k0, k_end, a0, acc); break;
+    case kFltLrg4: unit_sum_group<kFltLrg4, true>(sh, k0, k_end, a0, acc); break;
+    default: unit_sum_group<kFltMixed, true>(sh, k0, k_end, a0, acc); break;
+    }
+}
+
+// NA apertures per unit when the Eq. 7 filter is already in the term records
+// (every aperture of the job has the same D and d): the phase, one cosine and
+// the accumulation per (aperture, term), pairs of apertures in paired FP32
+// instructions.  NA even, or 1 for a lone aperture.
+template <int NA, int SLICES>
+__device__ __forceinline__ void unit_sum_prefiltered(const PisShared<SLICES>& sh, int k0, int k_end, int a0,
+                                                     float (&acc)[NA])
+{
+    if constexpr (NA == 1) {
+        const float x = sh.apx[a0], y = sh.apy[a0];
+        float s = 0.0f;
+        for (int k = k0; k < k_end; k += 32) {
+            const float4 T = sh.rec[k];
+            s = fmaf(T.z, __cosf(phase_df_psi(T.x, T.y, x, y, T.w) * 6.28318530717958648f), s);
+        }
+        acc[0] = s;
+    } else {
+        static_assert(NA % 2 == 0, "apertures in pairs");
+        constexpr int NP = NA / 2;
+        float2 x2[NP], y2[NP], acc2[NP];
 #pragma unroll
-        for (int i = 0; i < NA; ++i) {
-            const float A = airy_g(piF * D[i]);
-            acc[i] = fmaf(A * T.z, __cosf(phase_df_psi(T.x, T.y, x[i], y[i], T.w) * 6.28318530717958648f), acc[i]);
+        for (int q = 0; q < NP; ++q) {
+            x2[q] = make_float2(sh.apx[a0 + 2 * q], sh.apx[a0 + 2 * q + 1]);
+            y2[q] = make_float2(sh.apy[a0 + 2 * q], sh.apy[a0 + 2 * q + 1]);
+            acc2[q] = make_float2(0.0f, 0.0f);
+        }
+        const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
+        for (int k = k0; k < k_end; k += 32) {
+            const float4 T = sh.rec[k];
+            const float2 Tz = make_float2(T.z, T.z);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const float2 ang = __fmul2_rn(phase_df2_psi(T.x, T.y, x2[q], y2[q], T.w), two_pi);
+                acc2[q] = __ffma2_rn(Tz, make_float2(__cosf(ang.x), __cosf(ang.y)), acc2[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            acc[2 * q] = acc2[q].x;
+            acc[2 * q + 1] = acc2[q].y;
         }
     }
-#endif
 }
 
 template <class S>
@@ -169,16 +234,62 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
     constexpr int kPisTPB = S::kTPB, kPisWarps = S::kWarps, kPisSlice = S::kSlice;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_ap = J.n_ap;
+    // The apertures take slots in order of D (ties by index): a group of
+    // apertures that share a pass over the terms then has close diameters,
+    // so that its range of pi D |f| is narrow.  Each aperture's sum is formed
+    // the same way in any slot.  The slots are ranked in shared memory: the
+    // diameters first, then every aperture's rank against them.
+    // When every aperture has the same (D, d), the Eq. 7 filter is a function
+    // of the term alone: it is taken once per term into the record's
+    // amplitude, and the units evaluate no filter (and need no |f| order).
+    const float D0 = J.ap_D[0], d0 = J.ap_d ? J.ap_d[0] : 0.0f;
+    bool same = true;
     for (int a = tid; a < n_ap; a += kPisTPB) {
-        const float2 c = J.ap_xy[a];
-        sh.apx[a] = c.x; sh.apy[a] = c.y;
         const float D = J.ap_D[a], d = J.ap_d ? J.ap_d[a] : 0.0f;
-        sh.apD[a] = D;
-        sh.apd[a] = d;
-        sh.apwD[a] = d > 0.0f ? (D * D) / (D * D - d * d) : 1.0f;
-        sh.apwd[a] = d > 0.0f ? (d * d) / (D * D - d * d) : 0.0f;
-        sh.total[a] = 0.0f;
+        sh.apwD[a] = D;  // staging: the diameters in job order
+        same = same && D == D0 && d == d0;
     }
+    const bool prefilter = __syncthreads_and(same) != 0;
+    // order key: the float's bits mapped to an unsigned total order (any bit
+    // pattern, NaN included, gets a distinct slot: the slots are a permutation)
+    auto key = [](float v) {
+        const uint32_t u = __float_as_uint(v);
+        return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    };
+    int my_slot[(kPisMaxAp + kPisTPB - 1) / kPisTPB];
+#pragma unroll
+    for (int i = 0; i < (kPisMaxAp + kPisTPB - 1) / kPisTPB; ++i) {
+        const int a = tid + i * kPisTPB;
+        my_slot[i] = 0;
+        if (a < n_ap) {
+            const uint32_t ka = key(sh.apwD[a]);
+            int s = 0;
+            for (int b = 0; b < n_ap; ++b) {
+                const uint32_t kb = key(sh.apwD[b]);
+                s += (kb < ka || (kb == ka && b < a)) ? 1 : 0;
+            }
+            my_slot[i] = s;
+        }
+    }
+    __syncthreads();  // the staged diameters are read; the slots may be written
+#pragma unroll
+    for (int i = 0; i < (kPisMaxAp + kPisTPB - 1) / kPisTPB; ++i) {
+        const int a = tid + i * kPisTPB;
+        if (a < n_ap) {
+            const int s = my_slot[i];
+            const float D = J.ap_D[a], d = J.ap_d ? J.ap_d[a] : 0.0f;
+            const float2 c = J.ap_xy[a];
+            sh.rank[a] = (uint8_t)s;
+            sh.apx[s] = c.x; sh.apy[s] = c.y;
+            sh.apD[s] = D;
+            sh.apd[s] = d;
+            sh.apwD[s] = d > 0.0f ? (D * D) / (D * D - d * d) : 1.0f;
+            sh.apwd[s] = d > 0.0f ? (d * d) / (D * D - d * d) : 0.0f;
+            sh.total[s] = 0.0f;
+        }
+    }
+    const float wD0 = d0 > 0.0f ? (D0 * D0) / (D0 * D0 - d0 * d0) : 1.0f;
+    const float wd0 = d0 > 0.0f ? (d0 * d0) / (D0 * D0 - d0 * d0) : 0.0f;
     const DrawParams& p = J.p;
     const uint64_t nr0 = (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f;
     for (int64_t k_begin = 0; k_begin < p.n_f; k_begin += kPisChunk) {
@@ -188,29 +299,31 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             const uint64_t n = nr0 + (uint64_t)(k_begin + q);
             Words w;
             const Term t = draw_term<false, false>(p, n, k_begin + q, &w);
-            float amp;
+            float Fa;
             uint32_t u;
-            coef_polar_from_words(p, n, w, amp, u);
-            sh.rec[q] = make_float4(t.fx, t.fy, t.F * amp, (float)u * 0x1p-24f);
-            sh.fabs_[q] = sqrtf(t.fx * t.fx + t.fy * t.fy);
+            term_amp_polar(p, n, w, t.var, t.F, Fa, u);
+            const float fa = fast_abs_f(t.fx * t.fx + t.fy * t.fy);
+            if (prefilter) Fa = airy_filter_w(fa, D0, d0, wD0, wd0) * Fa;
+            sh.rec[q] = make_float4(t.fx, t.fy, Fa, (float)u * 0x1p-24f);
+            sh.pif[q] = 3.14159265358979f * fa;
         }
         __syncthreads();
-        // Terms in order of |f| bucket: a warp's lanes then share the Eq. 7
-        // filter's branch (x = pi D |f| below or above 4) instead of paying
-        // both, consecutive R2 terms having unrelated |f|.  Stable counting
-        // sort: per-warp bucket counts (match_any, no atomics), offsets
-        // bucket-major then warp, then ranks -- a deterministic order.
-        const bool sorted = n_ap >= kPisSortMinAp;
+        // Terms in order of |f| bucket: a warp's lanes then take the same
+        // filter form, and a slice covers a narrow range of |f|, consecutive
+        // R2 terms having unrelated |f|.  Stable counting sort: per-warp
+        // bucket counts (match_any, no atomics), offsets bucket-major then
+        // warp, then ranks -- a deterministic order.
+        const bool sorted = !prefilter && n_ap >= kPisSortMinAp;
         if (sorted) {
             static_assert(kPisWarps <= kPisMaxWarps, "bucket counters per warp");
-            const int base = (int)(__float_as_uint((float)p.fmax) >> 20) - (kPisBuckets - 1);
+            const int base = (int)(__float_as_uint(3.14159265358979f * (float)p.fmax) >> 20) - (kPisBuckets - 1);
             const int per_warp = (len + kPisTPB - 1) / kPisTPB * 32;  // items per warp, a multiple of 32
             const int q_begin = warp * per_warp, q_end = q_begin + per_warp;
             for (int b = lane; b < kPisBuckets; b += 32) sh.bcount[warp][b] = 0;
             __syncwarp();
             for (int q0 = q_begin; q0 < q_end; q0 += 32) {
                 const int q = q0 + lane;
-                const int b = q < len ? pis_bucket(sh.fabs_[q], base) : kPisBuckets;
+                const int b = q < len ? pis_bucket(sh.pif[q], base) : kPisBuckets;
                 const unsigned peers = __match_any_sync(0xffffffffu, b);
                 if (b < kPisBuckets && lane == __ffs(peers) - 1) sh.bcount[warp][b] += __popc(peers);
                 __syncwarp();
@@ -243,7 +356,7 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             __syncthreads();
             for (int q0 = q_begin; q0 < q_end; q0 += 32) {
                 const int q = q0 + lane;
-                const int b = q < len ? pis_bucket(sh.fabs_[q], base) : kPisBuckets;
+                const int b = q < len ? pis_bucket(sh.pif[q], base) : kPisBuckets;
                 const unsigned peers = __match_any_sync(0xffffffffu, b);
                 if (b < kPisBuckets) sh.sidx[sh.bcount[warp][b] + __popc(peers & ((1u << lane) - 1u))] = (uint16_t)q;
                 __syncwarp();
@@ -260,12 +373,52 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             const int q = u / n_sl, sl = u - q * n_sl;
             const int a0 = kPisGroup * q, a1 = a0 + kPisGroup - 1;
             const int k0 = sl * kPisSlice + lane, k_end = min(len, (sl + 1) * kPisSlice);
+            if (prefilter) {
+                if (a1 < n_ap) {
+                    float acc[kPisGroup];
+                    unit_sum_prefiltered<kPisGroup>(sh, k0, k_end, a0, acc);
+#pragma unroll
+                    for (int i = 0; i < kPisGroup; ++i) {
+                        const float v = warp_sum_f(acc[i]);
+                        if (lane == 0) sh.part[a0 + i][sl] = v;
+                    }
+                } else {
+                    for (int a = a0; a < n_ap; ++a) {
+                        float acc[1];
+                        unit_sum_prefiltered<1>(sh, k0, k_end, a, acc);
+                        const float v = warp_sum_f(acc[0]);
+                        if (lane == 0) sh.part[a][sl] = v;
+                    }
+                }
+                continue;
+            }
             bool plain = a1 < n_ap;
             for (int a = a0; plain && a <= a1; ++a) plain = sh.apd[a] <= 0.0f;
             if (plain) {
                 float acc[kPisGroup];
-                if (sorted) unit_sum_n<true>(sh, k0, k_end, a0, acc);
-                else unit_sum_n<false>(sh, k0, k_end, a0, acc);
+                if (sorted) {
+                    // The unit's filter arguments x = fl(pi |f| D) lie between
+                    // those of its smallest pi |f| and D and of its largest
+                    // (rounding is monotonic), so these bounds pick a form
+                    // valid for every term of the unit.
+                    float f_lo = 3.402823466e38f, f_hi = 0.0f;
+                    for (int k = k0; k < k_end; k += 32) {
+                        const float pf = sh.pif[sh.sidx[k]];
+                        f_lo = fminf(f_lo, pf);
+                        f_hi = fmaxf(f_hi, pf);
+                    }
+                    // pi |f| >= 0: the float bits order as the values
+                    f_lo = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(f_lo)));
+                    f_hi = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(f_hi)));
+                    float D_lo = sh.apD[a0], D_hi = D_lo;
+                    for (int a = a0 + 1; a <= a1; ++a) {
+                        D_lo = fminf(D_lo, sh.apD[a]);
+                        D_hi = fmaxf(D_hi, sh.apD[a]);
+                    }
+                    unit_sum_group_form(filter_form(f_lo * D_lo, f_hi * D_hi), sh, k0, k_end, a0, acc);
+                } else {
+                    unit_sum_group<kFltMixed, false>(sh, k0, k_end, a0, acc);
+                }
 #pragma unroll
                 for (int i = 0; i < kPisGroup; ++i) {
                     const float v = warp_sum_f(acc[i]);
@@ -297,13 +450,13 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
     }
     __syncthreads();
     if (J.piston)
-        for (int a = tid; a < n_ap; a += kPisTPB) J.piston[r * n_ap + a] = sh.total[a];
+        for (int a = tid; a < n_ap; a += kPisTPB) J.piston[r * n_ap + a] = sh.total[sh.rank[a]];
     if (J.delta)
         for (int q = tid; q < J.n_pairs; q += kPisTPB) {
             const int2 pr = J.pairs[q];
             float v = 0.0f;
             if (pr.x < 0 || pr.x >= n_ap || pr.y < 0 || pr.y >= n_ap) atomicExch(err, (int)QRS_ERR_DEVICE_CHECK);
-            else v = sh.total[pr.x] - sh.total[pr.y];
+            else v = sh.total[sh.rank[pr.x]] - sh.total[sh.rank[pr.y]];
             J.delta[r * J.n_pairs + q] = v;
         }
     __syncthreads();  // shared state reused by the next item

@@ -100,6 +100,7 @@ struct Term {
     float fx, fy;  // cycles/m (FP32)
     float F;       // sqrt(W J / N_f), times A(|f|) when the PSD is filtered
     float J;
+    float var;     // W J / N_f, the term's variance before the aperture filter
     float A;       // the aperture filter A(|f|) (1 without filter)
     float a, b;    // coefficients
     int32_t cell;
@@ -130,67 +131,123 @@ struct AiryCoef {
     }
 };
 
-// g(x) = 2 J1(x) / x.  Below x = 4: the Taylor series of J1 (11 terms, Horner
-// in x^2/4).  From x = 4: the large-argument form of Abramowitz & Stegun
-// (1964) eq. 9.4.6, x^(1/2) J1(x) = f1(3/x) cos(theta1), theta1 = x - 3 pi/4
-// + t1(3/x), degree-6 polynomials with |error| < 4e-8 (f1) and 9e-8 (theta1);
-// the cosine is taken in turns, x / (2 pi) - 3/8 + t1 / (2 pi) reduced mod 1,
-// so arguments in the hundreds keep their accuracy.  Both branches are short,
-// so warps whose lanes straddle x = 4 stay cheap.
-__device__ __forceinline__ float airy_g_large(float x);
+// Taylor coefficients of g in v = x^2 through v^M: c_m 4^-m (the series in
+// u = x^2/4 with the power of two folded in, which rounds every Horner step
+// exactly as the series in u does).  The first omitted term is below 1.1e-11
+// for M = 4 at x <= 0.5, 8.9e-11 for M = 6 at x <= 1.5, 3e-10 for M = 10 at
+// x <= 4.
+template <int M>
+struct AirySeriesK {
+    float c[M + 1];
+    constexpr AirySeriesK() : c()
+    {
+        constexpr AiryCoef K;
+        float s = 1.0f;
+        for (int m = 0; m <= M; ++m) {
+            c[m] = K.c[m] * s;
+            s *= 0.25f;
+        }
+    }
+};
+
+template <int M>
+__device__ __forceinline__ float airy_series_v(float v)
+{
+    constexpr AirySeriesK<M> K;
+    float s = K.c[M];
+#pragma unroll
+    for (int m = M - 1; m >= 0; --m) s = fmaf(s, v, K.c[m]);
+    return s;
+}
+
+template <int M>
+__device__ __forceinline__ float2 airy_series_v2(float2 v)
+{
+    constexpr AirySeriesK<M> K;
+    float2 s = make_float2(K.c[M], K.c[M]);
+#pragma unroll
+    for (int m = M - 1; m >= 0; --m) s = __ffma2_rn(s, v, make_float2(K.c[m], K.c[m]));
+    return s;
+}
+
+// The large-argument form from x0 on: J1 in modulus-phase form,
+//   g(x) = A(w) x^(-3/2) cos(2 pi [x / (2 pi) - 3/8 + u P(w)]),  u = 1/x, w = u^2,
+// with A = 2 sqrt(2/pi) M and P = T / (2 pi) polynomials in w fitted to the
+// modulus M and phase correction T of J1 + i Y1 (csrc/airy_fit.py, FP64
+// reference values); largest error of g with these FP32 coefficients, in
+// FP64: 1.5e-8 (x0 = 4, degree 4), 9.2e-9 (x0 = 8, degree 2), 1.3e-8
+// (x0 = 16, degree 1).  The cosine is taken in turns reduced to [-1/2, 1/2],
+// so arguments in the hundreds keep their accuracy; x^(-1/2) comes from one
+// reciprocal square root and 1/x = its square.
+template <int DEG>
+struct AiryLargeK;
+template <>
+struct AiryLargeK<4> {
+    float a[5] = {1.595769125e+00f, 2.991877180e-01f, -3.046086143e-01f, 1.014835449e+00f, -3.288978495e+00f};
+    float p[5] = {5.968310219e-02f, -2.610418597e-02f, 5.752221473e-02f, -2.702766955e-01f, 1.007727345e+00f};
+};
+template <>
+struct AiryLargeK<2> {
+    float a[3] = {1.595769132e+00f, 2.991233879e-01f, -2.871321887e-01f};
+    float p[3] = {5.968310043e-02f, -2.608808403e-02f, 5.298583715e-02f};
+};
+template <>
+struct AiryLargeK<1> {
+    float a[2] = {1.595769185e+00f, 2.983803074e-01f};
+    float p[2] = {5.968309142e-02f, -2.595410740e-02f};
+};
+
+template <int DEG>
+__device__ __forceinline__ float airy_large(float x)
+{
+    constexpr AiryLargeK<DEG> K;
+    const float rs = rsqrtf(x);
+    const float u = __fmul_rn(rs, rs), w = __fmul_rn(u, u), s = __fmul_rn(u, rs);
+    float a = K.a[DEG], p = K.p[DEG];
+#pragma unroll
+    for (int i = DEG - 1; i >= 0; --i) {
+        a = __fmaf_rn(a, w, K.a[i]);
+        p = __fmaf_rn(p, w, K.p[i]);
+    }
+    const float turns = __fmaf_rn(x, 0.159154943091895f, __fmaf_rn(u, p, -0.375f));
+    const float r = __fsub_rn(__fadd_rn(turns, 12582912.0f), 12582912.0f);  // rint (|turns| < 2^22)
+    const float c = __cosf(__fmul_rn(__fsub_rn(turns, r), 6.28318530717958648f));
+    return __fmul_rn(__fmul_rn(a, s), c);
+}
+
+// airy_large of two arguments in paired FP32 instructions, each element
+// rounded exactly as in airy_large.
+template <int DEG>
+__device__ __forceinline__ float2 airy_large2(float2 x)
+{
+    constexpr AiryLargeK<DEG> K;
+    auto C = [](float c) { return make_float2(c, c); };
+    const float2 rs = make_float2(rsqrtf(x.x), rsqrtf(x.y));
+    const float2 u = __fmul2_rn(rs, rs), w = __fmul2_rn(u, u), s = __fmul2_rn(u, rs);
+    float2 a = C(K.a[DEG]), p = C(K.p[DEG]);
+#pragma unroll
+    for (int i = DEG - 1; i >= 0; --i) {
+        a = __ffma2_rn(a, w, C(K.a[i]));
+        p = __ffma2_rn(p, w, C(K.p[i]));
+    }
+    const float2 turns = __ffma2_rn(x, C(0.159154943091895f), __ffma2_rn(u, p, C(-0.375f)));
+    const float2 r = __fadd2_rn(__fadd2_rn(turns, C(12582912.0f)), C(-12582912.0f));
+    const float2 ang = __fmul2_rn(__ffma2_rn(r, C(-1.0f), turns), C(6.28318530717958648f));
+    return __fmul2_rn(__fmul2_rn(a, s), make_float2(__cosf(ang.x), __cosf(ang.y)));
+}
+
+// g(x) = 2 J1(x) / x: below x = 4 its Taylor series (11 terms), from x = 4 on
+// the degree-4 large-argument form.  Absolute error near 2e-7 (FP32
+// evaluation of the series near x = 4), below 1e-7 beyond.
+__device__ __forceinline__ float airy_g_large(float x) { return airy_large<4>(x); }
 
 __device__ __forceinline__ float airy_g(float x)
 {
-    if (x < 4.0f) {
-        constexpr AiryCoef K;
-        const float u = 0.25f * x * x;
-        float s = K.c[10];
-#pragma unroll
-        for (int m = 9; m >= 0; --m) s = fmaf(s, u, K.c[m]);
-        return s;
-    }
+    if (x < 4.0f) return airy_series_v<10>(__fmul_rn(x, x));
     return airy_g_large(x);
 }
 
-// The large-argument branch of airy_g (x >= 4).
-__device__ __forceinline__ float airy_g_large(float x)
-{
-    const float z = __fdividef(3.0f, x);
-    const float f1 = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(-0.00020033f, z, 0.00113653f), z, -0.00249511f), z, 0.00017105f), z,
-                                    0.01659667f), z, 0.00000156f), z, 0.79788456f);
-    const float t1 = z * fmaf(fmaf(fmaf(fmaf(fmaf(-0.00029166f, z, 0.00079824f), z, 0.00074348f), z, -0.00637879f), z,
-                                   0.00005650f), z, 0.12499612f);
-    float turns = fmaf(x, 0.159154943091895f, fmaf(t1, 0.159154943091895f, -0.375f));
-    turns -= rintf(turns);
-    const float j1 = f1 * __cosf(turns * 6.28318530717958648f) * rsqrtf(x);
-    return __fdividef(2.0f * j1, x);
-}
-
-// airy_g_large of two arguments, the polynomial and product steps in paired
-// FP32 instructions; each element is rounded exactly as in airy_g_large.
-__device__ __forceinline__ float2 airy_g_large2(float2 x)
-{
-    auto C = [](float c) { return make_float2(c, c); };
-    const float2 z = make_float2(__fdividef(3.0f, x.x), __fdividef(3.0f, x.y));
-    const float2 f1 = __ffma2_rn(
-        __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(C(-0.00020033f), z, C(0.00113653f)), z, C(-0.00249511f)), z,
-                                         C(0.00017105f)),
-                              z, C(0.01659667f)),
-                   z, C(0.00000156f)),
-        z, C(0.79788456f));
-    const float2 t1 = __fmul2_rn(
-        z, __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(C(-0.00029166f), z, C(0.00079824f)), z, C(0.00074348f)), z,
-                                            C(-0.00637879f)),
-                                 z, C(0.00005650f)),
-                      z, C(0.12499612f)));
-    float2 turns = __ffma2_rn(x, C(0.159154943091895f), __ffma2_rn(t1, C(0.159154943091895f), C(-0.375f)));
-    turns = __ffma2_rn(make_float2(rintf(turns.x), rintf(turns.y)), C(-1.0f), turns);  // turns - rint(turns)
-    const float2 a = __fmul2_rn(turns, C(6.28318530717958648f));
-    const float2 j1 = __fmul2_rn(__fmul2_rn(f1, make_float2(__cosf(a.x), __cosf(a.y))),
-                                 make_float2(rsqrtf(x.x), rsqrtf(x.y)));
-    const float2 tj = __fmul2_rn(C(2.0f), j1);
-    return make_float2(__fdividef(tj.x, x.x), __fdividef(tj.y, x.y));
-}
+__device__ __forceinline__ float2 airy_g_large2(float2 x) { return airy_large2<4>(x); }
 
 // Eq. 7 aperture filter A(f) = 2 (D J1(pi D f) - d J1(pi d f)) / (pi (D^2 - d^2) f)
 //                            = (D^2 g(pi D f) - d^2 g(pi d f)) / (D^2 - d^2),  A(0) = 1.
@@ -295,7 +352,16 @@ __device__ __forceinline__ DF df_mul(DF a, DF b)
     e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
     return df_fast_two_sum(p, e);
 }
-__device__ __forceinline__ DF df_scale(DF a, int k) { return DF{ldexpf(a.hi, k), ldexpf(a.lo, k)}; }
+// a 2^k, exactly: one multiply by the power of two built from its exponent
+// field where 2^k and the scaled low part stay normal, ldexpf otherwise.
+__device__ __forceinline__ DF df_scale(DF a, int k)
+{
+    if (k >= -100 && k <= 100) {
+        const float s = __int_as_float((k + 127) << 23);
+        return DF{__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)};
+    }
+    return DF{ldexpf(a.hi, k), ldexpf(a.lo, k)};
+}
 
 // Compile-time tables in double, split into (hi, lo) floats:
 //   e2[j] = 2^(j/64), j < 64;  sc[j] = (sin, cos)(2 pi j / 256), j < 256,
@@ -486,6 +552,31 @@ __device__ __forceinline__ void coef_polar_from_words(const DrawParams& p, uint6
     }
 }
 
+// F amp of coef_polar_from_words for an unfiltered term, as one square root:
+// GAUSS amp = sqrt(-2 ln U1) (sign from the top bit of u), so F amp =
+// +-sqrt(var (-2 ln U1)), within an FP32 rounding of F amp; the literal Eq. 3
+// form takes F amp itself.  u as in coef_polar_from_words.
+__device__ __forceinline__ void term_amp_polar(const DrawParams& p, uint64_t n, const Words& w, float var, float F,
+                                               float& Fa, uint32_t& u)
+{
+    if (p.coef == kCoefEq3) {
+        float amp;
+        coef_polar_from_words(p, n, w, amp, u);
+        Fa = F * amp;
+        return;
+    }
+    const float U1 = (float)((w.w2 >> 8) + 1u) * 0x1p-24f;
+    Fa = sqrtf(var * (-2.0f * logf(U1)));
+    u = w.w3 >> 8;
+    if (u & 0x800000u) {
+        Fa = -Fa;
+        u &= 0x7FFFFFu;
+    }
+}
+
+// |f| from |f|^2 by one reciprocal square root (within 2 FP32 ulp; 0 at 0).
+__device__ __forceinline__ float fast_abs_f(float f2) { return f2 > 0.0f ? f2 * rsqrtf(f2) : 0.0f; }
+
 // Coefficients of stream point n alone (no placement, no FP64).
 __device__ __forceinline__ float2 draw_coef(const DrawParams& p, uint64_t n)
 {
@@ -608,7 +699,8 @@ __device__ __forceinline__ Term draw_term(const DrawParams& p, uint64_t n, int64
     else J = p.jac_c * f2 / ((float)(p.n_rho * p.n_theta) * p_cell);  // log-polar Jacobian / (cells x p_c)
     t.J = J;
     t.A = (p.ap_D > 0.0f) ? airy_filter_call(sqrtf(f2), p.ap_D, p.ap_d) : 1.0f;
-    t.F = sqrtf(psd_w(p.psd_c, p.psd_a, f2) * J * p.inv_nf) * t.A;
+    t.var = psd_w(p.psd_c, p.psd_a, f2) * J * p.inv_nf;
+    t.F = sqrtf(t.var) * t.A;
     if (COEF) {
         coef_from_words(p, n, w, t.a, t.b);
     } else {

@@ -229,6 +229,36 @@ def test_piston_annular_and_mixed_diameters(h):
 
 
 @pytest.mark.parametrize("flags", [0, qrs.PISTON_PERSISTENT | qrs.PISTON_GRAPH])
+def test_piston_equal_obstructed_apertures(h, flags):
+    """Apertures that all share D and d (unit telescopes, D = 8 m, d = 1.1 m):
+    the filter of Eq. 7 is taken once per term into its amplitude; 5
+    apertures (a group of four and a lone one) up to 150 m apart, per value
+    within 1e-5 of the value's piston sigma."""
+    rng = np.random.default_rng(8)
+    n_ap = 5
+    ap_xy = rng.uniform(-75, 75, size=(n_ap, 2)).astype(np.float32)
+    ap_D = np.full(n_ap, 8.0, np.float32)
+    ap_d = np.full(n_ap, 1.1, np.float32)
+    pairs = wl.all_pairs(n_ap)
+    p = oracle.params(seed=43, r0=0.1, L0=22.0, fmin=1e-3, fmax=10.0)
+    R, n_f, off = 6, 2048 + 300, 2
+    pis_ref, dlt_ref = oracle.diff_piston(p, n_f, R, ap_xy, ap_D, ap_d, pairs, real_offset=off)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    pis = torch.empty(R, n_ap, device="cuda")
+    dlt = torch.empty(R, pairs.shape[0], device="cuda")
+    job = qrs.piston_job(p, n_f, R, dev(ap_xy), dev(ap_D), dev(ap_d), dev(pairs), pis, dlt, real_offset=off)
+    qrs.qrs_diff_piston(h, [job], flags=flags)
+    qrs.qrs_sync(h)
+    from oracle import analytic as an
+    d = oracle.draw(p, n_f=n_f, n_real=R, real_offset=off)
+    f = np.hypot(d["f"][..., 0].astype(np.float64), d["f"][..., 1].astype(np.float64))
+    A = an.airy(f.ravel(), 8.0, 1.1).reshape(f.shape)
+    sig = np.sqrt(np.sum((d["F"] * A) ** 2, axis=1))
+    assert np.all(np.abs(pis.cpu().numpy() - pis_ref) <= TOL_FIELD * sig[:, None])
+    assert np.all(np.abs(dlt.cpu().numpy() - dlt_ref) <= TOL_FIELD * np.sqrt(2) * sig[:, None])
+
+
+@pytest.mark.parametrize("flags", [0, qrs.PISTON_PERSISTENT | qrs.PISTON_GRAPH])
 def test_piston_with_learned_cells(h, flags):
     """Pistons from importance draws in a baseline's frame folded over four
     mirrored sectors (the learned proposal's use): 9 apertures, so groups of
