@@ -76,9 +76,12 @@ def lib():
                                                  C.c_int, C.c_void_p, C.c_void_p]
             L.oracle_structure_fn.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
                                               C.c_void_p, C.c_int, C.c_void_p]
+            L.oracle_fft_spectrum.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int64,
+                                              C.c_double, C.c_uint64, C.c_int64, C.c_int64, C.c_void_p]
             L.oracle_nearest_neighbour.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
             L.oracle_star_discrepancy.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
-            for name in ("oracle_nearest_neighbour", "oracle_star_discrepancy", "oracle_draw", "oracle_synth_terms",
+            for name in ("oracle_fft_spectrum", "oracle_nearest_neighbour", "oracle_star_discrepancy", "oracle_draw",
+                         "oracle_synth_terms",
                          "oracle_synthesize",
                          "oracle_synthesize_shared", "oracle_diff_piston", "oracle_structure_fn"):
                 getattr(L, name).restype = C.c_int
@@ -262,3 +265,22 @@ def star_discrepancy(pts):
     out = np.zeros(pts.shape[0], np.float64)
     lib().oracle_star_discrepancy(_ptr(pts), pts.shape[0], pts.shape[1], _ptr(out))
     return out
+
+
+def fft_spectrum(p, n, dx, n_real, real_offset=0):
+    """The Eq. 2 spectrum on the FFT grid (see oracle_fft_spectrum): complex128 [n_real][n][n]."""
+    spec = np.zeros((n_real, n, n, 2), np.float64)
+    rc = lib().oracle_fft_spectrum(PSD[p["psd"]], float(p["r0"]), float(p.get("L0", 0.0) or 0.0),
+                                   float(p.get("ap_D", 0.0) or 0.0), float(p.get("ap_d", 0.0) or 0.0), int(n),
+                                   float(dx), int(p.get("seed", 0)) & (2**64 - 1), int(n_real), int(real_offset),
+                                   _ptr(spec))
+    assert rc == 0
+    return spec[..., 0] + 1j * spec[..., 1]
+
+
+def fft_screen(p, n, dx, n_real, real_offset=0):
+    """Eq. 2: n^2 times the inverse DFT of the spectrum, sum_f S(f) e^{2 pi i f.x} at
+    x = (j dx, i dx) (numpy, FP64); returns (real part, imaginary part), each [n_real][n][n]
+    (row i = y, column j = x)."""
+    chi = np.fft.ifft2(fft_spectrum(p, n, dx, n_real, real_offset), norm="forward")
+    return chi.real, chi.imag

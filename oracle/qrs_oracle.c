@@ -578,3 +578,42 @@ int oracle_star_discrepancy(const float* pts, int64_t n_sets, int64_t n, double*
     }
     return 0;
 }
+
+/* ------------------------------------------------- FFT screen (Eq. 2) ---
+ * The comparison method of Sec. 2.2: frequencies on the FFT grid of an n x n
+ * screen of pitch dx, f = (j', i') df with df = 1 / (n dx) and the signed
+ * index j' = j for j < (n + 1) / 2, j - n otherwise (the order of an FFT);
+ * the spectrum of realisation r is
+ *   S[r][i][j] = (a + i b) sqrt(W(f)) A(|f|) df,
+ * a, b ~ N(0,1) by Box-Muller from words 2 and 3 of counter
+ * ((real_offset + r) n^2 + i n + j, stream 4), A the Eq. 7 filter when
+ * ap_D > 0 (else 1), and S = 0 at f = 0 (the screen's mean, which no
+ * structure function sees).  The screen is n^2 times the inverse DFT of S
+ * (taken with numpy in oracle/__init__.py): sum_f S e^{2 pi i f.x}, whose
+ * real and imaginary parts are two screens.  spec [n_real][n][n][2]. */
+#define OR_STREAM_FFT 4u
+int oracle_fft_spectrum(int psd_kind, double r0, double L0, double ap_D, double ap_d, int64_t n, double dx,
+                        uint64_t seed, int64_t n_real, int64_t real_offset, double* spec)
+{
+    const double df = 1.0 / ((double)n * dx);
+    const int64_t half = (n + 1) / 2;
+    for (int64_t r = 0; r < n_real; ++r)
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = 0; j < n; ++j) {
+                double* s = spec + 2 * ((r * n + i) * n + j);
+                if (i == 0 && j == 0) { s[0] = 0.0; s[1] = 0.0; continue; }
+                const uint64_t idx = (uint64_t)(real_offset + r) * (uint64_t)(n * n) + (uint64_t)(i * n + j);
+                uint32_t w[4];
+                or_words(seed, idx, OR_STREAM_FFT, w);
+                double a, b;
+                or_box_muller(w[2], w[3], &a, &b);
+                const double fx = (double)(j < half ? j : j - n) * df;
+                const double fy = (double)(i < half ? i : i - n) * df;
+                const double f2 = fx * fx + fy * fy;
+                double F = sqrt(oracle_psd(psd_kind, r0, L0, f2)) * df;
+                if (ap_D > 0.0) F *= oracle_airy(sqrt(f2), ap_D, ap_d);
+                s[0] = a * F;
+                s[1] = b * F;
+            }
+    return 0;
+}
