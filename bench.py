@@ -653,6 +653,98 @@ def cpu_piston_plain(gpu_delta=None, per_core=1):
     return res
 
 
+def vk_phase_sf(r, r0, L0):
+    """The von Karman phase structure function on the whole frequency plane,
+    4 pi int f W(f) (1 - J0(2 pi f r)) df in closed form:
+    c' (L0/r0)^(5/3) [Gamma(5/6) / 2^(1/6) - x^(5/6) K_{5/6}(x)], x = 2 pi r / L0,
+    c' = 2^(1/6) Gamma(11/6) / pi^(8/3) (24/5 Gamma(6/5))^(5/6)."""
+    from scipy import special as sp
+    cp = 2 ** (1 / 6) * sp.gamma(11 / 6) / np.pi ** (8 / 3) * (24 / 5 * sp.gamma(6 / 5)) ** (5 / 6)
+    x = 2 * np.pi * r / L0
+    return float(cp * (L0 / r0) ** (5 / 3) * (sp.gamma(5 / 6) / 2 ** (1 / 6) - x ** (5 / 6) * sp.kv(5 / 6, x)))
+
+
+def hankel_phase_sf(r, r0, L0, fmin, fmax):
+    """The phase structure function over the annulus [fmin, fmax] that log-polar
+    draws sample: 4 pi int f W(f) (1 - J0(2 pi f r)) df, 8-point Gauss-Legendre on
+    geometric panels no wider than 1/(4 r)."""
+    from scipy import special as sp
+    e = np.geomspace(fmin, fmax, 400)
+    e = np.concatenate([np.linspace(a, c, max(1, int(np.ceil((c - a) * 4 * r))) + 1)[:-1] for a, c in zip(e[:-1], e[1:])]
+                       + [[fmax]])
+    x, w = np.polynomial.legendre.leggauss(8)
+    a, c = e[:-1, None], e[1:, None]
+    f = (0.5 * (c - a) * x + 0.5 * (c + a)).ravel()
+    ww = (0.5 * (c - a) * w).ravel()
+    W = 0.0228955871 * r0 ** (-5 / 3) * (f * f + L0 ** -2) ** (-11 / 6)
+    return float(np.sum(ww * 4 * np.pi * f * W * (1 - sp.j0(2 * np.pi * f * r))))
+
+
+def measure_fft_screen(qrs, h, torch, dev, R=1000, reps=3):
+    """The paper's comparison method (Eq. 2, static FFT sampling) against its own
+    method on the same square grid: 256 x 256 points at 8 m / 256 pitch, von
+    Karman r0 = 0.15 m, L0 = 30 m.  FFT: R/2 spectra (qrs_fft_spectrum) and their
+    inverse transforms by cuFFT, two screens each (real and imaginary parts);
+    quasi-random: R realisations of N_f = 4096 log-polar R2 terms over
+    [1e-3, 16] c/m by the separable tensor-core form.  Both timed; then the
+    structure function along x at 0.25, 1 and 4 m of each against the
+    continuum (the FFT grid's df = 0.125 c/m misses the outer scale)."""
+    from paper_2404_02978_gb300 import workloads as wl
+    n, L = 256, 8.0
+    dx = L / n
+    r0, L0 = 0.15, 30.0
+    p_fft = qrs.params(seed=21, r0=r0, L0=L0)
+    p_qrs = wl.method_params(dict(wl.PHASE_SCREEN, seed=22))
+    c = torch.from_numpy(((np.arange(n) + 0.5 - n / 2) * dx).astype(np.float32)).to(dev)
+    stream = torch.cuda.current_stream()
+    spec = torch.empty(R // 2, n, n, dtype=torch.complex64, device=dev)
+    grid = torch.empty(R, n, n, dtype=torch.float32, device=dev)
+
+    def run_fft(off):
+        qrs.qrs_fft_spectrum(h, p_fft, n, dx, R // 2, real_offset=off, out=spec, stream=stream)
+        chi = torch.fft.ifft2(spec, norm="forward")
+        return torch.stack([chi.real, chi.imag]).reshape(R, n, n)
+
+    def run_qrs(off):
+        return qrs.qrs_synthesize_grid(h, p_qrs, 4096, R, c, c, out=grid, mode="gemm_3xtf32", real_offset=off,
+                                       stream=stream)
+
+    res = {}
+    for name, fn in (("fft", run_fft), ("quasi_random_grid", run_qrs)):
+        out = fn(0)
+        qrs.qrs_sync(h, stream)
+        ms = []
+        for i in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(R * (i + 1))
+            e1.record(stream)
+            qrs.qrs_sync(h, stream)
+            ms.append(e0.elapsed_time(e1))
+        lags = np.array([8, 32, 128], np.int32)
+        delta = out.reshape(R, n, n).permute(1, 0, 2).contiguous()  # [row][realisation][column]
+        acc = qrs.qrs_structure_fn(h, delta, torch.from_numpy(lags).to(dev), stream=stream)
+        qrs.qrs_sync(h, stream)
+        a = acc.cpu().numpy()
+        per = a[:, :, 0] / a[:, :, 2]
+        mean, sem = per.mean(0), per.std(0, ddof=1) / np.sqrt(R)
+        sf = {}
+        for li, lag in enumerate(lags):
+            r = float(lag * dx)
+            cont = vk_phase_sf(r, r0, L0)
+            sf["%.2f_m" % r] = {"mean_rad2": float(mean[li]), "continuum_rad2": cont,
+                                "ratio_to_continuum": float(mean[li] / cont),
+                                "z_vs_continuum": float((mean[li] - cont) / sem[li])}
+            if name == "quasi_random_grid":
+                ann = hankel_phase_sf(r, r0, L0, 1e-3, 16.0)
+                sf["%.2f_m" % r].update(annulus_rad2=ann, z_vs_annulus=float((mean[li] - ann) / sem[li]))
+        res[name] = {"ms_per_%d_screens" % R: min(ms), "screens_per_s": R / (min(ms) / 1e3), "structure_function": sf}
+    res["fft"]["how"] = "qrs_fft_spectrum (%d spectra) + torch.fft.ifft2 (cuFFT); real and imaginary parts" % (R // 2)
+    res["quasi_random_grid"]["how"] = "qrs_synthesize_grid, N_f=4096 log-polar R2 per realisation, 3XTF32"
+    return {"workload": "256x256 square grid over 8 m, von Karman r0=0.15 m L0=30 m, %d screens per method" % R,
+            **res, "note": "z = (mean - expected) / Monte-Carlo standard error over the realisations"}
+
+
 def hankel_piston_sf(B, r0, L0, D, fmin, fmax):
     """Expected differential-piston SF of equal unobscured apertures over the
     annulus: 4 pi int f W(f) A(f)^2 (1 - J0(2 pi f B)) df, von Karman W,
@@ -903,6 +995,7 @@ def run_ours(a):
         line["other_forms"]["batched_pistons"] = measure_batched(qrs, h, torch, dev)
         line["other_forms"]["vlti_temporal_sf"] = measure_vlti(qrs, h, torch, dev)
         line["other_forms"]["sampling_quality"] = measure_sampling(qrs, h, torch, dev)
+        line["other_forms"]["fft_screen_baseline"] = measure_fft_screen(qrs, h, torch, dev)
         line["other_forms"]["learned_proposal"] = measure_learned(qrs, h, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, p, xy_np, gpu_rows=out[:4].cpu().numpy())

@@ -367,6 +367,25 @@ qrs_status qrs_choose_n(const qrs_psd* psd, double delta_f, double eps_rel, int3
 qrs_status qrs_structure_fn(qrs_handle* h, const float* delta, int64_t n_real, int64_t n_series,
                             int64_t T, const int32_t* lags, int32_t n_lags, double* acc, void* stream);
 
+/* ----------------------------------------- FFT screen spectrum (Eq. 2) ---
+ * The comparison method of Sec. 2.2 (static sampling of the frequency plane;
+ * not the paper's method, which is the direct sum above): the spectrum of
+ * n_real screens of n x n points at pitch dx (m),
+ *   spec[r][i][j] = (a + i b) sqrt(W(f)) A(|f|) df,  f = (j', i') df,
+ *   df = 1 / (n dx),  j' = j for j < (n + 1) / 2, j - n otherwise,
+ * a, b ~ N(0,1) by Box-Muller from words 2 and 3 of the Philox4x32-10
+ * counter ((real_offset + r) n^2 + i n + j, stream 4) with key seed, A the
+ * Eq. 7 filter when psd->ap_D_m > 0 (else 1), and spec = 0 at f = 0.  The
+ * screens are n^2 times its inverse DFT, sum_f spec(f) e^{2 pi i f.x} at
+ * x = (j dx, i dx): the real and the imaginary part are two screens, each of
+ * variance sum_f W df^2.  The caller takes that inverse transform (e.g.
+ * cuFFT); the static grid is what biases their structure function (Sec. 2.3).
+ *   spec [n_real][n][n][2] FP32 (interleaved complex), 8-byte aligned.
+ * n in [2, 32768], dx > 0, n_real >= 0 (0 is a no-op), real_offset >= 0;
+ * a KOLMOGOROV PSD is allowed (its f = 0 sample is the 0 above). */
+qrs_status qrs_fft_spectrum(qrs_handle* h, const qrs_psd* psd, int64_t n, double dx, uint64_t seed, int64_t n_real,
+                            int64_t real_offset, float* spec, void* stream);
+
 /* ------------------------------------------------- no-allocation variant ---
  * The paper has no counterpart: this is a deployment variant of
  * qrs_synthesize_points (mode QRS_SYNTH_FUSED) for callers that cannot

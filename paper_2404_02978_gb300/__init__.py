@@ -14,6 +14,7 @@ grid of Eq. 4, uniform, importance cells) and coefficient form (Eq. 3).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import threading
@@ -21,7 +22,7 @@ import threading
 import torch
 
 __all__ = ["params", "Handle", "qrs_create", "qrs_draw", "qrs_synthesize_points", "qrs_synthesize_grid", "qrs_diff_piston",
-           "qrs_pair_diff", "qrs_choose_n", "qrs_nearest_neighbour", "qrs_star_discrepancy", "qrs_structure_fn", "qrs_sync", "QrsError", "lib_path", "load"]
+           "qrs_pair_diff", "qrs_choose_n", "qrs_fft_spectrum", "fft_screens", "qrs_nearest_neighbour", "qrs_star_discrepancy", "qrs_structure_fn", "qrs_sync", "QrsError", "lib_path", "load"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libqrs.so")
@@ -372,6 +373,36 @@ def qrs_structure_fn(h: Handle, delta, lags, acc=None, stream=None):
     h._check(h.L.qrs_structure_fn(h.h, delta.data_ptr(), int(R), int(S), int(T), lags.data_ptr(),
                                   int(lags.shape[0]), acc.data_ptr(), _stream(stream)))
     return acc
+
+
+def qrs_fft_spectrum(h: Handle, p, n, dx, n_real, real_offset=0, out=None, stream=None):
+    """Spectrum of the Eq. 2 FFT screens (include/qrs.h): complex64 [n_real, n, n] on the device."""
+    if out is None:
+        out = torch.empty(n_real, n, n, dtype=torch.complex64, device=torch.device("cuda", h.device))
+    _check_dev(out, torch.complex64, "out")
+    if out.numel() != n_real * n * n:
+        raise ValueError("out must hold n_real * n * n values")
+    f = h.L.qrs_fft_spectrum
+    if f.argtypes is None:
+        f.argtypes = [C.c_void_p, C.POINTER(QrsPsd), C.c_int64, C.c_double, C.c_uint64, C.c_int64, C.c_int64,
+                      C.c_void_p, C.c_void_p]
+        f.restype = C.c_int
+    psd, _, _ = _structs(p)
+    h._check(f(h.h, C.byref(psd), int(n), float(dx), int(p.get("seed", 0)) & (2**64 - 1), int(n_real),
+               int(real_offset), out.data_ptr(), _stream(stream)))
+    return out
+
+
+def fft_screens(h: Handle, p, n, dx, n_real, real_offset=0, stream=None):
+    """The paper's comparison method (Eq. 2): n_real spectra from qrs_fft_spectrum, then
+    n^2 times their inverse DFT by cuFFT (torch.fft), whose real and imaginary parts are
+    two screens each: returns float32 [2, n_real, n, n] (part, realisation, row y,
+    column x), points (j dx, i dx).  Not the paper's method: a baseline whose static
+    frequency grid biases the structure function."""
+    spec = qrs_fft_spectrum(h, p, n, dx, n_real, real_offset, stream=stream)
+    with torch.cuda.stream(stream) if isinstance(stream, torch.cuda.Stream) else contextlib.nullcontext():
+        chi = torch.fft.ifft2(spec, norm="forward")
+        return torch.stack([chi.real, chi.imag])
 
 
 def qrs_synthesize_points_noalloc(p, n_f, n_real, xy, out=None, real_offset=0, stream=None):

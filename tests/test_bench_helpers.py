@@ -29,3 +29,15 @@ def test_hankel_piston_sf_limits():
     far = bench.hankel_piston_sf(1e5, r0, L0, D, 1.0, 10.0)
     assert far == pytest.approx(2 * an.piston_variance(r0, L0, D, 0.0, 1.0, 10.0), rel=1e-3)
     assert np.isfinite(far)
+
+
+@pytest.mark.parametrize("r", [0.05, 0.5, 2.0, 8.0, 40.0])
+def test_vk_phase_sf_matches_the_oracle_closed_form(r):
+    assert bench.vk_phase_sf(r, 0.15, 30.0) == pytest.approx(an.phase_sf_vk_infinite(r, 0.15, 30.0), rel=1e-10)
+
+
+@pytest.mark.parametrize("r", [0.1, 1.0, 4.0])
+def test_hankel_phase_sf_matches_the_oracle_quadrature(r):
+    got = bench.hankel_phase_sf(r, 0.15, 30.0, 1e-3, 16.0)
+    ref = an.phase_sf(r, 0.15, 30.0, 1e-3, 16.0)
+    assert got == pytest.approx(ref, rel=1e-6)
