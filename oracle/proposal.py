@@ -3,6 +3,8 @@ infrastructure only; never imported by the product package).
 
 Written from the definitions stated in include/qrs_proposal.h:
 * features of a geometry (r0, L0, D, Bx, By);
+* the per-cell prior of the logits (a quadrature of each cell's contribution
+  to the differential-piston structure function);
 * the 6 -> 128 -> 128 -> C ReLU network, softmax cross entropy, its analytic
   backward pass (pinned by central finite differences in the tests) and the
   bias-corrected Adam step;
@@ -66,7 +68,8 @@ def init(n_cells, seed):
     return np.where(fan > 0, z * np.sqrt(2.0 / np.maximum(fan, 1)), 0.0)
 
 
-def forward(P, geom, n_cells, keep=False):
+def forward(P, geom, n_cells, keep=False, prior=None):
+    """Logits z = MLP(features) (+ prior [n][C] when given)."""
     W1, b1, W2, b2, W3, b3 = unpack(P, n_cells)
     X = features(geom)
     A1 = X @ W1 + b1
@@ -74,9 +77,58 @@ def forward(P, geom, n_cells, keep=False):
     A2 = H1 @ W2 + b2
     H2 = np.maximum(A2, 0.0)
     Z = H2 @ W3 + b3
+    if prior is not None:
+        Z = Z + np.asarray(prior, np.float64)
     if keep:
         return Z, (X, A1, H1, A2, H2)
     return Z
+
+
+PRIOR_NODES = 64
+PRIOR_FLOOR = -60.0
+
+
+def prior_nodes(m=PRIOR_NODES):
+    """The first m points of the R2 sequence of Eq. 6 from s0 = (1/2, 1/2), exact in
+    0.64 fixed point, as FP64 fractions (S >> 11) 2^-53."""
+    a1, a2 = np.uint64(0xC13FA9A902A6328F), np.uint64(0x91E10DA5C79E7B1D)
+    k = np.arange(m, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        Sx = np.uint64(1 << 63) + k * a1
+        Sy = np.uint64(1 << 63) + k * a2
+    return (Sx >> np.uint64(11)).astype(np.float64) * 2.0 ** -53, (Sy >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+
+
+def prior(psd_kind, dom, n_rho, n_theta, fold, geom, raw=False):
+    """The prior of the proposal's logits: per importance cell c the mean, over
+    the PRIOR_NODES points (s_x, s_y) of prior_nodes placed in the cell
+    (u = (i_rho + s_x) / n_rho, t = (i_theta + s_y) / n_theta), of
+        g = W(rho) A(pi D rho)^2 (1 - cos(2 pi rho |B| cos phi)) rho^2,
+    rho = fmin (fmax / fmin)^u, phi the angle from the baseline: 2 pi t / fold
+    for fold >= 1 (the cell's sector; its mirror images hold the same values),
+    2 pi t - atan2(By, Bx) for fold 0.  That is the cell's mean contribution to
+    the differential-piston structure function at B (Sec. 4.4 with Eq. 7) up to
+    the constant 4 pi ln(fmax / fmin).  raw: v_c; else log(v_c / max v),
+    floored at PRIOR_FLOOR.  Returns [n][n_rho n_theta]."""
+    fmin, fmax = dom
+    sx, sy = prior_nodes()
+    u = (np.arange(n_rho)[:, None] + sx[None, :]) / n_rho          # [n_rho][M]
+    t = (np.arange(n_theta)[:, None] + sy[None, :]) / n_theta      # [n_theta][M]
+    rho = fmin * (fmax / fmin) ** u
+    g = np.asarray(geom, np.float64).reshape(-1, 5)
+    out = np.zeros((g.shape[0], n_rho * n_theta))
+    for i, (r0, L0, D, Bx, By) in enumerate(g):
+        B = np.hypot(Bx, By)
+        phi = 2.0 * np.pi * t / fold if fold else 2.0 * np.pi * t - np.arctan2(By, Bx)
+        env = an.psd(rho, r0, L0, psd_kind) * an.airy(rho.ravel(), D).reshape(rho.shape) ** 2 * rho ** 2
+        osc = 1.0 - np.cos(2.0 * np.pi * B * rho[:, None, :] * np.cos(phi)[None, :, :])  # [n_rho][n_theta][M]
+        v = np.mean(env[:, None, :] * osc, axis=2).ravel()
+        if raw:
+            out[i] = v
+        else:
+            with np.errstate(divide="ignore"):
+                out[i] = np.maximum(np.log(v / v.max()), PRIOR_FLOOR)
+    return out
 
 
 def log_softmax(Z):
@@ -84,17 +136,18 @@ def log_softmax(Z):
     return Z - m - np.log(np.exp(Z - m).sum(axis=1, keepdims=True))
 
 
-def loss(P, geom, T, n_cells):
-    Z = forward(P, geom, n_cells)
+def loss(P, geom, T, n_cells, prior=None):
+    Z = forward(P, geom, n_cells, prior=prior)
     return float(-np.mean(np.sum(np.asarray(T, np.float64) * log_softmax(Z), axis=1)))
 
 
-def loss_grad(P, geom, T, n_cells):
-    """Mean cross entropy and its gradient by the chain rule, layer by layer."""
+def loss_grad(P, geom, T, n_cells, prior=None):
+    """Mean cross entropy of softmax(z (+ prior)) and its gradient by the chain
+    rule, layer by layer (the prior is a constant input of the softmax)."""
     W1, b1, W2, b2, W3, b3 = unpack(P, n_cells)
     T = np.asarray(T, np.float64)
     n = T.shape[0]
-    Z, (X, A1, H1, A2, H2) = forward(P, geom, n_cells, keep=True)
+    Z, (X, A1, H1, A2, H2) = forward(P, geom, n_cells, keep=True, prior=prior)
     ls = log_softmax(Z)
     L = float(-np.mean(np.sum(T * ls, axis=1)))
     dZ = (np.exp(ls) - T) / n            # d L / d z (rows of T sum to 1)

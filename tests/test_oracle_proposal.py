@@ -110,3 +110,61 @@ def test_he_init_statistics():
     assert np.var(W3) == pytest.approx(2 / 128, rel=0.02)
     assert np.var(W2) == pytest.approx(2 / 128, rel=0.05)
     assert np.var(W1) == pytest.approx(2 / 6, rel=0.15)
+
+
+# ------------------------------------------------------------- logit prior
+@pytest.mark.parametrize("fold", [0, 1, 4])
+def test_prior_cells_add_up_to_the_hankel_integral(fold):
+    """The raw prior's cells, weighted by their share of the unit square and the
+    constant 4 pi ln(fmax / fmin) dropped from g, add up to the structure function
+    D(B) = 4 pi int f W A^2 (1 - J0(2 pi f B)) df (Sec. 4.4 with Eq. 7): the
+    quadrature of the whole annulus, up to the accuracy of 64 nodes per cell."""
+    g = _geom(4, 11)
+    v = pr.prior(0, (1e-3, 10.0), 96, 24, fold, g, raw=True)
+    for i, (r0, L0, D, Bx, By) in enumerate(g):
+        total = 4.0 * np.pi * np.log(1e4) * v[i].sum() / (96 * 24)
+        assert total == pytest.approx(an.piston_sf(np.hypot(Bx, By), r0, L0, D, 0.0, 1e-3, 10.0), rel=3e-3)
+
+
+def test_prior_normalisation_and_floor():
+    g = _geom(3, 12)
+    P = pr.prior(0, (1e-3, 10.0), 32, 16, 4, g)
+    assert np.allclose(P.max(axis=1), 0.0)
+    assert P.min() >= pr.PRIOR_FLOOR
+    # the nodes: the R2 sequence from (1/2, 1/2), first point the seed itself
+    sx, sy = pr.prior_nodes(4)
+    assert sx[0] == 0.5 and sy[0] == 0.5
+    psi = 1.32471795724474602596
+    assert sx[1] == pytest.approx((0.5 + 1 / psi) % 1.0, abs=1e-15)
+    assert sy[1] == pytest.approx((0.5 + 1 / psi ** 2) % 1.0, abs=1e-15)
+
+
+def test_prior_is_the_mean_of_the_plain_targets():
+    """The prior estimates by quadrature what the MEAN targets estimate by plain
+    draws: the two normalised distributions over the cells agree within the
+    Monte-Carlo noise of the draws (total variation distance)."""
+    g = _geom(3, 13)
+    nr, nt = 24, 8
+    v = pr.prior(0, (1e-3, 10.0), nr, nt, 4, g, raw=True)
+    p_q = v / v.sum(axis=1, keepdims=True)
+    t = pr.targets(0, (1e-3, 10.0), nr, nt, 5, 1024, 64, g, kind="mean", fold=4)
+    tv = 0.5 * np.abs(p_q - t).sum(axis=1)
+    assert np.all(tv < 0.03), tv
+
+
+def test_backward_with_prior_matches_finite_differences():
+    C = 8
+    rng = np.random.default_rng(1)
+    P = pr.init(C, 4) + 0.05 * rng.normal(size=pr.param_count(C))
+    g = _geom(5, 2)
+    T = rng.dirichlet(np.ones(C), size=5)
+    prior = rng.normal(size=(5, C)) * 3.0
+    L, G = pr.loss_grad(P, g, T, C, prior=prior)
+    assert L == pytest.approx(pr.loss(P, g, T, C, prior=prior), rel=1e-14)
+    idx = rng.choice(P.size, 40, replace=False)
+    h = 1e-6
+    for k in idx:
+        e = np.zeros_like(P)
+        e[k] = h
+        fd = (pr.loss(P + e, g, T, C, prior=prior) - pr.loss(P - e, g, T, C, prior=prior)) / (2 * h)
+        assert G[k] == pytest.approx(fd, rel=1e-6, abs=1e-9)
