@@ -763,19 +763,23 @@ def hankel_piston_sf(B, r0, L0, D, fmin, fmax):
     return float(np.sum(ww * 4 * np.pi * f * W * A * A * (1 - sp.j0(2 * np.pi * f * B))))
 
 
-def measure_learned(qrs, h, torch, dev, n_train=8000, n_test=200, draws=8, n_rho=128, n_theta=32, steps=8000,
-                    target_draws=1024, fold=4, lr=4e-3, beta=0.7, seeds=(3, 4, 5, 6)):
-    """Learned proposal (6 -> 128 -> 128 -> n_rho x n_theta logits): targets from the
-    plain method's own draws, training on the GPU, then the matched
+def measure_learned(qrs, h, torch, dev, n_train=8000, n_test=200, draws=8, n_rho=256, n_theta=32, steps=4000,
+                    target_draws=1024, fold=4, lr=2e-3, beta=1.0, seeds=(3, 4, 5, 6), prior=True, out_scale=0.01,
+                    test_seed=2):
+    """Learned proposal (6 -> 128 -> 128 -> n_rho x n_theta logits, plus, with
+    prior, the per-cell prior of qrs_proposal_prior): targets from the plain
+    method's own draws, training on the GPU, then the matched
     structure-function error (RMS over held-out geometries and draws of the
     per-draw SF relative to the Hankel integral) of learned importance draws
-    at N_f = 256..1024 against plain draws at N_f = 256..4096.  The cells lie in
+    at N_f = 256..1024 against plain draws at N_f = 256..8192.  The cells lie in
     each geometry's baseline frame, folded over `fold` mirrored sectors; Adam
     with a cosine learning-rate schedule; the sampled density is
-    softmax(beta z) (beta = 0.7 was chosen on 100 validation geometries
-    disjoint from the held-out ones).  The network of the first seed is
+    softmax(beta z).  The benchmark's settings (256 x 32 cells, the prior,
+    beta = 1) were chosen on 100 validation geometries (test_seed 3) disjoint
+    from the held-out ones (test_seed 2).  The network of the first seed is
     reported in full; the others (other initialisations, same data) give the
-    spread of the term reduction over training seeds."""
+    spread of the term reduction over training seeds; with the prior, the
+    prior alone as the density is reported beside it (the network's share)."""
     def geom(n, seed):
         rng = np.random.default_rng(seed)
         B = np.exp(rng.uniform(np.log(1), np.log(200), n))
@@ -787,17 +791,24 @@ def measure_learned(qrs, h, torch, dev, n_train=8000, n_test=200, draws=8, n_rho
     dom = dict(domain="logpolar", fmin=1e-3, fmax=10.0)
     C = n_rho * n_theta
     gtr = torch.from_numpy(geom(n_train, 1)).to(dev)
-    gte_np = geom(n_test, 2)
+    gte_np = geom(n_test, test_seed)
+    gte_dev = torch.from_numpy(gte_np).to(dev)
     t0 = time.perf_counter()
     T = qrs.qrs_proposal_targets(h, qrs.params(**dom), n_rho, n_theta, 77, 4096, target_draws, gtr, kind="rms",
                                  fold=fold)
     torch.cuda.synchronize()
     t_targets = time.perf_counter() - t0
     t0 = time.perf_counter()
-    P, hist = qrs.train_proposal(h, C, gtr, T, steps=steps, lr=lr, seed=seeds[0], log_every=1000, schedule="cosine")
+    Ptr = qrs.qrs_proposal_prior(h, qrs.params(**dom), n_rho, n_theta, gtr, fold=fold) if prior else None
+    Pte = qrs.qrs_proposal_prior(h, qrs.params(**dom), n_rho, n_theta, gte_dev, fold=fold) if prior else None
+    torch.cuda.synchronize()
+    t_prior = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P, hist = qrs.train_proposal(h, C, gtr, T, steps=steps, lr=lr, seed=seeds[0], log_every=1000, schedule="cosine",
+                                 prior=Ptr, out_scale=out_scale)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    logits = qrs.qrs_mlp_forward(h, C, P, torch.from_numpy(gte_np).to(dev))
+    logits = qrs.qrs_mlp_forward(h, C, P, gte_dev, prior=Pte)
     T_test = qrs.qrs_proposal_targets(h, qrs.params(**dom), n_rho, n_theta, 78, 4096, 512,
                                       torch.from_numpy(gte_np).to(dev), kind="rms", fold=fold)
     Drefs = [hankel_piston_sf(np.hypot(g[3], g[4]), g[0], g[1], g[2], 1e-3, 10.0) for g in gte_np]
@@ -826,28 +837,33 @@ def measure_learned(qrs, h, torch, dev, n_train=8000, n_test=200, draws=8, n_rho
         pi = importance(i, logits[i], beta)
         # the ceiling of any cell density on this grid: the geometry's own targets as the proposal
         px = importance(i, torch.log(T_test[i].clamp_min(1e-30)), 1.0)
-        for name, pp, nfs in (("plain", p, (256, 512, 1024, 2048, 4096)), ("learned", pi, (256, 512, 1024)),
-                              ("own_targets", px, (256, 512, 1024))):
+        runs = [("plain", p, (256, 512, 1024, 2048, 4096, 8192)), ("learned", pi, (256, 512, 1024)),
+                ("own_targets", px, (256, 512, 1024))]
+        if prior:  # ablation: the prior alone as the density (the network's logits left out)
+            runs.append(("prior_only", importance(i, Pte[i], beta), (256, 512, 1024)))
+        for name, pp, nfs in runs:
             for nf in nfs:
                 err.setdefault("%s_%d" % (name, nf), []).append(sq_err(pp, nf, i))
     rms = {k: float(np.sqrt(np.mean(v))) for k, v in err.items()}
-    plain_n = np.array([256, 512, 1024, 2048, 4096], float)
+    plain_n = np.array([256, 512, 1024, 2048, 4096, 8192], float)
     plain_e = np.array([rms["plain_%d" % n] for n in plain_n.astype(int)])
 
     def reduction(e, nf):
         """Plain terms needed for error e (log-log interpolation of the plain curve) / nf."""
         return float(np.exp(np.interp(-np.log(e), -np.log(plain_e), np.log(plain_n)))) / nf
 
-    equiv, cap = {}, {}
+    equiv, cap, pri = {}, {}, {}
     for nf in (256, 512, 1024):
         equiv[nf] = reduction(rms["learned_%d" % nf], nf) * nf
         cap[nf] = reduction(rms["own_targets_%d" % nf], nf) * nf
+        if prior:
+            pri[nf] = reduction(rms["prior_only_%d" % nf], nf)
     # the other training seeds: the spread of the reduction over initialisations
     per_seed = {str(seeds[0]): {str(nf): equiv[nf] / nf for nf in (256, 512, 1024)}}
-    gte_dev = torch.from_numpy(gte_np).to(dev)
     for sd in seeds[1:]:
-        Ps, _ = qrs.train_proposal(h, C, gtr, T, steps=steps, lr=lr, seed=sd, schedule="cosine")
-        zs = qrs.qrs_mlp_forward(h, C, Ps, gte_dev)
+        Ps, _ = qrs.train_proposal(h, C, gtr, T, steps=steps, lr=lr, seed=sd, schedule="cosine", prior=Ptr,
+                                   out_scale=out_scale)
+        zs = qrs.qrs_mlp_forward(h, C, Ps, gte_dev, prior=Pte)
         per_seed[str(sd)] = {}
         for nf in (256, 512, 1024):
             e = float(np.sqrt(np.mean([sq_err(importance(i, zs[i], beta), nf, i) for i in range(len(gte_np))])))
@@ -855,7 +871,10 @@ def measure_learned(qrs, h, torch, dev, n_train=8000, n_test=200, draws=8, n_rho
     return {"workload": "%d training geometries (r0 0.05-0.3 m, L0 10-100 m, D 1-8 m, |B| 1-200 m), "
                         "%d held out, %d draws each, cells %dx%d over [1e-3, 10] c/m, baseline frame, "
                         "%d mirrored sectors" % (n_train, n_test, draws, n_rho, n_theta, fold),
-            "targets_s": t_targets, "train_s": t_train, "train_steps": steps, "lr_schedule": "cosine from %g" % lr,
+            "targets_s": t_targets, "prior_s": t_prior if prior else None, "logit_prior": bool(prior),
+            "term_reduction_prior_only": {str(k): v for k, v in pri.items()} if prior else None,
+            "out_scale": out_scale,
+            "train_s": t_train, "train_steps": steps, "lr_schedule": "cosine from %g" % lr,
             "target_draws": target_draws, "beta": beta, "loss_first_last": [hist[0][1], hist[-1][1]],
             "matched_sf_error": rms,
             "plain_terms_for_equal_error": {str(k): v for k, v in equiv.items()},

@@ -18,7 +18,8 @@
  *
  * Network (FP32): features x = ((ln r0 - ln 0.12)/0.6, (ln L0 - ln 30)/0.8,
  * (ln D - ln 3)/0.6, (ln|B| - ln 15)/1.5, Bx/|B|, By/|B|); h1 = relu(x W1 + b1),
- * h2 = relu(h1 W2 + b2), z = h2 W3 + b3 (logits); widths 6 -> 128 -> 128 -> C,
+ * h2 = relu(h1 W2 + b2), z = h2 W3 + b3 + prior (logits; the prior of
+ * qrs_proposal_prior, or none); widths 6 -> 128 -> 128 -> C,
  * C = n_rho n_theta (2048 for 64 x 32).  Loss: mean over samples of the cross
  * entropy -sum_c t_c log softmax(z)_c.  Optimiser: Adam (beta1 0.9, beta2 0.999,
  * eps 1e-8, bias-corrected).
@@ -43,8 +44,10 @@ extern "C" {
 int64_t qrs_mlp_param_count(int32_t n_cells);
 
 /* He-normal initialisation (weights N(0, 2/fan_in) from Philox4x32-10 of `seed`
- * by Box-Muller, biases 0) of params [qrs_mlp_param_count(n_cells)]. */
-qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float* params, void* stream);
+ * by Box-Muller, biases 0) of params [qrs_mlp_param_count(n_cells)]; the
+ * output layer's weights W3 are multiplied by out_scale (1: He; small values
+ * start the logits at the prior when one is used).  out_scale >= 0. */
+qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float out_scale, float* params, void* stream);
 
 /* Training targets from plain draws: for each geometry geom[i] = (r0, L0, D,
  * Bx, By) (device FP64 [n][5]), the per-cell structure-function contributions
@@ -75,14 +78,34 @@ qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_dom
                                 int32_t n_theta, uint64_t seed, int64_t n_f, int32_t n_draws, int32_t kind,
                                 int32_t fold, const double* geom, int64_t n, float* targets, void* stream);
 
-/* Forward pass: logits [n][C] from geometries geom [n][5] (device FP64). */
-qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, const double* geom, int64_t n,
-                           float* logits, void* stream);
+/* Prior of the logits: for each geometry and importance cell c (the cells of
+ * an IMPORTANCE sampler with this fold and frame = atan2(By, Bx) / 2 pi), the
+ * mean over 64 points placed in the cell -- (u, t) = ((i_rho + s_x) / n_rho,
+ * (i_theta + s_y) / n_theta), (s_x, s_y) the first 64 points of the R2
+ * sequence of Eq. 6 from (1/2, 1/2) -- of
+ *     g = W(rho) A(pi D rho)^2 (1 - cos(2 pi rho |B| cos phi)) rho^2,
+ * rho = fmin (fmax/fmin)^u, phi the angle from the baseline (2 pi t / fold in
+ * the folded frame, 2 pi t - atan2(By, Bx) for fold 0): the cell's share of
+ * the differential-piston structure function at B (Sec. 4.4 with the Eq. 7
+ * filter) up to a constant, a PSD-aware mapping in the sense of Sec. 5.
+ * prior [n][n_rho n_theta] (device FP32) = log(v_c / max v), floored at -60.
+ * The PSD kind from psd (r0, L0 from the geometries; psd's own filter off). */
+qrs_status qrs_proposal_prior(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, int32_t n_rho,
+                              int32_t n_theta, int32_t fold, const double* geom, int64_t n, float* prior, void* stream);
+
+/* Forward pass: logits [n][C] = MLP(features of geom [n][5], device FP64)
+ * + prior [n][C] (device FP32, e.g. from qrs_proposal_prior), or the MLP
+ * alone when prior is NULL. */
+qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, const double* geom,
+                           const float* prior, int64_t n, float* logits, void* stream);
 
 /* Loss and gradient at params: grad [param_count] (overwritten), loss [1]
- * (device FP32, the mean cross entropy).  targets [n][C] rows sum to 1. */
+ * (device FP32, the mean cross entropy of softmax(logits) against targets,
+ * logits as in qrs_mlp_forward with the same prior or NULL; the prior is a
+ * constant of the loss).  targets [n][C] rows sum to 1. */
 qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params, const double* geom,
-                             const float* targets, int64_t n, float* grad, float* loss, void* stream);
+                             const float* prior, const float* targets, int64_t n, float* grad, float* loss,
+                             void* stream);
 
 /* One Adam step (step >= 1: bias correction t = step) with learning rate lr:
  * params, m, v [param_count] updated in place from grad. */
@@ -106,7 +129,8 @@ typedef struct qrs_mlp_state {
 #define QRS_LR_CONSTANT 0
 #define QRS_LR_COSINE 1
 
-/* Full-batch Adam on the mean cross entropy of qrs_mlp_loss_grad: `steps`
+/* Full-batch Adam on the mean cross entropy of qrs_mlp_loss_grad (with the
+ * prior [n][C] or NULL): `steps`
  * steps t = state->step + 1 .. state->step + steps, each the loss and
  * gradient at the current parameters followed by qrs_mlp_adam's update with
  * bias correction t; state->params, m, v are updated in place and
@@ -126,9 +150,9 @@ typedef struct qrs_mlp_state {
  * Workspace: the handle's (the backward pass's buffers and the gradient).
  * Errors: QRS_ERR_ARG for invalid sizes, pointers, lr <= 0, an unknown
  * schedule, total_steps too small; nothing is launched then. */
-qrs_status qrs_proposal_train(qrs_handle* h, qrs_mlp_state* state, const double* geom, const float* targets, int64_t n,
-                              int64_t steps, double lr, int32_t schedule, int64_t total_steps, float* loss_trace,
-                              void* stream);
+qrs_status qrs_proposal_train(qrs_handle* h, qrs_mlp_state* state, const double* geom, const float* prior,
+                              const float* targets, int64_t n, int64_t steps, double lr, int32_t schedule,
+                              int64_t total_steps, float* loss_trace, void* stream);
 
 /* Checkpoint of a training state: qrs_mlp_save writes n_cells, step, params,
  * m and v to the file `path` (host path; the file holds the 8 bytes

@@ -54,8 +54,9 @@ def features(geom):
                      (np.log(D) - np.log(3.0)) / 0.6, (np.log(B) - np.log(15.0)) / 1.5, Bx / B, By / B], -1)
 
 
-def init(n_cells, seed):
-    """He-normal weights from Philox normals (counter = parameter index, stream 3), zero biases."""
+def init(n_cells, seed, out_scale=1.0):
+    """He-normal weights from Philox normals (counter = parameter index, stream 3), zero biases;
+    the output layer's weights times out_scale."""
     n = param_count(n_cells)
     z = np.zeros(n, np.float64)
     _lib().oracle_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_int64, C.c_void_p]
@@ -65,7 +66,10 @@ def init(n_cells, seed):
     for (size, fan_in) in ((6 * H, 6), (H, 0), (H * H, H), (H, 0), (H * n_cells, H), (n_cells, 0)):
         fan[o:o + size] = fan_in
         o += size
-    return np.where(fan > 0, z * np.sqrt(2.0 / np.maximum(fan, 1)), 0.0)
+    w = np.where(fan > 0, z * np.sqrt(2.0 / np.maximum(fan, 1)), 0.0)
+    o3 = 6 * H + H + H * H + H
+    w[o3:o3 + H * n_cells] *= out_scale
+    return w
 
 
 def forward(P, geom, n_cells, keep=False, prior=None):
@@ -121,7 +125,8 @@ def prior(psd_kind, dom, n_rho, n_theta, fold, geom, raw=False):
         B = np.hypot(Bx, By)
         phi = 2.0 * np.pi * t / fold if fold else 2.0 * np.pi * t - np.arctan2(By, Bx)
         env = an.psd(rho, r0, L0, psd_kind) * an.airy(rho.ravel(), D).reshape(rho.shape) ** 2 * rho ** 2
-        osc = 1.0 - np.cos(2.0 * np.pi * B * rho[:, None, :] * np.cos(phi)[None, :, :])  # [n_rho][n_theta][M]
+        # 1 - cos x as 2 sin^2 (x / 2): no cancellation where the phase is small
+        osc = 2.0 * np.sin(np.pi * B * rho[:, None, :] * np.cos(phi)[None, :, :]) ** 2  # [n_rho][n_theta][M]
         v = np.mean(env[:, None, :] * osc, axis=2).ravel()
         if raw:
             out[i] = v

@@ -442,14 +442,39 @@ def qrs_mlp_param_count(n_cells) -> int:
     return int(_prop_fn("qrs_mlp_param_count", [C.c_int32], C.c_int64)(int(n_cells)))
 
 
-def qrs_mlp_init(h: Handle, n_cells, seed, params=None, stream=None):
+def qrs_mlp_init(h: Handle, n_cells, seed, params=None, stream=None, out_scale=1.0):
+    """He-normal parameters; the output layer's weights times out_scale."""
     n = qrs_mlp_param_count(n_cells)
     if params is None:
         params = torch.empty(n, dtype=torch.float32, device=torch.device("cuda", h.device))
     _check_dev(params, torch.float32, "params")
-    f = _prop_fn("qrs_mlp_init", [C.c_void_p, C.c_int32, C.c_uint64, C.c_void_p, C.c_void_p])
-    h._check(f(h.h, int(n_cells), int(seed) & (2**64 - 1), params.data_ptr(), _stream(stream)))
+    f = _prop_fn("qrs_mlp_init", [C.c_void_p, C.c_int32, C.c_uint64, C.c_float, C.c_void_p, C.c_void_p])
+    h._check(f(h.h, int(n_cells), int(seed) & (2**64 - 1), float(out_scale), params.data_ptr(), _stream(stream)))
     return params
+
+
+def qrs_proposal_prior(h: Handle, p, n_rho, n_theta, geom, fold=0, out=None, stream=None):
+    """Per-cell prior of the logits [n][n_rho n_theta] (geom: device float64 [n][5]); see include/qrs_proposal.h."""
+    _check_dev(geom, torch.float64, "geom")
+    n = geom.shape[0]
+    if out is None:
+        out = torch.empty(n, n_rho * n_theta, dtype=torch.float32, device=geom.device)
+    _check_dev(out, torch.float32, "out")
+    psd, dom, _ = _structs(p)
+    f = _prop_fn("qrs_proposal_prior", [C.c_void_p, C.POINTER(QrsPsd), C.POINTER(QrsDomain), C.c_int32, C.c_int32,
+                                        C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p])
+    h._check(f(h.h, C.byref(psd), C.byref(dom), int(n_rho), int(n_theta), int(fold), geom.data_ptr(), int(n),
+               out.data_ptr(), _stream(stream)))
+    return out
+
+
+def _opt_prior(prior, n, n_cells):
+    if prior is None:
+        return None
+    _check_dev(prior, torch.float32, "prior")
+    if prior.numel() != n * n_cells:
+        raise ValueError("prior must hold n * n_cells values")
+    return prior.data_ptr()
 
 
 TARGET = {"mean": 0, "rms": 1}
@@ -472,18 +497,21 @@ def qrs_proposal_targets(h: Handle, p, n_rho, n_theta, seed, n_f, n_draws, geom,
     return out
 
 
-def qrs_mlp_forward(h: Handle, n_cells, params, geom, out=None, stream=None):
+def qrs_mlp_forward(h: Handle, n_cells, params, geom, out=None, stream=None, prior=None):
+    """Logits [n][n_cells] = MLP(geom) (+ prior [n][n_cells] when given)."""
     _check_dev(params, torch.float32, "params")
     _check_dev(geom, torch.float64, "geom")
     n = geom.shape[0]
     if out is None:
         out = torch.empty(n, n_cells, dtype=torch.float32, device=geom.device)
-    f = _prop_fn("qrs_mlp_forward", [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p])
-    h._check(f(h.h, int(n_cells), params.data_ptr(), geom.data_ptr(), int(n), out.data_ptr(), _stream(stream)))
+    f = _prop_fn("qrs_mlp_forward", [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                     C.c_void_p])
+    h._check(f(h.h, int(n_cells), params.data_ptr(), geom.data_ptr(), _opt_prior(prior, n, n_cells), int(n),
+               out.data_ptr(), _stream(stream)))
     return out
 
 
-def qrs_mlp_loss_grad(h: Handle, n_cells, params, geom, targets, grad=None, loss=None, stream=None):
+def qrs_mlp_loss_grad(h: Handle, n_cells, params, geom, targets, grad=None, loss=None, stream=None, prior=None):
     _check_dev(params, torch.float32, "params")
     _check_dev(geom, torch.float64, "geom")
     _check_dev(targets, torch.float32, "targets")
@@ -491,10 +519,11 @@ def qrs_mlp_loss_grad(h: Handle, n_cells, params, geom, targets, grad=None, loss
         grad = torch.empty_like(params)
     if loss is None:
         loss = torch.empty(1, dtype=torch.float32, device=params.device)
-    f = _prop_fn("qrs_mlp_loss_grad", [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
-                                       C.c_void_p, C.c_void_p])
-    h._check(f(h.h, int(n_cells), params.data_ptr(), geom.data_ptr(), targets.data_ptr(), int(geom.shape[0]),
-               grad.data_ptr(), loss.data_ptr(), _stream(stream)))
+    f = _prop_fn("qrs_mlp_loss_grad", [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p])
+    n = int(geom.shape[0])
+    h._check(f(h.h, int(n_cells), params.data_ptr(), geom.data_ptr(), _opt_prior(prior, n, n_cells), targets.data_ptr(),
+               n, grad.data_ptr(), loss.data_ptr(), _stream(stream)))
     return grad, loss
 
 
@@ -557,7 +586,7 @@ class ProposalState:
 
 
 def qrs_proposal_train(h: Handle, state: ProposalState, geom, targets, steps, lr, schedule="constant",
-                       total_steps=None, loss_trace=None, stream=None):
+                       total_steps=None, loss_trace=None, stream=None, prior=None):
     """Full-batch Adam in libqrs (one call, include/qrs_proposal.h): advances
     `state` by `steps` steps; loss_trace (device float32 [steps]) receives
     each step's loss when given."""
@@ -570,17 +599,19 @@ def qrs_proposal_train(h: Handle, state: ProposalState, geom, targets, steps, lr
             raise ValueError("loss_trace must hold `steps` values")
         lt = loss_trace.data_ptr()
     total = int(total_steps) if total_steps is not None else state.step + int(steps)
-    f = _prop_fn("qrs_proposal_train", [C.c_void_p, C.POINTER(QrsMlpState), C.c_void_p, C.c_void_p, C.c_int64,
-                                        C.c_int64, C.c_double, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p])
+    f = _prop_fn("qrs_proposal_train", [C.c_void_p, C.POINTER(QrsMlpState), C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_int64, C.c_int64, C.c_double, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p])
     st = state._c()
-    h._check(f(h.h, C.byref(st), geom.data_ptr(), targets.data_ptr(), int(geom.shape[0]), int(steps), float(lr),
-               LR_SCHEDULE[schedule], total, lt, _stream(stream)))
+    n = int(geom.shape[0])
+    h._check(f(h.h, C.byref(st), geom.data_ptr(), _opt_prior(prior, n, state.n_cells), targets.data_ptr(), n,
+               int(steps), float(lr), LR_SCHEDULE[schedule], total, lt, _stream(stream)))
     state.step = int(st.step)
     return state
 
 
 def train_proposal(h: Handle, n_cells, geom, targets, steps=2000, lr=2e-3, seed=0, params=None, stream=None,
-                   log_every=0, state=None, return_state=False, schedule="constant", total_steps=None):
+                   log_every=0, state=None, return_state=False, schedule="constant", total_steps=None, prior=None,
+                   out_scale=1.0):
     """Adam on the mean cross entropy, full batch, as one libqrs call
     (qrs_proposal_train).  schedule "cosine": step t of a run of total_steps
     (default: this call's last step) uses lr (1 + cos(pi (t - 1) /
@@ -595,13 +626,13 @@ def train_proposal(h: Handle, n_cells, geom, targets, steps=2000, lr=2e-3, seed=
             raise ValueError("checkpoint has %d cells, not %d" % (state.n_cells, n_cells))
     else:
         if params is None:
-            params = qrs_mlp_init(h, n_cells, seed, stream=stream)
+            params = qrs_mlp_init(h, n_cells, seed, stream=stream, out_scale=out_scale)
         state = ProposalState(n_cells, params, torch.zeros_like(params), torch.zeros_like(params), 0)
     step0 = state.step
     trace = torch.empty(max(int(steps), 1), dtype=torch.float32, device=state.params.device) if log_every else None
     qrs_proposal_train(h, state, geom, targets, steps, lr, schedule=schedule,
                        total_steps=total_steps if total_steps is not None else step0 + steps, loss_trace=trace,
-                       stream=stream)
+                       stream=stream, prior=prior)
     hist = []
     if log_every and steps > 0:
         tr = trace.cpu().numpy()

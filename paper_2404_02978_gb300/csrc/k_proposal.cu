@@ -35,7 +35,7 @@ __host__ __device__ inline MlpView mlp_view(float* P, int C)
 }
 
 // ------------------------------------------------------------------ init
-__global__ void k_mlp_init(int C, uint64_t seed, float* __restrict__ P)
+__global__ void k_mlp_init(int C, uint64_t seed, float out_scale, float* __restrict__ P)
 {
     const int64_t n = mlp_params(C);
     const int64_t e1 = 6 * kHid, e2 = e1 + kHid, e3 = e2 + kHid * kHid, e4 = e3 + kHid, e5 = e4 + (int64_t)kHid * C;
@@ -51,6 +51,7 @@ __global__ void k_mlp_init(int C, uint64_t seed, float* __restrict__ P)
             const float U1 = (float)((w.w0 >> 8) + 1u) * 0x1p-24f;
             const float U2 = (float)(w.w1 >> 8) * 0x1p-24f;
             v = sqrtf(-2.0f * logf(U1)) * cospif(2.0f * U2) * sqrtf(2.0f / (float)fan);
+            if (i >= e4) v *= out_scale;  // the output layer's weights
         }
         P[i] = v;
     }
@@ -77,7 +78,9 @@ __global__ void k_features(const double* __restrict__ geom, int64_t n, float* __
 // op(B) [K][N] (B stored [K][N], or [N][K] if TB); epilogue: + bias[n],
 // relu, multiply by (mask[m][n] > 0).  64 x 64 tiles, 16-deep K steps,
 // 256 threads with 4 x 4 outputs each; ragged edges bounds-checked.
-enum { kEpiNone = 0, kEpiBias = 1, kEpiRelu = 2, kEpiMask = 4 };
+// epilogue: + bias[n], relu, multiply by (mask[m][n] > 0), + add[m][n] (the
+// `mask` pointer carries the addend for kEpiAdd)
+enum { kEpiNone = 0, kEpiBias = 1, kEpiRelu = 2, kEpiMask = 4, kEpiAdd = 8 };
 
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda,
@@ -139,6 +142,7 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
             if (EPI & kEpiBias) v += bias[n];
             if (EPI & kEpiRelu) v = fmaxf(v, 0.0f);
             if (EPI & kEpiMask) v = mask[(int64_t)m * ldm + n] > 0.0f ? v : 0.0f;
+            if (EPI & kEpiAdd) v += mask[(int64_t)m * ldm + n];
             Cm[(int64_t)m * ldc + n] = v;
         }
     }
@@ -420,9 +424,75 @@ static double vk_c()
            std::pow(24.0 / 5.0 * std::tgamma(6.0 / 5.0), 5.0 / 6.0);
 }
 
-// Forward pass into workspace (X, H1, H2) and Z.
+// ------------------------------------------------------------------ prior
+// One CTA per geometry: per importance cell the mean over kPriorNodes points
+// of g = W(rho) A(pi D rho)^2 (1 - cos(2 pi rho |B| cos phi)) rho^2, the cell's
+// share of the differential-piston structure function at B up to a constant
+// (Sec. 4.4 with the Eq. 7 filter); then log(v / max v), floored at kPriorFloor.
+// Node m sits at (u, t) = ((i_rho + s_x) / n_rho, (i_theta + s_y) / n_theta),
+// (s_x, s_y) point m of the R2 sequence of Eq. 6 from (1/2, 1/2) (0.64 fixed
+// point, top 24 bits); rho = fmin (fmax/fmin)^u; phi = 2 pi t / fold (the
+// sector of the baseline frame; mirror images hold the same values) or
+// 2 pi t - atan2(By, Bx) for fold 0.  The phase rho |B| cos phi is reduced to
+// [-1/2, 1/2] turn, and 1 - cos is taken as 2 sin^2 (no cancellation where the
+// phase is small).
+constexpr int kPriorNodes = 64;
+constexpr float kPriorFloor = -60.0f;
+
+__global__ void __launch_bounds__(256) k_prop_prior(const double* __restrict__ geom, int psd_kind, double c_vk,
+                                                    float fmin, float l2, int n_rho, int n_theta, int fold,
+                                                    float* __restrict__ out)
+{
+    __shared__ float s_node[kPriorNodes][2];
+    __shared__ float red[32];
+    __shared__ float s_pc, s_pa, s_D, s_B, s_phiB;
+    if (threadIdx.x < kPriorNodes) {
+        const uint64_t m = threadIdx.x;
+        s_node[m][0] = (float)((0x8000000000000000ULL + m * kR2StepX) >> 40) * 0x1p-24f;
+        s_node[m][1] = (float)((0x8000000000000000ULL + m * kR2StepY) >> 40) * 0x1p-24f;
+    }
+    if (threadIdx.x == 0) {
+        const double* g = geom + 5 * (int64_t)blockIdx.x;
+        s_pc = (float)(c_vk * pow(g[0], -5.0 / 3.0));
+        s_pa = psd_kind == kPsdKolmogorov ? 0.0f : (float)(1.0 / (g[1] * g[1]));
+        s_D = (float)g[2];
+        s_B = (float)hypot(g[3], g[4]);
+        s_phiB = (float)atan2(g[4], g[3]);
+    }
+    __syncthreads();
+    const int C = n_rho * n_theta;
+    float* o = out + (int64_t)blockIdx.x * C;
+    const float pc = s_pc, pa = s_pa, D = s_D, B = s_B, phiB = s_phiB;
+    const float dphi = fold ? 6.28318530717958648f / (float)fold : 6.28318530717958648f;
+    float vmax = 0.0f;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        const int ir = c / n_theta, it = c - ir * n_theta;
+        float v = 0.0f;
+        for (int m = 0; m < kPriorNodes; ++m) {
+            const float u = ((float)ir + s_node[m][0]) / (float)n_rho;
+            const float t = ((float)it + s_node[m][1]) / (float)n_theta;
+            const float rho = fmin * exp2f(u * l2);
+            const float phi = fold ? t * dphi : t * dphi - phiB;
+            const float A = airy_g(3.14159265358979f * D * rho);
+            const float ph = rho * B * __cosf(phi);
+            const float sn = sinpif(ph - rintf(ph));  // 1 - cos 2 pi ph = 2 sin^2 pi ph, without cancellation
+            v += psd_w(pc, pa, rho * rho) * A * A * (2.0f * sn * sn) * rho * rho;
+        }
+        v *= 1.0f / (float)kPriorNodes;
+        o[c] = v;
+        vmax = fmaxf(vmax, v);
+    }
+    vmax = block_reduce(vmax, red, true);
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        const float v = o[c];
+        o[c] = v > 0.0f && vmax > 0.0f ? fmaxf(logf(v / vmax), kPriorFloor) : kPriorFloor;
+    }
+}
+
+// Forward pass into workspace (X, H1, H2) and Z (+ prior [n][C] when non-NULL).
 static cudaError_t mlp_forward(int C, const float* P, const double* geom, int64_t n, float* X, float* H1, float* H2,
-                               float* Z, cudaStream_t s)
+                               float* Z, cudaStream_t s, const float* prior = nullptr)
 {
     MlpView w = mlp_view(const_cast<float*>(P), C);
     const int N = (int)n;
@@ -430,7 +500,10 @@ static cudaError_t mlp_forward(int C, const float* P, const double* geom, int64_
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = sgemm<false, false, kEpiBias | kEpiRelu>(N, kHid, 6, X, 6, w.W1, kHid, H1, kHid, w.b1, nullptr, 0, s);
     if (e == cudaSuccess) e = sgemm<false, false, kEpiBias | kEpiRelu>(N, kHid, kHid, H1, kHid, w.W2, kHid, H2, kHid, w.b2, nullptr, 0, s);
-    if (e == cudaSuccess) e = sgemm<false, false, kEpiBias>(N, C, kHid, H2, kHid, w.W3, C, Z, C, w.b3, nullptr, 0, s);
+    if (e == cudaSuccess) {
+        if (prior) e = sgemm<false, false, kEpiBias | kEpiAdd>(N, C, kHid, H2, kHid, w.W3, C, Z, C, w.b3, prior, C, s);
+        else e = sgemm<false, false, kEpiBias>(N, C, kHid, H2, kHid, w.W3, C, Z, C, w.b3, nullptr, 0, s);
+    }
     return e;
 }
 
@@ -456,7 +529,8 @@ static size_t mlp_ws_floats(int C, int64_t n)
 // The loss and its gradient (the launches of qrs_mlp_loss_grad) with the
 // workspace at ws (mlp_ws_floats(C, n) floats); *launches counts the kernels.
 static cudaError_t mlp_loss_grad(int C, const float* params, const double* geom, const float* targets, int64_t n,
-                                 float* grad, float* loss, float* ws, cudaStream_t s, int* launches_out)
+                                 float* grad, float* loss, float* ws, cudaStream_t s, int* launches_out,
+                                 const float* prior)
 {
     float* X = ws;
     float* H1 = X + 8 * n;
@@ -470,7 +544,7 @@ static cudaError_t mlp_loss_grad(int C, const float* params, const double* geom,
     MlpView w = mlp_view(const_cast<float*>(params), C);
     MlpView g = mlp_view(grad, C);
     const int N = (int)n;
-    cudaError_t e = mlp_forward(C, params, geom, n, X, H1, H2, Z, s);
+    cudaError_t e = mlp_forward(C, params, geom, n, X, H1, H2, Z, s, prior);
     if (e == cudaSuccess) {
         k_softmax_ce<<<(unsigned)n, 256, 0, s>>>(Z, targets, C, n, dZ, lrow);
         e = cudaGetLastError();
@@ -537,16 +611,17 @@ int64_t qrs_mlp_param_count(int32_t n_cells) { return n_cells >= 1 ? mlp_params(
 
 static bool cells_ok(int32_t C) { return C >= 1 && C <= 16384; }
 
-qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float* params, void* stream)
+qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float out_scale, float* params, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
     qrs::NvtxRange nvtx_range("qrs_mlp_init");
     if (qrs::injected_launch_fault(h, "qrs_mlp_init") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     if (!cells_ok(n_cells) || !params) return fail(h, QRS_ERR_ARG, "n_cells must be in [1, 16384] and params non-NULL");
+    if (!(std::isfinite(out_scale) && out_scale >= 0.0f)) return fail(h, QRS_ERR_ARG, "out_scale must be finite and >= 0");
     cudaError_t e = cudaSetDevice(h->device);
     if (e == cudaSuccess) {
-        k_mlp_init<<<256, 256, 0, (cudaStream_t)stream>>>(n_cells, seed, params);
+        k_mlp_init<<<256, 256, 0, (cudaStream_t)stream>>>(n_cells, seed, out_scale, params);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_init");
@@ -592,7 +667,9 @@ qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_dom
         k_prop_draws<<<(unsigned)std::min<int64_t>((n_rec + 255) / 256, 8192), 256, 0, s>>>(p, n_draws, rec);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && C * sizeof(float) > 48 * 1024)
+    // the histogram is dynamic shared memory beside the kernel's static arrays: the opt-in
+    // limit is raised whatever C is (the default 48 KB covers the sum only for small C)
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_prop_targets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(C * sizeof(float)));
     if (e == cudaSuccess) {
         k_prop_targets<<<(unsigned)n, 512, (size_t)C * sizeof(float), s>>>(rec, n_rec, p.inv_nf, geom, psd->kind, vk_c(),
@@ -606,8 +683,37 @@ qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_dom
     return QRS_OK;
 }
 
-qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, const double* geom, int64_t n,
-                           float* logits, void* stream)
+qrs_status qrs_proposal_prior(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, int32_t n_rho,
+                              int32_t n_theta, int32_t fold, const double* geom, int64_t n, float* prior, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    qrs::NvtxRange nvtx_range("qrs_proposal_prior");
+    if (qrs::injected_launch_fault(h, "qrs_proposal_prior") != QRS_OK) return QRS_ERR_CUDA;
+    h->last_error.clear();
+    if (fold != 0 && fold != 1 && fold != 2 && fold != 4) return fail(h, QRS_ERR_ARG, "fold must be 0, 1, 2 or 4");
+    if (!psd || (psd->kind != QRS_PSD_VON_KARMAN && psd->kind != QRS_PSD_KOLMOGOROV))
+        return fail(h, QRS_ERR_ARG, "psd must be non-NULL with a known kind");
+    if (!dom || dom->kind != QRS_DOMAIN_LOGPOLAR || !(dom->fmin > 0.0 && dom->fmax > dom->fmin && std::isfinite(dom->fmax)))
+        return fail(h, QRS_ERR_ARG, "the prior needs a LOGPOLAR domain with 0 < fmin < fmax");
+    const int64_t C = (int64_t)n_rho * n_theta;
+    if (n_rho < 1 || n_theta < 1 || !cells_ok((int32_t)C) || n < 0 || n > (1 << 24))
+        return fail(h, QRS_ERR_ARG, "n_rho x n_theta in [1, 16384], n in [0, 2^24]");
+    if (n == 0) return QRS_OK;
+    if (!geom || !prior) return fail(h, QRS_ERR_ARG, "geom and prior must be non-NULL");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) {
+        k_prop_prior<<<(unsigned)n, 256, 0, (cudaStream_t)stream>>>(geom, psd->kind, vk_c(), (float)dom->fmin,
+                                                                    (float)std::log2(dom->fmax / dom->fmin), n_rho,
+                                                                    n_theta, fold, prior);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_proposal_prior");
+    ++h->launches;
+    return QRS_OK;
+}
+
+qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, const double* geom,
+                           const float* prior, int64_t n, float* logits, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
     qrs::NvtxRange nvtx_range("qrs_mlp_forward");
@@ -622,14 +728,15 @@ qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, 
     float* H1 = X + 8 * n;
     float* H2 = H1 + kHid * n;
     cudaError_t e = cudaSetDevice(h->device);
-    if (e == cudaSuccess) e = mlp_forward(n_cells, params, geom, n, X, H1, H2, logits, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = mlp_forward(n_cells, params, geom, n, X, H1, H2, logits, (cudaStream_t)stream, prior);
     if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_forward");
     h->launches += 4;
     return QRS_OK;
 }
 
 qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params, const double* geom,
-                             const float* targets, int64_t n, float* grad, float* loss, void* stream)
+                             const float* prior, const float* targets, int64_t n, float* grad, float* loss,
+                             void* stream)
 {
     if (!h) return QRS_ERR_ARG;
     qrs::NvtxRange nvtx_range("qrs_mlp_loss_grad");
@@ -643,7 +750,7 @@ qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params
     cudaError_t e = cudaSetDevice(h->device);
     if (e == cudaSuccess)
         e = mlp_loss_grad(n_cells, params, geom, targets, n, grad, loss, static_cast<float*>(h->d_work),
-                          (cudaStream_t)stream, &launches);
+                          (cudaStream_t)stream, &launches, prior);
     if (e != cudaSuccess) return cuda_fail(h, e, "qrs_mlp_loss_grad");
     h->launches += launches;
     return QRS_OK;
@@ -665,9 +772,9 @@ qrs_status qrs_mlp_adam(qrs_handle* h, int32_t n_cells, float* params, float* m,
     return QRS_OK;
 }
 
-qrs_status qrs_proposal_train(qrs_handle* h, qrs_mlp_state* state, const double* geom, const float* targets, int64_t n,
-                              int64_t steps, double lr, int32_t schedule, int64_t total_steps, float* loss_trace,
-                              void* stream)
+qrs_status qrs_proposal_train(qrs_handle* h, qrs_mlp_state* state, const double* geom, const float* prior,
+                              const float* targets, int64_t n, int64_t steps, double lr, int32_t schedule,
+                              int64_t total_steps, float* loss_trace, void* stream)
 {
     if (!h) return QRS_ERR_ARG;
     qrs::NvtxRange nvtx_range("qrs_proposal_train");
@@ -706,7 +813,7 @@ qrs_status qrs_proposal_train(qrs_handle* h, qrs_mlp_state* state, const double*
                                 : lr;
         float* loss = loss_trace ? loss_trace + (t - state->step - 1) : loss_slot;
         int l = 0;
-        e = mlp_loss_grad(C, state->params, geom, targets, n, grad, loss, wsp, s, &l);
+        e = mlp_loss_grad(C, state->params, geom, targets, n, grad, loss, wsp, s, &l, prior);
         if (e == cudaSuccess) e = launch_adam(C, state->params, state->m, state->v, grad, (float)lr_t, t, s);
         launches += l + 1;
     }

@@ -36,6 +36,9 @@ def test_init_matches_reference(h):
     P = qrs.qrs_mlp_init(h, C, 21).cpu().numpy().astype(np.float64)
     ref = pr.init(C, 21)
     assert np.max(np.abs(P - ref)) <= 4e-6 * np.max(np.abs(ref))
+    P = qrs.qrs_mlp_init(h, C, 21, out_scale=0.01).cpu().numpy().astype(np.float64)
+    ref = pr.init(C, 21, out_scale=0.01)
+    assert np.max(np.abs(P - ref)) <= 4e-6 * np.max(np.abs(ref))
 
 
 def test_forward_loss_grad_adam_match_reference(h):
@@ -61,6 +64,41 @@ def test_forward_loss_grad_adam_match_reference(h):
     P2, m2, v2 = pr.adam(P, np.zeros_like(P), np.zeros_like(P), Gg, 1e-3, 1)
     P2, m2, v2 = pr.adam(P2, m2, v2, Gg, 1e-3, 2)
     assert np.max(np.abs(Pd.cpu().numpy() - P2)) <= 1e-6 + 1e-5 * np.max(np.abs(P2 - P))
+
+
+@pytest.mark.parametrize("fold", [0, 4])
+def test_prior_matches_reference(h, fold):
+    """The logit prior against the FP64 quadrature: equal log cell values where the
+    cell matters (above e^-25 of the largest), within 0.02 -- FP32 node positions
+    (24 bits) and phases rho |B| cos phi of up to ~2000 cycles move a node's
+    (1 - cos) by a few 1e-3 in the most oscillatory cells; the floor where both
+    are negligible."""
+    g = _geom(6, 21)
+    g[0, 3:] = (150.0, 80.0)  # a long baseline: oscillatory cells
+    p = qrs.params(psd="von_karman", **DOM)
+    got = qrs.qrs_proposal_prior(h, p, 48, 16, _dev(g, torch.float64), fold=fold).cpu().numpy().astype(np.float64)
+    ref = pr.prior("von_karman", (1e-3, 10.0), 48, 16, fold, g)
+    assert np.allclose(got.max(axis=1), 0.0, atol=1e-6)
+    m = ref > -25.0
+    assert np.max(np.abs(got - ref)[m]) <= 0.02
+    assert np.all(got[~m] <= -20.0)
+
+
+def test_forward_loss_grad_with_prior_match_reference(h):
+    rng = np.random.default_rng(4)
+    P = (pr.init(C, 6) + 0.02 * rng.normal(size=pr.param_count(C))).astype(np.float32).astype(np.float64)
+    g = _geom(200, 7)
+    T = rng.dirichlet(np.ones(C) * 0.5, size=200).astype(np.float32).astype(np.float64)
+    prior = (3.0 * rng.normal(size=(200, C))).astype(np.float32).astype(np.float64)
+    Pd, gd, Td, prd = _dev(P), _dev(g, torch.float64), _dev(T), _dev(prior)
+    Z = qrs.qrs_mlp_forward(h, C, Pd, gd, prior=prd).cpu().numpy()
+    Zr = pr.forward(P, g, C, prior=prior)
+    assert np.max(np.abs(Z - Zr)) <= 2e-5 * np.max(np.abs(Zr))
+    grad, loss = qrs.qrs_mlp_loss_grad(h, C, Pd, gd, Td, prior=prd)
+    L, G = pr.loss_grad(P, g, T, C, prior=prior)
+    assert float(loss.item()) == pytest.approx(L, rel=2e-5)
+    for a, b in zip(pr.unpack(grad.cpu().numpy().astype(np.float64), C), pr.unpack(G, C)):
+        assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b) + 1e-12
 
 
 @pytest.mark.parametrize("kind,fold", [("mean", 0), ("rms", 0), ("rms", 4), ("mean", 2), ("rms", 1)])
@@ -145,6 +183,43 @@ def test_trained_proposal_lowers_structure_function_error(h, fold):
         assert rms[("learned", 256)] <= 1.3 * rms[("plain", 1024)]
 
 
+def test_proposal_with_prior_reaches_four_times_fewer_terms(h):
+    """The proposal of the benchmark: 256 x 32 cells in the baseline frame over
+    four mirrored sectors, logits = the per-cell prior + the network, trained on
+    2000 geometries' RMS targets from plain draws (4000 cosine-scheduled Adam
+    steps, output layer started at 1/100 of He so the density starts at the
+    prior), density softmax(logits) with eps = 0.05.  On 48 held-out geometries
+    the importance draw at N_f terms reaches the plain draw's matched SF error
+    at 4 N_f for N_f = 256, 512 and 1024."""
+    from oracle import analytic as an
+    nr, nt, Cp = 256, 32, 256 * 32
+    gtr, gte = _geom(2000, 1), _geom(48, 2)
+    dom = qrs.params(**DOM)
+    T = qrs.qrs_proposal_targets(h, dom, nr, nt, 77, 4096, 1024, _dev(gtr, torch.float64), kind="rms", fold=4)
+    Ptr = qrs.qrs_proposal_prior(h, dom, nr, nt, _dev(gtr, torch.float64), fold=4)
+    Pte = qrs.qrs_proposal_prior(h, dom, nr, nt, _dev(gte, torch.float64), fold=4)
+    P, hist = qrs.train_proposal(h, Cp, _dev(gtr, torch.float64), T, steps=4000, lr=2e-3, seed=3, log_every=1000,
+                                 schedule="cosine", prior=Ptr, out_scale=0.01)
+    assert hist[-1][1] <= hist[0][1]
+    logits = qrs.qrs_mlp_forward(h, Cp, P, _dev(gte, torch.float64), prior=Pte)
+    err = {}
+    for i, (r0, L0, D, Bx, By) in enumerate(gte):
+        Dref = an.piston_sf(np.hypot(Bx, By), r0, L0, D, 0.0, 1e-3, 10.0)
+        p = qrs.params(r0=r0, L0=L0, seed=1000 + i, **DOM)
+        cdf = qrs.qrs_proposal_cdf(h, nr, nt, logits[i].contiguous(), 0.05, beta=1.0)
+        pi = dict(p, sampler="importance", n_rho=nr, n_theta=nt, cdf=cdf, fold=4,
+                  frame=float(np.arctan2(By, Bx) / (2 * np.pi)))
+        for name, pp, nfs in (("plain", p, (1024, 2048, 4096)), ("learned", pi, (256, 512, 1024))):
+            for nf in nfs:
+                d = qrs.qrs_draw(h, pp, nf, 8, outputs=("f_xy", "amp"))
+                e = (_cond_sf(d["f_xy"], d["amp"], D, (Bx, By)).cpu().numpy() - Dref) / Dref
+                err.setdefault((name, nf), []).append(np.mean(e ** 2))
+    rms = {k: float(np.sqrt(np.mean(v))) for k, v in err.items()}
+    print("matched SF error with the prior:", rms)
+    for nf in (256, 512, 1024):
+        assert rms[("learned", nf)] <= rms[("plain", 4 * nf)], nf
+
+
 def test_training_checkpoint_resumes_exactly(h, tmp_path):
     """20 Adam steps in one run equal 10 steps, a checkpoint written and read
     back through libqrs (qrs_mlp_save / qrs_mlp_load), and 10 more, on the
@@ -178,14 +253,16 @@ def test_training_in_one_c_call_equals_step_by_step(h):
     T = torch.softmax(torch.randn(n, C, device="cuda", generator=torch.Generator("cuda").manual_seed(4)), 1)
     P0 = qrs.qrs_mlp_init(h, C, 7)
     f = qrs.load().qrs_proposal_train
-    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(qrs.QrsMlpState), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
-                  ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(qrs.QrsMlpState), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_void_p]
     f.restype = ctypes.c_int
     p1, m1, v1 = P0.clone(), torch.zeros_like(P0), torch.zeros_like(P0)
     trace = torch.full((steps,), float("nan"), device="cuda")
     st = qrs.QrsMlpState(C, 0, 0, p1.data_ptr(), m1.data_ptr(), v1.data_ptr())
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    assert f(h.h, ctypes.byref(st), g.data_ptr(), T.data_ptr(), n, steps, lr, 1, total, trace.data_ptr(), stream) == 0
+    assert f(h.h, ctypes.byref(st), g.data_ptr(), None, T.data_ptr(), n, steps, lr, 1, total, trace.data_ptr(),
+             stream) == 0
     assert st.step == steps
     p2, m2, v2 = P0.clone(), torch.zeros_like(P0), torch.zeros_like(P0)
     grad, loss = torch.empty_like(P0), torch.empty(1, device="cuda")
@@ -199,6 +276,6 @@ def test_training_in_one_c_call_equals_step_by_step(h):
     assert torch.equal(trace, torch.cat(losses))
     # argument errors launch nothing
     st_bad = qrs.QrsMlpState(C, 0, 0, p1.data_ptr(), m1.data_ptr(), v1.data_ptr())
-    assert f(h.h, ctypes.byref(st_bad), g.data_ptr(), T.data_ptr(), n, 5, lr, 1, 4, None, stream) == -1
-    assert f(h.h, ctypes.byref(st_bad), g.data_ptr(), T.data_ptr(), n, 5, -1.0, 0, 0, None, stream) == -1
+    assert f(h.h, ctypes.byref(st_bad), g.data_ptr(), None, T.data_ptr(), n, 5, lr, 1, 4, None, stream) == -1
+    assert f(h.h, ctypes.byref(st_bad), g.data_ptr(), None, T.data_ptr(), n, 5, -1.0, 0, 0, None, stream) == -1
     assert st_bad.step == 0
