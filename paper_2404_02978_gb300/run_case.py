@@ -11,8 +11,9 @@ from paper_2404_02978_gb300 import workloads as wl
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="phase_screen", choices=["phase_screen", "piston_plain", "gemm_screen", "batched", "grid_screen"])
-    ap.add_argument("--mode", default="gemm_3xtf32", choices=["gemm_3xtf32", "gemm_bf16x3"])
+    ap.add_argument("--case", default="phase_screen",
+                    choices=["phase_screen", "piston_plain", "gemm_screen", "batched", "grid_screen", "fft_screen"])
+    ap.add_argument("--mode", default="gemm_3xtf32", choices=["gemm_3xtf32", "gemm_bf16x3", "gemm_tf32"])
     ap.add_argument("--points", type=int, default=0, help="gemm_screen: first N points only (0 = all)")
     ap.add_argument("--n-real", type=int, default=16)
     ap.add_argument("--n-inst", type=int, default=1000, help="batched: number of interferometers")
@@ -48,6 +49,10 @@ def main():
         for i in range(a.repeat):
             qrs.qrs_synthesize_grid(h, wl.method_params(cfg), cfg["n_f"], a.n_real, cd, cd, index=idx,
                                     mode=a.mode, real_offset=i * a.n_real)
+    elif a.case == "fft_screen":
+        p = qrs.params(seed=21, r0=0.15, L0=30.0)
+        for i in range(a.repeat):
+            qrs.fft_screens(h, p, 256, 8.0 / 256, a.n_real, real_offset=i * a.n_real)
     elif a.case == "batched":
         cfg = wl.BATCHED
         dev = lambda v: torch.from_numpy(v).cuda()
