@@ -183,6 +183,25 @@ qrs_status qrs_sync(qrs_handle* h, void* stream);
 /* Number of kernel launches this handle has enqueued since creation. */
 int64_t qrs_launch_count(const qrs_handle* h);
 
+/* --------------------------------------------------- bounds-checked build ---
+ * libqrs_checked.so is the same library compiled with QRS_CHECKED=1: in its
+ * kernels the computed index of every global- and shared-memory access the
+ * kernels make through their checked accessors (inputs, outputs, draw
+ * records, shared-memory term tables and operand tiles, bulk copies) is
+ * tested against the extent of its buffer before use.  An index out of range
+ * is not used (the access goes to a scratch sink) and QRS_ERR_DEVICE_CHECK
+ * is recorded in the device error word of the handle created last, reported
+ * by qrs_sync.  It is slower; results of valid calls are those of the
+ * default build.
+ * qrs_checked_build: 1 in the checked library, 0 in libqrs.so.
+ * qrs_check_selftest: checked library only (QRS_ERR_ARG in the default build,
+ * nothing launched): one thread stores through the checked accessor into an
+ * 8-float scratch of the handle at index i; i outside [0, 8) must record
+ * QRS_ERR_DEVICE_CHECK (seen at the next qrs_sync) and leave the scratch
+ * untouched -- a test of the checking machinery, not of a kernel. */
+int32_t qrs_checked_build(void);
+qrs_status qrs_check_selftest(qrs_handle* h, int64_t i, void* stream);
+
 /* ---------------------------------------------------------------- draw ---
  * The frequency draw of n_real realisations x n_f terms (Eq. 3 weights, Eq. 5/6
  * placement, Sec. 3.2 continuation), realisations real_offset .. +n_real-1.

@@ -25,7 +25,8 @@ __all__ = ["params", "Handle", "qrs_create", "qrs_draw", "qrs_synthesize_points"
            "qrs_pair_diff", "qrs_choose_n", "qrs_fft_spectrum", "fft_screens", "qrs_nearest_neighbour", "qrs_star_discrepancy", "qrs_structure_fn", "qrs_sync", "QrsError", "lib_path", "load"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libqrs.so")
+# QRS_CHECKED=1 loads the bounds-checked build of the same library
+_LIB_PATH = os.path.join(_HERE, "libqrs_checked.so" if os.environ.get("QRS_CHECKED") == "1" else "libqrs.so")
 
 PSD = {"von_karman": 0, "kolmogorov": 1}
 DOMAIN = {"square": 0, "disc": 1, "logpolar": 2}
@@ -98,6 +99,9 @@ def load():
         L.qrs_sync.argtypes = [vp, vp]
         L.qrs_launch_count.argtypes = [vp]
         L.qrs_launch_count.restype = i64
+        L.qrs_checked_build.argtypes = []
+        L.qrs_checked_build.restype = i32
+        L.qrs_check_selftest.argtypes = [vp, i64, vp]
         L.qrs_draw.argtypes = [vp, C.POINTER(QrsPsd), C.POINTER(QrsDomain), C.POINTER(QrsSampler), i64, i64, i64,
                                C.POINTER(QrsDrawOut), vp]
         L.qrs_synthesize_points.argtypes = [vp, C.POINTER(QrsPsd), C.POINTER(QrsDomain), C.POINTER(QrsSampler),
@@ -195,6 +199,18 @@ def qrs_create(device=0) -> Handle:
 
 def qrs_sync(h: Handle, stream=None):
     h._check(h.L.qrs_sync(h.h, _stream(stream)))
+
+
+def checked_build() -> bool:
+    """True when the loaded library is the bounds-checked build (QRS_CHECKED=1)."""
+    return bool(load().qrs_checked_build())
+
+
+def qrs_check_selftest(h: Handle, i: int, stream=None):
+    """Checked build only: one store through the checked accessor at index i
+    of an 8-float scratch (include/qrs.h); i outside [0, 8) is reported by the
+    next qrs_sync as QRS_ERR_DEVICE_CHECK."""
+    h._check(h.L.qrs_check_selftest(h.h, int(i), _stream(stream)))
 
 
 def qrs_draw(h: Handle, p, n_f, n_real, real_offset=0, outputs=("f_xy", "amp", "coef", "cell"), stream=None):

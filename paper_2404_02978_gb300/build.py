@@ -76,5 +76,20 @@ def build(force: bool = False, verbose: bool = False, extra=(), out: str = None,
     return OUT_
 
 
+CHECKED_OUT = os.path.join(HERE, "libqrs_checked.so")
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """The bounds-checked library (QRS_CHECKED=1, libqrs_checked.so): every
+    checked accessor in the kernels tests its index against its buffer's
+    extent (include/qrs.h, "bounds-checked build").  Loaded by the binding
+    instead of libqrs.so when QRS_CHECKED=1 is set in the environment."""
+    if not force and os.path.exists(CHECKED_OUT) and all(
+            os.path.getmtime(d) <= os.path.getmtime(CHECKED_OUT) for d in _deps()):
+        return CHECKED_OUT
+    return build(verbose=verbose, extra=["-DQRS_CHECKED=1"], out=CHECKED_OUT,
+                 build_dir=os.path.join(HERE, "_build_checked"))
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))

@@ -6,6 +6,8 @@
 
 namespace qrs {
 
+QRS_CHECK_HOOK(check_hook_draw)
+
 __global__ void k_draw(DrawParams p, int64_t n_real, float* __restrict__ f_xy, float* __restrict__ amp,
                        float* __restrict__ coef, int32_t* __restrict__ cell, uint32_t* __restrict__ words,
                        uint64_t* __restrict__ r2)
@@ -17,12 +19,12 @@ __global__ void k_draw(DrawParams p, int64_t n_real, float* __restrict__ f_xy, f
         Words w;
         uint64_t Sx, Sy;
         const Term t = draw_term(p, n, k, &w, &Sx, &Sy);
-        if (f_xy) reinterpret_cast<float2*>(f_xy)[i] = make_float2(t.fx, t.fy);
-        if (amp) amp[i] = t.F;
-        if (coef) reinterpret_cast<float2*>(coef)[i] = make_float2(t.a, t.b);
-        if (cell) cell[i] = t.cell;
-        if (words) reinterpret_cast<uint4*>(words)[i] = make_uint4(w.w0, w.w1, w.w2, w.w3);
-        if (r2) { r2[2 * i] = Sx; r2[2 * i + 1] = Sy; }
+        if (f_xy) *chk(reinterpret_cast<float2*>(f_xy), i, total) = make_float2(t.fx, t.fy);
+        if (amp) *chk(amp, i, total) = t.F;
+        if (coef) *chk(reinterpret_cast<float2*>(coef), i, total) = make_float2(t.a, t.b);
+        if (cell) *chk(cell, i, total) = t.cell;
+        if (words) *chk(reinterpret_cast<uint4*>(words), i, total) = make_uint4(w.w0, w.w1, w.w2, w.w3);
+        if (r2) { *chk(r2, 2 * i, 2 * total) = Sx; *chk(r2, 2 * i + 1, 2 * total) = Sy; }
     }
 }
 

@@ -19,6 +19,8 @@
 
 namespace qrs {
 
+QRS_CHECK_HOOK(check_hook_fft)
+
 constexpr uint32_t kStreamFft = 4u;
 
 __global__ void k_fft_spectrum(float psd_c, float psd_a, float ap_D, float ap_d, float df, int64_t n, int64_t total,
@@ -44,7 +46,7 @@ __global__ void k_fft_spectrum(float psd_c, float psd_a, float ap_D, float ap_d,
             if (ap_D > 0.0f) F *= airy_filter(sqrtf(f2), ap_D, ap_d);
             v = make_float2(F * (rad * cb), F * (rad * sb));
         }
-        spec[e] = v;
+        *chk(spec, e, total) = v;
     }
 }
 

@@ -72,6 +72,8 @@
 
 namespace qrs {
 
+QRS_CHECK_HOOK(check_hook_gemm)
+
 constexpr int kGM = 128;                                   // points per tile (UMMA M, TMEM lanes)
 constexpr int kGN = 256;                                   // columns per block (UMMA N)
 constexpr int kGStages = 2;
@@ -118,20 +120,21 @@ __global__ void k_gemm_freq(DrawParams p, int64_t nf_pad, const float* __restric
         if (k < p.n_f) {
             const Term t = draw_term<false>(p, n0 + (uint64_t)k, k);
             if (z.use_fixed)
-                fbasis[k] = make_int2(__float2int_rn(t.fx * z.fscale), __float2int_rn(t.fy * z.fscale));
+                *chk(fbasis, k, nf_pad) = make_int2(__float2int_rn(t.fx * z.fscale), __float2int_rn(t.fy * z.fscale));
             else
-                fbasis[k] = make_int2(__float_as_int(t.fx), __float_as_int(t.fy));
-            fw[k] = make_float4(t.fx * t.fx + t.fy * t.fy, t.J, t.A, 0.0f);
+                *chk(fbasis, k, nf_pad) = make_int2(__float_as_int(t.fx), __float_as_int(t.fy));
+            *chk(fw, k, nf_pad) = make_float4(t.fx * t.fx + t.fy * t.fy, t.J, t.A, 0.0f);
         } else {
-            fbasis[k] = make_int2(0, 0);
-            fw[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            *chk(fbasis, k, nf_pad) = make_int2(0, 0);
+            *chk(fw, k, nf_pad) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
     }
 }
 
 template <int PREC>
-__device__ __forceinline__ void split_store(void* hi_base, void* lo_base, int64_t idx, float x)
+__device__ __forceinline__ void split_store(void* hi_base, void* lo_base, int64_t idx, int64_t n, float x)
 {
+    if (!chk_ok(idx, 1, n)) return;
     if (!GemmCfg<PREC>::kSplit) {  // single pass: the TF32 rounding only
         static_cast<uint32_t*>(hi_base)[idx] = tf32_rna_bits(x);
     } else if (GemmCfg<PREC>::kTF32) {
@@ -165,7 +168,7 @@ __global__ void k_gemm_coef(DrawParams p, int64_t nf_pad, int64_t n_real, int64_
     __shared__ float s_c, s_a;
     if (threadIdx.x == 0) {
         if (col_psd && r < n_real) {
-            const double r0 = col_psd[2 * r], L0 = col_psd[2 * r + 1];
+            const double r0 = *chk(col_psd, 2 * r, 2 * n_real), L0 = *chk(col_psd, 2 * r + 1, 2 * n_real);
             s_c = (float)(c_vk * pow(r0, -5.0 / 3.0));
             s_a = p.psd_a == 0.0f ? 0.0f : (float)(1.0 / (L0 * L0));
         } else {
@@ -181,7 +184,7 @@ __global__ void k_gemm_coef(DrawParams p, int64_t nf_pad, int64_t n_real, int64_
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nf_pad; k += (int64_t)gridDim.x * blockDim.x) {
         float cc = 0.0f, cs = 0.0f;
         if (r < n_real && k < p.n_f) {
-            const float4 w = fw[k];
+            const float4 w = *chk(fw, k, nf_pad);
             const float F = sqrtf(psd_w(pc, pa, w.x) * w.y * p.inv_nf) * w.z;  // w.z: aperture filter
             const float2 ab = draw_coef(p, (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k);
             cc = F * ab.x;
@@ -189,8 +192,8 @@ __global__ void k_gemm_coef(DrawParams p, int64_t nf_pad, int64_t n_real, int64_
         }
         const int64_t c = k / T, j = k - c * T;
         const int64_t row = r * Kp;
-        split_store<PREC>(hi, lo, row + c * 2 * T + j, cc);
-        split_store<PREC>(hi, lo, row + c * 2 * T + T + j, cs);
+        split_store<PREC>(hi, lo, row + c * 2 * T + j, R_pad * Kp, cc);
+        split_store<PREC>(hi, lo, row + c * 2 * T + T + j, R_pad * Kp, cs);
     }
 }
 
@@ -336,8 +339,12 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
                     if (!*abort_flag) timeout();
                     break;
                 }
-                sm100::mbar_arrive_expect_tx(&fullF[f], kFreqChunkBytes);
-                sm100::bulk_load(ringF(i), g.fbasis + i * Cfg::kTermsPerChunk, kFreqChunkBytes, &fullF[f]);
+                if (chk_ok(i * Cfg::kTermsPerChunk, Cfg::kTermsPerChunk, n_chunks * Cfg::kTermsPerChunk)) {
+                    sm100::mbar_arrive_expect_tx(&fullF[f], kFreqChunkBytes);
+                    sm100::bulk_load(ringF(i), g.fbasis + i * Cfg::kTermsPerChunk, kFreqChunkBytes, &fullF[f]);
+                } else {
+                    sm100::mbar_arrive(&fullF[f]);  // checked build: the slot keeps its old frequencies
+                }
                 issued = i + 1;
             }
             if (*abort_flag) {
@@ -379,7 +386,7 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
 #pragma unroll
                     for (int q = 0; q < PC; ++q) {
                         const int64_t r = rblk * kGN + col0 + c0 + q;
-                        if (r < g.n_real) g.out[r * g.P + m] = __uint_as_float(v[q]);
+                        if (r < g.n_real) *chk(g.out, r * g.P + m, g.n_real * g.P) = __uint_as_float(v[q]);
                     }
                 }
             }
@@ -396,7 +403,7 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
         constexpr int kGroups = 4 / (kGProducers / 4);
         const int grp0 = (pw >> 2) * kGroups;      // its term groups [grp0, grp0 + kGroups)
         const int64_t m = tile * kGM + row;
-        const float2 pt = (m < g.P) ? g.xy[m] : make_float2(0.0f, 0.0f);
+        const float2 pt = (m < g.P) ? *chk(g.xy, m, g.P) : make_float2(0.0f, 0.0f);
         const FixedScales z = fixed_scales(g.fbound, *g.d_xbound, true);
         const int32_t X = __float2int_rn(pt.x * z.xscale), Y = __float2int_rn(pt.y * z.xscale);
         constexpr int TPG = Cfg::kTermsPer16B;
@@ -420,7 +427,8 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
                 float cv[TPG], sv[TPG];
 #pragma unroll
                 for (int t = 0; t < TPG; t += 2) {  // two terms per paired FP32 instruction
-                    const int2 f0 = fb[grp * TPG + t], f1 = fb[grp * TPG + t + 1];
+                    const int2 f0 = *chk(fb, grp * TPG + t, Cfg::kTermsPerChunk);
+                    const int2 f1 = *chk(fb, grp * TPG + t + 1, Cfg::kTermsPerChunk);
                     float2 ang;
                     if (z.use_fixed) {
                         const uint32_t m0 = phase_fx_word(f0.x, f0.y, X, Y, z.bias, z.shift);
@@ -442,11 +450,15 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
                 const uint32_t os = sm100::sw128_offset((uint32_t)row, (uint32_t)(4 + grp));
                 uint4 hi, lo;
                 pack16<PREC>(cv, hi, lo);
-                *reinterpret_cast<uint4*>(Ahi + oc) = hi;
-                if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + oc) = lo;
+                if (chk_ok(oc, 16, kGTileA)) {
+                    *reinterpret_cast<uint4*>(Ahi + oc) = hi;
+                    if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + oc) = lo;
+                }
                 pack16<PREC>(sv, hi, lo);
-                *reinterpret_cast<uint4*>(Ahi + os) = hi;
-                if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + os) = lo;
+                if (chk_ok(os, 16, kGTileA)) {
+                    *reinterpret_cast<uint4*>(Ahi + os) = hi;
+                    if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + os) = lo;
+                }
             }
             sm100::fence_proxy_async_smem();  // each thread: its row writes -> async proxy
             __syncwarp();

@@ -67,6 +67,8 @@
 
 namespace qrs {
 
+QRS_CHECK_HOOK(check_hook_grid)
+
 constexpr int kXM = 128;                                  // x values per tile (UMMA M, TMEM lanes)
 constexpr int kXN = 256;                                  // y values per block (UMMA N)
 constexpr int kXStages = 2;
@@ -97,6 +99,8 @@ struct GridArgs {
     int64_t n_chunks;      // K chunks per realisation
     int64_t nf_pad;
     int64_t n_mt, n_nb, n_items;
+    int64_t out_rows;      // realisations in `out` (bounds-checked build)
+    int64_t rec_rows;      // realisations in this slab of `rec`
     const int4* rec;       // [slab realisations][nf_pad] {Fx|fx, Fy|fy, F a, F b}
     float* master;         // [gridDim.x][kXN][kXM] FP32 accumulators of the CTAs' current items
     const float* d_bound;
@@ -147,7 +151,7 @@ __global__ void k_grid_draw(DrawParams p, int64_t n_real, int64_t nf_pad, const 
             v.z = __float_as_int(t.F * t.a);
             v.w = __float_as_int(t.F * t.b);
         }
-        rec[q] = v;
+        *chk(rec, q, total) = v;
     }
 }
 
@@ -174,18 +178,19 @@ __device__ __forceinline__ float phase1_rad(int32_t F, int32_t X, float f, float
 // the harmonic of coordinate x (SIDE 0: fx x, SIDE 1: fy y) for the chunk's
 // terms, plain (cos | sin) or, with COEF, weighted by the coefficients
 // (F(a cos - b sin) | -F(a sin + b cos)); split hi/lo into the swizzled tile.
-template <int PREC, bool FIXED, int SIDE, bool COEF, int NG>
+template <int PREC, bool FIXED, int SIDE, bool COEF, int NG, int TILE_BYTES>
 __device__ __forceinline__ void produce_row(const int4* __restrict__ rr, unsigned char* hi_t, unsigned char* lo_t,
                                             int row, int g0, int32_t Xq, float xf, uint64_t bias, uint32_t shift)
 {
     constexpr int TPG = GemmCfg<PREC>::kTermsPer16B;
+    constexpr int T = GemmCfg<PREC>::kTermsPerChunk;
 #pragma unroll
     for (int gi = 0; gi < NG; ++gi) {
         const int grp = g0 + gi;
         float cv[TPG], sv[TPG];
 #pragma unroll
         for (int t = 0; t < TPG; ++t) {
-            const int4 r = rr[grp * TPG + t];
+            const int4 r = *chk(rr, grp * TPG + t, T);
             const int32_t fq = SIDE == 0 ? r.x : r.y;
             const float ang = phase1_rad<FIXED>(fq, Xq, __int_as_float(fq), xf, bias, shift);
             const float sn = __sinf(ang), cs = __cosf(ang);
@@ -202,11 +207,15 @@ __device__ __forceinline__ void produce_row(const int4* __restrict__ rr, unsigne
         const uint32_t oc = sm100::sw128_offset((uint32_t)row, (uint32_t)grp);
         const uint32_t os = sm100::sw128_offset((uint32_t)row, (uint32_t)(4 + grp));
         pack16<PREC>(cv, h, l);
-        *reinterpret_cast<uint4*>(hi_t + oc) = h;
-        *reinterpret_cast<uint4*>(lo_t + oc) = l;
+        if (chk_ok(oc, 16, TILE_BYTES)) {
+            *reinterpret_cast<uint4*>(hi_t + oc) = h;
+            *reinterpret_cast<uint4*>(lo_t + oc) = l;
+        }
         pack16<PREC>(sv, h, l);
-        *reinterpret_cast<uint4*>(hi_t + os) = h;
-        *reinterpret_cast<uint4*>(lo_t + os) = l;
+        if (chk_ok(os, 16, TILE_BYTES)) {
+            *reinterpret_cast<uint4*>(hi_t + os) = h;
+            *reinterpret_cast<uint4*>(lo_t + os) = l;
+        }
     }
 }
 
@@ -221,14 +230,14 @@ __device__ __forceinline__ void produce_share(const int4* __restrict__ rr, unsig
 {
     constexpr bool CX = kXCoefX, CY = !kXCoefX;
     if (kXProducers == 8) {
-        produce_row<PREC, FIXED, 0, CX, 2>(rr, Ahi, Alo, t & 127, 2 * (t >> 7), XA, xa, bias, shift);
-        produce_row<PREC, FIXED, 1, CY, 4>(rr, Bhi, Blo, t, 0, YB, yb, bias, shift);
+        produce_row<PREC, FIXED, 0, CX, 2, kXTileA>(rr, Ahi, Alo, t & 127, 2 * (t >> 7), XA, xa, bias, shift);
+        produce_row<PREC, FIXED, 1, CY, 4, kXTileB>(rr, Bhi, Blo, t, 0, YB, yb, bias, shift);
     } else if (kXProducers == 12) {
-        if (t < kXM) produce_row<PREC, FIXED, 0, CX, 4>(rr, Ahi, Alo, t, 0, XA, xa, bias, shift);
-        else produce_row<PREC, FIXED, 1, CY, 4>(rr, Bhi, Blo, t - kXM, 0, YB, yb, bias, shift);
+        if (t < kXM) produce_row<PREC, FIXED, 0, CX, 4, kXTileA>(rr, Ahi, Alo, t, 0, XA, xa, bias, shift);
+        else produce_row<PREC, FIXED, 1, CY, 4, kXTileB>(rr, Bhi, Blo, t - kXM, 0, YB, yb, bias, shift);
     } else {
-        if (t < 2 * kXM) produce_row<PREC, FIXED, 0, CX, 2>(rr, Ahi, Alo, t & 127, 2 * (t >> 7), XA, xa, bias, shift);
-        else produce_row<PREC, FIXED, 1, CY, 4>(rr, Bhi, Blo, t - 2 * kXM, 0, YB, yb, bias, shift);
+        if (t < 2 * kXM) produce_row<PREC, FIXED, 0, CX, 2, kXTileA>(rr, Ahi, Alo, t & 127, 2 * (t >> 7), XA, xa, bias, shift);
+        else produce_row<PREC, FIXED, 1, CY, 4, kXTileB>(rr, Bhi, Blo, t - 2 * kXM, 0, YB, yb, bias, shift);
     }
 }
 
@@ -354,8 +363,12 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                         stop = true;
                         break;
                     }
-                    sm100::mbar_arrive_expect_tx(&fullR[f], (uint32_t)(T * 16));
-                    sm100::bulk_load(ringR(gc), src + i * T, (uint32_t)(T * 16), &fullR[f]);
+                    if (chk_ok(r * g.nf_pad + i * T, T, g.rec_rows * g.nf_pad)) {
+                        sm100::mbar_arrive_expect_tx(&fullR[f], (uint32_t)(T * 16));
+                        sm100::bulk_load(ringR(gc), src + i * T, (uint32_t)(T * 16), &fullR[f]);
+                    } else {
+                        sm100::mbar_arrive(&fullR[f]);  // checked build: the slot keeps its old records
+                    }
                 }
             }
             if (*abort_flag) {  // copies in flight land before the CTA exits
@@ -371,6 +384,7 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         const uint32_t col0 = (uint32_t)(((warp - 4) >> 2) * kSpan);
         float* mrow = g.master + (int64_t)blockIdx.x * kXN * kXM + row;  // this thread's master column
+        const int64_t n_master = (int64_t)gridDim.x * kXN * kXM;
         int64_t J = 0;
         bool stop = false;
         for (int64_t it = blockIdx.x; it < g.n_items && !stop; it += gridDim.x) {
@@ -397,7 +411,7 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                     uint32_t v[PC];
                     if (j > 0) {
 #pragma unroll
-                        for (int q = 0; q < PC; ++q) m[q] = mp[q * kXM];
+                        for (int q = 0; q < PC; ++q) m[q] = *chk(g.master, (mp - g.master) + q * kXM, n_master);
                     }
                     sm100::tmem_ld_cols(slot + (uint32_t)c0, v);
                     sm100::tmem_ld_wait();
@@ -407,7 +421,7 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                     }
                     if (!last) {
 #pragma unroll
-                        for (int q = 0; q < PC; ++q) mp[q * kXM] = __uint_as_float(v[q]);
+                        for (int q = 0; q < PC; ++q) *chk(g.master, (mp - g.master) + q * kXM, n_master) = __uint_as_float(v[q]);
                     } else if (xi < g.nx) {
 #pragma unroll
                         for (int q = 0; q < PC; ++q) {
@@ -415,11 +429,11 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                             if (yj < g.ny) {
                                 const int64_t node = yj * g.nx + xi;
                                 if (g.index) {
-                                    const int32_t pidx = g.index[node];
-                                    if (pidx >= 0 && pidx < g.P) g.out[orow * g.P + pidx] = __uint_as_float(v[q]);
+                                    const int32_t pidx = *chk(g.index, node, g.nx * g.ny);
+                                    if (pidx >= 0 && pidx < g.P) *chk(g.out, orow * g.P + pidx, g.out_rows * g.P) = __uint_as_float(v[q]);
                                     else if (pidx >= g.P) atomicExch(g.err, (int)QRS_ERR_DEVICE_CHECK);
                                 } else {
-                                    g.out[orow * g.ny * g.nx + node] = __uint_as_float(v[q]);
+                                    *chk(g.out, orow * g.ny * g.nx + node, g.out_rows * g.ny * g.nx) = __uint_as_float(v[q]);
                                 }
                             }
                         }
@@ -444,8 +458,8 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
             const int64_t r = it / per_real, rem = it - r * per_real;
             const int64_t mt = rem / g.n_nb, nb = rem - mt * g.n_nb;
             const int64_t xi = mt * kXM + xrow, yj = nb * kXN + yrow;
-            const float xa = (xrow >= 0 && xi < g.nx) ? g.x[xi] : 0.0f;
-            const float yb = (yrow >= 0 && yj < g.ny) ? g.y[yj] : 0.0f;
+            const float xa = (xrow >= 0 && xi < g.nx) ? *chk(g.x, xi, g.nx) : 0.0f;
+            const float yb = (yrow >= 0 && yj < g.ny) ? *chk(g.y, yj, g.ny) : 0.0f;
             const int32_t XA = __float2int_rn(xa * z.xscale), YB = __float2int_rn(yb * z.xscale);
             for (int64_t i = 0; i < n_chunks; ++i, ++gc) {
                 const int s = (int)(gc % kXStages);
@@ -487,6 +501,321 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
     }
 }
 
+// ------------------------------------------------------------ CTA pairs
+// k_grid_pair: the same product on a cluster of two CTAs (two SMs) sharing
+// one tcgen05.mma of M = 256 (cta_group::2).  A work item is (realisation,
+// pair of 128-column x tiles, 256-row y block): CTA rank q builds the x rows
+// of tile 2 p + q (with the coefficient products) and y rows [128 q, 128 q +
+// 128) of the block, so each SM produces 256 operand rows per K chunk instead
+// of 384; the even CTA issues the MMAs for both (A: each CTA's own x rows; B:
+// the two y halves), and each CTA's TMEM receives the 128 x 256 accumulator of
+// its own x tile, promoted and stored by its own promoters as in k_grid_main.
+// Three 64 KB stages.  Barriers: the even CTA's full[s] counts both CTAs'
+// producer warps and its seg_free[b] both CTAs' promoter warps (the odd CTA
+// arrives remotely); the MMA commits arrive at empty[s] and seg_full[b] in
+// both CTAs (multicast).  A time-out in either CTA raises both abort flags;
+// both CTAs meet at a cluster barrier before TMEM is freed, so no MMA of the
+// pair is in flight and no remote arrival is pending when either exits.
+#ifndef QRS_GRID_PAIR_PRODUCERS
+#define QRS_GRID_PAIR_PRODUCERS 16  // producer warps per CTA: 8 (whole rows) or 16 (half rows)
+#endif
+
+constexpr int kPStages = 3;
+constexpr int kPHalfN = 128;                                   // y rows per CTA
+constexpr int kPTileA = kXM * 128;                             // 16 KB
+constexpr int kPTileB = kPHalfN * 128;                         // 16 KB
+constexpr int kPStageBytes = 2 * kPTileA + 2 * kPTileB;        // 64 KB
+constexpr int kPProducers = QRS_GRID_PAIR_PRODUCERS;
+constexpr int kPPromoters = 4;
+constexpr int kPThreads = 128 + 32 * (kPPromoters + kPProducers);
+static_assert(kPProducers == 8 || kPProducers == 16, "pair producer warps");
+// The operand stages, then the record ring and barriers, inside a region that
+// extends 16 KB past the last stage's B tile (a read of twice a tile's rows
+// from any tile start stays inside the CTA's allocation).
+constexpr int kPRingOff = kPStages * kPStageBytes;
+constexpr int kPSmemBytes = kPStages * kPStageBytes + 16 * 1024 + 1024;
+static_assert(kPRingOff + kXRecSlots * kXRecBytes + 512 <= kPStages * kPStageBytes + 16 * 1024, "ring fits the pad");
+
+template <int PREC, bool FIXED>
+__device__ __forceinline__ void produce_share_pair(const int4* __restrict__ rr, unsigned char* Ahi, unsigned char* Alo,
+                                                   unsigned char* Bhi, unsigned char* Blo, int t, int32_t XA, float xa,
+                                                   int32_t YB, float yb, uint64_t bias, uint32_t shift)
+{
+    constexpr bool CX = kXCoefX, CY = !kXCoefX;
+    if (kPProducers == 8) {
+        if (t < kXM) produce_row<PREC, FIXED, 0, CX, 4, kPTileA>(rr, Ahi, Alo, t, 0, XA, xa, bias, shift);
+        else produce_row<PREC, FIXED, 1, CY, 4, kPTileB>(rr, Bhi, Blo, t - kXM, 0, YB, yb, bias, shift);
+    } else {
+        if (t < 2 * kXM) produce_row<PREC, FIXED, 0, CX, 2, kPTileA>(rr, Ahi, Alo, t & 127, 2 * (t >> 7), XA, xa, bias, shift);
+        else produce_row<PREC, FIXED, 1, CY, 2, kPTileB>(rr, Bhi, Blo, (t - 2 * kXM) & 127, 2 * ((t - 2 * kXM) >> 7), YB, yb,
+                                                bias, shift);
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kPThreads, 1) k_grid_pair(const __grid_constant__ GridArgs g)
+{
+    using Cfg = GemmCfg<PREC>;
+    constexpr int T = Cfg::kTermsPerChunk;
+    static_assert(T / Cfg::kTermsPer16B == 4, "four 16-byte groups per half row");
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* rring = smem + kPRingOff;
+    uint64_t* full = reinterpret_cast<uint64_t*>(rring + kXRecSlots * kXRecBytes);
+    uint64_t* empty = full + kPStages;
+    uint64_t* seg_full = empty + kPStages;  // [2]
+    uint64_t* seg_free = seg_full + 2;      // [2]
+    uint64_t* fullR = seg_free + 2;
+    uint64_t* freeR = fullR + kXRecSlots;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeR + kXRecSlots);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = sm100::cluster_ctarank();
+    const bool leader = rank == 0;
+    const int64_t cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
+    const int64_t n_chunks = g.n_chunks;
+    const int64_t n_seg = (n_chunks + Cfg::kSeg - 1) / Cfg::kSeg;
+    const int64_t n_mp = (g.n_mt + 1) >> 1;
+    const int64_t per_real = n_mp * g.n_nb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kPStages; ++s) {
+            sm100::mbar_init(&full[s], 2 * kPProducers);
+            sm100::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            sm100::mbar_init(&seg_full[b], 1);
+            sm100::mbar_init(&seg_free[b], 2 * kPPromoters);
+        }
+        for (int s = 0; s < kXRecSlots; ++s) {
+            sm100::mbar_init(&fullR[s], 1);
+            sm100::mbar_init(&freeR[s], kPProducers);
+        }
+        *abort_flag = 0;
+        sm100::fence_barrier_init();
+    }
+    if (warp == 1) sm100::tmem_alloc_pair(tmem_slot, 512);
+    sm100::tc_fence_before();
+    sm100::cluster_sync();  // both CTAs' barriers initialised before any remote arrival
+    sm100::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto stageA_hi = [&](int s) { return smem + s * kPStageBytes; };
+    auto stageA_lo = [&](int s) { return smem + s * kPStageBytes + kPTileA; };
+    auto stageB_hi = [&](int s) { return smem + s * kPStageBytes + 2 * kPTileA; };
+    auto stageB_lo = [&](int s) { return smem + s * kPStageBytes + 2 * kPTileA + kPTileB; };
+    auto ringR = [&](int64_t i) { return rring + (i % kXRecSlots) * kXRecBytes; };
+    const uint32_t peer_abort = sm100::mapa_shared((const void*)abort_flag, rank ^ 1u);
+    auto timeout = [&]() {
+        *abort_flag = 1;
+        sm100::st_remote_u32(peer_abort, 1u);
+        atomicExch(g.err, (int)QRS_ERR_TIMEOUT);
+    };
+    int64_t mma_segments = 0;
+
+    if (warp == 1) {
+        // ------------------------------------------ MMA issuer (even CTA)
+        if (leader && lane == 0) {
+            constexpr uint32_t idesc = sm100::idesc_f32acc(Cfg::kFormat, 2 * kXM, kXN);
+            int64_t J = 0, gc = 0;
+            bool stop = false;
+            for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+                int64_t i = 0;
+                for (int64_t j = 0; j < n_seg; ++j, ++J) {
+                    const int b = (int)(J & 1);
+                    if (*abort_flag ||
+                        (J >= 2 && !sm100::mbar_wait_cluster(&seg_free[b], (uint32_t)(((J - 2) >> 1) & 1), abort_flag,
+                                                             kXWaitCycles))) {
+                        if (!*abort_flag) timeout();
+                        stop = true;
+                        break;
+                    }
+                    const int64_t i_end = ((j + 1) * Cfg::kSeg < n_chunks) ? (j + 1) * Cfg::kSeg : n_chunks;
+                    const uint32_t tmem_seg = tmem_base + (uint32_t)(b * kXN);
+                    bool first = true;
+                    for (; i < i_end; ++i, ++gc) {
+                        const int s = (int)(gc % kPStages);
+                        const uint32_t ph = (uint32_t)((gc / kPStages) & 1);
+                        if (!sm100::mbar_wait_cluster(&full[s], ph, abort_flag, kXWaitCycles)) {
+                            if (!*abort_flag) timeout();
+                            stop = true;
+                            break;
+                        }
+                        sm100::tc_fence_after();
+                        const uint32_t ahi = sm100::smem_u32(stageA_hi(s)), alo = sm100::smem_u32(stageA_lo(s));
+                        const uint32_t bhi = sm100::smem_u32(stageB_hi(s)), blo = sm100::smem_u32(stageB_lo(s));
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t off = (uint32_t)kk * 32u;
+                            const uint64_t dAh = sm100::desc_k_sw128(ahi + off), dAl = sm100::desc_k_sw128(alo + off);
+                            const uint64_t dBh = sm100::desc_k_sw128(bhi + off), dBl = sm100::desc_k_sw128(blo + off);
+                            sm100::mma_pair<Cfg::kTF32>(tmem_seg, dAh, dBh, idesc, first ? 0u : 1u);
+                            first = false;
+                            sm100::mma_pair<Cfg::kTF32>(tmem_seg, dAh, dBl, idesc, 1u);
+                            sm100::mma_pair<Cfg::kTF32>(tmem_seg, dAl, dBh, idesc, 1u);
+                        }
+                        sm100::mma_commit_pair(&empty[s], (uint16_t)3);
+                    }
+                    sm100::mma_commit_pair(&seg_full[b], (uint16_t)3);
+                    mma_segments = J + 1;
+                    if (stop) break;
+                }
+            }
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------- record ring
+        if (lane == 0) {
+            int64_t gc = 0;
+            bool stop = false;
+            for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+                const int64_t r = it / per_real;
+                const int4* src = g.rec + r * g.nf_pad;
+                for (int64_t i = 0; i < n_chunks; ++i, ++gc) {
+                    const int f = (int)(gc % kXRecSlots);
+                    if (*abort_flag ||
+                        (gc >= kXRecSlots && !sm100::mbar_wait(&freeR[f], (uint32_t)(((gc / kXRecSlots) & 1) ^ 1),
+                                                               abort_flag, kXWaitCycles))) {
+                        if (!*abort_flag) timeout();
+                        stop = true;
+                        break;
+                    }
+                    if (chk_ok(r * g.nf_pad + i * T, T, g.rec_rows * g.nf_pad)) {
+                        sm100::mbar_arrive_expect_tx(&fullR[f], (uint32_t)(T * 16));
+                        sm100::bulk_load(ringR(gc), src + i * T, (uint32_t)(T * 16), &fullR[f]);
+                    } else {
+                        sm100::mbar_arrive(&fullR[f]);  // checked build: the slot keeps its old records
+                    }
+                }
+            }
+            if (*abort_flag) {
+                for (int64_t i = (gc > kXRecSlots ? gc - kXRecSlots : 0); i < gc; ++i)
+                    sm100::mbar_wait_for(&fullR[i % kXRecSlots], (uint32_t)((i / kXRecSlots) & 1), kXWaitCycles / 8);
+            }
+        }
+    } else if (warp >= 4 && warp < 4 + kPPromoters) {
+        // ------------------------------------------------------ promoters
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        float* mrow = g.master + (int64_t)blockIdx.x * kXN * kXM + row;
+        const int64_t n_master = (int64_t)gridDim.x * kXN * kXM;
+        const uint32_t seg_free0 = sm100::mapa_shared(&seg_free[0], 0u);
+        int64_t J = 0;
+        bool stop = false;
+        for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+            const int64_t r = it / per_real, rem = it - r * per_real;
+            const int64_t mp = rem / g.n_nb, nb = rem - mp * g.n_nb;
+            const int64_t xi = (2 * mp + rank) * kXM + row;
+            const int64_t orow = g.r0 + r;
+            for (int64_t j = 0; j < n_seg; ++j, ++J) {
+                const int b = (int)(J & 1);
+                if (!sm100::mbar_wait_cluster(&seg_full[b], (uint32_t)((J >> 1) & 1), abort_flag, kXWaitCycles)) {
+                    if (!*abort_flag) timeout();
+                    stop = true;
+                    break;
+                }
+                sm100::tc_fence_after();
+                const uint32_t slot = tmem_base + (uint32_t)(b * kXN) + lane_off;
+                const bool last = (j == n_seg - 1);
+                constexpr int PC = QRS_GRID_PROMOTE_COLS;
+#pragma unroll 1
+                for (int c0 = 0; c0 < kXN; c0 += PC) {
+                    float* mp_ = mrow + (int64_t)c0 * kXM;
+                    float m[PC];
+                    uint32_t v[PC];
+                    if (j > 0) {
+#pragma unroll
+                        for (int q = 0; q < PC; ++q) m[q] = *chk(g.master, (mp_ - g.master) + q * kXM, n_master);
+                    }
+                    sm100::tmem_ld_cols(slot + (uint32_t)c0, v);
+                    sm100::tmem_ld_wait();
+                    if (j > 0) {
+#pragma unroll
+                        for (int q = 0; q < PC; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + m[q]);
+                    }
+                    if (!last) {
+#pragma unroll
+                        for (int q = 0; q < PC; ++q) *chk(g.master, (mp_ - g.master) + q * kXM, n_master) = __uint_as_float(v[q]);
+                    } else if (xi < g.nx) {
+#pragma unroll
+                        for (int q = 0; q < PC; ++q) {
+                            const int64_t yj = nb * kXN + c0 + q;
+                            if (yj < g.ny) {
+                                const int64_t node = yj * g.nx + xi;
+                                if (g.index) {
+                                    const int32_t pidx = *chk(g.index, node, g.nx * g.ny);
+                                    if (pidx >= 0 && pidx < g.P) *chk(g.out, orow * g.P + pidx, g.out_rows * g.P) = __uint_as_float(v[q]);
+                                    else if (pidx >= g.P) atomicExch(g.err, (int)QRS_ERR_DEVICE_CHECK);
+                                } else {
+                                    *chk(g.out, orow * g.ny * g.nx + node, g.out_rows * g.ny * g.nx) = __uint_as_float(v[q]);
+                                }
+                            }
+                        }
+                    }
+                }
+                sm100::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) sm100::mbar_arrive_remote(seg_free0 + (uint32_t)(b * sizeof(uint64_t)));
+            }
+        }
+    } else if (warp >= 4 + kPPromoters) {
+        // ------------------------------------------------------ producers
+        const int t = (warp - 4 - kPPromoters) * 32 + lane;
+        const int xrow = kPProducers == 8 ? (t < kXM ? t : -1) : (t < 2 * kXM ? (t & 127) : -1);
+        const int yrow = kPProducers == 8 ? (t >= kXM ? t - kXM : -1) : (t >= 2 * kXM ? ((t - 2 * kXM) & 127) : -1);
+        const FixedScales z = fixed_scales(g.fbound, *g.d_bound, true);
+        const uint32_t full0 = sm100::mapa_shared(&full[0], 0u);
+        int64_t gc = 0;
+        bool stop = false;
+        for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+            const int64_t r = it / per_real, rem = it - r * per_real;
+            const int64_t mp = rem / g.n_nb, nb = rem - mp * g.n_nb;
+            const int64_t xi = (2 * mp + rank) * kXM + xrow, yj = nb * kXN + rank * kPHalfN + yrow;
+            const float xa = (xrow >= 0 && xi < g.nx) ? *chk(g.x, xi, g.nx) : 0.0f;
+            const float yb = (yrow >= 0 && yj < g.ny) ? *chk(g.y, yj, g.ny) : 0.0f;
+            const int32_t XA = __float2int_rn(xa * z.xscale), YB = __float2int_rn(yb * z.xscale);
+            for (int64_t i = 0; i < n_chunks; ++i, ++gc) {
+                const int s = (int)(gc % kPStages);
+                const uint32_t ph = (uint32_t)((gc / kPStages) & 1);
+                if (*abort_flag ||
+                    (gc >= kPStages && !sm100::mbar_wait_cluster(&empty[s], ph ^ 1u, abort_flag, kXWaitCycles)) ||
+                    !sm100::mbar_wait(&fullR[gc % kXRecSlots], (uint32_t)((gc / kXRecSlots) & 1), abort_flag,
+                                      kXWaitCycles)) {
+                    if (!*abort_flag) timeout();
+                    stop = true;
+                    break;
+                }
+                const int4* rr = reinterpret_cast<const int4*>(ringR(gc));
+                if (z.use_fixed)
+                    produce_share_pair<PREC, true>(rr, stageA_hi(s), stageA_lo(s), stageB_hi(s), stageB_lo(s), t, XA,
+                                                   xa, YB, yb, z.bias, z.shift);
+                else
+                    produce_share_pair<PREC, false>(rr, stageA_hi(s), stageA_lo(s), stageB_hi(s), stageB_lo(s), t, XA,
+                                                    xa, YB, yb, z.bias, z.shift);
+                sm100::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    sm100::mbar_arrive_remote(full0 + (uint32_t)(s * sizeof(uint64_t)));
+                    sm100::mbar_arrive(&freeR[gc % kXRecSlots]);
+                }
+            }
+        }
+    }
+    sm100::tc_fence_before();
+    __syncthreads();
+    if (warp == 1 && lane == 0 && leader && *abort_flag && mma_segments > 0) {
+        const int64_t Jl = mma_segments - 1;  // the pair's MMAs in flight finish first
+        sm100::mbar_wait_cluster_for(&seg_full[Jl & 1], (uint32_t)((Jl >> 1) & 1), kXWaitCycles / 8);
+    }
+    __syncwarp();
+    sm100::cluster_sync();  // neither CTA frees TMEM or exits while the pair still works on it
+    if (warp == 1) {
+        sm100::tc_fence_after();
+        sm100::tmem_dealloc_pair(tmem_base, 512);
+    }
+}
+
 // ------------------------------------------------------------------ host
 static int64_t grid_terms_per_chunk(int mode)
 {
@@ -521,6 +850,44 @@ int64_t grid_launch_count(int mode, int64_t n_f, int64_t n_real)
     return 1 + 2 * ((n_real + slab - 1) / slab);
 }
 
+static void pair_launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute (&at)[1], unsigned grid, cudaStream_t s)
+{
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(kPThreads, 1, 1);
+    cfg.dynamicSmemBytes = kPSmemBytes;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+}
+
+// Clusters of two k_grid_pair CTAs the GPU holds at once (cached per handle
+// and precision); 0 when pairs are switched off (QRS_GRID_PAIR=0 at
+// qrs_create) or unavailable.
+template <int PREC>
+static int grid_pair_clusters(qrs_handle* h)
+{
+    int& c = h->grid_pair_clusters[PREC == QRS_SYNTH_GEMM_3XTF32 ? 0 : 1];
+    if (!h->grid_pair) return 0;
+    if (c == 0) {
+        int n = 0;
+        cudaError_t e =
+            cudaFuncSetAttribute(k_grid_pair<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmemBytes);
+        if (e == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            pair_launch_config(cfg, at, (unsigned)(h->num_sms & ~1), nullptr);
+            e = cudaOccupancyMaxActiveClusters(&n, k_grid_pair<PREC>, &cfg);
+        }
+        if (e != cudaSuccess) cudaGetLastError();  // the single-SM kernel serves instead
+        c = (e == cudaSuccess && n > 0) ? (n < h->num_sms / 2 ? n : h->num_sms / 2) : -1;
+    }
+    return c > 0 ? c : 0;
+}
+
 template <int PREC>
 static cudaError_t launch_grid_t(qrs_handle* h, const DrawParams& p, const float* x, int64_t nx, const float* y,
                                  int64_t ny, const int32_t* index, int64_t P, int64_t n_real, float* out,
@@ -551,10 +918,13 @@ static cudaError_t launch_grid_t(qrs_handle* h, const DrawParams& p, const float
     a.n_mt = (nx + kXM - 1) / kXM;
     a.n_nb = (ny + kXN - 1) / kXN;
     a.rec = rec;
+    a.out_rows = n_real;
     a.master = master;
     a.d_bound = h->d_xbound;
     a.fbound = (float)freq_bound(p);
     a.err = h->d_err;
+    // CTA pairs when there are x tiles to pair and the GPU can hold a pair
+    const int clusters = a.n_mt >= 2 ? grid_pair_clusters<PREC>(h) : 0;
     for (int64_t r0 = 0; r0 < n_real; r0 += slab) {
         const int64_t nr = (n_real - r0 < slab) ? n_real - r0 : slab;
         DrawParams ps = p;
@@ -565,10 +935,21 @@ static cudaError_t launch_grid_t(qrs_handle* h, const DrawParams& p, const float
         k_grid_draw<<<gd, 256, 0, s>>>(ps, nr, nf_pad, h->d_xbound, a.fbound, rec);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         a.r0 = r0;
-        a.n_items = nr * a.n_mt * a.n_nb;
-        const int64_t ctas = a.n_items < h->num_sms ? a.n_items : h->num_sms;
-        k_grid_main<PREC><<<(unsigned)ctas, kXThreads, kXSmemBytes, s>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        a.rec_rows = nr;
+        if (clusters > 0) {
+            a.n_items = nr * ((a.n_mt + 1) / 2) * a.n_nb;
+            const int64_t nc = a.n_items < clusters ? a.n_items : clusters;
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            pair_launch_config(cfg, at, (unsigned)(2 * nc), s);
+            e = cudaLaunchKernelEx(&cfg, k_grid_pair<PREC>, a);
+        } else {
+            a.n_items = nr * a.n_mt * a.n_nb;
+            const int64_t ctas = a.n_items < h->num_sms ? a.n_items : h->num_sms;
+            k_grid_main<PREC><<<(unsigned)ctas, kXThreads, kXSmemBytes, s>>>(a);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

@@ -35,6 +35,8 @@
 
 namespace qrs {
 
+QRS_CHECK_HOOK(check_hook_piston)
+
 constexpr int kPisChunk = 2048;  // terms per shared-memory chunk
 constexpr int kPisBuckets = 64;  // |f| buckets of the per-chunk counting sort (8 per octave)
 constexpr int kPisSortMinAp = 8; // items with at least this many apertures sort their chunks
@@ -119,9 +121,9 @@ __device__ __forceinline__ float unit_sum(const PisShared<SLICES>& sh, int k0, i
 {
     float acc = 0.0f;
     for (int k = k0; k < k_end; k += 32) {
-        const int j = SORTED ? (int)sh.sidx[k] : k;
-        const float4 T = sh.rec[j];
-        const float pf = sh.pif[j];
+        const int j = SORTED ? (int)el(sh.sidx, k) : k;
+        const float4 T = el(sh.rec, j);
+        const float pf = el(sh.pif, j);
         const float A = OBST ? fmaf(wD, airy_g(pf * D), -wd * airy_g(pf * d)) : airy_g(pf * D);
         acc = fmaf(A * T.z, __cosf(phase_df_psi(T.x, T.y, x, y, T.w) * 6.28318530717958648f), acc);
     }
@@ -141,17 +143,17 @@ __device__ __forceinline__ void unit_sum_group(const PisShared<SLICES>& sh, int 
     float2 x2[NP], y2[NP], D2[NP], DD2[NP], acc2[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-        x2[q] = make_float2(sh.apx[a0 + 2 * q], sh.apx[a0 + 2 * q + 1]);
-        y2[q] = make_float2(sh.apy[a0 + 2 * q], sh.apy[a0 + 2 * q + 1]);
-        D2[q] = make_float2(sh.apD[a0 + 2 * q], sh.apD[a0 + 2 * q + 1]);
+        x2[q] = make_float2(el(sh.apx, a0 + 2 * q), el(sh.apx, a0 + 2 * q + 1));
+        y2[q] = make_float2(el(sh.apy, a0 + 2 * q), el(sh.apy, a0 + 2 * q + 1));
+        D2[q] = make_float2(el(sh.apD, a0 + 2 * q), el(sh.apD, a0 + 2 * q + 1));
         DD2[q] = __fmul2_rn(D2[q], D2[q]);
         acc2[q] = make_float2(0.0f, 0.0f);
     }
     const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
     for (int k = k0; k < k_end; k += 32) {
-        const int j = SORTED ? (int)sh.sidx[k] : k;
-        const float4 T = sh.rec[j];
-        const float pf = sh.pif[j];
+        const int j = SORTED ? (int)el(sh.sidx, k) : k;
+        const float4 T = el(sh.rec, j);
+        const float pf = el(sh.pif, j);
         const float pf2 = (FORM <= kFltSer10) ? pf * pf : 0.0f;
         const float2 Tz = make_float2(T.z, T.z);
 #pragma unroll
@@ -193,10 +195,10 @@ __device__ __forceinline__ void unit_sum_prefiltered(const PisShared<SLICES>& sh
                                                      float (&acc)[NA])
 {
     if constexpr (NA == 1) {
-        const float x = sh.apx[a0], y = sh.apy[a0];
+        const float x = el(sh.apx, a0), y = el(sh.apy, a0);
         float s = 0.0f;
         for (int k = k0; k < k_end; k += 32) {
-            const float4 T = sh.rec[k];
+            const float4 T = el(sh.rec, k);
             s = fmaf(T.z, __cosf(phase_df_psi(T.x, T.y, x, y, T.w) * 6.28318530717958648f), s);
         }
         acc[0] = s;
@@ -206,13 +208,13 @@ __device__ __forceinline__ void unit_sum_prefiltered(const PisShared<SLICES>& sh
         float2 x2[NP], y2[NP], acc2[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-            x2[q] = make_float2(sh.apx[a0 + 2 * q], sh.apx[a0 + 2 * q + 1]);
-            y2[q] = make_float2(sh.apy[a0 + 2 * q], sh.apy[a0 + 2 * q + 1]);
+            x2[q] = make_float2(el(sh.apx, a0 + 2 * q), el(sh.apx, a0 + 2 * q + 1));
+            y2[q] = make_float2(el(sh.apy, a0 + 2 * q), el(sh.apy, a0 + 2 * q + 1));
             acc2[q] = make_float2(0.0f, 0.0f);
         }
         const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
         for (int k = k0; k < k_end; k += 32) {
-            const float4 T = sh.rec[k];
+            const float4 T = el(sh.rec, k);
             const float2 Tz = make_float2(T.z, T.z);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
@@ -242,11 +244,11 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
     // When every aperture has the same (D, d), the Eq. 7 filter is a function
     // of the term alone: it is taken once per term into the record's
     // amplitude, and the units evaluate no filter (and need no |f| order).
-    const float D0 = J.ap_D[0], d0 = J.ap_d ? J.ap_d[0] : 0.0f;
+    const float D0 = *chk(J.ap_D, 0, n_ap), d0 = J.ap_d ? *chk(J.ap_d, 0, n_ap) : 0.0f;
     bool same = true;
     for (int a = tid; a < n_ap; a += kPisTPB) {
-        const float D = J.ap_D[a], d = J.ap_d ? J.ap_d[a] : 0.0f;
-        sh.apwD[a] = D;  // staging: the diameters in job order
+        const float D = *chk(J.ap_D, a, n_ap), d = J.ap_d ? *chk(J.ap_d, a, n_ap) : 0.0f;
+        el(sh.apwD, a) = D;  // staging: the diameters in job order
         same = same && D == D0 && d == d0;
     }
     const bool prefilter = __syncthreads_and(same) != 0;
@@ -262,10 +264,10 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
         const int a = tid + i * kPisTPB;
         my_slot[i] = 0;
         if (a < n_ap) {
-            const uint32_t ka = key(sh.apwD[a]);
+            const uint32_t ka = key(el(sh.apwD, a));
             int s = 0;
             for (int b = 0; b < n_ap; ++b) {
-                const uint32_t kb = key(sh.apwD[b]);
+                const uint32_t kb = key(el(sh.apwD, b));
                 s += (kb < ka || (kb == ka && b < a)) ? 1 : 0;
             }
             my_slot[i] = s;
@@ -277,15 +279,15 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
         const int a = tid + i * kPisTPB;
         if (a < n_ap) {
             const int s = my_slot[i];
-            const float D = J.ap_D[a], d = J.ap_d ? J.ap_d[a] : 0.0f;
-            const float2 c = J.ap_xy[a];
-            sh.rank[a] = (uint8_t)s;
-            sh.apx[s] = c.x; sh.apy[s] = c.y;
-            sh.apD[s] = D;
-            sh.apd[s] = d;
-            sh.apwD[s] = d > 0.0f ? (D * D) / (D * D - d * d) : 1.0f;
-            sh.apwd[s] = d > 0.0f ? (d * d) / (D * D - d * d) : 0.0f;
-            sh.total[s] = 0.0f;
+            const float D = *chk(J.ap_D, a, n_ap), d = J.ap_d ? *chk(J.ap_d, a, n_ap) : 0.0f;
+            const float2 c = *chk(J.ap_xy, a, n_ap);
+            el(sh.rank, a) = (uint8_t)s;
+            el(sh.apx, s) = c.x; el(sh.apy, s) = c.y;
+            el(sh.apD, s) = D;
+            el(sh.apd, s) = d;
+            el(sh.apwD, s) = d > 0.0f ? (D * D) / (D * D - d * d) : 1.0f;
+            el(sh.apwd, s) = d > 0.0f ? (d * d) / (D * D - d * d) : 0.0f;
+            el(sh.total, s) = 0.0f;
         }
     }
     const float wD0 = d0 > 0.0f ? (D0 * D0) / (D0 * D0 - d0 * d0) : 1.0f;
@@ -304,8 +306,8 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             term_amp_polar(p, n, w, t.var, t.F, Fa, u);
             const float fa = fast_abs_f(t.fx * t.fx + t.fy * t.fy);
             if (prefilter) Fa = airy_filter_w(fa, D0, d0, wD0, wd0) * Fa;
-            sh.rec[q] = make_float4(t.fx, t.fy, Fa, (float)u * 0x1p-24f);
-            sh.pif[q] = 3.14159265358979f * fa;
+            el(sh.rec, q) = make_float4(t.fx, t.fy, Fa, (float)u * 0x1p-24f);
+            el(sh.pif, q) = 3.14159265358979f * fa;
         }
         __syncthreads();
         // Terms in order of |f| bucket: a warp's lanes then take the same
@@ -319,21 +321,21 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             const int base = (int)(__float_as_uint(3.14159265358979f * (float)p.fmax) >> 20) - (kPisBuckets - 1);
             const int per_warp = (len + kPisTPB - 1) / kPisTPB * 32;  // items per warp, a multiple of 32
             const int q_begin = warp * per_warp, q_end = q_begin + per_warp;
-            for (int b = lane; b < kPisBuckets; b += 32) sh.bcount[warp][b] = 0;
+            for (int b = lane; b < kPisBuckets; b += 32) el(sh.bcount, warp, b) = 0;
             __syncwarp();
             for (int q0 = q_begin; q0 < q_end; q0 += 32) {
                 const int q = q0 + lane;
-                const int b = q < len ? pis_bucket(sh.pif[q], base) : kPisBuckets;
+                const int b = q < len ? pis_bucket(el(sh.pif, q), base) : kPisBuckets;
                 const unsigned peers = __match_any_sync(0xffffffffu, b);
-                if (b < kPisBuckets && lane == __ffs(peers) - 1) sh.bcount[warp][b] += __popc(peers);
+                if (b < kPisBuckets && lane == __ffs(peers) - 1) el(sh.bcount, warp, b) += __popc(peers);
                 __syncwarp();
             }
             __syncthreads();
             if (warp == 0) {
                 int t0 = 0, t1 = 0;  // bucket totals: lane holds buckets lane and lane + 32
                 for (int w = 0; w < kPisWarps; ++w) {
-                    t0 += sh.bcount[w][lane];
-                    t1 += sh.bcount[w][lane + 32];
+                    t0 += el(sh.bcount, w, lane);
+                    t1 += el(sh.bcount, w, lane + 32);
                 }
                 int i0 = t0, i1 = t1;  // inclusive scans over the lanes
 #pragma unroll
@@ -346,9 +348,9 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
                 }
                 int e0 = i0 - t0, e1 = __shfl_sync(0xffffffffu, i0, 31) + i1 - t1;
                 for (int w = 0; w < kPisWarps; ++w) {
-                    const int c0 = sh.bcount[w][lane], c1 = sh.bcount[w][lane + 32];
-                    sh.bcount[w][lane] = e0;
-                    sh.bcount[w][lane + 32] = e1;
+                    const int c0 = el(sh.bcount, w, lane), c1 = el(sh.bcount, w, lane + 32);
+                    el(sh.bcount, w, lane) = e0;
+                    el(sh.bcount, w, lane + 32) = e1;
                     e0 += c0;
                     e1 += c1;
                 }
@@ -356,11 +358,11 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
             __syncthreads();
             for (int q0 = q_begin; q0 < q_end; q0 += 32) {
                 const int q = q0 + lane;
-                const int b = q < len ? pis_bucket(sh.pif[q], base) : kPisBuckets;
+                const int b = q < len ? pis_bucket(el(sh.pif, q), base) : kPisBuckets;
                 const unsigned peers = __match_any_sync(0xffffffffu, b);
-                if (b < kPisBuckets) sh.sidx[sh.bcount[warp][b] + __popc(peers & ((1u << lane) - 1u))] = (uint16_t)q;
+                if (b < kPisBuckets) el(sh.sidx, el(sh.bcount, warp, b) + __popc(peers & ((1u << lane) - 1u))) = (uint16_t)q;
                 __syncwarp();
-                if (b < kPisBuckets && lane == __ffs(peers) - 1) sh.bcount[warp][b] += __popc(peers);
+                if (b < kPisBuckets && lane == __ffs(peers) - 1) el(sh.bcount, warp, b) += __popc(peers);
                 __syncwarp();
             }
             __syncthreads();
@@ -380,20 +382,20 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
 #pragma unroll
                     for (int i = 0; i < kPisGroup; ++i) {
                         const float v = warp_sum_f(acc[i]);
-                        if (lane == 0) sh.part[a0 + i][sl] = v;
+                        if (lane == 0) el(sh.part, a0 + i, sl) = v;
                     }
                 } else {
                     for (int a = a0; a < n_ap; ++a) {
                         float acc[1];
                         unit_sum_prefiltered<1>(sh, k0, k_end, a, acc);
                         const float v = warp_sum_f(acc[0]);
-                        if (lane == 0) sh.part[a][sl] = v;
+                        if (lane == 0) el(sh.part, a, sl) = v;
                     }
                 }
                 continue;
             }
             bool plain = a1 < n_ap;
-            for (int a = a0; plain && a <= a1; ++a) plain = sh.apd[a] <= 0.0f;
+            for (int a = a0; plain && a <= a1; ++a) plain = el(sh.apd, a) <= 0.0f;
             if (plain) {
                 float acc[kPisGroup];
                 if (sorted) {
@@ -403,17 +405,17 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
                     // valid for every term of the unit.
                     float f_lo = 3.402823466e38f, f_hi = 0.0f;
                     for (int k = k0; k < k_end; k += 32) {
-                        const float pf = sh.pif[sh.sidx[k]];
+                        const float pf = el(sh.pif, el(sh.sidx, k));
                         f_lo = fminf(f_lo, pf);
                         f_hi = fmaxf(f_hi, pf);
                     }
                     // pi |f| >= 0: the float bits order as the values
                     f_lo = __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(f_lo)));
                     f_hi = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(f_hi)));
-                    float D_lo = sh.apD[a0], D_hi = D_lo;
+                    float D_lo = el(sh.apD, a0), D_hi = D_lo;
                     for (int a = a0 + 1; a <= a1; ++a) {
-                        D_lo = fminf(D_lo, sh.apD[a]);
-                        D_hi = fmaxf(D_hi, sh.apD[a]);
+                        D_lo = fminf(D_lo, el(sh.apD, a));
+                        D_hi = fmaxf(D_hi, el(sh.apD, a));
                     }
                     unit_sum_group_form(filter_form(f_lo * D_lo, f_hi * D_hi), sh, k0, k_end, a0, acc);
                 } else {
@@ -422,13 +424,13 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
 #pragma unroll
                 for (int i = 0; i < kPisGroup; ++i) {
                     const float v = warp_sum_f(acc[i]);
-                    if (lane == 0) sh.part[a0 + i][sl] = v;
+                    if (lane == 0) el(sh.part, a0 + i, sl) = v;
                 }
                 continue;
             }
             for (int a = a0; a <= a1 && a < n_ap; ++a) {
-                const float x = sh.apx[a], y = sh.apy[a], D = sh.apD[a], d = sh.apd[a];
-                const float wD = sh.apwD[a], wd = sh.apwd[a];
+                const float x = el(sh.apx, a), y = el(sh.apy, a), D = el(sh.apD, a), d = el(sh.apd, a);
+                const float wD = el(sh.apwD, a), wd = el(sh.apwd, a);
                 float acc;
                 if (sorted) {
                     acc = d > 0.0f ? unit_sum<true, true>(sh, k0, k_end, x, y, D, d, wD, wd)
@@ -438,26 +440,26 @@ __device__ void piston_item(const PistonJobDev& J, int64_t r, PisShared<S::kSlic
                                    : unit_sum<false, false>(sh, k0, k_end, x, y, D, d, wD, wd);
                 }
                 acc = warp_sum_f(acc);
-                if (lane == 0) sh.part[a][sl] = acc;
+                if (lane == 0) el(sh.part, a, sl) = acc;
             }
         }
         __syncthreads();
         for (int a = tid; a < n_ap; a += kPisTPB) {
-            float t = sh.total[a];
-            for (int sl = 0; sl < n_sl; ++sl) t += sh.part[a][sl];
-            sh.total[a] = t;
+            float t = el(sh.total, a);
+            for (int sl = 0; sl < n_sl; ++sl) t += el(sh.part, a, sl);
+            el(sh.total, a) = t;
         }
     }
     __syncthreads();
     if (J.piston)
-        for (int a = tid; a < n_ap; a += kPisTPB) J.piston[r * n_ap + a] = sh.total[sh.rank[a]];
+        for (int a = tid; a < n_ap; a += kPisTPB) *chk(J.piston, r * n_ap + a, J.n_real * n_ap) = el(sh.total, el(sh.rank, a));
     if (J.delta)
         for (int q = tid; q < J.n_pairs; q += kPisTPB) {
-            const int2 pr = J.pairs[q];
+            const int2 pr = *chk(J.pairs, q, J.n_pairs);
             float v = 0.0f;
             if (pr.x < 0 || pr.x >= n_ap || pr.y < 0 || pr.y >= n_ap) atomicExch(err, (int)QRS_ERR_DEVICE_CHECK);
-            else v = sh.total[sh.rank[pr.x]] - sh.total[sh.rank[pr.y]];
-            J.delta[r * J.n_pairs + q] = v;
+            else v = el(sh.total, el(sh.rank, pr.x)) - el(sh.total, el(sh.rank, pr.y));
+            *chk(J.delta, r * J.n_pairs + q, J.n_real * J.n_pairs) = v;
         }
     __syncthreads();  // shared state reused by the next item
 }
@@ -490,9 +492,9 @@ __global__ void __launch_bounds__(S::kTPB, 1024 / S::kTPB) k_piston_persistent(c
         int lo = 0, hi = n_jobs;  // last job with item_begin <= g
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (jobs[mid].item_begin <= g) lo = mid; else hi = mid;
+            if (chk(jobs, mid, n_jobs)->item_begin <= g) lo = mid; else hi = mid;
         }
-        const PistonJobDev J = jobs[lo];
+        const PistonJobDev J = *chk(jobs, lo, n_jobs);
         piston_item<S>(J, g - J.item_begin, sh, err);
     }
 }

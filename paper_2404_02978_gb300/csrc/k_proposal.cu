@@ -13,6 +13,8 @@
 
 namespace qrs {
 
+QRS_CHECK_HOOK(check_hook_proposal)
+
 constexpr int kHid = 128;
 constexpr uint32_t kStreamInit = 3u;  // Philox stream of the initial weights
 
@@ -53,7 +55,7 @@ __global__ void k_mlp_init(int C, uint64_t seed, float out_scale, float* __restr
             v = sqrtf(-2.0f * logf(U1)) * cospif(2.0f * U2) * sqrtf(2.0f / (float)fan);
             if (i >= e4) v *= out_scale;  // the output layer's weights
         }
-        P[i] = v;
+        *chk(P, i, n) = v;
     }
 }
 
@@ -61,9 +63,9 @@ __global__ void k_mlp_init(int C, uint64_t seed, float out_scale, float* __restr
 __global__ void k_features(const double* __restrict__ geom, int64_t n, float* __restrict__ X)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double* g = geom + 5 * i;
+        const double* g = chk(geom, 5 * i, 5 * n);
         const double B = hypot(g[3], g[4]);
-        float* x = X + 6 * i;
+        float* x = chk(X, 6 * i, 6 * n);
         x[0] = (float)((log(g[0]) - log(0.12)) / 0.6);
         x[1] = (float)((log(g[1]) - log(30.0)) / 0.8);
         x[2] = (float)((log(g[2]) - log(3.0)) / 0.6);
@@ -90,6 +92,9 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
     __shared__ float As[16][64 + 4];
     __shared__ float Bs[16][64 + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t nA = (int64_t)(TA ? K : M) * lda, nB = (int64_t)(TB ? N : K) * ldb;
+    const int64_t nC = (int64_t)gridDim.z * M * ldc, nMask = (int64_t)M * ldm;
+    float* const C0 = Cm;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
     float2 acc[4][2];  // acc[i][jp] = outputs (i, 2 jp), (i, 2 jp + 1): one FFMA2 updates both
 #pragma unroll
@@ -100,11 +105,11 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
             int mm, kk;
             if (TA) { kk = e >> 6; mm = e & 63; } else { mm = e >> 4; kk = e & 15; }
             const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < kz1) ? (TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk]) : 0.0f;
+            el(As, kk, mm) = (gm < M && gk < kz1) ? *chk(A, TA ? (int64_t)gk * lda + gm : (int64_t)gm * lda + gk, nA) : 0.0f;
             int nn, kb;
             if (TB) { nn = e >> 4; kb = e & 15; } else { kb = e >> 6; nn = e & 63; }
             const int gn = n0 + nn, gkb = k0 + kb;
-            Bs[kb][nn] = (gn < N && gkb < kz1) ? (TB ? B[(int64_t)gn * ldb + gkb] : B[(int64_t)gkb * ldb + gn]) : 0.0f;
+            el(Bs, kb, nn) = (gn < N && gkb < kz1) ? *chk(B, TB ? (int64_t)gn * ldb + gkb : (int64_t)gkb * ldb + gn, nB) : 0.0f;
         }
         __syncthreads();
 #pragma unroll
@@ -136,14 +141,14 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
             if (n >= N) continue;
             float v = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
             if (gridDim.z > 1) {
-                Cm[(int64_t)m * ldc + n] = v;
+                *chk(C0, (Cm - C0) + (int64_t)m * ldc + n, nC) = v;
                 continue;
             }
-            if (EPI & kEpiBias) v += bias[n];
+            if (EPI & kEpiBias) v += *chk(bias, n, N);
             if (EPI & kEpiRelu) v = fmaxf(v, 0.0f);
-            if (EPI & kEpiMask) v = mask[(int64_t)m * ldm + n] > 0.0f ? v : 0.0f;
-            if (EPI & kEpiAdd) v += mask[(int64_t)m * ldm + n];
-            Cm[(int64_t)m * ldc + n] = v;
+            if (EPI & kEpiMask) v = *chk(mask, (int64_t)m * ldm + n, nMask) > 0.0f ? v : 0.0f;
+            if (EPI & kEpiAdd) v += *chk(mask, (int64_t)m * ldm + n, nMask);
+            *chk(C0, (int64_t)m * ldc + n, nC) = v;
         }
     }
 }
@@ -157,10 +162,11 @@ __global__ void k_sgemm_reduce(int M, int N, int S, const float* __restrict__ pa
     const int64_t total = (int64_t)M * N;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int m = (int)(e / N), n = (int)(e - (int64_t)m * N);
-        float v = part[(int64_t)m * ldc + n];
-        for (int z = 1; z < S; ++z) v += part[((int64_t)z * M + m) * ldc + n];
-        if (EPI & kEpiMask) v = mask[(int64_t)m * ldm + n] > 0.0f ? v : 0.0f;
-        Cm[(int64_t)m * ldc + n] = v;
+        const int64_t n_part = (int64_t)S * M * ldc;
+        float v = *chk(part, (int64_t)m * ldc + n, n_part);
+        for (int z = 1; z < S; ++z) v += *chk(part, ((int64_t)z * M + m) * ldc + n, n_part);
+        if (EPI & kEpiMask) v = *chk(mask, (int64_t)m * ldm + n, (int64_t)M * ldm) > 0.0f ? v : 0.0f;
+        *chk(Cm, (int64_t)m * ldc + n, (int64_t)M * ldc) = v;
     }
 }
 
@@ -197,13 +203,13 @@ __global__ void __launch_bounds__(256) k_colsum(const float* __restrict__ A, int
     const int c = blockIdx.x * 32 + (threadIdx.x & 31), g = threadIdx.x >> 5;
     float v = 0.0f;
     if (c < cols)
-        for (int r = g; r < rows; r += 8) v += A[(int64_t)r * cols + c];
-    red[g][threadIdx.x & 31] = v;
+        for (int r = g; r < rows; r += 8) v += *chk(A, (int64_t)r * cols + c, (int64_t)rows * cols);
+    el(red, g, threadIdx.x & 31) = v;
     __syncthreads();
     if (g == 0 && c < cols) {
-        float t = red[0][threadIdx.x];
-        for (int q = 1; q < 8; ++q) t += red[q][threadIdx.x];
-        out[c] = t;
+        float t = el(red, 0, threadIdx.x);
+        for (int q = 1; q < 8; ++q) t += el(red, q, threadIdx.x);
+        *chk(out, c, cols) = t;
     }
 }
 
@@ -234,8 +240,8 @@ __global__ void __launch_bounds__(256) k_softmax_ce(const float* __restrict__ Z,
 {
     __shared__ float red[32];
     const int64_t i = blockIdx.x;
-    const float* z = Z + i * C;
-    const float* t = T + i * C;
+    const float* z = chk(Z, i * C, n * C);
+    const float* t = chk(T, i * C, n * C);
     float mx = -INFINITY;
     for (int c = threadIdx.x; c < C; c += blockDim.x) mx = fmaxf(mx, z[c]);
     mx = block_reduce(mx, red, true);
@@ -247,11 +253,11 @@ __global__ void __launch_bounds__(256) k_softmax_ce(const float* __restrict__ Z,
     float l = 0.0f;
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
         const float q = expf(z[c] - lse);
-        dZ[i * C + c] = (q - t[c]) * inv_n;
+        *chk(dZ, i * C + c, n * C) = (q - t[c]) * inv_n;
         l += t[c] * (lse - z[c]);
     }
     l = block_reduce(l, red, false);
-    if (threadIdx.x == 0) loss_row[i] = l;
+    if (threadIdx.x == 0) *chk(loss_row, i, n) = l;
 }
 
 // Mean of loss_row in a fixed order (one CTA).
@@ -259,7 +265,7 @@ __global__ void k_loss_mean(const float* __restrict__ loss_row, int64_t n, float
 {
     __shared__ float red[32];
     float s = 0.0f;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += loss_row[i];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += *chk(loss_row, i, n);
     s = block_reduce(s, red, false);
     if (threadIdx.x == 0) *loss = s / (float)n;
 }
@@ -269,12 +275,12 @@ __global__ void k_adam(int64_t n, float* __restrict__ P, float* __restrict__ m, 
                        const float* __restrict__ g, float lr, float c1, float c2)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = 0.9f * m[i] + 0.1f * gi;
-        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        P[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+        const float gi = *chk(g, i, n);
+        const float mi = 0.9f * *chk(m, i, n) + 0.1f * gi;
+        const float vi = 0.999f * *chk(v, i, n) + 0.001f * gi * gi;
+        *chk(m, i, n) = mi;
+        *chk(v, i, n) = vi;
+        *chk(P, i, n) -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
     }
 }
 
@@ -286,7 +292,7 @@ __global__ void k_prop_draws(DrawParams p, int n_draws, float4* __restrict__ rec
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = i % p.n_f;
         const Term t = draw_term(p, (uint64_t)i, k);
-        rec[i] = make_float4(t.fx, t.fy, t.J, __int_as_float(t.cell));
+        *chk(rec, i, total) = make_float4(t.fx, t.fy, t.J, __int_as_float(t.cell));
     }
 }
 
@@ -310,7 +316,7 @@ __global__ void __launch_bounds__(512) k_prop_targets(const float4* __restrict__
     __shared__ unsigned long long s_frame;
     const int64_t i = blockIdx.x;
     if (threadIdx.x == 0) {
-        const double* g = geom + 5 * i;
+        const double* g = chk(geom, 5 * i, 5 * (int64_t)gridDim.x);
         s_pc = (float)(c_vk * pow(g[0], -5.0 / 3.0));
         s_pa = psd_kind == QRS_PSD_KOLMOGOROV ? 0.0f : (float)(1.0 / (g[1] * g[1]));
         s_D = (float)g[2];
@@ -319,11 +325,11 @@ __global__ void __launch_bounds__(512) k_prop_targets(const float4* __restrict__
         const double x = __ddiv_rn(atan2(g[4], g[3]), kTwoPi);
         s_frame = (unsigned long long)(long long)__dmul_rn(x, 0x1p63) * 2ull;
     }
-    for (int c = threadIdx.x; c < C; c += blockDim.x) hist[c] = 0.0f;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) *chk(hist, c, C) = 0.0f;
     __syncthreads();
     const float pc = s_pc, pa = s_pa, D = s_D, Bx = s_Bx, By = s_By;
     for (int64_t k = threadIdx.x; k < n_rec; k += blockDim.x) {
-        const float4 r = rec[k];
+        const float4 r = *chk(rec, k, n_rec);
         const float f2 = r.x * r.x + r.y * r.y;
         const float w = psd_w(pc, pa, f2) * r.z * inv_nf;
         const float A = airy_filter(sqrtf(f2), D, 0.0f);
@@ -338,7 +344,7 @@ __global__ void __launch_bounds__(512) k_prop_targets(const float4* __restrict__
             if (sec & 1ull) W = ~W;
             cell = (cell / n_theta) * n_theta + (int)(((W >> 32) * (uint64_t)n_theta) >> 32);
         }
-        atomicAdd(&hist[cell], kind == QRS_TARGET_RMS ? v * v : v);
+        atomicAdd(chk(hist, cell, C), kind == QRS_TARGET_RMS ? v * v : v);
     }
     __syncthreads();
     if (kind == QRS_TARGET_RMS)
@@ -348,7 +354,7 @@ __global__ void __launch_bounds__(512) k_prop_targets(const float4* __restrict__
     for (int c = threadIdx.x; c < C; c += blockDim.x) tot += hist[c];
     tot = block_reduce(tot, red, false);
     const float inv = tot > 0.0f ? 1.0f / tot : 0.0f;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) out[i * C + c] = hist[c] * inv;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) *chk(out, i * C + c, (int64_t)gridDim.x * C) = hist[c] * inv;
 }
 
 // ------------------------------------------------------------ sampling CDF
@@ -399,22 +405,23 @@ __global__ void __launch_bounds__(1024) k_prop_cdf(const float* __restrict__ z, 
     __syncthreads();
     const double sum = redd[0];
     for (int c = threadIdx.x; c < C; c += blockDim.x)
-        pbuf[c] = (1.0 - (double)eps) * ((double)expf(beta * (z[c] - mx)) / sum) + (double)eps / (double)C;
+        *chk(pbuf, c, (int64_t)C + n_rho) = (1.0 - (double)eps) * ((double)expf(beta * (z[c] - mx)) / sum) + (double)eps / (double)C;
     __syncthreads();
     double* band = pbuf + C;
     for (int i = threadIdx.x; i < n_rho; i += blockDim.x) {
         double s = 0.0;
-        for (int j = 0; j < n_theta; ++j) s += pbuf[i * n_theta + j];
-        band[i] = s;
+        for (int j = 0; j < n_theta; ++j) s += *chk(pbuf, (int64_t)i * n_theta + j, (int64_t)C);
+        *chk(band, i, n_rho) = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int i = 0; i < n_rho; ++i) t += band[i];
-        quantise_scan(band, n_rho, 1, t, cdf);
+        if (chk_ok(0, n_rho, (int64_t)n_rho + C)) quantise_scan(band, n_rho, 1, t, cdf);
     }
     for (int i = threadIdx.x; i < n_rho; i += blockDim.x)
-        quantise_scan(pbuf + i * n_theta, n_theta, 1, band[i], cdf + n_rho + (int64_t)i * n_theta);
+        if (chk_ok(n_rho + (int64_t)i * n_theta, n_theta, (int64_t)n_rho + C))
+            quantise_scan(pbuf + i * n_theta, n_theta, 1, band[i], cdf + n_rho + (int64_t)i * n_theta);
 }
 
 static double vk_c()
@@ -448,11 +455,11 @@ __global__ void __launch_bounds__(256) k_prop_prior(const double* __restrict__ g
     __shared__ float s_pc, s_pa, s_D, s_B, s_phiB;
     if (threadIdx.x < kPriorNodes) {
         const uint64_t m = threadIdx.x;
-        s_node[m][0] = (float)((0x8000000000000000ULL + m * kR2StepX) >> 40) * 0x1p-24f;
-        s_node[m][1] = (float)((0x8000000000000000ULL + m * kR2StepY) >> 40) * 0x1p-24f;
+        el(s_node, m, 0) = (float)((0x8000000000000000ULL + m * kR2StepX) >> 40) * 0x1p-24f;
+        el(s_node, m, 1) = (float)((0x8000000000000000ULL + m * kR2StepY) >> 40) * 0x1p-24f;
     }
     if (threadIdx.x == 0) {
-        const double* g = geom + 5 * (int64_t)blockIdx.x;
+        const double* g = chk(geom, 5 * (int64_t)blockIdx.x, 5 * (int64_t)gridDim.x);
         s_pc = (float)(c_vk * pow(g[0], -5.0 / 3.0));
         s_pa = psd_kind == kPsdKolmogorov ? 0.0f : (float)(1.0 / (g[1] * g[1]));
         s_D = (float)g[2];
@@ -461,7 +468,7 @@ __global__ void __launch_bounds__(256) k_prop_prior(const double* __restrict__ g
     }
     __syncthreads();
     const int C = n_rho * n_theta;
-    float* o = out + (int64_t)blockIdx.x * C;
+    const int64_t o0 = (int64_t)blockIdx.x * C, n_out = (int64_t)gridDim.x * C;
     const float pc = s_pc, pa = s_pa, D = s_D, B = s_B, phiB = s_phiB;
     const float dphi = fold ? 6.28318530717958648f / (float)fold : 6.28318530717958648f;
     float vmax = 0.0f;
@@ -479,14 +486,14 @@ __global__ void __launch_bounds__(256) k_prop_prior(const double* __restrict__ g
             v += psd_w(pc, pa, rho * rho) * A * A * (2.0f * sn * sn) * rho * rho;
         }
         v *= 1.0f / (float)kPriorNodes;
-        o[c] = v;
+        *chk(out, o0 + c, n_out) = v;
         vmax = fmaxf(vmax, v);
     }
     vmax = block_reduce(vmax, red, true);
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        const float v = o[c];
-        o[c] = v > 0.0f && vmax > 0.0f ? fmaxf(logf(v / vmax), kPriorFloor) : kPriorFloor;
+        const float v = *chk(out, o0 + c, n_out);
+        *chk(out, o0 + c, n_out) = v > 0.0f && vmax > 0.0f ? fmaxf(logf(v / vmax), kPriorFloor) : kPriorFloor;
     }
 }
 

@@ -10,6 +10,8 @@
 
 namespace qrs {
 
+QRS_CHECK_HOOK(check_hook_sf)
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -32,7 +34,7 @@ __global__ void __launch_bounds__(256) k_structure_fn(const float* __restrict__ 
     for (int64_t pair = blockIdx.y; pair < n_pairs; pair += gridDim.y) {  // uniform per block
         const int64_t s = pair / n_lags;
         const int l = (int)(pair - s * n_lags);
-        const int64_t L = lags[l];
+        const int64_t L = *chk(lags, l, n_lags);
         if (L < 0 || L >= T) {
             if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(err, (int)QRS_ERR_DEVICE_CHECK);
             continue;
@@ -49,8 +51,9 @@ __global__ void __launch_bounds__(256) k_structure_fn(const float* __restrict__ 
         double b2 = 0.0, b4 = 0.0;  // values too large for the FP32 fourth power
         int64_t n = 0;
         for (; i < total; i += stride) {
-            const float* v = delta + (r * n_series + s) * T;
-            const DF x = (L == 0) ? DF{v[t], 0.0f} : df_two_sum(v[t + L], -v[t]);  // exact difference
+            const int64_t v0 = (r * n_series + s) * T, n_delta = n_real * n_series * T;
+            const DF x = (L == 0) ? DF{*chk(delta, v0 + t, n_delta), 0.0f}
+                                  : df_two_sum(*chk(delta, v0 + t + L, n_delta), -*chk(delta, v0 + t, n_delta));  // exact difference
             if (fabsf(x.hi) < 1.0e9f) {
                 const DF x2 = df_mul(x, x);
                 const DF x4 = df_mul(x2, x2);
@@ -76,21 +79,21 @@ __global__ void __launch_bounds__(256) k_structure_fn(const float* __restrict__ 
         cnt = warp_sum(cnt);
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
         __syncthreads();  // red[] free from the previous pair
-        if (lane == 0) { red[0][w] = s2; red[1][w] = s4; red[2][w] = cnt; }
+        if (lane == 0) { el(red, 0, w) = s2; el(red, 1, w) = s4; el(red, 2, w) = cnt; }
         __syncthreads();
         if (w == 0) {
             const int nw = blockDim.x >> 5;
-            s2 = lane < nw ? red[0][lane] : 0.0;
-            s4 = lane < nw ? red[1][lane] : 0.0;
-            cnt = lane < nw ? red[2][lane] : 0.0;
+            s2 = lane < nw ? el(red, 0, lane) : 0.0;
+            s4 = lane < nw ? el(red, 1, lane) : 0.0;
+            cnt = lane < nw ? el(red, 2, lane) : 0.0;
             s2 = warp_sum(s2);
             s4 = warp_sum(s4);
             cnt = warp_sum(cnt);
             if (lane == 0 && cnt > 0.0) {
-                double* o = acc + (s * n_lags + l) * 3;
-                atomicAdd(o, s2);
-                atomicAdd(o + 1, s4);
-                atomicAdd(o + 2, cnt);
+                const int64_t o = (s * n_lags + l) * 3, n_acc = n_series * n_lags * 3;
+                atomicAdd(chk(acc, o, n_acc), s2);
+                atomicAdd(chk(acc, o + 1, n_acc), s4);
+                atomicAdd(chk(acc, o + 2, n_acc), cnt);
             }
         }
     }
@@ -106,16 +109,15 @@ __global__ void k_pair_diff(const float* __restrict__ v, int64_t n_real, int64_t
     const int64_t total = n_real * n_pairs;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / n_pairs, q = i - r * n_pairs;
-        const int2 pq = pairs[q];
+        const int2 pq = *chk(pairs, q, n_pairs);
         float d;
         if (pq.x < 0 || pq.x >= n_points || pq.y < 0 || pq.y >= n_points) {
             d = __int_as_float(0x7FC00000);
             atomicExch(err, (int)QRS_ERR_DEVICE_CHECK);
         } else {
-            const float* row = v + r * n_points;
-            d = row[pq.x] - row[pq.y];
+            d = *chk(v, r * n_points + pq.x, n_real * n_points) - *chk(v, r * n_points + pq.y, n_real * n_points);
         }
-        out[i] = d;
+        *chk(out, i, total) = d;
     }
 }
 

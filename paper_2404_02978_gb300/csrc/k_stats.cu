@@ -16,6 +16,8 @@
 
 namespace qrs {
 
+QRS_CHECK_HOOK(check_hook_stats)
+
 constexpr int kStatTPB = 256;
 constexpr int kStatTile = 2048;  // points per shared-memory tile (16 KB)
 
@@ -24,22 +26,23 @@ __global__ void __launch_bounds__(kStatTPB) k_nearest_neighbour(const float2* __
 {
     __shared__ float2 tile[kStatTile];
     const int64_t set = blockIdx.y;
-    const float2* p = pts + set * n;
+    const int64_t n_all = (int64_t)gridDim.y * n;
     const int64_t i = (int64_t)blockIdx.x * kStatTPB + threadIdx.x;
-    const float2 me = (i < n) ? p[i] : make_float2(0.0f, 0.0f);
+    const float2 me = (i < n) ? *chk(pts, set * n + i, n_all) : make_float2(0.0f, 0.0f);
     float best = __int_as_float(0x7F800000);  // +inf
     for (int64_t t0 = 0; t0 < n; t0 += kStatTile) {
         const int len = (int)((n - t0 < kStatTile) ? n - t0 : kStatTile);
         __syncthreads();
-        for (int k = threadIdx.x; k < len; k += kStatTPB) tile[k] = p[t0 + k];
+        for (int k = threadIdx.x; k < len; k += kStatTPB) el(tile, k) = *chk(pts, set * n + t0 + k, n_all);
         __syncthreads();
         for (int k = 0; k < len; ++k) {
-            const float dx = tile[k].x - me.x, dy = tile[k].y - me.y;
+            const float2 q = el(tile, k);
+            const float dx = q.x - me.x, dy = q.y - me.y;
             const float d2 = fmaf(dx, dx, dy * dy);
             if (t0 + k != i && d2 < best) best = d2;
         }
     }
-    if (i < n) out[set * n + i] = (n > 1) ? sqrtf(best) : 0.0f;
+    if (i < n) *chk(out, set * n + i, n_all) = (n > 1) ? sqrtf(best) : 0.0f;
 }
 
 __global__ void __launch_bounds__(kStatTPB) k_star_discrepancy(const float2* __restrict__ pts, int64_t n,
@@ -48,22 +51,22 @@ __global__ void __launch_bounds__(kStatTPB) k_star_discrepancy(const float2* __r
     __shared__ float2 tile[kStatTile];
     __shared__ double red[kStatTPB / 32];
     const int64_t set = blockIdx.y;
-    const float2* p = pts + set * n;
+    const int64_t n_all = (int64_t)gridDim.y * n;
     const int64_t corners = (n + 1) * (n + 1);
     const int64_t c = (int64_t)blockIdx.x * kStatTPB + threadIdx.x;
     const bool live = c < corners;
     const int64_t ci = live ? c / (n + 1) : 0, cj = live ? c - ci * (n + 1) : 0;
-    const float u = (ci < n) ? p[ci].x : 1.0f;
-    const float v = (cj < n) ? p[cj].y : 1.0f;
+    const float u = (ci < n) ? chk(pts, set * n + ci, n_all)->x : 1.0f;
+    const float v = (cj < n) ? chk(pts, set * n + cj, n_all)->y : 1.0f;
     int64_t closed = 0, open = 0;
     for (int64_t t0 = 0; t0 < n; t0 += kStatTile) {
         const int len = (int)((n - t0 < kStatTile) ? n - t0 : kStatTile);
         __syncthreads();
-        for (int k = threadIdx.x; k < len; k += kStatTPB) tile[k] = p[t0 + k];
+        for (int k = threadIdx.x; k < len; k += kStatTPB) el(tile, k) = *chk(pts, set * n + t0 + k, n_all);
         __syncthreads();
         int cc = 0, oo = 0;
         for (int k = 0; k < len; ++k) {
-            const float2 q = tile[k];
+            const float2 q = el(tile, k);
             cc += (q.x <= u && q.y <= v) ? 1 : 0;
             oo += (q.x < u && q.y < v) ? 1 : 0;
         }

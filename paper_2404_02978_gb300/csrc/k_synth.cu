@@ -37,6 +37,8 @@
 
 namespace qrs {
 
+QRS_CHECK_HOOK(check_hook_synth)
+
 // Tunables (compile-time; the defaults are the measured best on GB300).
 #ifndef QRS_SYNTH_PPT
 #define QRS_SYNTH_PPT 12     // points per thread
@@ -121,7 +123,7 @@ __device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restr
         for (int q = 0; q < NP; ++q) part[q] = make_float2(0.0f, 0.0f);
 #pragma unroll kSynthUnroll
         for (int k = k0; k < k1; ++k) {
-            const float4 T = st[k];
+            const float4 T = *chk(st, k, (int64_t)len);
             const float2 A = make_float2(T.z, T.z);
             const uint64_t C = (uint64_t)__float_as_uint(T.w) * z.psi_mul + z.bias;
 #pragma unroll
@@ -169,7 +171,7 @@ __device__ __forceinline__ void accumulate_chunk_df_paired(const float4* __restr
         for (int q = 0; q < NP; ++q) part[q] = make_float2(0.0f, 0.0f);
 #pragma unroll kSynthUnroll
         for (int k = k0; k < k1; ++k) {
-            const float4 T = st[k];
+            const float4 T = *chk(st, k, (int64_t)len);
             const float2 A = make_float2(T.z, T.z);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
@@ -198,7 +200,7 @@ __device__ __forceinline__ void accumulate_chunk(const float4* __restrict__ st, 
         for (int j = 0; j < kSynthPPT; ++j) part[j] = 0.0f;
 #pragma unroll kSynthUnroll
         for (int k = k0; k < k1; ++k) {
-            const float4 T = st[k];
+            const float4 T = *chk(st, k, (int64_t)len);
             const uint64_t C = FIXED ? (uint64_t)__float_as_uint(T.w) * z.psi_mul + z.bias : 0ull;
 #pragma unroll
             for (int j = 0; j < kSynthPPT; ++j) {
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
 #pragma unroll
         for (int j = 0; j < kSynthPPT; ++j) {
             const int64_t m = base + j * kSynthTPB + threadIdx.x;
-            const float2 v = (m < P) ? xy[m] : make_float2(0.0f, 0.0f);
+            const float2 v = (m < P) ? *chk(xy, m, P) : make_float2(0.0f, 0.0f);
             if (z.use_fixed) {
                 X[j] = __float2int_rn(v.x * z.xscale);
                 Y[j] = __float2int_rn(v.y * z.xscale);
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
                         rec.w = (float)u * 0x1p-24f;
                     }
                     rec.z = t.F * amp;
-                    sterm[q] = rec;
+                    *chk(sterm, q, (int64_t)chunk) = rec;
                 }
                 __syncthreads();
                 cached_r = r;
@@ -297,11 +299,11 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
 #endif
             }
         }
-        float* o = out + r * P;
+        const int64_t n_out = (n_items / n_tiles) * P;
 #pragma unroll
         for (int j = 0; j < kSynthPPT; ++j) {
             const int64_t m = base + j * kSynthTPB + threadIdx.x;
-            if (m < P) o[m] = acc[j];
+            if (m < P) *chk(out, r * P + m, n_out) = acc[j];
         }
     }
 }

@@ -14,6 +14,8 @@
 
 namespace qrs {
 
+QRS_CHECK_HOOK(check_hook_api)
+
 qrs_status fail(qrs_handle* h, qrs_status st, const char* fmt, ...)
 {
     if (h) {
@@ -194,6 +196,13 @@ qrs_status qrs_create(qrs_handle** out, int32_t device)
         if (std::strstr(f, "launch")) h->fault |= kFaultLaunch;
         if (std::strstr(f, "timeout")) h->fault |= kFaultTimeout;
     }
+    if (const char* f = std::getenv("QRS_GRID_PAIR")) h->grid_pair = std::strcmp(f, "0") != 0;
+    if (e == cudaSuccess && qrs::kChecked) {  // the checked build reports into this handle's error word
+        for (cudaError_t (*hook)(int*) : {check_hook_api, check_hook_draw, check_hook_fft, check_hook_gemm,
+                                          check_hook_grid, check_hook_piston, check_hook_proposal, check_hook_sf,
+                                          check_hook_stats, check_hook_synth})
+            if (e == cudaSuccess) e = hook(h->d_err);
+    }
     if (e != cudaSuccess) {
         if (h->d_err) cudaFree(h->d_err);
         delete h;
@@ -218,6 +227,33 @@ void qrs_destroy(qrs_handle* h)
 const char* qrs_last_error(const qrs_handle* h) { return h ? h->last_error.c_str() : "null handle"; }
 
 int64_t qrs_launch_count(const qrs_handle* h) { return h ? h->launches : 0; }
+
+namespace qrs {
+
+__global__ void k_check_selftest(float* scratch, int64_t i)
+{
+    *chk(scratch, i, (int64_t)8) = 1.0f;
+}
+
+}  // namespace qrs
+
+int32_t qrs_checked_build(void) { return qrs::kChecked ? 1 : 0; }
+
+qrs_status qrs_check_selftest(qrs_handle* h, int64_t i, void* stream)
+{
+    if (!h) return QRS_ERR_ARG;
+    h->last_error.clear();
+    if (!qrs::kChecked) return fail(h, QRS_ERR_ARG, "qrs_check_selftest needs the bounds-checked library");
+    float* scratch = reinterpret_cast<float*>(reinterpret_cast<char*>(h->d_err) + 32);  // 8 floats of the handle's 64 B
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) {
+        qrs::k_check_selftest<<<1, 1, 0, (cudaStream_t)stream>>>(scratch, i);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "qrs_check_selftest launch");
+    ++h->launches;
+    return QRS_OK;
+}
 
 qrs_status qrs_sync(qrs_handle* h, void* stream)
 {

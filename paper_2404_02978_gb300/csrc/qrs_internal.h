@@ -9,6 +9,7 @@
 #include <string>
 
 #include "../../include/qrs.h"
+#include "qrs_check.cuh"
 #include "qrs_device.cuh"
 
 struct qrs_handle {
@@ -34,6 +35,11 @@ struct qrs_handle {
     // "timeout" makes the next GEMM-form launch wait out a bounded wait on a
     // barrier that nothing arrives at (QRS_ERR_TIMEOUT at the next qrs_sync).
     int fault = 0;
+    // Grid form: CTA pairs (k_grid_pair) allowed (QRS_GRID_PAIR=0 at
+    // qrs_create switches them off), and the clusters of two the GPU holds
+    // per precision (0: not yet queried, -1: unavailable).
+    int grid_pair = 1;
+    int grid_pair_clusters[2] = {0, 0};
 };
 
 namespace qrs {
@@ -80,6 +86,19 @@ cudaError_t launch_star_discrepancy(const float* pts, int64_t n_sets, int64_t n,
 cudaError_t launch_structure_fn(const float* delta, int64_t n_real, int64_t n_series, int64_t T,
                                 const int32_t* lags, int32_t n_lags, double* acc, int num_sms, int* err,
                                 cudaStream_t s);
+
+// Bounds-checked build: one hook per translation unit with kernels (each
+// points that unit's check word at `err`; no-ops in the default build).
+cudaError_t check_hook_draw(int* err);
+cudaError_t check_hook_fft(int* err);
+cudaError_t check_hook_gemm(int* err);
+cudaError_t check_hook_grid(int* err);
+cudaError_t check_hook_piston(int* err);
+cudaError_t check_hook_proposal(int* err);
+cudaError_t check_hook_sf(int* err);
+cudaError_t check_hook_stats(int* err);
+cudaError_t check_hook_synth(int* err);
+cudaError_t check_hook_api(int* err);
 
 struct PistonJobDev;
 void destroy_piston_state(qrs_handle* h);

@@ -61,8 +61,11 @@ CASES = {
     # square domain (Eq. 5), literal Eq. 3 coefficients
     "square-eq3": dict(x=(-2.0, 2.0, 129), y=(-2.5, 2.5, 257), p=dict(domain="square", fmax=4.0, coef="eq3"),
                        n_f=37 * 37, n_real=2, off=1),
-    # a single node, a single term
+    # a single node, a single term (one x tile: the single-CTA kernel)
     "one-node": dict(x=(0.3, 0.3, 1), y=(-1.1, -1.1, 1), p=dict(fmax=16.0), n_f=1, n_real=4, off=2),
+    # three x tiles: the second CTA pair's odd CTA has no x tile of its own
+    # (it still builds its half of the y rows); one ragged y block
+    "odd-tiles": dict(x=(-3.0, 3.1, 300), y=(-2.0, 2.0, 100), p=dict(fmax=16.0), n_f=500, n_real=3, off=9),
 }
 
 
@@ -86,6 +89,37 @@ def test_grid_parity(h, mode, case):
     print("grid %s %s: max err %.3g sigma, rms %.3g sigma" % (mode, case, err.max(), np.sqrt(np.mean(err ** 2))))
     assert np.isfinite(got).all()
     assert err.max() <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", ["gemm_3xtf32", "gemm_bf16x3"])
+def test_grid_cta_pairs_and_single_ctas(h, monkeypatch, mode):
+    """Grids of two or more x tiles run on CTA pairs (one MMA over two SMs);
+    QRS_GRID_PAIR=0 at handle creation keeps every tile on its own CTA.  Both
+    against the oracle at the same tolerance, and against each other."""
+    monkeypatch.setenv("QRS_GRID_PAIR", "0")
+    h1 = qrs.Handle(0)
+    monkeypatch.delenv("QRS_GRID_PAIR")
+    rng = np.random.default_rng(12)
+    x = np.sort(rng.uniform(-3.0, 3.0, 390)).astype(np.float32)  # 4 x tiles, the last one ragged
+    y = np.sort(rng.uniform(-2.5, 2.5, 520)).astype(np.float32)  # 3 y blocks, the last one ragged
+    p = oracle.params(seed=74, fmax=16.0)
+    n_f, R = 700, 2
+    pair = qrs.qrs_synthesize_grid(h, p, n_f, R, _dev(x), _dev(y), mode=mode, real_offset=3)
+    single = qrs.qrs_synthesize_grid(h1, p, n_f, R, _dev(x), _dev(y), mode=mode, real_offset=3)
+    qrs.qrs_sync(h)
+    qrs.qrs_sync(h1)
+    sig = _sigma(p, n_f, R, 3)
+    rows = rng.choice(len(y), 40, replace=False)
+    pts = _points(x, y[rows])
+    ref = oracle.synthesize(p, n_f, R, pts, real_offset=3)
+    for name, got in (("pair", pair), ("single", single)):
+        g = got[:, rows, :].cpu().numpy().reshape(R, -1).astype(np.float64)
+        err = np.abs(g - ref) / sig[:, None]
+        print("grid %s %s: max err %.3g sigma" % (mode, name, err.max()))
+        assert err.max() <= TOL[mode], name
+    d = (pair - single).abs().max().item()
+    print("grid %s pair vs single: max |diff| %.3g (%s)" % (mode, d, "bit-identical" if d == 0 else "differ"))
+    assert d <= 2 * TOL[mode] * sig.max()
 
 
 def test_grid_pupil_index_equals_fused(h):

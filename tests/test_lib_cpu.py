@@ -43,6 +43,25 @@ def test_library_exports_every_declared_symbol(libqrs):
         getattr(libqrs, n)
 
 
+def test_checked_build_exports_the_same_symbols(libqrs):
+    """libqrs_checked.so (QRS_CHECKED=1) is the same library with its kernels'
+    accesses bounds-checked: same exports; qrs_checked_build tells them apart
+    (a host function, callable without a GPU); qrs_check_selftest refuses a
+    null handle in both."""
+    from paper_2404_02978_gb300 import build as B
+    path = B.build_checked()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    missing = sorted(n for n in _declared() if n not in exported)
+    assert not missing, missing
+    checked = C.CDLL(path)
+    for L, want in ((libqrs, 0), (checked, 1)):
+        L.qrs_checked_build.restype = C.c_int32
+        assert L.qrs_checked_build() == want
+        L.qrs_check_selftest.argtypes = [C.c_void_p, C.c_int64, C.c_void_p]
+        assert L.qrs_check_selftest(None, 0, None) == -1
+
+
 def test_null_handle_is_rejected_without_a_device(libqrs):
     libqrs.qrs_sync.argtypes = [C.c_void_p, C.c_void_p]
     assert libqrs.qrs_sync(None, None) == -1
