@@ -83,7 +83,9 @@ constexpr bool kXCoefX = QRS_GRID_COEF_X != 0;
 constexpr int kXThreads = 128 + 32 * (kXPromoters + kXProducers);
 static_assert(kXProducers == 8 || kXProducers == 12 || kXProducers == 16, "producer warps");
 static_assert(kXPromoters == 4 || kXPromoters == 8, "promoter warps");
-constexpr int kXSmemBytes = kXStages * kXStageBytes + kXRecSlots * kXRecBytes + 512 + 1024;
+constexpr int kXStageFloats = 2 * QRS_GRID_PROMOTE_COLS * 32;  // two promotion staging buffers per promoter warp
+constexpr int kXSmemBytes =
+    kXStages * kXStageBytes + kXRecSlots * kXRecBytes + 512 + kXPromoters * kXStageFloats * 4 + 1024;
 constexpr long long kXWaitCycles = 4000000000LL;          // ~2 s of SM clock per wait
 constexpr size_t kXSlabBytes = (size_t)256 << 20;         // draw records per slab of realisations
 
@@ -241,6 +243,81 @@ __device__ __forceinline__ void produce_share(const int4* __restrict__ rr, unsig
     }
 }
 
+// Output store of a promoted value: grid node (xi, yj) of realisation row
+// orow, through the node -> point index when there is one.
+__device__ __forceinline__ void store_node(const GridArgs& g, int64_t orow, int64_t xi, int64_t yj, float v)
+{
+    if (xi >= g.nx || yj >= g.ny) return;
+    const int64_t node = yj * g.nx + xi;
+    if (g.index) {
+        const int32_t pidx = *chk(g.index, node, g.nx * g.ny);
+        if (pidx >= 0 && pidx < g.P) *chk(g.out, orow * g.P + pidx, g.out_rows * g.P) = v;
+        else if (pidx >= g.P) atomicExch(g.err, (int)QRS_ERR_DEVICE_CHECK);
+    } else {
+        *chk(g.out, orow * g.ny * g.nx + node, g.out_rows * g.ny * g.nx) = v;
+    }
+}
+
+// One segment's promotion by a promoter warp: TMEM lanes of its quarter
+// (slot_q carries the lane offset), columns [col0, col0 + span).  The CTA's
+// FP32 master lives in global memory (L2) as [quarter][column][32 lanes], so
+// each 16- or 32-column piece of a warp is one contiguous run: the warp
+// stages the slot's piece in shared memory and lane 0 hands it to the bulk
+// copy engine --
+//   first segment:   master piece := slot (bulk copy);
+//   later segments:  master piece += slot (bulk FP32 reduction in L2, one
+//                    rounded add per element, as master + slot in registers);
+//   last segment:    value = slot + master piece (read back after the warp's
+//                    bulk operations completed), or the slot alone when there
+//                    is one segment, to store(column, value).
+// So the warp never waits on L2 round trips before it frees the slot.  Two
+// staging buffers alternate (lane 0 waits until the bulk operation before
+// the previous one has read its buffer).  Returns with every bulk operation
+// issued; the caller waits for them (bulk_wait) before the CTA exits.
+template <int PC, class Store>
+__device__ __forceinline__ void promote_segment(const GridArgs& g, uint32_t slot_q, int64_t mq_off, float* stage,
+                                                int lane, int64_t j, bool last, int col0, int span, Store&& store)
+{
+    const int64_t n_master = (int64_t)gridDim.x * kXN * kXM;
+    float* mq = g.master + mq_off;
+    if (last && j > 0) {
+        if (lane == 0) sm100::bulk_wait<0>();
+        __syncwarp();
+        sm100::fence_proxy_async_global();
+    }
+    int buf = 0;
+#pragma unroll 1
+    for (int c0 = col0; c0 < col0 + span; c0 += PC) {
+        uint32_t v[PC];
+        sm100::tmem_ld_cols(slot_q + (uint32_t)c0, v);
+        sm100::tmem_ld_wait();
+        if (last) {
+            if (j > 0) {
+#pragma unroll
+                for (int q = 0; q < PC; ++q)
+                    v[q] = __float_as_uint(__uint_as_float(v[q]) +
+                                           *chk(g.master, mq_off + (int64_t)(c0 + q) * 32 + lane, n_master));
+            }
+#pragma unroll
+            for (int q = 0; q < PC; ++q) store(c0 + q, __uint_as_float(v[q]));
+        } else {
+            float* sb = stage + buf * PC * 32;
+            if (lane == 0) sm100::bulk_wait_read<1>();
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < PC; ++q) sb[q * 32 + lane] = __uint_as_float(v[q]);
+            sm100::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0 && chk_ok(mq_off + (int64_t)c0 * 32, PC * 32, n_master)) {
+                if (j == 0) sm100::bulk_store(mq + (int64_t)c0 * 32, sb, PC * 32 * 4);
+                else sm100::bulk_reduce_add_f32(mq + (int64_t)c0 * 32, sb, PC * 32 * 4);
+                sm100::bulk_commit();
+            }
+            buf ^= 1;
+        }
+    }
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constant__ GridArgs g)
 {
@@ -259,6 +336,7 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
     uint64_t* freeR = fullR + kXRecSlots;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeR + kXRecSlots);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* pstage = reinterpret_cast<float*>(rring + kXRecSlots * kXRecBytes + 512);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n_chunks = g.n_chunks;
@@ -379,12 +457,15 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
     } else if (warp >= 4 && warp < 4 + kXPromoters) {
         // ------------------------------------------------------ promoters
         constexpr int kSpan = kXN / (kXPromoters / 4);  // columns per promoter warp
+        constexpr int PC = QRS_GRID_PROMOTE_COLS;
+        static_assert(PC == 32 || PC == 16, "promotion width");
+        static_assert((kSpan / PC) % 2 == 0, "an even number of pieces per segment (staging buffers alternate)");
         const int quarter = warp & 3;                   // TMEM lanes [32 quarter, 32 quarter + 32)
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const uint32_t col0 = (uint32_t)(((warp - 4) >> 2) * kSpan);
-        float* mrow = g.master + (int64_t)blockIdx.x * kXN * kXM + row;  // this thread's master column
-        const int64_t n_master = (int64_t)gridDim.x * kXN * kXM;
+        const int col0 = ((warp - 4) >> 2) * kSpan;
+        const int64_t mq_off = (int64_t)blockIdx.x * kXN * kXM + (int64_t)quarter * kXN * 32;
+        float* stage = pstage + (warp - 4) * 2 * PC * 32;
         int64_t J = 0;
         bool stop = false;
         for (int64_t it = blockIdx.x; it < g.n_items && !stop; it += gridDim.x) {
@@ -400,50 +481,15 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                     break;
                 }
                 sm100::tc_fence_after();
-                const uint32_t slot = tmem_base + (uint32_t)(b * kXN) + lane_off + col0;
-                const bool last = (j == n_seg - 1);
-                constexpr int PC = QRS_GRID_PROMOTE_COLS;
-                static_assert(PC == 32 || PC == 16, "promotion width");
-#pragma unroll 1
-                for (int c0 = 0; c0 < kSpan; c0 += PC) {
-                    float* mp = mrow + (int64_t)(col0 + c0) * kXM;
-                    float m[PC];
-                    uint32_t v[PC];
-                    if (j > 0) {
-#pragma unroll
-                        for (int q = 0; q < PC; ++q) m[q] = *chk(g.master, (mp - g.master) + q * kXM, n_master);
-                    }
-                    sm100::tmem_ld_cols(slot + (uint32_t)c0, v);
-                    sm100::tmem_ld_wait();
-                    if (j > 0) {
-#pragma unroll
-                        for (int q = 0; q < PC; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + m[q]);
-                    }
-                    if (!last) {
-#pragma unroll
-                        for (int q = 0; q < PC; ++q) *chk(g.master, (mp - g.master) + q * kXM, n_master) = __uint_as_float(v[q]);
-                    } else if (xi < g.nx) {
-#pragma unroll
-                        for (int q = 0; q < PC; ++q) {
-                            const int64_t yj = nb * kXN + col0 + c0 + q;
-                            if (yj < g.ny) {
-                                const int64_t node = yj * g.nx + xi;
-                                if (g.index) {
-                                    const int32_t pidx = *chk(g.index, node, g.nx * g.ny);
-                                    if (pidx >= 0 && pidx < g.P) *chk(g.out, orow * g.P + pidx, g.out_rows * g.P) = __uint_as_float(v[q]);
-                                    else if (pidx >= g.P) atomicExch(g.err, (int)QRS_ERR_DEVICE_CHECK);
-                                } else {
-                                    *chk(g.out, orow * g.ny * g.nx + node, g.out_rows * g.ny * g.nx) = __uint_as_float(v[q]);
-                                }
-                            }
-                        }
-                    }
-                }
+                promote_segment<PC>(g, tmem_base + (uint32_t)(b * kXN) + lane_off, mq_off, stage, lane, j,
+                                    j == n_seg - 1, col0, kSpan,
+                                    [&](int c, float v) { store_node(g, orow, xi, nb * kXN + c, v); });
                 sm100::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) sm100::mbar_arrive(&seg_free[b]);
             }
         }
+        if (lane == 0) sm100::bulk_wait<0>();  // staging buffers are read before the CTA exits
     } else if (warp >= 4 + kXPromoters) {
         // ------------------------------------------------------ producers
         const int t = (warp - 4 - kXPromoters) * 32 + lane;
@@ -510,10 +556,12 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
 // of 384; the even CTA issues the MMAs for both (A: each CTA's own x rows; B:
 // the two y halves), and each CTA's TMEM receives the 128 x 256 accumulator of
 // its own x tile, promoted and stored by its own promoters as in k_grid_main.
-// Three 64 KB stages.  Barriers: the even CTA's full[s] counts both CTAs'
-// producer warps and its seg_free[b] both CTAs' promoter warps (the odd CTA
-// arrives remotely); the MMA commits arrive at empty[s] and seg_full[b] in
-// both CTAs (multicast).  A time-out in either CTA raises both abort flags;
+// Three 64 KB stages.  Barriers: each CTA's producer and promoter warps
+// arrive at their own full[s] and seg_free[b]; in the odd CTA one relay
+// thread per barrier kind forwards each completed phase to the even CTA's
+// barrier with a single release at cluster scope (a remote arrival from
+// every warp would put a cluster-wide memory barrier on each of them); the
+// MMA commits arrive at empty[s] and seg_full[b] in both CTAs (multicast).  A time-out in either CTA raises both abort flags;
 // both CTAs meet at a cluster barrier before TMEM is freed, so no MMA of the
 // pair is in flight and no remote arrival is pending when either exits.
 #ifndef QRS_GRID_PAIR_PRODUCERS
@@ -533,7 +581,9 @@ static_assert(kPProducers == 8 || kPProducers == 16, "pair producer warps");
 // extends 16 KB past the last stage's B tile (a read of twice a tile's rows
 // from any tile start stays inside the CTA's allocation).
 constexpr int kPRingOff = kPStages * kPStageBytes;
-constexpr int kPSmemBytes = kPStages * kPStageBytes + 16 * 1024 + 1024;
+constexpr int kPStageOff = kPStages * kPStageBytes + 16 * 1024;  // promotion staging, after the pad
+constexpr int kPSmemBytes = kPStageOff + kPPromoters * kXStageFloats * 4 + 1024;
+static_assert(kPSmemBytes <= 232448 && kXSmemBytes <= 232448, "shared memory per CTA");
 static_assert(kPRingOff + kXRecSlots * kXRecBytes + 512 <= kPStages * kPStageBytes + 16 * 1024, "ring fits the pad");
 
 template <int PREC, bool FIXED>
@@ -569,6 +619,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_grid_pair(const __grid_constan
     uint64_t* freeR = fullR + kXRecSlots;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeR + kXRecSlots);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* pstage = reinterpret_cast<float*>(smem + kPStageOff);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = sm100::cluster_ctarank();
@@ -581,12 +632,12 @@ __global__ void __launch_bounds__(kPThreads, 1) k_grid_pair(const __grid_constan
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kPStages; ++s) {
-            sm100::mbar_init(&full[s], 2 * kPProducers);
+            sm100::mbar_init(&full[s], leader ? kPProducers + 1 : kPProducers);  // + the peer's relay
             sm100::mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             sm100::mbar_init(&seg_full[b], 1);
-            sm100::mbar_init(&seg_free[b], 2 * kPPromoters);
+            sm100::mbar_init(&seg_free[b], leader ? kPPromoters + 1 : kPPromoters);
         }
         for (int s = 0; s < kXRecSlots; ++s) {
             sm100::mbar_init(&fullR[s], 1);
@@ -663,6 +714,32 @@ __global__ void __launch_bounds__(kPThreads, 1) k_grid_pair(const __grid_constan
                 }
             }
         }
+    } else if (warp == 0 || warp == 3) {
+        // ------------------------------------ relays (odd CTA): one release
+        // at cluster scope per event instead of one per arriving warp.
+        // Warp 0 forwards each completed phase of the local full[s] (all
+        // producer warps wrote their operand rows) to the even CTA's full[s];
+        // warp 3 each completed phase of seg_free[b] (all promoter warps
+        // have read the slot).
+        if (!leader && lane == 0) {
+            uint64_t* local = warp == 0 ? full : seg_free;
+            const int n_bar = warp == 0 ? kPStages : 2;
+            const uint32_t remote0 = sm100::mapa_shared(local, 0u);
+            const int64_t per_item = warp == 0 ? n_chunks : n_seg;
+            int64_t e = 0;
+            bool stop = false;
+            for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+                for (int64_t i = 0; i < per_item; ++i, ++e) {
+                    const int s = (int)(e % n_bar);
+                    if (!sm100::mbar_wait(&local[s], (uint32_t)((e / n_bar) & 1), abort_flag, kXWaitCycles)) {
+                        if (!*abort_flag) timeout();
+                        stop = true;
+                        break;
+                    }
+                    sm100::mbar_arrive_remote(remote0 + (uint32_t)(s * sizeof(uint64_t)));
+                }
+            }
+        }
     } else if (warp == 2) {
         // ------------------------------------------------- record ring
         if (lane == 0) {
@@ -695,12 +772,13 @@ __global__ void __launch_bounds__(kPThreads, 1) k_grid_pair(const __grid_constan
         }
     } else if (warp >= 4 && warp < 4 + kPPromoters) {
         // ------------------------------------------------------ promoters
+        constexpr int PC = QRS_GRID_PROMOTE_COLS;
+        static_assert((kXN / PC) % 2 == 0, "an even number of pieces per segment (staging buffers alternate)");
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        float* mrow = g.master + (int64_t)blockIdx.x * kXN * kXM + row;
-        const int64_t n_master = (int64_t)gridDim.x * kXN * kXM;
-        const uint32_t seg_free0 = sm100::mapa_shared(&seg_free[0], 0u);
+        const int64_t mq_off = (int64_t)blockIdx.x * kXN * kXM + (int64_t)quarter * kXN * 32;
+        float* stage = pstage + (warp - 4) * 2 * PC * 32;
         int64_t J = 0;
         bool stop = false;
         for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
@@ -710,62 +788,27 @@ __global__ void __launch_bounds__(kPThreads, 1) k_grid_pair(const __grid_constan
             const int64_t orow = g.r0 + r;
             for (int64_t j = 0; j < n_seg; ++j, ++J) {
                 const int b = (int)(J & 1);
-                if (!sm100::mbar_wait_cluster(&seg_full[b], (uint32_t)((J >> 1) & 1), abort_flag, kXWaitCycles)) {
+                if (!sm100::mbar_wait(&seg_full[b], (uint32_t)((J >> 1) & 1), abort_flag, kXWaitCycles)) {
                     if (!*abort_flag) timeout();
                     stop = true;
                     break;
                 }
                 sm100::tc_fence_after();
-                const uint32_t slot = tmem_base + (uint32_t)(b * kXN) + lane_off;
-                const bool last = (j == n_seg - 1);
-                constexpr int PC = QRS_GRID_PROMOTE_COLS;
-#pragma unroll 1
-                for (int c0 = 0; c0 < kXN; c0 += PC) {
-                    float* mp_ = mrow + (int64_t)c0 * kXM;
-                    float m[PC];
-                    uint32_t v[PC];
-                    if (j > 0) {
-#pragma unroll
-                        for (int q = 0; q < PC; ++q) m[q] = *chk(g.master, (mp_ - g.master) + q * kXM, n_master);
-                    }
-                    sm100::tmem_ld_cols(slot + (uint32_t)c0, v);
-                    sm100::tmem_ld_wait();
-                    if (j > 0) {
-#pragma unroll
-                        for (int q = 0; q < PC; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + m[q]);
-                    }
-                    if (!last) {
-#pragma unroll
-                        for (int q = 0; q < PC; ++q) *chk(g.master, (mp_ - g.master) + q * kXM, n_master) = __uint_as_float(v[q]);
-                    } else if (xi < g.nx) {
-#pragma unroll
-                        for (int q = 0; q < PC; ++q) {
-                            const int64_t yj = nb * kXN + c0 + q;
-                            if (yj < g.ny) {
-                                const int64_t node = yj * g.nx + xi;
-                                if (g.index) {
-                                    const int32_t pidx = *chk(g.index, node, g.nx * g.ny);
-                                    if (pidx >= 0 && pidx < g.P) *chk(g.out, orow * g.P + pidx, g.out_rows * g.P) = __uint_as_float(v[q]);
-                                    else if (pidx >= g.P) atomicExch(g.err, (int)QRS_ERR_DEVICE_CHECK);
-                                } else {
-                                    *chk(g.out, orow * g.ny * g.nx + node, g.out_rows * g.ny * g.nx) = __uint_as_float(v[q]);
-                                }
-                            }
-                        }
-                    }
-                }
+                promote_segment<PC>(g, tmem_base + (uint32_t)(b * kXN) + lane_off, mq_off, stage, lane, j,
+                                    j == n_seg - 1, 0, kXN,
+                                    [&](int c, float v) { store_node(g, orow, xi, nb * kXN + c, v); });
                 sm100::tc_fence_before();
                 __syncwarp();
-                if (lane == 0) sm100::mbar_arrive_remote(seg_free0 + (uint32_t)(b * sizeof(uint64_t)));
+                if (lane == 0) sm100::mbar_arrive(&seg_free[b]);
             }
         }
+        if (lane == 0) sm100::bulk_wait<0>();  // staging buffers are read before the CTA exits
     } else if (warp >= 4 + kPPromoters) {
         // ------------------------------------------------------ producers
         const int t = (warp - 4 - kPPromoters) * 32 + lane;
         const int xrow = kPProducers == 8 ? (t < kXM ? t : -1) : (t < 2 * kXM ? (t & 127) : -1);
         const int yrow = kPProducers == 8 ? (t >= kXM ? t - kXM : -1) : (t >= 2 * kXM ? ((t - 2 * kXM) & 127) : -1);
         const FixedScales z = fixed_scales(g.fbound, *g.d_bound, true);
-        const uint32_t full0 = sm100::mapa_shared(&full[0], 0u);
         int64_t gc = 0;
         bool stop = false;
         for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
@@ -779,7 +822,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_grid_pair(const __grid_constan
                 const int s = (int)(gc % kPStages);
                 const uint32_t ph = (uint32_t)((gc / kPStages) & 1);
                 if (*abort_flag ||
-                    (gc >= kPStages && !sm100::mbar_wait_cluster(&empty[s], ph ^ 1u, abort_flag, kXWaitCycles)) ||
+                    (gc >= kPStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kXWaitCycles)) ||
                     !sm100::mbar_wait(&fullR[gc % kXRecSlots], (uint32_t)((gc / kXRecSlots) & 1), abort_flag,
                                       kXWaitCycles)) {
                     if (!*abort_flag) timeout();
@@ -796,7 +839,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_grid_pair(const __grid_constan
                 sm100::fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    sm100::mbar_arrive_remote(full0 + (uint32_t)(s * sizeof(uint64_t)));
+                    sm100::mbar_arrive(&full[s]);
                     sm100::mbar_arrive(&freeR[gc % kXRecSlots]);
                 }
             }

@@ -48,7 +48,7 @@ def main():
         idx = torch.from_numpy(index).cuda()
         for i in range(a.repeat):
             qrs.qrs_synthesize_grid(h, wl.method_params(cfg), cfg["n_f"], a.n_real, cd, cd, index=idx,
-                                    mode=a.mode, real_offset=i * a.n_real)
+                                    n_points=int(inside.sum()), mode=a.mode, real_offset=i * a.n_real)
     elif a.case == "fft_screen":
         p = qrs.params(seed=21, r0=0.15, L0=30.0)
         for i in range(a.repeat):
