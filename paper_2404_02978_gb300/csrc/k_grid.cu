@@ -564,8 +564,14 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
 // MMA commits arrive at empty[s] and seg_full[b] in both CTAs (multicast).  A time-out in either CTA raises both abort flags;
 // both CTAs meet at a cluster barrier before TMEM is freed, so no MMA of the
 // pair is in flight and no remote arrival is pending when either exits.
-#ifndef QRS_GRID_PAIR_PRODUCERS
-#define QRS_GRID_PAIR_PRODUCERS 16  // producer warps per CTA: 8 (whole rows) or 16 (half rows)
+// Producer warps per CTA, per precision: 8 (whole rows) or 16 (half rows).
+// BF16X3 has twice the basis elements per K chunk and gains from 16; 3XTF32
+// is fastest with 8 (less per-chunk synchronisation per element).
+#ifndef QRS_GRID_PAIR_PRODUCERS_TF32
+#define QRS_GRID_PAIR_PRODUCERS_TF32 8
+#endif
+#ifndef QRS_GRID_PAIR_PRODUCERS_BF16
+#define QRS_GRID_PAIR_PRODUCERS_BF16 16
 #endif
 
 constexpr int kPStages = 3;
@@ -573,10 +579,14 @@ constexpr int kPHalfN = 128;                                   // y rows per CTA
 constexpr int kPTileA = kXM * 128;                             // 16 KB
 constexpr int kPTileB = kPHalfN * 128;                         // 16 KB
 constexpr int kPStageBytes = 2 * kPTileA + 2 * kPTileB;        // 64 KB
-constexpr int kPProducers = QRS_GRID_PAIR_PRODUCERS;
 constexpr int kPPromoters = 4;
-constexpr int kPThreads = 128 + 32 * (kPPromoters + kPProducers);
-static_assert(kPProducers == 8 || kPProducers == 16, "pair producer warps");
+template <int PREC>
+struct PairShape {
+    static constexpr int kProducers =
+        GemmCfg<PREC>::kTF32 ? QRS_GRID_PAIR_PRODUCERS_TF32 : QRS_GRID_PAIR_PRODUCERS_BF16;
+    static constexpr int kThreads = 128 + 32 * (kPPromoters + kProducers);
+    static_assert(kProducers == 8 || kProducers == 16, "pair producer warps");
+};
 // The operand stages, then the record ring and barriers, inside a region that
 // extends 16 KB past the last stage's B tile (a read of twice a tile's rows
 // from any tile start stays inside the CTA's allocation).
@@ -586,13 +596,13 @@ constexpr int kPSmemBytes = kPStageOff + kPPromoters * kXStageFloats * 4 + 1024;
 static_assert(kPSmemBytes <= 232448 && kXSmemBytes <= 232448, "shared memory per CTA");
 static_assert(kPRingOff + kXRecSlots * kXRecBytes + 512 <= kPStages * kPStageBytes + 16 * 1024, "ring fits the pad");
 
-template <int PREC, bool FIXED>
+template <int PREC, bool FIXED, int NPROD>
 __device__ __forceinline__ void produce_share_pair(const int4* __restrict__ rr, unsigned char* Ahi, unsigned char* Alo,
                                                    unsigned char* Bhi, unsigned char* Blo, int t, int32_t XA, float xa,
                                                    int32_t YB, float yb, uint64_t bias, uint32_t shift)
 {
     constexpr bool CX = kXCoefX, CY = !kXCoefX;
-    if (kPProducers == 8) {
+    if (NPROD == 8) {
         if (t < kXM) produce_row<PREC, FIXED, 0, CX, 4, kPTileA>(rr, Ahi, Alo, t, 0, XA, xa, bias, shift);
         else produce_row<PREC, FIXED, 1, CY, 4, kPTileB>(rr, Bhi, Blo, t - kXM, 0, YB, yb, bias, shift);
     } else {
@@ -603,9 +613,10 @@ __device__ __forceinline__ void produce_share_pair(const int4* __restrict__ rr, 
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kPThreads, 1) k_grid_pair(const __grid_constant__ GridArgs g)
+__global__ void __launch_bounds__(PairShape<PREC>::kThreads, 1) k_grid_pair(const __grid_constant__ GridArgs g)
 {
     using Cfg = GemmCfg<PREC>;
+    constexpr int kPProducers = PairShape<PREC>::kProducers;
     constexpr int T = Cfg::kTermsPerChunk;
     static_assert(T / Cfg::kTermsPer16B == 4, "four 16-byte groups per half row");
     extern __shared__ unsigned char smem_raw[];
@@ -831,10 +842,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_grid_pair(const __grid_constan
                 }
                 const int4* rr = reinterpret_cast<const int4*>(ringR(gc));
                 if (z.use_fixed)
-                    produce_share_pair<PREC, true>(rr, stageA_hi(s), stageA_lo(s), stageB_hi(s), stageB_lo(s), t, XA,
+                    produce_share_pair<PREC, true, kPProducers>(rr, stageA_hi(s), stageA_lo(s), stageB_hi(s), stageB_lo(s), t, XA,
                                                    xa, YB, yb, z.bias, z.shift);
                 else
-                    produce_share_pair<PREC, false>(rr, stageA_hi(s), stageA_lo(s), stageB_hi(s), stageB_lo(s), t, XA,
+                    produce_share_pair<PREC, false, kPProducers>(rr, stageA_hi(s), stageA_lo(s), stageB_hi(s), stageB_lo(s), t, XA,
                                                     xa, YB, yb, z.bias, z.shift);
                 sm100::fence_proxy_async_smem();
                 __syncwarp();
@@ -893,10 +904,11 @@ int64_t grid_launch_count(int mode, int64_t n_f, int64_t n_real)
     return 1 + 2 * ((n_real + slab - 1) / slab);
 }
 
-static void pair_launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute (&at)[1], unsigned grid, cudaStream_t s)
+static void pair_launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute (&at)[1], unsigned grid, int threads,
+                               cudaStream_t s)
 {
     cfg.gridDim = dim3(grid, 1, 1);
-    cfg.blockDim = dim3(kPThreads, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
     cfg.dynamicSmemBytes = kPSmemBytes;
     cfg.stream = s;
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -922,7 +934,7 @@ static int grid_pair_clusters(qrs_handle* h)
         if (e == cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute at[1];
-            pair_launch_config(cfg, at, (unsigned)(h->num_sms & ~1), nullptr);
+            pair_launch_config(cfg, at, (unsigned)(h->num_sms & ~1), PairShape<PREC>::kThreads, nullptr);
             e = cudaOccupancyMaxActiveClusters(&n, k_grid_pair<PREC>, &cfg);
         }
         if (e != cudaSuccess) cudaGetLastError();  // the single-SM kernel serves instead
@@ -984,7 +996,7 @@ static cudaError_t launch_grid_t(qrs_handle* h, const DrawParams& p, const float
             const int64_t nc = a.n_items < clusters ? a.n_items : clusters;
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute at[1];
-            pair_launch_config(cfg, at, (unsigned)(2 * nc), s);
+            pair_launch_config(cfg, at, (unsigned)(2 * nc), PairShape<PREC>::kThreads, s);
             e = cudaLaunchKernelEx(&cfg, k_grid_pair<PREC>, a);
         } else {
             a.n_items = nr * a.n_mt * a.n_nb;
