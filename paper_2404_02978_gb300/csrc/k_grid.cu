@@ -261,29 +261,36 @@ __device__ __forceinline__ void store_node(const GridArgs& g, int64_t orow, int6
 // One segment's promotion by a promoter warp: TMEM lanes of its quarter
 // (slot_q carries the lane offset), columns [col0, col0 + span).  The CTA's
 // FP32 master lives in global memory (L2) as [quarter][column][32 lanes], so
-// each 16- or 32-column piece of a warp is one contiguous run: the warp
-// stages the slot's piece in shared memory and lane 0 hands it to the bulk
-// copy engine --
-//   first segment:   master piece := slot (bulk copy);
-//   later segments:  master piece += slot (bulk FP32 reduction in L2, one
-//                    rounded add per element, as master + slot in registers);
-//   last segment:    value = slot + master piece (read back after the warp's
-//                    bulk operations completed), or the slot alone when there
-//                    is one segment, to store(column, value).
-// So the warp never waits on L2 round trips before it frees the slot.  Two
-// staging buffers alternate (lane 0 waits until the bulk operation before
-// the previous one has read its buffer).  Returns with every bulk operation
-// issued; the caller waits for them (bulk_wait) before the CTA exits.
-template <int PC, class Store>
+// a warp's accesses to one column are one contiguous 128-byte run and each
+// 16-column piece one contiguous 2 KB run --
+//   first segment:   master := slot;
+//   later segments:  master += slot, an FP32 add in L2 (one rounded add per
+//                    element, as master + slot in registers would give);
+//   last segment:    value = slot + master (read back once the warp's adds
+//                    are complete), or the slot alone when there is one
+//                    segment, to store(column, value).
+// So the warp never waits on an L2 round trip before it frees the slot.  Two
+// ways to hand a piece to L2:
+//   RED:   each lane's reduction (red.global.add.f32) straight from registers;
+//   !RED:  the piece staged in shared memory and one bulk copy / bulk FP32
+//          reduction by lane 0 (two staging buffers alternate; lane 0 waits
+//          until the operation before the previous one has read its buffer).
+// Returns with every operation issued; with !RED the caller waits for them
+// (bulk_wait) before the CTA exits.
+template <int PC, bool RED, class Store>
 __device__ __forceinline__ void promote_segment(const GridArgs& g, uint32_t slot_q, int64_t mq_off, float* stage,
                                                 int lane, int64_t j, bool last, int col0, int span, Store&& store)
 {
     const int64_t n_master = (int64_t)gridDim.x * kXN * kXM;
     float* mq = g.master + mq_off;
     if (last && j > 0) {
-        if (lane == 0) sm100::bulk_wait<0>();
-        __syncwarp();
-        sm100::fence_proxy_async_global();
+        if (!RED) {
+            if (lane == 0) sm100::bulk_wait<0>();
+            __syncwarp();
+            sm100::fence_proxy_async_global();
+        } else {
+            __threadfence();  // this thread's reductions precede its loads of the same addresses
+        }
     }
     int buf = 0;
 #pragma unroll 1
@@ -300,6 +307,13 @@ __device__ __forceinline__ void promote_segment(const GridArgs& g, uint32_t slot
             }
 #pragma unroll
             for (int q = 0; q < PC; ++q) store(c0 + q, __uint_as_float(v[q]));
+        } else if (RED) {
+#pragma unroll
+            for (int q = 0; q < PC; ++q) {
+                float* a = chk(g.master, mq_off + (int64_t)(c0 + q) * 32 + lane, n_master);
+                if (j == 0) *a = __uint_as_float(v[q]);
+                else sm100::red_add_f32(a, __uint_as_float(v[q]));
+            }
         } else {
             float* sb = stage + buf * PC * 32;
             if (lane == 0) sm100::bulk_wait_read<1>();
@@ -481,8 +495,8 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                     break;
                 }
                 sm100::tc_fence_after();
-                promote_segment<PC>(g, tmem_base + (uint32_t)(b * kXN) + lane_off, mq_off, stage, lane, j,
-                                    j == n_seg - 1, col0, kSpan,
+                promote_segment<PC, false>(g, tmem_base + (uint32_t)(b * kXN) + lane_off, mq_off, stage, lane, j,
+                                           j == n_seg - 1, col0, kSpan,
                                     [&](int c, float v) { store_node(g, orow, xi, nb * kXN + c, v); });
                 sm100::tc_fence_before();
                 __syncwarp();
@@ -579,20 +593,30 @@ constexpr int kPHalfN = 128;                                   // y rows per CTA
 constexpr int kPTileA = kXM * 128;                             // 16 KB
 constexpr int kPTileB = kPHalfN * 128;                         // 16 KB
 constexpr int kPStageBytes = 2 * kPTileA + 2 * kPTileB;        // 64 KB
-constexpr int kPPromoters = 4;
+// Promoter warps per CTA (4, 8 or 16, sharing each TMEM lane quarter's 256
+// columns): the L2 reductions of a segment's slot then run from that many
+// warps in parallel.
+#ifndef QRS_GRID_PAIR_PROMOTERS_TF32
+#define QRS_GRID_PAIR_PROMOTERS_TF32 8
+#endif
+#ifndef QRS_GRID_PAIR_PROMOTERS_BF16
+#define QRS_GRID_PAIR_PROMOTERS_BF16 8
+#endif
 template <int PREC>
 struct PairShape {
     static constexpr int kProducers =
         GemmCfg<PREC>::kTF32 ? QRS_GRID_PAIR_PRODUCERS_TF32 : QRS_GRID_PAIR_PRODUCERS_BF16;
-    static constexpr int kThreads = 128 + 32 * (kPPromoters + kProducers);
+    static constexpr int kPromoters =
+        GemmCfg<PREC>::kTF32 ? QRS_GRID_PAIR_PROMOTERS_TF32 : QRS_GRID_PAIR_PROMOTERS_BF16;
+    static constexpr int kThreads = 128 + 32 * (kPromoters + kProducers);
     static_assert(kProducers == 8 || kProducers == 16, "pair producer warps");
+    static_assert(kPromoters == 4 || kPromoters == 8 || kPromoters == 16, "pair promoter warps");
 };
 // The operand stages, then the record ring and barriers, inside a region that
 // extends 16 KB past the last stage's B tile (a read of twice a tile's rows
 // from any tile start stays inside the CTA's allocation).
 constexpr int kPRingOff = kPStages * kPStageBytes;
-constexpr int kPStageOff = kPStages * kPStageBytes + 16 * 1024;  // promotion staging, after the pad
-constexpr int kPSmemBytes = kPStageOff + kPPromoters * kXStageFloats * 4 + 1024;
+constexpr int kPSmemBytes = kPStages * kPStageBytes + 16 * 1024 + 1024;
 static_assert(kPSmemBytes <= 232448 && kXSmemBytes <= 232448, "shared memory per CTA");
 static_assert(kPRingOff + kXRecSlots * kXRecBytes + 512 <= kPStages * kPStageBytes + 16 * 1024, "ring fits the pad");
 
@@ -617,6 +641,7 @@ __global__ void __launch_bounds__(PairShape<PREC>::kThreads, 1) k_grid_pair(cons
 {
     using Cfg = GemmCfg<PREC>;
     constexpr int kPProducers = PairShape<PREC>::kProducers;
+    constexpr int kPPromoters = PairShape<PREC>::kPromoters;
     constexpr int T = Cfg::kTermsPerChunk;
     static_assert(T / Cfg::kTermsPer16B == 4, "four 16-byte groups per half row");
     extern __shared__ unsigned char smem_raw[];
@@ -630,7 +655,6 @@ __global__ void __launch_bounds__(PairShape<PREC>::kThreads, 1) k_grid_pair(cons
     uint64_t* freeR = fullR + kXRecSlots;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeR + kXRecSlots);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    float* pstage = reinterpret_cast<float*>(smem + kPStageOff);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = sm100::cluster_ctarank();
@@ -784,12 +808,12 @@ __global__ void __launch_bounds__(PairShape<PREC>::kThreads, 1) k_grid_pair(cons
     } else if (warp >= 4 && warp < 4 + kPPromoters) {
         // ------------------------------------------------------ promoters
         constexpr int PC = QRS_GRID_PROMOTE_COLS;
-        static_assert((kXN / PC) % 2 == 0, "an even number of pieces per segment (staging buffers alternate)");
+        constexpr int kSpan = kXN / (kPPromoters / 4);  // columns per promoter warp
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const int col0 = ((warp - 4) >> 2) * kSpan;
         const int64_t mq_off = (int64_t)blockIdx.x * kXN * kXM + (int64_t)quarter * kXN * 32;
-        float* stage = pstage + (warp - 4) * 2 * PC * 32;
         int64_t J = 0;
         bool stop = false;
         for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
@@ -805,15 +829,14 @@ __global__ void __launch_bounds__(PairShape<PREC>::kThreads, 1) k_grid_pair(cons
                     break;
                 }
                 sm100::tc_fence_after();
-                promote_segment<PC>(g, tmem_base + (uint32_t)(b * kXN) + lane_off, mq_off, stage, lane, j,
-                                    j == n_seg - 1, 0, kXN,
+                promote_segment<PC, true>(g, tmem_base + (uint32_t)(b * kXN) + lane_off, mq_off, nullptr, lane, j,
+                                          j == n_seg - 1, col0, kSpan,
                                     [&](int c, float v) { store_node(g, orow, xi, nb * kXN + c, v); });
                 sm100::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) sm100::mbar_arrive(&seg_free[b]);
             }
         }
-        if (lane == 0) sm100::bulk_wait<0>();  // staging buffers are read before the CTA exits
     } else if (warp >= 4 + kPPromoters) {
         // ------------------------------------------------------ producers
         const int t = (warp - 4 - kPPromoters) * 32 + lane;

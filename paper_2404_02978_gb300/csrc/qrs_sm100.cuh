@@ -129,6 +129,12 @@ __device__ __forceinline__ void bulk_wait()
     asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// global FP32 += v in L2 (round to nearest), no value returned.
+__device__ __forceinline__ void red_add_f32(float* gaddr, float v)
+{
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(gaddr), "f"(v) : "memory");
+}
+
 // Async-proxy writes to global memory -> visible to generic loads.
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
