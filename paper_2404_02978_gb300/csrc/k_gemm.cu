@@ -19,28 +19,30 @@
 // map, into the basis representation), k_gemm_coef (B, hi and lo, into the
 // workspace, K'-contiguous rows so TMA can stream them), k_gemm_main.
 //
-// k_gemm_main: one CTA per (128-point tile, 256-column block), 640 threads:
+// k_gemm_main: a persistent grid, one CTA per SM, walking work items
+// (256-column block, 128-point tile), tile fastest, so the CTAs at work at
+// one time share a column block's coefficient tiles in L2.  Warps:
 //   warp 0      TMA producer: B_hi and B_lo tiles (256 rows x 128 B, 128-byte
 //               swizzle) per K chunk into a 2-stage ring (mbarrier complete_tx);
-//   warp 1      TMEM allocator (512 columns: a 128 x 256 FP32 master
-//               accumulator and a 128 x 256 segment slot) and single-thread
-//               MMA issuer: 3 x 4 tcgen05.mma per K chunk into the slot, one
-//               commit per segment of kSeg chunks (6 TF32, 8 BF16);
+//   warp 1      TMEM allocator (512 columns: two 128 x 256 FP32 segment
+//               slots) and single-thread MMA issuer: 3 x 4 tcgen05.mma per K
+//               chunk into the segment's slot, one commit per segment of kSeg
+//               chunks (6 TF32, 8 BF16, 18 single TF32); the slots alternate,
+//               so the MMAs never wait for a promotion;
 //   warp 2      frequency ring: bulk-copies each chunk's basis frequencies
 //               into an 8-slot shared-memory ring, up to 8 chunks ahead;
 //   warps 4-11  promoters, two per TMEM lane quarter (128 columns each): after
-//               each segment, master += slot in FP32 (round to nearest) through
-//               tcgen05.ld / tcgen05.st, then free the slot; after the last
-//               segment they store out[r][m] (coalesced over m).  The tensor
+//               each segment they hand the slot to the CTA's FP32 master in L2
+//               (promote_red: := slot, then += slot by FP32 reductions in L2),
+//               free the slot, and after an item's last segment store
+//               out[r][m] = slot + master (coalesced over m).  The tensor
 //               core's accumulation loses about 2^-26 per step with a
 //               consistent sign, so long chains drift; segments bound it;
-//   warps 12-19 basis producers, two per 32-row block, each taking half of
-//               the chunk's terms: evaluate cos/sin (fixed-point or
-//               double-float phase, MUFU sin/cos), split hi/lo by integer
-//               rounding and write their 16-byte pieces of the row in the
-//               swizzled A tiles, fence.proxy.async, one arrival per warp.
-//               (Basis production is the bound of this kernel; 8 producer
-//               warps beat 4 by 8 % (3xTF32) and 27 % (BF16x3).)
+//   warps 12-   basis producers, two or four per 32-row block, each taking a
+//               share of the chunk's terms: evaluate cos/sin (fixed-point or
+//               double-float phase, MUFU sin/cos), split hi/lo and write their
+//               16-byte pieces of the row in the swizzled A tiles,
+//               fence.proxy.async, one arrival per warp.
 // Every mbarrier wait is bounded in time; on time-out the CTA raises an abort
 // flag, records QRS_ERR_TIMEOUT in the device error word, waits (bounded) for
 // its TMA copies and MMAs in flight, frees TMEM and returns.
@@ -82,12 +84,14 @@ constexpr int kGTileB = kGN * 128;                         // 32 KB
 constexpr int kGStageBytes = 2 * kGTileA + 2 * kGTileB;    // A hi/lo + B hi/lo = 96 KB
 constexpr int kGFreqSlots = 8;                             // frequency ring, filled ahead by warp 2
 constexpr int kGFreqBytes = 256;                           // one chunk's basis frequencies (<= 32 x 8 B)
+constexpr int kGPromoters = 8;                             // promoter warps, two per TMEM lane quarter
 template <int PREC>
 struct GemmShape {
     static constexpr bool kBF16 = !GemmCfg<PREC>::kTF32;
     static constexpr int kProducers = kBF16 ? QRS_GEMM_PRODUCERS_BF16 : QRS_GEMM_PRODUCERS_TF32;
     static constexpr int kPromoteCols = kBF16 ? QRS_GEMM_PROMOTE_COLS_BF16 : QRS_GEMM_PROMOTE_COLS_TF32;
-    static constexpr int kThreads = 384 + 32 * kProducers;
+    static constexpr int kThreads = 128 + 32 * (kGPromoters + kProducers);
+    static constexpr bool kTmemMaster = GemmCfg<PREC>::kTF32 && GemmCfg<PREC>::kSplit;  // 3XTF32
     static_assert(kProducers == 4 || kProducers == 8 || kProducers == 16, "producer warps");
     static_assert(kPromoteCols == 32 || kPromoteCols == 16, "promotion width");
 };
@@ -101,6 +105,9 @@ struct GemmArgs {
     int64_t n_real;     // valid columns
     int64_t R_pad;      // rows of each B half (multiple of 256)
     int64_t n_chunks;   // K chunks (2 N_f_pad / elements per row)
+    int64_t n_tiles;    // 128-point tiles
+    int64_t n_items;    // work items (column block, point tile), tile fastest
+    float* master;      // [gridDim.x][4][256][32] FP32 segment sums of the CTAs' current items (L2)
     const int2* fbasis; // [N_f_pad] basis frequency (Fx, Fy) or float bits (fx, fy)
     const float* d_xbound;
     float fbound;
@@ -210,18 +217,24 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
     uint64_t* fullA = reinterpret_cast<uint64_t*>(fring + kGFreqSlots * kGFreqBytes);
     uint64_t* fullB = fullA + kGStages;
     uint64_t* empty = fullB + kGStages;
-    uint64_t* seg_full = empty + kGStages;
-    uint64_t* seg_free = seg_full + 1;
-    uint64_t* fullF = seg_free + 1;
+    uint64_t* seg_full = empty + kGStages;  // [2], one per TMEM segment slot
+    uint64_t* seg_free = seg_full + 2;      // [2]
+    uint64_t* fullF = seg_free + 2;
     uint64_t* freeF = fullF + kGFreqSlots;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeF + kGFreqSlots);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     uint64_t* never = reinterpret_cast<uint64_t*>(tmem_slot + 2);  // fault injection: no thread arrives here
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tile = blockIdx.x, rblk = blockIdx.y;
     const int64_t n_chunks = g.n_chunks;
     const int64_t n_seg = (n_chunks + Cfg::kSeg - 1) / Cfg::kSeg;
+    // 3XTF32 keeps its FP32 master in TMEM (one slot, the MMAs wait for each
+    // promotion; no memory traffic beside its operand streams), the other
+    // modes in L2 (two slots, the MMAs never wait; promote_red) -- whichever
+    // measured faster.  Segment J's slot, and the parities of its barriers:
+    constexpr bool kTmemMaster = GemmShape<PREC>::kTmemMaster;
+    auto slot_of = [](int64_t J) { return kTmemMaster ? 0 : (int)(J & 1); };
+    auto use_of = [](int64_t J) { return (uint32_t)((kTmemMaster ? J : (J >> 1)) & 1); };  // J-th use of its slot
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kGStages; ++s) {
@@ -229,8 +242,10 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
             sm100::mbar_init(&fullB[s], 1);
             sm100::mbar_init(&empty[s], 1);
         }
-        sm100::mbar_init(seg_full, 1);
-        sm100::mbar_init(seg_free, 8);  // one arrival per promoter warp
+        for (int b = 0; b < 2; ++b) {
+            sm100::mbar_init(&seg_full[b], 1);
+            sm100::mbar_init(&seg_free[b], kGPromoters);  // one arrival per promoter warp
+        }
         for (int s = 0; s < kGFreqSlots; ++s) {
             sm100::mbar_init(&fullF[s], 1);
             sm100::mbar_init(&freeF[s], kGProducers);
@@ -244,8 +259,7 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
     sm100::tc_fence_before();
     __syncthreads();
     sm100::tc_fence_after();
-    const uint32_t tmem_master = *tmem_slot;                 // columns [0, 256)
-    const uint32_t tmem_seg = tmem_master + (uint32_t)kGN;  // columns [256, 512)
+    const uint32_t tmem_base = *tmem_slot;  // two 256-column regions: slots 0, 1 (or master, slot)
 
     auto stageA_hi = [&](int s) { return smem + s * kGStageBytes; };
     auto stageA_lo = [&](int s) { return smem + s * kGStageBytes + kGTileA; };
@@ -263,19 +277,25 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
     if (warp == 0) {
         // ---------------------------------------------------- TMA producer
         if (lane == 0) {
-            int64_t issued = 0;
-            for (int64_t i = 0; i < n_chunks; ++i) {
-                const int s = (int)(i % kGStages);
-                const uint32_t ph = (uint32_t)((i / kGStages) & 1);
-                if (i >= kGStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kGWaitCycles)) {
-                    if (!*abort_flag) timeout();
-                    break;
+            int64_t gc = 0, issued = 0;
+            bool stop = false;
+            for (int64_t it = blockIdx.x; it < g.n_items && !stop; it += gridDim.x) {
+                const int64_t rblk = it / g.n_tiles;
+                for (int64_t i = 0; i < n_chunks; ++i, ++gc) {
+                    const int s = (int)(gc % kGStages);
+                    const uint32_t ph = (uint32_t)((gc / kGStages) & 1);
+                    if (*abort_flag || (gc >= kGStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kGWaitCycles))) {
+                        if (!*abort_flag) timeout();
+                        stop = true;
+                        break;
+                    }
+                    sm100::mbar_arrive_expect_tx(&fullB[s], (Cfg::kSplit ? 2u : 1u) * kGTileB);
+                    const int32_t x = (int32_t)(i * Cfg::kElemsPerRow);
+                    sm100::tma_load_2d(stageB_hi(s), &tmapB, &fullB[s], x, (int32_t)(rblk * kGN));
+                    if (Cfg::kSplit)
+                        sm100::tma_load_2d(stageB_lo(s), &tmapB, &fullB[s], x, (int32_t)(g.R_pad + rblk * kGN));
+                    issued = gc + 1;
                 }
-                sm100::mbar_arrive_expect_tx(&fullB[s], (Cfg::kSplit ? 2u : 1u) * kGTileB);
-                const int32_t x = (int32_t)(i * Cfg::kElemsPerRow);
-                sm100::tma_load_2d(stageB_hi(s), &tmapB, &fullB[s], x, (int32_t)(rblk * kGN));
-                if (Cfg::kSplit) sm100::tma_load_2d(stageB_lo(s), &tmapB, &fullB[s], x, (int32_t)(g.R_pad + rblk * kGN));
-                issued = i + 1;
             }
             if (*abort_flag) {  // let copies in flight land before the CTA exits
                 for (int64_t i = (issued > kGStages ? issued - kGStages : 0); i < issued; ++i)
@@ -291,191 +311,210 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
             // time-out path (abort flag, error word, drained copies, TMEM freed).
             if (g.inject_wait > 0 && !sm100::mbar_wait(never, 0u, abort_flag, g.inject_wait) && !*abort_flag)
                 timeout();
-            int64_t i = 0;
-            for (int64_t j = 0; j < n_seg && !*abort_flag; ++j) {
-                if (j >= 1 && !sm100::mbar_wait(seg_free, (uint32_t)((j - 1) & 1), abort_flag, kGWaitCycles)) {
-                    if (!*abort_flag) timeout();
-                    break;
-                }
-                const int64_t i_end = ((j + 1) * Cfg::kSeg < n_chunks) ? (j + 1) * Cfg::kSeg : n_chunks;
-                bool first = true;
-                for (; i < i_end; ++i) {
-                    const int s = (int)(i % kGStages);
-                    const uint32_t ph = (uint32_t)((i / kGStages) & 1);
-                    if (!sm100::mbar_wait(&fullA[s], ph, abort_flag, kGWaitCycles) ||
-                        !sm100::mbar_wait(&fullB[s], ph, abort_flag, kGWaitCycles)) {
+            int64_t J = 0, gc = 0;
+            bool stop = *abort_flag != 0;
+            for (int64_t it = blockIdx.x; it < g.n_items && !stop; it += gridDim.x) {
+                int64_t i = 0;
+                for (int64_t j = 0; j < n_seg; ++j, ++J) {
+                    const int b = slot_of(J);
+                    const int64_t Jp = J - (kTmemMaster ? 1 : 2);  // the slot's previous segment
+                    if (*abort_flag ||
+                        (Jp >= 0 && !sm100::mbar_wait(&seg_free[b], use_of(Jp), abort_flag, kGWaitCycles))) {
                         if (!*abort_flag) timeout();
+                        stop = true;
                         break;
                     }
-                    sm100::tc_fence_after();
-                    const uint32_t ahi = sm100::smem_u32(stageA_hi(s)), alo = sm100::smem_u32(stageA_lo(s));
-                    const uint32_t bhi = sm100::smem_u32(stageB_hi(s)), blo = sm100::smem_u32(stageB_lo(s));
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {  // four 32-byte K steps per 128-byte row
-                        const uint32_t off = (uint32_t)kk * 32u;
-                        const uint64_t dAh = sm100::desc_k_sw128(ahi + off), dAl = sm100::desc_k_sw128(alo + off);
-                        const uint64_t dBh = sm100::desc_k_sw128(bhi + off), dBl = sm100::desc_k_sw128(blo + off);
-                        sm100::mma<Cfg::kTF32>(tmem_seg, dAh, dBh, idesc, first ? 0u : 1u);
-                        first = false;
-                        if (Cfg::kSplit) {
-                            sm100::mma<Cfg::kTF32>(tmem_seg, dAh, dBl, idesc, 1u);
-                            sm100::mma<Cfg::kTF32>(tmem_seg, dAl, dBh, idesc, 1u);
+                    const int64_t i_end = ((j + 1) * Cfg::kSeg < n_chunks) ? (j + 1) * Cfg::kSeg : n_chunks;
+                    const uint32_t tmem_seg = tmem_base + (uint32_t)((kTmemMaster ? 1 : b) * kGN);
+                    bool first = true;
+                    for (; i < i_end; ++i, ++gc) {
+                        const int s = (int)(gc % kGStages);
+                        const uint32_t ph = (uint32_t)((gc / kGStages) & 1);
+                        if (!sm100::mbar_wait(&fullA[s], ph, abort_flag, kGWaitCycles) ||
+                            !sm100::mbar_wait(&fullB[s], ph, abort_flag, kGWaitCycles)) {
+                            if (!*abort_flag) timeout();
+                            stop = true;
+                            break;
                         }
+                        sm100::tc_fence_after();
+                        const uint32_t ahi = sm100::smem_u32(stageA_hi(s)), alo = sm100::smem_u32(stageA_lo(s));
+                        const uint32_t bhi = sm100::smem_u32(stageB_hi(s)), blo = sm100::smem_u32(stageB_lo(s));
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {  // four 32-byte K steps per 128-byte row
+                            const uint32_t off = (uint32_t)kk * 32u;
+                            const uint64_t dAh = sm100::desc_k_sw128(ahi + off), dAl = sm100::desc_k_sw128(alo + off);
+                            const uint64_t dBh = sm100::desc_k_sw128(bhi + off), dBl = sm100::desc_k_sw128(blo + off);
+                            sm100::mma<Cfg::kTF32>(tmem_seg, dAh, dBh, idesc, first ? 0u : 1u);
+                            first = false;
+                            if (Cfg::kSplit) {
+                                sm100::mma<Cfg::kTF32>(tmem_seg, dAh, dBl, idesc, 1u);
+                                sm100::mma<Cfg::kTF32>(tmem_seg, dAl, dBh, idesc, 1u);
+                            }
+                        }
+                        sm100::mma_commit(&empty[s]);  // frees stage s once these MMAs complete
                     }
-                    sm100::mma_commit(&empty[s]);  // frees stage s once these MMAs complete
+                    sm100::mma_commit(&seg_full[b]);  // segment done (or cut short by an abort)
+                    mma_segments = J + 1;
+                    if (stop) break;
                 }
-                sm100::mma_commit(seg_full);  // segment j done (or cut short by an abort)
-                mma_segments = j + 1;
             }
         }
     } else if (warp == 2) {
         // -------------------------------------------- frequency ring filler
         if (lane == 0) {
-            int64_t issued = 0;
-            for (int64_t i = 0; i < n_chunks; ++i) {
-                const int f = (int)(i % kGFreqSlots);
-                if (i >= kGFreqSlots &&
-                    !sm100::mbar_wait(&freeF[f], (uint32_t)(((i / kGFreqSlots) & 1) ^ 1), abort_flag, kGWaitCycles)) {
-                    if (!*abort_flag) timeout();
-                    break;
+            int64_t gc = 0, issued = 0;
+            bool stop = false;
+            for (int64_t it = blockIdx.x; it < g.n_items && !stop; it += gridDim.x) {
+                for (int64_t i = 0; i < n_chunks; ++i, ++gc) {
+                    const int f = (int)(gc % kGFreqSlots);
+                    if (*abort_flag || (gc >= kGFreqSlots &&
+                                        !sm100::mbar_wait(&freeF[f], (uint32_t)(((gc / kGFreqSlots) & 1) ^ 1),
+                                                          abort_flag, kGWaitCycles))) {
+                        if (!*abort_flag) timeout();
+                        stop = true;
+                        break;
+                    }
+                    if (chk_ok(i * Cfg::kTermsPerChunk, Cfg::kTermsPerChunk, n_chunks * Cfg::kTermsPerChunk)) {
+                        sm100::mbar_arrive_expect_tx(&fullF[f], kFreqChunkBytes);
+                        sm100::bulk_load(ringF(gc), g.fbasis + i * Cfg::kTermsPerChunk, kFreqChunkBytes, &fullF[f]);
+                    } else {
+                        sm100::mbar_arrive(&fullF[f]);  // checked build: the slot keeps its old frequencies
+                    }
+                    issued = gc + 1;
                 }
-                if (chk_ok(i * Cfg::kTermsPerChunk, Cfg::kTermsPerChunk, n_chunks * Cfg::kTermsPerChunk)) {
-                    sm100::mbar_arrive_expect_tx(&fullF[f], kFreqChunkBytes);
-                    sm100::bulk_load(ringF(i), g.fbasis + i * Cfg::kTermsPerChunk, kFreqChunkBytes, &fullF[f]);
-                } else {
-                    sm100::mbar_arrive(&fullF[f]);  // checked build: the slot keeps its old frequencies
-                }
-                issued = i + 1;
             }
             if (*abort_flag) {
                 for (int64_t i = (issued > kGFreqSlots ? issued - kGFreqSlots : 0); i < issued; ++i)
                     sm100::mbar_wait_for(&fullF[i % kGFreqSlots], (uint32_t)((i / kGFreqSlots) & 1), kGWaitCycles / 8);
             }
         }
-    } else if (warp >= 4 && warp < 12) {
+    } else if (warp >= 4 && warp < 4 + kGPromoters) {
         // ------------------------------------------------------ promoters
-        const int quarter = warp & 3;        // TMEM lanes [32 quarter, 32 quarter + 32)
-        const int half = (warp - 4) >> 2;    // columns [128 half, 128 half + 128)
+        constexpr int PC = GemmShape<PREC>::kPromoteCols;
+        constexpr int kSpan = kGN / (kGPromoters / 4);  // columns per promoter warp
+        const int quarter = warp & 3;                   // TMEM lanes [32 quarter, 32 quarter + 32)
         const int row = quarter * 32 + lane;
-        const int64_t m = tile * kGM + row;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const uint32_t col0 = (uint32_t)(half * 128);
-        bool ok = true;
-        for (int64_t j = 0; j < n_seg; ++j) {
-            if (!sm100::mbar_wait(seg_full, (uint32_t)(j & 1), abort_flag, kGWaitCycles)) {
-                if (!*abort_flag) timeout();
-                ok = false;
-                break;
-            }
-            sm100::tc_fence_after();
-            const bool last = (j == n_seg - 1);
-            constexpr int PC = GemmShape<PREC>::kPromoteCols;
-#pragma unroll 1
-            for (int c0 = 0; c0 < 128; c0 += PC) {
-                uint32_t v[PC], w[PC];
-                sm100::tmem_ld_cols(tmem_seg + lane_off + col0 + (uint32_t)c0, v);
-                if (j > 0) sm100::tmem_ld_cols(tmem_master + lane_off + col0 + (uint32_t)c0, w);
-                sm100::tmem_ld_wait();
-                if (j > 0) {
-#pragma unroll
-                    for (int q = 0; q < PC; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
+        const int col0 = ((warp - 4) >> 2) * kSpan;
+        const int64_t n_master = (int64_t)gridDim.x * kGN * kGM;
+        const int64_t mq_off = (int64_t)blockIdx.x * kGN * kGM + (int64_t)quarter * kGN * 32;
+        int64_t J = 0;
+        bool stop = false;
+        for (int64_t it = blockIdx.x; it < g.n_items && !stop; it += gridDim.x) {
+            const int64_t rblk = it / g.n_tiles, tile = it - rblk * g.n_tiles;
+            const int64_t m = tile * kGM + row;
+            for (int64_t j = 0; j < n_seg; ++j, ++J) {
+                const int b = slot_of(J);
+                if (!sm100::mbar_wait(&seg_full[b], use_of(J), abort_flag, kGWaitCycles)) {
+                    if (!*abort_flag) timeout();
+                    stop = true;
+                    break;
                 }
-                if (!last) {
-                    sm100::tmem_st_cols(tmem_master + lane_off + col0 + (uint32_t)c0, v);
-                } else if (m < g.P) {
-#pragma unroll
-                    for (int q = 0; q < PC; ++q) {
-                        const int64_t r = rblk * kGN + col0 + c0 + q;
-                        if (r < g.n_real) *chk(g.out, r * g.P + m, g.n_real * g.P) = __uint_as_float(v[q]);
-                    }
-                }
+                sm100::tc_fence_after();
+                auto store = [&](int c, float v) {
+                    const int64_t r = rblk * kGN + c;
+                    if (m < g.P && r < g.n_real) *chk(g.out, r * g.P + m, g.n_real * g.P) = v;
+                };
+                if (kTmemMaster)
+                    promote_tmem<PC>(tmem_base + lane_off, tmem_base + (uint32_t)kGN + lane_off, j, j == n_seg - 1,
+                                     col0, kSpan, store);
+                else
+                    promote_red<PC>(g.master, n_master, mq_off, tmem_base + (uint32_t)(b * kGN) + lane_off, lane, j,
+                                    j == n_seg - 1, col0, kSpan, store);
+                sm100::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) sm100::mbar_arrive(&seg_free[b]);
             }
-            sm100::tmem_st_wait();
-            sm100::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) sm100::mbar_arrive(seg_free);
         }
-        (void)ok;
-    } else if (warp >= 12) {
+    } else if (warp >= 4 + kGPromoters) {
         // ------------------------------------------- basis producers
-        const int pw = warp - 12;                  // producer warp
+        const int pw = warp - 4 - kGPromoters;     // producer warp
         const int row = (pw & 3) * 32 + lane;      // its row block
         constexpr int kGroups = 4 / (kGProducers / 4);
         const int grp0 = (pw >> 2) * kGroups;      // its term groups [grp0, grp0 + kGroups)
-        const int64_t m = tile * kGM + row;
-        const float2 pt = (m < g.P) ? *chk(g.xy, m, g.P) : make_float2(0.0f, 0.0f);
         const FixedScales z = fixed_scales(g.fbound, *g.d_xbound, true);
-        const int32_t X = __float2int_rn(pt.x * z.xscale), Y = __float2int_rn(pt.y * z.xscale);
         constexpr int TPG = Cfg::kTermsPer16B;
         const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
         const float2 neg_two_pi = make_float2(-6.28318530717958648f, -6.28318530717958648f);
-        for (int64_t i = 0; i < n_chunks && !*abort_flag; ++i) {
-            const int s = (int)(i % kGStages);
-            const uint32_t ph = (uint32_t)((i / kGStages) & 1);
-            if ((i >= kGStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kGWaitCycles)) ||
-                !sm100::mbar_wait(&fullF[i % kGFreqSlots], (uint32_t)((i / kGFreqSlots) & 1), abort_flag,
-                                  kGWaitCycles)) {
-                if (!*abort_flag) timeout();
-                break;
-            }
-            const int2* fb = reinterpret_cast<const int2*>(ringF(i));
-            unsigned char* Ahi = stageA_hi(s);
-            unsigned char* Alo = stageA_lo(s);
+        int64_t gc = 0;
+        bool stop = false;
+        for (int64_t it = blockIdx.x; it < g.n_items && !stop; it += gridDim.x) {
+            const int64_t tile = it % g.n_tiles;
+            const int64_t m = tile * kGM + row;
+            const float2 pt = (m < g.P) ? *chk(g.xy, m, g.P) : make_float2(0.0f, 0.0f);
+            const int32_t X = __float2int_rn(pt.x * z.xscale), Y = __float2int_rn(pt.y * z.xscale);
+            for (int64_t i = 0; i < n_chunks; ++i, ++gc) {
+                const int s = (int)(gc % kGStages);
+                const uint32_t ph = (uint32_t)((gc / kGStages) & 1);
+                if (*abort_flag || (gc >= kGStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kGWaitCycles)) ||
+                    !sm100::mbar_wait(&fullF[gc % kGFreqSlots], (uint32_t)((gc / kGFreqSlots) & 1), abort_flag,
+                                      kGWaitCycles)) {
+                    if (!*abort_flag) timeout();
+                    stop = true;
+                    break;
+                }
+                const int2* fb = reinterpret_cast<const int2*>(ringF(gc));
+                unsigned char* Ahi = stageA_hi(s);
+                unsigned char* Alo = stageA_lo(s);
 #pragma unroll
-            for (int gi = 0; gi < kGroups; ++gi) {
-                const int grp = grp0 + gi;
-                float cv[TPG], sv[TPG];
+                for (int gi = 0; gi < kGroups; ++gi) {
+                    const int grp = grp0 + gi;
+                    float cv[TPG], sv[TPG];
 #pragma unroll
-                for (int t = 0; t < TPG; t += 2) {  // two terms per paired FP32 instruction
-                    const int2 f0 = *chk(fb, grp * TPG + t, Cfg::kTermsPerChunk);
-                    const int2 f1 = *chk(fb, grp * TPG + t + 1, Cfg::kTermsPerChunk);
-                    float2 ang;
-                    if (z.use_fixed) {
-                        const uint32_t m0 = phase_fx_word(f0.x, f0.y, X, Y, z.bias, z.shift);
-                        const uint32_t m1 = phase_fx_word(f1.x, f1.y, X, Y, z.bias, z.shift);
-                        ang = __ffma2_rn(make_float2(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u),
-                                                     __uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u)),
-                                         two_pi, neg_two_pi);
-                    } else {
-                        ang = __fmul2_rn(phase_df2f(make_float2(__int_as_float(f0.x), __int_as_float(f1.x)),
-                                                    make_float2(__int_as_float(f0.y), __int_as_float(f1.y)), pt.x, pt.y),
-                                         two_pi);
+                    for (int t = 0; t < TPG; t += 2) {  // two terms per paired FP32 instruction
+                        const int2 f0 = *chk(fb, grp * TPG + t, Cfg::kTermsPerChunk);
+                        const int2 f1 = *chk(fb, grp * TPG + t + 1, Cfg::kTermsPerChunk);
+                        float2 ang;
+                        if (z.use_fixed) {
+                            const uint32_t m0 = phase_fx_word(f0.x, f0.y, X, Y, z.bias, z.shift);
+                            const uint32_t m1 = phase_fx_word(f1.x, f1.y, X, Y, z.bias, z.shift);
+                            ang = __ffma2_rn(make_float2(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u),
+                                                         __uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u)),
+                                             two_pi, neg_two_pi);
+                        } else {
+                            ang = __fmul2_rn(phase_df2f(make_float2(__int_as_float(f0.x), __int_as_float(f1.x)),
+                                                        make_float2(__int_as_float(f0.y), __int_as_float(f1.y)), pt.x,
+                                                        pt.y),
+                                             two_pi);
+                        }
+                        sv[t] = __sinf(ang.x);
+                        cv[t] = __cosf(ang.x);
+                        sv[t + 1] = __sinf(ang.y);
+                        cv[t + 1] = __cosf(ang.y);
                     }
-                    sv[t] = __sinf(ang.x);
-                    cv[t] = __cosf(ang.x);
-                    sv[t + 1] = __sinf(ang.y);
-                    cv[t + 1] = __cosf(ang.y);
+                    const uint32_t oc = sm100::sw128_offset((uint32_t)row, (uint32_t)grp);
+                    const uint32_t os = sm100::sw128_offset((uint32_t)row, (uint32_t)(4 + grp));
+                    uint4 hi, lo;
+                    pack16<PREC>(cv, hi, lo);
+                    if (chk_ok(oc, 16, kGTileA)) {
+                        *reinterpret_cast<uint4*>(Ahi + oc) = hi;
+                        if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + oc) = lo;
+                    }
+                    pack16<PREC>(sv, hi, lo);
+                    if (chk_ok(os, 16, kGTileA)) {
+                        *reinterpret_cast<uint4*>(Ahi + os) = hi;
+                        if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + os) = lo;
+                    }
                 }
-                const uint32_t oc = sm100::sw128_offset((uint32_t)row, (uint32_t)grp);
-                const uint32_t os = sm100::sw128_offset((uint32_t)row, (uint32_t)(4 + grp));
-                uint4 hi, lo;
-                pack16<PREC>(cv, hi, lo);
-                if (chk_ok(oc, 16, kGTileA)) {
-                    *reinterpret_cast<uint4*>(Ahi + oc) = hi;
-                    if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + oc) = lo;
+                sm100::fence_proxy_async_smem();  // each thread: its row writes -> async proxy
+                __syncwarp();
+                if (lane == 0) {
+                    sm100::mbar_arrive(&fullA[s]);
+                    sm100::mbar_arrive(&freeF[gc % kGFreqSlots]);
                 }
-                pack16<PREC>(sv, hi, lo);
-                if (chk_ok(os, 16, kGTileA)) {
-                    *reinterpret_cast<uint4*>(Ahi + os) = hi;
-                    if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + os) = lo;
-                }
-            }
-            sm100::fence_proxy_async_smem();  // each thread: its row writes -> async proxy
-            __syncwarp();
-            if (lane == 0) {
-                sm100::mbar_arrive(&fullA[s]);
-                sm100::mbar_arrive(&freeF[i % kGFreqSlots]);
             }
         }
     }
     sm100::tc_fence_before();
     __syncthreads();
     if (warp == 1) {
-        if (*abort_flag && lane == 0 && mma_segments > 0)  // MMAs in flight finish before TMEM is freed
-            sm100::mbar_wait_for(seg_full, (uint32_t)((mma_segments - 1) & 1), kGWaitCycles / 8);
+        if (*abort_flag && lane == 0 && mma_segments > 0) {  // MMAs in flight finish before TMEM is freed
+            const int64_t Jl = mma_segments - 1;
+            sm100::mbar_wait_for(&seg_full[slot_of(Jl)], use_of(Jl), kGWaitCycles / 8);
+        }
         __syncwarp();
         sm100::tc_fence_after();
-        sm100::tmem_dealloc(tmem_master, 512);
+        sm100::tmem_dealloc(tmem_base, 512);
     }
 }
 
@@ -494,7 +533,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode()
     return fn;
 }
 
-size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real)
+size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real, int num_sms)
 {
     const bool bf16 = mode == QRS_SYNTH_GEMM_BF16X3;
     const int T = bf16 ? GemmCfg<QRS_SYNTH_GEMM_BF16X3>::kTermsPerChunk : GemmCfg<QRS_SYNTH_GEMM_3XTF32>::kTermsPerChunk;
@@ -503,7 +542,8 @@ size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real)
     const int64_t nf_pad = (n_f + T - 1) / T * T;
     const int64_t R_pad = (n_real + kGN - 1) / kGN * kGN;
     const size_t b = (size_t)halves * R_pad * (2 * nf_pad) * eb;  // hi (and lo) halves
-    return 256 + b + (size_t)nf_pad * (sizeof(int2) + sizeof(float4)) + 1024;
+    return 256 + b + (size_t)nf_pad * (sizeof(int2) + sizeof(float4)) + 1024 +
+           (size_t)num_sms * kGN * kGM * sizeof(float);  // the CTAs' FP32 masters
 }
 
 template <int PREC>
@@ -521,6 +561,7 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     const size_t bbytes = (size_t)(Cfg::kSplit ? 2 : 1) * R_pad * Kp * Cfg::kElemBytes;
     int2* fbasis = reinterpret_cast<int2*>(base + bbytes);
     float4* fw = reinterpret_cast<float4*>(fbasis + nf_pad);
+    float* master = reinterpret_cast<float*>(((uintptr_t)(fw + nf_pad) + 255) & ~(uintptr_t)255);
 
     cudaError_t e = launch_point_bound(xy, P, h->d_xbound, s);
     if (e != cudaSuccess) return e;
@@ -550,6 +591,9 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     a.n_real = n_real;
     a.R_pad = R_pad;
     a.n_chunks = Kp / Cfg::kElemsPerRow;
+    a.n_tiles = (P + kGM - 1) / kGM;
+    a.n_items = a.n_tiles * (R_pad / kGN);
+    a.master = master;
     a.fbasis = fbasis;
     a.d_xbound = h->d_xbound;
     a.fbound = fbound;
@@ -561,8 +605,8 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     }
     e = cudaFuncSetAttribute(k_gemm_main<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemBytes);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((P + kGM - 1) / kGM), (unsigned)(R_pad / kGN));
-    k_gemm_main<PREC><<<grid, GemmShape<PREC>::kThreads, kGSmemBytes, s>>>(tmap, a);
+    const int64_t ctas = a.n_items < h->num_sms ? a.n_items : h->num_sms;  // persistent: one CTA per SM
+    k_gemm_main<PREC><<<(unsigned)ctas, GemmShape<PREC>::kThreads, kGSmemBytes, s>>>(tmap, a);
     return cudaGetLastError();
 }
 

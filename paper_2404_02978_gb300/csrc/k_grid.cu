@@ -258,39 +258,25 @@ __device__ __forceinline__ void store_node(const GridArgs& g, int64_t orow, int6
     }
 }
 
-// One segment's promotion by a promoter warp: TMEM lanes of its quarter
-// (slot_q carries the lane offset), columns [col0, col0 + span).  The CTA's
-// FP32 master lives in global memory (L2) as [quarter][column][32 lanes], so
-// a warp's accesses to one column are one contiguous 128-byte run and each
-// 16-column piece one contiguous 2 KB run --
-//   first segment:   master := slot;
-//   later segments:  master += slot, an FP32 add in L2 (one rounded add per
-//                    element, as master + slot in registers would give);
-//   last segment:    value = slot + master (read back once the warp's adds
-//                    are complete), or the slot alone when there is one
-//                    segment, to store(column, value).
-// So the warp never waits on an L2 round trip before it frees the slot.  Two
-// ways to hand a piece to L2:
-//   RED:   each lane's reduction (red.global.add.f32) straight from registers;
-//   !RED:  the piece staged in shared memory and one bulk copy / bulk FP32
-//          reduction by lane 0 (two staging buffers alternate; lane 0 waits
-//          until the operation before the previous one has read its buffer).
-// Returns with every operation issued; with !RED the caller waits for them
-// (bulk_wait) before the CTA exits.
-template <int PC, bool RED, class Store>
+// The single-CTA kernel's segment promotion: as promote_red (the master in
+// L2 as [quarter][column][32 lanes], := slot, += slot, slot + master at the
+// last segment), but each 16- or 32-column piece of the warp is staged in
+// shared memory and handed to L2 as one bulk copy / bulk FP32 reduction by
+// lane 0 (two staging buffers alternate; lane 0 waits until the operation
+// before the previous one has read its buffer).  Returns with every bulk
+// operation issued; the caller waits for them (bulk_wait) before the CTA
+// exits.  (With 4 promoter warps this beats per-lane reductions; the pair
+// kernel's 8 promoter warps use promote_red.)
+template <int PC, class Store>
 __device__ __forceinline__ void promote_segment(const GridArgs& g, uint32_t slot_q, int64_t mq_off, float* stage,
                                                 int lane, int64_t j, bool last, int col0, int span, Store&& store)
 {
     const int64_t n_master = (int64_t)gridDim.x * kXN * kXM;
     float* mq = g.master + mq_off;
     if (last && j > 0) {
-        if (!RED) {
-            if (lane == 0) sm100::bulk_wait<0>();
-            __syncwarp();
-            sm100::fence_proxy_async_global();
-        } else {
-            __threadfence();  // this thread's reductions precede its loads of the same addresses
-        }
+        if (lane == 0) sm100::bulk_wait<0>();
+        __syncwarp();
+        sm100::fence_proxy_async_global();
     }
     int buf = 0;
 #pragma unroll 1
@@ -307,13 +293,6 @@ __device__ __forceinline__ void promote_segment(const GridArgs& g, uint32_t slot
             }
 #pragma unroll
             for (int q = 0; q < PC; ++q) store(c0 + q, __uint_as_float(v[q]));
-        } else if (RED) {
-#pragma unroll
-            for (int q = 0; q < PC; ++q) {
-                float* a = chk(g.master, mq_off + (int64_t)(c0 + q) * 32 + lane, n_master);
-                if (j == 0) *a = __uint_as_float(v[q]);
-                else sm100::red_add_f32(a, __uint_as_float(v[q]));
-            }
         } else {
             float* sb = stage + buf * PC * 32;
             if (lane == 0) sm100::bulk_wait_read<1>();
@@ -495,8 +474,8 @@ __global__ void __launch_bounds__(kXThreads, 1) k_grid_main(const __grid_constan
                     break;
                 }
                 sm100::tc_fence_after();
-                promote_segment<PC, false>(g, tmem_base + (uint32_t)(b * kXN) + lane_off, mq_off, stage, lane, j,
-                                           j == n_seg - 1, col0, kSpan,
+                promote_segment<PC>(g, tmem_base + (uint32_t)(b * kXN) + lane_off, mq_off, stage, lane, j,
+                                    j == n_seg - 1, col0, kSpan,
                                     [&](int c, float v) { store_node(g, orow, xi, nb * kXN + c, v); });
                 sm100::tc_fence_before();
                 __syncwarp();
@@ -829,8 +808,8 @@ __global__ void __launch_bounds__(PairShape<PREC>::kThreads, 1) k_grid_pair(cons
                     break;
                 }
                 sm100::tc_fence_after();
-                promote_segment<PC, true>(g, tmem_base + (uint32_t)(b * kXN) + lane_off, mq_off, nullptr, lane, j,
-                                          j == n_seg - 1, col0, kSpan,
+                promote_red<PC>(g.master, (int64_t)gridDim.x * kXN * kXM, mq_off, tmem_base + (uint32_t)(b * kXN) + lane_off,
+                                lane, j, j == n_seg - 1, col0, kSpan,
                                     [&](int c, float v) { store_node(g, orow, xi, nb * kXN + c, v); });
                 sm100::tc_fence_before();
                 __syncwarp();

@@ -323,7 +323,7 @@ qrs_status qrs_synthesize_points(qrs_handle* h, const qrs_psd* psd, const qrs_do
     if (mode == QRS_SYNTH_GEMM_3XTF32 || mode == QRS_SYNTH_GEMM_BF16X3 || mode == QRS_SYNTH_GEMM_TF32) {
         if (n_real > 65280) return fail(h, QRS_ERR_ARG, "GEMM modes take at most 65280 realisations per call");
         if (col_psd && ((uintptr_t)col_psd & 7)) return fail(h, QRS_ERR_ARG, "col_psd must be 8-byte aligned");
-        st = ensure_work(h, gemm_workspace_bytes(mode, n_f, n_real));
+        st = ensure_work(h, gemm_workspace_bytes(mode, n_f, n_real, h->num_sms));
         if (st != QRS_OK) return st;
         e = launch_synth_gemm(h, mode, p, xy, n_points, n_real, col_psd, vk_constant(), out, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "qrs_synthesize_points GEMM launch");

@@ -103,7 +103,7 @@ cudaError_t check_hook_api(int* err);
 struct PistonJobDev;
 void destroy_piston_state(qrs_handle* h);
 
-size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real);
+size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real, int num_sms);
 cudaError_t launch_synth_gemm(qrs_handle* h, int mode, const DrawParams& p, const float* xy, int64_t P,
                               int64_t n_real, const double* col_psd, double c_vk, float* out, cudaStream_t s);
 

@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 
 #include "qrs_internal.h"
+#include "qrs_sm100.cuh"
 
 #ifndef QRS_GEMM_SEG_TF32
 #define QRS_GEMM_SEG_TF32 6   // K chunks per accumulation segment, 3XTF32 (72 accumulation steps)
@@ -143,6 +144,83 @@ __device__ __forceinline__ void pack16(const float (&v)[GemmCfg<PREC>::kTermsPer
 #endif
         }
     }
+}
+
+// Segment promotion of a 128 x 256 TMEM accumulator slot into an FP32
+// master held in global memory (L2), by one promoter warp: TMEM lanes of its
+// quarter (slot_q carries the lane offset), columns [col0, col0 + span), PC
+// columns per TMEM load.  The master of the CTA sits at master + mq_off (the
+// quarter's base) as [column][32 lanes], so the warp's accesses to a column
+// are one 128-byte run --
+//   first segment:   master := slot;
+//   later segments:  master += slot by FP32 reductions in L2 (red.global.add,
+//                    one rounded add per element, the same as master + slot
+//                    in registers), issued without waiting for a reply;
+//   last segment:    value = slot + master (this thread's own reductions are
+//                    ordered before its loads of the same addresses), or the
+//                    slot alone when there is one segment, to store(column,
+//                    value).
+// (Four-wide vector reductions measured slower.)  The tensor core's FP32
+// accumulation loses about 2^-26 per step with a consistent sign;
+// restarting the slot each segment and adding segments in FP32 with round
+// to nearest bounds that drift.
+template <int PC, class Store>
+__device__ __forceinline__ void promote_red(float* master, int64_t n_master, int64_t mq_off, uint32_t slot_q, int lane,
+                                            int64_t j, bool last, int col0, int span, Store&& store)
+{
+    if (last && j > 0) __threadfence();
+#pragma unroll 1
+    for (int c0 = col0; c0 < col0 + span; c0 += PC) {
+        uint32_t v[PC];
+        sm100::tmem_ld_cols(slot_q + (uint32_t)c0, v);
+        sm100::tmem_ld_wait();
+        if (last) {
+            if (j > 0) {
+#pragma unroll
+                for (int q = 0; q < PC; ++q)
+                    v[q] = __float_as_uint(__uint_as_float(v[q]) +
+                                           *chk(master, mq_off + (int64_t)(c0 + q) * 32 + lane, n_master));
+            }
+#pragma unroll
+            for (int q = 0; q < PC; ++q) store(c0 + q, __uint_as_float(v[q]));
+        } else {
+#pragma unroll
+            for (int q = 0; q < PC; ++q) {
+                float* a = chk(master, mq_off + (int64_t)(c0 + q) * 32 + lane, n_master);
+                if (j == 0) *a = __uint_as_float(v[q]);
+                else sm100::red_add_f32(a, __uint_as_float(v[q]));
+            }
+        }
+    }
+}
+
+// The same promotion with the master in TMEM (a second 128 x 256 region,
+// master_q with the lane offset): master := slot / master += slot through
+// tcgen05.ld / tcgen05.st, value = slot + master at the last segment.  No
+// memory traffic, but the slot and the master fill TMEM, so the MMAs of the
+// next segment wait until the promotion has read the slot.
+template <int PC, class Store>
+__device__ __forceinline__ void promote_tmem(uint32_t master_q, uint32_t slot_q, int64_t j, bool last, int col0,
+                                             int span, Store&& store)
+{
+#pragma unroll 1
+    for (int c0 = col0; c0 < col0 + span; c0 += PC) {
+        uint32_t v[PC], w[PC];
+        sm100::tmem_ld_cols(slot_q + (uint32_t)c0, v);
+        if (j > 0) sm100::tmem_ld_cols(master_q + (uint32_t)c0, w);
+        sm100::tmem_ld_wait();
+        if (j > 0) {
+#pragma unroll
+            for (int q = 0; q < PC; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
+        }
+        if (!last) {
+            sm100::tmem_st_cols(master_q + (uint32_t)c0, v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < PC; ++q) store(c0 + q, __uint_as_float(v[q]));
+        }
+    }
+    sm100::tmem_st_wait();
 }
 
 }  // namespace qrs
