@@ -533,12 +533,16 @@ static cudaError_t launch_persistent_t(const PistonJobDev* d_jobs, int n_jobs, i
     return cudaGetLastError();
 }
 
-int piston_shape_count() { return 3; }
+// The autotuner's candidates (threads per CTA, terms per (group, slice)
+// unit): more, shorter slices balance short draws (small N_f) across the
+// warps; longer ones amortise each unit's form choice and reduction.
+int piston_shape_count() { return 5; }
 
 const char* piston_shape_name(int shape)
 {
-    static const char* names[] = {"tpb256_slice256", "tpb256_slice128", "tpb128_slice128"};
-    return (shape >= 0 && shape < 3) ? names[shape] : "?";
+    static const char* names[] = {"tpb256_slice256", "tpb256_slice128", "tpb128_slice128", "tpb256_slice64",
+                                  "tpb128_slice256"};
+    return (shape >= 0 && shape < 5) ? names[shape] : "?";
 }
 
 cudaError_t launch_piston_persistent(int shape, const PistonJobDev* d_jobs, int n_jobs, int64_t n_items,
@@ -547,6 +551,8 @@ cudaError_t launch_piston_persistent(int shape, const PistonJobDev* d_jobs, int 
     switch (shape) {
     case 1: return launch_persistent_t<PisShape<256, 128>>(d_jobs, n_jobs, n_items, d_counter, num_sms, err, s);
     case 2: return launch_persistent_t<PisShape<128, 128>>(d_jobs, n_jobs, n_items, d_counter, num_sms, err, s);
+    case 3: return launch_persistent_t<PisShape<256, 64>>(d_jobs, n_jobs, n_items, d_counter, num_sms, err, s);
+    case 4: return launch_persistent_t<PisShape<128, 256>>(d_jobs, n_jobs, n_items, d_counter, num_sms, err, s);
     default: return launch_persistent_t<PisShape<256, 256>>(d_jobs, n_jobs, n_items, d_counter, num_sms, err, s);
     }
 }

@@ -103,7 +103,7 @@ def test_autotune_cache_file(tmp_path):
         hh = qrs.Handle(0)
         _submit(hh, _jobs(5, seed=3), qrs.PISTON_PERSISTENT)
         lines = path.read_text().split("\n")
-        assert lines[0].startswith("piston:") and int(lines[0].split()[1]) in (0, 1, 2)
+        assert lines[0].startswith("piston:") and int(lines[0].split()[1]) in range(5)  # one of the five shapes
         hh.close()
     finally:
         del os.environ["QRS_AUTOTUNE_CACHE"]
