@@ -61,18 +61,21 @@ def test_injected_launch_failure(monkeypatch):
     qrs.qrs_sync(h)  # nothing ran, nothing to report
 
 
-def test_grid_index_beyond_points_is_caught():
+@pytest.mark.parametrize("nx,ny", [(8, 8), (200, 40)])  # one x tile (single CTA) and two (CTA pair)
+def test_grid_index_beyond_points_is_caught(nx, ny):
     h = qrs.Handle(0)
-    x = torch.linspace(-1, 1, 8, device="cuda")
-    index = torch.arange(64, dtype=torch.int32, device="cuda").reshape(8, 8)
-    index[3, 5] = 1000  # beyond n_points = 64
-    out = torch.full((2, 64), float("nan"), device="cuda")
-    qrs.qrs_synthesize_grid(h, qrs.params(seed=3), 32, 2, x, x, index=index, n_points=64, out=out)
+    x = torch.linspace(-1, 1, nx, device="cuda")
+    y = torch.linspace(-1, 1, ny, device="cuda")
+    P = nx * ny
+    index = torch.arange(P, dtype=torch.int32, device="cuda").reshape(ny, nx)
+    index[3, 5] = P + 1000  # beyond n_points
+    out = torch.full((2, P), float("nan"), device="cuda")
+    qrs.qrs_synthesize_grid(h, qrs.params(seed=3), 32, 2, x, y, index=index, n_points=P, out=out)
     with pytest.raises(qrs.QrsError) as e:
         qrs.qrs_sync(h)
     assert e.value.status == -6
     written = torch.isfinite(out)
-    assert written.sum().item() == 2 * 63 and not written[:, 3 * 8 + 5].any()
+    assert written.sum().item() == 2 * (P - 1) and not written[:, 3 * nx + 5].any()
     qrs.qrs_sync(h)  # cleared
 
 
