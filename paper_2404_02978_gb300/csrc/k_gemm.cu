@@ -205,6 +205,59 @@ __global__ void k_gemm_coef(DrawParams p, int64_t nf_pad, int64_t n_real, int64_
 }
 
 // ------------------------------------------------------------ main kernel
+// One producer thread's share of a K chunk's A tile: basis row `row` (the
+// point with scaled coordinates X, Y / float coordinates pt), 16-byte term
+// groups [grp0, grp0 + NG) of the cos half and of the sin half, split hi/lo
+// into the swizzled tiles.
+template <int PREC, int NG>
+__device__ __forceinline__ void produce_basis(const int2* __restrict__ fb, unsigned char* Ahi, unsigned char* Alo,
+                                              int row, int grp0, const FixedScales& z, int32_t X, int32_t Y, float2 pt)
+{
+    using Cfg = GemmCfg<PREC>;
+    constexpr int TPG = Cfg::kTermsPer16B;
+    const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
+    const float2 neg_two_pi = make_float2(-6.28318530717958648f, -6.28318530717958648f);
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi) {
+        const int grp = grp0 + gi;
+        float cv[TPG], sv[TPG];
+#pragma unroll
+        for (int t = 0; t < TPG; t += 2) {  // two terms per paired FP32 instruction
+            const int2 f0 = *chk(fb, grp * TPG + t, Cfg::kTermsPerChunk);
+            const int2 f1 = *chk(fb, grp * TPG + t + 1, Cfg::kTermsPerChunk);
+            float2 ang;
+            if (z.use_fixed) {
+                const uint32_t m0 = phase_fx_word(f0.x, f0.y, X, Y, z.bias, z.shift);
+                const uint32_t m1 = phase_fx_word(f1.x, f1.y, X, Y, z.bias, z.shift);
+                ang = __ffma2_rn(make_float2(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u),
+                                             __uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u)),
+                                 two_pi, neg_two_pi);
+            } else {
+                ang = __fmul2_rn(phase_df2f(make_float2(__int_as_float(f0.x), __int_as_float(f1.x)),
+                                            make_float2(__int_as_float(f0.y), __int_as_float(f1.y)), pt.x, pt.y),
+                                 two_pi);
+            }
+            sv[t] = __sinf(ang.x);
+            cv[t] = __cosf(ang.x);
+            sv[t + 1] = __sinf(ang.y);
+            cv[t + 1] = __cosf(ang.y);
+        }
+        const uint32_t oc = sm100::sw128_offset((uint32_t)row, (uint32_t)grp);
+        const uint32_t os = sm100::sw128_offset((uint32_t)row, (uint32_t)(4 + grp));
+        uint4 hi, lo;
+        pack16<PREC>(cv, hi, lo);
+        if (chk_ok(oc, 16, kGTileA)) {
+            *reinterpret_cast<uint4*>(Ahi + oc) = hi;
+            if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + oc) = lo;
+        }
+        pack16<PREC>(sv, hi, lo);
+        if (chk_ok(os, 16, kGTileA)) {
+            *reinterpret_cast<uint4*>(Ahi + os) = hi;
+            if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + os) = lo;
+        }
+    }
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(const __grid_constant__ CUtensorMap tmapB,
                                                                            GemmArgs g)
@@ -433,9 +486,6 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
         constexpr int kGroups = 4 / (kGProducers / 4);
         const int grp0 = (pw >> 2) * kGroups;      // its term groups [grp0, grp0 + kGroups)
         const FixedScales z = fixed_scales(g.fbound, *g.d_xbound, true);
-        constexpr int TPG = Cfg::kTermsPer16B;
-        const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
-        const float2 neg_two_pi = make_float2(-6.28318530717958648f, -6.28318530717958648f);
         int64_t gc = 0;
         bool stop = false;
         for (int64_t it = blockIdx.x; it < g.n_items && !stop; it += gridDim.x) {
@@ -453,49 +503,8 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
                     stop = true;
                     break;
                 }
-                const int2* fb = reinterpret_cast<const int2*>(ringF(gc));
-                unsigned char* Ahi = stageA_hi(s);
-                unsigned char* Alo = stageA_lo(s);
-#pragma unroll
-                for (int gi = 0; gi < kGroups; ++gi) {
-                    const int grp = grp0 + gi;
-                    float cv[TPG], sv[TPG];
-#pragma unroll
-                    for (int t = 0; t < TPG; t += 2) {  // two terms per paired FP32 instruction
-                        const int2 f0 = *chk(fb, grp * TPG + t, Cfg::kTermsPerChunk);
-                        const int2 f1 = *chk(fb, grp * TPG + t + 1, Cfg::kTermsPerChunk);
-                        float2 ang;
-                        if (z.use_fixed) {
-                            const uint32_t m0 = phase_fx_word(f0.x, f0.y, X, Y, z.bias, z.shift);
-                            const uint32_t m1 = phase_fx_word(f1.x, f1.y, X, Y, z.bias, z.shift);
-                            ang = __ffma2_rn(make_float2(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u),
-                                                         __uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u)),
-                                             two_pi, neg_two_pi);
-                        } else {
-                            ang = __fmul2_rn(phase_df2f(make_float2(__int_as_float(f0.x), __int_as_float(f1.x)),
-                                                        make_float2(__int_as_float(f0.y), __int_as_float(f1.y)), pt.x,
-                                                        pt.y),
-                                             two_pi);
-                        }
-                        sv[t] = __sinf(ang.x);
-                        cv[t] = __cosf(ang.x);
-                        sv[t + 1] = __sinf(ang.y);
-                        cv[t + 1] = __cosf(ang.y);
-                    }
-                    const uint32_t oc = sm100::sw128_offset((uint32_t)row, (uint32_t)grp);
-                    const uint32_t os = sm100::sw128_offset((uint32_t)row, (uint32_t)(4 + grp));
-                    uint4 hi, lo;
-                    pack16<PREC>(cv, hi, lo);
-                    if (chk_ok(oc, 16, kGTileA)) {
-                        *reinterpret_cast<uint4*>(Ahi + oc) = hi;
-                        if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + oc) = lo;
-                    }
-                    pack16<PREC>(sv, hi, lo);
-                    if (chk_ok(os, 16, kGTileA)) {
-                        *reinterpret_cast<uint4*>(Ahi + os) = hi;
-                        if (Cfg::kSplit) *reinterpret_cast<uint4*>(Alo + os) = lo;
-                    }
-                }
+                produce_basis<PREC, kGroups>(reinterpret_cast<const int2*>(ringF(gc)), stageA_hi(s), stageA_lo(s), row,
+                                             grp0, z, X, Y, pt);
                 sm100::fence_proxy_async_smem();  // each thread: its row writes -> async proxy
                 __syncwarp();
                 if (lane == 0) {
@@ -515,6 +524,338 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
         __syncwarp();
         sm100::tc_fence_after();
         sm100::tmem_dealloc(tmem_base, 512);
+    }
+}
+
+// ------------------------------------------------------------ CTA pairs
+// k_gemm_pair: the same product on clusters of two CTAs (two SMs) sharing
+// one tcgen05.mma of M = 256 (cta_group::2).  A work item is (256-column
+// block, pair of 128-point tiles); CTA rank q builds the basis of tile
+// 2 p + q (A: its own 128 rows) and TMA-loads columns [128 q, 128 q + 128) of
+// the block's coefficient tiles (B: each CTA half of the 256 rows), so each
+// SM stages half the coefficient bytes per K chunk and the tensor cores read
+// each B row once for both tiles.  Each CTA's TMEM holds the 128 x 256
+// accumulator of its own tile; its promoters promote and store it as in
+// k_gemm_main, with two slots and the master in L2 for every mode.  Three 64 KB
+// stages.  Cross-SM signals: the odd CTA's relay threads forward its
+// stage-ready (A written and B landed) and slot-free phases to the even CTA,
+// one cluster-scope release each; the MMA commits arrive at empty[s] and
+// seg_full[b] in both CTAs (multicast).  A time-out in either CTA raises both
+// abort flags; both meet at a cluster barrier before TMEM is freed.
+constexpr int kPGStages = 3;
+constexpr int kPGTileB = (kGN / 2) * 128;                        // 16 KB: this CTA's half of the columns
+constexpr int kPGStageBytes = 2 * kGTileA + 2 * kPGTileB;        // 64 KB
+constexpr int kPGSmemBytes = kPGStages * kPGStageBytes + kGFreqSlots * kGFreqBytes + 512 + 1024;
+
+template <int PREC>
+__global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_pair(const __grid_constant__ CUtensorMap tmapB,
+                                                                           GemmArgs g)
+{
+    using Cfg = GemmCfg<PREC>;
+    constexpr int kGProducers = GemmShape<PREC>::kProducers;
+    // every mode keeps two TMEM slots and its master in L2 here: with half the
+    // coefficient bytes per SM the L2 reductions no longer cost more than the
+    // MMAs' waits for a TMEM-resident promotion (3XTF32: 12.4 against 13.7 ms)
+    constexpr bool kTmemMaster = false;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* fring = smem + kPGStages * kPGStageBytes;
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(fring + kGFreqSlots * kGFreqBytes);
+    uint64_t* fullB = fullA + kPGStages;
+    uint64_t* peerF = fullB + kPGStages;  // even CTA: the odd CTA's stage s is ready
+    uint64_t* empty = peerF + kPGStages;
+    uint64_t* seg_full = empty + kPGStages;  // [2]
+    uint64_t* seg_free = seg_full + 2;       // [2]
+    uint64_t* fullF = seg_free + 2;
+    uint64_t* freeF = fullF + kGFreqSlots;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(freeF + kGFreqSlots);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    uint64_t* never = reinterpret_cast<uint64_t*>(tmem_slot + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = sm100::cluster_ctarank();
+    const bool leader = rank == 0;
+    const int64_t cluster = blockIdx.x >> 1, n_clusters = gridDim.x >> 1;
+    const int64_t n_chunks = g.n_chunks;
+    const int64_t n_seg = (n_chunks + Cfg::kSeg - 1) / Cfg::kSeg;
+    const int64_t n_tp = (g.n_tiles + 1) >> 1;  // tile pairs per column block
+    auto slot_of = [](int64_t J) { return kTmemMaster ? 0 : (int)(J & 1); };
+    auto use_of = [](int64_t J) { return (uint32_t)((kTmemMaster ? J : (J >> 1)) & 1); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kPGStages; ++s) {
+            sm100::mbar_init(&fullA[s], kGProducers);
+            sm100::mbar_init(&fullB[s], 1);
+            sm100::mbar_init(&peerF[s], 1);
+            sm100::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            sm100::mbar_init(&seg_full[b], 1);
+            sm100::mbar_init(&seg_free[b], leader ? kGPromoters + 1 : kGPromoters);  // + the odd CTA's relay
+        }
+        for (int s = 0; s < kGFreqSlots; ++s) {
+            sm100::mbar_init(&fullF[s], 1);
+            sm100::mbar_init(&freeF[s], kGProducers);
+        }
+        sm100::mbar_init(never, 1);
+        *abort_flag = 0;
+        sm100::fence_barrier_init();
+    }
+    if (warp == 1) sm100::tmem_alloc_pair(tmem_slot, 512);
+    if (warp == 0 && lane == 0) sm100::prefetch_tmap(&tmapB);
+    sm100::tc_fence_before();
+    sm100::cluster_sync();  // both CTAs' barriers initialised before any remote arrival
+    sm100::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto stageA_hi = [&](int s) { return smem + s * kPGStageBytes; };
+    auto stageA_lo = [&](int s) { return smem + s * kPGStageBytes + kGTileA; };
+    auto stageB_hi = [&](int s) { return smem + s * kPGStageBytes + 2 * kGTileA; };
+    auto stageB_lo = [&](int s) { return smem + s * kPGStageBytes + 2 * kGTileA + kPGTileB; };
+    auto ringF = [&](int64_t i) { return fring + (i % kGFreqSlots) * kGFreqBytes; };
+    const uint32_t peer_abort = sm100::mapa_shared((const void*)abort_flag, rank ^ 1u);
+    auto timeout = [&]() {
+        *abort_flag = 1;
+        sm100::st_remote_u32(peer_abort, 1u);
+        atomicExch(g.err, (int)QRS_ERR_TIMEOUT);
+    };
+    int64_t mma_segments = 0;
+    constexpr uint32_t kFreqChunkBytes = Cfg::kTermsPerChunk * sizeof(int2);
+
+    if (warp == 0) {
+        // ---------------------------- TMA producer: this CTA's half of B
+        if (lane == 0) {
+            int64_t gc = 0, issued = 0;
+            bool stop = false;
+            for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+                const int64_t rblk = it / n_tp;
+                const int32_t y0 = (int32_t)(rblk * kGN + rank * (kGN / 2));
+                for (int64_t i = 0; i < n_chunks; ++i, ++gc) {
+                    const int s = (int)(gc % kPGStages);
+                    const uint32_t ph = (uint32_t)((gc / kPGStages) & 1);
+                    if (*abort_flag ||
+                        (gc >= kPGStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kGWaitCycles))) {
+                        if (!*abort_flag) timeout();
+                        stop = true;
+                        break;
+                    }
+                    sm100::mbar_arrive_expect_tx(&fullB[s], (Cfg::kSplit ? 2u : 1u) * kPGTileB);
+                    const int32_t x = (int32_t)(i * Cfg::kElemsPerRow);
+                    sm100::tma_load_2d(stageB_hi(s), &tmapB, &fullB[s], x, y0);
+                    if (Cfg::kSplit) sm100::tma_load_2d(stageB_lo(s), &tmapB, &fullB[s], x, (int32_t)g.R_pad + y0);
+                    issued = gc + 1;
+                }
+            }
+            if (*abort_flag) {
+                for (int64_t i = (issued > kPGStages ? issued - kPGStages : 0); i < issued; ++i)
+                    sm100::mbar_wait_for(&fullB[i % kPGStages], (uint32_t)((i / kPGStages) & 1), kGWaitCycles / 8);
+            }
+        }
+    } else if (warp == 1) {
+        if (leader && lane == 0) {
+            // ------------------------------------ MMA issuer (even CTA)
+            constexpr uint32_t idesc = sm100::idesc_f32acc(Cfg::kFormat, 2 * kGM, kGN);
+            if (g.inject_wait > 0 && !sm100::mbar_wait(never, 0u, abort_flag, g.inject_wait) && !*abort_flag)
+                timeout();
+            int64_t J = 0, gc = 0;
+            bool stop = *abort_flag != 0;
+            for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+                int64_t i = 0;
+                for (int64_t j = 0; j < n_seg; ++j, ++J) {
+                    const int b = slot_of(J);
+                    const int64_t Jp = J - (kTmemMaster ? 1 : 2);
+                    if (*abort_flag ||
+                        (Jp >= 0 && !sm100::mbar_wait_cluster(&seg_free[b], use_of(Jp), abort_flag, kGWaitCycles))) {
+                        if (!*abort_flag) timeout();
+                        stop = true;
+                        break;
+                    }
+                    const int64_t i_end = ((j + 1) * Cfg::kSeg < n_chunks) ? (j + 1) * Cfg::kSeg : n_chunks;
+                    const uint32_t tmem_seg = tmem_base + (uint32_t)((kTmemMaster ? 1 : b) * kGN);
+                    bool first = true;
+                    for (; i < i_end; ++i, ++gc) {
+                        const int s = (int)(gc % kPGStages);
+                        const uint32_t ph = (uint32_t)((gc / kPGStages) & 1);
+                        if (!sm100::mbar_wait(&fullA[s], ph, abort_flag, kGWaitCycles) ||
+                            !sm100::mbar_wait(&fullB[s], ph, abort_flag, kGWaitCycles) ||
+                            !sm100::mbar_wait_cluster(&peerF[s], ph, abort_flag, kGWaitCycles)) {
+                            if (!*abort_flag) timeout();
+                            stop = true;
+                            break;
+                        }
+                        sm100::tc_fence_after();
+                        const uint32_t ahi = sm100::smem_u32(stageA_hi(s)), alo = sm100::smem_u32(stageA_lo(s));
+                        const uint32_t bhi = sm100::smem_u32(stageB_hi(s)), blo = sm100::smem_u32(stageB_lo(s));
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t off = (uint32_t)kk * 32u;
+                            const uint64_t dAh = sm100::desc_k_sw128(ahi + off), dAl = sm100::desc_k_sw128(alo + off);
+                            const uint64_t dBh = sm100::desc_k_sw128(bhi + off), dBl = sm100::desc_k_sw128(blo + off);
+                            sm100::mma_pair<Cfg::kTF32>(tmem_seg, dAh, dBh, idesc, first ? 0u : 1u);
+                            first = false;
+                            if (Cfg::kSplit) {
+                                sm100::mma_pair<Cfg::kTF32>(tmem_seg, dAh, dBl, idesc, 1u);
+                                sm100::mma_pair<Cfg::kTF32>(tmem_seg, dAl, dBh, idesc, 1u);
+                            }
+                        }
+                        sm100::mma_commit_pair(&empty[s], (uint16_t)3);
+                    }
+                    sm100::mma_commit_pair(&seg_full[b], (uint16_t)3);
+                    mma_segments = J + 1;
+                    if (stop) break;
+                }
+            }
+        } else if (!leader && lane == 0) {
+            // -------------- relay (odd CTA): stage s ready -> even CTA
+            const uint32_t remote0 = sm100::mapa_shared(peerF, 0u);
+            int64_t gc = 0;
+            bool stop = false;
+            for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+                for (int64_t i = 0; i < n_chunks; ++i, ++gc) {
+                    const int s = (int)(gc % kPGStages);
+                    const uint32_t ph = (uint32_t)((gc / kPGStages) & 1);
+                    if (!sm100::mbar_wait(&fullA[s], ph, abort_flag, kGWaitCycles) ||
+                        !sm100::mbar_wait(&fullB[s], ph, abort_flag, kGWaitCycles)) {
+                        if (!*abort_flag) timeout();
+                        stop = true;
+                        break;
+                    }
+                    sm100::mbar_arrive_remote(remote0 + (uint32_t)(s * sizeof(uint64_t)));
+                }
+            }
+        }
+    } else if (warp == 2) {
+        // -------------------------------------------- frequency ring filler
+        if (lane == 0) {
+            int64_t gc = 0, issued = 0;
+            bool stop = false;
+            for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+                for (int64_t i = 0; i < n_chunks; ++i, ++gc) {
+                    const int f = (int)(gc % kGFreqSlots);
+                    if (*abort_flag || (gc >= kGFreqSlots &&
+                                        !sm100::mbar_wait(&freeF[f], (uint32_t)(((gc / kGFreqSlots) & 1) ^ 1),
+                                                          abort_flag, kGWaitCycles))) {
+                        if (!*abort_flag) timeout();
+                        stop = true;
+                        break;
+                    }
+                    if (chk_ok(i * Cfg::kTermsPerChunk, Cfg::kTermsPerChunk, n_chunks * Cfg::kTermsPerChunk)) {
+                        sm100::mbar_arrive_expect_tx(&fullF[f], kFreqChunkBytes);
+                        sm100::bulk_load(ringF(gc), g.fbasis + i * Cfg::kTermsPerChunk, kFreqChunkBytes, &fullF[f]);
+                    } else {
+                        sm100::mbar_arrive(&fullF[f]);
+                    }
+                    issued = gc + 1;
+                }
+            }
+            if (*abort_flag) {
+                for (int64_t i = (issued > kGFreqSlots ? issued - kGFreqSlots : 0); i < issued; ++i)
+                    sm100::mbar_wait_for(&fullF[i % kGFreqSlots], (uint32_t)((i / kGFreqSlots) & 1), kGWaitCycles / 8);
+            }
+        }
+    } else if (warp == 3) {
+        // ---------------- relay (odd CTA): slot read -> even CTA
+        if (!leader && lane == 0) {
+            const uint32_t remote0 = sm100::mapa_shared(seg_free, 0u);
+            int64_t J = 0;
+            bool stop = false;
+            for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+                for (int64_t j = 0; j < n_seg; ++j, ++J) {
+                    const int b = slot_of(J);
+                    if (!sm100::mbar_wait(&seg_free[b], use_of(J), abort_flag, kGWaitCycles)) {
+                        if (!*abort_flag) timeout();
+                        stop = true;
+                        break;
+                    }
+                    sm100::mbar_arrive_remote(remote0 + (uint32_t)(b * sizeof(uint64_t)));
+                }
+            }
+        }
+    } else if (warp >= 4 && warp < 4 + kGPromoters) {
+        // ------------------------------------------------------ promoters
+        constexpr int PC = GemmShape<PREC>::kPromoteCols;
+        constexpr int kSpan = kGN / (kGPromoters / 4);
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const int col0 = ((warp - 4) >> 2) * kSpan;
+        const int64_t n_master = (int64_t)gridDim.x * kGN * kGM;
+        const int64_t mq_off = (int64_t)blockIdx.x * kGN * kGM + (int64_t)quarter * kGN * 32;
+        int64_t J = 0;
+        bool stop = false;
+        for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+            const int64_t rblk = it / n_tp, tp = it - rblk * n_tp;
+            const int64_t m = (2 * tp + rank) * kGM + row;
+            for (int64_t j = 0; j < n_seg; ++j, ++J) {
+                const int b = slot_of(J);
+                if (!sm100::mbar_wait(&seg_full[b], use_of(J), abort_flag, kGWaitCycles)) {
+                    if (!*abort_flag) timeout();
+                    stop = true;
+                    break;
+                }
+                sm100::tc_fence_after();
+                auto store = [&](int c, float v) {
+                    const int64_t r = rblk * kGN + c;
+                    if (m < g.P && r < g.n_real) *chk(g.out, r * g.P + m, g.n_real * g.P) = v;
+                };
+                if (kTmemMaster)
+                    promote_tmem<PC>(tmem_base + lane_off, tmem_base + (uint32_t)kGN + lane_off, j, j == n_seg - 1,
+                                     col0, kSpan, store);
+                else
+                    promote_red<PC>(g.master, n_master, mq_off, tmem_base + (uint32_t)(b * kGN) + lane_off, lane, j,
+                                    j == n_seg - 1, col0, kSpan, store);
+                sm100::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) sm100::mbar_arrive(&seg_free[b]);
+            }
+        }
+    } else if (warp >= 4 + kGPromoters) {
+        // ------------------------------------------- basis producers
+        const int pw = warp - 4 - kGPromoters;
+        const int row = (pw & 3) * 32 + lane;
+        constexpr int kGroups = 4 / (kGProducers / 4);
+        const int grp0 = (pw >> 2) * kGroups;
+        const FixedScales z = fixed_scales(g.fbound, *g.d_xbound, true);
+        int64_t gc = 0;
+        bool stop = false;
+        for (int64_t it = cluster; it < g.n_items && !stop; it += n_clusters) {
+            const int64_t tp = it % n_tp;
+            const int64_t m = (2 * tp + rank) * kGM + row;
+            const float2 pt = (m < g.P) ? *chk(g.xy, m, g.P) : make_float2(0.0f, 0.0f);
+            const int32_t X = __float2int_rn(pt.x * z.xscale), Y = __float2int_rn(pt.y * z.xscale);
+            for (int64_t i = 0; i < n_chunks; ++i, ++gc) {
+                const int s = (int)(gc % kPGStages);
+                const uint32_t ph = (uint32_t)((gc / kPGStages) & 1);
+                if (*abort_flag ||
+                    (gc >= kPGStages && !sm100::mbar_wait(&empty[s], ph ^ 1u, abort_flag, kGWaitCycles)) ||
+                    !sm100::mbar_wait(&fullF[gc % kGFreqSlots], (uint32_t)((gc / kGFreqSlots) & 1), abort_flag,
+                                      kGWaitCycles)) {
+                    if (!*abort_flag) timeout();
+                    stop = true;
+                    break;
+                }
+                produce_basis<PREC, kGroups>(reinterpret_cast<const int2*>(ringF(gc)), stageA_hi(s), stageA_lo(s), row,
+                                             grp0, z, X, Y, pt);
+                sm100::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    sm100::mbar_arrive(&fullA[s]);
+                    sm100::mbar_arrive(&freeF[gc % kGFreqSlots]);
+                }
+            }
+        }
+    }
+    sm100::tc_fence_before();
+    __syncthreads();
+    if (warp == 1 && lane == 0 && leader && *abort_flag && mma_segments > 0) {
+        const int64_t Jl = mma_segments - 1;  // the pair's MMAs in flight finish first
+        sm100::mbar_wait_cluster_for(&seg_full[slot_of(Jl)], use_of(Jl), kGWaitCycles / 8);
+    }
+    __syncwarp();
+    sm100::cluster_sync();  // neither CTA frees TMEM or exits while the pair still works on it
+    if (warp == 1) {
+        sm100::tc_fence_after();
+        sm100::tmem_dealloc_pair(tmem_base, 512);
     }
 }
 
@@ -546,6 +887,45 @@ size_t gemm_workspace_bytes(int mode, int64_t n_f, int64_t n_real, int num_sms)
            (size_t)num_sms * kGN * kGM * sizeof(float);  // the CTAs' FP32 masters
 }
 
+static void gemm_pair_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute (&at)[1], unsigned grid, int threads,
+                             cudaStream_t s)
+{
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = kPGSmemBytes;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+}
+
+// Clusters of two k_gemm_pair CTAs the GPU holds at once (cached per handle
+// and mode); 0 when pairs are switched off (QRS_GEMM_PAIR=0 at qrs_create)
+// or unavailable.
+template <int PREC>
+static int gemm_pair_clusters(qrs_handle* h)
+{
+    int& c = h->gemm_pair_clusters[PREC == QRS_SYNTH_GEMM_3XTF32 ? 0 : PREC == QRS_SYNTH_GEMM_BF16X3 ? 1 : 2];
+    if (!h->gemm_pair) return 0;
+    if (c == 0) {
+        int n = 0;
+        cudaError_t e =
+            cudaFuncSetAttribute(k_gemm_pair<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPGSmemBytes);
+        if (e == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            gemm_pair_config(cfg, at, (unsigned)(h->num_sms & ~1), GemmShape<PREC>::kThreads, nullptr);
+            e = cudaOccupancyMaxActiveClusters(&n, k_gemm_pair<PREC>, &cfg);
+        }
+        if (e != cudaSuccess) cudaGetLastError();  // the single-CTA kernel serves instead
+        c = (e == cudaSuccess && n > 0) ? (n < h->num_sms / 2 ? n : h->num_sms / 2) : -1;
+    }
+    return c > 0 ? c : 0;
+}
+
 template <int PREC>
 static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float* xy, int64_t P, int64_t n_real,
                                  const double* col_psd, double c_vk, float* out, cudaStream_t s)
@@ -572,12 +952,15 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     k_gemm_coef<PREC><<<cg, 256, 0, s>>>(p, nf_pad, n_real, R_pad, fw, col_psd, c_vk, B);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
+    // CTA pairs when there are point tiles to pair and the GPU can hold a pair
+    const int64_t n_tiles = (P + kGM - 1) / kGM;
+    const int clusters = n_tiles >= 2 ? gemm_pair_clusters<PREC>(h) : 0;
     PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode();
     if (!encode) return cudaErrorNotSupported;
     CUtensorMap tmap;
     const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)((Cfg::kSplit ? 2 : 1) * R_pad)};
     const cuuint64_t gstride[1] = {(cuuint64_t)(Kp * Cfg::kElemBytes)};
-    const cuuint32_t box[2] = {(cuuint32_t)Cfg::kElemsPerRow, (cuuint32_t)kGN};
+    const cuuint32_t box[2] = {(cuuint32_t)Cfg::kElemsPerRow, (cuuint32_t)(clusters > 0 ? kGN / 2 : kGN)};
     const cuuint32_t estride[2] = {1, 1};
     CUresult cr = encode(&tmap, Cfg::kTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B,
                          gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -591,8 +974,8 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     a.n_real = n_real;
     a.R_pad = R_pad;
     a.n_chunks = Kp / Cfg::kElemsPerRow;
-    a.n_tiles = (P + kGM - 1) / kGM;
-    a.n_items = a.n_tiles * (R_pad / kGN);
+    a.n_tiles = n_tiles;
+    a.n_items = (clusters > 0 ? (n_tiles + 1) / 2 : n_tiles) * (R_pad / kGN);
     a.master = master;
     a.fbasis = fbasis;
     a.d_xbound = h->d_xbound;
@@ -602,6 +985,13 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     if (h->fault & kFaultTimeout) {  // one-shot: this launch only
         a.inject_wait = 2000000;     // about 1 ms of SM clock
         h->fault &= ~kFaultTimeout;
+    }
+    if (clusters > 0) {
+        const int64_t nc = a.n_items < clusters ? a.n_items : clusters;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        gemm_pair_config(cfg, at, (unsigned)(2 * nc), GemmShape<PREC>::kThreads, s);
+        return cudaLaunchKernelEx(&cfg, k_gemm_pair<PREC>, tmap, a);
     }
     e = cudaFuncSetAttribute(k_gemm_main<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemBytes);
     if (e != cudaSuccess) return e;

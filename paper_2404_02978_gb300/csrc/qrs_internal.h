@@ -40,6 +40,10 @@ struct qrs_handle {
     // per precision (0: not yet queried, -1: unavailable).
     int grid_pair = 1;
     int grid_pair_clusters[2] = {0, 0};
+    // Shared-draw GEMM form: the same for k_gemm_pair (QRS_GEMM_PAIR=0 at
+    // qrs_create), per mode (3XTF32, BF16X3, TF32).
+    int gemm_pair = 1;
+    int gemm_pair_clusters[3] = {0, 0, 0};
 };
 
 namespace qrs {

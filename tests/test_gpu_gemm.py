@@ -83,6 +83,34 @@ def test_gemm_column0_equals_fused_realisation(h):
     assert np.max(np.abs(g[0] - fu.cpu().numpy()[0])) <= 2e-5 * sig[0]
 
 
+@pytest.mark.parametrize("mode", ["gemm_3xtf32", "gemm_bf16x3", "gemm_tf32"])
+def test_gemm_cta_pairs_and_single_ctas(h, monkeypatch, mode):
+    """Two or more point tiles run on CTA pairs (one MMA over two SMs, each
+    CTA staging half the coefficient columns); QRS_GEMM_PAIR=0 at handle
+    creation keeps every tile on its own CTA.  An odd tile count (the last
+    pair's second CTA has no points) and two column blocks; both against the
+    oracle at the mode's tolerance, and against each other."""
+    monkeypatch.setenv("QRS_GEMM_PAIR", "0")
+    h1 = qrs.Handle(0)
+    monkeypatch.delenv("QRS_GEMM_PAIR")
+    rng = np.random.default_rng(21)
+    xy = rng.uniform(-4.0, 4.0, size=(3 * 128 + 17, 2)).astype(np.float32)  # 4 tiles, the last ragged
+    p = oracle.params(seed=66)
+    n_f, R, off = 300, 300, 2  # two column blocks
+    pair = _run(h, p, n_f, R, xy, mode, off, None)
+    single = _run(h1, p, n_f, R, xy, mode, off, None)
+    sig = _col_sigma(p, n_f, R, off, None)
+    cols = [0, 1, 255, 256, 299]
+    ref = oracle.synthesize_shared(p, n_f, R, xy.astype(np.float64), real_offset=off)
+    for name, g in (("pair", pair), ("single", single)):
+        err = np.abs(g[cols].astype(np.float64) - ref[cols]) / sig[cols, None]
+        print("gemm %s %s: max err %.3g sigma" % (mode, name, err.max()))
+        assert err.max() <= TOL[mode], name
+    d = np.abs(pair - single).max()
+    print("gemm %s pair vs single: max |diff| %.3g (%s)" % (mode, d, "bit-identical" if d == 0 else "differ"))
+    assert d <= 2 * TOL[mode] * sig.max()
+
+
 # Full-size bounds per value (max) and over the sampled values (rms), in units
 # of the column's sigma.  3XTF32 keeps the 1e-5 bar.  BF16X3 carries about
 # 2^-17 relative per split product (8-bit high part, its BF16 residual, the
