@@ -952,9 +952,12 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
     k_gemm_coef<PREC><<<cg, 256, 0, s>>>(p, nf_pad, n_real, R_pad, fw, col_psd, c_vk, B);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-    // CTA pairs when there are point tiles to pair and the GPU can hold a pair
+    // CTA pairs for the split modes when there are point tiles to pair and the
+    // GPU can hold a pair (single-pass TF32, with a third of the MMA work per
+    // chunk, measured faster on single CTAs: 8.3 against 10.3 ms per batch)
     const int64_t n_tiles = (P + kGM - 1) / kGM;
-    const int clusters = n_tiles >= 2 ? gemm_pair_clusters<PREC>(h) : 0;
+    int clusters = 0;
+    if constexpr (Cfg::kSplit) clusters = n_tiles >= 2 ? gemm_pair_clusters<PREC>(h) : 0;
     PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode();
     if (!encode) return cudaErrorNotSupported;
     CUtensorMap tmap;
@@ -986,12 +989,14 @@ static cudaError_t launch_gemm_t(qrs_handle* h, const DrawParams& p, const float
         a.inject_wait = 2000000;     // about 1 ms of SM clock
         h->fault &= ~kFaultTimeout;
     }
-    if (clusters > 0) {
-        const int64_t nc = a.n_items < clusters ? a.n_items : clusters;
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        gemm_pair_config(cfg, at, (unsigned)(2 * nc), GemmShape<PREC>::kThreads, s);
-        return cudaLaunchKernelEx(&cfg, k_gemm_pair<PREC>, tmap, a);
+    if constexpr (Cfg::kSplit) {
+        if (clusters > 0) {
+            const int64_t nc = a.n_items < clusters ? a.n_items : clusters;
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            gemm_pair_config(cfg, at, (unsigned)(2 * nc), GemmShape<PREC>::kThreads, s);
+            return cudaLaunchKernelEx(&cfg, k_gemm_pair<PREC>, tmap, a);
+        }
     }
     e = cudaFuncSetAttribute(k_gemm_main<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemBytes);
     if (e != cudaSuccess) return e;

@@ -83,10 +83,11 @@ def test_gemm_column0_equals_fused_realisation(h):
     assert np.max(np.abs(g[0] - fu.cpu().numpy()[0])) <= 2e-5 * sig[0]
 
 
-@pytest.mark.parametrize("mode", ["gemm_3xtf32", "gemm_bf16x3", "gemm_tf32"])
+@pytest.mark.parametrize("mode", ["gemm_3xtf32", "gemm_bf16x3"])
 def test_gemm_cta_pairs_and_single_ctas(h, monkeypatch, mode):
-    """Two or more point tiles run on CTA pairs (one MMA over two SMs, each
-    CTA staging half the coefficient columns); QRS_GEMM_PAIR=0 at handle
+    """In the split modes, two or more point tiles run on CTA pairs (one MMA
+    over two SMs, each CTA staging half the coefficient columns; single-pass
+    TF32 stays on single CTAs); QRS_GEMM_PAIR=0 at handle
     creation keeps every tile on its own CTA.  An odd tile count (the last
     pair's second CTA has no points) and two column blocks; both against the
     oracle at the mode's tolerance, and against each other."""
