@@ -42,7 +42,12 @@
  *     next GEMM-form launch of the handle first waits on a barrier that no
  *     thread arrives at, with a limit of about 1 ms, and unwinds through its
  *     time-out path: QRS_ERR_TIMEOUT at the next qrs_sync, later calls run
- *     normally).
+ *     normally), QRS_GRID_PAIR=0 and QRS_GEMM_PAIR=0 (read at qrs_create:
+ *     the grid form and the split-precision GEMM form then run every
+ *     128-point tile on its own CTA instead of on pairs of CTAs sharing one
+ *     tensor-core product across two SMs; results are identical),
+ *     QRS_CHECKED=1 (read by the Python binding: it loads the bounds-checked
+ *     build, see below).
  */
 #ifndef QRS_H
 #define QRS_H
