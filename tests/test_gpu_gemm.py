@@ -112,6 +112,25 @@ def test_gemm_cta_pairs_and_single_ctas(h, monkeypatch, mode):
     assert d <= 2 * TOL[mode] * sig.max()
 
 
+@pytest.mark.parametrize("P,R", [(129, 1), (256, 257), (257, 256)])
+@pytest.mark.parametrize("mode", ["gemm_3xtf32", "gemm_bf16x3"])
+def test_gemm_pair_edges(h, mode, P, R):
+    """Tile and column counts at the pair boundaries: two tiles of which the
+    second holds one point, an exact pair with a second column block of one
+    column, and a third tile (the second pair's odd CTA empty)."""
+    rng = np.random.default_rng(P + R)
+    xy = rng.uniform(-2.0, 2.0, size=(P, 2)).astype(np.float32)
+    p = oracle.params(seed=67)
+    n_f, off = 96, 4
+    got = _run(h, p, n_f, R, xy, mode, off, None)
+    sig = _col_sigma(p, n_f, R, off, None)
+    cols = sorted({0, R // 2, R - 1})
+    ref = oracle.synthesize_shared(p, n_f, R, xy.astype(np.float64), real_offset=off)
+    err = np.abs(got[cols] - ref[cols]) / sig[cols, None]
+    assert np.isfinite(got).all()
+    assert err.max() <= TOL[mode], err.max()
+
+
 # Full-size bounds per value (max) and over the sampled values (rms), in units
 # of the column's sigma.  3XTF32 keeps the 1e-5 bar.  BF16X3 carries about
 # 2^-17 relative per split product (8-bit high part, its BF16 residual, the
