@@ -466,7 +466,8 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_main(cons
                 sm100::tc_fence_after();
                 auto store = [&](int c, float v) {
                     const int64_t r = rblk * kGN + c;
-                    if (m < g.P && r < g.n_real) *chk(g.out, r * g.P + m, g.n_real * g.P) = v;
+                    // streaming store: the field is not read again, the coefficient tiles are
+                    if (m < g.P && r < g.n_real) __stcs(chk(g.out, r * g.P + m, g.n_real * g.P), v);
                 };
                 if (kTmemMaster)
                     promote_tmem<PC>(tmem_base + lane_off, tmem_base + (uint32_t)kGN + lane_off, j, j == n_seg - 1,
@@ -796,7 +797,8 @@ __global__ void __launch_bounds__(GemmShape<PREC>::kThreads, 1) k_gemm_pair(cons
                 sm100::tc_fence_after();
                 auto store = [&](int c, float v) {
                     const int64_t r = rblk * kGN + c;
-                    if (m < g.P && r < g.n_real) *chk(g.out, r * g.P + m, g.n_real * g.P) = v;
+                    // streaming store: the field is not read again, the coefficient tiles are
+                    if (m < g.P && r < g.n_real) __stcs(chk(g.out, r * g.P + m, g.n_real * g.P), v);
                 };
                 if (kTmemMaster)
                     promote_tmem<PC>(tmem_base + lane_off, tmem_base + (uint32_t)kGN + lane_off, j, j == n_seg - 1,
