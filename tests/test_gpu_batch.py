@@ -109,6 +109,39 @@ def test_autotune_cache_file(tmp_path):
         del os.environ["QRS_AUTOTUNE_CACHE"]
 
 
+def test_every_autotuner_shape_matches_the_oracle(tmp_path):
+    """Each of the five persistent kernel shapes, forced through the autotuner's
+    cache file (the bucket key from a first run, the shape number replaced),
+    against per-job launches and the FP64 oracle; jobs with 8 or more
+    apertures take the sorted-chunk path, the others the unsorted one."""
+    path = tmp_path / "tune.txt"
+    jobs = _jobs(10, seed=4) + [dict(j, ap_xy=np.concatenate([j["ap_xy"]] * 3), ap_D=np.concatenate([j["ap_D"]] * 3),
+                                     ap_d=np.concatenate([j["ap_d"]] * 3), pairs=wl.all_pairs(3 * len(j["ap_D"])))
+                                for j in _jobs(4, seed=5)]
+    os.environ["QRS_AUTOTUNE_CACHE"] = str(path)
+    try:
+        h0 = qrs.Handle(0)
+        _, ref = _submit(h0, jobs, 0)
+        _submit(h0, jobs, qrs.PISTON_PERSISTENT)
+        key = path.read_text().split()[0]
+        h0.close()
+        for shape in range(5):
+            path.write_text("%s %d\n" % (key, shape))
+            hs = qrs.Handle(0)
+            _, got = _submit(hs, jobs, qrs.PISTON_PERSISTENT)
+            for idx, j in enumerate(jobs):
+                sig = _sigma(j)
+                assert np.all(np.abs(got[idx][0].cpu().numpy() - ref[idx][0].cpu().numpy()) <= 1e-5 * sig), (shape,
+                                                                                                           idx)
+            pis_o, _ = oracle.diff_piston(jobs[-1]["p"], jobs[-1]["n_f"], jobs[-1]["n_real"], jobs[-1]["ap_xy"],
+                                          jobs[-1]["ap_D"], jobs[-1]["ap_d"], jobs[-1]["pairs"],
+                                          real_offset=jobs[-1]["off"])
+            assert np.all(np.abs(got[-1][0].cpu().numpy() - pis_o) <= 1e-5 * _sigma(jobs[-1])), shape
+            hs.close()
+    finally:
+        del os.environ["QRS_AUTOTUNE_CACHE"]
+
+
 def test_batched_interferometers_full_size(h):
     """1000 interferometers: n_ap ~ U{4..64}, D ~ U(1.8, 8) m, centres in a
     200 m disc, N_f ~ U{256..8192}, 256 realisations each, all pairs, one
