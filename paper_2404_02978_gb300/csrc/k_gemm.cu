@@ -58,12 +58,16 @@
 // the terms) and the TMEM columns a promoter thread holds at a time (32 or
 // 16), per precision: BF16X3 has twice the basis elements per K chunk and
 // gains from 16 producers (promoters then read 16 columns to fit the
-// registers); 3XTF32 is fastest with 8.
+// registers); 3XTF32 is fastest with 8; single-pass TF32, with a third of
+// the MMA work per chunk, with 16 (its promoters also read 16 columns).
 #ifndef QRS_GEMM_PRODUCERS_TF32
 #define QRS_GEMM_PRODUCERS_TF32 8
 #endif
 #ifndef QRS_GEMM_PRODUCERS_BF16
 #define QRS_GEMM_PRODUCERS_BF16 16
+#endif
+#ifndef QRS_GEMM_PRODUCERS_TF32_SINGLE
+#define QRS_GEMM_PRODUCERS_TF32_SINGLE 16  // one product per K chunk: the basis is the pace (8.15 -> 7.45 ms)
 #endif
 #ifndef QRS_GEMM_PROMOTE_COLS_TF32
 #define QRS_GEMM_PROMOTE_COLS_TF32 32
@@ -88,8 +92,10 @@ constexpr int kGPromoters = 8;                             // promoter warps, tw
 template <int PREC>
 struct GemmShape {
     static constexpr bool kBF16 = !GemmCfg<PREC>::kTF32;
-    static constexpr int kProducers = kBF16 ? QRS_GEMM_PRODUCERS_BF16 : QRS_GEMM_PRODUCERS_TF32;
-    static constexpr int kPromoteCols = kBF16 ? QRS_GEMM_PROMOTE_COLS_BF16 : QRS_GEMM_PROMOTE_COLS_TF32;
+    static constexpr bool kSingle = !GemmCfg<PREC>::kSplit;  // single-pass TF32
+    static constexpr int kProducers =
+        kBF16 ? QRS_GEMM_PRODUCERS_BF16 : (kSingle ? QRS_GEMM_PRODUCERS_TF32_SINGLE : QRS_GEMM_PRODUCERS_TF32);
+    static constexpr int kPromoteCols = (kBF16 || kSingle) ? QRS_GEMM_PROMOTE_COLS_BF16 : QRS_GEMM_PROMOTE_COLS_TF32;
     static constexpr int kThreads = 128 + 32 * (kGPromoters + kProducers);
     static constexpr bool kTmemMaster = GemmCfg<PREC>::kTF32 && GemmCfg<PREC>::kSplit;  // 3XTF32
     static_assert(kProducers == 4 || kProducers == 8 || kProducers == 16, "producer warps");
