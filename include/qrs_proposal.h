@@ -28,6 +28,8 @@
  * qrs_mlp_param_count(C) gives its length (281,600 for C = 2048).
  *
  * Conventions as in qrs.h: device pointers, caller-owned, enqueued on `stream`.
+ * Cell counts: 1 <= C = n_rho n_theta <= 32768 in every call (formed in 64
+ * bits; QRS_ERR_ARG otherwise, nothing launched).
  */
 #ifndef QRS_PROPOSAL_H
 #define QRS_PROPOSAL_H

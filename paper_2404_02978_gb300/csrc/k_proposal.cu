@@ -616,7 +616,10 @@ extern "C" {
 
 int64_t qrs_mlp_param_count(int32_t n_cells) { return n_cells >= 1 ? mlp_params(n_cells) : 0; }
 
-static bool cells_ok(int32_t C) { return C >= 1 && C <= 16384; }
+// Cell counts the proposal kernels take: the targets kernel holds one FP32
+// histogram bin per cell in shared memory (128 KB at the limit).
+constexpr int64_t kMaxCells = 32768;
+static bool cells_ok(int64_t C) { return C >= 1 && C <= kMaxCells; }
 
 qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float out_scale, float* params, void* stream)
 {
@@ -624,7 +627,7 @@ qrs_status qrs_mlp_init(qrs_handle* h, int32_t n_cells, uint64_t seed, float out
     qrs::NvtxRange nvtx_range("qrs_mlp_init");
     if (qrs::injected_launch_fault(h, "qrs_mlp_init") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
-    if (!cells_ok(n_cells) || !params) return fail(h, QRS_ERR_ARG, "n_cells must be in [1, 16384] and params non-NULL");
+    if (!cells_ok(n_cells) || !params) return fail(h, QRS_ERR_ARG, "n_cells must be in [1, 32768] and params non-NULL");
     if (!(std::isfinite(out_scale) && out_scale >= 0.0f)) return fail(h, QRS_ERR_ARG, "out_scale must be finite and >= 0");
     cudaError_t e = cudaSetDevice(h->device);
     if (e == cudaSuccess) {
@@ -649,7 +652,7 @@ qrs_status qrs_proposal_targets(qrs_handle* h, const qrs_psd* psd, const qrs_dom
     if (!dom || dom->kind != QRS_DOMAIN_LOGPOLAR) return fail(h, QRS_ERR_ARG, "targets need a LOGPOLAR domain");
     if (n_draws < 1 || n < 0) return fail(h, QRS_ERR_ARG, "n_draws >= 1, n >= 0");
     const int64_t C = (int64_t)n_rho * n_theta;
-    if (!cells_ok((int32_t)C) || n_rho < 1 || n_theta < 1) return fail(h, QRS_ERR_ARG, "n_rho x n_theta in [1, 16384]");
+    if (n_rho < 1 || n_theta < 1 || !cells_ok(C)) return fail(h, QRS_ERR_ARG, "n_rho x n_theta in [1, 32768]");
     qrs_sampler smp;
     memset(&smp, 0, sizeof(smp));
     smp.seed = seed;
@@ -703,8 +706,8 @@ qrs_status qrs_proposal_prior(qrs_handle* h, const qrs_psd* psd, const qrs_domai
     if (!dom || dom->kind != QRS_DOMAIN_LOGPOLAR || !(dom->fmin > 0.0 && dom->fmax > dom->fmin && std::isfinite(dom->fmax)))
         return fail(h, QRS_ERR_ARG, "the prior needs a LOGPOLAR domain with 0 < fmin < fmax");
     const int64_t C = (int64_t)n_rho * n_theta;
-    if (n_rho < 1 || n_theta < 1 || !cells_ok((int32_t)C) || n < 0 || n > (1 << 24))
-        return fail(h, QRS_ERR_ARG, "n_rho x n_theta in [1, 16384], n in [0, 2^24]");
+    if (n_rho < 1 || n_theta < 1 || !cells_ok(C) || n < 0 || n > (1 << 24))
+        return fail(h, QRS_ERR_ARG, "n_rho x n_theta in [1, 32768], n in [0, 2^24]");
     if (n == 0) return QRS_OK;
     if (!geom || !prior) return fail(h, QRS_ERR_ARG, "geom and prior must be non-NULL");
     cudaError_t e = cudaSetDevice(h->device);
@@ -726,7 +729,7 @@ qrs_status qrs_mlp_forward(qrs_handle* h, int32_t n_cells, const float* params, 
     qrs::NvtxRange nvtx_range("qrs_mlp_forward");
     if (qrs::injected_launch_fault(h, "qrs_mlp_forward") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
-    if (!cells_ok(n_cells) || n < 0 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 16384], n in [0, 2^24]");
+    if (!cells_ok(n_cells) || n < 0 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 32768], n in [0, 2^24]");
     if (n == 0) return QRS_OK;
     if (!params || !geom || !logits) return fail(h, QRS_ERR_ARG, "params, geom and logits must be non-NULL");
     qrs_status st = ensure_work(h, mlp_ws_floats(n_cells, n) * sizeof(float));
@@ -749,7 +752,7 @@ qrs_status qrs_mlp_loss_grad(qrs_handle* h, int32_t n_cells, const float* params
     qrs::NvtxRange nvtx_range("qrs_mlp_loss_grad");
     if (qrs::injected_launch_fault(h, "qrs_mlp_loss_grad") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
-    if (!cells_ok(n_cells) || n < 1 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 16384], n in [1, 2^24]");
+    if (!cells_ok(n_cells) || n < 1 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 32768], n in [1, 2^24]");
     if (!params || !geom || !targets || !grad || !loss) return fail(h, QRS_ERR_ARG, "null pointer argument");
     qrs_status st = ensure_work(h, mlp_ws_floats(n_cells, n) * sizeof(float));
     if (st != QRS_OK) return st;
@@ -789,7 +792,7 @@ qrs_status qrs_proposal_train(qrs_handle* h, qrs_mlp_state* state, const double*
     h->last_error.clear();
     if (!state) return fail(h, QRS_ERR_ARG, "state must be non-NULL");
     const int C = state->n_cells;
-    if (!cells_ok(C) || n < 1 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 16384], n in [1, 2^24]");
+    if (!cells_ok(C) || n < 1 || n > (1 << 24)) return fail(h, QRS_ERR_ARG, "n_cells in [1, 32768], n in [1, 2^24]");
     if (!state->params || !state->m || !state->v || !geom || !targets)
         return fail(h, QRS_ERR_ARG, "state vectors, geom and targets must be non-NULL");
     if (state->step < 0 || steps < 0 || steps > ((int64_t)1 << 40))
@@ -840,7 +843,7 @@ qrs_status qrs_mlp_save(qrs_handle* h, const qrs_mlp_state* state, const char* p
     if (!h) return QRS_ERR_ARG;
     h->last_error.clear();
     if (!state || !path || !cells_ok(state->n_cells) || !state->params || !state->m || !state->v || state->step < 0)
-        return fail(h, QRS_ERR_ARG, "state (n_cells in [1, 16384], vectors, step >= 0) and path must be valid");
+        return fail(h, QRS_ERR_ARG, "state (n_cells in [1, 32768], vectors, step >= 0) and path must be valid");
     const int64_t P = mlp_params(state->n_cells);
     std::vector<float> buf((size_t)(3 * P));
     cudaError_t e = cudaSetDevice(h->device);
@@ -867,7 +870,7 @@ qrs_status qrs_mlp_load(qrs_handle* h, qrs_mlp_state* state, const char* path, v
     if (!h) return QRS_ERR_ARG;
     h->last_error.clear();
     if (!state || !path || !cells_ok(state->n_cells) || !state->params || !state->m || !state->v)
-        return fail(h, QRS_ERR_ARG, "state (n_cells in [1, 16384], vectors) and path must be valid");
+        return fail(h, QRS_ERR_ARG, "state (n_cells in [1, 32768], vectors) and path must be valid");
     const int64_t P = mlp_params(state->n_cells);
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(h, QRS_ERR_ARG, "cannot open %s", path);
@@ -903,8 +906,8 @@ qrs_status qrs_proposal_cdf(qrs_handle* h, int32_t n_rho, int32_t n_theta, const
     if (qrs::injected_launch_fault(h, "qrs_proposal_cdf") != QRS_OK) return QRS_ERR_CUDA;
     h->last_error.clear();
     const int64_t C = (int64_t)n_rho * n_theta;
-    if (n_rho < 1 || n_theta < 1 || !cells_ok((int32_t)C) || !(eps > 0.0f && eps <= 1.0f))
-        return fail(h, QRS_ERR_ARG, "n_rho x n_theta in [1, 16384], 0 < eps <= 1");
+    if (n_rho < 1 || n_theta < 1 || !cells_ok(C) || !(eps > 0.0f && eps <= 1.0f))
+        return fail(h, QRS_ERR_ARG, "n_rho x n_theta in [1, 32768], 0 < eps <= 1");
     if (!(beta > 0.0f && beta <= 16.0f)) return fail(h, QRS_ERR_ARG, "0 < beta <= 16");
     if (!logits || !cdf) return fail(h, QRS_ERR_ARG, "logits and cdf must be non-NULL");
     qrs_status st = ensure_work(h, (size_t)(C + n_rho) * sizeof(double) + 256);

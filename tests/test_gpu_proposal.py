@@ -130,6 +130,21 @@ def test_cdf_valid_and_close(h, beta):
         assert np.all(np.abs(w - wr) <= 8 + 2e-6 * wr)
 
 
+def test_cell_counts_are_checked_in_64_bits(h):
+    """n_rho n_theta beyond 32768, including products that wrap a 32-bit
+    integer into the valid range, are argument errors (nothing launched)."""
+    z = torch.zeros(64, device="cuda")
+    out = torch.zeros(64 * 65, dtype=torch.int32, device="cuda")
+    before = h.launch_count()
+    for nr, nt in [(4, 1073741849), (2, 2147483647), (256, 256), (0, 32)]:
+        with pytest.raises(qrs.QrsError) as e:
+            qrs.qrs_proposal_cdf(h, nr, nt, z, 0.1, out=out)
+        assert e.value.status == -1
+    assert h.launch_count() == before
+    qrs.qrs_proposal_cdf(h, 1, 64, z, 0.1, out=out[:65])  # 64 cells: fine
+    qrs.qrs_sync(h)
+
+
 def _cond_sf(f, F, D, B):
     """Exact coefficient average of the differential-piston SF of one draw (the
     matched-error metric): sum_k F_k^2 A(|f_k|)^2 2 (1 - cos 2 pi f_k.B)."""
