@@ -771,7 +771,7 @@ def measure_learned(qrs, h, torch, dev, n_train=8000, n_test=200, draws=8, n_rho
     method's own draws, training on the GPU, then the matched
     structure-function error (RMS over held-out geometries and draws of the
     per-draw SF relative to the Hankel integral) of learned importance draws
-    at N_f = 256..1024 against plain draws at N_f = 256..8192.  The cells lie in
+    at N_f = 256..1024 against plain draws at N_f = 256..32768.  The cells lie in
     each geometry's baseline frame, folded over `fold` mirrored sectors; Adam
     with a cosine learning-rate schedule; the sampled density is
     softmax(beta z).  The benchmark's settings (the prior, beta = 1, and
@@ -839,7 +839,7 @@ def measure_learned(qrs, h, torch, dev, n_train=8000, n_test=200, draws=8, n_rho
         pi = importance(i, logits[i], beta)
         # the ceiling of any cell density on this grid: the geometry's own targets as the proposal
         px = importance(i, torch.log(T_test[i].clamp_min(1e-30)), 1.0)
-        runs = [("plain", p, (256, 512, 1024, 2048, 4096, 8192)), ("learned", pi, (256, 512, 1024)),
+        runs = [("plain", p, (256, 512, 1024, 2048, 4096, 8192, 16384, 32768)), ("learned", pi, (256, 512, 1024)),
                 ("own_targets", px, (256, 512, 1024))]
         if prior:  # ablation: the prior alone as the density (the network's logits left out)
             runs.append(("prior_only", importance(i, Pte[i], beta), (256, 512, 1024)))
@@ -847,11 +847,12 @@ def measure_learned(qrs, h, torch, dev, n_train=8000, n_test=200, draws=8, n_rho
             for nf in nfs:
                 err.setdefault("%s_%d" % (name, nf), []).append(sq_err(pp, nf, i))
     rms = {k: float(np.sqrt(np.mean(v))) for k, v in err.items()}
-    plain_n = np.array([256, 512, 1024, 2048, 4096, 8192], float)
+    plain_n = np.array([256, 512, 1024, 2048, 4096, 8192, 16384, 32768], float)
     plain_e = np.array([rms["plain_%d" % n] for n in plain_n.astype(int)])
 
     def reduction(e, nf):
-        """Plain terms needed for error e (log-log interpolation of the plain curve) / nf."""
+        """Plain terms needed for error e (log-log interpolation of the plain curve) / nf
+        (a lower bound, 32768 / nf, for errors below the plain curve's end)."""
         return float(np.exp(np.interp(-np.log(e), -np.log(plain_e), np.log(plain_n)))) / nf
 
     equiv, cap, pri = {}, {}, {}
