@@ -46,6 +46,10 @@
  *     the grid form and the split-precision GEMM form then run every
  *     128-point tile on its own CTA instead of on pairs of CTAs sharing one
  *     tensor-core product across two SMs; results are identical),
+ *     QRS_SYNTH_ANCHOR=0 (read at qrs_create, and by
+ *     qrs_synthesize_points_noalloc at each call: the fused form keeps its
+ *     exact per-point phase paths instead of the anchored one, see
+ *     qrs_synthesize_points; results agree within the stated tolerance),
  *     QRS_CHECKED=1 (read by the Python binding: it loads the bounds-checked
  *     build, see below).
  */
@@ -246,7 +250,14 @@ qrs_status qrs_draw(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, co
  *                         in one persistent kernel, each term as one cosine in
  *                         Eq. 3's amplitude-phase form F amp cos 2 pi (phi + psi)
  *                         (amp, psi: the polar form of (a, b)); col_psd must be
- *                         NULL.
+ *                         NULL.  Where each group of 12 consecutive points lies
+ *                         within d of the group's first or last point with
+ *                         f_max d <= 8 (and the fixed-point phase applies),
+ *                         the exact phase is formed at those two anchors
+ *                         only and each point adds its FP32 offset
+ *                         2 pi f . (x_m - x_anchor) (the anchored path; within
+ *                         1e-5 of the field standard deviation per value, as
+ *                         the exact paths); QRS_SYNTH_ANCHOR=0 turns it off.
  *   QRS_SYNTH_GEMM_*      shared draw: all n_real columns use the frequencies of
  *                         realisation real_offset; column r takes its coefficients
  *                         from stream points (real_offset + r) N_f + k and, if
@@ -419,8 +430,8 @@ qrs_status qrs_fft_spectrum(qrs_handle* h, const qrs_psd* psd, int64_t n, double
  * never calls cudaMalloc / cudaFree or any allocating routine.
  *   Scratch: a file-scope device array of QRS_NOALLOC_SCRATCH_BYTES per GPU,
  *   held by every GPU that loads the library until the process exits.  The
- *   fused path keeps one float in it (the point bound that selects the phase
- *   path), whatever the problem size, so no size outgrows it; requests outside
+ *   fused path keeps two floats in it (the point and anchor bounds that select
+ *   the phase path), whatever the problem size, so no size outgrows it; requests outside
  *   the limits of qrs_synthesize_points return QRS_ERR_ARG.  The bound is
  *   rewritten by every call, so nothing needs clearing between calls.
  *   Device: the calling thread's current device (at most 64 devices).  The

@@ -30,6 +30,20 @@
 // a + b = 55 (fbound * xbound <= 64 with room in the ceilings), the fraction
 // is the low 23 bits of the phase word's high half and needs no shift.
 //
+// Anchored path (the fixed-point path's fast form, Eq. 3 unchanged): each
+// thread takes kSynthPPT consecutive points instead, and the group's first
+// and last points are its two anchors.  Per term the thread forms the exact
+// 64-bit fixed-point phase of the two anchors only; every point adds its
+// FP32 offset from the nearer anchor, 2 pi (fx dx + fy dy), to that anchor's
+// phase in radians, so a (point, term) costs three paired FP32 instructions
+// and the cosine instead of two wide integer multiply-adds.  The offset's
+// rounding error grows with f . dx, so the path applies only where the
+// prepass finds every point within dbound of its anchor with
+// fbound * dbound <= kAnchorTurns (8 turns): the error of a term is then at
+// most a few 2^-24 of 2 pi (1 + 2 fbound dbound) radians, and the terms
+// with large f . dx are those with small amplitudes.  Scattered points, or
+// point bounds too large for the fixed-point phase, take the exact paths.
+//
 // Accumulation: every 64 terms a partial sum is folded into the running sum,
 // which keeps the FP32 rounding error of N_f = 4096..16384-term sums near
 // 1e-7 of the field's standard deviation.
@@ -59,6 +73,10 @@ QRS_CHECK_HOOK(check_hook_synth)
 #define QRS_SYNTH_PAIRED 1   // 1: paired FP32 instructions (two points per FFMA2) where they apply
 #endif
 
+#ifndef QRS_SYNTH_ANCHOR
+#define QRS_SYNTH_ANCHOR 1   // 1: the anchored path where the point groups allow it
+#endif
+
 #ifndef QRS_SYNTH_TPB
 #define QRS_SYNTH_TPB 128    // threads per CTA
 #endif
@@ -71,26 +89,72 @@ constexpr int kSynthUnroll = QRS_SYNTH_UNROLL;
 // Largest a + b of the fixed-point phase: 55 where the paired path can take
 // the fraction from the high word, 54 (funnel-shift extraction) otherwise.
 constexpr int kSynthMaxAB = (QRS_SYNTH_PAIRED && QRS_SYNTH_FOLD) ? 55 : 54;
+// The anchored path needs the radian fold and the paired instructions.
+constexpr bool kAnchorBuilt = QRS_SYNTH_ANCHOR && QRS_SYNTH_PAIRED && QRS_SYNTH_FOLD;
+constexpr double kAnchorTurns = 8.0;  // ceiling of fbound * dbound on the anchored path
+// Shared memory per cached term: the 16-byte record and the anchored path's
+// 2 pi (fx, fy).
+constexpr int kSynthTermBytes = (int)(sizeof(float4) + sizeof(float2));
 
-// Prepass: one CTA computes max(|x|, |y|) over all points (no atomics, no
-// zeroing); the synthesis kernel reads it to pick its phase path and scales.
+// The anchor of a point of its group (first point a0, last point a1): the
+// nearer in the max norm, ties to a0.  Returns true for a1 and the FP32
+// offset from the chosen anchor in d.  The prepass and the kernel call the
+// same function, so the offsets the kernel uses are those the prepass bounds.
+__device__ __forceinline__ bool anchor_pick(float2 v, float2 a0, float2 a1, float2& d)
+{
+    const float dx0 = v.x - a0.x, dy0 = v.y - a0.y;
+    const float dx1 = v.x - a1.x, dy1 = v.y - a1.y;
+    const bool second = fmaxf(fabsf(dx1), fabsf(dy1)) < fmaxf(fabsf(dx0), fabsf(dy0));
+    d = second ? make_float2(dx1, dy1) : make_float2(dx0, dy0);
+    return second;
+}
+
+// Prepass: one CTA computes the point bound max(|x|, |y|) into out[0] and the
+// anchor bound (the largest offset of a point from its anchor, over the
+// groups of kSynthPPT consecutive points; +inf if a coordinate is not finite)
+// into out[1], without atomics or zeroing; the synthesis kernel reads both
+// to pick its phase path and scales.
 __global__ void k_point_bound(const float2* __restrict__ xy, int64_t n, float* __restrict__ out)
 {
-    float m = 0.0f;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const float2 v = xy[i];
-        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    float m = 0.0f, dm = 0.0f;
+    bool finite = true;
+    for (int64_t g0 = (int64_t)threadIdx.x * kSynthPPT; g0 < n; g0 += (int64_t)blockDim.x * kSynthPPT) {
+        const int nv = (int)min((int64_t)kSynthPPT, n - g0);
+        const float2 a0 = xy[g0], a1 = xy[g0 + nv - 1];
+        for (int j = 0; j < nv; ++j) {
+            const float2 v = xy[g0 + j];
+            finite = finite && isfinite(v.x) && isfinite(v.y);
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+            float2 d;
+            anchor_pick(v, a0, a1, d);
+            dm = fmaxf(dm, fmaxf(fabsf(d.x), fabsf(d.y)));
+        }
     }
+    if (!finite) dm = INFINITY;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    __shared__ float wmax[32];
-    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    }
+    __shared__ float wmax[2][32];
+    if ((threadIdx.x & 31) == 0) {
+        wmax[0][threadIdx.x >> 5] = m;
+        wmax[1][threadIdx.x >> 5] = dm;
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
-        m = (threadIdx.x < (blockDim.x >> 5)) ? wmax[threadIdx.x] : 0.0f;
+        const bool live = threadIdx.x < (blockDim.x >> 5);
+        m = live ? wmax[0][threadIdx.x] : 0.0f;
+        dm = live ? wmax[1][threadIdx.x] : 0.0f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) *out = m;
+        for (int o = 16; o > 0; o >>= 1) {
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+        }
+        if (threadIdx.x == 0) {
+            out[0] = m;
+            out[1] = dm;
+        }
     }
 }
 
@@ -136,6 +200,59 @@ __device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restr
                 const float2 mant = make_float2(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u),
                                                 __uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u));
                 const float2 ang = __ffma2_rn(mant, two_pi, neg_two_pi);  // (1 + t) 2 pi - 2 pi
+                const float2 c = make_float2(__cosf(ang.x), __cosf(ang.y));
+                part[q] = __ffma2_rn(A, c, part[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            acc[2 * q] += part[q].x;
+            acc[2 * q + 1] += part[q].y;
+        }
+    }
+}
+
+// The anchored path's term loop.  Per term: the exact phases of the two
+// anchors (fixed point, radians in [0, 2 pi)), then per pair of points one
+// FFMA2 picks the anchor's phase (S = 0 or 1 against D = A1 - A0; exact for
+// S = 0, within one ulp of A1 for S = 1), two FFMA2 add 2 pi fx dx and
+// 2 pi fy dy, and the cosine and the accumulating FFMA2 follow as in the
+// exact paths.
+template <bool HI>
+__device__ __forceinline__ void accumulate_chunk_anchor(const float4* __restrict__ st, const float2* __restrict__ sw,
+                                                        int len, int32_t X0, int32_t Y0, int32_t X1, int32_t Y1,
+                                                        const float2 (&DX)[kSynthPPT / 2],
+                                                        const float2 (&DY)[kSynthPPT / 2],
+                                                        const float2 (&S)[kSynthPPT / 2], float (&acc)[kSynthPPT],
+                                                        const FixedScales& z)
+{
+    constexpr int NP = kSynthPPT / 2;
+    for (int k0 = 0; k0 < len; k0 += kSynthGroup) {
+        const int k1 = min(k0 + kSynthGroup, len);
+        float2 part[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) part[q] = make_float2(0.0f, 0.0f);
+#pragma unroll kSynthUnroll
+        for (int k = k0; k < k1; ++k) {
+            const float4 T = *chk(st, k, (int64_t)len);
+            const float2 W = *chk(sw, k, (int64_t)len);
+            const uint64_t C = (uint64_t)__float_as_uint(T.w) * z.psi_mul + z.bias;
+            const int32_t Fx = __float_as_int(T.x), Fy = __float_as_int(T.y);
+            const uint32_t m0 = HI ? phase_fx_word_hi(Fx, Fy, X0, Y0, C) : phase_fx_word(Fx, Fy, X0, Y0, C, z.shift);
+            const uint32_t m1 = HI ? phase_fx_word_hi(Fx, Fy, X1, Y1, C) : phase_fx_word(Fx, Fy, X1, Y1, C, z.shift);
+            const float a0 = fmaf(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u), 6.28318530717958648f,
+                                  -6.28318530717958648f);
+            const float a1 = fmaf(__uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u), 6.28318530717958648f,
+                                  -6.28318530717958648f);
+            const float2 A0 = make_float2(a0, a0);
+            const float2 D = make_float2(a1 - a0, a1 - a0);
+            const float2 TX = make_float2(W.x, W.x), TY = make_float2(W.y, W.y);
+            const float2 A = make_float2(T.z, T.z);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                float2 ang = __ffma2_rn(S[q], D, A0);
+                ang = __ffma2_rn(TX, DX[q], ang);
+                ang = __ffma2_rn(TY, DY[q], ang);
                 const float2 c = make_float2(__cosf(ang.x), __cosf(ang.y));
                 part[q] = __ffma2_rn(A, c, part[q]);
             }
@@ -224,12 +341,41 @@ __device__ __forceinline__ void accumulate_chunk(const float4* __restrict__ st, 
     }
 }
 
-__global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawParams p, const float2* __restrict__ xy, int64_t P,
-                                                           float* __restrict__ out, const float* __restrict__ d_xbound,
-                                                           float fbound, int chunk, int64_t n_tiles, int64_t n_items)
+// Draws terms [k_begin, k_begin + len) of realisation r into the CTA's
+// shared-memory records (and, for the anchored path, 2 pi (fx, fy)).
+__device__ __forceinline__ void draw_chunk(const DrawParams& p, const FixedScales& z, int64_t r, int64_t k_begin,
+                                           int len, int chunk, float4* __restrict__ sterm, float2* __restrict__ sw,
+                                           bool anchored)
 {
-    extern __shared__ float4 sterm[];
-    const FixedScales z = fixed_scales(fbound, *d_xbound, QRS_SYNTH_FOLD != 0, kSynthMaxAB);
+    const uint64_t n0 = (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k_begin;
+    for (int q = threadIdx.x; q < len; q += kSynthTPB) {
+        Words w;
+        const Term t = draw_term<false, false>(p, n0 + (uint64_t)q, k_begin + q, &w);
+        float amp;
+        uint32_t u;
+        coef_polar_from_words(p, n0 + (uint64_t)q, w, amp, u);
+        float4 rec;
+        if (z.use_fixed) {
+            rec.x = __int_as_float(__float2int_rn(t.fx * z.fscale));
+            rec.y = __int_as_float(__float2int_rn(t.fy * z.fscale));
+            rec.w = __uint_as_float(u);
+        } else {
+            rec.x = t.fx;
+            rec.y = t.fy;
+            rec.w = (float)u * 0x1p-24f;
+        }
+        rec.z = t.F * amp;
+        *chk(sterm, q, (int64_t)chunk) = rec;
+        if (anchored) *chk(sw, q, (int64_t)chunk) = make_float2(t.fx * 6.28318530717958648f, t.fy * 6.28318530717958648f);
+    }
+}
+
+// The exact paths: a thread's points strided by the CTA width (coalesced),
+// each (point, term) phase formed in full.
+__device__ __forceinline__ void synth_items_exact(const DrawParams& p, const float2* __restrict__ xy, int64_t P,
+                                                  float* __restrict__ out, const FixedScales& z, int chunk,
+                                                  int64_t n_tiles, int64_t n_items, float4* __restrict__ sterm)
+{
     const int64_t G = gridDim.x;
     const int64_t it0 = (n_items * (int64_t)blockIdx.x) / G;
     const int64_t it1 = (n_items * ((int64_t)blockIdx.x + 1)) / G;
@@ -260,26 +406,7 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
             const int len = (int)min((int64_t)chunk, p.n_f - k_begin);
             if (r != cached_r || c != cached_c) {
                 __syncthreads();  // previous chunk fully consumed
-                const uint64_t n0 = (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k_begin;
-                for (int q = threadIdx.x; q < len; q += kSynthTPB) {
-                    Words w;
-                    const Term t = draw_term<false, false>(p, n0 + (uint64_t)q, k_begin + q, &w);
-                    float amp;
-                    uint32_t u;
-                    coef_polar_from_words(p, n0 + (uint64_t)q, w, amp, u);
-                    float4 rec;
-                    if (z.use_fixed) {
-                        rec.x = __int_as_float(__float2int_rn(t.fx * z.fscale));
-                        rec.y = __int_as_float(__float2int_rn(t.fy * z.fscale));
-                        rec.w = __uint_as_float(u);
-                    } else {
-                        rec.x = t.fx;
-                        rec.y = t.fy;
-                        rec.w = (float)u * 0x1p-24f;
-                    }
-                    rec.z = t.F * amp;
-                    *chk(sterm, q, (int64_t)chunk) = rec;
-                }
+                draw_chunk(p, z, r, k_begin, len, chunk, sterm, nullptr, false);
                 __syncthreads();
                 cached_r = r;
                 cached_c = c;
@@ -308,46 +435,92 @@ __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawP
     }
 }
 
-cudaError_t launch_synth_fused(qrs_handle* h, const DrawParams& p, const float* xy, int64_t n_points, int64_t n_real,
-                               float* out, cudaStream_t s)
+// The anchored path: a thread's kSynthPPT consecutive points (one group of
+// the prepass), offsets from the nearer of the group's first and last points.
+__device__ __forceinline__ void synth_items_anchor(const DrawParams& p, const float2* __restrict__ xy, int64_t P,
+                                                   float* __restrict__ out, const FixedScales& z, int chunk,
+                                                   int64_t n_tiles, int64_t n_items, float4* __restrict__ sterm,
+                                                   float2* __restrict__ sw)
 {
-    cudaError_t e = launch_point_bound(xy, n_points, h->d_xbound, s);
-    if (e != cudaSuccess) return e;
-    ++h->launches;
-    const int chunk = (int)(p.n_f < kSynthChunkMax ? p.n_f : kSynthChunkMax);
-    const size_t smem = (size_t)chunk * sizeof(float4);
-    e = cudaFuncSetAttribute(k_synth_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kSynthChunkMax * sizeof(float4)));
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_synth_fused, kSynthTPB, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int64_t n_tiles = (n_points + kSynthTile - 1) / kSynthTile;
-    const int64_t n_items = n_tiles * n_real;
-    int64_t grid = (int64_t)h->num_sms * per_sm;
-    if (grid > n_items) grid = n_items;
-    k_synth_fused<<<(unsigned)grid, kSynthTPB, smem, s>>>(p, reinterpret_cast<const float2*>(xy), n_points, out,
-                                                          h->d_xbound, (float)freq_bound(p), chunk, n_tiles, n_items);
-    return cudaGetLastError();
+    constexpr int NP = kSynthPPT / 2;
+    const int64_t G = gridDim.x;
+    const int64_t it0 = (n_items * (int64_t)blockIdx.x) / G;
+    const int64_t it1 = (n_items * ((int64_t)blockIdx.x + 1)) / G;
+    const int n_chunks = (int)((p.n_f + chunk - 1) / chunk);
+    int64_t cached_r = -1;
+    int cached_c = -1;
+    for (int64_t item = it0; item < it1; ++item) {
+        const int64_t r = item / n_tiles;
+        const int64_t tile = item - r * n_tiles;
+        const int64_t g0 = tile * kSynthTile + (int64_t)threadIdx.x * kSynthPPT;
+        const int64_t rem = P - g0;
+        const int nv = rem <= 0 ? 0 : (rem < kSynthPPT ? (int)rem : kSynthPPT);  // valid points of the group
+        const float2 a0 = nv > 0 ? *chk(xy, g0, P) : make_float2(0.0f, 0.0f);
+        const float2 a1 = nv > 0 ? *chk(xy, g0 + nv - 1, P) : make_float2(0.0f, 0.0f);
+        const int32_t X0 = __float2int_rn(a0.x * z.xscale), Y0 = __float2int_rn(a0.y * z.xscale);
+        const int32_t X1 = __float2int_rn(a1.x * z.xscale), Y1 = __float2int_rn(a1.y * z.xscale);
+        float2 DX[NP], DY[NP], S[NP];
+        float acc[kSynthPPT];
+#pragma unroll
+        for (int j = 0; j < kSynthPPT; ++j) {
+            float2 d = make_float2(0.0f, 0.0f);
+            const bool second = j < nv && anchor_pick(*chk(xy, g0 + j, P), a0, a1, d);
+            if (j & 1) {
+                DX[j >> 1].y = d.x;
+                DY[j >> 1].y = d.y;
+                S[j >> 1].y = second ? 1.0f : 0.0f;
+            } else {
+                DX[j >> 1].x = d.x;
+                DY[j >> 1].x = d.y;
+                S[j >> 1].x = second ? 1.0f : 0.0f;
+            }
+            acc[j] = 0.0f;
+        }
+        for (int c = 0; c < n_chunks; ++c) {
+            const int64_t k_begin = (int64_t)c * chunk;
+            const int len = (int)min((int64_t)chunk, p.n_f - k_begin);
+            if (r != cached_r || c != cached_c) {
+                __syncthreads();  // previous chunk fully consumed
+                draw_chunk(p, z, r, k_begin, len, chunk, sterm, sw, true);
+                __syncthreads();
+                cached_r = r;
+                cached_c = c;
+            }
+            if (z.shift == 32) accumulate_chunk_anchor<true>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+            else accumulate_chunk_anchor<false>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+        }
+        const int64_t n_out = (n_items / n_tiles) * P;
+#pragma unroll
+        for (int j = 0; j < kSynthPPT; ++j)
+            if (j < nv) *chk(out, r * P + g0 + j, n_out) = acc[j];
+    }
 }
 
-}  // namespace qrs
-
-namespace qrs {
-
-// Same two launches as launch_synth_fused (point-bound prepass, then the fused
-// kernel), for callers that bring their own device scratch word instead of a
-// handle: `d_bound` receives the point bound; `num_sms` sizes the grid.
-cudaError_t launch_synth_fused_raw(int num_sms, float* d_bound, const DrawParams& p, const float* xy,
-                                   int64_t n_points, int64_t n_real, float* out, cudaStream_t s)
+// d_bound: [0] the point bound, [1] the anchor bound (k_point_bound).
+// allow_anchor = 0 keeps the exact paths whatever the bounds.
+__global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawParams p, const float2* __restrict__ xy, int64_t P,
+                                                           float* __restrict__ out, const float* __restrict__ d_bound,
+                                                           float fbound, int chunk, int64_t n_tiles, int64_t n_items,
+                                                           int allow_anchor)
 {
-    cudaError_t e = launch_point_bound(xy, n_points, d_bound, s);
-    if (e != cudaSuccess) return e;
+    extern __shared__ float4 sterm[];
+    float2* sw = reinterpret_cast<float2*>(sterm + chunk);
+    const FixedScales z = fixed_scales(fbound, d_bound[0], QRS_SYNTH_FOLD != 0, kSynthMaxAB);
+    const bool anchored = kAnchorBuilt && allow_anchor != 0 && z.use_fixed &&
+                          (double)fbound * (double)d_bound[1] <= kAnchorTurns;
+    if (anchored) synth_items_anchor(p, xy, P, out, z, chunk, n_tiles, n_items, sterm, sw);
+    else synth_items_exact(p, xy, P, out, z, chunk, n_tiles, n_items, sterm);
+}
+
+// The fused kernel after the prepass has written d_bound[0..1]: a persistent
+// grid of num_sms x the resident CTAs per SM.
+static cudaError_t launch_fused_kernel(int num_sms, const float* d_bound, const DrawParams& p, const float* xy,
+                                      int64_t n_points, int64_t n_real, float* out, int allow_anchor, cudaStream_t s)
+{
     const int chunk = (int)(p.n_f < kSynthChunkMax ? p.n_f : kSynthChunkMax);
-    const size_t smem = (size_t)chunk * sizeof(float4);
-    e = cudaFuncSetAttribute(k_synth_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kSynthChunkMax * sizeof(float4)));
+    const size_t smem = (size_t)chunk * kSynthTermBytes;
+    cudaError_t e = cudaFuncSetAttribute(k_synth_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSynthChunkMax * kSynthTermBytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_synth_fused, kSynthTPB, smem);
@@ -358,8 +531,34 @@ cudaError_t launch_synth_fused_raw(int num_sms, float* d_bound, const DrawParams
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > n_items) grid = n_items;
     k_synth_fused<<<(unsigned)grid, kSynthTPB, smem, s>>>(p, reinterpret_cast<const float2*>(xy), n_points, out,
-                                                          d_bound, (float)freq_bound(p), chunk, n_tiles, n_items);
+                                                          d_bound, (float)freq_bound(p), chunk, n_tiles, n_items,
+                                                          allow_anchor);
     return cudaGetLastError();
+}
+
+cudaError_t launch_synth_fused(qrs_handle* h, const DrawParams& p, const float* xy, int64_t n_points, int64_t n_real,
+                               float* out, cudaStream_t s)
+{
+    cudaError_t e = launch_point_bound(xy, n_points, h->d_xbound, s);
+    if (e != cudaSuccess) return e;
+    ++h->launches;
+    return launch_fused_kernel(h->num_sms, h->d_xbound, p, xy, n_points, n_real, out, h->synth_anchor, s);
+}
+
+}  // namespace qrs
+
+namespace qrs {
+
+// Same two launches as launch_synth_fused (point-bound prepass, then the fused
+// kernel), for callers that bring their own device scratch instead of a
+// handle: `d_bound` (two floats) receives the point and anchor bounds;
+// `num_sms` sizes the grid; allow_anchor as the handle's switch.
+cudaError_t launch_synth_fused_raw(int num_sms, float* d_bound, const DrawParams& p, const float* xy,
+                                   int64_t n_points, int64_t n_real, float* out, int allow_anchor, cudaStream_t s)
+{
+    cudaError_t e = launch_point_bound(xy, n_points, d_bound, s);
+    if (e != cudaSuccess) return e;
+    return launch_fused_kernel(num_sms, d_bound, p, xy, n_points, n_real, out, allow_anchor, s);
 }
 
 }  // namespace qrs

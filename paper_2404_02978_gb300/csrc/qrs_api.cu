@@ -198,6 +198,7 @@ qrs_status qrs_create(qrs_handle** out, int32_t device)
     }
     if (const char* f = std::getenv("QRS_GRID_PAIR")) h->grid_pair = std::strcmp(f, "0") != 0;
     if (const char* f = std::getenv("QRS_GEMM_PAIR")) h->gemm_pair = std::strcmp(f, "0") != 0;
+    if (const char* f = std::getenv("QRS_SYNTH_ANCHOR")) h->synth_anchor = std::strcmp(f, "0") != 0;
     if (e == cudaSuccess && qrs::kChecked) {  // the checked build reports into this handle's error word
         for (cudaError_t (*hook)(int*) : {check_hook_api, check_hook_draw, check_hook_fft, check_hook_gemm,
                                           check_hook_grid, check_hook_piston, check_hook_proposal, check_hook_sf,

@@ -20,7 +20,7 @@ struct qrs_handle {
     std::string last_error;
     // Device workspace owned by the handle (allocated once in qrs_create).
     int* d_err = nullptr;          // device error word (0 = fine)
-    float* d_xbound = nullptr;     // per-call point bound max(|x|, |y|) of a synthesis
+    float* d_xbound = nullptr;     // per-call point bound max(|x|, |y|) of a synthesis, then the anchor bound
     // Growing device workspace for the GEMM form and batched pistons.
     void* d_work = nullptr;
     size_t work_bytes = 0;
@@ -44,6 +44,9 @@ struct qrs_handle {
     // qrs_create), per mode (3XTF32, BF16X3, TF32).
     int gemm_pair = 1;
     int gemm_pair_clusters[3] = {0, 0, 0};
+    // Fused form: the anchored phase path allowed where the point groups
+    // permit it (QRS_SYNTH_ANCHOR=0 at qrs_create keeps the exact paths).
+    int synth_anchor = 1;
 };
 
 namespace qrs {

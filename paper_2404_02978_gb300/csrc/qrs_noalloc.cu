@@ -6,18 +6,20 @@
 // latency-bound loop in which an allocation could block or synchronise the
 // device.  Creating a qrs_handle allocates its workspace, so those callers
 // use this entry point instead: it takes no handle, allocates nothing, and
-// keeps its only scratch -- the one-float point bound that picks the phase
-// path of the fused kernel -- in the file-scope device array below, which
+// keeps its only scratch -- the two-float point and anchor bounds that pick
+// the phase path of the fused kernel -- in the file-scope device array below, which
 // every GPU that loads the library holds until the process exits.
 #include <cuda.h>
 
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "qrs_internal.h"
 
 namespace qrs {
 cudaError_t launch_synth_fused_raw(int num_sms, float* d_bound, const DrawParams& p, const float* xy,
-                                   int64_t n_points, int64_t n_real, float* out, cudaStream_t s);
+                                   int64_t n_points, int64_t n_real, float* out, int allow_anchor, cudaStream_t s);
 }
 
 namespace {
@@ -102,14 +104,17 @@ extern "C" qrs_status qrs_synthesize_points_noalloc(const qrs_psd* psd, const qr
     if (!counters_fit(n_f, real_offset, n_real)) return QRS_ERR_ARG;  // the limits of qrs_synthesize_points
     if (n_real == 0 || n_points == 0) return QRS_OK;
     if (!xy || !out || ((uintptr_t)xy & 7) || ((uintptr_t)out & 3)) return QRS_ERR_ARG;
-    // the fused path needs one float of scratch, whatever the problem size
-    static_assert(sizeof(float) <= kNoAllocScratchBytes, "scratch holds the point bound");
+    // the fused path needs two floats of scratch, whatever the problem size
+    static_assert(2 * sizeof(float) <= kNoAllocScratchBytes, "scratch holds the point and anchor bounds");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return QRS_ERR_CUDA;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return QRS_ERR_UNSUPPORTED;
     st = noalloc_setup(dev);
     if (st != QRS_OK) return st;
+    // the phase path follows the same QRS_SYNTH_ANCHOR switch as a handle, so the outputs stay identical
+    const char* anchor_env = std::getenv("QRS_SYNTH_ANCHOR");
+    const int allow_anchor = (anchor_env && std::strcmp(anchor_env, "0") == 0) ? 0 : 1;
     cudaError_t e = launch_synth_fused_raw(g_noalloc_sms[dev], g_noalloc_bound[dev], p, xy, n_points, n_real, out,
-                                           (cudaStream_t)stream);
+                                           allow_anchor, (cudaStream_t)stream);
     return e == cudaSuccess ? QRS_OK : QRS_ERR_CUDA;
 }
