@@ -11,10 +11,11 @@ point, fused in libqrs's persistent kernel, FP32 output [1000 x 51,468].
 Printed: one JSON line.  `value` = freq-term evals/s (point x term x
 realisation) over all ranks, inputs resident on the device; `e2e` = the same
 through the C ABI with host buffers (pinned H2D of the points, D2H of the
-field) inside the timed region; `roofline` = the fused kernel against the
-smaller of its two ALU bounds (one cosine per term on the MUFU, two 64-bit
-integer multiply-adds per term for the exact phase); `cpu_baseline` = the FP64 CPU reference on a
-bounded sample on the host cores.
+field) inside the timed region; `roofline` = the fused form's anchored
+kernel against its ALU bound (one cosine per term on the MUFU; the exact
+fixed-point phase is formed at two anchors per 16-point group, and each point's
+FP32 offset costs three FP32 operations); `cpu_baseline` = the FP64 CPU
+reference on a bounded sample on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (torchrun): each rank synthesises its own 1000 realisations
@@ -52,9 +53,33 @@ SM_MAX_MHZ = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq-term evals/s"
 UNIT = "term/s"
-# DRAM bytes (read + write) per k_synth_fused launch on the workload above, from the ncu launch
-# list summarised in profiles/k_synth_fused_phase_screen.md (5.28 MB read + 146.66 MB write).
-SYNTH_TRAFFIC_BYTES = 151.94e6
+# DRAM bytes (read + write) per k_synth_anchor launch on the workload above, from the ncu launch
+# list summarised in profiles/k_synth_anchor_phase_screen.md; None until taken for this kernel.
+SYNTH_TRAFFIC_BYTES = None
+# The anchored path's group and ceiling (k_synth.cu: kAnchorPPT, kAnchorTurns), used only to label
+# which path the workload takes.
+ANCHOR_GROUP = 16
+ANCHOR_TURNS = 8.0
+# FP32-pipe operations per (point, term) on the anchored path: the anchor's phase picked (1), the
+# offsets fx dx and fy dy (2), the radian-to-turn product of the cosine (1), the accumulation (1).
+ANCHOR_FMA_OPS = 5
+
+
+def anchor_path_applies(xy, fmax):
+    """The anchored path's rule on the host: each group of ANCHOR_GROUP consecutive points, every
+    point's FP32 offset from the nearer (max norm) of the group's first and last point."""
+    n = xy.shape[0]
+    pad = (-n) % ANCHOR_GROUP
+    g = np.concatenate([xy, np.repeat(xy[-1:], pad, 0)]).reshape(-1, ANCHOR_GROUP, 2)
+    last = np.full(g.shape[0], ANCHOR_GROUP - 1)
+    if pad:
+        last[-1] = ANCHOR_GROUP - 1 - pad
+    a0 = g[:, :1, :]
+    a1 = g[np.arange(g.shape[0]), last][:, None, :]
+    d0 = np.abs(g - a0).max(-1)
+    d1 = np.abs(g - a1).max(-1)
+    d = np.where(d1 < d0, d1, d0)
+    return float(fmax) * float(d.max()) <= ANCHOR_TURNS
 
 
 def _args():
@@ -970,10 +995,15 @@ def run_ours(a):
     if os.path.exists(MEASURED_PEAKS):
         peaks = json.load(open(MEASURED_PEAKS))
     sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ))
-    # per term: 1 MUFU cosine (amplitude-phase form of Eq. 3) and 2 wide multiply-adds (exact phase)
+    # per (point, term) on the anchored path: 1 MUFU cosine (amplitude-phase form of Eq. 3),
+    # ANCHOR_FMA_OPS FP32 operations, and 4 wide multiply-adds per group of 16 points (the two
+    # anchors' exact phases); on the exact path 2 wide multiply-adds per (point, term)
+    anchored = anchor_path_applies(xy_np, p["fmax"])
     mufu_terms = N_SM * MUFU_PER_SM_CLK * sm_max * 1e6
-    imad_terms = N_SM * IMAD_WIDE_PER_SM_CLK / 2 * sm_max * 1e6
-    peak_terms = min(mufu_terms, imad_terms)
+    fma_terms = N_SM * FMA_PER_SM_CLK / ANCHOR_FMA_OPS * sm_max * 1e6
+    imad_per_term = 4.0 / ANCHOR_GROUP if anchored else 2.0
+    imad_terms = N_SM * IMAD_WIDE_PER_SM_CLK / imad_per_term * sm_max * 1e6
+    peak_terms = min(mufu_terms, imad_terms, fma_terms) if anchored else min(mufu_terms, imad_terms)
     achieved = terms_step / (t_step / 1e3)  # per launch, one GPU
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -982,13 +1012,18 @@ def run_ours(a):
         "realizations_per_s": R * a.steps * world / t_tot,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_terms / 1e9, "unit": "Gterm/s",
                      "frac": achieved / peak_terms, "traffic": SYNTH_TRAFFIC_BYTES,
-                     "traffic_source": "profiles/k_synth_fused_phase_screen.md (ncu dram__bytes_read.sum + "
+                     "traffic_source": "profiles/k_synth_anchor_phase_screen.md (ncu dram__bytes_read.sum + "
                                        "dram__bytes_write.sum per launch of this kernel on this workload)",
                      "algorithmic_bytes": int(xy_np.nbytes + R * P * 4),
-                     "kernel": "k_synth_fused (+ k_point_bound prepass, <0.01%)",
-                     "peak_basis": "min(1 cos per term at 16 per SM-clock: %.0f, 2 mad.wide.s32 per term at %.2f "
-                                   "per SM-clock: %.0f) Gterm/s, 152 SM at %.0f MHz (unit rates measured)"
-                                   % (mufu_terms / 1e9, IMAD_WIDE_PER_SM_CLK, imad_terms / 1e9, sm_max),
+                     "path": "anchored" if anchored else "exact",
+                     "kernel": ("k_synth_anchor (+ k_point_bound prepass and k_synth_fused, which returns at once)"
+                                if anchored else "k_synth_fused (+ k_point_bound prepass)"),
+                     "peak_basis": "min(1 cos per term at 16 per SM-clock: %.0f, %.2f mad.wide.s32 per term at %.2f "
+                                   "per SM-clock: %.0f%s) Gterm/s, 152 SM at %.0f MHz (unit rates measured)"
+                                   % (mufu_terms / 1e9, imad_per_term, IMAD_WIDE_PER_SM_CLK, imad_terms / 1e9,
+                                      (", %d FP32 ops per term at 128 per SM-clock: %.0f" % (ANCHOR_FMA_OPS,
+                                                                                          fma_terms / 1e9))
+                                      if anchored else "", sm_max),
                      "frac_of_mufu_bound": achieved / mufu_terms},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xy_np.nbytes),
                 "d2h_bytes_per_step": int(R * P * 4), "steps": e2e_steps},

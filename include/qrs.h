@@ -250,7 +250,7 @@ qrs_status qrs_draw(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, co
  *                         in one persistent kernel, each term as one cosine in
  *                         Eq. 3's amplitude-phase form F amp cos 2 pi (phi + psi)
  *                         (amp, psi: the polar form of (a, b)); col_psd must be
- *                         NULL.  Where each group of 12 consecutive points lies
+ *                         NULL.  Where each group of 16 consecutive points lies
  *                         within d of the group's first or last point with
  *                         f_max d <= 8 (and the fixed-point phase applies),
  *                         the exact phase is formed at those two anchors

@@ -30,9 +30,9 @@
 // a + b = 55 (fbound * xbound <= 64 with room in the ceilings), the fraction
 // is the low 23 bits of the phase word's high half and needs no shift.
 //
-// Anchored path (the fixed-point path's fast form, Eq. 3 unchanged): each
-// thread takes kSynthPPT consecutive points instead, and the group's first
-// and last points are its two anchors.  Per term the thread forms the exact
+// Anchored path (the fixed-point path's fast form, Eq. 3 unchanged; its own
+// kernel, k_synth_anchor): each thread takes kAnchorPPT (16) consecutive
+// points, and the group's first and last points are its two anchors.  Per term the thread forms the exact
 // 64-bit fixed-point phase of the two anchors only; every point adds its
 // FP32 offset from the nearer anchor, 2 pi (fx dx + fy dy), to that anchor's
 // phase in radians, so a (point, term) costs three paired FP32 instructions
@@ -84,17 +84,44 @@ constexpr int kSynthTPB = QRS_SYNTH_TPB;
 constexpr int kSynthPPT = QRS_SYNTH_PPT;
 constexpr int kSynthTile = kSynthTPB * kSynthPPT;
 constexpr int kSynthChunkMax = 4096;  // terms cached per CTA (64 KB)
+
+// The anchored kernel's own tunables (compile-time; defaults measured best on
+// GB300): threads per CTA, points per thread (= the anchor group), minimum
+// resident CTAs per SM, terms per shared-memory chunk, term-loop unroll.
+#ifndef QRS_ANCHOR_TPB
+#define QRS_ANCHOR_TPB 128
+#endif
+#ifndef QRS_ANCHOR_PPT
+#define QRS_ANCHOR_PPT 16
+#endif
+#ifndef QRS_ANCHOR_MINB
+#define QRS_ANCHOR_MINB 3
+#endif
+#ifndef QRS_ANCHOR_CHUNK
+#define QRS_ANCHOR_CHUNK 2048
+#endif
+#ifndef QRS_ANCHOR_UNROLL
+#define QRS_ANCHOR_UNROLL 16
+#endif
+constexpr int kAnchorTPB = QRS_ANCHOR_TPB;
+constexpr int kAnchorPPT = QRS_ANCHOR_PPT;
+constexpr int kAnchorTile = kAnchorTPB * kAnchorPPT;
+constexpr int kAnchorChunk = QRS_ANCHOR_CHUNK;
+constexpr int kAnchorUnroll = QRS_ANCHOR_UNROLL;
+static_assert(kAnchorPPT % 2 == 0 && kAnchorPPT >= 2, "anchor groups hold pairs of points");
+
 constexpr int kSynthGroup = QRS_SYNTH_GROUP;
 constexpr int kSynthUnroll = QRS_SYNTH_UNROLL;
+static_assert(kAnchorChunk % kSynthGroup == 0, "anchored chunks hold whole partial sums");
 // Largest a + b of the fixed-point phase: 55 where the paired path can take
 // the fraction from the high word, 54 (funnel-shift extraction) otherwise.
 constexpr int kSynthMaxAB = (QRS_SYNTH_PAIRED && QRS_SYNTH_FOLD) ? 55 : 54;
 // The anchored path needs the radian fold and the paired instructions.
 constexpr bool kAnchorBuilt = QRS_SYNTH_ANCHOR && QRS_SYNTH_PAIRED && QRS_SYNTH_FOLD;
 constexpr double kAnchorTurns = 8.0;  // ceiling of fbound * dbound on the anchored path
-// Shared memory per cached term: the 16-byte record and the anchored path's
-// 2 pi (fx, fy).
-constexpr int kSynthTermBytes = (int)(sizeof(float4) + sizeof(float2));
+// Shared memory per cached term of the anchored kernel: the 16-byte record
+// and 2 pi (fx, fy).
+constexpr int kAnchorTermBytes = (int)(sizeof(float4) + sizeof(float2));
 
 // The anchor of a point of its group (first point a0, last point a1): the
 // nearer in the max norm, ties to a0.  Returns true for a1 and the FP32
@@ -111,15 +138,15 @@ __device__ __forceinline__ bool anchor_pick(float2 v, float2 a0, float2 a1, floa
 
 // Prepass: one CTA computes the point bound max(|x|, |y|) into out[0] and the
 // anchor bound (the largest offset of a point from its anchor, over the
-// groups of kSynthPPT consecutive points; +inf if a coordinate is not finite)
+// groups of kAnchorPPT consecutive points; +inf if a coordinate is not finite)
 // into out[1], without atomics or zeroing; the synthesis kernel reads both
 // to pick its phase path and scales.
 __global__ void k_point_bound(const float2* __restrict__ xy, int64_t n, float* __restrict__ out)
 {
     float m = 0.0f, dm = 0.0f;
     bool finite = true;
-    for (int64_t g0 = (int64_t)threadIdx.x * kSynthPPT; g0 < n; g0 += (int64_t)blockDim.x * kSynthPPT) {
-        const int nv = (int)min((int64_t)kSynthPPT, n - g0);
+    for (int64_t g0 = (int64_t)threadIdx.x * kAnchorPPT; g0 < n; g0 += (int64_t)blockDim.x * kAnchorPPT) {
+        const int nv = (int)min((int64_t)kAnchorPPT, n - g0);
         const float2 a0 = xy[g0], a1 = xy[g0 + nv - 1];
         for (int j = 0; j < nv; ++j) {
             const float2 v = xy[g0 + j];
@@ -221,18 +248,18 @@ __device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restr
 template <bool HI>
 __device__ __forceinline__ void accumulate_chunk_anchor(const float4* __restrict__ st, const float2* __restrict__ sw,
                                                         int len, int32_t X0, int32_t Y0, int32_t X1, int32_t Y1,
-                                                        const float2 (&DX)[kSynthPPT / 2],
-                                                        const float2 (&DY)[kSynthPPT / 2],
-                                                        const float2 (&S)[kSynthPPT / 2], float (&acc)[kSynthPPT],
+                                                        const float2 (&DX)[kAnchorPPT / 2],
+                                                        const float2 (&DY)[kAnchorPPT / 2],
+                                                        const float2 (&S)[kAnchorPPT / 2], float (&acc)[kAnchorPPT],
                                                         const FixedScales& z)
 {
-    constexpr int NP = kSynthPPT / 2;
+    constexpr int NP = kAnchorPPT / 2;
     for (int k0 = 0; k0 < len; k0 += kSynthGroup) {
         const int k1 = min(k0 + kSynthGroup, len);
         float2 part[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) part[q] = make_float2(0.0f, 0.0f);
-#pragma unroll kSynthUnroll
+#pragma unroll kAnchorUnroll
         for (int k = k0; k < k1; ++k) {
             const float4 T = *chk(st, k, (int64_t)len);
             const float2 W = *chk(sw, k, (int64_t)len);
@@ -343,12 +370,13 @@ __device__ __forceinline__ void accumulate_chunk(const float4* __restrict__ st, 
 
 // Draws terms [k_begin, k_begin + len) of realisation r into the CTA's
 // shared-memory records (and, for the anchored path, 2 pi (fx, fy)).
+template <int TPB>
 __device__ __forceinline__ void draw_chunk(const DrawParams& p, const FixedScales& z, int64_t r, int64_t k_begin,
                                            int len, int chunk, float4* __restrict__ sterm, float2* __restrict__ sw,
                                            bool anchored)
 {
     const uint64_t n0 = (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k_begin;
-    for (int q = threadIdx.x; q < len; q += kSynthTPB) {
+    for (int q = threadIdx.x; q < len; q += TPB) {
         Words w;
         const Term t = draw_term<false, false>(p, n0 + (uint64_t)q, k_begin + q, &w);
         float amp;
@@ -406,7 +434,7 @@ __device__ __forceinline__ void synth_items_exact(const DrawParams& p, const flo
             const int len = (int)min((int64_t)chunk, p.n_f - k_begin);
             if (r != cached_r || c != cached_c) {
                 __syncthreads();  // previous chunk fully consumed
-                draw_chunk(p, z, r, k_begin, len, chunk, sterm, nullptr, false);
+                draw_chunk<kSynthTPB>(p, z, r, k_begin, len, chunk, sterm, nullptr, false);
                 __syncthreads();
                 cached_r = r;
                 cached_c = c;
@@ -435,92 +463,136 @@ __device__ __forceinline__ void synth_items_exact(const DrawParams& p, const flo
     }
 }
 
-// The anchored path: a thread's kSynthPPT consecutive points (one group of
-// the prepass), offsets from the nearer of the group's first and last points.
-__device__ __forceinline__ void synth_items_anchor(const DrawParams& p, const float2* __restrict__ xy, int64_t P,
-                                                   float* __restrict__ out, const FixedScales& z, int chunk,
-                                                   int64_t n_tiles, int64_t n_items, float4* __restrict__ sterm,
-                                                   float2* __restrict__ sw)
+// Whether the anchored path applies to a launch: the fixed-point phase is
+// available and every point lies within dbound of its anchor with
+// fbound * dbound <= kAnchorTurns.  Both kernels evaluate it from the same
+// prepass output, so exactly one of them does the work.
+__device__ __forceinline__ bool anchor_applies(const FixedScales& z, float fbound, const float* d_bound,
+                                               int allow_anchor)
 {
-    constexpr int NP = kSynthPPT / 2;
+    return kAnchorBuilt && allow_anchor != 0 && z.use_fixed && (double)fbound * (double)d_bound[1] <= kAnchorTurns;
+}
+
+// The anchored kernel.  Work items and their split over the persistent grid
+// are those of k_synth_fused (realisation-major (realisation, tile) items, one
+// contiguous range per CTA), with tiles of kAnchorTPB x kAnchorPPT points and
+// each thread's kAnchorPPT consecutive points one anchor group.  The terms
+// are taken chunk by chunk for each realisation of the range: the CTA draws a
+// chunk once and runs every tile of that realisation through it, carrying each
+// point's running sum from chunk to chunk in `out` (an FP32 store and reload,
+// so the sums are those of one pass over all terms).  Chunks therefore stay
+// small (kAnchorChunk terms) and several CTAs fit on an SM.
+// d_bound: [0] the point bound, [1] the anchor bound (k_point_bound).
+__global__ void __launch_bounds__(kAnchorTPB, QRS_ANCHOR_MINB) k_synth_anchor(DrawParams p, const float2* __restrict__ xy,
+                                                              int64_t P, float* __restrict__ out,
+                                                              const float* __restrict__ d_bound, float fbound,
+                                                              int chunk, int64_t n_tiles, int64_t n_items,
+                                                              int allow_anchor)
+{
+    extern __shared__ float4 sterm[];
+    float2* sw = reinterpret_cast<float2*>(sterm + chunk);
+    const FixedScales z = fixed_scales(fbound, d_bound[0], true, kSynthMaxAB);
+    if (!anchor_applies(z, fbound, d_bound, allow_anchor)) return;  // k_synth_fused does the work
+    constexpr int NP = kAnchorPPT / 2;
     const int64_t G = gridDim.x;
     const int64_t it0 = (n_items * (int64_t)blockIdx.x) / G;
     const int64_t it1 = (n_items * ((int64_t)blockIdx.x + 1)) / G;
     const int n_chunks = (int)((p.n_f + chunk - 1) / chunk);
-    int64_t cached_r = -1;
-    int cached_c = -1;
-    for (int64_t item = it0; item < it1; ++item) {
-        const int64_t r = item / n_tiles;
-        const int64_t tile = item - r * n_tiles;
-        const int64_t g0 = tile * kSynthTile + (int64_t)threadIdx.x * kSynthPPT;
-        const int64_t rem = P - g0;
-        const int nv = rem <= 0 ? 0 : (rem < kSynthPPT ? (int)rem : kSynthPPT);  // valid points of the group
-        const float2 a0 = nv > 0 ? *chk(xy, g0, P) : make_float2(0.0f, 0.0f);
-        const float2 a1 = nv > 0 ? *chk(xy, g0 + nv - 1, P) : make_float2(0.0f, 0.0f);
-        const int32_t X0 = __float2int_rn(a0.x * z.xscale), Y0 = __float2int_rn(a0.y * z.xscale);
-        const int32_t X1 = __float2int_rn(a1.x * z.xscale), Y1 = __float2int_rn(a1.y * z.xscale);
-        float2 DX[NP], DY[NP], S[NP];
-        float acc[kSynthPPT];
-#pragma unroll
-        for (int j = 0; j < kSynthPPT; ++j) {
-            float2 d = make_float2(0.0f, 0.0f);
-            const bool second = j < nv && anchor_pick(*chk(xy, g0 + j, P), a0, a1, d);
-            if (j & 1) {
-                DX[j >> 1].y = d.x;
-                DY[j >> 1].y = d.y;
-                S[j >> 1].y = second ? 1.0f : 0.0f;
-            } else {
-                DX[j >> 1].x = d.x;
-                DY[j >> 1].x = d.y;
-                S[j >> 1].x = second ? 1.0f : 0.0f;
-            }
-            acc[j] = 0.0f;
-        }
+    const int64_t n_out = (n_items / n_tiles) * P;
+    for (int64_t seg = it0; seg < it1;) {
+        const int64_t r = seg / n_tiles;
+        const int64_t seg_end = min(it1, (r + 1) * n_tiles);  // this range's items of realisation r
         for (int c = 0; c < n_chunks; ++c) {
             const int64_t k_begin = (int64_t)c * chunk;
             const int len = (int)min((int64_t)chunk, p.n_f - k_begin);
-            if (r != cached_r || c != cached_c) {
-                __syncthreads();  // previous chunk fully consumed
-                draw_chunk(p, z, r, k_begin, len, chunk, sterm, sw, true);
-                __syncthreads();
-                cached_r = r;
-                cached_c = c;
-            }
-            if (z.shift == 32) accumulate_chunk_anchor<true>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
-            else accumulate_chunk_anchor<false>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
-        }
-        const int64_t n_out = (n_items / n_tiles) * P;
+            __syncthreads();  // previous chunk fully consumed
+            draw_chunk<kAnchorTPB>(p, z, r, k_begin, len, chunk, sterm, sw, true);
+            __syncthreads();
+            for (int64_t item = seg; item < seg_end; ++item) {
+                const int64_t tile = item - r * n_tiles;
+                const int64_t g0 = tile * kAnchorTile + (int64_t)threadIdx.x * kAnchorPPT;
+                const int64_t rem = P - g0;
+                const int nv = rem <= 0 ? 0 : (rem < kAnchorPPT ? (int)rem : kAnchorPPT);  // valid points
+                const float2 a0 = nv > 0 ? *chk(xy, g0, P) : make_float2(0.0f, 0.0f);
+                const float2 a1 = nv > 0 ? *chk(xy, g0 + nv - 1, P) : make_float2(0.0f, 0.0f);
+                const int32_t X0 = __float2int_rn(a0.x * z.xscale), Y0 = __float2int_rn(a0.y * z.xscale);
+                const int32_t X1 = __float2int_rn(a1.x * z.xscale), Y1 = __float2int_rn(a1.y * z.xscale);
+                float2 DX[NP], DY[NP], S[NP];
+                float acc[kAnchorPPT];
 #pragma unroll
-        for (int j = 0; j < kSynthPPT; ++j)
-            if (j < nv) *chk(out, r * P + g0 + j, n_out) = acc[j];
+                for (int j = 0; j < kAnchorPPT; ++j) {
+                    float2 d = make_float2(0.0f, 0.0f);
+                    const bool second = j < nv && anchor_pick(*chk(xy, g0 + j, P), a0, a1, d);
+                    if (j & 1) {
+                        DX[j >> 1].y = d.x;
+                        DY[j >> 1].y = d.y;
+                        S[j >> 1].y = second ? 1.0f : 0.0f;
+                    } else {
+                        DX[j >> 1].x = d.x;
+                        DY[j >> 1].x = d.y;
+                        S[j >> 1].x = second ? 1.0f : 0.0f;
+                    }
+                    acc[j] = (c > 0 && j < nv) ? *chk(out, r * P + g0 + j, n_out) : 0.0f;
+                }
+                if (nv == 0) continue;  // past the last point (the last tile's idle warps skip the terms)
+                if (z.shift == 32) accumulate_chunk_anchor<true>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                else accumulate_chunk_anchor<false>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+#pragma unroll
+                for (int j = 0; j < kAnchorPPT; ++j)
+                    if (j < nv) *chk(out, r * P + g0 + j, n_out) = acc[j];
+            }
+        }
+        seg = seg_end;
     }
 }
 
-// d_bound: [0] the point bound, [1] the anchor bound (k_point_bound).
-// allow_anchor = 0 keeps the exact paths whatever the bounds.
+// The exact kernel.  d_bound: [0] the point bound, [1] the anchor bound
+// (k_point_bound); it returns at once where the anchored path applies
+// (k_synth_anchor, launched beside it, does the work).
 __global__ void __launch_bounds__(kSynthTPB, QRS_SYNTH_MINB) k_synth_fused(DrawParams p, const float2* __restrict__ xy, int64_t P,
                                                            float* __restrict__ out, const float* __restrict__ d_bound,
                                                            float fbound, int chunk, int64_t n_tiles, int64_t n_items,
                                                            int allow_anchor)
 {
     extern __shared__ float4 sterm[];
-    float2* sw = reinterpret_cast<float2*>(sterm + chunk);
     const FixedScales z = fixed_scales(fbound, d_bound[0], QRS_SYNTH_FOLD != 0, kSynthMaxAB);
-    const bool anchored = kAnchorBuilt && allow_anchor != 0 && z.use_fixed &&
-                          (double)fbound * (double)d_bound[1] <= kAnchorTurns;
-    if (anchored) synth_items_anchor(p, xy, P, out, z, chunk, n_tiles, n_items, sterm, sw);
-    else synth_items_exact(p, xy, P, out, z, chunk, n_tiles, n_items, sterm);
+    if (anchor_applies(z, fbound, d_bound, allow_anchor)) return;  // use_fixed does not depend on the fold
+    synth_items_exact(p, xy, P, out, z, chunk, n_tiles, n_items, sterm);
 }
 
-// The fused kernel after the prepass has written d_bound[0..1]: a persistent
-// grid of num_sms x the resident CTAs per SM.
+// The fused form after the prepass has written d_bound[0..1]: the anchored
+// kernel and the exact kernel, each a persistent grid of num_sms x its
+// resident CTAs per SM; the one whose path does not apply returns at once.
 static cudaError_t launch_fused_kernel(int num_sms, const float* d_bound, const DrawParams& p, const float* xy,
-                                      int64_t n_points, int64_t n_real, float* out, int allow_anchor, cudaStream_t s)
+                                      int64_t n_points, int64_t n_real, float* out, int allow_anchor, cudaStream_t s,
+                                      int64_t* launched = nullptr)
 {
+    const float fbound = (float)freq_bound(p);
+    if (kAnchorBuilt && allow_anchor) {
+        const int chunk = (int)(p.n_f < kAnchorChunk ? p.n_f : kAnchorChunk);
+        const size_t smem = (size_t)chunk * kAnchorTermBytes;
+        cudaError_t e = cudaFuncSetAttribute(k_synth_anchor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kAnchorChunk * kAnchorTermBytes);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_synth_anchor, kAnchorTPB, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        const int64_t n_tiles = (n_points + kAnchorTile - 1) / kAnchorTile;
+        const int64_t n_items = n_tiles * n_real;
+        int64_t grid = (int64_t)num_sms * per_sm;
+        if (grid > n_items) grid = n_items;
+        k_synth_anchor<<<(unsigned)grid, kAnchorTPB, smem, s>>>(p, reinterpret_cast<const float2*>(xy), n_points,
+                                                                out, d_bound, fbound, chunk, n_tiles, n_items,
+                                                                allow_anchor);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (launched) ++*launched;
+    }
     const int chunk = (int)(p.n_f < kSynthChunkMax ? p.n_f : kSynthChunkMax);
-    const size_t smem = (size_t)chunk * kSynthTermBytes;
+    const size_t smem = (size_t)chunk * sizeof(float4);
     cudaError_t e = cudaFuncSetAttribute(k_synth_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSynthChunkMax * kSynthTermBytes);
+                                         (int)(kSynthChunkMax * sizeof(float4)));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_synth_fused, kSynthTPB, smem);
@@ -531,8 +603,7 @@ static cudaError_t launch_fused_kernel(int num_sms, const float* d_bound, const 
     int64_t grid = (int64_t)num_sms * per_sm;
     if (grid > n_items) grid = n_items;
     k_synth_fused<<<(unsigned)grid, kSynthTPB, smem, s>>>(p, reinterpret_cast<const float2*>(xy), n_points, out,
-                                                          d_bound, (float)freq_bound(p), chunk, n_tiles, n_items,
-                                                          allow_anchor);
+                                                          d_bound, fbound, chunk, n_tiles, n_items, allow_anchor);
     return cudaGetLastError();
 }
 
@@ -542,7 +613,8 @@ cudaError_t launch_synth_fused(qrs_handle* h, const DrawParams& p, const float* 
     cudaError_t e = launch_point_bound(xy, n_points, h->d_xbound, s);
     if (e != cudaSuccess) return e;
     ++h->launches;
-    return launch_fused_kernel(h->num_sms, h->d_xbound, p, xy, n_points, n_real, out, h->synth_anchor, s);
+    return launch_fused_kernel(h->num_sms, h->d_xbound, p, xy, n_points, n_real, out, h->synth_anchor, s,
+                               &h->launches);
 }
 
 }  // namespace qrs

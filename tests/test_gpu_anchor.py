@@ -1,6 +1,6 @@
 """The fused form's anchored phase path against the FP64 oracle, and its selection.
 
-On the anchored path each group of 12 consecutive points forms the exact
+On the anchored path each group of 16 consecutive points forms the exact
 fixed-point phase (Eq. 3's f . x mod 1) at its first and last point only;
 every point adds its FP32 offset from the nearer of the two.  The path applies
 when fmax times the largest such offset is at most 8 turns; otherwise the
@@ -63,7 +63,7 @@ def _track():
 
 CASES = [
     # the phase screen's 256^2 pupil grid (dx = 8/256 m): groups cross rows,
-    # ragged tail (7001 points: 4.6 tiles of 1536, a 5-point last group),
+    # ragged tail (7001 points: 3.4 tiles of 2048, a 9-point last group),
     # 700 terms (a 60-term last partial sum)
     dict(name="pupil256", pts=lambda: wl.pupil_grid(256, 8.0)[:7001],
          p=dict(domain="logpolar", fmax=16.0), n_f=700, n_real=2, anchored=True),
@@ -81,11 +81,12 @@ CASES = [
     # fewer points than one group
     dict(name="five-points", pts=lambda: _line(5, 0.01, 0.3),
          p=dict(domain="logpolar", fmax=16.0), n_f=300, n_real=3, anchored=True),
-    # a line of 120 points 0.09 m apart: largest offset 5 x 0.09 m, 16 x 0.45 = 7.2 turns
-    dict(name="line-below-limit", pts=lambda: _line(120, 0.09), p=dict(domain="logpolar", fmax=16.0), n_f=300,
+    # a line of 128 points 0.065 m apart (whole groups): largest offset 7 x 0.065 m,
+    # 16 x 0.455 = 7.3 turns
+    dict(name="line-below-limit", pts=lambda: _line(128, 0.065), p=dict(domain="logpolar", fmax=16.0), n_f=300,
          n_real=2, anchored=True),
-    # 0.11 m apart: 16 x 0.55 = 8.8 turns, above the limit: exact paths
-    dict(name="line-above-limit", pts=lambda: _line(120, 0.11), p=dict(domain="logpolar", fmax=16.0), n_f=300,
+    # 0.08 m apart: 16 x 0.56 = 9.0 turns, above the limit: exact paths
+    dict(name="line-above-limit", pts=lambda: _line(128, 0.08), p=dict(domain="logpolar", fmax=16.0), n_f=300,
          n_real=2, anchored=False),
     # the pupil grid in a random order: offsets span the pupil, exact paths
     dict(name="scattered", pts=lambda: wl.pupil_grid(256, 8.0)[np.random.default_rng(5).permutation(51468)[:4000]],
