@@ -58,7 +58,7 @@ print("selftest ok")
 
 
 def test_parity_suites_pass_on_the_checked_build():
-    files = ["tests/test_gpu_parity.py", "tests/test_gpu_edges.py", "tests/test_gpu_grid.py", "tests/test_gpu_gemm.py",
+    files = ["tests/test_gpu_parity.py", "tests/test_gpu_anchor.py", "tests/test_gpu_edges.py", "tests/test_gpu_grid.py", "tests/test_gpu_gemm.py",
              "tests/test_gpu_fft.py", "tests/test_gpu_stats.py", "tests/test_gpu_proposal.py", "tests/test_gpu_fig5.py",
              "tests/test_gpu_batch.py"]
     files = [f for f in files if os.path.exists(os.path.join(ROOT, f))]
