@@ -252,8 +252,8 @@ qrs_status qrs_draw(qrs_handle* h, const qrs_psd* psd, const qrs_domain* dom, co
  *                         (amp, psi: the polar form of (a, b)); col_psd must be
  *                         NULL.  Where each group of 16 consecutive points lies
  *                         within d of the group's first or last point with
- *                         f_max d <= 8 (and the fixed-point phase applies),
- *                         the exact phase is formed at those two anchors
+ *                         f_max d <= 8, the exact phase is formed at those
+ *                         two anchors
  *                         only and each point adds its FP32 offset
  *                         2 pi f . (x_m - x_anchor) (the anchored path; within
  *                         1e-5 of the field standard deviation per value, as

@@ -30,19 +30,20 @@
 // a + b = 55 (fbound * xbound <= 64 with room in the ceilings), the fraction
 // is the low 23 bits of the phase word's high half and needs no shift.
 //
-// Anchored path (the fixed-point path's fast form, Eq. 3 unchanged; its own
-// kernel, k_synth_anchor): each thread takes kAnchorPPT (16) consecutive
-// points, and the group's first and last points are its two anchors.  Per term the thread forms the exact
-// 64-bit fixed-point phase of the two anchors only; every point adds its
-// FP32 offset from the nearer anchor, 2 pi (fx dx + fy dy), to that anchor's
-// phase in radians, so a (point, term) costs three paired FP32 instructions
-// and the cosine instead of two wide integer multiply-adds.  The offset's
-// rounding error grows with f . dx, so the path applies only where the
-// prepass finds every point within dbound of its anchor with
-// fbound * dbound <= kAnchorTurns (8 turns): the error of a term is then at
-// most a few 2^-24 of 2 pi (1 + 2 fbound dbound) radians, and the terms
-// with large f . dx are those with small amplitudes.  Scattered points, or
-// point bounds too large for the fixed-point phase, take the exact paths.
+// Anchored path (Eq. 3 unchanged; its own kernel, k_synth_anchor): each
+// thread takes kAnchorPPT (16) consecutive points, and the group's first and
+// last points are its two anchors.  Per term the thread reduces the phase of
+// the two anchors only, exactly (fixed point, or double-float where the
+// point bound is too large for it); every point adds its FP32 offset from
+// the nearer anchor, 2 pi (fx dx + fy dy), to that anchor's phase in
+// radians, so a (point, term) costs three paired FP32 instructions and the
+// cosine instead of two wide integer multiply-adds (or the double-float
+// reduction).  The offset's rounding error grows with f . dx, so the path
+// applies only where the prepass finds every point within dbound of its
+// anchor with fbound * dbound <= kAnchorTurns (8 turns): the error of a term
+// is then at most a few 2^-24 of 2 pi (1.5 + 2 fbound dbound) radians, and
+// the terms with large f . dx are those with small amplitudes.  Scattered
+// points take the exact paths.
 //
 // Accumulation: every 64 terms a partial sum is folded into the running sum,
 // which keeps the FP32 rounding error of N_f = 4096..16384-term sums near
@@ -240,12 +241,16 @@ __device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restr
 }
 
 // The anchored path's term loop.  Per term: the exact phases of the two
-// anchors (fixed point, radians in [0, 2 pi)), then per pair of points one
-// FFMA2 picks the anchor's phase (S = 0 or 1 against D = A1 - A0; exact for
-// S = 0, within one ulp of A1 for S = 1), two FFMA2 add 2 pi fx dx and
-// 2 pi fy dy, and the cosine and the accumulating FFMA2 follow as in the
-// exact paths.
-template <bool HI>
+// anchors in radians -- fixed point (PH = kAnchorFxHi / kAnchorFx: the
+// anchors' int32 coordinates in X0..Y1, [0, 2 pi)) or double-float
+// (PH = kAnchorDf: their float bits, |phase| <= 3 pi) -- then per pair of
+// points one FFMA2 picks the anchor's phase (S = 0 or 1 against
+// D = A1 - A0; exact for S = 0, within one ulp of A1 for S = 1), two FFMA2
+// add 2 pi fx dx and 2 pi fy dy, and the cosine and the accumulating FFMA2
+// follow as in the exact paths.
+constexpr int kAnchorFxHi = 0, kAnchorFx = 1, kAnchorDf = 2;
+
+template <int PH>
 __device__ __forceinline__ void accumulate_chunk_anchor(const float4* __restrict__ st, const float2* __restrict__ sw,
                                                         int len, int32_t X0, int32_t Y0, int32_t X1, int32_t Y1,
                                                         const float2 (&DX)[kAnchorPPT / 2],
@@ -254,6 +259,9 @@ __device__ __forceinline__ void accumulate_chunk_anchor(const float4* __restrict
                                                         const FixedScales& z)
 {
     constexpr int NP = kAnchorPPT / 2;
+    const float2 two_pi = make_float2(6.28318530717958648f, 6.28318530717958648f);
+    const float2 XA = make_float2(__int_as_float(X0), __int_as_float(X1));
+    const float2 YA = make_float2(__int_as_float(Y0), __int_as_float(Y1));
     for (int k0 = 0; k0 < len; k0 += kSynthGroup) {
         const int k1 = min(k0 + kSynthGroup, len);
         float2 part[NP];
@@ -263,14 +271,23 @@ __device__ __forceinline__ void accumulate_chunk_anchor(const float4* __restrict
         for (int k = k0; k < k1; ++k) {
             const float4 T = *chk(st, k, (int64_t)len);
             const float2 W = *chk(sw, k, (int64_t)len);
-            const uint64_t C = (uint64_t)__float_as_uint(T.w) * z.psi_mul + z.bias;
-            const int32_t Fx = __float_as_int(T.x), Fy = __float_as_int(T.y);
-            const uint32_t m0 = HI ? phase_fx_word_hi(Fx, Fy, X0, Y0, C) : phase_fx_word(Fx, Fy, X0, Y0, C, z.shift);
-            const uint32_t m1 = HI ? phase_fx_word_hi(Fx, Fy, X1, Y1, C) : phase_fx_word(Fx, Fy, X1, Y1, C, z.shift);
-            const float a0 = fmaf(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u), 6.28318530717958648f,
-                                  -6.28318530717958648f);
-            const float a1 = fmaf(__uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u), 6.28318530717958648f,
-                                  -6.28318530717958648f);
+            float a0, a1;
+            if constexpr (PH == kAnchorDf) {
+                const float2 A01 = __fmul2_rn(phase_df2_psi(T.x, T.y, XA, YA, T.w), two_pi);
+                a0 = A01.x;
+                a1 = A01.y;
+            } else {
+                const uint64_t C = (uint64_t)__float_as_uint(T.w) * z.psi_mul + z.bias;
+                const int32_t Fx = __float_as_int(T.x), Fy = __float_as_int(T.y);
+                const uint32_t m0 = PH == kAnchorFxHi ? phase_fx_word_hi(Fx, Fy, X0, Y0, C)
+                                                      : phase_fx_word(Fx, Fy, X0, Y0, C, z.shift);
+                const uint32_t m1 = PH == kAnchorFxHi ? phase_fx_word_hi(Fx, Fy, X1, Y1, C)
+                                                      : phase_fx_word(Fx, Fy, X1, Y1, C, z.shift);
+                a0 = fmaf(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u), 6.28318530717958648f,
+                          -6.28318530717958648f);
+                a1 = fmaf(__uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u), 6.28318530717958648f,
+                          -6.28318530717958648f);
+            }
             const float2 A0 = make_float2(a0, a0);
             const float2 D = make_float2(a1 - a0, a1 - a0);
             const float2 TX = make_float2(W.x, W.x), TY = make_float2(W.y, W.y);
@@ -463,14 +480,15 @@ __device__ __forceinline__ void synth_items_exact(const DrawParams& p, const flo
     }
 }
 
-// Whether the anchored path applies to a launch: the fixed-point phase is
-// available and every point lies within dbound of its anchor with
-// fbound * dbound <= kAnchorTurns.  Both kernels evaluate it from the same
+// Whether the anchored path applies to a launch: every point lies within
+// dbound of its anchor with fbound * dbound <= kAnchorTurns (the anchors'
+// phases are exact on either reduction, so the point bound does not enter).  Both kernels evaluate it from the same
 // prepass output, so exactly one of them does the work.
 __device__ __forceinline__ bool anchor_applies(const FixedScales& z, float fbound, const float* d_bound,
                                                int allow_anchor)
 {
-    return kAnchorBuilt && allow_anchor != 0 && z.use_fixed && (double)fbound * (double)d_bound[1] <= kAnchorTurns;
+    (void)z;
+    return kAnchorBuilt && allow_anchor != 0 && (double)fbound * (double)d_bound[1] <= kAnchorTurns;
 }
 
 // The anchored kernel.  Work items and their split over the persistent grid
@@ -515,8 +533,11 @@ __global__ void __launch_bounds__(kAnchorTPB, QRS_ANCHOR_MINB) k_synth_anchor(Dr
                 const int nv = rem <= 0 ? 0 : (rem < kAnchorPPT ? (int)rem : kAnchorPPT);  // valid points
                 const float2 a0 = nv > 0 ? *chk(xy, g0, P) : make_float2(0.0f, 0.0f);
                 const float2 a1 = nv > 0 ? *chk(xy, g0 + nv - 1, P) : make_float2(0.0f, 0.0f);
-                const int32_t X0 = __float2int_rn(a0.x * z.xscale), Y0 = __float2int_rn(a0.y * z.xscale);
-                const int32_t X1 = __float2int_rn(a1.x * z.xscale), Y1 = __float2int_rn(a1.y * z.xscale);
+                // the anchors as the phase reduction takes them: int32 at scale 2^b, or float bits
+                const int32_t X0 = z.use_fixed ? __float2int_rn(a0.x * z.xscale) : __float_as_int(a0.x);
+                const int32_t Y0 = z.use_fixed ? __float2int_rn(a0.y * z.xscale) : __float_as_int(a0.y);
+                const int32_t X1 = z.use_fixed ? __float2int_rn(a1.x * z.xscale) : __float_as_int(a1.x);
+                const int32_t Y1 = z.use_fixed ? __float2int_rn(a1.y * z.xscale) : __float_as_int(a1.y);
                 float2 DX[NP], DY[NP], S[NP];
                 float acc[kAnchorPPT];
 #pragma unroll
@@ -535,8 +556,12 @@ __global__ void __launch_bounds__(kAnchorTPB, QRS_ANCHOR_MINB) k_synth_anchor(Dr
                     acc[j] = (c > 0 && j < nv) ? *chk(out, r * P + g0 + j, n_out) : 0.0f;
                 }
                 if (nv == 0) continue;  // past the last point (the last tile's idle warps skip the terms)
-                if (z.shift == 32) accumulate_chunk_anchor<true>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
-                else accumulate_chunk_anchor<false>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                if (!z.use_fixed)
+                    accumulate_chunk_anchor<kAnchorDf>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                else if (z.shift == 32)
+                    accumulate_chunk_anchor<kAnchorFxHi>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                else
+                    accumulate_chunk_anchor<kAnchorFx>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
 #pragma unroll
                 for (int j = 0; j < kAnchorPPT; ++j)
                     if (j < nv) *chk(out, r * P + g0 + j, n_out) = acc[j];

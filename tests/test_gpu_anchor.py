@@ -1,7 +1,8 @@
 """The fused form's anchored phase path against the FP64 oracle, and its selection.
 
 On the anchored path each group of 16 consecutive points forms the exact
-fixed-point phase (Eq. 3's f . x mod 1) at its first and last point only;
+phase (Eq. 3's f . x mod 1, fixed point or double-float) at its first and
+last point only;
 every point adds its FP32 offset from the nearer of the two.  The path applies
 when fmax times the largest such offset is at most 8 turns; otherwise the
 exact per-point paths run.  Tolerance: the field tolerance of every synthesis
@@ -73,6 +74,10 @@ CASES = [
     # literal Eq. 3 coefficients, square domain
     dict(name="pupil256-square-eq3", pts=lambda: wl.pupil_grid(256, 8.0)[9000:12000],
          p=dict(domain="square", fmax=4.0, coef="eq3"), n_f=37 * 37, n_real=2, anchored=True),
+    # the pupil grid 170 m off the origin: f_max |x| far above the fixed-point
+    # limit, so the anchors take the double-float reduction
+    dict(name="pupil256-offset-df", pts=lambda: wl.pupil_grid(256, 8.0)[:5000] + np.float32([150.0, -80.0]),
+         p=dict(domain="logpolar", fmax=16.0), n_f=600, n_real=2, anchored=True),
     # the Sec. 4.3 tracks with the Eq. 7 piston PSD: |x| up to 56.5 m, a group
     # that straddles the two tracks takes one anchor on each
     dict(name="track-piston", pts=_track,
