@@ -144,13 +144,23 @@ __device__ __forceinline__ bool anchor_pick(float2 v, float2 a0, float2 a1, floa
 // to pick its phase path and scales.
 __global__ void k_point_bound(const float2* __restrict__ xy, int64_t n, float* __restrict__ out)
 {
+    static_assert(32 % kAnchorPPT == 0, "an anchor group is a whole part of a warp");
     float m = 0.0f, dm = 0.0f;
     bool finite = true;
-    for (int64_t g0 = (int64_t)threadIdx.x * kAnchorPPT; g0 < n; g0 += (int64_t)blockDim.x * kAnchorPPT) {
-        const int nv = (int)min((int64_t)kAnchorPPT, n - g0);
-        const float2 a0 = xy[g0], a1 = xy[g0 + nv - 1];
-        for (int j = 0; j < nv; ++j) {
-            const float2 v = xy[g0 + j];
+    const int lane = threadIdx.x & 31;
+    const int first = lane & ~(kAnchorPPT - 1);  // lane of the group's first point
+    // each pass reads blockDim.x consecutive points (coalesced); a group's
+    // points sit in kAnchorPPT neighbouring lanes and meet through shuffles
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t g0 = i - (lane - first);
+        const int64_t left = n - g0;
+        const int nv = left <= 0 ? 1 : (left < kAnchorPPT ? (int)left : kAnchorPPT);
+        const float2 v = i < n ? xy[i] : make_float2(0.0f, 0.0f);
+        const float2 a0 = make_float2(__shfl_sync(0xffffffffu, v.x, first), __shfl_sync(0xffffffffu, v.y, first));
+        const float2 a1 = make_float2(__shfl_sync(0xffffffffu, v.x, first + nv - 1),
+                                      __shfl_sync(0xffffffffu, v.y, first + nv - 1));
+        if (i < n) {
             finite = finite && isfinite(v.x) && isfinite(v.y);
             m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
             float2 d;
