@@ -151,21 +151,33 @@ __global__ void k_point_bound(const float2* __restrict__ xy, int64_t n, float* _
     const int first = lane & ~(kAnchorPPT - 1);  // lane of the group's first point
     // each pass reads blockDim.x consecutive points (coalesced); a group's
     // points sit in kAnchorPPT neighbouring lanes and meet through shuffles
-    for (int64_t base = 0; base < n; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const int64_t g0 = i - (lane - first);
-        const int64_t left = n - g0;
-        const int nv = left <= 0 ? 1 : (left < kAnchorPPT ? (int)left : kAnchorPPT);
-        const float2 v = i < n ? xy[i] : make_float2(0.0f, 0.0f);
-        const float2 a0 = make_float2(__shfl_sync(0xffffffffu, v.x, first), __shfl_sync(0xffffffffu, v.y, first));
-        const float2 a1 = make_float2(__shfl_sync(0xffffffffu, v.x, first + nv - 1),
-                                      __shfl_sync(0xffffffffu, v.y, first + nv - 1));
-        if (i < n) {
-            finite = finite && isfinite(v.x) && isfinite(v.y);
-            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-            float2 d;
-            anchor_pick(v, a0, a1, d);
-            dm = fmaxf(dm, fmaxf(fabsf(d.x), fabsf(d.y)));
+    // (four passes' loads issued together, so that a single CTA keeps enough
+    // of them in flight)
+    constexpr int kLoads = 4;
+    for (int64_t base = 0; base < n; base += (int64_t)kLoads * blockDim.x) {
+        float2 v[kLoads];
+#pragma unroll
+        for (int u = 0; u < kLoads; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+            v[u] = i < n ? xy[i] : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < kLoads; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x + threadIdx.x;
+            const int64_t g0 = i - (lane - first);
+            const int64_t left = n - g0;
+            const int nv = left <= 0 ? 1 : (left < kAnchorPPT ? (int)left : kAnchorPPT);
+            const float2 a0 = make_float2(__shfl_sync(0xffffffffu, v[u].x, first),
+                                          __shfl_sync(0xffffffffu, v[u].y, first));
+            const float2 a1 = make_float2(__shfl_sync(0xffffffffu, v[u].x, first + nv - 1),
+                                          __shfl_sync(0xffffffffu, v[u].y, first + nv - 1));
+            if (i < n) {
+                finite = finite && isfinite(v[u].x) && isfinite(v[u].y);
+                m = fmaxf(m, fmaxf(fabsf(v[u].x), fabsf(v[u].y)));
+                float2 d;
+                anchor_pick(v[u], a0, a1, d);
+                dm = fmaxf(dm, fmaxf(fabsf(d.x), fabsf(d.y)));
+            }
         }
     }
     if (!finite) dm = INFINITY;
