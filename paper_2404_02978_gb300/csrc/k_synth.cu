@@ -121,8 +121,10 @@ constexpr int kSynthMaxAB = (QRS_SYNTH_PAIRED && QRS_SYNTH_FOLD) ? 55 : 54;
 constexpr bool kAnchorBuilt = QRS_SYNTH_ANCHOR && QRS_SYNTH_PAIRED && QRS_SYNTH_FOLD;
 constexpr double kAnchorTurns = 8.0;  // ceiling of fbound * dbound on the anchored path
 // Shared memory per cached term of the anchored kernel: the 16-byte record
-// and 2 pi (fx, fy).
-constexpr int kAnchorTermBytes = (int)(sizeof(float4) + sizeof(float2));
+// and {2 pi fx, 2 pi fy, C} with C the term's 64-bit addend of the
+// fixed-point phase word (phase offset and rounding bias), formed once in
+// the draw instead of once per thread.
+constexpr int kAnchorTermBytes = (int)(sizeof(float4) + sizeof(float4));
 
 // The anchor of a point of its group (first point a0, last point a1): the
 // nearer in the max norm, ties to a0.  Returns true for a1 and the FP32
@@ -273,7 +275,7 @@ __device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restr
 constexpr int kAnchorFxHi = 0, kAnchorFx = 1, kAnchorDf = 2;
 
 template <int PH>
-__device__ __forceinline__ void accumulate_chunk_anchor(const float4* __restrict__ st, const float2* __restrict__ sw,
+__device__ __forceinline__ void accumulate_chunk_anchor(const float4* __restrict__ st, const float4* __restrict__ sw,
                                                         int len, int32_t X0, int32_t Y0, int32_t X1, int32_t Y1,
                                                         const float2 (&DX)[kAnchorPPT / 2],
                                                         const float2 (&DY)[kAnchorPPT / 2],
@@ -292,23 +294,24 @@ __device__ __forceinline__ void accumulate_chunk_anchor(const float4* __restrict
 #pragma unroll kAnchorUnroll
         for (int k = k0; k < k1; ++k) {
             const float4 T = *chk(st, k, (int64_t)len);
-            const float2 W = *chk(sw, k, (int64_t)len);
+            const float4 W = *chk(sw, k, (int64_t)len);
             float a0, a1;
             if constexpr (PH == kAnchorDf) {
                 const float2 A01 = __fmul2_rn(phase_df2_psi(T.x, T.y, XA, YA, T.w), two_pi);
                 a0 = A01.x;
                 a1 = A01.y;
             } else {
-                const uint64_t C = (uint64_t)__float_as_uint(T.w) * z.psi_mul + z.bias;
+                const uint64_t C = ((uint64_t)__float_as_uint(W.w) << 32) | (uint64_t)__float_as_uint(W.z);
                 const int32_t Fx = __float_as_int(T.x), Fy = __float_as_int(T.y);
                 const uint32_t m0 = PH == kAnchorFxHi ? phase_fx_word_hi(Fx, Fy, X0, Y0, C)
                                                       : phase_fx_word(Fx, Fy, X0, Y0, C, z.shift);
                 const uint32_t m1 = PH == kAnchorFxHi ? phase_fx_word_hi(Fx, Fy, X1, Y1, C)
                                                       : phase_fx_word(Fx, Fy, X1, Y1, C, z.shift);
-                a0 = fmaf(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u), 6.28318530717958648f,
-                          -6.28318530717958648f);
-                a1 = fmaf(__uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u), 6.28318530717958648f,
-                          -6.28318530717958648f);
+                const float2 A01 = __ffma2_rn(make_float2(__uint_as_float((m0 & 0x007FFFFFu) | 0x3F800000u),
+                                                          __uint_as_float((m1 & 0x007FFFFFu) | 0x3F800000u)),
+                                              two_pi, make_float2(-6.28318530717958648f, -6.28318530717958648f));
+                a0 = A01.x;
+                a1 = A01.y;
             }
             const float2 A0 = make_float2(a0, a0);
             const float2 D = make_float2(a1 - a0, a1 - a0);
@@ -408,10 +411,11 @@ __device__ __forceinline__ void accumulate_chunk(const float4* __restrict__ st, 
 }
 
 // Draws terms [k_begin, k_begin + len) of realisation r into the CTA's
-// shared-memory records (and, for the anchored path, 2 pi (fx, fy)).
+// shared-memory records (and, for the anchored path, 2 pi (fx, fy) and the
+// fixed-point addend C).
 template <int TPB>
 __device__ __forceinline__ void draw_chunk(const DrawParams& p, const FixedScales& z, int64_t r, int64_t k_begin,
-                                           int len, int chunk, float4* __restrict__ sterm, float2* __restrict__ sw,
+                                           int len, int chunk, float4* __restrict__ sterm, float4* __restrict__ sw,
                                            bool anchored)
 {
     const uint64_t n0 = (uint64_t)(p.real_offset + r) * (uint64_t)p.n_f + (uint64_t)k_begin;
@@ -433,7 +437,11 @@ __device__ __forceinline__ void draw_chunk(const DrawParams& p, const FixedScale
         }
         rec.z = t.F * amp;
         *chk(sterm, q, (int64_t)chunk) = rec;
-        if (anchored) *chk(sw, q, (int64_t)chunk) = make_float2(t.fx * 6.28318530717958648f, t.fy * 6.28318530717958648f);
+        if (anchored) {
+            const uint64_t C = z.use_fixed ? (uint64_t)u * z.psi_mul + z.bias : 0ull;
+            *chk(sw, q, (int64_t)chunk) = make_float4(t.fx * 6.28318530717958648f, t.fy * 6.28318530717958648f,
+                                                      __uint_as_float((uint32_t)C), __uint_as_float((uint32_t)(C >> 32)));
+        }
     }
 }
 
@@ -530,7 +538,7 @@ __global__ void __launch_bounds__(kAnchorTPB, QRS_ANCHOR_MINB) k_synth_anchor(Dr
                                                               int allow_anchor)
 {
     extern __shared__ float4 sterm[];
-    float2* sw = reinterpret_cast<float2*>(sterm + chunk);
+    float4* sw = reinterpret_cast<float4*>(sterm + chunk);
     const FixedScales z = fixed_scales(fbound, d_bound[0], true, kSynthMaxAB);
     if (!anchor_applies(z, fbound, d_bound, allow_anchor)) return;  // k_synth_fused does the work
     constexpr int NP = kAnchorPPT / 2;
