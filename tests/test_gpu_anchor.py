@@ -83,6 +83,11 @@ CASES = [
     dict(name="track-piston", pts=_track,
          p=dict(domain="square", fmax=0.25, L0=22.0, r0=0.10, ap_D=8.0, ap_d=1.1), n_f=44 * 44, n_real=2,
          anchored=True),
+    # one term, and one term past a whole 64-term partial sum
+    dict(name="one-term", pts=lambda: wl.pupil_grid(256, 8.0)[3000:3500],
+         p=dict(domain="logpolar", fmax=16.0), n_f=1, n_real=3, anchored=True),
+    dict(name="65-terms", pts=lambda: wl.pupil_grid(256, 8.0)[3000:3500],
+         p=dict(domain="logpolar", fmax=16.0), n_f=65, n_real=3, anchored=True),
     # fewer points than one group
     dict(name="five-points", pts=lambda: _line(5, 0.01, 0.3),
          p=dict(domain="logpolar", fmax=16.0), n_f=300, n_real=3, anchored=True),

@@ -46,6 +46,8 @@ def test_noalloc_matches_handle_entry_point_twice():
         (qrs.params(seed=51), 700, 3, wl.pupil_grid(96, 8.0)),
         # baselines to 150 m: double-float phase path (the point bound in scratch changes)
         (qrs.params(seed=52, fmax=2.0), 300, 2, rng.uniform(-150, 150, size=(3001, 2)).astype(np.float32)),
+        # rows of the phase screen's grid: the anchored kernel (the anchor bound in scratch)
+        (qrs.params(seed=53), 500, 2, wl.pupil_grid(256, 8.0)[:4001]),
     ]
     for p, n_f, n_real, xy_np in cases:
         xy = torch.from_numpy(xy_np).cuda()
@@ -59,6 +61,7 @@ def test_noalloc_matches_handle_entry_point_twice():
         sig = torch.sqrt(torch.mean(ref.double() ** 2, dim=1, keepdim=True))
         err = ((out.double() - ref.double()).abs() / sig).max().item()
         assert err <= TOL_FIELD, err
+        assert torch.equal(out, ref)  # the same kernels on the same launch shapes
     # the contract itself: a warm call leaves the device's free memory unchanged
     p, n_f, n_real, xy_np = cases[0]
     xy = torch.from_numpy(xy_np).cuda()
