@@ -54,8 +54,8 @@ L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq-term evals/s"
 UNIT = "term/s"
 # DRAM bytes (read + write) per k_synth_anchor launch on the workload above, from the ncu launch
-# list summarised in profiles/k_synth_anchor_phase_screen.md (36.82 MB read + 256.32 MB write).
-SYNTH_TRAFFIC_BYTES = 293.14e6
+# list summarised in profiles/k_synth_anchor_phase_screen.md (35.60 MB read + 254.86 MB write).
+SYNTH_TRAFFIC_BYTES = 290.46e6
 # The anchored path's group and ceiling (k_synth.cu: kAnchorPPT, kAnchorTurns), used only to label
 # which path the workload takes.
 ANCHOR_GROUP = 16
