@@ -1,7 +1,9 @@
 // k_synth.cu -- K2: fused per-realisation draw + cosine-accumulate (Eq. 3 at
-// arbitrary points), and the point-bound prepass that picks its phase path.
+// arbitrary points): the point-bound prepass that picks the phase path, the
+// anchored kernel (k_synth_anchor) and the exact kernel (k_synth_fused); both
+// kernels are launched and the one whose path does not apply returns at once.
 //
-// Work decomposition.  A work item is (realisation r, tile of TPB*PPT points);
+// Work decomposition of the exact kernel.  A work item is (realisation r, tile of TPB*PPT points);
 // items are numbered realisation-major and each CTA of a persistent grid (a
 // whole number of CTAs per SM) takes one contiguous range of them, so it
 // visits few realisations.  The N_f terms of the current realisation are
@@ -43,7 +45,9 @@
 // anchor with fbound * dbound <= kAnchorTurns (8 turns): the error of a term
 // is then at most a few 2^-24 of 2 pi (1.5 + 2 fbound dbound) radians, and
 // the terms with large f . dx are those with small amplitudes.  Scattered
-// points take the exact paths.
+// points take the exact paths.  The anchored kernel takes its terms in small
+// chunks per realisation segment and carries each point's running sum from
+// chunk to chunk in the output, so three CTAs fit on an SM.
 //
 // Accumulation: every 64 terms a partial sum is folded into the running sum,
 // which keeps the FP32 rounding error of N_f = 4096..16384-term sums near
