@@ -278,7 +278,7 @@ __device__ __forceinline__ void accumulate_chunk_fx_paired(const float4* __restr
 // follow as in the exact paths.
 constexpr int kAnchorFxHi = 0, kAnchorFx = 1, kAnchorDf = 2;
 
-template <int PH>
+template <int PH, bool DY0>
 __device__ __forceinline__ void accumulate_chunk_anchor(const float4* __restrict__ st, const float4* __restrict__ sw,
                                                         int len, int32_t X0, int32_t Y0, int32_t X1, int32_t Y1,
                                                         const float2 (&DX)[kAnchorPPT / 2],
@@ -325,7 +325,7 @@ __device__ __forceinline__ void accumulate_chunk_anchor(const float4* __restrict
             for (int q = 0; q < NP; ++q) {
                 float2 ang = __ffma2_rn(S[q], D, A0);
                 ang = __ffma2_rn(TX, DX[q], ang);
-                ang = __ffma2_rn(TY, DY[q], ang);
+                if constexpr (!DY0) ang = __ffma2_rn(TY, DY[q], ang);  // DY0: every dy is 0, fma(ty, 0, a) = a
                 const float2 c = make_float2(__cosf(ang.x), __cosf(ang.y));
                 part[q] = __ffma2_rn(A, c, part[q]);
             }
@@ -574,6 +574,7 @@ __global__ void __launch_bounds__(kAnchorTPB, QRS_ANCHOR_MINB) k_synth_anchor(Dr
                 const int32_t Y1 = z.use_fixed ? __float2int_rn(a1.y * z.xscale) : __float_as_int(a1.y);
                 float2 DX[NP], DY[NP], S[NP];
                 float acc[kAnchorPPT];
+                bool dy0 = true;  // every point on its anchor's row (grids in row order, tracks along x)
 #pragma unroll
                 for (int j = 0; j < kAnchorPPT; ++j) {
                     float2 d = make_float2(0.0f, 0.0f);
@@ -588,14 +589,22 @@ __global__ void __launch_bounds__(kAnchorTPB, QRS_ANCHOR_MINB) k_synth_anchor(Dr
                         S[j >> 1].x = second ? 1.0f : 0.0f;
                     }
                     acc[j] = (c > 0 && j < nv) ? *chk(out, r * P + g0 + j, n_out) : 0.0f;
+                    dy0 = dy0 && d.y == 0.0f;
                 }
+                // a warp whose offsets are all along x drops the y product: the
+                // same sums bit for bit, one paired instruction fewer per pair
+                dy0 = __all_sync(0xffffffffu, dy0);
                 if (nv == 0) continue;  // past the last point (the last tile's idle warps skip the terms)
-                if (!z.use_fixed)
-                    accumulate_chunk_anchor<kAnchorDf>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
-                else if (z.shift == 32)
-                    accumulate_chunk_anchor<kAnchorFxHi>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
-                else
-                    accumulate_chunk_anchor<kAnchorFx>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                if (!z.use_fixed) {
+                    if (dy0) accumulate_chunk_anchor<kAnchorDf, true>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                    else accumulate_chunk_anchor<kAnchorDf, false>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                } else if (z.shift == 32) {
+                    if (dy0) accumulate_chunk_anchor<kAnchorFxHi, true>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                    else accumulate_chunk_anchor<kAnchorFxHi, false>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                } else {
+                    if (dy0) accumulate_chunk_anchor<kAnchorFx, true>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                    else accumulate_chunk_anchor<kAnchorFx, false>(sterm, sw, len, X0, Y0, X1, Y1, DX, DY, S, acc, z);
+                }
 #pragma unroll
                 for (int j = 0; j < kAnchorPPT; ++j)
                     if (j < nv) *chk(out, r * P + g0 + j, n_out) = acc[j];
