@@ -54,14 +54,15 @@ L2_FLUSH_BYTES = 256 << 20
 METRIC = "freq-term evals/s"
 UNIT = "term/s"
 # DRAM bytes (read + write) per k_synth_anchor launch on the workload above, from the ncu launch
-# list summarised in profiles/k_synth_anchor_phase_screen.md (35.60 MB read + 254.86 MB write).
-SYNTH_TRAFFIC_BYTES = 290.46e6
+# list summarised in profiles/k_synth_anchor_phase_screen.md (37.62 MB read + 260.71 MB write).
+SYNTH_TRAFFIC_BYTES = 298.33e6
 # The anchored path's group and ceiling (k_synth.cu: kAnchorPPT, kAnchorTurns), used only to label
 # which path the workload takes.
 ANCHOR_GROUP = 16
 ANCHOR_TURNS = 8.0
 # FP32-pipe operations per (point, term) on the anchored path: the anchor's phase picked (1), the
-# offsets fx dx and fy dy (2), the radian-to-turn product of the cosine (1), the accumulation (1).
+# offsets fx dx and fy dy (2; 1 where every offset of a warp lies along x), the radian-to-turn
+# product of the cosine (1), the accumulation (1).  The cosine binds either way.
 ANCHOR_FMA_OPS = 5
 
 
